@@ -1,0 +1,99 @@
+"""Nonlinear shallow-water pieces (paper Sec. 3, Eq. 1-3; Sec. 4.4 Strang splitting).
+
+N(U) is the third column of the paper's split (Eq. sw_compact):
+
+    N_Phi   = -V.grad Phi' - Phi' div V     = -div(Phi' V)
+    N_zeta  = -div(zeta V)
+    N_delta =  k.curl(zeta V) - lap (V.V / 2)
+
+evaluated pseudo-spectrally: V from psi = lap^-1 zeta and chi = lap^-1 delta (Sec. 3), products
+on the Gauss grid, divergence / curl / Laplacian by analysis.
+
+Time integrators (Sec. 4.1, 4.4; Table 2):
+  * erk  : 2nd-order explicit Runge-Kutta.  Reading taken (the paper does not name the
+           variant): the midpoint rule.
+  * ver1 : T(U) = N^{dt/2} o L^{dt} o N^{dt/2} (U), the linear part L = L_g + L_c by REXI
+           (method id l_rexi_n_erk_ver1, Coriolis inside REXI).
+  * ver0 : T(U) = L^{dt/2} o N^{dt} o L^{dt/2} (U).
+  * rk4  : classical 4th-order Runge-Kutta of the full system, used as the small-step
+           reference (the paper's reference solution uses RK4 with a tiny step, Sec. 5).
+"""
+import numpy as np
+
+from . import linop, rexi, sht
+
+
+def nonlinear(U, grid):
+    """N(U) for U[3, nlm] = (Phi', zeta, delta) on the Gauss grid of `grid`."""
+    T, a = grid.T, grid.a
+    Phi, zeta, delta = U
+    psi = sht.inv_laplacian(zeta, T, a)
+    chi = sht.inv_laplacian(delta, T, a)
+    Pg = grid.synth(Phi)
+    Zg = grid.synth(zeta)
+    Ug, Vg = grid.synth_uv(psi, chi)
+    div1, _ = grid.analys_divcurl(Pg * Ug, Pg * Vg)
+    div2, cur2 = grid.analys_divcurl(Zg * Ug, Zg * Vg)
+    ke = (Ug * Ug + Vg * Vg) / (2.0 * grid.coslat2[:, None])
+    kes = grid.analys(ke)
+    lap = sht.laplacian_eig(T, a)
+    out = np.empty_like(U, dtype=np.complex128)
+    out[0] = -div1
+    out[1] = -div2
+    out[2] = cur2 - lap * kes
+    out[1, 0] = 0.0
+    out[2, 0] = 0.0
+    return out
+
+
+def rk2_nonlinear(U, grid, tau):
+    """Integrate dU/dt = N(U) over tau with the midpoint rule (erk, 2nd order)."""
+    k1 = nonlinear(U, grid)
+    k2 = nonlinear(U + 0.5 * tau * k1, grid)
+    return U + tau * k2
+
+
+def strang_ver1(U, grid, dt, Omega, Phibar, z, w):
+    """One step of l_rexi_n_erk_ver1:  N^{dt/2} o L^{dt} o N^{dt/2}  (Sec. 4.4, version 1)."""
+    T, a = grid.T, grid.a
+    U1 = rk2_nonlinear(U, grid, 0.5 * dt)
+    U2 = rexi.rexi_step(U1, T, dt, Omega, a, Phibar, z, w)
+    return rk2_nonlinear(U2, grid, 0.5 * dt)
+
+
+def strang_ver0(U, grid, dt, Omega, Phibar, z_half, w_half):
+    """One step of l_rexi_n_erk_ver0:  L^{dt/2} o N^{dt} o L^{dt/2}  (Sec. 4.4, version 0);
+    z_half, w_half are REXI coefficients for a step of dt/2."""
+    T, a = grid.T, grid.a
+    U1 = rexi.rexi_step(U, T, 0.5 * dt, Omega, a, Phibar, z_half, w_half)
+    U2 = rk2_nonlinear(U1, grid, dt)
+    return rexi.rexi_step(U2, T, 0.5 * dt, Omega, a, Phibar, z_half, w_half)
+
+
+def full_tendency(U, grid, Omega, Phibar):
+    """dU/dt = L U + N(U) (Eq. sw_compact with L = L_g + L_c)."""
+    return linop.apply_L(U, grid.T, Omega, grid.a, Phibar) + nonlinear(U, grid)
+
+
+def rk4_full(U, grid, dt, nsub, Omega, Phibar):
+    """nsub classical RK4 steps of the full SWE over a total time dt."""
+    h = dt / nsub
+    for _ in range(nsub):
+        k1 = full_tendency(U, grid, Omega, Phibar)
+        k2 = full_tendency(U + 0.5 * h * k1, grid, Omega, Phibar)
+        k3 = full_tendency(U + 0.5 * h * k2, grid, Omega, Phibar)
+        k4 = full_tendency(U + h * k3, grid, Omega, Phibar)
+        U = U + (h / 6.0) * (k1 + 2 * k2 + 2 * k3 + k4)
+    return U
+
+
+def rk4_linear(U, T, dt, nsub, Omega, radius, Phibar):
+    """nsub classical RK4 steps of dU/dt = L U over a total time dt (pin P6)."""
+    h = dt / nsub
+    for _ in range(nsub):
+        k1 = linop.apply_L(U, T, Omega, radius, Phibar)
+        k2 = linop.apply_L(U + 0.5 * h * k1, T, Omega, radius, Phibar)
+        k3 = linop.apply_L(U + 0.5 * h * k2, T, Omega, radius, Phibar)
+        k4 = linop.apply_L(U + h * k3, T, Omega, radius, Phibar)
+        U = U + (h / 6.0) * (k1 + 2 * k2 + 2 * k3 + k4)
+    return U

@@ -1,0 +1,105 @@
+"""Pins of the oracle's nonlinear term and Strang step (Sec. 3 Eq. 1-3, Sec. 4.4).
+
+* Steady zonal flow in gradient-wind balance (the standard solid-body-rotation state,
+  u = u0 cos(lat), g h = g h0 - (a Omega u0 + u0^2/2) sin^2(lat)) is a fixed point of the
+  full tendency L U + N(U): this pins the curl / kinetic-energy part of N_delta with a
+  closed form.
+* The flux forms -div(Phi' V), -div(zeta V), k.curl(zeta V) equal their advective forms
+  -(V.grad q + q delta) and zeta^2 + (dq/dx v - dq/dy u), computed through a different
+  route (scalar gradients on the grid), to rounding.
+* Strang ver1 with REXI converges at 2nd order to a small-step RK4 reference (the paper's
+  own reference is RK4 with a tiny step, Sec. 5).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import coeffs, linop, rexi, sht, swe
+from paper_1805_06557_gb300 import synthetic as syn
+
+OM, A, PB = syn.OMEGA, syn.RADIUS, syn.PHIBAR
+
+
+def _tc2(T, grid, u0=38.61):
+    U = np.zeros((3, sht.nlm(T)), complex)
+    U[1, sht.idx(T, 0, 1)] = 2 * u0 / A / math.sqrt(3 / (4 * math.pi))
+    phi = -(A * OM * u0 + 0.5 * u0 * u0) * (grid.mu[:, None] ** 2) * np.ones((1, grid.nlon))
+    U[0] = grid.analys(phi)
+    return U
+
+
+def test_steady_zonal_flow_full_tendency():
+    T, nlat, nlon = 15, 24, 48
+    g = sht.Grid(T, nlat, nlon, A)
+    U = _tc2(T, g)
+    L = linop.apply_L(U, T, OM, A, PB)
+    N = swe.nonlinear(U, g)
+    tot = L + N
+    for f in (0, 2):
+        scale = max(np.max(np.abs(L[f])), np.max(np.abs(N[f])), 1e-300)
+        assert np.max(np.abs(tot[f])) < 1e-10 * scale
+    assert np.max(np.abs(tot[1])) < 1e-10 * np.max(np.abs(L[2]))
+    # the nonlinear part alone is not zero: the balance needs the u0^2/2 term
+    assert np.max(np.abs(N[2])) > 1e-3 * np.max(np.abs(L[2]))
+
+
+def _grad_grid(grid, q):
+    """(1 - mu^2) dq/dmu and dq/dlambda on the grid, through synth_uv(-a q, 0)."""
+    Uq, Vq = grid.synth_uv(-grid.a * q, np.zeros_like(q))
+    return Uq, -Vq
+
+
+@pytest.mark.parametrize("T,nlat,nlon", [(15, 24, 48), (21, 33, 66)])
+def test_flux_vs_advective_forms(T, nlat, nlon):
+    g = sht.Grid(T, nlat, nlon, A)
+    U = syn.gaussian_state(T, 5, scales=(1e3, 2e-5, 5e-6))
+    N = swe.nonlinear(U, g)
+    Phi, zeta, delta = U
+    psi = sht.inv_laplacian(zeta, T, A)
+    chi = sht.inv_laplacian(delta, T, A)
+    Ug, Vg = g.synth_uv(psi, chi)
+    c2 = g.coslat2[:, None]
+    Dg = g.synth(delta)
+    lap = sht.laplacian_eig(T, A)
+    for f, q in ((0, Phi), (1, zeta)):
+        qg = g.synth(q)
+        dmu, dlam = _grad_grid(g, q)
+        adv = (Ug * dlam + Vg * dmu) / (A * c2)
+        ref = -g.analys(adv + qg * Dg)
+        ref[0] = N[f][0]
+        assert np.linalg.norm(N[f] - ref) <= 1e-11 * np.linalg.norm(ref)
+    Zg = g.synth(zeta)
+    dmu, dlam = _grad_grid(g, zeta)
+    curl = Zg * Zg + (dlam * Vg - dmu * Ug) / (A * c2)
+    ke = (Ug * Ug + Vg * Vg) / (2 * c2)
+    ref = g.analys(curl) - lap * g.analys(ke)
+    ref[0] = 0
+    assert np.linalg.norm(N[2] - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+def test_mass_conservation():
+    T = 15
+    g = sht.Grid(T, 24, 48, A)
+    N = swe.nonlinear(syn.balanced_state(T, 2), g)
+    assert abs(N[0][0]) < 1e-12 * np.max(np.abs(N[0]))
+
+
+def test_strang_ver1_second_order():
+    T, nlat, nlon = 15, 24, 48
+    g = sht.Grid(T, nlat, nlon, A)
+    U0 = syn.balanced_state(T, 2, urms=40.0)
+    U0[2] = syn.gaussian_state(T, 8, scales=(0, 0, 2e-6))[2]   # add some divergence
+    t_end = 4 * 1800.0
+    ref = swe.rk4_full(U0, g, t_end, 240, OM, PB)
+    errs = []
+    for dt in (1800.0, 900.0, 450.0):
+        X = rexi.spectrum_bound(T, dt, OM, A, PB)
+        # the circle through p0 and +-iXc must not pass close to the origin: p0 <= Xc
+        z, w = coeffs.rexi_coefficients(128, min(6.0, 1.6 * X), 1.6 * X)
+        U = U0
+        for _ in range(int(round(t_end / dt))):
+            U = swe.strang_ver1(U, g, dt, OM, PB, z, w)
+        errs.append(float(np.max(rexi.rel_l2(U, ref, T))))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(1.7 < r < 2.5 for r in rates), (errs, rates)
