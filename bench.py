@@ -1,0 +1,328 @@
+#!/usr/bin/env python3
+"""Benchmark of the REXI linear step (arXiv 1805.06557, Eq. rexi) on GB300.
+
+Workload: T255 spectral states (geopotential, vorticity, divergence; n^-1.5 Gaussian
+coefficients, seeded), N = 512 Cauchy-contour poles (p0 = 14, Xc = 1.4 X), dt = 3600 s,
+a batch of 16 independent states per rank per step.  One step = one rexi_step call on the
+batch (pre-pass, light/heavy mixed-precision solves with the fused pole sums, finalize).
+
+Headline `value`: state-steps/s of the batched mixed-precision plan (all ranks).  Also
+reported: the plain FP64 plan one state at a time and batched, the mixed plan one state at
+a time, p50/p99 step latency, the mixed-vs-FP64 error, the dominant kernel's roofline, the
+end-to-end rate through rexi_step_host with host buffers, and the CPU oracle.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "REXI steps/s at T255, batched/mixed vs plain FP64 at ≤1e-8 rel err; p50/p99"
+T_DEF, N_DEF, DT_DEF, B_DEF = 255, 512, 3600.0, 16
+SAMPLE_M = list(range(0, 256, 2))      # cpu_baseline sample: every second zonal order
+REF_STEP_M = [0, 85, 170, 254]         # --impl reference: zonal orders solved per step
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=B_DEF)
+    ap.add_argument("--T", type=int, default=T_DEF)
+    ap.add_argument("--N", type=int, default=N_DEF)
+    ap.add_argument("--dt", type=float, default=DT_DEF)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    return ap.parse_args()
+
+
+def contour(X):
+    """Contour of the benchmark and parity tests: p0 <= Xc, Xc = 1.6 X for X < 20 else
+    p0 = 14, Xc = 1.4 X (chosen by a search minimising max(e_s, amplification * eps))."""
+    if X < 20:
+        return min(6.0, 1.6 * X), 1.6 * X
+    return 14.0, 1.4 * X
+
+
+def workload_config(args, world):
+    return {"workload": "REXI linear step, T%d, %d Cauchy poles, dt=%g s, batch %d states/GPU, "
+                        "n^-1.5 Gaussian spectral states" % (args.T, args.N, args.dt, args.batch),
+            "T": args.T, "N_poles": args.N, "dt_s": args.dt, "batch_per_gpu": args.batch,
+            "global_batch": args.batch * world, "precision": "mixed (FP32 solves, FP64 pole sums)",
+            "l2": "flushed (256 MB write) between timed steps",
+            "parallelism": "independent states sharded over GPUs, no collective"}
+
+
+# ---------------------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------
+def cpu_oracle_rate(T, N, dt, m_list, states):
+    """Oracle (pivoted banded LU per pole and zonal order, FP64 sum) on the zonal orders
+    m_list of each state; returns (state-steps/s extrapolated to the full step, seconds)."""
+    from oracle import coeffs as oc
+    from oracle import rexi as orx
+    from paper_1805_06557_gb300 import synthetic as syn
+    X = orx.spectrum_bound(T, dt, syn.OMEGA, syn.RADIUS, syn.PHIBAR)
+    p0, Xc = contour(X)
+    z, w = oc.rexi_coefficients(N, p0, Xc)
+    work = sum(T + 1 - m for m in m_list)
+    full = (T + 1) * (T + 2) // 2
+    t0 = time.perf_counter()
+    for U in states:
+        orx.rexi_step(U, T, dt, syn.OMEGA, syn.RADIUS, syn.PHIBAR, z, w, m_list=m_list)
+    sec = time.perf_counter() - t0
+    per_state = sec / len(states) * full / work
+    return 1.0 / per_state, sec
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_1805_06557_gb300 import synthetic as syn
+    U = syn.gaussian_state(args.T, 1000)
+    times = []
+    for i in range(args.warmup + args.steps):
+        rate, sec = cpu_oracle_rate(args.T, args.N, args.dt, REF_STEP_M, [U])
+        if i >= args.warmup:
+            times.append(1.0 / rate)
+    per = statistics.mean(times)
+    value = 1.0 / per
+    cfg = workload_config(args, 1)
+    cfg["precision"] = "FP64 (oracle)"
+    sample = ("oracle on zonal orders %s of one T%d state per step (%d of %d coefficients), "
+              "extrapolated to the full step" % (REF_STEP_M, args.T,
+                                                 sum(args.T + 1 - m for m in REF_STEP_M),
+                                                 (args.T + 1) * (args.T + 2) // 2))
+    line = {"metric": METRIC, "value": value, "unit": "steps/s", "impl": "reference",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1805_06557_gb300 import rexi
+    from paper_1805_06557_gb300 import synthetic as syn
+
+    T, N, dt, B = args.T, args.N, args.dt, args.batch
+    X = rexi.spectrum_bound(T, dt, syn.OMEGA, syn.RADIUS, syn.PHIBAR)
+    p0, Xc = contour(X)
+    nlm = rexi.nlm(T)
+    host = np.stack([syn.gaussian_state(T, 1000 + rank * B + i) for i in range(B)])
+    u0 = torch.from_numpy(host).cuda()
+    u1 = torch.empty_like(u0)
+    ref64 = torch.empty_like(u0)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    fp64_tf, fp32_tf = rexi.alu_peaks()
+    kw = dict(omega=syn.OMEGA, radius=syn.RADIUS, phibar=syn.PHIBAR, p0=p0, Xc=Xc)
+    mixed = rexi.Plan(T, N, dt, precision="mixed", max_batch=B, **kw)
+    fp64 = rexi.Plan(T, N, dt, precision="fp64", max_batch=B, **kw)
+
+    def timed(plan, a, b, nb, steps, warmup):
+        for _ in range(warmup):
+            plan.step(a, b, nb)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        for e0, e1 in evs:
+            flush.zero_()
+            e0.record()
+            plan.step(a, b, nb)
+            e1.record()
+        torch.cuda.synchronize()
+        return [e0.elapsed_time(e1) for e0, e1 in evs]
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- headline: batched mixed plan ------------------------------------------------
+    for _ in range(args.warmup):
+        mixed.step(u0, u1, B)
+    mixed.set_profiling(True)
+    mixed.profile(reset=True)
+    barrier()
+    clk = Clocks(local)
+    clk.start()
+    ms = timed(mixed, u0, u1, B, args.steps, 0)
+    clocks = clk.stop()
+    prof = mixed.profile(reset=True)
+    mixed.set_profiling(False)
+    mean_ms = statistics.mean(ms)
+    tmax = torch.tensor([sum(ms)], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    barrier()
+    total_ms = float(tmax.item())
+    value = B * world * args.steps / (total_ms * 1e-3)
+
+    # ---- secondary measurements (rank-local) -------------------------------------------
+    ks = max(3, min(args.steps, 10))
+    fp64.step(u0, ref64, B)
+    torch.cuda.synchronize()
+    err = []
+    a, r = u1.cpu().numpy(), ref64.cpu().numpy()
+    wts = np.where(np.arange(nlm) <= T, 1.0, 2.0)
+    for f in range(3):
+        num = np.sqrt(np.sum(wts * np.abs(a[:, f] - r[:, f]) ** 2))
+        den = np.sqrt(np.sum(wts * np.abs(r[:, f]) ** 2))
+        err.append(float(num / den))
+    fp64_b1 = timed(fp64, u0[:1].contiguous(), u1[:1].contiguous(), 1, ks, 2)
+    fp64_bb = timed(fp64, u0, u1, B, ks, 1)
+    mix_b1 = timed(mixed, u0[:1].contiguous(), u1[:1].contiguous(), 1, ks, 2)
+
+    # ---- roofline of the dominant kernel (event times of the timed region) ---------------
+    info = mixed.info()
+    n_light = N - info["n_heavy"]
+    elems = 2 * nlm * B  # chain elements per pole per launch (two parity chains per m)
+    # algorithmic flops per chain element (FMA = 2): forward elimination 22, back
+    # substitution 8, right-hand side and diagonal 7, weighted pole sums 12
+    FLOPS_SOLVE = 49.0
+    kname, (kms, kn) = max(((k, v) for k, v in prof.items() if v[1] > 0), key=lambda kv: kv[1][0])
+    if kname == "k_rexi_light":
+        flops = FLOPS_SOLVE * elems * n_light
+        peak, ptype = fp32_tf, "fp32"
+    elif kname == "k_rexi_heavy":
+        flops = 14.0 * elems * info["n_heavy"]   # FP64: pole sums 12 + refinement update 2
+        peak, ptype = fp64_tf, "fp64"
+    else:
+        flops = FLOPS_SOLVE * elems * N
+        peak, ptype = fp64_tf, "fp64"
+    avg_s = kms / kn * 1e-3
+    achieved = flops / avg_s / 1e12
+    roof = {"bound": "alu", "kernel": kname, "pipe": ptype, "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": "measured %s FMA probe (rexi_alu_peaks) in this run" % ptype,
+            "kernel_ms": {k: (v[0] / v[1] if v[1] else None) for k, v in prof.items()}}
+
+    # ---- end to end through the C ABI with host buffers ---------------------------------
+    hin = torch.from_numpy(host).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    for _ in range(2):
+        mixed.step_host_ptr(hin.data_ptr(), hout.data_ptr(), B)
+    ke = max(3, min(args.steps, 10))
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        mixed.step_host_ptr(hin.data_ptr(), hout.data_ptr(), B)
+    e2e_s = (time.perf_counter() - t0) / ke
+    bytes_step = B * 3 * nlm * 16
+    e2e = {"value": B * world / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": bytes_step,
+           "d2h_bytes_per_step": bytes_step, "api": "rexi_step_host (pinned host buffers)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import multiprocessing as mp  # noqa: F401  (the oracle runs in this process)
+        rate, sec = cpu_oracle_rate(T, N, dt, SAMPLE_M, [host[0]])
+        cpu = {"value": rate, "unit": "steps/s", "cores": 1, "kind": "oracle",
+               "seconds": sec,
+               "sample": "pivoted banded LU oracle on %d of %d zonal orders of one state, "
+                         "extrapolated to a full T%d step" % (len(SAMPLE_M), T + 1, T)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic", "config": workload_config(args, world),
+        "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+        "rel_err_vs_fp64_gpu": err,
+        "fp64_plain_steps_per_s": 1e3 / statistics.mean(fp64_b1),
+        "fp64_batched_steps_per_s": B * 1e3 / statistics.mean(fp64_bb),
+        "mixed_single_steps_per_s": 1e3 / statistics.mean(mix_b1),
+        "speedup_vs_fp64_plain": value / world / (1e3 / statistics.mean(fp64_b1)),
+        "plan": {k: info[k] for k in ("n_heavy", "n_groups", "q_slots", "grid_light", "grid_heavy")},
+        "alu_peaks_tflops": {"fp64": fp64_tf, "fp32": fp32_tf},
+        "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+        "gpu_launches": 4 * args.steps,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    mixed.close()
+    fp64.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

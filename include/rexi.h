@@ -1,0 +1,178 @@
+/*
+ * rexi.h -- C ABI of librexi.so, a GB300-native (sm_103a) implementation of the REXI time
+ * step of the rotating shallow-water equations (Schreiber, Schaeffer & Loft,
+ * arXiv 1805.06557).
+ *
+ * All entry points are plain C: pointers plus sizes, no C++ or framework types.  Every
+ * function returns an int status, 0 on success and one of the negative REXI_E* codes on
+ * failure; rexi_last_error() then returns a thread-local, human-readable message.  Device
+ * buffers are owned by the caller; plans own their device tables and workspace.  Compute
+ * entry points are asynchronous on the plan's CUDA stream and never allocate.
+ *
+ * Spectral layout (shared by every entry point): triangular truncation T,
+ * nlm = (T+1)(T+2)/2 complex coefficients per field, m-major,
+ *     idx(m, n) = m (2T + 3 - m) / 2 + (n - m),   0 <= m <= n <= T,
+ * complex128 as interleaved (re, im) doubles.  Coefficients are of the orthonormal
+ * spherical harmonics Y_n^m = Pt_n^m(mu) e^{i m lambda} (no Condon-Shortley phase), a real
+ * field being  f = sum_n c_n^0 Y_n^0 + 2 Re sum_{m>=1} c_n^m Y_n^m.
+ * A state has three fields in the order (Phi', zeta, delta): geopotential perturbation,
+ * relative vorticity, divergence (paper Sec. 3).  A batch of states is [batch][3][nlm].
+ */
+#ifndef REXI_H
+#define REXI_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define REXI_OK 0
+#define REXI_EINVAL (-1)   /* bad argument (size, pointer, aliasing, unsupported option) */
+#define REXI_ENOMEM (-2)   /* device or host allocation failed (plan creation only)     */
+#define REXI_ECUDA (-3)    /* a CUDA runtime call failed                                 */
+#define REXI_ETIMEOUT (-4) /* a bounded device-side wait gave up                         */
+#define REXI_EBUSY (-5)    /* resource busy (serving slots / memory budget exhausted)    */
+
+#define REXI_FP64 0   /* every solve and sum in FP64                                         */
+#define REXI_MIXED 1  /* FP32 solves; poles with large weight refined (double-float residual) */
+                      /* and summed in FP64; the others summed in FP32                        */
+
+/* Thread-local description of the last error of the calling thread ("" if none). */
+const char* rexi_last_error(void);
+
+/*
+ * rexi_coeffs -- Cauchy-contour REXI coefficients (paper Sec. 4.2.1-4.2.2,
+ * Eq. cauchy_alpha / cauchy_beta).
+ *
+ * The circle passes through p0 (real, > 0) and +-i Xc, so R = (p0^2 + Xc^2)/(2 p0) and its
+ * centre is mu = p0 - R; nodes theta_n = 2 pi (n - 1/2)/N, n = 1..N.  Outputs
+ *     z_n = mu + R e^{i theta_n}            (= -alpha_n of the paper)
+ *     w_n = (R e^{i theta_n} / N) psi_k(z_n) (= -beta_n of the paper)
+ * so that  psi_k(x) ~ sum_n w_n / (z_n - x)  for x on [-i X, i X], X < Xc.  psi_0 = exp,
+ * psi_1(z) = (e^z - 1)/z, psi_2(z) = (e^z - 1 - z)/z^2 (Sec. 4.3; series near 0).
+ *   N       number of poles, >= 1
+ *   p0, Xc  contour points; p0 > 0, Xc > 0
+ *   phi     0, 1 or 2 (the psi_k above)
+ *   z_out, w_out  caller-owned host arrays of 2N doubles (re, im interleaved)
+ * Host only, FP64.  Errors: REXI_EINVAL.
+ */
+int rexi_coeffs(int N, double p0, double Xc, int phi, double* z_out, double* w_out);
+
+/*
+ * rexi_contour_select -- default contour for covering the spectrum [-iX, iX] with N poles:
+ * Xc = margin X and p0 <= Xc picked from a small candidate set to minimise
+ * max(scalar error, amplification * 2^-53) (the cancellation trade-off of Sec. 4.2.2).
+ * Host only.  Outputs p0, Xc.  Errors: REXI_EINVAL.
+ */
+int rexi_contour_select(double X, int N, double* p0, double* Xc);
+
+/* X = dt (sqrt(phibar T (T+1)) / radius + 2 omega): bound on |dt lambda| over the spectrum
+ * of dt L (gravity-wave frequency of degree T plus the largest Coriolis frequency). */
+double rexi_spectrum_bound(int T, double dt, double omega, double radius, double phibar);
+
+typedef struct rexi_plan rexi_plan;
+
+typedef struct rexi_plan_desc {
+  int T;              /* triangular truncation, 1 <= T <= 1023                           */
+  int N;              /* number of poles, 1 <= N <= 8192                                 */
+  double dt;          /* time step [s]                                                   */
+  double omega;       /* rotation rate Omega [1/s]                                       */
+  double radius;      /* sphere radius a [m]                                             */
+  double phibar;      /* mean geopotential Phibar = g h0 [m^2/s^2]                       */
+  double p0, Xc;      /* contour (used when z == NULL)                                   */
+  const double* z;    /* optional host array, 2N doubles: poles z_n (= -alpha_n)         */
+  const double* w;    /* optional host array, 2N doubles: weights w_n (= -beta_n)        */
+  int precision;      /* REXI_FP64 or REXI_MIXED                                         */
+  double heavy_tau;   /* REXI_MIXED: a pole whose gain |w_n| / dist(z_n, [-iX, iX])      */
+                      /* exceeds heavy_tau is refined and summed in FP64; < 0: 1e-3      */
+  int max_batch;      /* largest batch passed to rexi_step, >= 1                         */
+  void* stream;       /* cudaStream_t the plan launches on (NULL: legacy default stream) */
+} rexi_plan_desc;
+
+/*
+ * rexi_plan_create -- build a plan for  U1 = sum_n w_n (z_n - dt L)^-1 U0  (paper Eq. rexi),
+ * L = L_g + L_c the linear gravity + Coriolis operator (Sec. 3, the L_g and L_c columns of
+ * the split).  In spectral space, per zonal order m, with eps_n = sqrt((n^2-m^2)/(4n^2-1)):
+ *   dPhi_n/dt  = -Phibar delta_n
+ *   dzeta_n/dt = i w_n zeta_n - 2 Omega [(n+1)/n eps_n delta_{n-1} + n/(n+1) eps_{n+1} delta_{n+1}]
+ *   ddelta_n/dt= n(n+1)/a^2 Phi_n + i w_n delta_n
+ *                + 2 Omega [(n+1)/n eps_n zeta_{n-1} + n/(n+1) eps_{n+1} zeta_{n+1}]
+ * w_n = 2 Omega m / (n(n+1)); the n = 0 vorticity and divergence are left unchanged.
+ * The Coriolis coupling makes each (pole, m) system banded in n (Sec. 5.3); the library
+ * eliminates Phi and solves two tridiagonal parity chains per (pole, m).
+ * Allocates device tables and workspace (FP64 plan: per-warp scratch for the elimination).
+ * Errors: REXI_EINVAL, REXI_ENOMEM, REXI_ECUDA.
+ */
+int rexi_plan_create(const rexi_plan_desc* desc, rexi_plan** out);
+
+/* Frees the plan and its device memory.  NULL is allowed.  Synchronises the plan stream. */
+int rexi_plan_destroy(rexi_plan* plan);
+
+/*
+ * rexi_step -- one REXI linear step for `batch` independent states.
+ *   U0  device pointer, [batch][3][nlm] complex128 (caller-owned, read only)
+ *   U1  device pointer, [batch][3][nlm] complex128 (caller-owned, written)
+ * U0 and U1 must not overlap (REXI_EINVAL).  1 <= batch <= max_batch.  Asynchronous on the
+ * plan stream; allocates nothing; launches the pre-pass (mixed), the solve kernels and the
+ * finalize kernel.  With conjugate pole pairs the result is the m >= 0 half of a real field.
+ * Errors: REXI_EINVAL, REXI_ECUDA (launch failure).
+ */
+int rexi_step(rexi_plan* plan, const void* U0, void* U1, int batch);
+
+/*
+ * rexi_step_host -- rexi_step on HOST buffers: copies U0 to plan-owned device staging
+ * memory, runs the step and copies U1 back, all on the plan stream, then synchronises it.
+ * U0/U1: host arrays of batch*3*nlm complex128 (pinned memory gives full copy bandwidth).
+ * Errors: REXI_EINVAL, REXI_ECUDA.
+ */
+int rexi_step_host(rexi_plan* plan, const double* U0, double* U1, int batch);
+
+/* Synchronises the plan stream and reports any error raised by device work since the last
+ * call (REXI_ECUDA).  */
+int rexi_sync(rexi_plan* plan);
+
+/* Plan facts for benchmarking and tests. */
+typedef struct rexi_plan_info {
+  int T, N, nlm, precision;
+  int n_heavy;            /* poles refined and summed in FP64 (mixed), N for FP64 plans  */
+  int n_groups;           /* 32-pole groups (N rounded up to a multiple of 32)           */
+  int n_tiles;            /* work tiles per state                                        */
+  int q_slots;            /* pole ranges summed separately before the final sum          */
+  int grid_fp64, grid_light, grid_heavy;   /* persistent grid sizes (blocks)            */
+  long long workspace_bytes;               /* device memory owned by the plan           */
+  double s0_re, s0_im;    /* sum_n w_n / z_n                                             */
+  double X;               /* covered half-width used for the heavy classification        */
+} rexi_plan_info;
+
+int rexi_plan_get_info(const rexi_plan* plan, rexi_plan_info* info);
+
+/* Copies the plan's poles and weights (in the plan's internal order, 2*N doubles each)
+ * and the per-pole heavy flags (N ints) to host arrays; any pointer may be NULL. */
+int rexi_plan_get_poles(const rexi_plan* plan, double* z, double* w, int* heavy);
+
+/*
+ * Per-kernel timing.  When enabled, rexi_step records a CUDA event pair on the plan stream
+ * around every kernel it launches and accumulates the elapsed times at the next
+ * rexi_plan_get_profile call (which synchronises the stream).  Kernel ids: 0 pre-pass,
+ * 1 FP64 solve, 2 light solve, 3 heavy solve, 4 finalize.  ms[i] receives the total time
+ * and launches[i] the number of launches of kernel i since the last reset (reset = 1
+ * clears them after reading).  Enabling adds event records between launches; disabled by
+ * default.  Errors: REXI_EINVAL, REXI_ECUDA.
+ */
+#define REXI_NKERNELS 5
+int rexi_plan_set_profiling(rexi_plan* plan, int enable);
+int rexi_plan_get_profile(rexi_plan* plan, double* ms, int* launches, int reset);
+
+/*
+ * rexi_alu_peaks -- measures the FP64 and FP32 FMA throughput of the current device
+ * (TFLOP/s, an FMA counted as 2 flops) with two short probe kernels: 8 independent FMA
+ * chains per thread, 16 blocks of 256 threads per SM, timed with CUDA events.  These are
+ * the roofline denominators of the ALU-bound solve kernels.  Synchronous; allocates and
+ * frees a small device buffer.  Errors: REXI_EINVAL, REXI_ECUDA.
+ */
+int rexi_alu_peaks(double* fp64_tflops, double* fp32_tflops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* REXI_H */

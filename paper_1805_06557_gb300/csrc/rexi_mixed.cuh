@@ -1,0 +1,435 @@
+// Mixed-precision REXI solve kernels.
+//
+// The poles split into two classes at plan time by their gain
+//     g_n = |w_n| / dist(z_n, [-iX, iX]),
+// the largest factor by which an error in the solve of pole n reaches the REXI sum.  Only a
+// few poles near the positive real end of the contour have large weights e^{Re z}; for the
+// rest an FP32 solve already contributes less than the target error.
+//
+//  * light poles (k_rexi_light): FP32 Thomas elimination, weighted sums in FP32 over the 32
+//    poles of a warp, added into the FP64 partial sums.  The forward coefficients are not
+//    stored: the sweep keeps a checkpoint of the recurrence state every 16 elements and the
+//    backward pass recomputes each 16-element segment in registers, so the kernel needs no
+//    per-element scratch traffic.
+//  * heavy poles (k_rexi_heavy): FP32 solve, one step of iterative refinement whose
+//    residual r - A x is evaluated in double-float arithmetic (pairs of FP32 numbers,
+//    error-free products by FMA, Knuth's two-sum), FP32 solve of the correction with the
+//    same factorisation, and weighted sums over poles in FP64.
+// Both kernels share the tile scheme and chain equations of the FP64 kernel.
+#pragma once
+#include "common.cuh"
+#include "rexi_fp64.cuh"
+
+namespace rexi {
+
+constexpr int MIX_WARPS = 4;
+constexpr int SEG = 16;        // checkpoint interval and transposition block of the light path
+constexpr int LTROW = 33;      // padded row (float2) of the light transposition tile
+
+// ---- double-float arithmetic (value = hi + lo, |lo| <= ulp(hi)/2) --------------------
+struct df {
+  float hi, lo;
+};
+__device__ __forceinline__ df df_two_sum(float a, float b) {
+  float s = a + b;
+  float bb = s - a;
+  float e = (a - (s - bb)) + (b - bb);
+  return df{s, e};
+}
+__device__ __forceinline__ df df_fast(float s, float e) {  // |s| >= |e|
+  float h = s + e;
+  return df{h, e - (h - s)};
+}
+__device__ __forceinline__ df df_add(df x, df y) {
+  df s = df_two_sum(x.hi, y.hi);
+  return df_fast(s.hi, s.lo + (x.lo + y.lo));
+}
+__device__ __forceinline__ df df_neg(df x) { return df{-x.hi, -x.lo}; }
+__device__ __forceinline__ df df_mul(df x, df y) {
+  float p = x.hi * y.hi;
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, e));
+  return df_fast(p, e);
+}
+__device__ __forceinline__ df df_mulf(df x, float f) {
+  float p = x.hi * f;
+  float e = fmaf(x.hi, f, -p);
+  e = fmaf(x.lo, f, e);
+  return df_fast(p, e);
+}
+struct dfc {
+  df re, im;
+};
+__device__ __forceinline__ dfc dfc_mul(dfc a, dfc b) {
+  return dfc{df_add(df_mul(a.re, b.re), df_neg(df_mul(a.im, b.im))),
+             df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+}
+__host__ __device__ inline float4 split4(double a, double b) {
+  float ah = (float)a, bh = (float)b;
+  return make_float4(ah, (float)(a - (double)ah), bh, (float)(b - (double)bh));
+}
+__device__ __forceinline__ dfc dfc_of(float4 v) { return dfc{df{v.x, v.y}, df{v.z, v.w}}; }
+
+// per-(m,n) table in double-float: (dt w, cm), (cp, q) as (hi, lo) pairs
+struct TabDF {
+  float4 a, b;  // a = (hw.hi, hw.lo, cm.hi, cm.lo), b = (cp.hi, cp.lo, q.hi, q.lo)
+};
+// per-pole constants in double-float
+struct PoleDF {
+  float4 z, iz, gz;
+};
+// right-hand-side pieces produced by the pre-pass for every (state, m, n)
+struct Rhs32 {
+  float2 bz, bd, qbp;  // bzeta, bdelta, q * bPhi
+};
+struct RhsDF {
+  float4 bz, bd, qbp;
+};
+
+// Rhs32[batch][nlm] followed (256-byte aligned) by RhsDF[batch][nlm]
+inline size_t mixed_rhs32_bytes(int nlm, int batch) {
+  return (sizeof(Rhs32) * (size_t)nlm * batch + 255) / 256 * 256;
+}
+inline size_t mixed_rhs_bytes(int nlm, int batch) {
+  return mixed_rhs32_bytes(nlm, batch) + sizeof(RhsDF) * (size_t)nlm * batch;
+}
+
+
+struct MixedArgs {
+  const double2* U0;
+  double2* partial;
+  const float4* tab32;
+  const TabDF* tabdf;
+  const PoleF* p32;
+  const PoleD* p64;
+  const PoleDF* pdf;
+  const Tile* tiles;
+  const Rhs32* rhs32;   // [B][nlm]
+  const RhsDF* rhsdf;   // [B][nlm]
+  void* scratch;
+  int ntiles_light, ntiles_heavy;  // light tiles first, then heavy tiles, in `tiles`
+  int B, T, nlm, Q, kmax, nseg_max;
+  int warps_light;      // warps of the light grid (the heavy scratch starts after theirs)
+};
+
+// ---- pre-pass: FP32 and double-float right-hand-side pieces ----------------------------
+__global__ void k_mixed_rhs(const double2* __restrict__ U0, const D4* __restrict__ tab,
+                            Rhs32* __restrict__ r32, RhsDF* __restrict__ rdf, int B, int nlm) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)B * nlm) return;
+  const int b = (int)(i / nlm), idx = (int)(i - (long long)b * nlm);
+  const double2* u = U0 + (size_t)b * 3 * nlm;
+  const double2 bp = u[idx], bz = u[nlm + idx], bd = u[2 * nlm + idx];
+  const double q = tab[idx].w;
+  const double2 qbp = make_double2(q * bp.x, q * bp.y);
+  r32[i] = Rhs32{make_float2((float)bz.x, (float)bz.y), make_float2((float)bd.x, (float)bd.y),
+                 make_float2((float)qbp.x, (float)qbp.y)};
+  rdf[i] = RhsDF{split4(bz.x, bz.y), split4(bd.x, bd.y), split4(qbp.x, qbp.y)};
+}
+
+// ---- light kernel ------------------------------------------------------------------
+struct LightSmem {
+  float2 tile[SEG][LTROW];
+  float2 w[32], wz[32];
+};
+
+// one forward step of the FP32 chain recurrence for element k (n = m + k)
+__device__ __forceinline__ void light_fwd(const MixedArgs& a, const PoleF& pf, const Rhs32* rb,
+                                          int off, int k, int c, float2& ct, float2& y) {
+  const float4 tb = __ldg(a.tab32 + off + k);
+  const Rhs32 rr = rb[off + k];
+  const bool isZ = ((k & 1) == c);
+  const float lo = isZ ? tb.y : -tb.y;
+  const float up = isZ ? tb.z : -tb.z;
+  float2 d, r;
+  if (isZ) {
+    d = make_float2(pf.z.x, pf.z.y - tb.x);
+    r = rr.bz;
+  } else {
+    d = make_float2(fmaf(tb.w, pf.gz.x, pf.z.x), fmaf(tb.w, pf.gz.y, pf.z.y - tb.x));
+    r = cfmaf(pf.iz, rr.qbp, rr.bd);
+  }
+  const float2 den = make_float2(fmaf(-lo, ct.x, d.x), fmaf(-lo, ct.y, d.y));
+  const float2 inv = crcpf(den);
+  ct = make_float2(up * inv.x, up * inv.y);
+  y = cmulf(make_float2(fmaf(-lo, y.x, r.x), fmaf(-lo, y.y, r.y)), inv);
+}
+
+__global__ void __launch_bounds__(MIX_WARPS * 32)
+k_rexi_light(MixedArgs a) {
+  __shared__ LightSmem sm[MIX_WARPS];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  LightSmem& S = sm[wib];
+  const int gw = blockIdx.x * MIX_WARPS + wib;
+  const int W = gridDim.x * MIX_WARPS;
+  float4* ckpt = reinterpret_cast<float4*>(a.scratch) + (size_t)gw * a.nseg_max * 32;
+  const int total = a.ntiles_light * a.B;
+  const int T = a.T, nlm = a.nlm;
+  for (int round = 0; round * W < total; ++round) {
+    const int t = round * W + ((round & 1) ? (W - 1 - gw) : gw);
+    if (t >= total) continue;
+    const int it = t / a.B, b = t - it * a.B;
+    const Tile tl = a.tiles[it];
+    const int m = tl.m, c = tl.chain, K = T + 1 - m, off = moff(T, m);
+    const int nseg = (K + SEG - 1) / SEG;
+    const Rhs32* rb = a.rhs32 + (size_t)b * nlm;
+    double2* part = a.partial + ((size_t)b * a.Q + tl.q) * 3 * nlm;
+
+    for (int gi = 0; gi < tl.ng; ++gi) {
+      const PoleF pf = a.p32[(tl.g0 + gi) * 32 + lane];
+      __syncwarp();
+      S.w[lane] = pf.w;
+      S.wz[lane] = pf.wz;
+      float2 ca[SEG], ya[SEG];
+      // ---- pass 1: forward sweep with checkpoints ------------------------------------
+      float2 ct = make_float2(0.f, 0.f), y = make_float2(0.f, 0.f);
+      for (int s = 0; s < nseg; ++s) {
+#pragma unroll
+        for (int i = 0; i < SEG; ++i) {
+          const int k = s * SEG + i;
+          if (k < K) light_fwd(a, pf, rb, off, k, c, ct, y);
+          ca[i] = ct;
+          ya[i] = y;
+        }
+        if (s + 1 < nseg) ckpt[(size_t)s * 32 + lane] = make_float4(ct.x, ct.y, y.x, y.y);
+      }
+      // ---- pass 2: backward over segments, recomputing each from its checkpoint -------
+      float2 xn = make_float2(0.f, 0.f);
+      for (int s = nseg - 1; s >= 0; --s) {
+        if (s != nseg - 1) {
+          if (s > 0) {
+            const float4 st = ckpt[(size_t)(s - 1) * 32 + lane];
+            ct = make_float2(st.x, st.y);
+            y = make_float2(st.z, st.w);
+          } else {
+            ct = make_float2(0.f, 0.f);
+            y = make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int i = 0; i < SEG; ++i) {
+            light_fwd(a, pf, rb, off, s * SEG + i, c, ct, y);  // full segment: k < K here
+            ca[i] = ct;
+            ya[i] = y;
+          }
+        }
+#pragma unroll
+        for (int i = SEG - 1; i >= 0; --i) {
+          const int k = s * SEG + i;
+          if (k < K) {
+            const float2 x = make_float2(ya[i].x - fmaf(ca[i].x, xn.x, -ca[i].y * xn.y),
+                                         ya[i].y - fmaf(ca[i].x, xn.y, ca[i].y * xn.x));
+            S.tile[i][lane] = x;
+            xn = x;
+          }
+        }
+        __syncwarp();
+        // block reduction: row r = lane & 15, poles [16h, 16h+16)
+        {
+          const int r = lane & 15, h = lane >> 4;
+          const int k = s * SEG + r;
+          const bool valid = k < K;
+          const bool isD = ((k & 1) != c);
+          float2 acc = make_float2(0.f, 0.f), acc2 = make_float2(0.f, 0.f);
+          if (valid) {
+#pragma unroll
+            for (int p = 16 * h; p < 16 * h + 16; ++p) {
+              const float2 x = S.tile[r][p];
+              acc = cfmaf(S.w[p], x, acc);
+              if (isD) acc2 = cfmaf(S.wz[p], x, acc2);
+            }
+          }
+          acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
+          acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
+          acc2.x += __shfl_xor_sync(0xffffffffu, acc2.x, 16);
+          acc2.y += __shfl_xor_sync(0xffffffffu, acc2.y, 16);
+          if (h == 0 && valid) {
+            double2* dst = part + (isD ? nlm : 0) + off + k;
+            const double2 v = make_double2((double)acc.x, (double)acc.y);
+            *dst = (gi == 0) ? v : cadd(*dst, v);
+            if (isD) {
+              double2* dst2 = part + 2 * nlm + off + k;
+              const double2 v2 = make_double2((double)acc2.x, (double)acc2.y);
+              *dst2 = (gi == 0) ? v2 : cadd(*dst2, v2);
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+}
+
+// ---- heavy kernel ------------------------------------------------------------------
+// residual of chain row k in double-float:  r_k - d_k x_k - lo_k x_{k-1} - up_k x_{k+1}
+__device__ __forceinline__ float2 heavy_residual(const MixedArgs& a, const PoleDF& pq,
+                                                 const RhsDF* rb, int off, int k, int K, int c,
+                                                 float2 xm, float2 x0, float2 xp) {
+  const TabDF tb = a.tabdf[off + k];
+  const bool isZ = ((k & 1) == c);
+  const df hw{tb.a.x, tb.a.y}, cm{tb.a.z, tb.a.w}, cp{tb.b.x, tb.b.y}, q{tb.b.z, tb.b.w};
+  const RhsDF rr = rb[off + k];
+  const dfc z = dfc_of(pq.z);
+  dfc d, r;
+  if (isZ) {
+    d = dfc{z.re, df_add(z.im, df_neg(hw))};
+    r = dfc_of(rr.bz);
+  } else {
+    const dfc gz = dfc_of(pq.gz);
+    d = dfc{df_add(z.re, df_mul(q, gz.re)), df_add(df_add(z.im, df_neg(hw)), df_mul(q, gz.im))};
+    const dfc t = dfc_mul(dfc_of(pq.iz), dfc_of(rr.qbp));
+    const dfc bd = dfc_of(rr.bd);
+    r = dfc{df_add(bd.re, t.re), df_add(bd.im, t.im)};
+  }
+  const df lo = isZ ? cm : df_neg(cm);
+  const df up = isZ ? cp : df_neg(cp);
+  // acc = r - d x
+  df re = df_add(r.re, df_neg(df_add(df_mulf(d.re, x0.x), df_neg(df_mulf(d.im, x0.y)))));
+  df im = df_add(r.im, df_neg(df_add(df_mulf(d.re, x0.y), df_mulf(d.im, x0.x))));
+  if (k > 0) {
+    re = df_add(re, df_neg(df_mulf(lo, xm.x)));
+    im = df_add(im, df_neg(df_mulf(lo, xm.y)));
+  }
+  if (k + 1 < K) {
+    re = df_add(re, df_neg(df_mulf(up, xp.x)));
+    im = df_add(im, df_neg(df_mulf(up, xp.y)));
+  }
+  return make_float2(re.hi + re.lo, im.hi + im.lo);
+}
+
+__global__ void __launch_bounds__(MIX_WARPS * 32)
+k_rexi_heavy(MixedArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  double2* s_tile = reinterpret_cast<double2*>(smem_raw) + wib * (32 * FP64_TROW);
+  double2* s_w = reinterpret_cast<double2*>(smem_raw) + MIX_WARPS * 32 * FP64_TROW + wib * 64;
+  double2* s_wz = s_w + 32;
+  const int gw = blockIdx.x * MIX_WARPS + wib;
+  const int W = gridDim.x * MIX_WARPS;
+  // heavy scratch: after the light checkpoints; per warp S1 [kmax][32] float4, S2 [kmax][32] float2
+  char* base = reinterpret_cast<char*>(a.scratch) +
+               (size_t)a.warps_light * a.nseg_max * 32 * sizeof(float4) +
+               (size_t)gw * a.kmax * 32 * (sizeof(float4) + sizeof(float2));
+  float4* S1 = reinterpret_cast<float4*>(base);
+  float2* S2 = reinterpret_cast<float2*>(base + (size_t)a.kmax * 32 * sizeof(float4));
+  const int total = a.ntiles_heavy * a.B;
+  const int T = a.T, nlm = a.nlm;
+
+  for (int round = 0; round * W < total; ++round) {
+    const int t = round * W + ((round & 1) ? (W - 1 - gw) : gw);
+    if (t >= total) continue;
+    const int it = t / a.B, b = t - it * a.B;
+    const Tile tl = a.tiles[a.ntiles_light + it];
+    const int m = tl.m, c = tl.chain, K = T + 1 - m, off = moff(T, m);
+    const Rhs32* rb = a.rhs32 + (size_t)b * nlm;
+    const RhsDF* rbd = a.rhsdf + (size_t)b * nlm;
+    double2* part = a.partial + ((size_t)b * a.Q + tl.q) * 3 * nlm;
+
+    for (int gi = 0; gi < tl.ng; ++gi) {
+      const int pidx = (tl.g0 + gi) * 32 + lane;
+      const PoleF pf = a.p32[pidx];
+      const PoleDF pq = a.pdf[pidx];
+      {
+        const PoleD pd = a.p64[pidx];
+        __syncwarp();
+        s_w[lane] = pd.w;
+        s_wz[lane] = pd.wz;
+      }
+      // ---- A: FP32 forward, store (inv, y) ------------------------------------------
+      float2 ct = make_float2(0.f, 0.f), y = make_float2(0.f, 0.f);
+      for (int k = 0; k < K; ++k) {
+        const float4 tb = __ldg(a.tab32 + off + k);
+        const Rhs32 rr = rb[off + k];
+        const bool isZ = ((k & 1) == c);
+        const float lo = isZ ? tb.y : -tb.y;
+        const float up = isZ ? tb.z : -tb.z;
+        float2 d, r;
+        if (isZ) {
+          d = make_float2(pf.z.x, pf.z.y - tb.x);
+          r = rr.bz;
+        } else {
+          d = make_float2(fmaf(tb.w, pf.gz.x, pf.z.x), fmaf(tb.w, pf.gz.y, pf.z.y - tb.x));
+          r = cfmaf(pf.iz, rr.qbp, rr.bd);
+        }
+        const float2 den = make_float2(fmaf(-lo, ct.x, d.x), fmaf(-lo, ct.y, d.y));
+        const float2 inv = crcpf(den);
+        ct = make_float2(up * inv.x, up * inv.y);
+        y = cmulf(make_float2(fmaf(-lo, y.x, r.x), fmaf(-lo, y.y, r.y)), inv);
+        S1[(size_t)k * 32 + lane] = make_float4(inv.x, inv.y, y.x, y.y);
+      }
+      // ---- A: back substitution, store x -------------------------------------------
+      float2 xn = make_float2(0.f, 0.f);
+      for (int k = K - 1; k >= 0; --k) {
+        const float4 s = S1[(size_t)k * 32 + lane];
+        const float4 tb = __ldg(a.tab32 + off + k);
+        const float up = ((k & 1) == c) ? tb.z : -tb.z;
+        const float2 cc = make_float2(up * s.x, up * s.y);
+        const float2 x = make_float2(s.z - fmaf(cc.x, xn.x, -cc.y * xn.y),
+                                     s.w - fmaf(cc.x, xn.y, cc.y * xn.x));
+        S2[(size_t)k * 32 + lane] = x;
+        xn = x;
+      }
+      // ---- B: double-float residual and forward sweep of the correction ---------------
+      float2 xm = make_float2(0.f, 0.f), x0 = S2[lane];
+      float2 yc = make_float2(0.f, 0.f);
+      for (int k = 0; k < K; ++k) {
+        const float2 xp = (k + 1 < K) ? S2[(size_t)(k + 1) * 32 + lane] : make_float2(0.f, 0.f);
+        const float2 res = heavy_residual(a, pq, rbd, off, k, K, c, xm, x0, xp);
+        const float4 tb = __ldg(a.tab32 + off + k);
+        const float lo = ((k & 1) == c) ? tb.y : -tb.y;
+        const float4 s = S1[(size_t)k * 32 + lane];
+        const float2 inv = make_float2(s.x, s.y);
+        yc = cmulf(make_float2(fmaf(-lo, yc.x, res.x), fmaf(-lo, yc.y, res.y)), inv);
+        S1[(size_t)k * 32 + lane] = make_float4(s.x, s.y, yc.x, yc.y);
+        xm = x0;
+        x0 = xp;
+      }
+      // ---- C: back substitution of the correction, FP64 weighted sums ----------------
+      float2 dn = make_float2(0.f, 0.f);
+      for (int k = K - 1; k >= 0; --k) {
+        const float4 s = S1[(size_t)k * 32 + lane];
+        const float4 tb = __ldg(a.tab32 + off + k);
+        const float up = ((k & 1) == c) ? tb.z : -tb.z;
+        const float2 cc = make_float2(up * s.x, up * s.y);
+        const float2 dx = make_float2(s.z - fmaf(cc.x, dn.x, -cc.y * dn.y),
+                                      s.w - fmaf(cc.x, dn.y, cc.y * dn.x));
+        dn = dx;
+        const float2 x = S2[(size_t)k * 32 + lane];
+        s_tile[(k & 31) * FP64_TROW + lane] =
+            make_double2((double)x.x + (double)dx.x, (double)x.y + (double)dx.y);
+        if ((k & 31) == 0) {
+          __syncwarp();
+          const int kk = k + lane;
+          if (kk < K) {
+            double2 acc = make_double2(0.0, 0.0);
+#pragma unroll 8
+            for (int p = 0; p < 32; ++p) acc = cfma(s_w[p], s_tile[lane * FP64_TROW + p], acc);
+            double2* dst = part + (((kk & 1) == c) ? 0 : nlm) + off + kk;
+            *dst = (gi == 0) ? acc : cadd(*dst, acc);
+          }
+          const int j = lane & 15, h = lane >> 4;
+          const int rowd = 2 * j + (1 - c);
+          const int kd = k + rowd;
+          double2 acc2 = make_double2(0.0, 0.0);
+          if (kd < K) {
+#pragma unroll 8
+            for (int p = 16 * h; p < 16 * h + 16; ++p)
+              acc2 = cfma(s_wz[p], s_tile[rowd * FP64_TROW + p], acc2);
+          }
+          acc2.x += __shfl_xor_sync(0xffffffffu, acc2.x, 16);
+          acc2.y += __shfl_xor_sync(0xffffffffu, acc2.y, 16);
+          if (h == 0 && kd < K) {
+            double2* dst = part + 2 * nlm + off + kd;
+            *dst = (gi == 0) ? acc2 : cadd(*dst, acc2);
+          }
+          __syncwarp();
+        }
+      }
+    }
+  }
+}
+
+inline size_t heavy_smem_bytes() {
+  return sizeof(double2) * (MIX_WARPS * 32 * FP64_TROW + MIX_WARPS * 64);
+}
+
+}  // namespace rexi

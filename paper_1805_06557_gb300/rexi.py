@@ -1,0 +1,227 @@
+"""ctypes binding of librexi.so (argument marshalling only; every step runs in the library).
+
+Importing this module loads the library and raises ImportError if it has not been built
+(``python -c "import __graft_entry__ as g; g.build()"``).  There is no fallback path.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librexi.so")
+HEADER_DIR = os.path.join(os.path.dirname(_HERE), "include")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("librexi.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+_lib = ctypes.CDLL(LIB_PATH)
+
+REXI_OK, REXI_EINVAL, REXI_ENOMEM, REXI_ECUDA, REXI_ETIMEOUT, REXI_EBUSY = 0, -1, -2, -3, -4, -5
+REXI_FP64, REXI_MIXED = 0, 1
+_PREC = {"fp64": REXI_FP64, "mixed": REXI_MIXED}
+
+
+class RexiError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (code %d)" % (msg, code))
+        self.code = code
+
+
+def _check(rc):
+    if rc != REXI_OK:
+        raise RexiError(rc, _lib.rexi_last_error().decode())
+    return rc
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int), ("N", ctypes.c_int), ("dt", ctypes.c_double),
+                ("omega", ctypes.c_double), ("radius", ctypes.c_double),
+                ("phibar", ctypes.c_double), ("p0", ctypes.c_double), ("Xc", ctypes.c_double),
+                ("z", _dp), ("w", _dp), ("precision", ctypes.c_int),
+                ("heavy_tau", ctypes.c_double), ("max_batch", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int), ("N", ctypes.c_int), ("nlm", ctypes.c_int),
+                ("precision", ctypes.c_int), ("n_heavy", ctypes.c_int),
+                ("n_groups", ctypes.c_int), ("n_tiles", ctypes.c_int), ("q_slots", ctypes.c_int),
+                ("grid_fp64", ctypes.c_int), ("grid_light", ctypes.c_int),
+                ("grid_heavy", ctypes.c_int), ("workspace_bytes", ctypes.c_longlong),
+                ("s0_re", ctypes.c_double), ("s0_im", ctypes.c_double), ("X", ctypes.c_double)]
+
+
+_lib.rexi_last_error.restype = ctypes.c_char_p
+_lib.rexi_coeffs.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp]
+_lib.rexi_contour_select.argtypes = [ctypes.c_double, ctypes.c_int, _dp, _dp]
+_lib.rexi_spectrum_bound.argtypes = [ctypes.c_int] + [ctypes.c_double] * 4
+_lib.rexi_spectrum_bound.restype = ctypes.c_double
+_lib.rexi_plan_create.argtypes = [ctypes.POINTER(PlanDesc), ctypes.POINTER(ctypes.c_void_p)]
+_lib.rexi_plan_destroy.argtypes = [ctypes.c_void_p]
+_lib.rexi_step.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+_lib.rexi_step_host.argtypes = [ctypes.c_void_p, _dp, _dp, ctypes.c_int]
+_lib.rexi_sync.argtypes = [ctypes.c_void_p]
+_lib.rexi_plan_get_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(PlanInfo)]
+_lib.rexi_plan_get_poles.argtypes = [ctypes.c_void_p, _dp, _dp, _ip]
+_lib.rexi_alu_peaks.argtypes = [_dp, _dp]
+_lib.rexi_plan_set_profiling.argtypes = [ctypes.c_void_p, ctypes.c_int]
+_lib.rexi_plan_get_profile.argtypes = [ctypes.c_void_p, _dp, _ip, ctypes.c_int]
+KERNEL_NAMES = ["k_mixed_rhs", "k_rexi_fp64", "k_rexi_light", "k_rexi_heavy", "k_rexi_finalize"]
+
+
+def alu_peaks():
+    """Measured (FP64, FP32) FMA throughput of the current device in TFLOP/s."""
+    a = ctypes.c_double()
+    b = ctypes.c_double()
+    _check(_lib.rexi_alu_peaks(ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def exported_symbols():
+    """Names of every function declared in include/*.h."""
+    names = []
+    for f in sorted(os.listdir(HEADER_DIR)):
+        if f.endswith(".h"):
+            txt = open(os.path.join(HEADER_DIR, f)).read()
+            names += re.findall(r"^\s*(?:const\s+)?[a-z_][\w\s\*]*?\b([a-z]\w*)\s*\(", txt, re.M)
+    return sorted(set(n for n in names if not n.startswith(("if", "for", "while", "sizeof"))))
+
+
+def library():
+    return _lib
+
+
+def last_error():
+    return _lib.rexi_last_error().decode()
+
+
+def coeffs(N, p0, Xc, phi=0):
+    """Poles z_n and weights w_n of  psi_phi(x) ~ sum_n w_n / (z_n - x)  (complex128 arrays)."""
+    z = np.empty(2 * N)
+    w = np.empty(2 * N)
+    _check(_lib.rexi_coeffs(int(N), float(p0), float(Xc), int(phi),
+                            z.ctypes.data_as(_dp), w.ctypes.data_as(_dp)))
+    return z.view(np.complex128), w.view(np.complex128)
+
+
+def contour_select(X, N):
+    p0 = ctypes.c_double()
+    Xc = ctypes.c_double()
+    _check(_lib.rexi_contour_select(float(X), int(N), ctypes.byref(p0), ctypes.byref(Xc)))
+    return p0.value, Xc.value
+
+
+def spectrum_bound(T, dt, omega, radius, phibar):
+    return _lib.rexi_spectrum_bound(int(T), float(dt), float(omega), float(radius), float(phibar))
+
+
+def nlm(T):
+    return (T + 1) * (T + 2) // 2
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Plan:
+    """REXI plan: U1 = sum_n w_n (z_n - dt L)^-1 U0 for batches of spectral states."""
+
+    def __init__(self, T, N, dt, omega, radius, phibar, p0=None, Xc=None, z=None, w=None,
+                 precision="fp64", heavy_tau=-1.0, max_batch=1, stream=None):
+        d = PlanDesc()
+        d.T, d.N, d.dt = int(T), int(N), float(dt)
+        d.omega, d.radius, d.phibar = float(omega), float(radius), float(phibar)
+        d.p0 = float(p0) if p0 is not None else 0.0
+        d.Xc = float(Xc) if Xc is not None else 0.0
+        self._zw = None
+        if z is not None:
+            zz = np.ascontiguousarray(np.asarray(z, dtype=np.complex128)).view(np.float64)
+            ww = np.ascontiguousarray(np.asarray(w, dtype=np.complex128)).view(np.float64)
+            self._zw = (zz, ww)
+            d.z = zz.ctypes.data_as(_dp)
+            d.w = ww.ctypes.data_as(_dp)
+        d.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
+        d.heavy_tau = float(heavy_tau)
+        d.max_batch = int(max_batch)
+        d.stream = ctypes.c_void_p(_stream_handle(stream))
+        h = ctypes.c_void_p()
+        _check(_lib.rexi_plan_create(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+        self.T, self.N, self.nlm, self.max_batch = int(T), int(N), nlm(T), int(max_batch)
+
+    def step(self, U0, U1, batch=None):
+        """U0, U1: CUDA complex128 tensors of shape [batch, 3, nlm] (or [3, nlm])."""
+        if batch is None:
+            batch = 1 if U0.dim() == 2 else U0.shape[0]
+        for t in (U0, U1):
+            if not (t.is_cuda and t.is_contiguous()) or t.numel() != batch * 3 * self.nlm:
+                raise ValueError("need contiguous CUDA complex128 tensors of %d x 3 x %d"
+                                 % (batch, self.nlm))
+        _check(_lib.rexi_step(self._h, ctypes.c_void_p(U0.data_ptr()),
+                              ctypes.c_void_p(U1.data_ptr()), int(batch)))
+        return U1
+
+    def step_raw(self, U0_ptr, U1_ptr, batch):
+        return _lib.rexi_step(self._h, ctypes.c_void_p(U0_ptr), ctypes.c_void_p(U1_ptr), int(batch))
+
+    def step_host(self, U0, U1=None):
+        """Host numpy complex128 arrays [batch, 3, nlm]; copies inside the call."""
+        U0 = np.ascontiguousarray(U0, dtype=np.complex128)
+        batch = 1 if U0.ndim == 2 else U0.shape[0]
+        if U1 is None:
+            U1 = np.empty_like(U0)
+        _check(_lib.rexi_step_host(self._h, U0.view(np.float64).ctypes.data_as(_dp),
+                                   U1.view(np.float64).ctypes.data_as(_dp), int(batch)))
+        return U1
+
+    def step_host_ptr(self, U0_ptr, U1_ptr, batch):
+        _check(_lib.rexi_step_host(self._h, ctypes.cast(U0_ptr, _dp), ctypes.cast(U1_ptr, _dp),
+                                   int(batch)))
+
+    def sync(self):
+        _check(_lib.rexi_sync(self._h))
+
+    def info(self):
+        i = PlanInfo()
+        _check(_lib.rexi_plan_get_info(self._h, ctypes.byref(i)))
+        return {k: getattr(i, k) for k, _ in PlanInfo._fields_}
+
+    def poles(self):
+        z = np.empty(2 * self.N)
+        w = np.empty(2 * self.N)
+        hv = np.empty(self.N, dtype=np.int32)
+        _check(_lib.rexi_plan_get_poles(self._h, z.ctypes.data_as(_dp), w.ctypes.data_as(_dp),
+                                        hv.ctypes.data_as(_ip)))
+        return z.view(np.complex128), w.view(np.complex128), hv.astype(bool)
+
+    def set_profiling(self, enable=True):
+        _check(_lib.rexi_plan_set_profiling(self._h, 1 if enable else 0))
+
+    def profile(self, reset=True):
+        """{kernel name: (total ms, launches)} since the last reset (synchronises)."""
+        ms = np.zeros(len(KERNEL_NAMES))
+        n = np.zeros(len(KERNEL_NAMES), dtype=np.int32)
+        _check(_lib.rexi_plan_get_profile(self._h, ms.ctypes.data_as(_dp), n.ctypes.data_as(_ip),
+                                          1 if reset else 0))
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_NAMES)}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.rexi_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,218 @@
+"""GPU parity of rexi_step (paper Eq. rexi) against the FP64 CPU oracle, through the C ABI.
+
+Tolerances (per-field relative L2, m > 0 weighted by 2):
+  * FP64 plans: 1e-11, raised to 8 * amp * 2^-53 where the amplification
+    amp = max_x sum_n |w_n| / |z_n - ix| of the contour makes FP64 rounding of the
+    individual solves larger (T255 at dt = 3600 s: amp = 3.5e5, bound 3.1e-10).
+  * mixed plans: 1e-8 (the stated bound of the reduced-precision path).
+"""
+import numpy as np
+import pytest
+
+from oracle import coeffs as oc
+from oracle import rexi as orx
+from paper_1805_06557_gb300 import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+OM, A, PB = syn.OMEGA, syn.RADIUS, syn.PHIBAR
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1805_06557_gb300 import rexi
+    return torch, rexi
+
+
+def contour(T, dt, N):
+    X = orx.spectrum_bound(T, dt, OM, A, PB)
+    if X < 20:
+        return min(6.0, 1.6 * X), 1.6 * X, X
+    return 14.0, 1.4 * X, X
+
+
+def fp64_tol(z, w, X):
+    return max(1e-11, 8 * oc.amplification(z, w, X) * 2.0 ** -53)
+
+
+def run_plan(env, T, N, dt, U0, prec, p0, Xc, batch=None, **kw):
+    torch, rexi = env
+    Ub = U0 if U0.ndim == 3 else U0[None]
+    B = Ub.shape[0]
+    plan = rexi.Plan(T, N, dt, OM, A, PB, p0=p0, Xc=Xc, precision=prec, max_batch=B, **kw)
+    u0 = torch.from_numpy(np.ascontiguousarray(Ub)).cuda()
+    u1 = torch.empty_like(u0)
+    plan.step(u0, u1)
+    plan.sync()
+    out = u1.cpu().numpy()
+    info = plan.info()
+    plan.close()
+    return (out if U0.ndim == 3 else out[0]), info
+
+
+def masked_rel(x, ref, T, ms):
+    mask = np.zeros(x.shape[-1], bool)
+    for m in ms:
+        o = m * (2 * T + 3 - m) // 2
+        mask[o: o + T + 1 - m] = True
+    w = np.where(np.arange(x.shape[-1]) <= T, 1.0, 2.0)[mask]
+    num = np.sqrt(np.sum(w * np.abs(x[..., mask] - ref[..., mask]) ** 2, axis=-1))
+    den = np.sqrt(np.sum(w * np.abs(ref[..., mask]) ** 2, axis=-1))
+    return num / den
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_config_T63_N256(env, prec):
+    """T63, N = 256 poles, dt = 3600 s, n^-1.5 Gaussian coefficients (seed 1)."""
+    T, N, dt = 63, 256, 3600.0
+    p0, Xc, X = contour(T, dt, N)
+    U0 = syn.gaussian_state(T, 1)
+    z, w = oc.rexi_coefficients(N, p0, Xc)
+    ref = orx.rexi_step(U0, T, dt, OM, A, PB, z, w)
+    out, info = run_plan(env, T, N, dt, U0, prec, p0, Xc)
+    err = orx.rel_l2(out, ref, T)
+    tol = fp64_tol(z, w, X) if prec == "fp64" else 1e-8
+    assert np.all(err < tol), (err, tol, info)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("T,N", [(1, 8), (2, 40), (5, 33), (17, 96), (40, 64), (47, 200)])
+def test_small_and_ragged(env, prec, T, N):
+    """Tiny truncations (single-element chains), pole counts that are not a multiple of 32,
+    chain lengths that are not a multiple of the 16/32-element blocks."""
+    dt = 3600.0
+    p0, Xc, X = contour(T, dt, N)
+    U0 = syn.gaussian_state(T, 10 + T)
+    z, w = oc.rexi_coefficients(N, p0, Xc)
+    ref = orx.rexi_step(U0, T, dt, OM, A, PB, z, w)
+    out, _ = run_plan(env, T, N, dt, U0, prec, p0, Xc)
+    err = orx.rel_l2(out, ref, T)
+    tol = fp64_tol(z, w, X) if prec == "fp64" else 1e-8
+    assert np.all(err < tol), (err, tol)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_T127_N512(env, prec):
+    """The linear part of the T127 / dt = 1800 s / 512-pole nonlinear configuration."""
+    T, N, dt = 127, 512, 1800.0
+    p0, Xc, X = contour(T, dt, N)
+    U0 = syn.balanced_state(T, 2)
+    U0[2] = syn.gaussian_state(T, 22, scales=(0, 0, 1e-6))[2]
+    z, w = oc.rexi_coefficients(N, p0, Xc)
+    ms = [0, 1, 2, 3, 31, 64, 100, 126, 127]
+    ref = orx.rexi_step(U0, T, dt, OM, A, PB, z, w, m_list=ms)
+    out, _ = run_plan(env, T, N, dt, U0, prec, p0, Xc)
+    err = masked_rel(out, ref, T, ms)
+    tol = fp64_tol(z, w, X) if prec == "fp64" else 1e-8
+    assert np.all(err < tol), (err, tol)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_T255_N512_batched_sampled(env, prec):
+    """Full benchmark size: a batch of 4 T255 states (seeds 101-104), N = 512, dt = 3600 s,
+    in the bench launch configuration; the oracle checks sampled zonal orders."""
+    T, N, dt = 255, 512, 3600.0
+    p0, Xc, X = contour(T, dt, N)
+    U0 = np.stack([syn.gaussian_state(T, 101 + i) for i in range(4)])
+    z, w = oc.rexi_coefficients(N, p0, Xc)
+    ms = [0, 1, 2, 31, 100, 254, 255]
+    out, info = run_plan(env, T, N, dt, U0, prec, p0, Xc)
+    tol = fp64_tol(z, w, X) if prec == "fp64" else 1e-8
+    for b in (0, 3):
+        ref = orx.rexi_step(U0[b], T, dt, OM, A, PB, z, w, m_list=ms)
+        err = masked_rel(out[b], ref, T, ms)
+        assert np.all(err < tol), (b, err, tol, info)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_matches_single_and_is_deterministic(env, prec):
+    torch, rexi = env
+    T, N, dt = 63, 256, 3600.0
+    p0, Xc, X = contour(T, dt, N)
+    U0 = np.stack([syn.gaussian_state(T, 200 + i) for i in range(5)])
+    plan = rexi.Plan(T, N, dt, OM, A, PB, p0=p0, Xc=Xc, precision=prec, max_batch=5)
+    u0 = torch.from_numpy(U0).cuda()
+    u1 = torch.empty_like(u0)
+    plan.step(u0, u1)
+    u1b = torch.empty_like(u0)
+    plan.step(u0, u1b)
+    plan.sync()
+    assert torch.equal(u1, u1b), "repeated call is not bitwise reproducible"
+    tol = 1e-13 if prec == "fp64" else 1e-9
+    for b in range(5):
+        one = torch.empty_like(u0[b:b + 1])
+        plan.step(u0[b:b + 1].contiguous(), one)
+        plan.sync()
+        err = orx.rel_l2(one.cpu().numpy()[0], u1[b].cpu().numpy(), T)
+        assert np.all(err < tol), (b, err)
+    plan.close()
+
+
+def test_step_host_matches_device(env):
+    torch, rexi = env
+    T, N, dt = 31, 64, 3600.0
+    p0, Xc, _ = contour(T, dt, N)
+    U0 = np.stack([syn.gaussian_state(T, 300 + i) for i in range(2)])
+    plan = rexi.Plan(T, N, dt, OM, A, PB, p0=p0, Xc=Xc, precision="fp64", max_batch=2)
+    h = plan.step_host(U0)
+    u0 = torch.from_numpy(U0).cuda()
+    u1 = torch.empty_like(u0)
+    plan.step(u0, u1)
+    plan.sync()
+    assert np.array_equal(h, u1.cpu().numpy())
+    plan.close()
+
+
+def test_explicit_poles_and_zero_input(env):
+    """Poles given explicitly (the oracle's) give the same result; a zero state stays zero."""
+    torch, rexi = env
+    T, N, dt = 21, 64, 3600.0
+    p0, Xc, X = contour(T, dt, N)
+    z, w = oc.rexi_coefficients(N, p0, Xc)
+    U0 = syn.gaussian_state(T, 5)
+    a, _ = run_plan(env, T, N, dt, U0, "fp64", p0, Xc)
+    b, _ = run_plan(env, T, N, dt, U0, "fp64", None, None, z=z, w=w)
+    assert np.max(orx.rel_l2(a, b, T)) < 1e-14
+    zero, _ = run_plan(env, T, N, dt, np.zeros_like(U0), "mixed", p0, Xc)
+    assert np.all(zero == 0)
+
+
+def test_errors(env):
+    torch, rexi = env
+    T, N, dt = 15, 32, 3600.0
+    p0, Xc, _ = contour(T, dt, N)
+    with pytest.raises(rexi.RexiError) as e:
+        rexi.Plan(0, N, dt, OM, A, PB, p0=p0, Xc=Xc)
+    assert e.value.code == rexi.REXI_EINVAL
+    with pytest.raises(rexi.RexiError):
+        rexi.Plan(T, N, -1.0, OM, A, PB, p0=p0, Xc=Xc)
+    with pytest.raises(rexi.RexiError):
+        rexi.Plan(T, N, dt, OM, A, PB, p0=p0, Xc=Xc, precision=7)
+    plan = rexi.Plan(T, N, dt, OM, A, PB, p0=p0, Xc=Xc, max_batch=2)
+    u = torch.zeros(3, 3, rexi.nlm(T), dtype=torch.complex128, device="cuda")
+    assert plan.step_raw(u.data_ptr(), u.data_ptr(), 1) == rexi.REXI_EINVAL      # aliasing
+    assert plan.step_raw(u.data_ptr(), u[1].data_ptr(), 3) == rexi.REXI_EINVAL   # batch > max
+    assert plan.step_raw(u.data_ptr(), u[1].data_ptr(), 0) == rexi.REXI_EINVAL
+    assert plan.step_raw(0, u[1].data_ptr(), 1) == rexi.REXI_EINVAL
+    assert "batch" in rexi.last_error() or "null" in rexi.last_error()
+    assert plan.step_raw(u[0].data_ptr(), u[1].data_ptr(), 1) == rexi.REXI_OK
+    plan.sync()
+    plan.close()
+
+
+def test_mixed_heavy_classification(env):
+    torch, rexi = env
+    T, N, dt = 255, 512, 3600.0
+    p0, Xc, X = contour(T, dt, N)
+    plan = rexi.Plan(T, N, dt, OM, A, PB, p0=p0, Xc=Xc, precision="mixed")
+    z, w, heavy = plan.poles()
+    info = plan.info()
+    assert info["n_heavy"] % 32 == 0 and 0 < info["n_heavy"] < N
+    yi = np.clip(z.imag, -X, X)
+    gain = np.abs(w) / np.abs(z - 1j * yi)
+    assert gain[heavy].min() >= gain[~heavy].max()
+    assert np.sum(gain > 1e-3) <= info["n_heavy"]
+    plan.close()
