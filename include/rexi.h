@@ -163,6 +163,34 @@ int rexi_plan_set_profiling(rexi_plan* plan, int enable);
 int rexi_plan_get_profile(rexi_plan* plan, double* ms, int* launches, int reset);
 
 /*
+ * rexi_step_fp64_static -- the FP64 REXI step for callers that cannot allocate device
+ * memory: code running inside a host framework that owns all device memory through its
+ * own pool, loops that must never trigger the device-wide synchronisation of an
+ * allocation, or deployments that fix every byte at load time.  The paper has no
+ * counterpart; it is a service of this library.
+ *
+ * Computes the same  U1 = sum_n w_n (z_n - dt L)^-1 U0  as an FP64 plan built from
+ * (p0, Xc), for one state, with the same kernels, but takes every table, the elimination
+ * scratch and the partial sums from one fixed array of device memory that is part of the
+ * library image (rexi_static_scratch_bytes(), about 18 MB; every GPU on which the library
+ * is used keeps it until the process exits).  It calls no cudaMalloc / cudaFree and no
+ * allocating routine.
+ *   T <= 63, N <= 1024 (REXI_EINVAL beyond); U0, U1 device pointers of 3*nlm complex128,
+ *   not overlapping; stream: cudaStream_t (NULL = legacy default stream).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and sets the solve kernel's shared-memory limit: make that first call before any stream
+ * capture.  Every call reuses the same array and leaves the last call's contents in it
+ * (everything a call reads is written by it first); calls that overlap on the GPU (two
+ * streams, or two host threads) race on that array and must be serialised by the caller.
+ * Asynchronous on `stream`.  Errors: REXI_EINVAL, REXI_ECUDA.
+ */
+int rexi_step_fp64_static(int T, int N, double dt, double omega, double radius, double phibar,
+                          double p0, double Xc, const void* U0, void* U1, void* stream);
+
+/* Size in bytes of the fixed device array used by rexi_step_fp64_static. */
+long long rexi_static_scratch_bytes(void);
+
+/*
  * rexi_alu_peaks -- measures the FP64 and FP32 FMA throughput of the current device
  * (TFLOP/s, an FMA counted as 2 flops) with two short probe kernels: 8 independent FMA
  * chains per thread, 16 blocks of 256 threads per SM, timed with CUDA events.  These are

@@ -40,7 +40,7 @@ struct Fp64Args {
 constexpr int FP64_WARPS = 4;
 constexpr int FP64_TROW = 33;  // padded row (in double2) of the transposition tile
 
-__global__ void __launch_bounds__(FP64_WARPS * 32)
+static __global__ void __launch_bounds__(FP64_WARPS * 32)
 k_rexi_fp64(Fp64Args a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -145,7 +145,7 @@ inline size_t fp64_smem_bytes() {
 }
 
 // U1 = (bPhi S0 - dt Phibar S_wz, S_zeta, S_delta), summing the Q partial slots in order.
-__global__ void k_rexi_finalize(const double2* __restrict__ U0, const double2* __restrict__ partial,
+static __global__ void k_rexi_finalize(const double2* __restrict__ U0, const double2* __restrict__ partial,
                                 double2* __restrict__ U1, int B, int nlm, int Q, double2 S0,
                                 double hphibar) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;

@@ -113,7 +113,7 @@ struct MixedArgs {
 };
 
 // ---- pre-pass: FP32 and double-float right-hand-side pieces ----------------------------
-__global__ void k_mixed_rhs(const double2* __restrict__ U0, const D4* __restrict__ tab,
+static __global__ void k_mixed_rhs(const double2* __restrict__ U0, const D4* __restrict__ tab,
                             Rhs32* __restrict__ r32, RhsDF* __restrict__ rdf, int B, int nlm) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (long long)B * nlm) return;
@@ -155,7 +155,7 @@ __device__ __forceinline__ void light_fwd(const MixedArgs& a, const PoleF& pf, c
   y = cmulf(make_float2(fmaf(-lo, y.x, r.x), fmaf(-lo, y.y, r.y)), inv);
 }
 
-__global__ void __launch_bounds__(MIX_WARPS * 32)
+static __global__ void __launch_bounds__(MIX_WARPS * 32)
 k_rexi_light(MixedArgs a) {
   __shared__ LightSmem sm[MIX_WARPS];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -296,7 +296,7 @@ __device__ __forceinline__ float2 heavy_residual(const MixedArgs& a, const PoleD
   return make_float2(re.hi + re.lo, im.hi + im.lo);
 }
 
-__global__ void __launch_bounds__(MIX_WARPS * 32)
+static __global__ void __launch_bounds__(MIX_WARPS * 32)
 k_rexi_heavy(MixedArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;

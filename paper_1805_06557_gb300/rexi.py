@@ -71,6 +71,24 @@ _lib.rexi_plan_get_poles.argtypes = [ctypes.c_void_p, _dp, _dp, _ip]
 _lib.rexi_alu_peaks.argtypes = [_dp, _dp]
 _lib.rexi_plan_set_profiling.argtypes = [ctypes.c_void_p, ctypes.c_int]
 _lib.rexi_plan_get_profile.argtypes = [ctypes.c_void_p, _dp, _ip, ctypes.c_int]
+_lib.rexi_step_fp64_static.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 6 + \
+    [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+_lib.rexi_static_scratch_bytes.restype = ctypes.c_longlong
+
+
+def step_fp64_static(T, N, dt, omega, radius, phibar, p0, Xc, U0, U1, stream=None):
+    """Allocation-free FP64 REXI step on one state (CUDA complex128 tensors [3, nlm])."""
+    _check(_lib.rexi_step_fp64_static(int(T), int(N), float(dt), float(omega), float(radius),
+                                      float(phibar), float(p0), float(Xc),
+                                      ctypes.c_void_p(U0.data_ptr()), ctypes.c_void_p(U1.data_ptr()),
+                                      ctypes.c_void_p(_stream_handle(stream))))
+    return U1
+
+
+def static_scratch_bytes():
+    return int(_lib.rexi_static_scratch_bytes())
+
+
 KERNEL_NAMES = ["k_mixed_rhs", "k_rexi_fp64", "k_rexi_light", "k_rexi_heavy", "k_rexi_finalize"]
 
 
