@@ -1,0 +1,76 @@
+/*
+ * sht.h -- spherical-harmonic transforms of librexi (paper Sec. 3.2: the pseudo-spectral
+ * space discretisation whose transforms serve the nonlinear term N(U); the paper uses SHTns,
+ * this is an independent GPU implementation).
+ *
+ * Grid: nlat Gauss-Legendre latitudes (mu = sin(latitude), north to south; nlat even) times
+ * nlon equispaced longitudes lambda_k = 2 pi k / nlon, nlon > 2T.  Grid arrays are
+ * [field][nlat][nlon] FP64, row-major.  Spectral arrays use the layout of rexi.h:
+ * [field][nlm] complex128, m-major, orthonormal Y_n^m without Condon-Shortley phase,
+ * f = sum_n c_n^0 Y_n^0 + 2 Re sum_{m>=1} c_n^m Y_n^m.
+ * Every transform is asynchronous on the plan stream and does not allocate.  Status codes
+ * and rexi_last_error() as in rexi.h.
+ */
+#ifndef SHT_H
+#define SHT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SH_FP64 0  /* Legendre contraction in FP64 on CUDA cores                           */
+#define SH_TF32 1  /* Legendre contraction on tcgen05 tensor cores, TF32 inputs, FP32 sums    */
+#define SH_BF16 2  /* Legendre contraction on tcgen05 tensor cores, BF16 inputs, FP32 sums    */
+
+typedef struct sh_plan sh_plan;
+
+typedef struct sh_plan_desc {
+  int T;            /* triangular truncation, 1 <= T <= 1023                                */
+  int nlat, nlon;   /* Gauss grid, nlat even and > T, nlon > 2T, nlon = 2^p 3^q              */
+  double radius;    /* sphere radius a [m] (vector transforms)                              */
+  int precision;    /* SH_FP64, SH_TF32 or SH_BF16                                          */
+  int max_fields;   /* largest nfields passed to a transform                                */
+  void* stream;     /* cudaStream_t                                                         */
+} sh_plan_desc;
+
+/* Builds the Gauss grid (Newton iteration on P_nlat), the orthonormal associated Legendre
+ * table Pt_n^m(mu_j) and Ht_n^m = (1 - mu^2) dPt_n^m/dmu for the northern half (the
+ * southern half follows from Pt_n^m(-mu) = (-1)^{n-m} Pt_n^m(mu)), the FFT twiddles and a
+ * Fourier-space workspace.  Errors: REXI_EINVAL, REXI_ENOMEM, REXI_ECUDA. */
+int sh_plan_create(const sh_plan_desc* desc, sh_plan** out);
+int sh_plan_destroy(sh_plan* plan);
+
+/* Gauss nodes mu_j and weights w_j (all nlat, north to south) into host arrays. */
+int sh_plan_get_grid(const sh_plan* plan, double* mu, double* w);
+
+/* Scalar synthesis: grid = sum_n c^0 Y^0 + 2 Re sum_{m>=1} c^m Y^m  (Legendre per m, then a
+ * complex-to-real FFT of length nlon).  spec: device [nfields][nlm] complex128; grid: device
+ * [nfields][nlat][nlon] double. */
+int sh_synthesis(sh_plan* plan, const void* spec, void* grid, int nfields);
+
+/* Scalar analysis: c_n^m = sum_j w_j Pt_n^m(mu_j) (2 pi / nlon) sum_k f_jk e^{-i m lambda_k}. */
+int sh_analysis(sh_plan* plan, const void* grid, void* spec, int nfields);
+
+/* Velocity synthesis from stream function psi and velocity potential chi (paper Sec. 3:
+ * V = k x grad psi + grad chi), returned as U = u cos(lat), V = v cos(lat):
+ *   U = (1/a)[-(1-mu^2) dpsi/dmu + dchi/dlambda],  V = (1/a)[dpsi/dlambda + (1-mu^2) dchi/dmu]. */
+int sh_synthesis_uv(sh_plan* plan, const void* psi, const void* chi, void* U, void* V,
+                    int nfields);
+
+/* Divergence and vertical curl of a vector field given as A = P_u cos(lat), B = P_v cos(lat)
+ * on the grid, by integration by parts against conj(Y):
+ *   div_n^m  = (1/a) sum_j w_j/(1-mu_j^2) [ i m A_m Pt_n^m - B_m Ht_n^m ]
+ *   curl_n^m = (1/a) sum_j w_j/(1-mu_j^2) [ i m B_m Pt_n^m + A_m Ht_n^m ]. */
+int sh_analysis_divcurl(sh_plan* plan, const void* A, const void* B, void* div, void* curl,
+                        int nfields);
+
+/* Synchronises the plan stream; returns REXI_ETIMEOUT if a tensor-core kernel's bounded
+ * wait on its copy / MMA barriers gave up since the plan was created (its results are then
+ * invalid), REXI_ECUDA on a CUDA error, REXI_OK otherwise. */
+int sh_plan_check(sh_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHT_H */

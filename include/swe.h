@@ -1,0 +1,53 @@
+/*
+ * swe.h -- nonlinear shallow-water time step of librexi (paper Sec. 3, Eq. 1-3 with the split
+ * into L_g, L_c and N; Sec. 4.4 Strang splitting; Table 2 method identifiers).
+ *
+ * State: device [3][nlm] complex128 (Phi', zeta, delta), layout of rexi.h.
+ * N(U) = ( -div(Phi' V), -div(zeta V), k.curl(zeta V) - lap(V.V/2) ) is evaluated
+ * pseudo-spectrally: psi = lap^-1 zeta, chi = lap^-1 delta, V from (psi, chi) by the vector
+ * synthesis of sht.h, products on the Gauss grid, divergence / curl / scalar analysis.
+ * The linear part L = L_g + L_c (Coriolis inside) is integrated by a REXI plan (rexi.h), the
+ * nonlinear part by 2nd-order explicit Runge-Kutta (midpoint rule).
+ * Status codes and rexi_last_error() as in rexi.h.
+ */
+#ifndef SWE_H
+#define SWE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SWE_L_REXI_N_ERK_VER1 0 /* U+ = N^{dt/2} o L^{dt} o N^{dt/2} (U)  (Sec. 4.4, version 1) */
+#define SWE_L_REXI_N_ERK_VER0 1 /* U+ = L^{dt/2} o N^{dt} o L^{dt/2} (U)  (Sec. 4.4, version 0) */
+
+typedef struct swe_plan swe_plan;
+
+typedef struct swe_plan_desc {
+  int T, nlat, nlon;        /* truncation and Gauss grid (see sht.h)                       */
+  double dt;                /* time step [s]                                                */
+  double omega, radius, phibar;
+  int N;                    /* REXI poles                                                   */
+  double p0, Xc;            /* REXI contour for the linear sub-step (dt for ver1, dt/2 ver0) */
+  int rexi_precision;       /* REXI_FP64 or REXI_MIXED                                      */
+  int sh_precision;         /* SH_FP64, SH_TF32 or SH_BF16                                  */
+  int scheme;               /* SWE_L_REXI_N_ERK_VER1 or SWE_L_REXI_N_ERK_VER0               */
+  void* stream;             /* cudaStream_t                                                  */
+} swe_plan_desc;
+
+/* Creates the REXI plan, the SH plan and all work buffers.
+ * Errors: REXI_EINVAL, REXI_ENOMEM, REXI_ECUDA. */
+int swe_plan_create(const swe_plan_desc* desc, swe_plan** out);
+int swe_plan_destroy(swe_plan* plan);
+
+/* Advances `state` (device, [3][nlm] complex128) in place by nsteps steps of the scheme.
+ * Asynchronous on the plan stream; no allocation.  Errors: REXI_EINVAL, REXI_ECUDA. */
+int swe_step(swe_plan* plan, void* state, int nsteps);
+
+/* tendency = N(state) (device [3][nlm] complex128 each; no aliasing). */
+int swe_nonlinear(swe_plan* plan, const void* state, void* tendency);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWE_H */

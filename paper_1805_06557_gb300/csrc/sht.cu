@@ -1,0 +1,627 @@
+// Spherical-harmonic transforms on a Gaussian grid (paper Sec. 3.2), FP64 path.
+//
+// Synthesis = Legendre contraction per zonal order m (G_m(mu_j) = sum_n c_n^m Pt_n^m(mu_j))
+// followed by a complex-to-real FFT along each latitude; analysis is the reverse.  The
+// Legendre tables hold the northern half only: Pt_n^m(-mu) = (-1)^{n-m} Pt_n^m(mu) and
+// Ht_n^m(-mu) = -(-1)^{n-m} Ht_n^m(mu), so every contraction forms even and odd partial sums
+// over the northern latitudes and combines them for both hemispheres.
+//
+// Layouts: Legendre tables [moff(m)+k][nh] (nh = nlat/2, latitude fastest: coalesced over
+// threads that own latitudes); Fourier workspace [field][m][nlat]; grids [field][nlat][nlon].
+// The FFT is a shared-memory Stockham autosort transform with radix-2 and radix-3 passes,
+// two real latitude rows packed into one complex sequence.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "../../include/sht.h"
+#include "common.cuh"
+#include "sht_tc.cuh"
+
+namespace rexi {
+namespace {
+
+// ---- Legendre tables (scaled three-term recurrence, one thread per (m, latitude)) -------
+__device__ __forceinline__ double eps_d(int n, int m) {
+  if (n <= m) return 0.0;
+  return sqrt((double(n) * n - double(m) * m) / (4.0 * n * n - 1.0));
+}
+
+__global__ void k_legendre_table(const double* __restrict__ mu, double* __restrict__ P,
+                                 double* __restrict__ H, int T, int nh) {
+  const int jh = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = blockIdx.y;
+  if (jh >= nh) return;
+  const double x = mu[jh];
+  const double s = sqrt((1.0 - x) * (1.0 + x));
+  const double TWO256 = 1.157920892373162e77, INV256 = 8.636168555094445e-78;  // 2^256, 2^-256
+  double p = 0.28209479177387814;  // 1/sqrt(4 pi)
+  int e = 0;
+  for (int k = 1; k <= m; ++k) {
+    p *= sqrt((2.0 * k + 1.0) / (2.0 * k)) * s;
+    if (fabs(p) < INV256) {
+      p *= TWO256;
+      e -= 256;
+    }
+  }
+  const size_t base = (size_t)moff(T, m) * nh + jh;
+  // sliding window of converted values v_{n-1}, v_n, v_{n+1}
+  double vprev = 0.0, vcur = ldexp(p, e);
+  double pprev = 0.0, pcur = p;
+  for (int n = m; n <= T; ++n) {
+    // advance the recurrence to n + 1
+    const double pnew = (x * pcur - eps_d(n, m) * pprev) / eps_d(n + 1, m);
+    pprev = pcur;
+    pcur = pnew;
+    if (fabs(pcur) > TWO256) {
+      pcur *= INV256;
+      pprev *= INV256;
+      e += 256;
+    }
+    const double vnext = ldexp(pcur, e);
+    const size_t o = base + (size_t)(n - m) * nh;
+    P[o] = vcur;
+    H[o] = -n * eps_d(n + 1, m) * vnext + (n + 1.0) * eps_d(n, m) * vprev;
+    vprev = vcur;
+    vcur = vnext;
+  }
+}
+
+// ---- Legendre synthesis ------------------------------------------------------------
+constexpr int LTH = 128;
+
+__global__ void __launch_bounds__(LTH) k_leg_synth(const double* __restrict__ P,
+                                                   const double2* __restrict__ spec,
+                                                   double2* __restrict__ F, int T, int nlat, int nlm) {
+  const int m = blockIdx.x, f = blockIdx.y;
+  const int nh = nlat / 2;
+  const int jh = blockIdx.z * LTH + threadIdx.x;
+  if (jh >= nh) return;
+  const int K = T + 1 - m, base = moff(T, m);
+  const double2* c = spec + (size_t)f * nlm + base;
+  const double* Pm = P + (size_t)base * nh + jh;
+  double2 e = make_double2(0, 0), o = make_double2(0, 0);
+  int k = 0;
+  for (; k + 1 < K; k += 2) {
+    const double pe = Pm[(size_t)k * nh], po = Pm[(size_t)(k + 1) * nh];
+    const double2 ce = c[k], co = c[k + 1];
+    e.x = fma(pe, ce.x, e.x);
+    e.y = fma(pe, ce.y, e.y);
+    o.x = fma(po, co.x, o.x);
+    o.y = fma(po, co.y, o.y);
+  }
+  if (k < K) {
+    const double pe = Pm[(size_t)k * nh];
+    e.x = fma(pe, c[k].x, e.x);
+    e.y = fma(pe, c[k].y, e.y);
+  }
+  double2* out = F + ((size_t)f * (T + 1) + m) * nlat;
+  out[jh] = make_double2(e.x + o.x, e.y + o.y);
+  out[nlat - 1 - jh] = make_double2(e.x - o.x, e.y - o.y);
+}
+
+__device__ __forceinline__ double2 imul(int m, double2 v) { return make_double2(-m * v.y, m * v.x); }
+
+__global__ void __launch_bounds__(LTH) k_leg_synth_uv(const double* __restrict__ P,
+                                                      const double* __restrict__ H,
+                                                      const double2* __restrict__ psi,
+                                                      const double2* __restrict__ chi,
+                                                      double2* __restrict__ FU, double2* __restrict__ FV,
+                                                      int T, int nlat, int nlm, double inv_a) {
+  const int m = blockIdx.x, f = blockIdx.y;
+  const int nh = nlat / 2;
+  const int jh = blockIdx.z * LTH + threadIdx.x;
+  if (jh >= nh) return;
+  const int K = T + 1 - m, base = moff(T, m);
+  const double2* cp = psi + (size_t)f * nlm + base;
+  const double2* cc = chi + (size_t)f * nlm + base;
+  const double* Pm = P + (size_t)base * nh + jh;
+  const double* Hm = H + (size_t)base * nh + jh;
+  // [0] even k, [1] odd k
+  double2 pps[2] = {}, pch[2] = {}, hps[2] = {}, hch[2] = {};
+  for (int k = 0; k < K; ++k) {
+    const int par = k & 1;
+    const double p = Pm[(size_t)k * nh], h = Hm[(size_t)k * nh];
+    const double2 a = cp[k], b = cc[k];
+    pps[par].x = fma(p, a.x, pps[par].x);
+    pps[par].y = fma(p, a.y, pps[par].y);
+    pch[par].x = fma(p, b.x, pch[par].x);
+    pch[par].y = fma(p, b.y, pch[par].y);
+    hps[par].x = fma(h, a.x, hps[par].x);
+    hps[par].y = fma(h, a.y, hps[par].y);
+    hch[par].x = fma(h, b.x, hch[par].x);
+    hch[par].y = fma(h, b.y, hch[par].y);
+  }
+  double2* outU = FU + ((size_t)f * (T + 1) + m) * nlat;
+  double2* outV = FV + ((size_t)f * (T + 1) + m) * nlat;
+  for (int hemi = 0; hemi < 2; ++hemi) {
+    // north: P sums e + o, H sums e + o; south: P sums e - o, H sums -(e - o)
+    const double sp = hemi ? -1.0 : 1.0;
+    const double sh = hemi ? -1.0 : 1.0;
+    auto comb = [&](const double2* v, double s_odd, double s_all) {
+      return make_double2(s_all * (v[0].x + s_odd * v[1].x), s_all * (v[0].y + s_odd * v[1].y));
+    };
+    const double2 Pps = comb(pps, sp, 1.0), Pch = comb(pch, sp, 1.0);
+    const double2 Hps = comb(hps, sp, sh), Hch = comb(hch, sp, sh);
+    const double2 ich = imul(m, Pch), ips = imul(m, Pps);
+    const int j = hemi ? nlat - 1 - jh : jh;
+    outU[j] = make_double2(inv_a * (-Hps.x + ich.x), inv_a * (-Hps.y + ich.y));
+    outV[j] = make_double2(inv_a * (ips.x + Hch.x), inv_a * (ips.y + Hch.y));
+  }
+}
+
+// ---- Legendre analysis -------------------------------------------------------------
+constexpr int ATH = 256;
+
+__device__ __forceinline__ double2 warp_sum2(double2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+__global__ void __launch_bounds__(ATH) k_leg_anal(const double* __restrict__ P,
+                                                  const double* __restrict__ w,
+                                                  const double2* __restrict__ F,
+                                                  double2* __restrict__ spec, int T, int nlat, int nlm) {
+  extern __shared__ double2 sm2[];
+  const int m = blockIdx.x, f = blockIdx.y;
+  const int nh = nlat / 2;
+  double2* Se = sm2;
+  double2* So = sm2 + nh;
+  const double2* in = F + ((size_t)f * (T + 1) + m) * nlat;
+  for (int j = threadIdx.x; j < nh; j += ATH) {
+    const double2 a = in[j], b = in[nlat - 1 - j];
+    const double wj = w[j];
+    Se[j] = make_double2(wj * (a.x + b.x), wj * (a.y + b.y));
+    So[j] = make_double2(wj * (a.x - b.x), wj * (a.y - b.y));
+  }
+  __syncthreads();
+  const int K = T + 1 - m, base = moff(T, m);
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  for (int k = wp; k < K; k += ATH / 32) {
+    const double* Pk = P + (size_t)(base + k) * nh;
+    const double2* src = (k & 1) ? So : Se;
+    double2 acc = make_double2(0, 0);
+    for (int j = lane; j < nh; j += 32) {
+      const double p = Pk[j];
+      acc.x = fma(p, src[j].x, acc.x);
+      acc.y = fma(p, src[j].y, acc.y);
+    }
+    acc = warp_sum2(acc);
+    if (lane == 0) spec[(size_t)f * nlm + base + k] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(ATH) k_leg_anal_divcurl(const double* __restrict__ P,
+                                                          const double* __restrict__ H,
+                                                          const double* __restrict__ wq,
+                                                          const double2* __restrict__ FA,
+                                                          const double2* __restrict__ FB,
+                                                          double2* __restrict__ dv,
+                                                          double2* __restrict__ cu, int T, int nlat,
+                                                          int nlm, double inv_a) {
+  extern __shared__ double2 sm2[];
+  const int m = blockIdx.x, f = blockIdx.y;
+  const int nh = nlat / 2;
+  double2* Ap = sm2;
+  double2* Am = sm2 + nh;
+  double2* Bp = sm2 + 2 * nh;
+  double2* Bm = sm2 + 3 * nh;
+  const double2* ia = FA + ((size_t)f * (T + 1) + m) * nlat;
+  const double2* ib = FB + ((size_t)f * (T + 1) + m) * nlat;
+  for (int j = threadIdx.x; j < nh; j += ATH) {
+    const double2 an = ia[j], as = ia[nlat - 1 - j], bn = ib[j], bs = ib[nlat - 1 - j];
+    const double q = wq[j];
+    Ap[j] = make_double2(q * (an.x + as.x), q * (an.y + as.y));
+    Am[j] = make_double2(q * (an.x - as.x), q * (an.y - as.y));
+    Bp[j] = make_double2(q * (bn.x + bs.x), q * (bn.y + bs.y));
+    Bm[j] = make_double2(q * (bn.x - bs.x), q * (bn.y - bs.y));
+  }
+  __syncthreads();
+  const int K = T + 1 - m, base = moff(T, m);
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  for (int k = wp; k < K; k += ATH / 32) {
+    const double* Pk = P + (size_t)(base + k) * nh;
+    const double* Hk = H + (size_t)(base + k) * nh;
+    const bool odd = k & 1;
+    // P terms pair with (north + s south), H terms with (north - s south), s = (-1)^k
+    const double2* AP = odd ? Am : Ap;
+    const double2* BP = odd ? Bm : Bp;
+    const double2* AH = odd ? Ap : Am;
+    const double2* BH = odd ? Bp : Bm;
+    double2 sPA = make_double2(0, 0), sPB = sPA, sHA = sPA, sHB = sPA;
+    for (int j = lane; j < nh; j += 32) {
+      const double p = Pk[j], h = Hk[j];
+      sPA.x = fma(p, AP[j].x, sPA.x);
+      sPA.y = fma(p, AP[j].y, sPA.y);
+      sPB.x = fma(p, BP[j].x, sPB.x);
+      sPB.y = fma(p, BP[j].y, sPB.y);
+      sHA.x = fma(h, AH[j].x, sHA.x);
+      sHA.y = fma(h, AH[j].y, sHA.y);
+      sHB.x = fma(h, BH[j].x, sHB.x);
+      sHB.y = fma(h, BH[j].y, sHB.y);
+    }
+    sPA = warp_sum2(sPA);
+    sPB = warp_sum2(sPB);
+    sHA = warp_sum2(sHA);
+    sHB = warp_sum2(sHB);
+    if (lane == 0) {
+      const double2 iPA = imul(m, sPA), iPB = imul(m, sPB);
+      dv[(size_t)f * nlm + base + k] = make_double2(inv_a * (iPA.x - sHB.x), inv_a * (iPA.y - sHB.y));
+      cu[(size_t)f * nlm + base + k] = make_double2(inv_a * (iPB.x + sHA.x), inv_a * (iPB.y + sHA.y));
+    }
+  }
+}
+
+// ---- longitude FFT (Stockham autosort, radix 2 and 3, shared memory) ---------------------
+struct FftPlan {
+  int n, nrad;
+  int rad[24];
+};
+
+constexpr int FTH = 256;
+constexpr double SQRT3_2 = 0.86602540378443864676;  // sin(2 pi / 3)
+
+// in-place on two shared buffers; returns the buffer holding the result.  sign = -1 forward,
+// +1 inverse (no scaling).  tw[k] = e^{-2 pi i k / n}.
+__device__ double2* fft_smem(double2* a, double2* b, const FftPlan& fp, const double2* __restrict__ tw,
+                             int sign) {
+  const int n = fp.n;
+  int Ns = 1;
+  for (int s = 0; s < fp.nrad; ++s) {
+    const int R = fp.rad[s];
+    const int nb = n / R;
+    const int stride = n / (Ns * R);
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+      const int jm = j % Ns;
+      double2 v[3];
+      for (int r = 0; r < R; ++r) {
+        double2 x = a[j + r * nb];
+        if (r > 0) {
+          double2 t = tw[(r * jm * stride) % n];
+          if (sign > 0) t.y = -t.y;
+          x = cmul(x, t);
+        }
+        v[r] = x;
+      }
+      const int idxD = (j / Ns) * Ns * R + jm;
+      if (R == 2) {
+        b[idxD] = cadd(v[0], v[1]);
+        b[idxD + Ns] = make_double2(v[0].x - v[1].x, v[0].y - v[1].y);
+      } else {  // R == 3
+        const double2 t1 = cadd(v[1], v[2]);
+        const double2 t2 = make_double2(v[0].x - 0.5 * t1.x, v[0].y - 0.5 * t1.y);
+        const double2 d = make_double2(v[1].x - v[2].x, v[1].y - v[2].y);
+        const double sg = sign * SQRT3_2;
+        // i * sg * d = (-sg d.y, sg d.x)
+        b[idxD] = cadd(v[0], t1);
+        b[idxD + Ns] = make_double2(t2.x - sg * d.y, t2.y + sg * d.x);
+        b[idxD + 2 * Ns] = make_double2(t2.x + sg * d.y, t2.y - sg * d.x);
+      }
+    }
+    __syncthreads();
+    double2* t = a;
+    a = b;
+    b = t;
+    Ns *= R;
+  }
+  return a;
+}
+
+// synthesis: F[field][m][nlat] (m <= T) -> grid[field][nlat][nlon], two latitude rows per block
+__global__ void __launch_bounds__(FTH) k_fft_synth(const double2* __restrict__ F, double* __restrict__ grid,
+                                                   FftPlan fp, const double2* __restrict__ tw, int T,
+                                                   int nlat) {
+  extern __shared__ double2 sm2[];
+  const int n = fp.n;
+  const int f = blockIdx.y;
+  const int j0 = 2 * blockIdx.x;
+  double2* a = sm2;
+  double2* b = sm2 + n;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) a[k] = make_double2(0.0, 0.0);
+  __syncthreads();
+  const double2* in = F + (size_t)f * (T + 1) * nlat;
+  for (int m = threadIdx.x; m <= T; m += blockDim.x) {
+    const double2 A = in[(size_t)m * nlat + j0], B = in[(size_t)m * nlat + j0 + 1];
+    if (m == 0) {
+      a[0] = make_double2(A.x, B.x);
+    } else {
+      a[m] = make_double2(A.x - B.y, A.y + B.x);       // A + i B
+      a[n - m] = make_double2(A.x + B.y, B.x - A.y);   // conj(A) + i conj(B)
+    }
+  }
+  __syncthreads();
+  const double2* z = fft_smem(a, b, fp, tw, +1);
+  double* r0 = grid + ((size_t)f * nlat + j0) * n;
+  double* r1 = r0 + n;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    r0[k] = z[k].x;
+    r1[k] = z[k].y;
+  }
+}
+
+// analysis: grid[field][nlat][nlon] -> F[field][m][nlat] = (2 pi / n) sum_k f e^{-i m lambda_k}
+__global__ void __launch_bounds__(FTH) k_fft_anal(const double* __restrict__ grid, double2* __restrict__ F,
+                                                  FftPlan fp, const double2* __restrict__ tw, int T,
+                                                  int nlat) {
+  extern __shared__ double2 sm2[];
+  const int n = fp.n;
+  const int f = blockIdx.y;
+  const int j0 = 2 * blockIdx.x;
+  double2* a = sm2;
+  double2* b = sm2 + n;
+  const double* r0 = grid + ((size_t)f * nlat + j0) * n;
+  const double* r1 = r0 + n;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) a[k] = make_double2(r0[k], r1[k]);
+  __syncthreads();
+  const double2* z = fft_smem(a, b, fp, tw, -1);
+  const double sc = 3.14159265358979323846 / n;  // (2 pi / n) / 2
+  double2* out = F + (size_t)f * (T + 1) * nlat;
+  for (int m = threadIdx.x; m <= T; m += blockDim.x) {
+    const double2 zm = z[m], zn = z[m == 0 ? 0 : n - m];
+    // A = (Z_m + conj(Z_{n-m})) / 2,  B = (Z_m - conj(Z_{n-m})) / (2i)
+    out[(size_t)m * nlat + j0] = make_double2(sc * (zm.x + zn.x), sc * (zm.y - zn.y));
+    out[(size_t)m * nlat + j0 + 1] = make_double2(sc * (zm.y + zn.y), -sc * (zm.x - zn.x));
+  }
+}
+
+// Gauss-Legendre nodes (north to south) and weights: Newton iteration on P_n
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+    }
+    x[i] = z;
+    x[n - 1 - i] = -z;
+    w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+bool fft_factor(int n, FftPlan& fp) {
+  fp.n = n;
+  fp.nrad = 0;
+  int m = n;
+  while (m % 2 == 0 && fp.nrad < 24) {
+    fp.rad[fp.nrad++] = 2;
+    m /= 2;
+  }
+  while (m % 3 == 0 && fp.nrad < 24) {
+    fp.rad[fp.nrad++] = 3;
+    m /= 3;
+  }
+  return m == 1;
+}
+
+}  // namespace
+}  // namespace rexi
+
+using namespace rexi;
+
+struct sh_plan {
+  sh_plan_desc d{};
+  int nh = 0, nlm = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<double> mu, w;
+  double* d_mu = nullptr;   // northern nodes [nh]
+  double* d_w = nullptr;    // northern weights [nh]
+  double* d_wq = nullptr;   // w / (1 - mu^2) [nh]
+  double* d_P = nullptr;    // [nlm][nh]
+  double* d_H = nullptr;
+  double2* d_tw = nullptr;  // [nlon]
+  double2* d_F = nullptr;   // Fourier workspace [2 * max_fields][T+1][nlat]
+  FftPlan fp{};
+  TcLegendre* tc = nullptr;  // tensor-core Legendre state (SH_TF32 / SH_BF16)
+};
+
+static size_t fft_smem(const sh_plan* p) { return sizeof(double2) * 2 * (size_t)p->d.nlon; }
+
+extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
+  if (!desc || !out) return fail(REXI_EINVAL, "sh_plan_create: null argument");
+  *out = nullptr;
+  const sh_plan_desc& d = *desc;
+  if (d.T < 1 || d.T > 1023) return fail(REXI_EINVAL, "sh_plan_create: T = %d outside [1, 1023]", d.T);
+  if (d.nlat < 2 || d.nlat % 2 || d.nlat <= d.T)
+    return fail(REXI_EINVAL, "sh_plan_create: nlat must be even and > T (got %d)", d.nlat);
+  if (d.nlon <= 2 * d.T) return fail(REXI_EINVAL, "sh_plan_create: nlon must exceed 2T");
+  if (!(d.radius > 0) || d.max_fields < 1) return fail(REXI_EINVAL, "sh_plan_create: radius > 0, max_fields >= 1");
+  if (d.precision != SH_FP64 && d.precision != SH_TF32 && d.precision != SH_BF16)
+    return fail(REXI_EINVAL, "sh_plan_create: unknown precision %d", d.precision);
+  sh_plan* p = new sh_plan();
+  p->d = d;
+  p->nh = d.nlat / 2;
+  p->nlm = (d.T + 1) * (d.T + 2) / 2;
+  p->stream = (cudaStream_t)d.stream;
+  auto bail = [&](int code) {
+    sh_plan_destroy(p);
+    return code;
+  };
+  if (!fft_factor(d.nlon, p->fp)) return bail(fail(REXI_EINVAL, "nlon = %d is not 2^p 3^q", d.nlon));
+  if (fft_smem(p) > 200 * 1024) return bail(fail(REXI_EINVAL, "nlon = %d too large", d.nlon));
+  gauss_legendre(d.nlat, p->mu, p->w);
+  std::vector<double> wq(p->nh);
+  for (int j = 0; j < p->nh; ++j) wq[j] = p->w[j] / ((1.0 - p->mu[j]) * (1.0 + p->mu[j]));
+  std::vector<double2> tw(d.nlon);
+  for (int k = 0; k < d.nlon; ++k) {
+    const double a = -2.0 * M_PI * k / d.nlon;
+    tw[k] = make_double2(std::cos(a), std::sin(a));
+  }
+  const size_t tab = (size_t)p->nlm * p->nh;
+  cudaError_t e;
+  if ((e = cudaMalloc(&p->d_mu, sizeof(double) * p->nh)) || (e = cudaMalloc(&p->d_w, sizeof(double) * p->nh)) ||
+      (e = cudaMalloc(&p->d_wq, sizeof(double) * p->nh)) || (e = cudaMalloc(&p->d_P, sizeof(double) * tab)) ||
+      (e = cudaMalloc(&p->d_H, sizeof(double) * tab)) || (e = cudaMalloc(&p->d_tw, sizeof(double2) * d.nlon)) ||
+      (e = cudaMalloc(&p->d_F, sizeof(double2) * 2 * (size_t)d.max_fields * (d.T + 1) * d.nlat))) {
+    cudaGetLastError();
+    return bail(fail(REXI_ENOMEM, "sh_plan_create: cudaMalloc failed: %s", cudaGetErrorString(e)));
+  }
+  if ((e = cudaMemcpy(p->d_mu, p->mu.data(), sizeof(double) * p->nh, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(p->d_w, p->w.data(), sizeof(double) * p->nh, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(p->d_wq, wq.data(), sizeof(double) * p->nh, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(p->d_tw, tw.data(), sizeof(double2) * d.nlon, cudaMemcpyHostToDevice)))
+    return bail(cuda_fail(e, "sh_plan_create: cudaMemcpy"));
+  k_legendre_table<<<dim3((p->nh + 127) / 128, d.T + 1), 128, 0, p->stream>>>(p->d_mu, p->d_P, p->d_H, d.T, p->nh);
+  if ((e = cudaGetLastError())) return bail(cuda_fail(e, "k_legendre_table"));
+  if ((e = cudaFuncSetAttribute(k_fft_synth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p))) ||
+      (e = cudaFuncSetAttribute(k_fft_anal, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p))))
+    return bail(cuda_fail(e, "cudaFuncSetAttribute(fft)"));
+  if (d.precision != SH_FP64) {
+    int rc = tc_legendre_create(&p->tc, p->d_P, p->d_H, p->d_w, p->d_wq, d.T, d.nlat, d.max_fields,
+                                d.precision == SH_BF16, p->stream);
+    if (rc) return bail(rc);
+  }
+  if ((e = cudaStreamSynchronize(p->stream))) return bail(cuda_fail(e, "sh_plan_create: table kernel"));
+  *out = p;
+  return REXI_OK;
+}
+
+extern "C" int sh_plan_destroy(sh_plan* p) {
+  if (!p) return REXI_OK;
+  cudaStreamSynchronize(p->stream);
+  cudaFree(p->d_mu);
+  cudaFree(p->d_w);
+  cudaFree(p->d_wq);
+  cudaFree(p->d_P);
+  cudaFree(p->d_H);
+  cudaFree(p->d_tw);
+  cudaFree(p->d_F);
+  tc_legendre_destroy(p->tc);
+  delete p;
+  return REXI_OK;
+}
+
+extern "C" int sh_plan_get_grid(const sh_plan* p, double* mu, double* w) {
+  if (!p) return fail(REXI_EINVAL, "sh_plan_get_grid: null plan");
+  for (int j = 0; j < p->d.nlat; ++j) {
+    if (mu) mu[j] = p->mu[j];
+    if (w) w[j] = p->w[j];
+  }
+  return REXI_OK;
+}
+
+static int check_call(sh_plan* p, const void* a, const void* b, int nf, const char* who) {
+  if (!p || !a || !b) return fail(REXI_EINVAL, "%s: null argument", who);
+  if (nf < 1 || nf > p->d.max_fields) return fail(REXI_EINVAL, "%s: nfields %d outside [1, %d]", who, nf, p->d.max_fields);
+  return REXI_OK;
+}
+
+// Fourier buffer slots: slot 0 = first nf fields, slot 1 = second
+static double2* fslot(sh_plan* p, int s) {
+  return p->d_F + (size_t)s * p->d.max_fields * (p->d.T + 1) * p->d.nlat;
+}
+
+static int launch_fft_synth(sh_plan* p, const double2* F, double* grid, int nf) {
+  k_fft_synth<<<dim3(p->d.nlat / 2, nf), FTH, fft_smem(p), p->stream>>>(F, grid, p->fp, p->d_tw, p->d.T, p->d.nlat);
+  return REXI_OK;
+}
+static int launch_fft_anal(sh_plan* p, const double* grid, double2* F, int nf) {
+  k_fft_anal<<<dim3(p->d.nlat / 2, nf), FTH, fft_smem(p), p->stream>>>(grid, F, p->fp, p->d_tw, p->d.T, p->d.nlat);
+  return REXI_OK;
+}
+
+extern "C" int sh_synthesis(sh_plan* p, const void* spec, void* grid, int nf) {
+  int rc = check_call(p, spec, grid, nf, "sh_synthesis");
+  if (rc) return rc;
+  double2* F = fslot(p, 0);
+  if (p->tc) {
+    rc = tc_leg_synth(p->tc, (const double2*)spec, F, nf, p->stream);
+    if (rc) return rc;
+  } else {
+    k_leg_synth<<<dim3(p->d.T + 1, nf, (p->nh + LTH - 1) / LTH), LTH, 0, p->stream>>>(
+        p->d_P, (const double2*)spec, F, p->d.T, p->d.nlat, p->nlm);
+  }
+  launch_fft_synth(p, F, (double*)grid, nf);
+  cudaError_t e = cudaGetLastError();
+  return e ? cuda_fail(e, "sh_synthesis") : REXI_OK;
+}
+
+extern "C" int sh_analysis(sh_plan* p, const void* grid, void* spec, int nf) {
+  int rc = check_call(p, grid, spec, nf, "sh_analysis");
+  if (rc) return rc;
+  double2* F = fslot(p, 0);
+  launch_fft_anal(p, (const double*)grid, F, nf);
+  if (p->tc) {
+    rc = tc_leg_anal(p->tc, F, (double2*)spec, nf, p->stream);
+    if (rc) return rc;
+  } else {
+    k_leg_anal<<<dim3(p->d.T + 1, nf), ATH, sizeof(double2) * 2 * p->nh, p->stream>>>(
+        p->d_P, p->d_w, F, (double2*)spec, p->d.T, p->d.nlat, p->nlm);
+  }
+  cudaError_t e = cudaGetLastError();
+  return e ? cuda_fail(e, "sh_analysis") : REXI_OK;
+}
+
+extern "C" int sh_synthesis_uv(sh_plan* p, const void* psi, const void* chi, void* U, void* V, int nf) {
+  int rc = check_call(p, psi, chi, nf, "sh_synthesis_uv");
+  if (rc) return rc;
+  if (!U || !V) return fail(REXI_EINVAL, "sh_synthesis_uv: null output");
+  double2* FU = fslot(p, 0);
+  double2* FV = fslot(p, 1);
+  if (p->tc) {
+    rc = tc_leg_synth_uv(p->tc, (const double2*)psi, (const double2*)chi, FU, FV, nf, 1.0 / p->d.radius, p->stream);
+    if (rc) return rc;
+  } else {
+    k_leg_synth_uv<<<dim3(p->d.T + 1, nf, (p->nh + LTH - 1) / LTH), LTH, 0, p->stream>>>(
+        p->d_P, p->d_H, (const double2*)psi, (const double2*)chi, FU, FV, p->d.T, p->d.nlat, p->nlm,
+        1.0 / p->d.radius);
+  }
+  launch_fft_synth(p, FU, (double*)U, nf);
+  launch_fft_synth(p, FV, (double*)V, nf);
+  cudaError_t e = cudaGetLastError();
+  return e ? cuda_fail(e, "sh_synthesis_uv") : REXI_OK;
+}
+
+extern "C" int sh_analysis_divcurl(sh_plan* p, const void* A, const void* B, void* dv, void* cu, int nf) {
+  int rc = check_call(p, A, B, nf, "sh_analysis_divcurl");
+  if (rc) return rc;
+  if (!dv || !cu) return fail(REXI_EINVAL, "sh_analysis_divcurl: null output");
+  double2* FA = fslot(p, 0);
+  double2* FB = fslot(p, 1);
+  launch_fft_anal(p, (const double*)A, FA, nf);
+  launch_fft_anal(p, (const double*)B, FB, nf);
+  if (p->tc) {
+    rc = tc_leg_anal_divcurl(p->tc, FA, FB, (double2*)dv, (double2*)cu, nf, 1.0 / p->d.radius, p->stream);
+    if (rc) return rc;
+  } else {
+    k_leg_anal_divcurl<<<dim3(p->d.T + 1, nf), ATH, sizeof(double2) * 4 * p->nh, p->stream>>>(
+        p->d_P, p->d_H, p->d_wq, FA, FB, (double2*)dv, (double2*)cu, p->d.T, p->d.nlat, p->nlm,
+        1.0 / p->d.radius);
+  }
+  cudaError_t e = cudaGetLastError();
+  return e ? cuda_fail(e, "sh_analysis_divcurl") : REXI_OK;
+}
+
+extern "C" int sh_plan_check(sh_plan* p) {
+  if (!p) return fail(REXI_EINVAL, "sh_plan_check: null plan");
+  REXI_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  REXI_CUDA_TRY(cudaGetLastError());
+  int flag = 0;
+  int rc = tc_legendre_error(p->tc, &flag);
+  if (rc) return rc;
+  if (flag) return fail(REXI_ETIMEOUT, "sh_plan_check: a tensor-core wait timed out (code %d)", flag);
+  return REXI_OK;
+}

@@ -1,0 +1,591 @@
+// Tensor-core (tcgen05) Legendre contractions for sh_plan precisions SH_TF32 / SH_BF16
+// (paper Sec. 3.2: the dense Legendre contraction per zonal order m of the SH transforms).
+//
+// Every contraction is a set of GEMM jobs D[128 x Ncols] = A[128 x K] B[K x Ncols]:
+//   synthesis, per (m, parity of n - m, 128-latitude tile, table P or H):
+//       A = table^T (rows = northern latitudes, K = degrees of that parity),
+//       B = spectral coefficients (columns = fields x re/im [x psi/chi])
+//   analysis, per (m, parity, 128-degree tile, table P or H):
+//       A = table (rows = degrees of that parity, K = northern latitudes),
+//       B = weighted hemispheric sums / differences of the Fourier coefficients.
+// Operands are stored in the canonical no-swizzle K-major layout of the tensor cores
+// (8-row x 16-byte core matrices; cores adjacent along K 128 B apart), the tables pre-tiled
+// at plan time so that each K-chunk of A is one contiguous block moved by the bulk-copy
+// engine (cp.async.bulk, completion on an mbarrier) into a 3-stage shared-memory ring.
+// One thread issues the MMAs (accumulator in TMEM, FP32); after the last commit all four
+// warps read the accumulator rows with tcgen05.ld and store D.  Epilogue kernels combine
+// the parities (north = even + odd, south = even - odd for P; the opposite sign for H) in
+// FP64.  All mbarrier waits are bounded; on a timeout the kernel records an error flag.
+#include <algorithm>
+#include <cuda_bf16.h>
+#include <vector>
+
+#include "sht_tc.cuh"
+#include "tc_common.cuh"
+
+namespace rexi {
+
+namespace {
+
+constexpr int TC_STAGES = 3;
+constexpr int TC_MAXCOL = 32;
+
+struct Job {
+  long long a_off;  // byte offset of the job's first A chunk in its table
+  int b_off;        // byte offset of the job's B operand in the B buffer
+  int d_off;        // float offset of the job's D tile in the D buffer
+  int nchunk;       // K chunks
+  int kpad;         // K extent of B (nchunk * KC)
+  int tab;          // 0 = P, 1 = H
+  int pad;
+};
+
+struct GemmArgs {
+  const unsigned char* tabP;
+  const unsigned char* tabH;
+  const unsigned char* B;
+  float* D;
+  const Job* jobs;
+  int njobs, ncols, bf16;
+  int* err;
+};
+
+__global__ void __launch_bounds__(128) k_tc_gemm(GemmArgs g) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x;
+  const int jid = blockIdx.x;
+  if (jid >= g.njobs) return;
+  const Job jb = g.jobs[jid];
+  const int E = g.bf16 ? 8 : 4, eb = g.bf16 ? 2 : 4, kstep = g.bf16 ? 16 : 8;
+  const int KC = g.bf16 ? 64 : 32;
+  const uint32_t chunk_bytes = 128u * KC * eb;
+  const uint32_t b_bytes = (uint32_t)g.ncols * jb.kpad * eb;
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + TC_STAGES * chunk_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + ((b_bytes + 127) / 128) * 128);
+  // bars: full[0..S), done[0..S), bfull, final ; then the TMEM address
+  uint32_t* taddr_s = reinterpret_cast<uint32_t*>(bars + 2 * TC_STAGES + 2);
+  const uint32_t full0 = tc::smem_u32(bars), done0 = full0 + 8 * TC_STAGES;
+  const uint32_t bfull = full0 + 16 * TC_STAGES, fin = bfull + 8;
+  const uint32_t ncols_alloc = 32;
+  if (tid == 0) {
+    for (int i = 0; i < 2 * TC_STAGES + 2; ++i) tc::mbar_init(full0 + 8 * i, 1);
+    tc::mbar_fence_init();
+  }
+  __syncthreads();
+  if (tid < 32) tc::tmem_alloc(tc::smem_u32(taddr_s), ncols_alloc);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *taddr_s;
+  const unsigned char* A = (jb.tab ? g.tabH : g.tabP) + jb.a_off;
+  bool ok = true;
+  if (tid == 0) {
+    const uint32_t idesc = tc::instr_desc(128, g.ncols, g.bf16 ? 1 : 2);
+    const uint32_t sa0 = tc::smem_u32(sA), sb0 = tc::smem_u32(sB);
+    const uint32_t sboA = (uint32_t)(KC / E) * 128u, sboB = (uint32_t)(jb.kpad / E) * 128u;
+    tc::mbar_expect_tx(bfull, b_bytes);
+    tc::bulk_g2s(sb0, g.B + jb.b_off, b_bytes, bfull);
+    const int pre = min(TC_STAGES, jb.nchunk);
+    for (int c = 0; c < pre; ++c) {
+      tc::mbar_expect_tx(full0 + 8 * c, chunk_bytes);
+      tc::bulk_g2s(sa0 + c * chunk_bytes, A + (size_t)c * chunk_bytes, chunk_bytes, full0 + 8 * c);
+    }
+    ok = tc::mbar_wait(bfull, 0);
+    int issued = pre;
+    for (int c = 0; c < jb.nchunk && ok; ++c) {
+      const int s = c % TC_STAGES;
+      ok = tc::mbar_wait(full0 + 8 * s, (c / TC_STAGES) & 1);
+      if (!ok) break;
+      tc::fence_after_sync();
+#pragma unroll 1
+      for (int kk = 0; kk < KC; kk += kstep) {
+        const uint64_t ad = tc::smem_desc(sa0 + s * chunk_bytes + (kk / E) * 128u, 128u, sboA);
+        const uint64_t bd = tc::smem_desc(sb0 + ((c * KC + kk) / E) * 128u, 128u, sboB);
+        const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+        if (g.bf16) tc::mma_f16(tmem, ad, bd, idesc, acc);
+        else tc::mma_tf32(tmem, ad, bd, idesc, acc);
+      }
+      tc::mma_commit(done0 + 8 * s);
+      if (c + TC_STAGES < jb.nchunk) {
+        ok = tc::mbar_wait(done0 + 8 * s, (c / TC_STAGES) & 1);
+        if (!ok) break;
+        tc::mbar_expect_tx(full0 + 8 * s, chunk_bytes);
+        tc::bulk_g2s(sa0 + s * chunk_bytes, A + (size_t)(c + TC_STAGES) * chunk_bytes, chunk_bytes,
+                     full0 + 8 * s);
+        ++issued;
+      }
+    }
+    if (!ok) {
+      // drain: wait (bounded) for every bulk copy issued so far before the block exits
+      for (int c = 0; c < issued; ++c) tc::mbar_wait(full0 + 8 * (c % TC_STAGES), (c / TC_STAGES) & 1, 100000u);
+      atomicExch(g.err, 1);
+    }
+    tc::mma_commit(fin);
+  }
+  __syncwarp();
+  const bool fin_ok = tc::mbar_wait(fin, 0);
+  tc::fence_after_sync();
+  const int w = tid >> 5, lane = tid & 31;
+  if (fin_ok) {
+    float* Dj = g.D + jb.d_off + (size_t)(32 * w + lane) * g.ncols;
+    for (int c = 0; c < g.ncols; c += 8) {
+      float v[8];
+      tc::tmem_ld8(tmem + ((uint32_t)(32 * w) << 16) + c, v);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) Dj[c + i] = v[i];
+    }
+  } else if (lane == 0) {
+    atomicExch(g.err, 2);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (tid < 32) tc::tmem_dealloc(tmem, ncols_alloc);
+}
+
+// ---- canonical layout helpers ---------------------------------------------------------
+__device__ __forceinline__ size_t canon_off(int row, int kk, int E, int eb, int sbo) {
+  return (size_t)(row >> 3) * sbo + (size_t)(kk / E) * 128 + (row & 7) * 16 + (kk % E) * eb;
+}
+__device__ __forceinline__ void store_elem(unsigned char* base, size_t off, float v, int bf16) {
+  if (bf16) {
+    *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(v);
+  } else {
+    uint32_t t;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(v));
+    *reinterpret_cast<uint32_t*>(base + off) = t;
+  }
+}
+
+// tables: one thread per (job, row), looping over K; src = FP64 table [moff+k][nh]
+struct TabJob {
+  long long a_off;
+  int m, par, tile, nchunk;
+};
+__global__ void k_tc_table(const double* __restrict__ src, unsigned char* __restrict__ dst,
+                           const TabJob* __restrict__ jobs, int njobs, int T, int nh, int synth,
+                           int bf16) {
+  const int jid = blockIdx.x;
+  if (jid >= njobs) return;
+  const TabJob j = jobs[jid];
+  const int r = threadIdx.x;  // 0..127
+  const int E = bf16 ? 8 : 4, eb = bf16 ? 2 : 4, KC = bf16 ? 64 : 32;
+  const int sbo = (KC / E) * 128;
+  const int K = T + 1 - j.m, base = moff(T, j.m);
+  unsigned char* out = dst + j.a_off;
+  for (int c = 0; c < j.nchunk; ++c) {
+    unsigned char* ch = out + (size_t)c * 128 * KC * eb;
+    for (int kk = 0; kk < KC; ++kk) {
+      float v = 0.f;
+      if (synth) {  // rows = latitudes, K = degrees of the parity
+        const int lat = j.tile * 128 + r;
+        const int k = j.par + 2 * (c * KC + kk);
+        if (lat < nh && k < K) v = (float)src[(size_t)(base + k) * nh + lat];
+      } else {      // rows = degrees of the parity, K = latitudes
+        const int k = j.par + 2 * (j.tile * 128 + r);
+        const int lat = c * KC + kk;
+        if (lat < nh && k < K) v = (float)src[(size_t)(base + k) * nh + lat];
+      }
+      store_elem(ch, canon_off(r, kk, E, eb, sbo), v, bf16);
+    }
+  }
+}
+
+// synthesis B operand of (m, par): column col = f * cpf + q, K index kk <-> k = par + 2 kk.
+// q in [0, cpf): scalar (cpf = 2): re, im of spec f; vector (cpf = 4): psi re, psi im, chi re,
+// chi im.
+__global__ void k_tc_bsynth(const double2* __restrict__ s0, const double2* __restrict__ s1,
+                            unsigned char* __restrict__ B, const int* __restrict__ boff,
+                            const int* __restrict__ kpad, int T, int nlm, int nf, int cpf, int ncols,
+                            int bf16) {
+  const int m = blockIdx.x, par = blockIdx.y;
+  const int id = m * 2 + par;
+  const int kp = kpad[id];
+  if (kp == 0) return;
+  const int E = bf16 ? 8 : 4, eb = bf16 ? 2 : 4;
+  const int sbo = (kp / E) * 128;
+  const int K = T + 1 - m, base = moff(T, m);
+  unsigned char* out = B + boff[id];
+  for (int idx = threadIdx.x; idx < ncols * kp; idx += blockDim.x) {
+    const int col = idx / kp, kk = idx - col * kp;
+    const int k = par + 2 * kk;
+    float v = 0.f;
+    const int f = col / cpf, q = col - f * cpf;
+    if (f < nf && k < K) {
+      const double2 c = (q < 2 ? s0 : s1)[(size_t)f * nlm + base + k];
+      v = (float)((q & 1) ? c.y : c.x);
+    }
+    store_elem(out, canon_off(col, kk, E, eb, sbo), v, bf16);
+  }
+}
+
+// analysis B operand of (m, sign): K index = latitude j of the northern half,
+//   scalar (cpf = 2):  w_j (F_N +- F_S)           columns (re, im) per field
+//   vector (cpf = 4):  wq_j (A_N +- A_S), wq_j (B_N +- B_S)   columns (A re, A im, B re, B im)
+__global__ void k_tc_banal(const double2* __restrict__ F0, const double2* __restrict__ F1,
+                           const double* __restrict__ wts, unsigned char* __restrict__ B,
+                           const int* __restrict__ boff, int kpad, int T, int nlat, int nf, int cpf,
+                           int ncols, int bf16) {
+  const int m = blockIdx.x, sg = blockIdx.y;  // sg 0: plus, 1: minus
+  const int id = m * 2 + sg;
+  const int E = bf16 ? 8 : 4, eb = bf16 ? 2 : 4;
+  const int sbo = (kpad / E) * 128;
+  const int nh = nlat / 2;
+  unsigned char* out = B + boff[id];
+  for (int idx = threadIdx.x; idx < ncols * kpad; idx += blockDim.x) {
+    const int col = idx / kpad, j = idx - col * kpad;
+    float v = 0.f;
+    const int f = col / cpf, q = col - f * cpf;
+    if (f < nf && j < nh) {
+      const double2* Fq = (q < 2 ? F0 : F1) + ((size_t)f * (T + 1) + m) * nlat;
+      const double2 a = Fq[j], b = Fq[nlat - 1 - j];
+      const double s = sg ? -1.0 : 1.0;
+      const double re = a.x + s * b.x, im = a.y + s * b.y;
+      v = (float)(wts[j] * ((q & 1) ? im : re));
+    }
+    store_elem(out, canon_off(col, j, E, eb, sbo), v, bf16);
+  }
+}
+
+__device__ __forceinline__ double2 imul_d(int m, double2 v) { return make_double2(-m * v.y, m * v.x); }
+
+// synthesis epilogue: thread per (m, northern latitude); jobs indexed jid(m, par, tile, tab)
+__global__ void k_tc_esynth(const float* __restrict__ D, const int* __restrict__ dmap, double2* __restrict__ F0,
+                            double2* __restrict__ F1, int T, int nlat, int nf, int cpf, int ncols, int ntile,
+                            int vector, double inv_a) {
+  const int m = blockIdx.y;
+  const int nh = nlat / 2;
+  const int lat = blockIdx.x * blockDim.x + threadIdx.x;
+  if (lat >= nh) return;
+  const int tile = lat / 128, r = lat % 128;
+  auto val = [&](int par, int tab, int col) -> float {
+    const int o = dmap[((m * 2 + par) * ntile + tile) * 2 + tab];
+    return o < 0 ? 0.f : D[o + (size_t)r * ncols + col];
+  };
+  for (int f = 0; f < nf; ++f) {
+    const int c0 = f * cpf;
+    double2* o0 = F0 + ((size_t)f * (T + 1) + m) * nlat;
+    if (!vector) {
+      const double2 e = make_double2(val(0, 0, c0), val(0, 0, c0 + 1));
+      const double2 od = make_double2(val(1, 0, c0), val(1, 0, c0 + 1));
+      o0[lat] = make_double2(e.x + od.x, e.y + od.y);
+      o0[nlat - 1 - lat] = make_double2(e.x - od.x, e.y - od.y);
+    } else {
+      double2* o1 = F1 + ((size_t)f * (T + 1) + m) * nlat;
+      double2 Pps[2], Pch[2], Hps[2], Hch[2];
+      for (int par = 0; par < 2; ++par) {
+        Pps[par] = make_double2(val(par, 0, c0), val(par, 0, c0 + 1));
+        Pch[par] = make_double2(val(par, 0, c0 + 2), val(par, 0, c0 + 3));
+        Hps[par] = make_double2(val(par, 1, c0), val(par, 1, c0 + 1));
+        Hch[par] = make_double2(val(par, 1, c0 + 2), val(par, 1, c0 + 3));
+      }
+      for (int hemi = 0; hemi < 2; ++hemi) {
+        const double so = hemi ? -1.0 : 1.0, sh = hemi ? -1.0 : 1.0;
+        auto cb = [&](const double2* v, double sa) {
+          return make_double2(sa * (v[0].x + so * v[1].x), sa * (v[0].y + so * v[1].y));
+        };
+        const double2 pps = cb(Pps, 1.0), pch = cb(Pch, 1.0), hps = cb(Hps, sh), hch = cb(Hch, sh);
+        const double2 ich = imul_d(m, pch), ips = imul_d(m, pps);
+        const int jj = hemi ? nlat - 1 - lat : lat;
+        o0[jj] = make_double2(inv_a * (-hps.x + ich.x), inv_a * (-hps.y + ich.y));
+        o1[jj] = make_double2(inv_a * (ips.x + hch.x), inv_a * (ips.y + hch.y));
+      }
+    }
+  }
+}
+
+// analysis epilogue: thread per (m, k)
+__global__ void k_tc_eanal(const float* __restrict__ D, const int* __restrict__ dmap, double2* __restrict__ s0,
+                           double2* __restrict__ s1, int T, int nlm, int nf, int cpf, int ncols, int ntile,
+                           int vector, double inv_a) {
+  const int m = blockIdx.y;
+  const int K = T + 1 - m;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  const int par = k & 1, kk = k >> 1, tile = kk / 128, r = kk % 128;
+  auto val = [&](int tab, int col) -> float {
+    const int o = dmap[((m * 2 + par) * ntile + tile) * 2 + tab];
+    return o < 0 ? 0.f : D[o + (size_t)r * ncols + col];
+  };
+  const size_t i = moff(T, m) + k;
+  for (int f = 0; f < nf; ++f) {
+    const int c0 = f * cpf;
+    if (!vector) {
+      s0[(size_t)f * nlm + i] = make_double2(val(0, c0), val(0, c0 + 1));
+    } else {
+      const double2 PA = make_double2(val(0, c0), val(0, c0 + 1)), PB = make_double2(val(0, c0 + 2), val(0, c0 + 3));
+      const double2 HA = make_double2(val(1, c0), val(1, c0 + 1)), HB = make_double2(val(1, c0 + 2), val(1, c0 + 3));
+      const double2 iPA = imul_d(m, PA), iPB = imul_d(m, PB);
+      s0[(size_t)f * nlm + i] = make_double2(inv_a * (iPA.x - HB.x), inv_a * (iPA.y - HB.y));
+      s1[(size_t)f * nlm + i] = make_double2(inv_a * (iPB.x + HA.x), inv_a * (iPB.y + HA.y));
+    }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+struct TcLegendre {
+  int T = 0, nlat = 0, nh = 0, nlm = 0, max_fields = 0, bf16 = 0, E = 4, eb = 4, KC = 32;
+  int ntile_s = 0, ntile_a = 0, kpad_a = 0;
+  unsigned char *tabPs = nullptr, *tabHs = nullptr, *tabPa = nullptr, *tabHa = nullptr;
+  unsigned char* B = nullptr;
+  float* D = nullptr;
+  int* err = nullptr;
+  const double *w = nullptr, *wq = nullptr;
+  // synthesis jobs (scalar uses the P half), analysis jobs; job lists and D maps per variant
+  Job *jobs_s = nullptr, *jobs_a = nullptr;
+  int njobs_s = 0, njobs_a = 0, njobs_sP = 0, njobs_aP = 0;
+  int *dmap_s = nullptr, *dmap_a = nullptr;   // [(m*2+par)*ntile+tile][tab] -> D offset or -1
+  int *boff_s = nullptr, *kpad_s = nullptr, *boff_a = nullptr;
+  size_t smem_s = 0, smem_a = 0;
+};
+
+static int tc_fail(const char* what, cudaError_t e) { return cuda_fail(e, what); }
+
+int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const double* w, const double* wq,
+                       int T, int nlat, int max_fields, bool bf16, cudaStream_t stream) {
+  *out = nullptr;
+  if (max_fields > 8) return fail(REXI_EINVAL, "sh_plan_create: tensor-core precisions support max_fields <= 8");
+  TcLegendre* t = new TcLegendre();
+  t->T = T;
+  t->nlat = nlat;
+  t->nh = nlat / 2;
+  t->nlm = (T + 1) * (T + 2) / 2;
+  t->max_fields = max_fields;
+  t->bf16 = bf16 ? 1 : 0;
+  t->E = bf16 ? 8 : 4;
+  t->eb = bf16 ? 2 : 4;
+  t->KC = bf16 ? 64 : 32;
+  t->w = w;
+  t->wq = wq;
+  const int KC = t->KC, eb = t->eb;
+  const size_t chunk = 128ull * KC * eb;
+  t->ntile_s = (t->nh + 127) / 128;
+  // ---- synthesis jobs: (m, par, tile, tab), K = degrees of the parity ----------------------
+  std::vector<TabJob> tj;
+  std::vector<Job> js;
+  std::vector<int> dmap_s(2 * (T + 1) * 2 * t->ntile_s, -1), boff_s(2 * (T + 1)), kpad_s(2 * (T + 1));
+  long long aoff = 0;
+  int boff = 0, doff = 0;
+  const int ncols_max = TC_MAXCOL;
+  std::vector<Job> jsP, jsH;
+  for (int m = 0; m <= T; ++m)
+    for (int par = 0; par < 2; ++par) {
+      const int K = T + 1 - m;
+      const int kpar = (K - par + 1) / 2;
+      const int nchunk = (kpar + KC - 1) / KC;
+      boff_s[m * 2 + par] = boff;
+      kpad_s[m * 2 + par] = nchunk * KC;
+      boff += ncols_max * nchunk * KC * eb;
+      if (nchunk == 0) continue;
+      for (int tile = 0; tile < t->ntile_s; ++tile) {
+        tj.push_back(TabJob{aoff, m, par, tile, nchunk});
+        for (int tab = 0; tab < 2; ++tab) {
+          Job j{aoff, boff_s[m * 2 + par], doff, nchunk, nchunk * KC, tab, 0};
+          (tab ? jsH : jsP).push_back(j);
+          dmap_s[((m * 2 + par) * t->ntile_s + tile) * 2 + tab] = doff;
+          doff += 128 * ncols_max;
+        }
+        aoff += (long long)nchunk * chunk;
+      }
+    }
+  const long long tab_s_bytes = aoff;
+  const int bsz_s = boff;
+  const int dsz_s = doff;
+  auto bylen = [](const Job& a, const Job& b) { return a.nchunk > b.nchunk; };
+  std::stable_sort(jsP.begin(), jsP.end(), bylen);
+  std::stable_sort(jsH.begin(), jsH.end(), bylen);
+  t->njobs_sP = (int)jsP.size();
+  js = jsP;
+  js.insert(js.end(), jsH.begin(), jsH.end());
+  t->njobs_s = (int)js.size();
+  // ---- analysis jobs: (m, par, degree tile, tab), K = northern latitudes ------------------
+  t->kpad_a = (t->nh + KC - 1) / KC * KC;
+  const int nchunk_a = t->kpad_a / KC;
+  int ntile_a = 0;
+  for (int m = 0; m <= T; ++m) ntile_a = std::max(ntile_a, ((T + 1 - m + 1) / 2 + 127) / 128);
+  t->ntile_a = ntile_a;
+  std::vector<TabJob> ta;
+  std::vector<Job> jaP, jaH;
+  std::vector<int> dmap_a(2 * (T + 1) * 2 * ntile_a, -1), boff_a(2 * (T + 1));
+  aoff = 0;
+  boff = 0;
+  doff = 0;
+  for (int m = 0; m <= T; ++m)
+    for (int sg = 0; sg < 2; ++sg) {
+      boff_a[m * 2 + sg] = boff;
+      boff += ncols_max * t->kpad_a * eb;
+    }
+  for (int m = 0; m <= T; ++m)
+    for (int par = 0; par < 2; ++par) {
+      const int K = T + 1 - m;
+      const int kpar = (K - par + 1) / 2;
+      const int ntiles = (kpar + 127) / 128;
+      for (int tile = 0; tile < ntiles; ++tile) {
+        ta.push_back(TabJob{aoff, m, par, tile, nchunk_a});
+        for (int tab = 0; tab < 2; ++tab) {
+          // P pairs with (N + s S), H with (N - s S), s = (-1)^par: plus for (P, even), (H, odd)
+          const int sg = (tab == 0) ? par : 1 - par;
+          Job j{aoff, boff_a[m * 2 + sg], doff, nchunk_a, t->kpad_a, tab, 0};
+          (tab ? jaH : jaP).push_back(j);
+          dmap_a[((m * 2 + par) * ntile_a + tile) * 2 + tab] = doff;
+          doff += 128 * ncols_max;
+        }
+        aoff += (long long)nchunk_a * chunk;
+      }
+    }
+  const long long tab_a_bytes = aoff;
+  const int bsz_a = boff;
+  const int dsz = std::max(dsz_s, doff);
+  t->njobs_aP = (int)jaP.size();
+  std::vector<Job> ja = jaP;
+  ja.insert(ja.end(), jaH.begin(), jaH.end());
+  t->njobs_a = (int)ja.size();
+  // ---- device buffers ---------------------------------------------------------------------
+  TabJob *d_tj = nullptr, *d_ta = nullptr;
+  cudaError_t e;
+  if ((e = cudaMalloc(&t->tabPs, tab_s_bytes)) || (e = cudaMalloc(&t->tabHs, tab_s_bytes)) ||
+      (e = cudaMalloc(&t->tabPa, tab_a_bytes)) || (e = cudaMalloc(&t->tabHa, tab_a_bytes)) ||
+      (e = cudaMalloc(&t->B, std::max(bsz_s, bsz_a))) || (e = cudaMalloc(&t->D, sizeof(float) * (size_t)dsz)) ||
+      (e = cudaMalloc(&t->err, sizeof(int))) || (e = cudaMalloc(&t->jobs_s, sizeof(Job) * js.size())) ||
+      (e = cudaMalloc(&t->jobs_a, sizeof(Job) * ja.size())) ||
+      (e = cudaMalloc(&t->dmap_s, sizeof(int) * dmap_s.size())) ||
+      (e = cudaMalloc(&t->dmap_a, sizeof(int) * dmap_a.size())) ||
+      (e = cudaMalloc(&t->boff_s, sizeof(int) * boff_s.size())) ||
+      (e = cudaMalloc(&t->kpad_s, sizeof(int) * kpad_s.size())) ||
+      (e = cudaMalloc(&t->boff_a, sizeof(int) * boff_a.size())) ||
+      (e = cudaMalloc(&d_tj, sizeof(TabJob) * tj.size())) || (e = cudaMalloc(&d_ta, sizeof(TabJob) * ta.size()))) {
+    cudaGetLastError();
+    tc_legendre_destroy(t);
+    cudaFree(d_tj);
+    cudaFree(d_ta);
+    return fail(REXI_ENOMEM, "tensor-core Legendre tables: cudaMalloc failed: %s", cudaGetErrorString(e));
+  }
+  cudaMemset(t->err, 0, sizeof(int));
+  cudaMemcpy(t->jobs_s, js.data(), sizeof(Job) * js.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(t->jobs_a, ja.data(), sizeof(Job) * ja.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(t->dmap_s, dmap_s.data(), sizeof(int) * dmap_s.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(t->dmap_a, dmap_a.data(), sizeof(int) * dmap_a.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(t->boff_s, boff_s.data(), sizeof(int) * boff_s.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(t->kpad_s, kpad_s.data(), sizeof(int) * kpad_s.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(t->boff_a, boff_a.data(), sizeof(int) * boff_a.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(d_tj, tj.data(), sizeof(TabJob) * tj.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(d_ta, ta.data(), sizeof(TabJob) * ta.size(), cudaMemcpyHostToDevice);
+  k_tc_table<<<(int)tj.size(), 128, 0, stream>>>(P, t->tabPs, d_tj, (int)tj.size(), T, t->nh, 1, t->bf16);
+  k_tc_table<<<(int)tj.size(), 128, 0, stream>>>(H, t->tabHs, d_tj, (int)tj.size(), T, t->nh, 1, t->bf16);
+  k_tc_table<<<(int)ta.size(), 128, 0, stream>>>(P, t->tabPa, d_ta, (int)ta.size(), T, t->nh, 0, t->bf16);
+  k_tc_table<<<(int)ta.size(), 128, 0, stream>>>(H, t->tabHa, d_ta, (int)ta.size(), T, t->nh, 0, t->bf16);
+  e = cudaStreamSynchronize(stream);
+  cudaFree(d_tj);
+  cudaFree(d_ta);
+  if (e != cudaSuccess) {
+    tc_legendre_destroy(t);
+    return tc_fail("tensor-core Legendre table kernels", e);
+  }
+  int kpad_max = 0;
+  for (int v : kpad_s) kpad_max = std::max(kpad_max, v);
+  auto smem_for = [&](int kp) {
+    return (size_t)TC_STAGES * chunk + ((size_t)ncols_max * kp * eb + 127) / 128 * 128 + 8 * (2 * TC_STAGES + 2) + 16;
+  };
+  t->smem_s = smem_for(kpad_max);
+  t->smem_a = smem_for(t->kpad_a);
+  const size_t smax = std::max(t->smem_s, t->smem_a);
+  if (smax > 220 * 1024) {
+    tc_legendre_destroy(t);
+    return fail(REXI_EINVAL, "tensor-core Legendre: shared memory %zu bytes exceeds the limit", smax);
+  }
+  if ((e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax))) {
+    tc_legendre_destroy(t);
+    return tc_fail("cudaFuncSetAttribute(k_tc_gemm)", e);
+  }
+  *out = t;
+  return REXI_OK;
+}
+
+void tc_legendre_destroy(TcLegendre* t) {
+  if (!t) return;
+  for (void* p : {(void*)t->tabPs, (void*)t->tabHs, (void*)t->tabPa, (void*)t->tabHa, (void*)t->B, (void*)t->D,
+                  (void*)t->err, (void*)t->jobs_s, (void*)t->jobs_a, (void*)t->dmap_s, (void*)t->dmap_a,
+                  (void*)t->boff_s, (void*)t->kpad_s, (void*)t->boff_a})
+    cudaFree(p);
+  delete t;
+}
+
+static int gemm(TcLegendre* t, bool synth, bool both_tabs, int ncols, cudaStream_t s) {
+  GemmArgs g;
+  g.tabP = synth ? t->tabPs : t->tabPa;
+  g.tabH = synth ? t->tabHs : t->tabHa;
+  g.B = t->B;
+  g.D = t->D;
+  g.jobs = synth ? t->jobs_s : t->jobs_a;
+  g.njobs = both_tabs ? (synth ? t->njobs_s : t->njobs_a) : (synth ? t->njobs_sP : t->njobs_aP);
+  g.ncols = ncols;
+  g.bf16 = t->bf16;
+  g.err = t->err;
+  k_tc_gemm<<<g.njobs, 128, synth ? t->smem_s : t->smem_a, s>>>(g);
+  cudaError_t e = cudaGetLastError();
+  return e ? cuda_fail(e, "k_tc_gemm launch") : REXI_OK;
+}
+
+static int ncols_for(int nf, int cpf) {
+  const int c = nf * cpf;
+  return std::max(16, (c + 15) / 16 * 16);
+}
+
+int tc_leg_synth(TcLegendre* t, const double2* spec, double2* F, int nf, cudaStream_t s) {
+  const int nc = ncols_for(nf, 2);
+  k_tc_bsynth<<<dim3(t->T + 1, 2), 256, 0, s>>>(spec, spec, t->B, t->boff_s, t->kpad_s, t->T, t->nlm, nf, 2, nc,
+                                                t->bf16);
+  int rc = gemm(t, true, false, nc, s);
+  if (rc) return rc;
+  k_tc_esynth<<<dim3((t->nh + 127) / 128, t->T + 1), 128, 0, s>>>(t->D, t->dmap_s, F, F, t->T, t->nlat, nf, 2, nc,
+                                                                   t->ntile_s, 0, 0.0);
+  return REXI_OK;
+}
+
+int tc_leg_synth_uv(TcLegendre* t, const double2* psi, const double2* chi, double2* FU, double2* FV, int nf,
+                    double inv_a, cudaStream_t s) {
+  const int nc = ncols_for(nf, 4);
+  k_tc_bsynth<<<dim3(t->T + 1, 2), 256, 0, s>>>(psi, chi, t->B, t->boff_s, t->kpad_s, t->T, t->nlm, nf, 4, nc,
+                                                t->bf16);
+  int rc = gemm(t, true, true, nc, s);
+  if (rc) return rc;
+  k_tc_esynth<<<dim3((t->nh + 127) / 128, t->T + 1), 128, 0, s>>>(t->D, t->dmap_s, FU, FV, t->T, t->nlat, nf, 4, nc,
+                                                                   t->ntile_s, 1, inv_a);
+  return REXI_OK;
+}
+
+int tc_leg_anal(TcLegendre* t, const double2* F, double2* spec, int nf, cudaStream_t s) {
+  const int nc = ncols_for(nf, 2);
+  k_tc_banal<<<dim3(t->T + 1, 2), 256, 0, s>>>(F, F, t->w, t->B, t->boff_a, t->kpad_a, t->T, t->nlat, nf, 2, nc,
+                                               t->bf16);
+  int rc = gemm(t, false, false, nc, s);
+  if (rc) return rc;
+  k_tc_eanal<<<dim3((t->T + 1 + 127) / 128, t->T + 1), 128, 0, s>>>(t->D, t->dmap_a, spec, spec, t->T, t->nlm, nf,
+                                                                     2, nc, t->ntile_a, 0, 0.0);
+  return REXI_OK;
+}
+
+int tc_leg_anal_divcurl(TcLegendre* t, const double2* FA, const double2* FB, double2* dv, double2* cu, int nf,
+                        double inv_a, cudaStream_t s) {
+  const int nc = ncols_for(nf, 4);
+  k_tc_banal<<<dim3(t->T + 1, 2), 256, 0, s>>>(FA, FB, t->wq, t->B, t->boff_a, t->kpad_a, t->T, t->nlat, nf, 4, nc,
+                                               t->bf16);
+  int rc = gemm(t, false, true, nc, s);
+  if (rc) return rc;
+  k_tc_eanal<<<dim3((t->T + 1 + 127) / 128, t->T + 1), 128, 0, s>>>(t->D, t->dmap_a, dv, cu, t->T, t->nlm, nf, 4,
+                                                                     nc, t->ntile_a, 1, inv_a);
+  return REXI_OK;
+}
+
+int tc_legendre_error(TcLegendre* t, int* flag) {
+  if (!t) {
+    *flag = 0;
+    return REXI_OK;
+  }
+  cudaError_t e = cudaMemcpy(flag, t->err, sizeof(int), cudaMemcpyDeviceToHost);
+  return e ? cuda_fail(e, "tc error flag") : REXI_OK;
+}
+
+}  // namespace rexi

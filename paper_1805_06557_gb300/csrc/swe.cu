@@ -1,0 +1,220 @@
+// Nonlinear shallow-water step (paper Sec. 3 Eq. 1-3, Sec. 4.4): N(U) on the Gauss grid and
+// the Strang splittings around the REXI linear step.
+#include <vector>
+
+#include "../../include/sht.h"
+#include "../../include/swe.h"
+#include "common.cuh"
+
+namespace rexi {
+namespace {
+
+// psi = lap^-1 zeta, chi = lap^-1 delta with lap Y_n = -n(n+1)/a^2 Y_n; n = 0 -> 0
+__global__ void k_inv_lap(const double2* __restrict__ U, double2* __restrict__ psi,
+                          double2* __restrict__ chi, int T, int nlm, double a2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nlm) return;
+  int m = 0;
+  // zonal order of coefficient i (m-major): largest m with moff(m) <= i
+  int lo = 0, hi = T;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (moff(T, mid) <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  m = lo;
+  const int n = m + (i - moff(T, m));
+  const double s = n > 0 ? -a2 / (double(n) * (n + 1)) : 0.0;
+  const double2 z = U[nlm + i], d = U[2 * nlm + i];
+  psi[i] = make_double2(s * z.x, s * z.y);
+  chi[i] = make_double2(s * d.x, s * d.y);
+}
+
+// grid products: A = (Phi U, zeta U), B = (Phi V, zeta V), KE = (U^2 + V^2) / (2 cos^2)
+__global__ void k_swe_products(const double* __restrict__ PZ, const double* __restrict__ Ug,
+                               const double* __restrict__ Vg, const double* __restrict__ c2,
+                               double* __restrict__ A, double* __restrict__ B, double* __restrict__ KE,
+                               int nlat, int nlon) {
+  const int npt = nlat * nlon;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npt) return;
+  const double u = Ug[i], v = Vg[i], ph = PZ[i], ze = PZ[npt + i];
+  A[i] = ph * u;
+  A[npt + i] = ze * u;
+  B[i] = ph * v;
+  B[npt + i] = ze * v;
+  KE[i] = (u * u + v * v) / (2.0 * c2[i / nlon]);
+}
+
+// out = base + tau * N,  N = (-div(Phi V), -div(zeta V), curl(zeta V) + n(n+1)/a^2 KE_s);
+// the n = 0 vorticity and divergence tendencies are 0 (global means).
+__global__ void k_swe_combine(const double2* __restrict__ base, const double2* __restrict__ dv,
+                              const double2* __restrict__ cu, const double2* __restrict__ kes,
+                              double2* __restrict__ out, double tau, int T, int nlm, double inv_a2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nlm) return;
+  int lo = 0, hi = T;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (moff(T, mid) <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  const int n = lo + (i - moff(T, lo));
+  double2 nP = make_double2(-dv[i].x, -dv[i].y);
+  double2 nZ = make_double2(-dv[nlm + i].x, -dv[nlm + i].y);
+  const double l = double(n) * (n + 1) * inv_a2;
+  double2 nD = make_double2(cu[nlm + i].x + l * kes[i].x, cu[nlm + i].y + l * kes[i].y);
+  if (i == 0) nZ = nD = make_double2(0.0, 0.0);
+  if (tau == 0.0) {  // plain tendency
+    out[i] = nP;
+    out[nlm + i] = nZ;
+    out[2 * nlm + i] = nD;
+    return;
+  }
+  out[i] = make_double2(fma(tau, nP.x, base[i].x), fma(tau, nP.y, base[i].y));
+  out[nlm + i] = make_double2(fma(tau, nZ.x, base[nlm + i].x), fma(tau, nZ.y, base[nlm + i].y));
+  out[2 * nlm + i] = make_double2(fma(tau, nD.x, base[2 * nlm + i].x), fma(tau, nD.y, base[2 * nlm + i].y));
+}
+
+}  // namespace
+}  // namespace rexi
+
+using namespace rexi;
+
+struct swe_plan {
+  swe_plan_desc d{};
+  int nlm = 0, npt = 0;
+  cudaStream_t stream = nullptr;
+  rexi_plan* rp = nullptr;
+  sh_plan* sp = nullptr;
+  double2 *psi = nullptr, *chi = nullptr, *Um = nullptr, *Ut = nullptr, *dv = nullptr, *cu = nullptr,
+          *kes = nullptr;
+  double *PZ = nullptr, *Ug = nullptr, *Vg = nullptr, *A = nullptr, *B = nullptr, *KE = nullptr,
+         *c2 = nullptr;
+};
+
+extern "C" int swe_plan_destroy(swe_plan* p) {
+  if (!p) return REXI_OK;
+  cudaStreamSynchronize(p->stream);
+  rexi_plan_destroy(p->rp);
+  sh_plan_destroy(p->sp);
+  for (void* q : {(void*)p->psi, (void*)p->chi, (void*)p->Um, (void*)p->Ut, (void*)p->dv, (void*)p->cu,
+                  (void*)p->kes, (void*)p->PZ, (void*)p->Ug, (void*)p->Vg, (void*)p->A, (void*)p->B,
+                  (void*)p->KE, (void*)p->c2})
+    cudaFree(q);
+  delete p;
+  return REXI_OK;
+}
+
+extern "C" int swe_plan_create(const swe_plan_desc* desc, swe_plan** out) {
+  if (!desc || !out) return fail(REXI_EINVAL, "swe_plan_create: null argument");
+  *out = nullptr;
+  const swe_plan_desc& d = *desc;
+  if (d.scheme != SWE_L_REXI_N_ERK_VER1 && d.scheme != SWE_L_REXI_N_ERK_VER0)
+    return fail(REXI_EINVAL, "swe_plan_create: unknown scheme %d", d.scheme);
+  swe_plan* p = new swe_plan();
+  p->d = d;
+  p->stream = (cudaStream_t)d.stream;
+  p->nlm = (d.T + 1) * (d.T + 2) / 2;
+  p->npt = d.nlat * d.nlon;
+  auto bail = [&](int code) {
+    swe_plan_destroy(p);
+    return code;
+  };
+  sh_plan_desc sd{};
+  sd.T = d.T;
+  sd.nlat = d.nlat;
+  sd.nlon = d.nlon;
+  sd.radius = d.radius;
+  sd.precision = d.sh_precision;
+  sd.max_fields = 2;
+  sd.stream = d.stream;
+  int rc = sh_plan_create(&sd, &p->sp);
+  if (rc) return bail(rc);
+  rexi_plan_desc rd{};
+  rd.T = d.T;
+  rd.N = d.N;
+  rd.dt = d.scheme == SWE_L_REXI_N_ERK_VER1 ? d.dt : 0.5 * d.dt;
+  rd.omega = d.omega;
+  rd.radius = d.radius;
+  rd.phibar = d.phibar;
+  rd.p0 = d.p0;
+  rd.Xc = d.Xc;
+  rd.precision = d.rexi_precision;
+  rd.heavy_tau = -1.0;
+  rd.max_batch = 1;
+  rd.stream = d.stream;
+  rc = rexi_plan_create(&rd, &p->rp);
+  if (rc) return bail(rc);
+  const size_t s3 = sizeof(double2) * 3 * (size_t)p->nlm, s1 = sizeof(double2) * (size_t)p->nlm;
+  const size_t g1 = sizeof(double) * (size_t)p->npt;
+  cudaError_t e;
+  if ((e = cudaMalloc(&p->psi, s1)) || (e = cudaMalloc(&p->chi, s1)) || (e = cudaMalloc(&p->Um, s3)) ||
+      (e = cudaMalloc(&p->Ut, s3)) || (e = cudaMalloc(&p->dv, 2 * s1)) || (e = cudaMalloc(&p->cu, 2 * s1)) ||
+      (e = cudaMalloc(&p->kes, s1)) || (e = cudaMalloc(&p->PZ, 2 * g1)) || (e = cudaMalloc(&p->Ug, g1)) ||
+      (e = cudaMalloc(&p->Vg, g1)) || (e = cudaMalloc(&p->A, 2 * g1)) || (e = cudaMalloc(&p->B, 2 * g1)) ||
+      (e = cudaMalloc(&p->KE, g1)) || (e = cudaMalloc(&p->c2, sizeof(double) * d.nlat))) {
+    cudaGetLastError();
+    return bail(fail(REXI_ENOMEM, "swe_plan_create: cudaMalloc failed: %s", cudaGetErrorString(e)));
+  }
+  std::vector<double> mu(d.nlat), c2(d.nlat);
+  sh_plan_get_grid(p->sp, mu.data(), nullptr);
+  for (int j = 0; j < d.nlat; ++j) c2[j] = (1.0 - mu[j]) * (1.0 + mu[j]);
+  if ((e = cudaMemcpy(p->c2, c2.data(), sizeof(double) * d.nlat, cudaMemcpyHostToDevice)))
+    return bail(cuda_fail(e, "swe_plan_create: cudaMemcpy"));
+  *out = p;
+  return REXI_OK;
+}
+
+// out = base + tau * N(U)   (tau = 0: out = N(U))
+static int nonlinear_update(swe_plan* p, const double2* U, const double2* base, double tau, double2* out) {
+  const int T = p->d.T, nlm = p->nlm;
+  const int tb = 256;
+  k_inv_lap<<<(nlm + tb - 1) / tb, tb, 0, p->stream>>>(U, p->psi, p->chi, T, nlm, p->d.radius * p->d.radius);
+  int rc;
+  if ((rc = sh_synthesis(p->sp, U, p->PZ, 2))) return rc;  // Phi', zeta
+  if ((rc = sh_synthesis_uv(p->sp, p->psi, p->chi, p->Ug, p->Vg, 1))) return rc;
+  k_swe_products<<<(p->npt + tb - 1) / tb, tb, 0, p->stream>>>(p->PZ, p->Ug, p->Vg, p->c2, p->A, p->B, p->KE,
+                                                              p->d.nlat, p->d.nlon);
+  if ((rc = sh_analysis_divcurl(p->sp, p->A, p->B, p->dv, p->cu, 2))) return rc;
+  if ((rc = sh_analysis(p->sp, p->KE, p->kes, 1))) return rc;
+  k_swe_combine<<<(nlm + tb - 1) / tb, tb, 0, p->stream>>>(base, p->dv, p->cu, p->kes, out, tau, T, nlm,
+                                                           1.0 / (p->d.radius * p->d.radius));
+  cudaError_t e = cudaGetLastError();
+  return e ? cuda_fail(e, "swe nonlinear kernels") : REXI_OK;
+}
+
+// U <- U + tau N(U + tau/2 N(U))   (explicit midpoint rule)
+static int rk2_nonlinear(swe_plan* p, double2* U, double tau) {
+  int rc = nonlinear_update(p, U, U, 0.5 * tau, p->Um);
+  if (rc) return rc;
+  return nonlinear_update(p, p->Um, U, tau, U);
+}
+
+extern "C" int swe_nonlinear(swe_plan* p, const void* state, void* tend) {
+  if (!p || !state || !tend) return fail(REXI_EINVAL, "swe_nonlinear: null argument");
+  if (state == tend) return fail(REXI_EINVAL, "swe_nonlinear: state and tendency alias");
+  return nonlinear_update(p, (const double2*)state, nullptr, 0.0, (double2*)tend);
+}
+
+extern "C" int swe_step(swe_plan* p, void* state, int nsteps) {
+  if (!p || !state) return fail(REXI_EINVAL, "swe_step: null argument");
+  if (nsteps < 0) return fail(REXI_EINVAL, "swe_step: nsteps < 0");
+  double2* U = (double2*)state;
+  const size_t s3 = sizeof(double2) * 3 * (size_t)p->nlm;
+  const double dt = p->d.dt;
+  for (int s = 0; s < nsteps; ++s) {
+    int rc;
+    if (p->d.scheme == SWE_L_REXI_N_ERK_VER1) {
+      if ((rc = rk2_nonlinear(p, U, 0.5 * dt))) return rc;
+      if ((rc = rexi_step(p->rp, U, p->Ut, 1))) return rc;
+      REXI_CUDA_TRY(cudaMemcpyAsync(U, p->Ut, s3, cudaMemcpyDeviceToDevice, p->stream));
+      if ((rc = rk2_nonlinear(p, U, 0.5 * dt))) return rc;
+    } else {
+      if ((rc = rexi_step(p->rp, U, p->Ut, 1))) return rc;
+      if ((rc = rk2_nonlinear(p, p->Ut, dt))) return rc;
+      if ((rc = rexi_step(p->rp, p->Ut, U, 1))) return rc;
+    }
+  }
+  return REXI_OK;
+}

@@ -243,3 +243,138 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+# ---- spherical-harmonic transforms (include/sht.h) ------------------------------------
+SH_FP64, SH_TF32, SH_BF16 = 0, 1, 2
+_SH_PREC = {"fp64": SH_FP64, "tf32": SH_TF32, "bf16": SH_BF16}
+
+
+class ShDesc(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int), ("nlat", ctypes.c_int), ("nlon", ctypes.c_int),
+                ("radius", ctypes.c_double), ("precision", ctypes.c_int),
+                ("max_fields", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+_lib.sh_plan_create.argtypes = [ctypes.POINTER(ShDesc), ctypes.POINTER(ctypes.c_void_p)]
+_lib.sh_plan_destroy.argtypes = [ctypes.c_void_p]
+_lib.sh_plan_get_grid.argtypes = [ctypes.c_void_p, _dp, _dp]
+for _n in ("sh_synthesis", "sh_analysis"):
+    getattr(_lib, _n).argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+_lib.sh_plan_check.argtypes = [ctypes.c_void_p]
+for _n in ("sh_synthesis_uv", "sh_analysis_divcurl"):
+    getattr(_lib, _n).argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 4 + [ctypes.c_int]
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class ShPlan:
+    """Spherical-harmonic transforms on a Gauss grid (nlat x nlon), truncation T."""
+
+    def __init__(self, T, nlat, nlon, radius, precision="fp64", max_fields=1, stream=None):
+        d = ShDesc()
+        d.T, d.nlat, d.nlon, d.radius = int(T), int(nlat), int(nlon), float(radius)
+        d.precision = _SH_PREC[precision] if isinstance(precision, str) else int(precision)
+        d.max_fields = int(max_fields)
+        d.stream = ctypes.c_void_p(_stream_handle(stream))
+        h = ctypes.c_void_p()
+        _check(_lib.sh_plan_create(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+        self.T, self.nlat, self.nlon, self.nlm = int(T), int(nlat), int(nlon), nlm(T)
+
+    def grid(self):
+        mu = np.empty(self.nlat)
+        w = np.empty(self.nlat)
+        _check(_lib.sh_plan_get_grid(self._h, mu.ctypes.data_as(_dp), w.ctypes.data_as(_dp)))
+        return mu, w
+
+    def synthesis(self, spec, grid, nfields=1):
+        _check(_lib.sh_synthesis(self._h, _ptr(spec), _ptr(grid), int(nfields)))
+        return grid
+
+    def analysis(self, grid, spec, nfields=1):
+        _check(_lib.sh_analysis(self._h, _ptr(grid), _ptr(spec), int(nfields)))
+        return spec
+
+    def synthesis_uv(self, psi, chi, U, V, nfields=1):
+        _check(_lib.sh_synthesis_uv(self._h, _ptr(psi), _ptr(chi), _ptr(U), _ptr(V), int(nfields)))
+        return U, V
+
+    def check(self):
+        """Synchronise; raise if a device-side bounded wait gave up."""
+        _check(_lib.sh_plan_check(self._h))
+
+    def analysis_divcurl(self, A, B, div, curl, nfields=1):
+        _check(_lib.sh_analysis_divcurl(self._h, _ptr(A), _ptr(B), _ptr(div), _ptr(curl),
+                                        int(nfields)))
+        return div, curl
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.sh_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- nonlinear shallow-water step (include/swe.h) ---------------------------------------
+SWE_VER1, SWE_VER0 = 0, 1
+
+
+class SweDesc(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int), ("nlat", ctypes.c_int), ("nlon", ctypes.c_int),
+                ("dt", ctypes.c_double), ("omega", ctypes.c_double), ("radius", ctypes.c_double),
+                ("phibar", ctypes.c_double), ("N", ctypes.c_int), ("p0", ctypes.c_double),
+                ("Xc", ctypes.c_double), ("rexi_precision", ctypes.c_int),
+                ("sh_precision", ctypes.c_int), ("scheme", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+_lib.swe_plan_create.argtypes = [ctypes.POINTER(SweDesc), ctypes.POINTER(ctypes.c_void_p)]
+_lib.swe_plan_destroy.argtypes = [ctypes.c_void_p]
+_lib.swe_step.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+_lib.swe_nonlinear.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+
+
+class SwePlan:
+    """Strang-split nonlinear SWE step (l_rexi_n_erk_ver1 / ver0) on a Gauss grid."""
+
+    def __init__(self, T, nlat, nlon, dt, omega, radius, phibar, N, p0, Xc, rexi_precision="fp64",
+                 sh_precision="fp64", scheme="ver1", stream=None):
+        d = SweDesc()
+        d.T, d.nlat, d.nlon, d.dt = int(T), int(nlat), int(nlon), float(dt)
+        d.omega, d.radius, d.phibar = float(omega), float(radius), float(phibar)
+        d.N, d.p0, d.Xc = int(N), float(p0), float(Xc)
+        d.rexi_precision = _PREC[rexi_precision] if isinstance(rexi_precision, str) else int(rexi_precision)
+        d.sh_precision = _SH_PREC[sh_precision] if isinstance(sh_precision, str) else int(sh_precision)
+        d.scheme = {"ver1": SWE_VER1, "ver0": SWE_VER0}[scheme] if isinstance(scheme, str) else int(scheme)
+        d.stream = ctypes.c_void_p(_stream_handle(stream))
+        h = ctypes.c_void_p()
+        _check(_lib.swe_plan_create(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+        self.T, self.nlm = int(T), nlm(T)
+
+    def step(self, state, nsteps=1):
+        _check(_lib.swe_step(self._h, _ptr(state), int(nsteps)))
+        return state
+
+    def nonlinear(self, state, tendency):
+        _check(_lib.swe_nonlinear(self._h, _ptr(state), _ptr(tendency)))
+        return tendency
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.swe_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

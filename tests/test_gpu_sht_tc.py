@@ -1,0 +1,97 @@
+"""Tensor-core (tcgen05) Legendre precisions of the SH transforms against the FP64 oracle.
+
+Stated per-field bounds (relative L2), from the input rounding of the operands with FP32
+accumulation: TF32 (10-bit mantissa) 2e-3, BF16 (7-bit mantissa) 1.5e-2 for synthesis and
+analysis of band-limited / smooth fields; the measured values are printed by the tests."""
+import numpy as np
+import pytest
+
+from oracle import sht as osht
+
+pytestmark = pytest.mark.gpu
+
+A = 6.37122e6
+BOUND = {"tf32": 2e-3, "bf16": 1.5e-2}
+SIZES = [(31, 48, 96), (127, 192, 384), (511, 768, 1536)]
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1805_06557_gb300 import rexi
+    return torch, rexi
+
+
+def _spec(T, seed, nf=1, slope=-1.0):
+    rng = np.random.default_rng(seed)
+    n = np.concatenate([np.arange(m, T + 1) for m in range(T + 1)]).astype(float)
+    amp = np.maximum(n, 1.0) ** slope
+    c = (rng.standard_normal((nf, osht.nlm(T))) + 1j * rng.standard_normal((nf, osht.nlm(T)))) * amp
+    c[:, : T + 1] = c[:, : T + 1].real
+    return c
+
+
+def _rel(x, ref):
+    return float(np.linalg.norm(x - ref) / np.linalg.norm(ref))
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("T,nlat,nlon", SIZES)
+def test_tc_scalar(env, prec, T, nlat, nlon):
+    torch, rexi = env
+    nf = 2
+    c = _spec(T, 3, nf)
+    ref64 = rexi.ShPlan(T, nlat, nlon, A, "fp64", max_fields=nf)
+    p = rexi.ShPlan(T, nlat, nlon, A, prec, max_fields=nf)
+    cs = torch.from_numpy(c).cuda()
+    g64 = torch.empty(nf, nlat, nlon, dtype=torch.float64, device="cuda")
+    g = torch.empty_like(g64)
+    ref64.synthesis(cs, g64, nf)
+    p.synthesis(cs, g, nf)
+    s64 = torch.empty_like(cs)
+    s = torch.empty_like(cs)
+    ref64.analysis(g64, s64, nf)
+    p.analysis(g64, s, nf)
+    p.check()
+    G, G64 = g.cpu().numpy(), g64.cpu().numpy()
+    S, S64 = s.cpu().numpy(), s64.cpu().numpy()
+    if T <= 127:  # the oracle itself for the smaller sizes
+        og = osht.Grid(T, nlat, nlon, A)
+        assert _rel(G64[0], og.synth(c[0])) < 1e-12
+    es = max(_rel(G[f], G64[f]) for f in range(nf))
+    ea = max(_rel(S[f], S64[f]) for f in range(nf))
+    print("%s T%d synthesis %.2e analysis %.2e" % (prec, T, es, ea))
+    assert es < BOUND[prec] and ea < BOUND[prec]
+    p.close()
+    ref64.close()
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("T,nlat,nlon", SIZES[:2])
+def test_tc_vector(env, prec, T, nlat, nlon):
+    torch, rexi = env
+    nf = 2
+    og = osht.Grid(T, nlat, nlon, A)
+    psi, chi = _spec(T, 5, nf), _spec(T, 6, nf)
+    psi[:, 0] = chi[:, 0] = 0
+    p = rexi.ShPlan(T, nlat, nlon, A, prec, max_fields=nf)
+    U = torch.empty(nf, nlat, nlon, dtype=torch.float64, device="cuda")
+    V = torch.empty_like(U)
+    p.synthesis_uv(torch.from_numpy(psi).cuda(), torch.from_numpy(chi).cuda(), U, V, nf)
+    rng = np.random.default_rng(2)
+    Ag = np.stack([og.synth(_spec(T, 11 + f)[0]) for f in range(nf)])
+    Bg = np.stack([og.synth(_spec(T, 21 + f)[0]) for f in range(nf)])
+    dv = torch.empty(nf, osht.nlm(T), dtype=torch.complex128, device="cuda")
+    cu = torch.empty_like(dv)
+    p.analysis_divcurl(torch.from_numpy(Ag).cuda(), torch.from_numpy(Bg).cuda(), dv, cu, nf)
+    p.check()
+    for f in range(nf):
+        Uo, Vo = og.synth_uv(psi[f], chi[f])
+        do, co = og.analys_divcurl(Ag[f], Bg[f])
+        errs = [_rel(U.cpu().numpy()[f], Uo), _rel(V.cpu().numpy()[f], Vo),
+                _rel(dv.cpu().numpy()[f], do), _rel(cu.cpu().numpy()[f], co)]
+        print("%s T%d uv/divcurl" % (prec, T), ["%.2e" % e for e in errs])
+        assert max(errs) < BOUND[prec], errs
+    p.close()
