@@ -150,6 +150,56 @@ int rexi_plan_get_info(const rexi_plan* plan, rexi_plan_info* info);
 int rexi_plan_get_poles(const rexi_plan* plan, double* z, double* w, int* heavy);
 
 /*
+ * Ragged plans -- one launch over instances of different truncation T, time step dt and pole
+ * count N (uneven per-m chain lengths from many states; the ensemble and serving forms).
+ * Each instance gets its own Cauchy pole set; the tiles of all instances are sorted by cost
+ * and dealt to the same persistent kernels as rexi_step.  States are concatenated:
+ * instance i occupies [3][nlm_i] complex128 at complex offset soff[i] (rexi_ragged_offsets).
+ */
+typedef struct rexi_ragged rexi_ragged;
+
+typedef struct rexi_ragged_desc {
+  int Tmax;            /* largest truncation of any instance, <= 1023                        */
+  int max_inst;        /* largest number of instances per set                                */
+  int max_poles;       /* capacity of the pole arena (sum of padded pole counts)             */
+  long long max_elems; /* largest sum over instances of nlm_i                                */
+  double omega, radius, phibar;
+  int precision;       /* REXI_FP64 or REXI_MIXED                                            */
+  double heavy_tau;    /* as in rexi_plan_desc                                               */
+  void* stream;        /* cudaStream_t (graph capture needs a non-default stream)            */
+} rexi_ragged_desc;
+
+typedef struct rexi_instance {
+  int T, N;            /* truncation, poles                                                  */
+  double dt;           /* time step [s]                                                      */
+  double p0, Xc;       /* contour (rexi_coeffs)                                              */
+  long long soff;      /* complex offset of the state in U0 / U1; -1: concatenate in order   */
+                       /* (either every instance gives an offset or none; states must not    */
+                       /* overlap)                                                           */
+} rexi_instance;
+
+/* Allocates tables (Tmax), pole arena, workspace.  Errors: REXI_EINVAL, REXI_ENOMEM, REXI_ECUDA. */
+int rexi_ragged_create(const rexi_ragged_desc* desc, rexi_ragged** out);
+int rexi_ragged_destroy(rexi_ragged* r);
+/* Sets the instance list (host array).  Pole sets are generated on the host and cached by
+ * (T, N, dt, p0, Xc); tiles and descriptors are rebuilt and uploaded (synchronously).
+ * Errors: REXI_EINVAL (bad instance), REXI_EBUSY (capacity exceeded), REXI_ECUDA. */
+int rexi_ragged_set(rexi_ragged* r, int ninst, const rexi_instance* inst);
+/* soff[0..ninst]: complex offsets of the states in the concatenated layout (soff[ninst] = total). */
+int rexi_ragged_offsets(const rexi_ragged* r, long long* soff);
+/* One REXI step of every instance: U1 = sum_n w_n (z_n - dt L)^-1 U0 per instance.
+ * Asynchronous, no allocation; replays the captured graph if (U0, U1) match the capture. */
+int rexi_ragged_step(rexi_ragged* r, const void* U0, void* U1);
+/* Captures one step for fixed (U0, U1) into a CUDA graph (one graph launch per step). */
+int rexi_ragged_capture(rexi_ragged* r, const void* U0, void* U1);
+/* Autotuner: times tile densities {1, 2, 4, 8} tiles per resident warp on the current set,
+ * keeps the fastest.  Synchronous; overwrites U1. */
+int rexi_ragged_tune(rexi_ragged* r, const void* U0, void* U1, int reps, int* best_qmul, double* best_ms);
+int rexi_ragged_sync(rexi_ragged* r);
+int rexi_ragged_set_profiling(rexi_ragged* r, int enable);
+int rexi_ragged_get_profile(rexi_ragged* r, double* ms, int* launches, int reset);
+
+/*
  * Per-kernel timing.  When enabled, rexi_step records a CUDA event pair on the plan stream
  * around every kernel it launches and accumulates the elapsed times at the next
  * rexi_plan_get_profile call (which synchronises the stream).  Kernel ids: 0 pre-pass,

@@ -80,11 +80,41 @@ struct PoleF {
   float2 z, w, wz, iz, gz;
 };
 
-// One unit of work: zonal order m, parity chain, a range of 32-pole groups, and the slot
-// of the partial sums it owns.  Sorted by decreasing cost.
+// One unit of work: instance, zonal order m, parity chain, a range of 32-pole groups of the
+// instance's pole set, and the slot of the partial sums it owns.  Sorted by decreasing cost.
 struct Tile {
-  int m, chain, g0, ng, q, heavy, cost, pad;
+  int m, chain, g0, ng, q, heavy, cost, inst;
 };
+
+// One state of a launch.  Offsets are relative to the launch's base pointers.
+struct Inst {
+  long long soff;  // complex offset of the state [3][nlm] in U0 / U1
+  long long poff;  // complex offset of its partial sums [Q][3][nlm]
+  long long roff;  // element offset of its right-hand-side pieces [nlm]
+  int T, nlm, Q, pole0;  // truncation, coefficients per field, pole ranges, first pole
+  double2 S0;      // sum_n w_n / z_n of its pole set
+};
+
+// index of the instance owning global element e: largest i with ecum[i] <= e
+__host__ __device__ __forceinline__ int inst_of(const long long* ecum, int ninst, long long e) {
+  int lo = 0, hi = ninst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (ecum[mid] <= e) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+// zonal order of coefficient idx for truncation T (m-major layout)
+__host__ __device__ __forceinline__ int m_of(int T, int idx) {
+  int lo = 0, hi = T;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (mid * (2 * T + 3 - mid) / 2 <= idx) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
 
 __host__ __device__ __forceinline__ int moff(int T, int m) { return m * (2 * T + 3 - m) / 2; }
 

@@ -1,17 +1,22 @@
 // FP64 REXI solve kernel (the plain FP64 path).
 //
-// Work decomposition: a tile is (state b, zonal order m, parity chain c, range of 32-pole
-// groups).  One warp owns a tile; lane l solves the chain for pole g*32 + l, so the 32
-// systems of a warp share m, the chain and every table / right-hand-side element (warp
-// broadcast loads), and differ only in the pole z.
+// Work decomposition: a tile is (instance, zonal order m, parity chain c, range of 32-pole
+// groups of the instance's pole set).  One warp owns a tile; lane l solves the chain for
+// pole g*32 + l, so the 32 systems of a warp share m, the chain and every table /
+// right-hand-side element (warp broadcast loads), and differ only in the pole.  Instances
+// may differ in truncation, time step and pole set (ragged launches).
 //
-// Per (pole, m) the banded system (z - dt L_m) u = U0_m is reduced exactly as follows:
-//   Phi_n = (bPhi_n - dt Phibar delta_n) / z                       (Phi row)
-// which leaves two tridiagonal chains in (zeta, delta) by parity of n - m.  Row n reads
-//   zeta row : (z - i dt w_n) zeta_n + cm_n x_{n-1} + cp_n x_{n+1} = bzeta_n
-//   delta row: (z - i dt w_n + q_n dt Phibar / z) delta_n - cm_n x_{n-1} - cp_n x_{n+1}
-//              = bdelta_n + q_n bPhi_n / z
-// with cm_n = dt 2 Omega (n+1)/n eps_n, cp_n = dt 2 Omega n/(n+1) eps_{n+1}, q_n = dt n(n+1)/a^2.
+// The system (z - dt L_m) u = U0_m is solved in the equivalent scaled form
+// (z' - L_m) v = U0_m with z' = z / dt and v = dt u, so the tables are independent of dt and
+// every instance brings its own scaled poles (z', w' = w / dt, w/z, 1/z', Phibar / z').
+// Eliminating Phi_n = (bPhi_n - Phibar delta_n) / z' leaves two tridiagonal chains in
+// (zeta, delta) by parity of n - m.  Row n reads
+//   zeta row : (z' - i w_n) zeta_n + cm_n x_{n-1} + cp_n x_{n+1} = bzeta_n
+//   delta row: (z' - i w_n + q_n Phibar / z') delta_n - cm_n x_{n-1} - cp_n x_{n+1}
+//              = bdelta_n + q_n bPhi_n / z'
+// with w_n = 2 Omega m / (n(n+1)), cm_n = 2 Omega (n+1)/n eps_n, cp_n = 2 Omega n/(n+1) eps_{n+1},
+// q_n = n(n+1)/a^2 (one table for the largest truncation of the launch serves all: the
+// coupling beyond an instance's last degree never enters its elimination).
 // The chain is solved by the Thomas algorithm without pivoting: for the REXI poles the
 // shifted operator is a scaled identity plus a skew-adjoint part in the energy norm, so the
 // elimination is stable.  The forward coefficients are kept in a per-warp global scratch
@@ -21,20 +26,22 @@
 // The weighted sums over poles are formed by transposing 32 solution rows through shared
 // memory, so that lane r sums row r over the 32 poles of the group:
 //   S_zeta / S_delta = sum_p w_p x_p,   S_wz = sum_p (w_p / z_p) delta_p,
-// and Phi = bPhi * sum_p w_p/z_p - dt Phibar * S_wz is formed in the finalize kernel.
+// (S over the scaled solutions with the scaled weights), and
+// Phi = bPhi * sum_p w_p/z_p - Phibar * S_wz is formed in the finalize kernel.
 #pragma once
 #include "common.cuh"
 
 namespace rexi {
 
 struct Fp64Args {
-  const double2* U0;   // [B][3][nlm]
-  double2* partial;    // [B][Q][3][nlm]
-  const D4* tab;  // [nlm] (dt w_n, cm_n, cp_n, q_n)
-  const PoleD* poles;  // [Npad]
-  const Tile* tiles;   // [ntiles] for one state
-  D4* scratch;    // [warps][kmax][32]
-  int ntiles, B, T, nlm, Q, kmax;
+  const double2* U0;   // state base
+  double2* partial;    // partial-sum base
+  const D4* tab;       // [moff(Ttab, m) + n - m] (w_n, cm_n, cp_n, q_n)
+  const PoleD* poles;  // scaled poles of every pole set of the launch
+  const Tile* tiles;   // [ntiles]
+  const Inst* insts;
+  D4* scratch;         // [warps][kmax][32]
+  int ntiles, Ttab, kmax;
 };
 
 constexpr int FP64_WARPS = 4;
@@ -51,22 +58,22 @@ k_rexi_fp64(Fp64Args a) {
   const int gw = blockIdx.x * FP64_WARPS + wib;
   const int W = gridDim.x * FP64_WARPS;
   D4* scr = a.scratch + (size_t)gw * a.kmax * 32;
-  const int total = a.ntiles * a.B;
-  const int T = a.T, nlm = a.nlm;
+  const int total = a.ntiles;
 
   for (int round = 0; round * W < total; ++round) {
     const int t = round * W + ((round & 1) ? (W - 1 - gw) : gw);  // snake over LPT order
     if (t >= total) continue;
-    const int it = t / a.B, b = t - it * a.B;
-    const Tile tl = a.tiles[it];
-    const int m = tl.m, c = tl.chain, K = T + 1 - m, off = moff(T, m);
-    const double2* bP = a.U0 + (size_t)b * 3 * nlm;
+    const Tile tl = a.tiles[t];
+    const Inst I = a.insts[tl.inst];
+    const int T = I.T, nlm = I.nlm;
+    const int m = tl.m, c = tl.chain, K = T + 1 - m, off = moff(T, m), toff = moff(a.Ttab, m);
+    const double2* bP = a.U0 + I.soff;
     const double2* bZ = bP + nlm;
     const double2* bD = bP + 2 * nlm;
-    double2* part = a.partial + ((size_t)b * a.Q + tl.q) * 3 * nlm;
+    double2* part = a.partial + I.poff + (size_t)tl.q * 3 * nlm;
 
     for (int gi = 0; gi < tl.ng; ++gi) {
-      const PoleD pd = a.poles[(tl.g0 + gi) * 32 + lane];
+      const PoleD pd = a.poles[I.pole0 + (tl.g0 + gi) * 32 + lane];
       __syncwarp();
       s_w[lane] = pd.w;
       s_wz[lane] = pd.wz;
@@ -75,7 +82,7 @@ k_rexi_fp64(Fp64Args a) {
       double2 ct = make_double2(0.0, 0.0), y = make_double2(0.0, 0.0);
       for (int k = 0; k < K; ++k) {
         const int idx = off + k;
-        const D4 tb = a.tab[idx];  // x: dt w, y: cm, z: cp, w: q
+        const D4 tb = a.tab[toff + k];  // x: w_n, y: cm, z: cp, w: q
         const bool isZ = ((k & 1) == c);
         const double lo = isZ ? tb.y : -tb.y;
         const double up = isZ ? tb.z : -tb.z;
@@ -144,25 +151,29 @@ inline size_t fp64_smem_bytes() {
   return sizeof(double2) * (FP64_WARPS * 32 * FP64_TROW + FP64_WARPS * 64);
 }
 
-// U1 = (bPhi S0 - dt Phibar S_wz, S_zeta, S_delta), summing the Q partial slots in order.
+// U1 = (bPhi S0 - Phibar S_wz, S_zeta, S_delta) for every coefficient of every instance,
+// summing the instance's Q partial slots in order.
 static __global__ void k_rexi_finalize(const double2* __restrict__ U0, const double2* __restrict__ partial,
-                                double2* __restrict__ U1, int B, int nlm, int Q, double2 S0,
-                                double hphibar) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long long)B * nlm) return;
-  const int b = (int)(i / nlm), idx = (int)(i - (long long)b * nlm);
+                                       double2* __restrict__ U1, const Inst* __restrict__ insts,
+                                       const long long* __restrict__ ecum, int ninst, long long total,
+                                       double phibar) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int i = inst_of(ecum, ninst, e);
+  const Inst I = insts[i];
+  const int nlm = I.nlm, idx = (int)(e - ecum[i]);
   double2 sz = make_double2(0, 0), sd = sz, sw = sz;
-  const double2* p = partial + (size_t)b * Q * 3 * nlm + idx;
-  for (int q = 0; q < Q; ++q) {
+  const double2* p = partial + I.poff + idx;
+  for (int q = 0; q < I.Q; ++q) {
     sz = cadd(sz, p[0]);
     sd = cadd(sd, p[nlm]);
     sw = cadd(sw, p[2 * nlm]);
     p += 3 * nlm;
   }
-  const double2 bp = U0[(size_t)b * 3 * nlm + idx];
-  double2 phi = cmul(S0, bp);
-  if (idx != 0) phi = make_double2(fma(-hphibar, sw.x, phi.x), fma(-hphibar, sw.y, phi.y));
-  double2* o = U1 + (size_t)b * 3 * nlm + idx;
+  const double2 bp = U0[I.soff + idx];
+  double2 phi = cmul(I.S0, bp);
+  if (idx != 0) phi = make_double2(fma(-phibar, sw.x, phi.x), fma(-phibar, sw.y, phi.y));
+  double2* o = U1 + I.soff + idx;
   o[0] = phi;
   o[nlm] = sz;
   o[2 * nlm] = sd;

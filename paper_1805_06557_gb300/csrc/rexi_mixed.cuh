@@ -96,7 +96,7 @@ inline size_t mixed_rhs_bytes(int nlm, int batch) {
 
 
 struct MixedArgs {
-  const double2* U0;
+  const double2* U0;    // state base
   double2* partial;
   const float4* tab32;
   const TabDF* tabdf;
@@ -104,27 +104,34 @@ struct MixedArgs {
   const PoleD* p64;
   const PoleDF* pdf;
   const Tile* tiles;
-  const Rhs32* rhs32;   // [B][nlm]
-  const RhsDF* rhsdf;   // [B][nlm]
+  const Inst* insts;
+  const Rhs32* rhs32;   // [sum nlm]
+  const RhsDF* rhsdf;   // [sum nlm]
   void* scratch;
   int ntiles_light, ntiles_heavy;  // light tiles first, then heavy tiles, in `tiles`
-  int B, T, nlm, Q, kmax, nseg_max;
+  int Ttab, kmax, nseg_max;
   int warps_light;      // warps of the light grid (the heavy scratch starts after theirs)
 };
 
 // ---- pre-pass: FP32 and double-float right-hand-side pieces ----------------------------
-static __global__ void k_mixed_rhs(const double2* __restrict__ U0, const D4* __restrict__ tab,
-                            Rhs32* __restrict__ r32, RhsDF* __restrict__ rdf, int B, int nlm) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long long)B * nlm) return;
-  const int b = (int)(i / nlm), idx = (int)(i - (long long)b * nlm);
-  const double2* u = U0 + (size_t)b * 3 * nlm;
+static __global__ void k_mixed_rhs(const double2* __restrict__ U0, const D4* __restrict__ tab, int Ttab,
+                                   Rhs32* __restrict__ r32, RhsDF* __restrict__ rdf,
+                                   const Inst* __restrict__ insts, const long long* __restrict__ ecum,
+                                   int ninst, long long total) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int i = inst_of(ecum, ninst, e);
+  const Inst I = insts[i];
+  const int nlm = I.nlm, idx = (int)(e - ecum[i]);
+  const int m = m_of(I.T, idx);
+  const double q = tab[moff(Ttab, m) + (idx - moff(I.T, m))].w;
+  const double2* u = U0 + I.soff;
   const double2 bp = u[idx], bz = u[nlm + idx], bd = u[2 * nlm + idx];
-  const double q = tab[idx].w;
   const double2 qbp = make_double2(q * bp.x, q * bp.y);
-  r32[i] = Rhs32{make_float2((float)bz.x, (float)bz.y), make_float2((float)bd.x, (float)bd.y),
+  const size_t o = I.roff + idx;
+  r32[o] = Rhs32{make_float2((float)bz.x, (float)bz.y), make_float2((float)bd.x, (float)bd.y),
                  make_float2((float)qbp.x, (float)qbp.y)};
-  rdf[i] = RhsDF{split4(bz.x, bz.y), split4(bd.x, bd.y), split4(qbp.x, qbp.y)};
+  rdf[o] = RhsDF{split4(bz.x, bz.y), split4(bd.x, bd.y), split4(qbp.x, qbp.y)};
 }
 
 // ---- light kernel ------------------------------------------------------------------
@@ -135,8 +142,8 @@ struct LightSmem {
 
 // one forward step of the FP32 chain recurrence for element k (n = m + k)
 __device__ __forceinline__ void light_fwd(const MixedArgs& a, const PoleF& pf, const Rhs32* rb,
-                                          int off, int k, int c, float2& ct, float2& y) {
-  const float4 tb = __ldg(a.tab32 + off + k);
+                                          int off, int toff, int k, int c, float2& ct, float2& y) {
+  const float4 tb = __ldg(a.tab32 + toff + k);
   const Rhs32 rr = rb[off + k];
   const bool isZ = ((k & 1) == c);
   const float lo = isZ ? tb.y : -tb.y;
@@ -163,20 +170,20 @@ k_rexi_light(MixedArgs a) {
   const int gw = blockIdx.x * MIX_WARPS + wib;
   const int W = gridDim.x * MIX_WARPS;
   float4* ckpt = reinterpret_cast<float4*>(a.scratch) + (size_t)gw * a.nseg_max * 32;
-  const int total = a.ntiles_light * a.B;
-  const int T = a.T, nlm = a.nlm;
+  const int total = a.ntiles_light;
   for (int round = 0; round * W < total; ++round) {
     const int t = round * W + ((round & 1) ? (W - 1 - gw) : gw);
     if (t >= total) continue;
-    const int it = t / a.B, b = t - it * a.B;
-    const Tile tl = a.tiles[it];
-    const int m = tl.m, c = tl.chain, K = T + 1 - m, off = moff(T, m);
+    const Tile tl = a.tiles[t];
+    const Inst I = a.insts[tl.inst];
+    const int T = I.T, nlm = I.nlm;
+    const int m = tl.m, c = tl.chain, K = T + 1 - m, off = moff(T, m), toff = moff(a.Ttab, m);
     const int nseg = (K + SEG - 1) / SEG;
-    const Rhs32* rb = a.rhs32 + (size_t)b * nlm;
-    double2* part = a.partial + ((size_t)b * a.Q + tl.q) * 3 * nlm;
+    const Rhs32* rb = a.rhs32 + I.roff;
+    double2* part = a.partial + I.poff + (size_t)tl.q * 3 * nlm;
 
     for (int gi = 0; gi < tl.ng; ++gi) {
-      const PoleF pf = a.p32[(tl.g0 + gi) * 32 + lane];
+      const PoleF pf = a.p32[I.pole0 + (tl.g0 + gi) * 32 + lane];
       __syncwarp();
       S.w[lane] = pf.w;
       S.wz[lane] = pf.wz;
@@ -187,7 +194,7 @@ k_rexi_light(MixedArgs a) {
 #pragma unroll
         for (int i = 0; i < SEG; ++i) {
           const int k = s * SEG + i;
-          if (k < K) light_fwd(a, pf, rb, off, k, c, ct, y);
+          if (k < K) light_fwd(a, pf, rb, off, toff, k, c, ct, y);
           ca[i] = ct;
           ya[i] = y;
         }
@@ -207,7 +214,7 @@ k_rexi_light(MixedArgs a) {
           }
 #pragma unroll
           for (int i = 0; i < SEG; ++i) {
-            light_fwd(a, pf, rb, off, s * SEG + i, c, ct, y);  // full segment: k < K here
+            light_fwd(a, pf, rb, off, toff, s * SEG + i, c, ct, y);  // full segment: k < K here
             ca[i] = ct;
             ya[i] = y;
           }
@@ -262,9 +269,9 @@ k_rexi_light(MixedArgs a) {
 // ---- heavy kernel ------------------------------------------------------------------
 // residual of chain row k in double-float:  r_k - d_k x_k - lo_k x_{k-1} - up_k x_{k+1}
 __device__ __forceinline__ float2 heavy_residual(const MixedArgs& a, const PoleDF& pq,
-                                                 const RhsDF* rb, int off, int k, int K, int c,
-                                                 float2 xm, float2 x0, float2 xp) {
-  const TabDF tb = a.tabdf[off + k];
+                                                 const RhsDF* rb, int off, int toff, int k, int K,
+                                                 int c, float2 xm, float2 x0, float2 xp) {
+  const TabDF tb = a.tabdf[toff + k];
   const bool isZ = ((k & 1) == c);
   const df hw{tb.a.x, tb.a.y}, cm{tb.a.z, tb.a.w}, cp{tb.b.x, tb.b.y}, q{tb.b.z, tb.b.w};
   const RhsDF rr = rb[off + k];
@@ -311,21 +318,21 @@ k_rexi_heavy(MixedArgs a) {
                (size_t)gw * a.kmax * 32 * (sizeof(float4) + sizeof(float2));
   float4* S1 = reinterpret_cast<float4*>(base);
   float2* S2 = reinterpret_cast<float2*>(base + (size_t)a.kmax * 32 * sizeof(float4));
-  const int total = a.ntiles_heavy * a.B;
-  const int T = a.T, nlm = a.nlm;
+  const int total = a.ntiles_heavy;
 
   for (int round = 0; round * W < total; ++round) {
     const int t = round * W + ((round & 1) ? (W - 1 - gw) : gw);
     if (t >= total) continue;
-    const int it = t / a.B, b = t - it * a.B;
-    const Tile tl = a.tiles[a.ntiles_light + it];
-    const int m = tl.m, c = tl.chain, K = T + 1 - m, off = moff(T, m);
-    const Rhs32* rb = a.rhs32 + (size_t)b * nlm;
-    const RhsDF* rbd = a.rhsdf + (size_t)b * nlm;
-    double2* part = a.partial + ((size_t)b * a.Q + tl.q) * 3 * nlm;
+    const Tile tl = a.tiles[a.ntiles_light + t];
+    const Inst I = a.insts[tl.inst];
+    const int T = I.T, nlm = I.nlm;
+    const int m = tl.m, c = tl.chain, K = T + 1 - m, off = moff(T, m), toff = moff(a.Ttab, m);
+    const Rhs32* rb = a.rhs32 + I.roff;
+    const RhsDF* rbd = a.rhsdf + I.roff;
+    double2* part = a.partial + I.poff + (size_t)tl.q * 3 * nlm;
 
     for (int gi = 0; gi < tl.ng; ++gi) {
-      const int pidx = (tl.g0 + gi) * 32 + lane;
+      const int pidx = I.pole0 + (tl.g0 + gi) * 32 + lane;
       const PoleF pf = a.p32[pidx];
       const PoleDF pq = a.pdf[pidx];
       {
@@ -337,7 +344,7 @@ k_rexi_heavy(MixedArgs a) {
       // ---- A: FP32 forward, store (inv, y) ------------------------------------------
       float2 ct = make_float2(0.f, 0.f), y = make_float2(0.f, 0.f);
       for (int k = 0; k < K; ++k) {
-        const float4 tb = __ldg(a.tab32 + off + k);
+        const float4 tb = __ldg(a.tab32 + toff + k);
         const Rhs32 rr = rb[off + k];
         const bool isZ = ((k & 1) == c);
         const float lo = isZ ? tb.y : -tb.y;
@@ -360,7 +367,7 @@ k_rexi_heavy(MixedArgs a) {
       float2 xn = make_float2(0.f, 0.f);
       for (int k = K - 1; k >= 0; --k) {
         const float4 s = S1[(size_t)k * 32 + lane];
-        const float4 tb = __ldg(a.tab32 + off + k);
+        const float4 tb = __ldg(a.tab32 + toff + k);
         const float up = ((k & 1) == c) ? tb.z : -tb.z;
         const float2 cc = make_float2(up * s.x, up * s.y);
         const float2 x = make_float2(s.z - fmaf(cc.x, xn.x, -cc.y * xn.y),
@@ -373,8 +380,8 @@ k_rexi_heavy(MixedArgs a) {
       float2 yc = make_float2(0.f, 0.f);
       for (int k = 0; k < K; ++k) {
         const float2 xp = (k + 1 < K) ? S2[(size_t)(k + 1) * 32 + lane] : make_float2(0.f, 0.f);
-        const float2 res = heavy_residual(a, pq, rbd, off, k, K, c, xm, x0, xp);
-        const float4 tb = __ldg(a.tab32 + off + k);
+        const float2 res = heavy_residual(a, pq, rbd, off, toff, k, K, c, xm, x0, xp);
+        const float4 tb = __ldg(a.tab32 + toff + k);
         const float lo = ((k & 1) == c) ? tb.y : -tb.y;
         const float4 s = S1[(size_t)k * 32 + lane];
         const float2 inv = make_float2(s.x, s.y);
@@ -387,7 +394,7 @@ k_rexi_heavy(MixedArgs a) {
       float2 dn = make_float2(0.f, 0.f);
       for (int k = K - 1; k >= 0; --k) {
         const float4 s = S1[(size_t)k * 32 + lane];
-        const float4 tb = __ldg(a.tab32 + off + k);
+        const float4 tb = __ldg(a.tab32 + toff + k);
         const float up = ((k & 1) == c) ? tb.z : -tb.z;
         const float2 cc = make_float2(up * s.x, up * s.y);
         const float2 dx = make_float2(s.z - fmaf(cc.x, dn.x, -cc.y * dn.y),

@@ -1,10 +1,17 @@
-// REXI plan: tables, pole ordering, tiles and launches (paper Sec. 4.2, Eq. rexi).
+// REXI plans (paper Sec. 4.2, Eq. rexi): tables, pole sets, tiles and launches.
+//
+// An engine owns the dt-free tables of one largest truncation, an arena of scaled pole sets
+// (one per (T, N, dt, contour)), the workspace and the launch descriptors.  A launch is a
+// list of instances (states), each with its own truncation and pole set, cut into tiles
+// (instance, m, chain, pole range) sorted by cost; the kernels are the same for a uniform
+// batch (rexi_plan) and a ragged one (rexi_ragged).
 #include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstring>
 #include <map>
 #include <numeric>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -14,39 +21,147 @@
 using namespace rexi;
 using cplx = std::complex<double>;
 
-struct rexi_plan {
-  rexi_plan_desc d{};
-  int T = 0, N = 0, nlm = 0, Npad = 0, ngroups = 0, precision = 0, device = 0, nsm = 0;
-  int n_heavy = 0, g_light = 0, g_heavy = 0;
-  double X = 0;
+namespace {
+
+double eps_nm(int n, int m) {
+  if (n <= m) return 0.0;
+  return std::sqrt((double(n) * n - double(m) * m) / (4.0 * n * n - 1.0));
+}
+
+template <class P>
+int dev_alloc(P** p, size_t bytes, long long* acc) {
+  cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(bytes, 16));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(REXI_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  *acc += (long long)bytes;
+  return REXI_OK;
+}
+
+// ---- pole sets (host) -----------------------------------------------------------------
+struct PoleSet {
+  int T = 0, N = 0, Npad = 0, ngroups = 0, n_heavy = 0, g_light = 0, g_heavy = 0;
+  double dt = 0, X = 0;
   cplx S0 = 0;
-  std::vector<cplx> z_sorted, w_sorted;  // internal order (padded)
-  std::vector<int> heavy_sorted;
-  cudaStream_t stream = nullptr;
-  // device
-  D4* d_tab64 = nullptr;
-  float4* d_tab32 = nullptr;
-  PoleD* d_p64 = nullptr;
-  PoleF* d_p32 = nullptr;
-  double2* d_partial = nullptr;
-  size_t partial_elems = 0;
-  void* d_scratch = nullptr;
-  size_t scratch_bytes = 0;
-  void* d_rhs = nullptr;  // mixed pre-pass output: Rhs32[max_batch][nlm] then RhsDF[max_batch][nlm]
-  TabDF* d_tabdf = nullptr;
-  PoleDF* d_pdf = nullptr;
-  double2* d_stage_in = nullptr;
-  double2* d_stage_out = nullptr;
-  // persistent grids
-  int grid_fp64 = 0, grid_light = 0, grid_heavy = 0;
-  // tiles per Q choice: Q -> (device tiles, count)
-  struct TileSet {
-    Tile* d = nullptr;
-    int n = 0, n_light = 0, Q = 0;
+  std::vector<cplx> z, w;   // internal order, padded, unscaled
+  std::vector<int> heavy;
+  int pole0 = -1;           // position in the device arena (-1: not uploaded)
+};
+
+// Orders (and pads) the poles.  FP64: given order, padding at the end.  MIXED: light poles
+// first, heavy ones (largest gain |w| / dist(z, [-iX, iX]), padded to whole groups) last.
+int make_poleset(PoleSet& ps, int precision, int T, int N, double dt, double X, const cplx* z,
+                 const cplx* w, double heavy_tau) {
+  ps.T = T;
+  ps.N = N;
+  ps.dt = dt;
+  ps.X = X;
+  for (int n = 0; n < N; ++n)
+    if (std::abs(z[n]) < 1e-12) return fail(REXI_EINVAL, "pole %d is zero", n);
+  cplx s = 0, comp = 0;  // S0 = sum w/z, compensated
+  for (int n = 0; n < N; ++n) {
+    const cplx yv = w[n] / z[n] - comp;
+    const cplx t = s + yv;
+    comp = (t - s) - yv;
+    s = t;
+  }
+  ps.S0 = s;
+  ps.Npad = (N + 31) / 32 * 32;
+  ps.ngroups = ps.Npad / 32;
+  const int npad = ps.Npad - N;
+  ps.z.clear();
+  ps.w.clear();
+  ps.heavy.clear();
+  auto push = [&](cplx zz, cplx ww, int h) {
+    ps.z.push_back(zz);
+    ps.w.push_back(ww);
+    ps.heavy.push_back(h);
   };
-  std::map<int, TileSet> tilesets;
+  if (precision == REXI_FP64) {
+    for (int n = 0; n < N; ++n) push(z[n], w[n], 1);
+    for (int i = 0; i < npad; ++i) push(1.0, 0.0, 1);
+    ps.n_heavy = N;
+    ps.g_light = 0;
+    ps.g_heavy = ps.ngroups;
+    return REXI_OK;
+  }
+  const double tau = heavy_tau < 0 ? 1e-3 : heavy_tau;
+  std::vector<double> gain(N);
+  int nh = 0;
+  for (int n = 0; n < N; ++n) {
+    const double yi = std::min(std::max(z[n].imag(), -X), X);
+    gain[n] = std::abs(w[n]) / std::max(std::abs(z[n] - cplx(0.0, yi)), 1e-300);
+    if (gain[n] > tau) ++nh;
+  }
+  const int nh_pad = std::min((nh + 31) / 32 * 32, N);
+  if (nh_pad == N && N % 32 != 0) {  // everything heavy, padding at the end
+    for (int n = 0; n < N; ++n) push(z[n], w[n], 1);
+    for (int i = 0; i < npad; ++i) push(1.0, 0.0, 1);
+    ps.n_heavy = N;
+    ps.g_light = 0;
+    ps.g_heavy = ps.ngroups;
+    return REXI_OK;
+  }
+  std::vector<int> by_gain(N);
+  std::iota(by_gain.begin(), by_gain.end(), 0);
+  std::stable_sort(by_gain.begin(), by_gain.end(), [&](int a, int b) { return gain[a] > gain[b]; });
+  std::vector<int> hv(N, 0);
+  for (int i = 0; i < nh_pad; ++i) hv[by_gain[i]] = 1;
+  for (int n = 0; n < N; ++n)
+    if (!hv[n]) push(z[n], w[n], 0);
+  for (int i = 0; i < npad; ++i) push(1.0, 0.0, 0);
+  for (int n = 0; n < N; ++n)
+    if (hv[n]) push(z[n], w[n], 1);
+  ps.n_heavy = nh_pad;
+  ps.g_light = (ps.Npad - nh_pad) / 32;
+  ps.g_heavy = nh_pad / 32;
+  return REXI_OK;
+}
+
+int make_poleset_from_contour(PoleSet& ps, int precision, int T, int N, double dt, double X, double p0,
+                              double Xc, double heavy_tau) {
+  std::vector<double> zz(2 * N), ww(2 * N);
+  int rc = rexi_coeffs(N, p0, Xc, 0, zz.data(), ww.data());
+  if (rc) return rc;
+  std::vector<cplx> z(N), w(N);
+  for (int n = 0; n < N; ++n) {
+    z[n] = cplx(zz[2 * n], zz[2 * n + 1]);
+    w[n] = cplx(ww[2 * n], ww[2 * n + 1]);
+  }
+  return make_poleset(ps, precision, T, N, dt, X, z.data(), w.data(), heavy_tau);
+}
+
+int ranges_used(int G, int Q) {
+  if (G == 0) return 0;
+  const int per = (G + Q - 1) / Q;
+  return (G + per - 1) / per;
+}
+
+}  // namespace
+
+// ---- engine -----------------------------------------------------------------------------
+struct Engine {
+  int precision = 0, Ttab = 0, device = 0, nsm = 0, kmax = 0, nseg_max = 0;
+  double omega = 0, radius = 0, phibar = 0;
+  cudaStream_t stream = nullptr;
+  D4* tab64 = nullptr;
+  float4* tab32 = nullptr;
+  TabDF* tabdf = nullptr;
+  PoleD* p64 = nullptr;
+  PoleF* p32 = nullptr;
+  PoleDF* pdf = nullptr;
+  int pole_cap = 0, pole_used = 0;
+  double2* partial = nullptr;
+  size_t partial_cap = 0;
+  void* rhs = nullptr;
+  size_t rhs_cap = 0;  // elements
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  int grid_fp64 = 0, grid_light = 0, grid_heavy = 0;
   long long workspace = 0;
-  // per-kernel event timing
+  // profiling
   int profiling = 0;
   struct Pend {
     cudaEvent_t a, b;
@@ -58,134 +173,364 @@ struct rexi_plan {
   int prof_n[REXI_NKERNELS] = {0};
 };
 
-namespace {
-cudaEvent_t take_event(rexi_plan* p) {
-  if (!p->event_pool.empty()) {
-    cudaEvent_t e = p->event_pool.back();
-    p->event_pool.pop_back();
-    return e;
-  }
-  cudaEvent_t e;
-  cudaEventCreate(&e);
-  return e;
-}
-// Records the start event of kernel `kid` (profiling only); returns the pending index.
-int prof_begin(rexi_plan* p, int kid) {
-  if (!p->profiling) return -1;
-  rexi_plan::Pend q{take_event(p), take_event(p), kid};
-  cudaEventRecord(q.a, p->stream);
-  p->pending.push_back(q);
-  return (int)p->pending.size() - 1;
-}
-void prof_end(rexi_plan* p, int h) {
-  if (h >= 0) cudaEventRecord(p->pending[h].b, p->stream);
-}
-}  // namespace
+// Device copy of one launch: instances, tiles (light then heavy), element prefix sums.
+struct LaunchSet {
+  Inst* insts = nullptr;
+  Tile* tiles = nullptr;
+  long long* ecum = nullptr;
+  int ninst = 0, ntiles = 0, ntiles_light = 0;
+  long long total = 0, partial_elems = 0;
+};
 
 namespace {
 
-double eps_nm(int n, int m) {
-  if (n <= m) return 0.0;
-  return std::sqrt((double(n) * n - double(m) * m) / (4.0 * n * n - 1.0));
+void free_launch(LaunchSet& L) {
+  cudaFree(L.insts);
+  cudaFree(L.tiles);
+  cudaFree(L.ecum);
+  L = LaunchSet();
 }
 
-template <class P>
-int dev_alloc(P** p, size_t bytes, long long* acc) {
-  cudaError_t e = cudaMalloc((void**)p, bytes);
-  if (e != cudaSuccess) {
-    *p = nullptr;
-    cudaGetLastError();
-    return fail(REXI_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+void engine_free(Engine& e) {
+  if (e.stream || e.tab64) cudaStreamSynchronize(e.stream);
+  for (void* p : {(void*)e.tab64, (void*)e.tab32, (void*)e.tabdf, (void*)e.p64, (void*)e.p32, (void*)e.pdf,
+                  (void*)e.partial, (void*)e.rhs, (void*)e.scratch})
+    cudaFree(p);
+  for (auto& q : e.pending) {
+    cudaEventDestroy(q.a);
+    cudaEventDestroy(q.b);
   }
-  *acc += (long long)bytes;
-  return REXI_OK;
+  for (auto ev : e.event_pool) cudaEventDestroy(ev);
+  e.pending.clear();
+  e.event_pool.clear();
 }
 
-int ranges_used(int G, int Q) {
-  if (G == 0) return 0;
-  const int per = (G + Q - 1) / Q;
-  return (G + per - 1) / per;
-}
+size_t rhs32_bytes(size_t elems) { return (sizeof(Rhs32) * elems + 255) / 256 * 256; }
 
-// Tiles for one state: light groups [0, gl) split into Ql ranges, heavy groups [gl, gl+gh)
-// into Qh ranges; every range gets one tile per (m, chain).  Sorted by decreasing cost.
-std::vector<Tile> build_tiles(int T, int gl, int Ql, int gh, int Qh, int heavy_cost) {
-  std::vector<Tile> v;
-  auto add_ranges = [&](int gbase, int G, int Q, int qbase, int heavy) {
-    if (G == 0) return;
-    const int per = (G + Q - 1) / Q;
-    int q = qbase;
-    for (int g = 0; g < G; g += per, ++q) {
-      const int ng = std::min(per, G - g);
-      for (int m = 0; m <= T; ++m)
-        for (int c = 0; c < 2; ++c) {
-          Tile t{};
-          t.m = m;
-          t.chain = c;
-          t.g0 = gbase + g;
-          t.ng = ng;
-          t.q = q;
-          t.heavy = heavy;
-          t.cost = (T + 1 - m) * ng * (heavy ? heavy_cost : 1);
-          v.push_back(t);
-        }
+// tables for truncation Ttab (dt-free), persistent grids, scratch, pole arena, workspace
+int engine_init(Engine& e, int precision, int Ttab, double omega, double radius, double phibar,
+                cudaStream_t stream, int pole_cap, size_t partial_cap, size_t rhs_cap) {
+  e.precision = precision;
+  e.Ttab = Ttab;
+  e.omega = omega;
+  e.radius = radius;
+  e.phibar = phibar;
+  e.stream = stream;
+  e.kmax = Ttab + 1;
+  e.nseg_max = (e.kmax + SEG - 1) / SEG;
+  if (cudaGetDevice(&e.device) != cudaSuccess) return fail(REXI_ECUDA, "no CUDA device");
+  cudaDeviceGetAttribute(&e.nsm, cudaDevAttrMultiProcessorCount, e.device);
+  const int nlm = (Ttab + 1) * (Ttab + 2) / 2;
+  std::vector<D4> t64(nlm);
+  std::vector<float4> t32(nlm);
+  std::vector<TabDF> tdf(nlm);
+  for (int m = 0; m <= Ttab; ++m)
+    for (int n = m; n <= Ttab; ++n) {
+      const int idx = moff(Ttab, m) + (n - m);
+      const double nn1 = double(n) * (n + 1);
+      const double wn = n > 0 ? 2.0 * omega * m / nn1 : 0.0;
+      const double cm = (n > m && n - 1 > 0) ? 2.0 * omega * (n + 1.0) / n * eps_nm(n, m) : 0.0;
+      const double cp = 2.0 * omega * n / (n + 1.0) * eps_nm(n + 1, m);
+      const double q = nn1 / (radius * radius);
+      t64[idx] = D4{wn, cm, cp, q};
+      t32[idx] = make_float4((float)wn, (float)cm, (float)cp, (float)q);
+      tdf[idx] = TabDF{split4(wn, cm), split4(cp, q)};
     }
-  };
-  add_ranges(0, gl, Ql, 0, 0);
-  add_ranges(gl, gh, Qh, ranges_used(gl, Ql), 1);
-  // light tiles first, then heavy tiles; each part sorted by decreasing cost
-  std::stable_sort(v.begin(), v.end(), [](const Tile& a, const Tile& b) {
-    if (a.heavy != b.heavy) return a.heavy < b.heavy;
-    return a.cost > b.cost;
-  });
-  return v;
-}
-
-// Number of pole ranges so that a batch of B states gives about `target` warp tiles.
-int choose_Q(int groups, int B, int T, int target) {
-  const long long per_q = (long long)B * 2 * (T + 1);
-  int Q = (int)std::max<long long>(1, (target + per_q - 1) / per_q);
-  return std::min(Q, std::max(groups, 1));
-}
-
-int get_tiles(rexi_plan* p, int B, rexi_plan::TileSet** out) {
-  int Ql = 0, Qh = 0;
-  const int hc = 3;
-  if (p->precision == REXI_FP64) {
-    Qh = choose_Q(p->ngroups, B, p->T, 4 * p->grid_fp64 * FP64_WARPS);
+  long long& ws = e.workspace;
+  int rc;
+  cudaError_t ce;
+  if ((rc = dev_alloc(&e.tab64, sizeof(D4) * nlm, &ws))) return rc;
+  if ((ce = cudaMemcpy(e.tab64, t64.data(), sizeof(D4) * nlm, cudaMemcpyHostToDevice)))
+    return cuda_fail(ce, "cudaMemcpy(tables)");
+  e.pole_cap = pole_cap;
+  if ((rc = dev_alloc(&e.p64, sizeof(PoleD) * pole_cap, &ws))) return rc;
+  if (precision == REXI_FP64) {
+    const size_t smem = fp64_smem_bytes();
+    if ((ce = cudaFuncSetAttribute(k_rexi_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+      return cuda_fail(ce, "cudaFuncSetAttribute(k_rexi_fp64)");
+    int per_sm = 0;
+    if ((ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rexi_fp64, FP64_WARPS * 32, smem)))
+      return cuda_fail(ce, "occupancy(k_rexi_fp64)");
+    e.grid_fp64 = e.nsm * std::max(1, std::min(per_sm, 2));
+    e.scratch_bytes = sizeof(D4) * (size_t)e.grid_fp64 * FP64_WARPS * e.kmax * 32;
   } else {
-    const int target_l = 4 * p->grid_light * MIX_WARPS;
-    const int target_h = 4 * p->grid_heavy * MIX_WARPS;
-    Ql = p->g_light ? choose_Q(p->g_light, B, p->T, target_l) : 0;
-    Qh = p->g_heavy ? choose_Q(p->g_heavy, B, p->T, target_h) : 0;
+    if ((rc = dev_alloc(&e.tab32, sizeof(float4) * nlm, &ws))) return rc;
+    if ((rc = dev_alloc(&e.tabdf, sizeof(TabDF) * nlm, &ws))) return rc;
+    if ((ce = cudaMemcpy(e.tab32, t32.data(), sizeof(float4) * nlm, cudaMemcpyHostToDevice)) ||
+        (ce = cudaMemcpy(e.tabdf, tdf.data(), sizeof(TabDF) * nlm, cudaMemcpyHostToDevice)))
+      return cuda_fail(ce, "cudaMemcpy(tables)");
+    if ((rc = dev_alloc(&e.p32, sizeof(PoleF) * pole_cap, &ws))) return rc;
+    if ((rc = dev_alloc(&e.pdf, sizeof(PoleDF) * pole_cap, &ws))) return rc;
+    const size_t hsm = heavy_smem_bytes();
+    if ((ce = cudaFuncSetAttribute(k_rexi_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm)))
+      return cuda_fail(ce, "cudaFuncSetAttribute(k_rexi_heavy)");
+    int per_l = 0, per_h = 0;
+    if ((ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_l, k_rexi_light, MIX_WARPS * 32, 0)))
+      return cuda_fail(ce, "occupancy(k_rexi_light)");
+    if ((ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_h, k_rexi_heavy, MIX_WARPS * 32, hsm)))
+      return cuda_fail(ce, "occupancy(k_rexi_heavy)");
+    e.grid_light = e.nsm * std::max(1, std::min(per_l, 4));
+    e.grid_heavy = e.nsm * std::max(1, std::min(per_h, 2));
+    e.scratch_bytes = sizeof(float4) * (size_t)e.grid_light * MIX_WARPS * e.nseg_max * 32 +
+                      (sizeof(float4) + sizeof(float2)) * (size_t)e.grid_heavy * MIX_WARPS * e.kmax * 32;
+    e.rhs_cap = rhs_cap;
+    if ((rc = dev_alloc((char**)&e.rhs, rhs32_bytes(rhs_cap) + sizeof(RhsDF) * rhs_cap, &ws))) return rc;
   }
-  const int key = Ql * 100000 + Qh;
-  auto it = p->tilesets.find(key);
-  if (it == p->tilesets.end()) {
-    std::vector<Tile> v = (p->precision == REXI_FP64)
-                              ? build_tiles(p->T, 0, 1, p->ngroups, Qh, 1)
-                              : build_tiles(p->T, p->g_light, std::max(Ql, 1), p->g_heavy,
-                                            std::max(Qh, 1), hc);
-    rexi_plan::TileSet ts;
-    ts.n = (int)v.size();
-    ts.n_light = 0;
-    for (const Tile& t : v) ts.n_light += t.heavy ? 0 : 1;
-    ts.Q = ranges_used(p->precision == REXI_FP64 ? 0 : p->g_light, std::max(Ql, 1)) +
-           ranges_used(p->precision == REXI_FP64 ? p->ngroups : p->g_heavy, std::max(Qh, 1));
-    cudaError_t e = cudaMalloc(&ts.d, sizeof(Tile) * v.size());
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(tiles)");
-    e = cudaMemcpy(ts.d, v.data(), sizeof(Tile) * v.size(), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(tiles)");
-    p->workspace += (long long)(sizeof(Tile) * v.size());
-    it = p->tilesets.emplace(key, ts).first;
-  }
-  if ((size_t)B * it->second.Q * 3 * p->nlm > p->partial_elems)
-    return fail(REXI_EINVAL, "internal: partial buffer too small (B=%d Q=%d)", B, it->second.Q);
-  *out = &it->second;
+  if ((rc = dev_alloc((char**)&e.scratch, e.scratch_bytes, &ws))) return rc;
+  e.partial_cap = partial_cap;
+  if ((rc = dev_alloc(&e.partial, sizeof(double2) * partial_cap, &ws))) return rc;
   return REXI_OK;
 }
 
+// Appends a pole set to the arena (scaled by 1/dt: z' = z/dt, w' = w/dt, w/z, 1/z', Phibar/z').
+int engine_upload_poles(Engine& e, PoleSet& ps) {
+  if (e.pole_used + ps.Npad > e.pole_cap)
+    return fail(REXI_EBUSY, "pole arena full (%d + %d > %d)", e.pole_used, ps.Npad, e.pole_cap);
+  std::vector<PoleD> pd(ps.Npad);
+  std::vector<PoleF> pf(ps.Npad);
+  std::vector<PoleDF> pq(ps.Npad);
+  for (int i = 0; i < ps.Npad; ++i) {
+    const cplx z = ps.z[i], w = ps.w[i];
+    const cplx zs = z / ps.dt, ws = w / ps.dt, wz = w / z, iz = 1.0 / zs, gz = e.phibar / zs;
+    auto D = [](cplx c) { return make_double2(c.real(), c.imag()); };
+    auto F = [](cplx c) { return make_float2((float)c.real(), (float)c.imag()); };
+    pd[i] = PoleD{D(zs), D(ws), D(wz), D(iz), D(gz)};
+    pf[i] = PoleF{F(zs), F(ws), F(wz), F(iz), F(gz)};
+    pq[i] = PoleDF{split4(zs.real(), zs.imag()), split4(iz.real(), iz.imag()), split4(gz.real(), gz.imag())};
+  }
+  cudaError_t ce = cudaMemcpy(e.p64 + e.pole_used, pd.data(), sizeof(PoleD) * ps.Npad, cudaMemcpyHostToDevice);
+  if (!ce && e.p32) ce = cudaMemcpy(e.p32 + e.pole_used, pf.data(), sizeof(PoleF) * ps.Npad, cudaMemcpyHostToDevice);
+  if (!ce && e.pdf) ce = cudaMemcpy(e.pdf + e.pole_used, pq.data(), sizeof(PoleDF) * ps.Npad, cudaMemcpyHostToDevice);
+  if (ce) return cuda_fail(ce, "cudaMemcpy(poles)");
+  ps.pole0 = e.pole_used;
+  e.pole_used += ps.Npad;
+  return REXI_OK;
+}
+
+struct InstReq {
+  const PoleSet* ps;
+  long long soff;
+};
+
+// Builds the host launch description: per-instance descriptors (partial / rhs offsets),
+// tiles sorted by cost (light first, then heavy), element prefix sums.  Pole groups are cut
+// into ranges so that the launch has about qmul tiles per resident warp.
+void build_launch(const Engine& e, const std::vector<InstReq>& req, std::vector<Inst>& insts,
+                  std::vector<Tile>& tiles, std::vector<long long>& ecum, int& ntiles_light,
+                  long long& partial_elems, int qmul = 4) {
+  insts.clear();
+  tiles.clear();
+  ecum.clear();
+  long long units = 0;
+  for (auto& r : req) units += 2LL * (r.ps->T + 1);
+  units = std::max<long long>(units, 1);
+  int Ql_glob = 1, Qh_glob = 1;
+  if (e.precision == REXI_FP64) {
+    Qh_glob = (int)std::max<long long>(1, (qmul * (long long)e.grid_fp64 * FP64_WARPS + units - 1) / units);
+  } else {
+    Ql_glob = (int)std::max<long long>(1, (qmul * (long long)e.grid_light * MIX_WARPS + units - 1) / units);
+    Qh_glob = (int)std::max<long long>(1, (qmul * (long long)e.grid_heavy * MIX_WARPS + units - 1) / units);
+  }
+  long long poff = 0, roff = 0, ec = 0;
+  std::vector<Tile> light, heavy;
+  for (size_t i = 0; i < req.size(); ++i) {
+    const PoleSet& ps = *req[i].ps;
+    const int T = ps.T, nlm = (T + 1) * (T + 2) / 2;
+    const int Ql = ps.g_light ? std::min(Ql_glob, ps.g_light) : 1;
+    const int Qh = ps.g_heavy ? std::min(Qh_glob, ps.g_heavy) : 1;
+    const int ql = ranges_used(ps.g_light, Ql), qh = ranges_used(ps.g_heavy, Qh);
+    Inst I;
+    I.soff = req[i].soff;
+    I.poff = poff;
+    I.roff = roff;
+    I.T = T;
+    I.nlm = nlm;
+    I.Q = ql + qh;
+    I.pole0 = ps.pole0;
+    I.S0 = make_double2(ps.S0.real(), ps.S0.imag());
+    insts.push_back(I);
+    ecum.push_back(ec);
+    auto add = [&](int gbase, int G, int Q, int qbase, int hv, std::vector<Tile>& out) {
+      if (G == 0) return;
+      const int per = (G + Q - 1) / Q;
+      int q = qbase;
+      for (int g = 0; g < G; g += per, ++q) {
+        const int ng = std::min(per, G - g);
+        for (int m = 0; m <= T; ++m)
+          for (int c = 0; c < 2; ++c) {
+            const int w = (hv && e.precision != REXI_FP64) ? 3 : 1;
+            out.push_back(Tile{m, c, gbase + g, ng, q, hv, (T + 1 - m) * ng * w, (int)i});
+          }
+      }
+    };
+    add(0, ps.g_light, Ql, 0, 0, light);
+    add(ps.g_light, ps.g_heavy, Qh, ql, 1, heavy);
+    poff += (long long)I.Q * 3 * nlm;
+    roff += nlm;
+    ec += nlm;
+  }
+  ecum.push_back(ec);
+  auto bycost = [](const Tile& a, const Tile& b) { return a.cost > b.cost; };
+  std::stable_sort(light.begin(), light.end(), bycost);
+  std::stable_sort(heavy.begin(), heavy.end(), bycost);
+  ntiles_light = (int)light.size();
+  tiles = light;
+  tiles.insert(tiles.end(), heavy.begin(), heavy.end());
+  partial_elems = poff;
+}
+
+int upload_launch(LaunchSet& L, const std::vector<Inst>& insts, const std::vector<Tile>& tiles,
+                  const std::vector<long long>& ecum, int ntiles_light, long long partial_elems) {
+  free_launch(L);
+  cudaError_t ce;
+  if ((ce = cudaMalloc(&L.insts, sizeof(Inst) * std::max<size_t>(insts.size(), 1))) ||
+      (ce = cudaMalloc(&L.tiles, sizeof(Tile) * std::max<size_t>(tiles.size(), 1))) ||
+      (ce = cudaMalloc(&L.ecum, sizeof(long long) * ecum.size()))) {
+    cudaGetLastError();
+    return fail(REXI_ENOMEM, "launch descriptors: cudaMalloc failed");
+  }
+  if ((ce = cudaMemcpy(L.insts, insts.data(), sizeof(Inst) * insts.size(), cudaMemcpyHostToDevice)) ||
+      (ce = cudaMemcpy(L.tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice)) ||
+      (ce = cudaMemcpy(L.ecum, ecum.data(), sizeof(long long) * ecum.size(), cudaMemcpyHostToDevice)))
+    return cuda_fail(ce, "cudaMemcpy(launch descriptors)");
+  L.ninst = (int)insts.size();
+  L.ntiles = (int)tiles.size();
+  L.ntiles_light = ntiles_light;
+  L.total = ecum.back();
+  L.partial_elems = partial_elems;
+  return REXI_OK;
+}
+
+cudaEvent_t take_event(Engine& e) {
+  if (!e.event_pool.empty()) {
+    cudaEvent_t ev = e.event_pool.back();
+    e.event_pool.pop_back();
+    return ev;
+  }
+  cudaEvent_t ev;
+  cudaEventCreate(&ev);
+  return ev;
+}
+int prof_begin(Engine& e, int kid) {
+  if (!e.profiling) return -1;
+  Engine::Pend q{take_event(e), take_event(e), kid};
+  cudaEventRecord(q.a, e.stream);
+  e.pending.push_back(q);
+  return (int)e.pending.size() - 1;
+}
+void prof_end(Engine& e, int h) {
+  if (h >= 0) cudaEventRecord(e.pending[h].b, e.stream);
+}
+
+// Launches one REXI step of the launch set.  No allocation.
+int engine_launch(Engine& e, const LaunchSet& L, const double2* U0, double2* U1) {
+  if (L.partial_elems > (long long)e.partial_cap) return fail(REXI_EINVAL, "internal: partial buffer too small");
+  if (e.precision == REXI_FP64) {
+    Fp64Args a;
+    a.U0 = U0;
+    a.partial = e.partial;
+    a.tab = e.tab64;
+    a.poles = e.p64;
+    a.tiles = L.tiles;
+    a.insts = L.insts;
+    a.scratch = (D4*)e.scratch;
+    a.ntiles = L.ntiles;
+    a.Ttab = e.Ttab;
+    a.kmax = e.kmax;
+    const int h = prof_begin(e, 1);
+    k_rexi_fp64<<<e.grid_fp64, FP64_WARPS * 32, fp64_smem_bytes(), e.stream>>>(a);
+    prof_end(e, h);
+  } else {
+    if (L.total > (long long)e.rhs_cap) return fail(REXI_EINVAL, "internal: rhs buffer too small");
+    Rhs32* r32 = (Rhs32*)e.rhs;
+    RhsDF* rdf = (RhsDF*)((char*)e.rhs + rhs32_bytes(e.rhs_cap));
+    int h = prof_begin(e, 0);
+    k_mixed_rhs<<<(unsigned)((L.total + 255) / 256), 256, 0, e.stream>>>(U0, e.tab64, e.Ttab, r32, rdf, L.insts,
+                                                                         L.ecum, L.ninst, L.total);
+    prof_end(e, h);
+    MixedArgs a;
+    a.U0 = U0;
+    a.partial = e.partial;
+    a.tab32 = e.tab32;
+    a.tabdf = e.tabdf;
+    a.p32 = e.p32;
+    a.p64 = e.p64;
+    a.pdf = e.pdf;
+    a.tiles = L.tiles;
+    a.insts = L.insts;
+    a.rhs32 = r32;
+    a.rhsdf = rdf;
+    a.scratch = e.scratch;
+    a.ntiles_light = L.ntiles_light;
+    a.ntiles_heavy = L.ntiles - L.ntiles_light;
+    a.Ttab = e.Ttab;
+    a.kmax = e.kmax;
+    a.nseg_max = e.nseg_max;
+    a.warps_light = e.grid_light * MIX_WARPS;
+    if (a.ntiles_light) {
+      h = prof_begin(e, 2);
+      k_rexi_light<<<e.grid_light, MIX_WARPS * 32, 0, e.stream>>>(a);
+      prof_end(e, h);
+    }
+    if (a.ntiles_heavy) {
+      h = prof_begin(e, 3);
+      k_rexi_heavy<<<e.grid_heavy, MIX_WARPS * 32, heavy_smem_bytes(), e.stream>>>(a);
+      prof_end(e, h);
+    }
+  }
+  cudaError_t ce = cudaGetLastError();
+  if (ce != cudaSuccess) return cuda_fail(ce, "solve kernel launch");
+  const int hf = prof_begin(e, 4);
+  k_rexi_finalize<<<(unsigned)((L.total + 255) / 256), 256, 0, e.stream>>>(U0, e.partial, U1, L.insts, L.ecum,
+                                                                          L.ninst, L.total, e.phibar);
+  prof_end(e, hf);
+  ce = cudaGetLastError();
+  if (ce != cudaSuccess) return cuda_fail(ce, "finalize kernel launch");
+  return REXI_OK;
+}
+
+int engine_profile(Engine& e, double* ms, int* launches, int reset) {
+  REXI_CUDA_TRY(cudaStreamSynchronize(e.stream));
+  for (auto& q : e.pending) {
+    float t = 0.f;
+    REXI_CUDA_TRY(cudaEventElapsedTime(&t, q.a, q.b));
+    e.prof_ms[q.kid] += t;
+    e.prof_n[q.kid] += 1;
+    e.event_pool.push_back(q.a);
+    e.event_pool.push_back(q.b);
+  }
+  e.pending.clear();
+  for (int i = 0; i < REXI_NKERNELS; ++i) {
+    if (ms) ms[i] = e.prof_ms[i];
+    if (launches) launches[i] = e.prof_n[i];
+    if (reset) {
+      e.prof_ms[i] = 0;
+      e.prof_n[i] = 0;
+    }
+  }
+  return REXI_OK;
+}
+
+bool overlaps(const void* a, const void* b, size_t bytes) {
+  const char* x = (const char*)a;
+  const char* y = (const char*)b;
+  return x < y + bytes && y < x + bytes;
+}
+
 }  // namespace
+
+// =========================================================================================
+// Uniform plans: one pole set, batches of states with the same truncation
+// =========================================================================================
+struct rexi_plan {
+  rexi_plan_desc d{};
+  Engine e;
+  PoleSet ps;
+  int nlm = 0;
+  std::map<int, LaunchSet> launches;  // by batch size
+  double2* stage_in = nullptr;
+  double2* stage_out = nullptr;
+};
 
 extern "C" int rexi_plan_create(const rexi_plan_desc* desc, rexi_plan** out) {
   if (!desc || !out) return fail(REXI_EINVAL, "rexi_plan_create: null argument");
@@ -200,339 +545,98 @@ extern "C" int rexi_plan_create(const rexi_plan_desc* desc, rexi_plan** out) {
   if (d.max_batch < 1) return fail(REXI_EINVAL, "max_batch must be >= 1");
   if ((d.z == nullptr) != (d.w == nullptr)) return fail(REXI_EINVAL, "give both z and w or neither");
   if (!d.z && (!(d.p0 > 0) || !(d.Xc > 0))) return fail(REXI_EINVAL, "need p0 > 0 and Xc > 0");
-
   rexi_plan* p = new rexi_plan();
   p->d = d;
   p->d.z = p->d.w = nullptr;
-  p->T = d.T;
-  p->N = d.N;
   p->nlm = (d.T + 1) * (d.T + 2) / 2;
-  p->precision = d.precision;
-  p->stream = (cudaStream_t)d.stream;
   auto bail = [&](int code) {
     rexi_plan_destroy(p);
     return code;
   };
-  if (cudaGetDevice(&p->device) != cudaSuccess) return bail(fail(REXI_ECUDA, "no CUDA device"));
-  cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->device);
-
-  // ---- poles and weights --------------------------------------------------------------
-  std::vector<cplx> z(d.N), w(d.N);
+  const double X = rexi_spectrum_bound(d.T, d.dt, d.omega, d.radius, d.phibar);
+  int rc;
   if (d.z) {
+    std::vector<cplx> z(d.N), w(d.N);
     for (int n = 0; n < d.N; ++n) {
       z[n] = cplx(d.z[2 * n], d.z[2 * n + 1]);
       w[n] = cplx(d.w[2 * n], d.w[2 * n + 1]);
     }
+    rc = make_poleset(p->ps, d.precision, d.T, d.N, d.dt, X, z.data(), w.data(), d.heavy_tau);
   } else {
-    std::vector<double> zz(2 * d.N), ww(2 * d.N);
-    int rc = rexi_coeffs(d.N, d.p0, d.Xc, 0, zz.data(), ww.data());
-    if (rc) return bail(rc);
-    for (int n = 0; n < d.N; ++n) {
-      z[n] = cplx(zz[2 * n], zz[2 * n + 1]);
-      w[n] = cplx(ww[2 * n], ww[2 * n + 1]);
-    }
+    rc = make_poleset_from_contour(p->ps, d.precision, d.T, d.N, d.dt, X, d.p0, d.Xc, d.heavy_tau);
   }
-  for (int n = 0; n < d.N; ++n)
-    if (std::abs(z[n]) < 1e-12) return bail(fail(REXI_EINVAL, "pole %d is zero", n));
-  // S0 = sum w/z with compensated summation
-  {
-    cplx s = 0, comp = 0;
-    for (int n = 0; n < d.N; ++n) {
-      cplx yv = w[n] / z[n] - comp;
-      cplx t = s + yv;
-      comp = (t - s) - yv;
-      s = t;
-    }
-    p->S0 = s;
-  }
-  p->X = rexi_spectrum_bound(d.T, d.dt, d.omega, d.radius, d.phibar);
-  p->Npad = (d.N + 31) / 32 * 32;
-  p->ngroups = p->Npad / 32;
-
-  // internal order: FP64 keeps the given order; MIXED puts the light poles first and the
-  // heavy ones (largest gain |w| / dist(z, [-iX, iX]), padded to whole groups) last.
-  std::vector<int> order(d.N);
-  std::iota(order.begin(), order.end(), 0);
-  std::vector<int> heavy(d.N, p->precision == REXI_FP64 ? 1 : 0);
-  if (p->precision == REXI_MIXED) {
-    const double tau = d.heavy_tau < 0 ? 1e-3 : d.heavy_tau;
-    std::vector<double> gain(d.N);
-    int nh = 0;
-    for (int n = 0; n < d.N; ++n) {
-      const double yi = std::min(std::max(z[n].imag(), -p->X), p->X);
-      const double dist = std::abs(z[n] - cplx(0.0, yi));
-      gain[n] = std::abs(w[n]) / std::max(dist, 1e-300);
-      if (gain[n] > tau) ++nh;
-    }
-    const int nh_pad = std::min((nh + 31) / 32 * 32, d.N);
-    std::vector<int> by_gain(d.N);
-    std::iota(by_gain.begin(), by_gain.end(), 0);
-    std::stable_sort(by_gain.begin(), by_gain.end(), [&](int a, int b) { return gain[a] > gain[b]; });
-    for (int i = 0; i < nh_pad; ++i) heavy[by_gain[i]] = 1;
-    p->n_heavy = nh_pad;
-    std::stable_partition(order.begin(), order.end(), [&](int n) { return !heavy[n]; });
-  } else {
-    p->n_heavy = d.N;
-  }
-  // padding: dummy poles (w = 0) fill the light part (mixed) or the tail (FP64)
-  const int npad = p->Npad - d.N;
-  p->z_sorted.clear();
-  p->w_sorted.clear();
-  p->heavy_sorted.clear();
-  const int nlight = d.N - (p->precision == REXI_MIXED ? p->n_heavy : d.N);
-  for (int i = 0; i < (p->precision == REXI_MIXED ? nlight : d.N); ++i) {
-    p->z_sorted.push_back(z[order[i]]);
-    p->w_sorted.push_back(w[order[i]]);
-    p->heavy_sorted.push_back(heavy[order[i]]);
-  }
-  if (p->precision == REXI_MIXED) {
-    // light part padded to whole groups, then the heavy groups
-    for (int i = 0; i < npad; ++i) {
-      p->z_sorted.push_back(cplx(1.0, 0.0));
-      p->w_sorted.push_back(0.0);
-      p->heavy_sorted.push_back(0);
-    }
-    for (int i = nlight; i < d.N; ++i) {
-      p->z_sorted.push_back(z[order[i]]);
-      p->w_sorted.push_back(w[order[i]]);
-      p->heavy_sorted.push_back(1);
-    }
-    p->g_light = (nlight + npad) / 32;
-    p->g_heavy = p->n_heavy / 32;
-    if ((nlight + npad) % 32 != 0 || p->n_heavy % 32 != 0) {
-      // nh_pad == N with N not a multiple of 32: everything heavy, padding at the end
-      p->z_sorted.clear();
-      p->w_sorted.clear();
-      p->heavy_sorted.clear();
-      for (int n = 0; n < d.N; ++n) {
-        p->z_sorted.push_back(z[n]);
-        p->w_sorted.push_back(w[n]);
-        p->heavy_sorted.push_back(1);
-      }
-      for (int i = 0; i < npad; ++i) {
-        p->z_sorted.push_back(cplx(1.0, 0.0));
-        p->w_sorted.push_back(0.0);
-        p->heavy_sorted.push_back(1);
-      }
-      p->g_light = 0;
-      p->g_heavy = p->ngroups;
-      p->n_heavy = d.N;
-    }
-  } else {
-    for (int i = 0; i < npad; ++i) {
-      p->z_sorted.push_back(cplx(1.0, 0.0));
-      p->w_sorted.push_back(0.0);
-      p->heavy_sorted.push_back(1);
-    }
-  }
-
-  // ---- device tables ------------------------------------------------------------------
-  const int T = d.T;
-  std::vector<D4> tab64(p->nlm);
-  std::vector<float4> tab32(p->nlm);
-  for (int m = 0; m <= T; ++m)
-    for (int n = m; n <= T; ++n) {
-      const int idx = moff(T, m) + (n - m);
-      const double nn1 = double(n) * (n + 1);
-      const double wn = n > 0 ? 2.0 * d.omega * m / nn1 : 0.0;
-      const double cm = (n > m && n - 1 > 0) ? d.dt * 2.0 * d.omega * (n + 1.0) / n * eps_nm(n, m) : 0.0;
-      const double cp = (n < T) ? d.dt * 2.0 * d.omega * n / (n + 1.0) * eps_nm(n + 1, m) : 0.0;
-      const double q = d.dt * nn1 / (d.radius * d.radius);
-      tab64[idx] = D4{d.dt * wn, cm, cp, q};
-      tab32[idx] = make_float4((float)(d.dt * wn), (float)cm, (float)cp, (float)q);
-    }
-  std::vector<PoleD> p64(p->Npad);
-  std::vector<PoleF> p32(p->Npad);
-  const double hpb = d.dt * d.phibar;
-  for (int i = 0; i < p->Npad; ++i) {
-    const cplx zz = p->z_sorted[i], ww = p->w_sorted[i];
-    const cplx iz = 1.0 / zz, wz = ww / zz, gz = hpb / zz;
-    auto D = [](cplx c) { return make_double2(c.real(), c.imag()); };
-    auto F = [](cplx c) { return make_float2((float)c.real(), (float)c.imag()); };
-    p64[i] = PoleD{D(zz), D(ww), D(wz), D(iz), D(gz)};
-    p32[i] = PoleF{F(zz), F(ww), F(wz), F(iz), F(gz)};
-  }
-  long long& ws = p->workspace;
-  int rc;
-  if ((rc = dev_alloc(&p->d_tab64, sizeof(D4) * p->nlm, &ws))) return bail(rc);
-  if ((rc = dev_alloc(&p->d_tab32, sizeof(float4) * p->nlm, &ws))) return bail(rc);
-  if ((rc = dev_alloc(&p->d_p64, sizeof(PoleD) * p->Npad, &ws))) return bail(rc);
-  if ((rc = dev_alloc(&p->d_p32, sizeof(PoleF) * p->Npad, &ws))) return bail(rc);
-  cudaError_t e;
-  if ((e = cudaMemcpy(p->d_tab64, tab64.data(), sizeof(D4) * p->nlm, cudaMemcpyHostToDevice)) ||
-      (e = cudaMemcpy(p->d_tab32, tab32.data(), sizeof(float4) * p->nlm, cudaMemcpyHostToDevice)) ||
-      (e = cudaMemcpy(p->d_p64, p64.data(), sizeof(PoleD) * p->Npad, cudaMemcpyHostToDevice)) ||
-      (e = cudaMemcpy(p->d_p32, p32.data(), sizeof(PoleF) * p->Npad, cudaMemcpyHostToDevice)))
-    return bail(cuda_fail(e, "cudaMemcpy(tables)"));
-
-  // ---- persistent grids and scratch ----------------------------------------------------
-  const int kmax = T + 1;
-  if (p->precision == REXI_FP64) {
-    const size_t smem = fp64_smem_bytes();
-    if ((e = cudaFuncSetAttribute(k_rexi_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
-      return bail(cuda_fail(e, "cudaFuncSetAttribute(k_rexi_fp64)"));
-    int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rexi_fp64, FP64_WARPS * 32, smem)))
-      return bail(cuda_fail(e, "occupancy(k_rexi_fp64)"));
-    per_sm = std::max(1, std::min(per_sm, 2));
-    p->grid_fp64 = p->nsm * per_sm;
-    p->scratch_bytes = sizeof(D4) * (size_t)p->grid_fp64 * FP64_WARPS * kmax * 32;
-  } else {
-    const size_t hsm = heavy_smem_bytes();
-    if ((e = cudaFuncSetAttribute(k_rexi_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm)))
-      return bail(cuda_fail(e, "cudaFuncSetAttribute(k_rexi_heavy)"));
-    int per_l = 0, per_h = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_l, k_rexi_light, MIX_WARPS * 32, 0)))
-      return bail(cuda_fail(e, "occupancy(k_rexi_light)"));
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_h, k_rexi_heavy, MIX_WARPS * 32, hsm)))
-      return bail(cuda_fail(e, "occupancy(k_rexi_heavy)"));
-    p->grid_light = p->nsm * std::max(1, std::min(per_l, 4));
-    p->grid_heavy = p->nsm * std::max(1, std::min(per_h, 2));
-    const int nseg_max = (kmax + SEG - 1) / SEG;
-    p->scratch_bytes = sizeof(float4) * (size_t)p->grid_light * MIX_WARPS * nseg_max * 32 +
-                       (sizeof(float4) + sizeof(float2)) * (size_t)p->grid_heavy * MIX_WARPS * kmax * 32;
-    if ((rc = dev_alloc((char**)&p->d_rhs, mixed_rhs_bytes(p->nlm, d.max_batch), &ws))) return bail(rc);
-    std::vector<TabDF> tdf(p->nlm);
-    for (int i = 0; i < p->nlm; ++i)
-      tdf[i] = TabDF{split4(tab64[i].x, tab64[i].y), split4(tab64[i].z, tab64[i].w)};
-    std::vector<PoleDF> pdf(p->Npad);
-    for (int i = 0; i < p->Npad; ++i)
-      pdf[i] = PoleDF{split4(p64[i].z.x, p64[i].z.y), split4(p64[i].iz.x, p64[i].iz.y),
-                      split4(p64[i].gz.x, p64[i].gz.y)};
-    if ((rc = dev_alloc(&p->d_tabdf, sizeof(TabDF) * p->nlm, &ws))) return bail(rc);
-    if ((rc = dev_alloc(&p->d_pdf, sizeof(PoleDF) * p->Npad, &ws))) return bail(rc);
-    if ((e = cudaMemcpy(p->d_tabdf, tdf.data(), sizeof(TabDF) * p->nlm, cudaMemcpyHostToDevice)) ||
-        (e = cudaMemcpy(p->d_pdf, pdf.data(), sizeof(PoleDF) * p->Npad, cudaMemcpyHostToDevice)))
-      return bail(cuda_fail(e, "cudaMemcpy(double-float tables)"));
-  }
-  if ((rc = dev_alloc((char**)&p->d_scratch, p->scratch_bytes, &ws))) return bail(rc);
-
-  // partial sums: the largest B * Q over the batch sizes a call may use
-  size_t maxBQ = 0;
+  if (rc) return bail(rc);
+  rc = engine_init(p->e, d.precision, d.T, d.omega, d.radius, d.phibar, (cudaStream_t)d.stream, p->ps.Npad, 0,
+                   (size_t)p->nlm * d.max_batch);
+  if (rc) return bail(rc);
+  // largest partial-sum footprint over the batch sizes a call may use
+  size_t maxp = 0;
   for (int B = 1; B <= d.max_batch; ++B) {
-    int Ql = 0, Qh = 0;
-    if (p->precision == REXI_FP64) {
-      Qh = ranges_used(p->ngroups, choose_Q(p->ngroups, B, T, 4 * p->grid_fp64 * FP64_WARPS));
-    } else {
-      if (p->g_light) Ql = ranges_used(p->g_light, choose_Q(p->g_light, B, T, 4 * p->grid_light * MIX_WARPS));
-      if (p->g_heavy) Qh = ranges_used(p->g_heavy, choose_Q(p->g_heavy, B, T, 4 * p->grid_heavy * MIX_WARPS));
-    }
-    maxBQ = std::max(maxBQ, (size_t)B * (Ql + Qh));
+    std::vector<InstReq> req;
+    for (int b = 0; b < B; ++b) req.push_back(InstReq{&p->ps, (long long)b * 3 * p->nlm});
+    std::vector<Inst> I;
+    std::vector<Tile> Tl;
+    std::vector<long long> ec;
+    int ntl;
+    long long pe;
+    build_launch(p->e, req, I, Tl, ec, ntl, pe);
+    maxp = std::max(maxp, (size_t)pe);
   }
-  p->partial_elems = maxBQ * 3 * p->nlm;
-  if ((rc = dev_alloc(&p->d_partial, sizeof(double2) * p->partial_elems, &ws))) return bail(rc);
-  const size_t state_bytes = sizeof(double2) * 3 * (size_t)p->nlm * d.max_batch;
-  if ((rc = dev_alloc(&p->d_stage_in, state_bytes, &ws))) return bail(rc);
-  if ((rc = dev_alloc(&p->d_stage_out, state_bytes, &ws))) return bail(rc);
+  cudaFree(p->e.partial);
+  p->e.partial = nullptr;
+  p->e.partial_cap = maxp;
+  if ((rc = dev_alloc(&p->e.partial, sizeof(double2) * maxp, &p->e.workspace))) return bail(rc);
+  if ((rc = engine_upload_poles(p->e, p->ps))) return bail(rc);
+  const size_t sb = sizeof(double2) * 3 * (size_t)p->nlm * d.max_batch;
+  if ((rc = dev_alloc(&p->stage_in, sb, &p->e.workspace))) return bail(rc);
+  if ((rc = dev_alloc(&p->stage_out, sb, &p->e.workspace))) return bail(rc);
   *out = p;
   return REXI_OK;
 }
 
 extern "C" int rexi_plan_destroy(rexi_plan* p) {
   if (!p) return REXI_OK;
-  if (p->stream || p->d_tab64) cudaStreamSynchronize(p->stream);
-  cudaFree(p->d_tab64);
-  cudaFree(p->d_tab32);
-  cudaFree(p->d_p64);
-  cudaFree(p->d_p32);
-  cudaFree(p->d_partial);
-  cudaFree(p->d_scratch);
-  cudaFree(p->d_rhs);
-  cudaFree(p->d_tabdf);
-  cudaFree(p->d_pdf);
-  cudaFree(p->d_stage_in);
-  cudaFree(p->d_stage_out);
-  for (auto& kv : p->tilesets) cudaFree(kv.second.d);
-  for (auto& q : p->pending) {
-    cudaEventDestroy(q.a);
-    cudaEventDestroy(q.b);
-  }
-  for (auto ev : p->event_pool) cudaEventDestroy(ev);
+  engine_free(p->e);
+  for (auto& kv : p->launches) free_launch(kv.second);
+  cudaFree(p->stage_in);
+  cudaFree(p->stage_out);
   delete p;
   return REXI_OK;
 }
 
-extern "C" int rexi_step(rexi_plan* p, const void* U0v, void* U1v, int batch) {
-  if (!p || !U0v || !U1v) return fail(REXI_EINVAL, "rexi_step: null argument");
+static int plan_launchset(rexi_plan* p, int B, LaunchSet** out) {
+  auto it = p->launches.find(B);
+  if (it == p->launches.end()) {
+    std::vector<InstReq> req;
+    for (int b = 0; b < B; ++b) req.push_back(InstReq{&p->ps, (long long)b * 3 * p->nlm});
+    std::vector<Inst> I;
+    std::vector<Tile> Tl;
+    std::vector<long long> ec;
+    int ntl;
+    long long pe;
+    build_launch(p->e, req, I, Tl, ec, ntl, pe);
+    LaunchSet L;
+    int rc = upload_launch(L, I, Tl, ec, ntl, pe);
+    if (rc) {
+      free_launch(L);
+      return rc;
+    }
+    it = p->launches.emplace(B, L).first;
+  }
+  *out = &it->second;
+  return REXI_OK;
+}
+
+extern "C" int rexi_step(rexi_plan* p, const void* U0, void* U1, int batch) {
+  if (!p || !U0 || !U1) return fail(REXI_EINVAL, "rexi_step: null argument");
   if (batch < 1 || batch > p->d.max_batch)
     return fail(REXI_EINVAL, "rexi_step: batch %d outside [1, %d]", batch, p->d.max_batch);
-  const size_t bytes = sizeof(double2) * 3 * (size_t)p->nlm * batch;
-  const char* a0 = (const char*)U0v;
-  const char* a1 = (const char*)U1v;
-  if (a0 < a1 + bytes && a1 < a0 + bytes) return fail(REXI_EINVAL, "rexi_step: U0 and U1 overlap");
-  const double2* U0 = (const double2*)U0v;
-  double2* U1 = (double2*)U1v;
-  rexi_plan::TileSet* ts = nullptr;
-  int rc = get_tiles(p, batch, &ts);
+  if (overlaps(U0, U1, sizeof(double2) * 3 * (size_t)p->nlm * batch))
+    return fail(REXI_EINVAL, "rexi_step: U0 and U1 overlap");
+  LaunchSet* L = nullptr;
+  int rc = plan_launchset(p, batch, &L);
   if (rc) return rc;
-  if (p->precision == REXI_FP64) {
-    Fp64Args a;
-    a.U0 = U0;
-    a.partial = p->d_partial;
-    a.tab = p->d_tab64;
-    a.poles = p->d_p64;
-    a.tiles = ts->d;
-    a.scratch = (D4*)p->d_scratch;
-    a.ntiles = ts->n;
-    a.B = batch;
-    a.T = p->T;
-    a.nlm = p->nlm;
-    a.Q = ts->Q;
-    a.kmax = p->T + 1;
-    const int h = prof_begin(p, 1);
-    k_rexi_fp64<<<p->grid_fp64, FP64_WARPS * 32, fp64_smem_bytes(), p->stream>>>(a);
-    prof_end(p, h);
-  } else {
-    const long long tot = (long long)batch * p->nlm;
-    Rhs32* r32 = (Rhs32*)p->d_rhs;
-    RhsDF* rdf = (RhsDF*)((char*)p->d_rhs + mixed_rhs32_bytes(p->nlm, p->d.max_batch));
-    int h = prof_begin(p, 0);
-    k_mixed_rhs<<<(unsigned)((tot + 255) / 256), 256, 0, p->stream>>>(U0, p->d_tab64, r32, rdf,
-                                                                       batch, p->nlm);
-    prof_end(p, h);
-    MixedArgs a;
-    a.U0 = U0;
-    a.partial = p->d_partial;
-    a.tab32 = p->d_tab32;
-    a.tabdf = p->d_tabdf;
-    a.p32 = p->d_p32;
-    a.p64 = p->d_p64;
-    a.pdf = p->d_pdf;
-    a.tiles = ts->d;
-    a.rhs32 = r32;
-    a.rhsdf = rdf;
-    a.scratch = p->d_scratch;
-    a.ntiles_light = ts->n_light;
-    a.ntiles_heavy = ts->n - ts->n_light;
-    a.B = batch;
-    a.T = p->T;
-    a.nlm = p->nlm;
-    a.Q = ts->Q;
-    a.kmax = p->T + 1;
-    a.nseg_max = (p->T + 1 + SEG - 1) / SEG;
-    a.warps_light = p->grid_light * MIX_WARPS;
-    if (p->g_light) {
-      h = prof_begin(p, 2);
-      k_rexi_light<<<p->grid_light, MIX_WARPS * 32, 0, p->stream>>>(a);
-      prof_end(p, h);
-    }
-    if (p->g_heavy) {
-      h = prof_begin(p, 3);
-      k_rexi_heavy<<<p->grid_heavy, MIX_WARPS * 32, heavy_smem_bytes(), p->stream>>>(a);
-      prof_end(p, h);
-    }
-  }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "solve kernel launch");
-  const long long tot = (long long)batch * p->nlm;
-  const int hf = prof_begin(p, 4);
-  k_rexi_finalize<<<(unsigned)((tot + 255) / 256), 256, 0, p->stream>>>(
-      U0, p->d_partial, U1, batch, p->nlm, ts->Q, make_double2(p->S0.real(), p->S0.imag()),
-      p->d.dt * p->d.phibar);
-  prof_end(p, hf);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "finalize kernel launch");
-  return REXI_OK;
+  return engine_launch(p->e, *L, (const double2*)U0, (double2*)U1);
 }
 
 extern "C" int rexi_step_host(rexi_plan* p, const double* U0, double* U1, int batch) {
@@ -540,17 +644,17 @@ extern "C" int rexi_step_host(rexi_plan* p, const double* U0, double* U1, int ba
   if (batch < 1 || batch > p->d.max_batch)
     return fail(REXI_EINVAL, "rexi_step_host: batch %d outside [1, %d]", batch, p->d.max_batch);
   const size_t bytes = sizeof(double2) * 3 * (size_t)p->nlm * batch;
-  REXI_CUDA_TRY(cudaMemcpyAsync(p->d_stage_in, U0, bytes, cudaMemcpyHostToDevice, p->stream));
-  int rc = rexi_step(p, p->d_stage_in, p->d_stage_out, batch);
+  REXI_CUDA_TRY(cudaMemcpyAsync(p->stage_in, U0, bytes, cudaMemcpyHostToDevice, p->e.stream));
+  int rc = rexi_step(p, p->stage_in, p->stage_out, batch);
   if (rc) return rc;
-  REXI_CUDA_TRY(cudaMemcpyAsync(U1, p->d_stage_out, bytes, cudaMemcpyDeviceToHost, p->stream));
-  REXI_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  REXI_CUDA_TRY(cudaMemcpyAsync(U1, p->stage_out, bytes, cudaMemcpyDeviceToHost, p->e.stream));
+  REXI_CUDA_TRY(cudaStreamSynchronize(p->e.stream));
   return REXI_OK;
 }
 
 extern "C" int rexi_sync(rexi_plan* p) {
   if (!p) return fail(REXI_EINVAL, "rexi_sync: null plan");
-  REXI_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  REXI_CUDA_TRY(cudaStreamSynchronize(p->e.stream));
   REXI_CUDA_TRY(cudaGetLastError());
   return REXI_OK;
 }
@@ -558,39 +662,40 @@ extern "C" int rexi_sync(rexi_plan* p) {
 extern "C" int rexi_plan_get_info(const rexi_plan* p, rexi_plan_info* info) {
   if (!p || !info) return fail(REXI_EINVAL, "rexi_plan_get_info: null argument");
   std::memset(info, 0, sizeof(*info));
-  info->T = p->T;
-  info->N = p->N;
+  info->T = p->ps.T;
+  info->N = p->ps.N;
   info->nlm = p->nlm;
-  info->precision = p->precision;
-  info->n_heavy = p->n_heavy;
-  info->n_groups = p->ngroups;
-  info->n_tiles = p->tilesets.empty() ? 0 : p->tilesets.begin()->second.n;
-  info->q_slots = p->tilesets.empty() ? 0 : p->tilesets.begin()->second.Q;
-  info->grid_fp64 = p->grid_fp64;
-  info->grid_light = p->grid_light;
-  info->grid_heavy = p->grid_heavy;
-  info->workspace_bytes = p->workspace;
-  info->s0_re = p->S0.real();
-  info->s0_im = p->S0.imag();
-  info->X = p->X;
+  info->precision = p->e.precision;
+  info->n_heavy = p->ps.n_heavy;
+  info->n_groups = p->ps.ngroups;
+  if (!p->launches.empty()) {
+    info->n_tiles = p->launches.begin()->second.ntiles;
+    info->q_slots = (int)(p->launches.begin()->second.partial_elems / (3 * (long long)p->nlm));
+  }
+  info->grid_fp64 = p->e.grid_fp64;
+  info->grid_light = p->e.grid_light;
+  info->grid_heavy = p->e.grid_heavy;
+  info->workspace_bytes = p->e.workspace;
+  info->s0_re = p->ps.S0.real();
+  info->s0_im = p->ps.S0.imag();
+  info->X = p->ps.X;
   return REXI_OK;
 }
 
 extern "C" int rexi_plan_get_poles(const rexi_plan* p, double* z, double* w, int* heavy) {
   if (!p) return fail(REXI_EINVAL, "rexi_plan_get_poles: null plan");
   int k = 0;
-  for (int i = 0; i < p->Npad; ++i) {
-    if (std::abs(p->w_sorted[i]) == 0.0 && p->z_sorted[i] == cplx(1.0, 0.0)) continue;  // padding
-    if (k >= p->N) break;
+  for (int i = 0; i < p->ps.Npad && k < p->ps.N; ++i) {
+    if (std::abs(p->ps.w[i]) == 0.0 && p->ps.z[i] == cplx(1.0, 0.0)) continue;  // padding
     if (z) {
-      z[2 * k] = p->z_sorted[i].real();
-      z[2 * k + 1] = p->z_sorted[i].imag();
+      z[2 * k] = p->ps.z[i].real();
+      z[2 * k + 1] = p->ps.z[i].imag();
     }
     if (w) {
-      w[2 * k] = p->w_sorted[i].real();
-      w[2 * k + 1] = p->w_sorted[i].imag();
+      w[2 * k] = p->ps.w[i].real();
+      w[2 * k + 1] = p->ps.w[i].imag();
     }
-    if (heavy) heavy[k] = p->heavy_sorted[i];
+    if (heavy) heavy[k] = p->ps.heavy[i];
     ++k;
   }
   return REXI_OK;
@@ -598,29 +703,272 @@ extern "C" int rexi_plan_get_poles(const rexi_plan* p, double* z, double* w, int
 
 extern "C" int rexi_plan_set_profiling(rexi_plan* p, int enable) {
   if (!p) return fail(REXI_EINVAL, "rexi_plan_set_profiling: null plan");
-  p->profiling = enable ? 1 : 0;
+  p->e.profiling = enable ? 1 : 0;
   return REXI_OK;
 }
 
 extern "C" int rexi_plan_get_profile(rexi_plan* p, double* ms, int* launches, int reset) {
   if (!p) return fail(REXI_EINVAL, "rexi_plan_get_profile: null plan");
-  REXI_CUDA_TRY(cudaStreamSynchronize(p->stream));
-  for (auto& q : p->pending) {
-    float t = 0.f;
-    REXI_CUDA_TRY(cudaEventElapsedTime(&t, q.a, q.b));
-    p->prof_ms[q.kid] += t;
-    p->prof_n[q.kid] += 1;
-    p->event_pool.push_back(q.a);
-    p->event_pool.push_back(q.b);
+  return engine_profile(p->e, ms, launches, reset);
+}
+
+// =========================================================================================
+// Ragged plans: instances of different truncation, time step and pole count in one launch
+// =========================================================================================
+struct rexi_ragged {
+  rexi_ragged_desc d{};
+  Engine e;
+  std::map<std::tuple<int, int, double, double, double>, PoleSet> cache;
+  std::vector<const PoleSet*> cur;
+  std::vector<long long> soff;
+  long long extent = 0;  // complex elements spanned by the states in U0 / U1
+  LaunchSet L;
+  int qmul = 4;
+  // captured graph of one step for fixed (U0, U1)
+  cudaGraphExec_t gexec = nullptr;
+  const void* g_u0 = nullptr;
+  void* g_u1 = nullptr;
+};
+
+extern "C" int rexi_ragged_create(const rexi_ragged_desc* desc, rexi_ragged** out) {
+  if (!desc || !out) return fail(REXI_EINVAL, "rexi_ragged_create: null argument");
+  *out = nullptr;
+  const rexi_ragged_desc& d = *desc;
+  if (d.Tmax < 1 || d.Tmax > 1023) return fail(REXI_EINVAL, "rexi_ragged_create: Tmax must be in [1, 1023]");
+  if (d.max_inst < 1 || d.max_poles < 32 || d.max_elems < 3)
+    return fail(REXI_EINVAL, "rexi_ragged_create: need max_inst >= 1, max_poles >= 32, max_elems >= 3");
+  if (d.precision != REXI_FP64 && d.precision != REXI_MIXED)
+    return fail(REXI_EINVAL, "rexi_ragged_create: bad precision");
+  if (!(d.radius > 0) || !(d.phibar > 0) || !(d.omega >= 0))
+    return fail(REXI_EINVAL, "rexi_ragged_create: bad physical constants");
+  rexi_ragged* r = new rexi_ragged();
+  r->d = d;
+  // partial sums: at most 64 pole ranges per instance
+  const int maxq = (int)std::min<long long>(64, std::max(2, d.max_poles / 32));
+  const size_t partial_cap = (size_t)3 * d.max_elems * maxq;
+  int rc = engine_init(r->e, d.precision, d.Tmax, d.omega, d.radius, d.phibar, (cudaStream_t)d.stream, d.max_poles,
+                       partial_cap, (size_t)d.max_elems);
+  if (rc) {
+    rexi_ragged_destroy(r);
+    return rc;
   }
-  p->pending.clear();
-  for (int i = 0; i < REXI_NKERNELS; ++i) {
-    if (ms) ms[i] = p->prof_ms[i];
-    if (launches) launches[i] = p->prof_n[i];
-    if (reset) {
-      p->prof_ms[i] = 0;
-      p->prof_n[i] = 0;
+  *out = r;
+  return REXI_OK;
+}
+
+extern "C" int rexi_ragged_destroy(rexi_ragged* r) {
+  if (!r) return REXI_OK;
+  if (r->gexec) cudaGraphExecDestroy(r->gexec);
+  engine_free(r->e);
+  free_launch(r->L);
+  delete r;
+  return REXI_OK;
+}
+
+static int ragged_rebuild(rexi_ragged* r) {
+  std::vector<InstReq> req;
+  for (size_t i = 0; i < r->cur.size(); ++i) req.push_back(InstReq{r->cur[i], r->soff[i]});
+  std::vector<Inst> I;
+  std::vector<Tile> Tl;
+  std::vector<long long> ec;
+  int ntl;
+  long long pe;
+  build_launch(r->e, req, I, Tl, ec, ntl, pe, r->qmul);
+  if (pe > (long long)r->e.partial_cap) return fail(REXI_EBUSY, "rexi_ragged: partial-sum workspace exceeded");
+  return upload_launch(r->L, I, Tl, ec, ntl, pe);
+}
+
+extern "C" int rexi_ragged_set(rexi_ragged* r, int ninst, const rexi_instance* inst) {
+  if (!r || !inst || ninst < 1) return fail(REXI_EINVAL, "rexi_ragged_set: bad arguments");
+  if (ninst > r->d.max_inst)
+    return fail(REXI_EBUSY, "rexi_ragged_set: %d instances > max_inst %d", ninst, r->d.max_inst);
+  long long elems = 0;
+  for (int i = 0; i < ninst; ++i) {
+    const rexi_instance& q = inst[i];
+    if (q.T < 1 || q.T > r->d.Tmax)
+      return fail(REXI_EINVAL, "rexi_ragged_set: instance %d: T = %d outside [1, %d]", i, q.T, r->d.Tmax);
+    if (q.N < 1 || q.N > 8192 || !(q.dt > 0) || !(q.p0 > 0) || !(q.Xc > 0))
+      return fail(REXI_EINVAL, "rexi_ragged_set: instance %d: need 1 <= N <= 8192, dt, p0, Xc > 0", i);
+    elems += (long long)(q.T + 1) * (q.T + 2) / 2;
+  }
+  if (elems > r->d.max_elems)
+    return fail(REXI_EBUSY, "rexi_ragged_set: %lld coefficients > max_elems %lld", elems, r->d.max_elems);
+  if (r->gexec) {
+    cudaGraphExecDestroy(r->gexec);
+    r->gexec = nullptr;
+  }
+  // pole sets are cached by (T, N, dt, p0, Xc); the arena starts over when it overflows
+  auto ensure = [&](const rexi_instance& q, const PoleSet** out) -> int {
+    auto key = std::make_tuple(q.T, q.N, q.dt, q.p0, q.Xc);
+    auto it = r->cache.find(key);
+    if (it != r->cache.end()) {
+      *out = &it->second;
+      return REXI_OK;
+    }
+    PoleSet ps;
+    const double X = rexi_spectrum_bound(q.T, q.dt, r->d.omega, r->d.radius, r->d.phibar);
+    int rc = make_poleset_from_contour(ps, r->d.precision, q.T, q.N, q.dt, X, q.p0, q.Xc, r->d.heavy_tau);
+    if (rc) return rc;
+    if (r->e.pole_used + ps.Npad > r->e.pole_cap) return REXI_EBUSY;
+    rc = engine_upload_poles(r->e, ps);
+    if (rc) return rc;
+    it = r->cache.emplace(key, std::move(ps)).first;
+    *out = &it->second;
+    return REXI_OK;
+  };
+  std::vector<const PoleSet*> cur(ninst);
+  int rc = REXI_OK;
+  for (int i = 0; i < ninst && !rc; ++i) rc = ensure(inst[i], &cur[i]);
+  if (rc == REXI_EBUSY) {  // arena full: start over with the current pole sets only
+    r->cache.clear();
+    r->e.pole_used = 0;
+    rc = REXI_OK;
+    for (int i = 0; i < ninst && !rc; ++i) rc = ensure(inst[i], &cur[i]);
+    if (rc == REXI_EBUSY) return fail(REXI_EBUSY, "rexi_ragged_set: pole sets exceed max_poles");
+  }
+  if (rc) return rc;
+  const bool given = inst[0].soff >= 0;
+  for (int i = 0; i < ninst; ++i)
+    if ((inst[i].soff >= 0) != given)
+      return fail(REXI_EINVAL, "rexi_ragged_set: either every instance gives soff or none");
+  std::vector<long long> so(ninst);
+  long long off = 0, ext = 0;
+  for (int i = 0; i < ninst; ++i) {
+    const long long sz = 3LL * (inst[i].T + 1) * (inst[i].T + 2) / 2;
+    so[i] = given ? inst[i].soff : off;
+    off += sz;
+    ext = std::max(ext, so[i] + sz);
+  }
+  if (given) {  // states must not overlap
+    std::vector<int> ord(ninst);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) { return so[a] < so[b]; });
+    for (int k = 1; k < ninst; ++k) {
+      const int a = ord[k - 1], b = ord[k];
+      if (so[a] + 3LL * (inst[a].T + 1) * (inst[a].T + 2) / 2 > so[b])
+        return fail(REXI_EINVAL, "rexi_ragged_set: states %d and %d overlap", a, b);
     }
   }
+  r->cur = cur;
+  r->soff = so;
+  r->extent = ext;
+  return ragged_rebuild(r);
+}
+
+extern "C" int rexi_ragged_offsets(const rexi_ragged* r, long long* soff) {
+  if (!r || !soff) return fail(REXI_EINVAL, "rexi_ragged_offsets: null argument");
+  for (size_t i = 0; i < r->soff.size(); ++i) soff[i] = r->soff[i];
+  soff[r->soff.size()] = r->extent;
   return REXI_OK;
+}
+
+extern "C" int rexi_ragged_step(rexi_ragged* r, const void* U0, void* U1) {
+  if (!r || !U0 || !U1) return fail(REXI_EINVAL, "rexi_ragged_step: null argument");
+  if (r->cur.empty()) return fail(REXI_EINVAL, "rexi_ragged_step: no instances set");
+  if (overlaps(U0, U1, sizeof(double2) * (size_t)r->extent))
+    return fail(REXI_EINVAL, "rexi_ragged_step: U0 and U1 overlap");
+  if (r->gexec && U0 == r->g_u0 && U1 == r->g_u1) {
+    REXI_CUDA_TRY(cudaGraphLaunch(r->gexec, r->e.stream));
+    return REXI_OK;
+  }
+  return engine_launch(r->e, r->L, (const double2*)U0, (double2*)U1);
+}
+
+extern "C" int rexi_ragged_capture(rexi_ragged* r, const void* U0, void* U1) {
+  if (!r || !U0 || !U1) return fail(REXI_EINVAL, "rexi_ragged_capture: null argument");
+  if (r->cur.empty()) return fail(REXI_EINVAL, "rexi_ragged_capture: no instances set");
+  if (r->e.stream == nullptr) return fail(REXI_EINVAL, "rexi_ragged_capture: needs a non-default stream");
+  if (r->gexec) {
+    cudaGraphExecDestroy(r->gexec);
+    r->gexec = nullptr;
+  }
+  const int prof = r->e.profiling;
+  r->e.profiling = 0;
+  REXI_CUDA_TRY(cudaStreamBeginCapture(r->e.stream, cudaStreamCaptureModeThreadLocal));
+  int rc = engine_launch(r->e, r->L, (const double2*)U0, (double2*)U1);
+  cudaGraph_t g = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(r->e.stream, &g);
+  r->e.profiling = prof;
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+  ce = cudaGraphInstantiate(&r->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate");
+  r->g_u0 = U0;
+  r->g_u1 = U1;
+  return REXI_OK;
+}
+
+// Autotuner: times the candidate tile densities (pole ranges per (m, chain), expressed as
+// tiles per resident warp) on the current instance set and keeps the fastest.
+extern "C" int rexi_ragged_tune(rexi_ragged* r, const void* U0, void* U1, int reps, int* best_qmul,
+                                double* best_ms) {
+  if (!r || !U0 || !U1) return fail(REXI_EINVAL, "rexi_ragged_tune: null argument");
+  if (r->cur.empty()) return fail(REXI_EINVAL, "rexi_ragged_tune: no instances set");
+  if (reps < 1) reps = 3;
+  const int cand[] = {1, 2, 4, 8};
+  double best = 1e300;
+  int bq = r->qmul;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  int rc = REXI_OK;
+  for (int qm : cand) {
+    r->qmul = qm;
+    rc = ragged_rebuild(r);
+    if (rc == REXI_EBUSY) {
+      rc = REXI_OK;
+      continue;
+    }
+    if (rc) break;
+    if ((rc = engine_launch(r->e, r->L, (const double2*)U0, (double2*)U1))) break;  // warm-up
+    cudaEventRecord(a, r->e.stream);
+    for (int i = 0; i < reps && !rc; ++i) rc = engine_launch(r->e, r->L, (const double2*)U0, (double2*)U1);
+    cudaEventRecord(b, r->e.stream);
+    cudaError_t ce = cudaEventSynchronize(b);
+    if (ce != cudaSuccess) {
+      rc = cuda_fail(ce, "rexi_ragged_tune");
+      break;
+    }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    if (ms / reps < best) {
+      best = ms / reps;
+      bq = qm;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc) return rc;
+  r->qmul = bq;
+  if (r->gexec) {
+    cudaGraphExecDestroy(r->gexec);
+    r->gexec = nullptr;
+  }
+  rc = ragged_rebuild(r);
+  if (rc) return rc;
+  if (best_qmul) *best_qmul = bq;
+  if (best_ms) *best_ms = best;
+  return REXI_OK;
+}
+
+extern "C" int rexi_ragged_sync(rexi_ragged* r) {
+  if (!r) return fail(REXI_EINVAL, "rexi_ragged_sync: null plan");
+  REXI_CUDA_TRY(cudaStreamSynchronize(r->e.stream));
+  REXI_CUDA_TRY(cudaGetLastError());
+  return REXI_OK;
+}
+
+extern "C" int rexi_ragged_set_profiling(rexi_ragged* r, int enable) {
+  if (!r) return fail(REXI_EINVAL, "rexi_ragged_set_profiling: null plan");
+  r->e.profiling = enable ? 1 : 0;
+  return REXI_OK;
+}
+
+extern "C" int rexi_ragged_get_profile(rexi_ragged* r, double* ms, int* launches, int reset) {
+  if (!r) return fail(REXI_EINVAL, "rexi_ragged_get_profile: null plan");
+  return engine_profile(r->e, ms, launches, reset);
 }

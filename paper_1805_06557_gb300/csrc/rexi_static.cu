@@ -39,7 +39,9 @@ constexpr size_t OFF_POLE = al(OFF_TAB + SZ_TAB);
 constexpr size_t SZ_POLE = sizeof(PoleD) * (size_t)ST_NMAX;
 constexpr size_t OFF_TILE = al(OFF_POLE + SZ_POLE);
 constexpr size_t SZ_TILE = sizeof(Tile) * (size_t)ST_TILES;
-constexpr size_t ST_BYTES = al(OFF_TILE + SZ_TILE);
+constexpr size_t OFF_INST = al(OFF_TILE + SZ_TILE);
+constexpr size_t OFF_ECUM = al(OFF_INST + sizeof(Inst));
+constexpr size_t ST_BYTES = al(OFF_ECUM + 2 * sizeof(long long));
 
 // The scratch.  In host code this name is only a stand-in for the symbol: the device
 // address comes from cudaGetSymbolAddress (once per device, in static_setup).
@@ -72,10 +74,11 @@ __device__ __forceinline__ double eps_dev(int n, int m) {
   return sqrt((double(n) * n - double(m) * m) / (4.0 * n * n - 1.0));
 }
 
-// tables (dt w_n, cm_n, cp_n, q_n), poles, and tiles in decreasing-cost order
-__global__ void k_static_setup(D4* tab, PoleD* poles, Tile* tiles, int T, int N, int Npad,
-                               double dt, double omega, double radius, double phibar, double p0,
-                               double Xc, int Q, int per, int G) {
+// dt-free tables (w_n, cm_n, cp_n, q_n), poles scaled by 1/dt (z/dt, w/dt, w/z, dt/z,
+// Phibar dt/z), tiles in decreasing-cost order, the instance descriptor
+__global__ void k_static_setup(D4* tab, PoleD* poles, Tile* tiles, Inst* inst, long long* ecum, int T,
+                               int N, int Npad, double dt, double omega, double radius, double phibar,
+                               double p0, double Xc, int Q, int per, int G, double2 S0) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int nlm = (T + 1) * (T + 2) / 2;
   if (i < nlm) {
@@ -84,9 +87,9 @@ __global__ void k_static_setup(D4* tab, PoleD* poles, Tile* tiles, int T, int N,
     const int n = m + (i - moff(T, m));
     const double nn1 = double(n) * (n + 1);
     const double wn = n > 0 ? 2.0 * omega * m / nn1 : 0.0;
-    const double cm = (n > m && n - 1 > 0) ? dt * 2.0 * omega * (n + 1.0) / n * eps_dev(n, m) : 0.0;
-    const double cp = (n < T) ? dt * 2.0 * omega * n / (n + 1.0) * eps_dev(n + 1, m) : 0.0;
-    tab[i] = D4{dt * wn, cm, cp, dt * nn1 / (radius * radius)};
+    const double cm = (n > m && n - 1 > 0) ? 2.0 * omega * (n + 1.0) / n * eps_dev(n, m) : 0.0;
+    const double cp = 2.0 * omega * n / (n + 1.0) * eps_dev(n + 1, m);
+    tab[i] = D4{wn, cm, cp, nn1 / (radius * radius)};
   }
   if (i < Npad) {
     const double hpb = dt * phibar;
@@ -102,11 +105,26 @@ __global__ void k_static_setup(D4* tab, PoleD* poles, Tile* tiles, int T, int N,
       const double2 w = cmul(ring, make_double2(ex * ec, ex * es));
       const double zz = z.x * z.x + z.y * z.y;
       const double2 iz = make_double2(z.x / zz, -z.y / zz);
-      poles[i] = PoleD{z, w, cmul(w, iz), iz, make_double2(hpb * iz.x, hpb * iz.y)};
+      poles[i] = PoleD{make_double2(z.x / dt, z.y / dt), make_double2(w.x / dt, w.y / dt), cmul(w, iz),
+                       make_double2(dt * iz.x, dt * iz.y), make_double2(hpb * iz.x, hpb * iz.y)};
     } else {
-      poles[i] = PoleD{make_double2(1.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0),
-                       make_double2(1.0, 0.0), make_double2(hpb, 0.0)};
+      poles[i] = PoleD{make_double2(1.0 / dt, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0),
+                       make_double2(dt, 0.0), make_double2(hpb, 0.0)};
     }
+  }
+  if (i == 0) {
+    Inst I;
+    I.soff = 0;
+    I.poff = 0;
+    I.roff = 0;
+    I.T = T;
+    I.nlm = nlm;
+    I.Q = Q;
+    I.pole0 = 0;
+    I.S0 = S0;
+    *inst = I;
+    ecum[0] = 0;
+    ecum[1] = nlm;
   }
   if (i < 2 * (T + 1) * Q) {
     const int m = i / (2 * Q), r = i % (2 * Q);
@@ -118,6 +136,7 @@ __global__ void k_static_setup(D4* tab, PoleD* poles, Tile* tiles, int T, int N,
     t.ng = min(per, G - t.g0);
     t.heavy = 1;
     t.cost = (T + 1 - m) * t.ng;
+    t.inst = 0;
     tiles[i] = t;
   }
 }
@@ -169,26 +188,27 @@ extern "C" int rexi_step_fp64_static(int T, int N, double dt, double omega, doub
   D4* tab = reinterpret_cast<D4*>(base + OFF_TAB);
   PoleD* poles = reinterpret_cast<PoleD*>(base + OFF_POLE);
   Tile* tiles = reinterpret_cast<Tile*>(base + OFF_TILE);
+  Inst* inst = reinterpret_cast<Inst*>(base + OFF_INST);
+  long long* ecum = reinterpret_cast<long long*>(base + OFF_ECUM);
   double2* part = reinterpret_cast<double2*>(base + OFF_PART);
   const int nset = std::max(std::max(nlm, Npad), ntiles);
-  k_static_setup<<<(nset + 127) / 128, 128, 0, s>>>(tab, poles, tiles, T, N, Npad, dt, omega, radius,
-                                                   phibar, p0, Xc, Q, per, G);
+  k_static_setup<<<(nset + 127) / 128, 128, 0, s>>>(tab, poles, tiles, inst, ecum, T, N, Npad, dt, omega,
+                                                   radius, phibar, p0, Xc, Q, per, G,
+                                                   make_double2(S0.real(), S0.imag()));
   Fp64Args a;
   a.U0 = (const double2*)U0;
   a.partial = part;
   a.tab = tab;
   a.poles = poles;
   a.tiles = tiles;
+  a.insts = inst;
   a.scratch = reinterpret_cast<D4*>(base + OFF_SCR);
   a.ntiles = ntiles;
-  a.B = 1;
-  a.T = T;
-  a.nlm = nlm;
-  a.Q = Q;
+  a.Ttab = T;
   a.kmax = ST_KMAX;
   k_rexi_fp64<<<ST_BLOCKS, FP64_WARPS * 32, fp64_smem_bytes(), s>>>(a);
-  k_rexi_finalize<<<(nlm + 255) / 256, 256, 0, s>>>((const double2*)U0, part, (double2*)U1, 1, nlm, Q,
-                                                    make_double2(S0.real(), S0.imag()), dt * phibar);
+  k_rexi_finalize<<<(nlm + 255) / 256, 256, 0, s>>>((const double2*)U0, part, (double2*)U1, inst, ecum, 1,
+                                                    (long long)nlm, phibar);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "rexi_step_fp64_static launch");
   return REXI_OK;

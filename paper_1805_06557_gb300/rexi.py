@@ -89,6 +89,103 @@ def static_scratch_bytes():
     return int(_lib.rexi_static_scratch_bytes())
 
 
+class RaggedDesc(ctypes.Structure):
+    _fields_ = [("Tmax", ctypes.c_int), ("max_inst", ctypes.c_int), ("max_poles", ctypes.c_int),
+                ("max_elems", ctypes.c_longlong), ("omega", ctypes.c_double),
+                ("radius", ctypes.c_double), ("phibar", ctypes.c_double),
+                ("precision", ctypes.c_int), ("heavy_tau", ctypes.c_double),
+                ("stream", ctypes.c_void_p)]
+
+
+class Instance(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int), ("N", ctypes.c_int), ("dt", ctypes.c_double),
+                ("p0", ctypes.c_double), ("Xc", ctypes.c_double), ("soff", ctypes.c_longlong)]
+
+
+_lib.rexi_ragged_create.argtypes = [ctypes.POINTER(RaggedDesc), ctypes.POINTER(ctypes.c_void_p)]
+_lib.rexi_ragged_destroy.argtypes = [ctypes.c_void_p]
+_lib.rexi_ragged_set.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(Instance)]
+_lib.rexi_ragged_offsets.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)]
+_lib.rexi_ragged_step.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+_lib.rexi_ragged_capture.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+_lib.rexi_ragged_tune.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                  _ip, _dp]
+_lib.rexi_ragged_sync.argtypes = [ctypes.c_void_p]
+_lib.rexi_ragged_set_profiling.argtypes = [ctypes.c_void_p, ctypes.c_int]
+_lib.rexi_ragged_get_profile.argtypes = [ctypes.c_void_p, _dp, _ip, ctypes.c_int]
+
+
+class RaggedPlan:
+    """One REXI launch over states of different truncation, time step and pole count."""
+
+    def __init__(self, Tmax, max_inst, max_poles, max_elems, omega, radius, phibar,
+                 precision="mixed", heavy_tau=-1.0, stream=None):
+        d = RaggedDesc()
+        d.Tmax, d.max_inst, d.max_poles, d.max_elems = int(Tmax), int(max_inst), int(max_poles), int(max_elems)
+        d.omega, d.radius, d.phibar = float(omega), float(radius), float(phibar)
+        d.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
+        d.heavy_tau = float(heavy_tau)
+        d.stream = ctypes.c_void_p(_stream_handle(stream))
+        h = ctypes.c_void_p()
+        _check(_lib.rexi_ragged_create(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+        self.n = 0
+
+    def set(self, instances):
+        """instances: iterable of (T, N, dt, p0, Xc) or (T, N, dt, p0, Xc, soff); returns the
+        complex offsets of the states (and the extent as the last entry)."""
+        arr = (Instance * len(instances))()
+        for i, inst in enumerate(instances):
+            T, N, dt, p0, Xc = inst[:5]
+            arr[i].T, arr[i].N, arr[i].dt, arr[i].p0, arr[i].Xc = int(T), int(N), float(dt), float(p0), float(Xc)
+            arr[i].soff = int(inst[5]) if len(inst) > 5 else -1
+        _check(_lib.rexi_ragged_set(self._h, len(instances), arr))
+        self.n = len(instances)
+        return self.offsets()
+
+    def offsets(self):
+        o = (ctypes.c_longlong * (self.n + 1))()
+        _check(_lib.rexi_ragged_offsets(self._h, o))
+        return [int(v) for v in o]
+
+    def step(self, U0, U1):
+        _check(_lib.rexi_ragged_step(self._h, _ptr(U0), _ptr(U1)))
+        return U1
+
+    def capture(self, U0, U1):
+        _check(_lib.rexi_ragged_capture(self._h, _ptr(U0), _ptr(U1)))
+
+    def tune(self, U0, U1, reps=3):
+        q = ctypes.c_int()
+        ms = ctypes.c_double()
+        _check(_lib.rexi_ragged_tune(self._h, _ptr(U0), _ptr(U1), int(reps), ctypes.byref(q), ctypes.byref(ms)))
+        return q.value, ms.value
+
+    def sync(self):
+        _check(_lib.rexi_ragged_sync(self._h))
+
+    def set_profiling(self, enable=True):
+        _check(_lib.rexi_ragged_set_profiling(self._h, 1 if enable else 0))
+
+    def profile(self, reset=True):
+        ms = np.zeros(len(KERNEL_NAMES))
+        n = np.zeros(len(KERNEL_NAMES), dtype=np.int32)
+        _check(_lib.rexi_ragged_get_profile(self._h, ms.ctypes.data_as(_dp), n.ctypes.data_as(_ip),
+                                            1 if reset else 0))
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_NAMES)}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.rexi_ragged_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 KERNEL_NAMES = ["k_mixed_rhs", "k_rexi_fp64", "k_rexi_light", "k_rexi_heavy", "k_rexi_finalize"]
 
 
