@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--N", type=int, default=N_DEF)
     ap.add_argument("--dt", type=float, default=DT_DEF)
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the ragged-ensemble figure")
+    ap.add_argument("--serving", type=int, default=0,
+                    help="run the request-stream workload with this many requests instead")
     return ap.parse_args()
 
 
@@ -165,6 +168,82 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------------------------
+def ensemble(torch, rexi, syn, steps):
+    """Ragged ensemble: 64 states of truncation T ~ U{63..255} (seed 3), 512 poles each,
+    dt = 3600 s, one ragged launch per step replayed from a captured CUDA graph after the
+    tile-density autotuner; mixed precision, error per field against the FP64 ragged plan."""
+    import numpy as np
+    Ts = syn.ensemble_truncations(64, seed=3)
+    dt, N = 3600.0, 512
+    inst = []
+    for T in Ts:
+        X = rexi.spectrum_bound(T, dt, syn.OMEGA, syn.RADIUS, syn.PHIBAR)
+        p0, Xc = contour(X)
+        inst.append((T, N, dt, p0, Xc))
+    elems = sum((T + 1) * (T + 2) // 2 for T in Ts)
+    stream = torch.cuda.Stream()
+    out = {}
+    res = {}
+    for prec in ("mixed", "fp64"):
+        r = rexi.RaggedPlan(max(Ts), len(Ts), 64 * 512, elems, syn.OMEGA, syn.RADIUS, syn.PHIBAR,
+                            precision=prec, stream=stream)
+        off = r.set(inst)
+        U0 = np.zeros(off[-1], complex)
+        for i, T in enumerate(Ts):
+            U0[off[i]: off[i + 1]] = syn.gaussian_state(T, 100 + i).reshape(-1)
+        u0 = torch.from_numpy(U0).cuda()
+        u1 = torch.empty_like(u0)
+        torch.cuda.synchronize()
+        q, _ = r.tune(u0, u1, reps=2)
+        r.capture(u0, u1)
+        r.step(u0, u1)
+        r.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            r.step(u0, u1)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[prec] = {"steps_per_s": len(Ts) * 1e3 / ms, "ms_per_launch": ms, "tuned_tiles_per_warp": q}
+        res[prec] = (u1.cpu().numpy(), off)
+        r.close()
+    a, off = res["mixed"]
+    b, _ = res["fp64"]
+    worst = [0.0, 0.0, 0.0]
+    for i, T in enumerate(Ts):
+        x = a[off[i]: off[i + 1]].reshape(3, -1)
+        y = b[off[i]: off[i + 1]].reshape(3, -1)
+        w = np.where(np.arange(x.shape[1]) <= T, 1.0, 2.0)
+        for f in range(3):
+            e = np.sqrt(np.sum(w * np.abs(x[f] - y[f]) ** 2) / np.sum(w * np.abs(y[f]) ** 2))
+            worst[f] = max(worst[f], float(e))
+    return {"workload": "64 states, T~U{63..255} (seed 3), 512 poles, dt=3600 s, one ragged "
+                        "captured-graph launch per step", "mixed": out["mixed"], "fp64": out["fp64"],
+            "max_rel_err_mixed_vs_fp64": worst}
+
+
+def serving_run(args):
+    import torch
+    from paper_1805_06557_gb300 import serving
+    n = args.serving
+    # calibration: capacity of the batched engine with everything queued at once
+    cal = serving.make_requests(min(n, 200), seed=5, rate=1e9)
+    eng = serving.ServingEngine(Tmax=511, max_slots=64, hbm_bytes=8 << 30, max_poles=64 * 2048)
+    cstats = eng.run(cal)
+    eng.close()
+    rate = 0.8 * cstats["steps_per_s"]
+    reqs = serving.make_requests(n, seed=5, rate=rate)
+    eng = serving.ServingEngine(Tmax=511, max_slots=64, hbm_bytes=8 << 30, max_poles=64 * 2048)
+    st = eng.run(reqs)
+    eng.close()
+    base = serving.one_at_a_time(serving.make_requests(n, seed=5, rate=rate), precision="fp64")
+    line = {"metric": "served REXI steps/s and latency, Poisson stream (T 63-511, dt 600-14400 s, "
+                      "N 256-2048)", "unit": "steps/s", "requests": n, "rate_per_s": rate,
+            "calibration": cstats, "batched_mixed": st, "one_at_a_time_fp64": base}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -172,6 +251,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.serving:
+        serving_run(args)
         return
 
     import numpy as np
@@ -291,6 +373,8 @@ def main():
     e2e = {"value": B * world / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": bytes_step,
            "d2h_bytes_per_step": bytes_step, "api": "rexi_step_host (pinned host buffers)"}
 
+    ens = None if args.no_ensemble else ensemble(torch, rexi, syn, max(3, min(args.steps, 10)))
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         import multiprocessing as mp  # noqa: F401  (the oracle runs in this process)
@@ -313,6 +397,7 @@ def main():
         "speedup_vs_fp64_plain": value / world / (1e3 / statistics.mean(fp64_b1)),
         "plan": {k: info[k] for k in ("n_heavy", "n_groups", "q_slots", "grid_light", "grid_heavy")},
         "alu_peaks_tflops": {"fp64": fp64_tf, "fp32": fp32_tf},
+        "ensemble": ens,
         "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
         "gpu_launches": 4 * args.steps,
     }
