@@ -307,8 +307,9 @@ static __global__ void __launch_bounds__(MIX_WARPS * 32)
 k_rexi_heavy(MixedArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  double2* s_tile = reinterpret_cast<double2*>(smem_raw) + wib * (32 * FP64_TROW);
-  double2* s_w = reinterpret_cast<double2*>(smem_raw) + MIX_WARPS * 32 * FP64_TROW + wib * 64;
+  // transposition tile of 16 rows x 33 (double2) per warp, then the pole weights
+  double2* s_tile = reinterpret_cast<double2*>(smem_raw) + wib * (SEG * FP64_TROW);
+  double2* s_w = reinterpret_cast<double2*>(smem_raw) + MIX_WARPS * SEG * FP64_TROW + wib * 64;
   double2* s_wz = s_w + 32;
   const int gw = blockIdx.x * MIX_WARPS + wib;
   const int W = gridDim.x * MIX_WARPS;
@@ -343,6 +344,7 @@ k_rexi_heavy(MixedArgs a) {
       }
       // ---- A: FP32 forward, store (inv, y) ------------------------------------------
       float2 ct = make_float2(0.f, 0.f), y = make_float2(0.f, 0.f);
+#pragma unroll 4
       for (int k = 0; k < K; ++k) {
         const float4 tb = __ldg(a.tab32 + toff + k);
         const Rhs32 rr = rb[off + k];
@@ -365,6 +367,7 @@ k_rexi_heavy(MixedArgs a) {
       }
       // ---- A: back substitution, store x -------------------------------------------
       float2 xn = make_float2(0.f, 0.f);
+#pragma unroll 4
       for (int k = K - 1; k >= 0; --k) {
         const float4 s = S1[(size_t)k * 32 + lane];
         const float4 tb = __ldg(a.tab32 + toff + k);
@@ -378,6 +381,7 @@ k_rexi_heavy(MixedArgs a) {
       // ---- B: double-float residual and forward sweep of the correction ---------------
       float2 xm = make_float2(0.f, 0.f), x0 = S2[lane];
       float2 yc = make_float2(0.f, 0.f);
+#pragma unroll 4
       for (int k = 0; k < K; ++k) {
         const float2 xp = (k + 1 < K) ? S2[(size_t)(k + 1) * 32 + lane] : make_float2(0.f, 0.f);
         const float2 res = heavy_residual(a, pq, rbd, off, toff, k, K, c, xm, x0, xp);
@@ -391,42 +395,48 @@ k_rexi_heavy(MixedArgs a) {
         x0 = xp;
       }
       // ---- C: back substitution of the correction, FP64 weighted sums ----------------
+      // 16-row blocks: lane (r, h) sums row r over the 16 poles of half h; halves combined
+      // by a shuffle (as in the light kernel), which keeps the tile small enough for
+      // several resident blocks per SM.
       float2 dn = make_float2(0.f, 0.f);
+#pragma unroll 4
       for (int k = K - 1; k >= 0; --k) {
         const float4 s = S1[(size_t)k * 32 + lane];
         const float4 tb = __ldg(a.tab32 + toff + k);
+        const float2 x = S2[(size_t)k * 32 + lane];
         const float up = ((k & 1) == c) ? tb.z : -tb.z;
         const float2 cc = make_float2(up * s.x, up * s.y);
         const float2 dx = make_float2(s.z - fmaf(cc.x, dn.x, -cc.y * dn.y),
                                       s.w - fmaf(cc.x, dn.y, cc.y * dn.x));
         dn = dx;
-        const float2 x = S2[(size_t)k * 32 + lane];
-        s_tile[(k & 31) * FP64_TROW + lane] =
+        s_tile[(k & (SEG - 1)) * FP64_TROW + lane] =
             make_double2((double)x.x + (double)dx.x, (double)x.y + (double)dx.y);
-        if ((k & 31) == 0) {
+        if ((k & (SEG - 1)) == 0) {
           __syncwarp();
-          const int kk = k + lane;
-          if (kk < K) {
-            double2 acc = make_double2(0.0, 0.0);
-#pragma unroll 8
-            for (int p = 0; p < 32; ++p) acc = cfma(s_w[p], s_tile[lane * FP64_TROW + p], acc);
-            double2* dst = part + (((kk & 1) == c) ? 0 : nlm) + off + kk;
-            *dst = (gi == 0) ? acc : cadd(*dst, acc);
+          const int r = lane & 15, h = lane >> 4;
+          const int kk = k + r;
+          const bool valid = kk < K;
+          const bool isD = ((kk & 1) != c);
+          double2 acc = make_double2(0.0, 0.0), acc2 = make_double2(0.0, 0.0);
+          if (valid) {
+#pragma unroll 4
+            for (int p = 16 * h; p < 16 * h + 16; ++p) {
+              const double2 v = s_tile[r * FP64_TROW + p];
+              acc = cfma(s_w[p], v, acc);
+              if (isD) acc2 = cfma(s_wz[p], v, acc2);
+            }
           }
-          const int j = lane & 15, h = lane >> 4;
-          const int rowd = 2 * j + (1 - c);
-          const int kd = k + rowd;
-          double2 acc2 = make_double2(0.0, 0.0);
-          if (kd < K) {
-#pragma unroll 8
-            for (int p = 16 * h; p < 16 * h + 16; ++p)
-              acc2 = cfma(s_wz[p], s_tile[rowd * FP64_TROW + p], acc2);
-          }
+          acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
+          acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
           acc2.x += __shfl_xor_sync(0xffffffffu, acc2.x, 16);
           acc2.y += __shfl_xor_sync(0xffffffffu, acc2.y, 16);
-          if (h == 0 && kd < K) {
-            double2* dst = part + 2 * nlm + off + kd;
-            *dst = (gi == 0) ? acc2 : cadd(*dst, acc2);
+          if (h == 0 && valid) {
+            double2* dst = part + (isD ? nlm : 0) + off + kk;
+            *dst = (gi == 0) ? acc : cadd(*dst, acc);
+            if (isD) {
+              double2* dst2 = part + 2 * nlm + off + kk;
+              *dst2 = (gi == 0) ? acc2 : cadd(*dst2, acc2);
+            }
           }
           __syncwarp();
         }
@@ -436,7 +446,7 @@ k_rexi_heavy(MixedArgs a) {
 }
 
 inline size_t heavy_smem_bytes() {
-  return sizeof(double2) * (MIX_WARPS * 32 * FP64_TROW + MIX_WARPS * 64);
+  return sizeof(double2) * (MIX_WARPS * SEG * FP64_TROW + MIX_WARPS * 64);
 }
 
 }  // namespace rexi

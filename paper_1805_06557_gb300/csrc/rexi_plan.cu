@@ -160,6 +160,7 @@ struct Engine {
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
   int grid_fp64 = 0, grid_light = 0, grid_heavy = 0;
+  int max_q = 0;  // cap on pole ranges per class and instance (0: none)
   long long workspace = 0;
   // profiling
   int profiling = 0;
@@ -270,7 +271,7 @@ int engine_init(Engine& e, int precision, int Ttab, double omega, double radius,
     if ((ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_h, k_rexi_heavy, MIX_WARPS * 32, hsm)))
       return cuda_fail(ce, "occupancy(k_rexi_heavy)");
     e.grid_light = e.nsm * std::max(1, std::min(per_l, 4));
-    e.grid_heavy = e.nsm * std::max(1, std::min(per_h, 2));
+    e.grid_heavy = e.nsm * std::max(1, std::min(per_h, 5));
     e.scratch_bytes = sizeof(float4) * (size_t)e.grid_light * MIX_WARPS * e.nseg_max * 32 +
                       (sizeof(float4) + sizeof(float2)) * (size_t)e.grid_heavy * MIX_WARPS * e.kmax * 32;
     e.rhs_cap = rhs_cap;
@@ -330,6 +331,10 @@ void build_launch(const Engine& e, const std::vector<InstReq>& req, std::vector<
   } else {
     Ql_glob = (int)std::max<long long>(1, (qmul * (long long)e.grid_light * MIX_WARPS + units - 1) / units);
     Qh_glob = (int)std::max<long long>(1, (qmul * (long long)e.grid_heavy * MIX_WARPS + units - 1) / units);
+  }
+  if (e.max_q > 0) {
+    Ql_glob = std::min(Ql_glob, e.max_q);
+    Qh_glob = std::min(Qh_glob, e.max_q);
   }
   long long poff = 0, roff = 0, ec = 0;
   std::vector<Tile> light, heavy;
@@ -743,9 +748,10 @@ extern "C" int rexi_ragged_create(const rexi_ragged_desc* desc, rexi_ragged** ou
     return fail(REXI_EINVAL, "rexi_ragged_create: bad physical constants");
   rexi_ragged* r = new rexi_ragged();
   r->d = d;
-  // partial sums: at most 64 pole ranges per instance
-  const int maxq = (int)std::min<long long>(64, std::max(2, d.max_poles / 32));
-  const size_t partial_cap = (size_t)3 * d.max_elems * maxq;
+  // partial sums: at most RAGGED_MAXQ pole ranges per class and instance
+  const int RAGGED_MAXQ = 2;
+  const size_t partial_cap = (size_t)3 * d.max_elems * 2 * RAGGED_MAXQ;
+  r->e.max_q = RAGGED_MAXQ;
   int rc = engine_init(r->e, d.precision, d.Tmax, d.omega, d.radius, d.phibar, (cudaStream_t)d.stream, d.max_poles,
                        partial_cap, (size_t)d.max_elems);
   if (rc) {
