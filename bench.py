@@ -29,7 +29,28 @@ sys.path.insert(0, ROOT)
 METRIC = "REXI steps/s at T255, batched/mixed vs plain FP64 at ≤1e-8 rel err; p50/p99"
 T_DEF, N_DEF, DT_DEF, B_DEF = 255, 512, 3600.0, 16
 SAMPLE_M = list(range(0, 256, 2))      # cpu_baseline sample: every second zonal order
-REF_STEP_M = [0, 85, 170, 254]         # --impl reference: zonal orders solved per step
+
+
+def ref_step_m(T):
+    """--impl reference: the four zonal orders solved per step (spread over 0..T)."""
+    return sorted({0, T // 3, (2 * T) // 3, max(T - 1, 0)})
+
+
+def shard_seeds(rank, batch):
+    """Seeds of the states rank `rank` owns: ranks hold disjoint, independent states
+    (the units of the job are sharded, no data-path collective)."""
+    return [1000 + rank * batch + i for i in range(batch)]
+
+
+def job_rate(local_ms, batch, world, steps, dist=None, device="cpu"):
+    """Whole-job state-steps/s from each rank's timed-region length: the slowest rank's
+    time (max over ranks) bounds the job.  Returns (value, max_ms)."""
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    return batch * world * steps / (max_ms * 1e-3), max_ms
 
 
 def parse():
@@ -143,9 +164,10 @@ def run_reference(args, rank, world):
         return
     from paper_1805_06557_gb300 import synthetic as syn
     U = syn.gaussian_state(args.T, 1000)
+    ms = ref_step_m(args.T)
     times = []
     for i in range(args.warmup + args.steps):
-        rate, sec = cpu_oracle_rate(args.T, args.N, args.dt, REF_STEP_M, [U])
+        rate, sec = cpu_oracle_rate(args.T, args.N, args.dt, ms, [U])
         if i >= args.warmup:
             times.append(1.0 / rate)
     per = statistics.mean(times)
@@ -153,8 +175,8 @@ def run_reference(args, rank, world):
     cfg = workload_config(args, 1)
     cfg["precision"] = "FP64 (oracle)"
     sample = ("oracle on zonal orders %s of one T%d state per step (%d of %d coefficients), "
-              "extrapolated to the full step" % (REF_STEP_M, args.T,
-                                                 sum(args.T + 1 - m for m in REF_STEP_M),
+              "extrapolated to the full step" % (ms, args.T,
+                                                 sum(args.T + 1 - m for m in ms),
                                                  (args.T + 1) * (args.T + 2) // 2))
     line = {"metric": METRIC, "value": value, "unit": "steps/s", "impl": "reference",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -270,7 +292,7 @@ def main():
     X = rexi.spectrum_bound(T, dt, syn.OMEGA, syn.RADIUS, syn.PHIBAR)
     p0, Xc = contour(X)
     nlm = rexi.nlm(T)
-    host = np.stack([syn.gaussian_state(T, 1000 + rank * B + i) for i in range(B)])
+    host = np.stack([syn.gaussian_state(T, sd) for sd in shard_seeds(rank, B)])
     u0 = torch.from_numpy(host).cuda()
     u1 = torch.empty_like(u0)
     ref64 = torch.empty_like(u0)
@@ -312,13 +334,8 @@ def main():
     clocks = clk.stop()
     prof = mixed.profile(reset=True)
     mixed.set_profiling(False)
-    mean_ms = statistics.mean(ms)
-    tmax = torch.tensor([sum(ms)], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    value, total_ms = job_rate(sum(ms), B, world, args.steps, dist, "cuda")
     barrier()
-    total_ms = float(tmax.item())
-    value = B * world * args.steps / (total_ms * 1e-3)
 
     # ---- secondary measurements (rank-local) -------------------------------------------
     ks = max(3, min(args.steps, 10))

@@ -80,7 +80,7 @@ struct PoleF {
   float2 z, w, wz, iz, gz;
 };
 
-// One unit of work: instance, zonal order m, parity chain, a range of 32-pole groups of the
+// One unit of work: instance, zonal order m, parity chain (2 = both chains, light tiles), a range of 32-pole groups of the
 // instance's pole set, and the slot of the partial sums it owns.  Sorted by decreasing cost.
 struct Tile {
   int m, chain, g0, ng, q, heavy, cost, inst;

@@ -14,7 +14,8 @@
 //  * heavy poles (k_rexi_heavy): FP32 solve, one step of iterative refinement whose
 //    residual r - A x is evaluated in double-float arithmetic (pairs of FP32 numbers,
 //    error-free products by FMA, Knuth's two-sum), FP32 solve of the correction with the
-//    same factorisation, and weighted sums over poles in FP64.
+//    same factorisation, and weighted sums over poles in double-float arithmetic (16 poles at a
+//    time), added in FP64 across the pole halves and tiles.
 // Both kernels share the tile scheme and chain equations of the FP64 kernel.
 #pragma once
 #include "common.cuh"
@@ -23,7 +24,7 @@
 namespace rexi {
 
 constexpr int MIX_WARPS = 4;
-constexpr int SEG = 16;        // checkpoint interval and transposition block of the light path
+constexpr int SEG = 16;        // transposition block of the heavy path
 constexpr int LTROW = 33;      // padded row (float2) of the light transposition tile
 
 // ---- double-float arithmetic (value = hi + lo, |lo| <= ulp(hi)/2) --------------------
@@ -70,13 +71,34 @@ __host__ __device__ inline float4 split4(double a, double b) {
 }
 __device__ __forceinline__ dfc dfc_of(float4 v) { return dfc{df{v.x, v.y}, df{v.z, v.w}}; }
 
+// (ah, al) += (wh + wl) * (xh + xl), with the rounding error of wh * xh recovered by FMA and that
+// of the sum by two-sum.  xl is the refinement correction of xh; wl * xl is dropped, which like
+// the FP32 rounding of wh * xl is 2^-24 |xl / xh| of the product, far below the error the one
+// refinement step leaves in xh + xl.  al is left unnormalised over the 16 terms.
+__device__ __forceinline__ void df_acc(float& ah, float& al, float wh, float wl, float xh, float xl) {
+  const float p = wh * xh;
+  float e = fmaf(wh, xh, -p);
+  e = fmaf(wh, xl, fmaf(wl, xh, e));
+  const float s = ah + p;
+  const float bb = s - ah;
+  al += ((ah - (s - bb)) + (p - bb)) + e;
+  ah = s;
+}
+// complex (acc.re, acc.im) += w * v; w = (re.hi, re.lo, im.hi, im.lo), v likewise
+__device__ __forceinline__ void dfc_acc(float4& acc, const float4 w, const float4 v) {
+  df_acc(acc.x, acc.y, w.x, w.y, v.x, v.y);
+  df_acc(acc.x, acc.y, -w.z, -w.w, v.z, v.w);
+  df_acc(acc.z, acc.w, w.x, w.y, v.z, v.w);
+  df_acc(acc.z, acc.w, w.z, w.w, v.x, v.y);
+}
+
 // per-(m,n) table in double-float: (dt w, cm), (cp, q) as (hi, lo) pairs
 struct TabDF {
   float4 a, b;  // a = (hw.hi, hw.lo, cm.hi, cm.lo), b = (cp.hi, cp.lo, q.hi, q.lo)
 };
 // per-pole constants in double-float
 struct PoleDF {
-  float4 z, iz, gz;
+  float4 z, iz, gz, w, wz;
 };
 // right-hand-side pieces produced by the pre-pass for every (state, m, n)
 struct Rhs32 {
@@ -135,41 +157,53 @@ static __global__ void k_mixed_rhs(const double2* __restrict__ U0, const D4* __r
 }
 
 // ---- light kernel ------------------------------------------------------------------
+// One lane solves BOTH parity chains of its (pole, m): at element k (n = m + k) chain k & 1
+// holds the zeta row and the other chain the delta row, so the two recurrences share every
+// table and right-hand-side load and give each lane two independent dependency chains.
+constexpr int LSEG = 8;        // checkpoint interval and transposition block of the light path
+
 struct LightSmem {
-  float2 tile[SEG][LTROW];
+  float2 tz[LSEG][LTROW], td[LSEG][LTROW];  // zeta_n and delta_n of the block's rows, per pole
   float2 w[32], wz[32];
 };
 
-// one forward step of the FP32 chain recurrence for element k (n = m + k)
-__device__ __forceinline__ void light_fwd(const MixedArgs& a, const PoleF& pf, const Rhs32* rb,
-                                          int off, int toff, int k, int c, float2& ct, float2& y) {
+// Light checkpoints per warp: [segment][chain][lane] float4 (ct, y).
+__host__ __device__ inline size_t light_ckpt_f4_per_warp(int nseg_max) { return (size_t)nseg_max * 2 * 32; }
+
+// One forward step of both chains at element k: (ctz, yz) is the chain whose row k is a zeta
+// row (diagonal z - i hw, off-diagonals +cm, +cp, right-hand side bzeta), (ctd, yd) the chain
+// whose row k is a delta row (diagonal z - i hw + q Phibar/z, off-diagonals -cm, -cp,
+// right-hand side bdelta + q bPhi / z).
+__device__ __forceinline__ void light_fwd2(const MixedArgs& a, const PoleF& pf, const Rhs32* rb,
+                                           int off, int toff, int k, float2& ctz, float2& yz,
+                                           float2& ctd, float2& yd) {
   const float4 tb = __ldg(a.tab32 + toff + k);
   const Rhs32 rr = rb[off + k];
-  const bool isZ = ((k & 1) == c);
-  const float lo = isZ ? tb.y : -tb.y;
-  const float up = isZ ? tb.z : -tb.z;
-  float2 d, r;
-  if (isZ) {
-    d = make_float2(pf.z.x, pf.z.y - tb.x);
-    r = rr.bz;
-  } else {
-    d = make_float2(fmaf(tb.w, pf.gz.x, pf.z.x), fmaf(tb.w, pf.gz.y, pf.z.y - tb.x));
-    r = cfmaf(pf.iz, rr.qbp, rr.bd);
+  const float2 dz = make_float2(pf.z.x, pf.z.y - tb.x);
+  {
+    const float2 den = make_float2(fmaf(-tb.y, ctz.x, dz.x), fmaf(-tb.y, ctz.y, dz.y));
+    const float2 inv = crcpf(den);
+    ctz = make_float2(tb.z * inv.x, tb.z * inv.y);
+    yz = cmulf(make_float2(fmaf(-tb.y, yz.x, rr.bz.x), fmaf(-tb.y, yz.y, rr.bz.y)), inv);
   }
-  const float2 den = make_float2(fmaf(-lo, ct.x, d.x), fmaf(-lo, ct.y, d.y));
-  const float2 inv = crcpf(den);
-  ct = make_float2(up * inv.x, up * inv.y);
-  y = cmulf(make_float2(fmaf(-lo, y.x, r.x), fmaf(-lo, y.y, r.y)), inv);
+  {
+    const float2 dd = make_float2(fmaf(tb.w, pf.gz.x, dz.x), fmaf(tb.w, pf.gz.y, dz.y));
+    const float2 r = cfmaf(pf.iz, rr.qbp, rr.bd);
+    const float2 den = make_float2(fmaf(tb.y, ctd.x, dd.x), fmaf(tb.y, ctd.y, dd.y));
+    const float2 inv = crcpf(den);
+    ctd = make_float2(-tb.z * inv.x, -tb.z * inv.y);
+    yd = cmulf(make_float2(fmaf(tb.y, yd.x, r.x), fmaf(tb.y, yd.y, r.y)), inv);
+  }
 }
 
-static __global__ void __launch_bounds__(MIX_WARPS * 32)
+static __global__ void __launch_bounds__(MIX_WARPS * 32, 4)
 k_rexi_light(MixedArgs a) {
   __shared__ LightSmem sm[MIX_WARPS];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   LightSmem& S = sm[wib];
   const int gw = blockIdx.x * MIX_WARPS + wib;
   const int W = gridDim.x * MIX_WARPS;
-  float4* ckpt = reinterpret_cast<float4*>(a.scratch) + (size_t)gw * a.nseg_max * 32;
+  float4* ckpt = reinterpret_cast<float4*>(a.scratch) + (size_t)gw * light_ckpt_f4_per_warp(a.nseg_max);
   const int total = a.ntiles_light;
   for (int round = 0; round * W < total; ++round) {
     const int t = round * W + ((round & 1) ? (W - 1 - gw) : gw);
@@ -177,8 +211,8 @@ k_rexi_light(MixedArgs a) {
     const Tile tl = a.tiles[t];
     const Inst I = a.insts[tl.inst];
     const int T = I.T, nlm = I.nlm;
-    const int m = tl.m, c = tl.chain, K = T + 1 - m, off = moff(T, m), toff = moff(a.Ttab, m);
-    const int nseg = (K + SEG - 1) / SEG;
+    const int m = tl.m, K = T + 1 - m, off = moff(T, m), toff = moff(a.Ttab, m);
+    const int nseg = (K + LSEG - 1) / LSEG;
     const Rhs32* rb = a.rhs32 + I.roff;
     double2* part = a.partial + I.poff + (size_t)tl.q * 3 * nlm;
 
@@ -187,76 +221,109 @@ k_rexi_light(MixedArgs a) {
       __syncwarp();
       S.w[lane] = pf.w;
       S.wz[lane] = pf.wz;
-      float2 ca[SEG], ya[SEG];
-      // ---- pass 1: forward sweep with checkpoints ------------------------------------
-      float2 ct = make_float2(0.f, 0.f), y = make_float2(0.f, 0.f);
+      // ca[c][i], ya[c][i]: forward state of chain c after element i of the current segment
+      float2 ca[2][LSEG], ya[2][LSEG];
+      float2 ct[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+      float2 y[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+      // ---- pass 1: forward sweep of both chains with checkpoints ---------------------------
       for (int s = 0; s < nseg; ++s) {
 #pragma unroll
-        for (int i = 0; i < SEG; ++i) {
-          const int k = s * SEG + i;
-          if (k < K) light_fwd(a, pf, rb, off, toff, k, c, ct, y);
-          ca[i] = ct;
-          ya[i] = y;
+        for (int i = 0; i < LSEG; ++i) {
+          const int k = s * LSEG + i;
+          const int P = i & 1;  // k & 1, the segment start being even
+          if (k < K) light_fwd2(a, pf, rb, off, toff, k, ct[P], y[P], ct[1 - P], y[1 - P]);
+          ca[0][i] = ct[0];
+          ya[0][i] = y[0];
+          ca[1][i] = ct[1];
+          ya[1][i] = y[1];
         }
-        if (s + 1 < nseg) ckpt[(size_t)s * 32 + lane] = make_float4(ct.x, ct.y, y.x, y.y);
+        if (s + 1 < nseg) {
+          ckpt[((size_t)s * 2 + 0) * 32 + lane] = make_float4(ct[0].x, ct[0].y, y[0].x, y[0].y);
+          ckpt[((size_t)s * 2 + 1) * 32 + lane] = make_float4(ct[1].x, ct[1].y, y[1].x, y[1].y);
+        }
       }
-      // ---- pass 2: backward over segments, recomputing each from its checkpoint -------
-      float2 xn = make_float2(0.f, 0.f);
+      // ---- pass 2: backward over segments, recomputing each from its checkpoint -----------
+      float2 xn[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
       for (int s = nseg - 1; s >= 0; --s) {
         if (s != nseg - 1) {
-          if (s > 0) {
-            const float4 st = ckpt[(size_t)(s - 1) * 32 + lane];
-            ct = make_float2(st.x, st.y);
-            y = make_float2(st.z, st.w);
-          } else {
-            ct = make_float2(0.f, 0.f);
-            y = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            if (s > 0) {
+              const float4 st = ckpt[((size_t)(s - 1) * 2 + c) * 32 + lane];
+              ct[c] = make_float2(st.x, st.y);
+              y[c] = make_float2(st.z, st.w);
+            } else {
+              ct[c] = make_float2(0.f, 0.f);
+              y[c] = make_float2(0.f, 0.f);
+            }
           }
 #pragma unroll
-          for (int i = 0; i < SEG; ++i) {
-            light_fwd(a, pf, rb, off, toff, s * SEG + i, c, ct, y);  // full segment: k < K here
-            ca[i] = ct;
-            ya[i] = y;
+          for (int i = 0; i < LSEG; ++i) {
+            const int P = i & 1;
+            light_fwd2(a, pf, rb, off, toff, s * LSEG + i, ct[P], y[P], ct[1 - P], y[1 - P]);  // k < K
+            ca[0][i] = ct[0];
+            ya[0][i] = y[0];
+            ca[1][i] = ct[1];
+            ya[1][i] = y[1];
           }
         }
 #pragma unroll
-        for (int i = SEG - 1; i >= 0; --i) {
-          const int k = s * SEG + i;
+        for (int i = LSEG - 1; i >= 0; --i) {
+          const int k = s * LSEG + i;
           if (k < K) {
-            const float2 x = make_float2(ya[i].x - fmaf(ca[i].x, xn.x, -ca[i].y * xn.y),
-                                         ya[i].y - fmaf(ca[i].x, xn.y, ca[i].y * xn.x));
-            S.tile[i][lane] = x;
-            xn = x;
+            float2 x[2];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+              x[c] = make_float2(ya[c][i].x - fmaf(ca[c][i].x, xn[c].x, -ca[c][i].y * xn[c].y),
+                                 ya[c][i].y - fmaf(ca[c][i].x, xn[c].y, ca[c][i].y * xn[c].x));
+              xn[c] = x[c];
+            }
+            S.tz[i][lane] = x[i & 1];        // zeta_{m+k}
+            S.td[i][lane] = x[1 - (i & 1)];  // delta_{m+k}
           }
         }
         __syncwarp();
-        // block reduction: row r = lane & 15, poles [16h, 16h+16)
+        // block reduction: lane (r, h) sums row r over the 8 poles [8h, 8h + 8); the four
+        // quarters are combined by shuffles
         {
-          const int r = lane & 15, h = lane >> 4;
-          const int k = s * SEG + r;
+          const int r = lane & (LSEG - 1), h = lane >> 3;
+          const int k = s * LSEG + r;
           const bool valid = k < K;
-          const bool isD = ((k & 1) != c);
-          float2 acc = make_float2(0.f, 0.f), acc2 = make_float2(0.f, 0.f);
+          float2 az = make_float2(0.f, 0.f), ad = az, af = az;
           if (valid) {
 #pragma unroll
-            for (int p = 16 * h; p < 16 * h + 16; ++p) {
-              const float2 x = S.tile[r][p];
-              acc = cfmaf(S.w[p], x, acc);
-              if (isD) acc2 = cfmaf(S.wz[p], x, acc2);
+            for (int p = 8 * h; p < 8 * h + 8; ++p) {
+              const float2 xz = S.tz[r][p], xd = S.td[r][p];
+              const float2 wp = S.w[p];
+              az = cfmaf(wp, xz, az);
+              ad = cfmaf(wp, xd, ad);
+              af = cfmaf(S.wz[p], xd, af);
             }
           }
-          acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
-          acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
-          acc2.x += __shfl_xor_sync(0xffffffffu, acc2.x, 16);
-          acc2.y += __shfl_xor_sync(0xffffffffu, acc2.y, 16);
+#pragma unroll
+          for (int sh = 8; sh <= 16; sh <<= 1) {
+            az.x += __shfl_xor_sync(0xffffffffu, az.x, sh);
+            az.y += __shfl_xor_sync(0xffffffffu, az.y, sh);
+            ad.x += __shfl_xor_sync(0xffffffffu, ad.x, sh);
+            ad.y += __shfl_xor_sync(0xffffffffu, ad.y, sh);
+            af.x += __shfl_xor_sync(0xffffffffu, af.x, sh);
+            af.y += __shfl_xor_sync(0xffffffffu, af.y, sh);
+          }
           if (h == 0 && valid) {
-            double2* dst = part + (isD ? nlm : 0) + off + k;
-            const double2 v = make_double2((double)acc.x, (double)acc.y);
-            *dst = (gi == 0) ? v : cadd(*dst, v);
-            if (isD) {
-              double2* dst2 = part + 2 * nlm + off + k;
-              const double2 v2 = make_double2((double)acc2.x, (double)acc2.y);
-              *dst2 = (gi == 0) ? v2 : cadd(*dst2, v2);
+            double2* d0 = part + off + k;
+            double2* d1 = d0 + nlm;
+            double2* d2 = d1 + nlm;
+            const double2 vz = make_double2((double)az.x, (double)az.y);
+            const double2 vd = make_double2((double)ad.x, (double)ad.y);
+            const double2 vf = make_double2((double)af.x, (double)af.y);
+            if (gi == 0) {
+              *d0 = vz;
+              *d1 = vd;
+              *d2 = vf;
+            } else {
+              *d0 = cadd(*d0, vz);
+              *d1 = cadd(*d1, vd);
+              *d2 = cadd(*d2, vf);
             }
           }
         }
@@ -307,15 +374,16 @@ static __global__ void __launch_bounds__(MIX_WARPS * 32)
 k_rexi_heavy(MixedArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  // transposition tile of 16 rows x 33 (double2) per warp, then the pole weights
-  double2* s_tile = reinterpret_cast<double2*>(smem_raw) + wib * (SEG * FP64_TROW);
-  double2* s_w = reinterpret_cast<double2*>(smem_raw) + MIX_WARPS * SEG * FP64_TROW + wib * 64;
-  double2* s_wz = s_w + 32;
+  // transposition tile of 16 rows x 33 (float4: x and its correction, re and im) per warp,
+  // then the pole weights w and w/z in double-float
+  float4* s_tile = reinterpret_cast<float4*>(smem_raw) + wib * (SEG * FP64_TROW);
+  float4* s_w = reinterpret_cast<float4*>(smem_raw) + MIX_WARPS * SEG * FP64_TROW + wib * 64;
+  float4* s_wz = s_w + 32;
   const int gw = blockIdx.x * MIX_WARPS + wib;
   const int W = gridDim.x * MIX_WARPS;
   // heavy scratch: after the light checkpoints; per warp S1 [kmax][32] float4, S2 [kmax][32] float2
   char* base = reinterpret_cast<char*>(a.scratch) +
-               (size_t)a.warps_light * a.nseg_max * 32 * sizeof(float4) +
+               (size_t)a.warps_light * light_ckpt_f4_per_warp(a.nseg_max) * sizeof(float4) +
                (size_t)gw * a.kmax * 32 * (sizeof(float4) + sizeof(float2));
   float4* S1 = reinterpret_cast<float4*>(base);
   float2* S2 = reinterpret_cast<float2*>(base + (size_t)a.kmax * 32 * sizeof(float4));
@@ -336,12 +404,9 @@ k_rexi_heavy(MixedArgs a) {
       const int pidx = I.pole0 + (tl.g0 + gi) * 32 + lane;
       const PoleF pf = a.p32[pidx];
       const PoleDF pq = a.pdf[pidx];
-      {
-        const PoleD pd = a.p64[pidx];
-        __syncwarp();
-        s_w[lane] = pd.w;
-        s_wz[lane] = pd.wz;
-      }
+      __syncwarp();
+      s_w[lane] = pq.w;
+      s_wz[lane] = pq.wz;
       // ---- A: FP32 forward, store (inv, y) ------------------------------------------
       float2 ct = make_float2(0.f, 0.f), y = make_float2(0.f, 0.f);
 #pragma unroll 4
@@ -394,10 +459,10 @@ k_rexi_heavy(MixedArgs a) {
         xm = x0;
         x0 = xp;
       }
-      // ---- C: back substitution of the correction, FP64 weighted sums ----------------
-      // 16-row blocks: lane (r, h) sums row r over the 16 poles of half h; halves combined
-      // by a shuffle (as in the light kernel), which keeps the tile small enough for
-      // several resident blocks per SM.
+      // ---- C: back substitution of the correction, weighted sums ---------------------
+      // 16-row blocks: lane (r, h) sums row r over the 16 poles of half h in double-float
+      // (v = x + dx kept as the pair (x, dx)); the halves are converted to FP64 and combined
+      // by a shuffle, then added into the tile's FP64 partial sums.
       float2 dn = make_float2(0.f, 0.f);
 #pragma unroll 4
       for (int k = K - 1; k >= 0; --k) {
@@ -409,23 +474,24 @@ k_rexi_heavy(MixedArgs a) {
         const float2 dx = make_float2(s.z - fmaf(cc.x, dn.x, -cc.y * dn.y),
                                       s.w - fmaf(cc.x, dn.y, cc.y * dn.x));
         dn = dx;
-        s_tile[(k & (SEG - 1)) * FP64_TROW + lane] =
-            make_double2((double)x.x + (double)dx.x, (double)x.y + (double)dx.y);
+        s_tile[(k & (SEG - 1)) * FP64_TROW + lane] = make_float4(x.x, dx.x, x.y, dx.y);
         if ((k & (SEG - 1)) == 0) {
           __syncwarp();
           const int r = lane & 15, h = lane >> 4;
           const int kk = k + r;
           const bool valid = kk < K;
           const bool isD = ((kk & 1) != c);
-          double2 acc = make_double2(0.0, 0.0), acc2 = make_double2(0.0, 0.0);
+          float4 f1 = make_float4(0.f, 0.f, 0.f, 0.f), f2 = f1;
           if (valid) {
 #pragma unroll 4
             for (int p = 16 * h; p < 16 * h + 16; ++p) {
-              const double2 v = s_tile[r * FP64_TROW + p];
-              acc = cfma(s_w[p], v, acc);
-              if (isD) acc2 = cfma(s_wz[p], v, acc2);
+              const float4 v = s_tile[r * FP64_TROW + p];
+              dfc_acc(f1, s_w[p], v);
+              if (isD) dfc_acc(f2, s_wz[p], v);
             }
           }
+          double2 acc = make_double2((double)f1.x + (double)f1.y, (double)f1.z + (double)f1.w);
+          double2 acc2 = make_double2((double)f2.x + (double)f2.y, (double)f2.z + (double)f2.w);
           acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
           acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
           acc2.x += __shfl_xor_sync(0xffffffffu, acc2.x, 16);
@@ -446,7 +512,7 @@ k_rexi_heavy(MixedArgs a) {
 }
 
 inline size_t heavy_smem_bytes() {
-  return sizeof(double2) * (MIX_WARPS * SEG * FP64_TROW + MIX_WARPS * 64);
+  return sizeof(float4) * (MIX_WARPS * SEG * FP64_TROW + MIX_WARPS * 64);
 }
 
 }  // namespace rexi

@@ -218,7 +218,7 @@ int engine_init(Engine& e, int precision, int Ttab, double omega, double radius,
   e.phibar = phibar;
   e.stream = stream;
   e.kmax = Ttab + 1;
-  e.nseg_max = (e.kmax + SEG - 1) / SEG;
+  e.nseg_max = (e.kmax + LSEG - 1) / LSEG;
   if (cudaGetDevice(&e.device) != cudaSuccess) return fail(REXI_ECUDA, "no CUDA device");
   cudaDeviceGetAttribute(&e.nsm, cudaDevAttrMultiProcessorCount, e.device);
   const int nlm = (Ttab + 1) * (Ttab + 2) / 2;
@@ -272,7 +272,7 @@ int engine_init(Engine& e, int precision, int Ttab, double omega, double radius,
       return cuda_fail(ce, "occupancy(k_rexi_heavy)");
     e.grid_light = e.nsm * std::max(1, std::min(per_l, 4));
     e.grid_heavy = e.nsm * std::max(1, std::min(per_h, 5));
-    e.scratch_bytes = sizeof(float4) * (size_t)e.grid_light * MIX_WARPS * e.nseg_max * 32 +
+    e.scratch_bytes = sizeof(float4) * (size_t)e.grid_light * MIX_WARPS * light_ckpt_f4_per_warp(e.nseg_max) +
                       (sizeof(float4) + sizeof(float2)) * (size_t)e.grid_heavy * MIX_WARPS * e.kmax * 32;
     e.rhs_cap = rhs_cap;
     if ((rc = dev_alloc((char**)&e.rhs, rhs32_bytes(rhs_cap) + sizeof(RhsDF) * rhs_cap, &ws))) return rc;
@@ -297,7 +297,8 @@ int engine_upload_poles(Engine& e, PoleSet& ps) {
     auto F = [](cplx c) { return make_float2((float)c.real(), (float)c.imag()); };
     pd[i] = PoleD{D(zs), D(ws), D(wz), D(iz), D(gz)};
     pf[i] = PoleF{F(zs), F(ws), F(wz), F(iz), F(gz)};
-    pq[i] = PoleDF{split4(zs.real(), zs.imag()), split4(iz.real(), iz.imag()), split4(gz.real(), gz.imag())};
+    pq[i] = PoleDF{split4(zs.real(), zs.imag()), split4(iz.real(), iz.imag()), split4(gz.real(), gz.imag()),
+                   split4(ws.real(), ws.imag()), split4(wz.real(), wz.imag())};
   }
   cudaError_t ce = cudaMemcpy(e.p64 + e.pole_used, pd.data(), sizeof(PoleD) * ps.Npad, cudaMemcpyHostToDevice);
   if (!ce && e.p32) ce = cudaMemcpy(e.p32 + e.pole_used, pf.data(), sizeof(PoleF) * ps.Npad, cudaMemcpyHostToDevice);
@@ -322,14 +323,16 @@ void build_launch(const Engine& e, const std::vector<InstReq>& req, std::vector<
   insts.clear();
   tiles.clear();
   ecum.clear();
+  // units = tiles per pole range: (m, chain) pairs; a light tile holds both chains of its m
   long long units = 0;
   for (auto& r : req) units += 2LL * (r.ps->T + 1);
   units = std::max<long long>(units, 1);
+  const long long units_l = std::max<long long>(units / 2, 1);
   int Ql_glob = 1, Qh_glob = 1;
   if (e.precision == REXI_FP64) {
     Qh_glob = (int)std::max<long long>(1, (qmul * (long long)e.grid_fp64 * FP64_WARPS + units - 1) / units);
   } else {
-    Ql_glob = (int)std::max<long long>(1, (qmul * (long long)e.grid_light * MIX_WARPS + units - 1) / units);
+    Ql_glob = (int)std::max<long long>(1, (qmul * (long long)e.grid_light * MIX_WARPS + units_l - 1) / units_l);
     Qh_glob = (int)std::max<long long>(1, (qmul * (long long)e.grid_heavy * MIX_WARPS + units - 1) / units);
   }
   if (e.max_q > 0) {
@@ -361,11 +364,16 @@ void build_launch(const Engine& e, const std::vector<InstReq>& req, std::vector<
       int q = qbase;
       for (int g = 0; g < G; g += per, ++q) {
         const int ng = std::min(per, G - g);
-        for (int m = 0; m <= T; ++m)
+        for (int m = 0; m <= T; ++m) {
+          if (!hv && e.precision != REXI_FP64) {  // light: both chains in one tile (chain = 2)
+            out.push_back(Tile{m, 2, gbase + g, ng, q, 0, 2 * (T + 1 - m) * ng, (int)i});
+            continue;
+          }
           for (int c = 0; c < 2; ++c) {
             const int w = (hv && e.precision != REXI_FP64) ? 3 : 1;
             out.push_back(Tile{m, c, gbase + g, ng, q, hv, (T + 1 - m) * ng * w, (int)i});
           }
+        }
       }
     };
     add(0, ps.g_light, Ql, 0, 0, light);

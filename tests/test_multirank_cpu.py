@@ -1,0 +1,96 @@
+"""The N>1 form of the benchmark on CPU ranks (gloo, world size 2): every rank owns disjoint,
+independent states (the REXI step of one state needs nothing from another, so the units are
+sharded with no data-path collective), the job's time is the slowest rank's, and the
+reference arm under torchrun prints one line from rank 0 while the other ranks exit 0."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from oracle import coeffs as oc  # noqa: E402
+from oracle import rexi as orx  # noqa: E402
+from paper_1805_06557_gb300 import synthetic as syn  # noqa: E402
+
+T, N, DT, B = 7, 16, 3600.0, 2
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _step_states(seeds):
+    X = orx.spectrum_bound(T, DT, syn.OMEGA, syn.RADIUS, syn.PHIBAR)
+    p0, Xc = bench.contour(X)
+    z, w = oc.rexi_coefficients(N, p0, Xc)
+    return [orx.rexi_step(syn.gaussian_state(T, sd), T, DT, syn.OMEGA, syn.RADIUS, syn.PHIBAR, z, w)
+            for sd in seeds]
+
+
+def _rank(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    seeds = bench.shard_seeds(rank, B)
+    out = _step_states(seeds)          # this rank's units, no exchange with the other rank
+    local_ms = 100.0 + 50.0 * rank     # rank 1 is the slower one
+    value, max_ms = bench.job_rate(local_ms, B, world, 4, dist)
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((rank, seeds, [o.tolist() for o in out], value, max_ms))
+
+
+def test_two_ranks_shard_states_and_take_max_time():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=240) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    res.sort()
+    seeds = [s for r in res for s in r[1]]
+    assert len(set(seeds)) == 2 * B                   # disjoint shards
+    assert seeds == bench.shard_seeds(0, 2 * B)       # together: the job's states
+    whole = _step_states(seeds)                       # one process over the whole job
+    got = [np.array(o) for r in res for o in r[2]]
+    for a, b in zip(got, whole):
+        assert np.array_equal(a, b)
+    for r in res:
+        assert r[4] == 150.0                          # max over ranks
+        assert abs(r[3] - B * 2 * 4 / 0.150) < 1e-9
+
+
+def test_reference_arm_under_torchrun_rank0_only():
+    port = _free_port()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0", "--T", "15",
+           "--N", "32"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle"
+    assert d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_ref_step_m_within_truncation():
+    for t in (1, 2, 15, 63, 255, 511):
+        ms = bench.ref_step_m(t)
+        assert ms[0] == 0 and all(0 <= m <= t for m in ms)
