@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--dt", type=float, default=DT_DEF)
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the ragged-ensemble figure")
+    ap.add_argument("--no-sh", action="store_true",
+                    help="skip the SH-transform and nonlinear SWE-step figures")
     ap.add_argument("--serving", type=int, default=0,
                     help="run the request-stream workload with this many requests instead")
     return ap.parse_args()
@@ -245,6 +247,159 @@ def ensemble(torch, rexi, syn, steps):
             "max_rel_err_mixed_vs_fp64": worst}
 
 
+def _rel_fields(a, b, T):
+    """Per-field relative L2 (m > 0 weighted by 2) of spectral states [3][nlm]."""
+    import numpy as np
+    nlm = (T + 1) * (T + 2) // 2
+    wts = np.where(np.arange(nlm) <= T, 1.0, 2.0)
+    out = []
+    for f in range(3):
+        den = np.sqrt(np.sum(wts * np.abs(b[f]) ** 2))
+        out.append(float(np.sqrt(np.sum(wts * np.abs(a[f] - b[f]) ** 2)) / den) if den > 0 else 0.0)
+    return out
+
+
+def sh_transforms(torch, rexi, T=511, nlat=768, nlon=1536, nf=2, reps=5):
+    """Synthesis and analysis of nf scalar fields and of one vector field (psi/chi -> U, V;
+    A, B -> div, curl) at T511 on the 768 x 1536 Gauss grid in every Legendre precision.
+    Per-stage device times from the plan's event profile; the roofline of the Legendre
+    contraction is HBM-bound on its table (algorithmic bytes: the nlat/2 x nlm table read
+    once per transform -- P for scalar transforms, P and H for vector transforms -- in the
+    stored element type, plus the spectral and Fourier operands), of the FFT on its grid and
+    Fourier arrays."""
+    import numpy as np
+    from paper_1805_06557_gb300 import synthetic as syn
+    hbm = _hbm_peak()
+    nh, nlm = nlat // 2, (T + 1) * (T + 2) // 2
+    rng = np.random.default_rng(4)
+    n = np.concatenate([np.arange(m, T + 1) for m in range(T + 1)]).astype(float)
+    amp = np.maximum(n, 1.0) ** -1.5
+    c = (rng.standard_normal((nf, nlm)) + 1j * rng.standard_normal((nf, nlm))) * amp
+    c[:, :T + 1] = c[:, :T + 1].real
+    spec = torch.from_numpy(c).cuda()
+    grid = torch.empty(nf, nlat, nlon, dtype=torch.float64, device="cuda")
+    back = torch.empty_like(spec)
+    U = torch.empty(1, nlat, nlon, dtype=torch.float64, device="cuda")
+    V = torch.empty_like(U)
+    dv = torch.empty(1, nlm, dtype=torch.complex128, device="cuda")
+    cu = torch.empty_like(dv)
+    out = {"workload": "T%d, %d x %d Gauss grid, %d scalar fields + 1 vector field, n^-1.5 "
+                       "spectra (seed 4)" % (T, nlat, nlon, nf), "hbm_peak_gbs": hbm}
+    ref = {}
+    for prec in ("fp64", "tf32", "bf16"):
+        p = rexi.ShPlan(T, nlat, nlon, syn.RADIUS, prec, max_fields=nf)
+        eb = {"fp64": 8, "tf32": 4, "bf16": 2}[prec]
+        res = {}
+        for kind in ("synthesis", "analysis", "synthesis_uv", "analysis_divcurl"):
+            def call():
+                if kind == "synthesis":
+                    p.synthesis(spec, grid, nf)
+                elif kind == "analysis":
+                    p.analysis(grid, back, nf)
+                elif kind == "synthesis_uv":
+                    p.synthesis_uv(spec[:1], spec[1:2], U, V, 1)
+                else:
+                    p.analysis_divcurl(grid[:1], grid[1:2], dv, cu, 1)
+            for _ in range(2):
+                call()
+            p.set_profiling(True)
+            p.profile(reset=True)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                call()
+            e1.record()
+            torch.cuda.synchronize()
+            prof = p.profile(reset=True)
+            p.set_profiling(False)
+            total = e0.elapsed_time(e1) / reps
+            vec = kind in ("synthesis_uv", "analysis_divcurl")
+            ntab = 2 if vec else 1        # P, or P and H
+            narr = 2 if vec else nf       # spectral arrays = Fourier arrays = grids
+            leg_ms = sum(prof[k][0] for k in ("legendre_fp64", "tc_pack", "tc_gemm", "tc_epilogue")) / reps
+            gemm_ms = (prof["legendre_fp64"][0] if prec == "fp64" else prof["tc_gemm"][0]) / reps
+            tab_bytes = ntab * nh * nlm * eb
+            leg_bytes = tab_bytes + narr * (nlm + (T + 1) * nlat) * 16
+            fft_ms = prof["fft"][0] / reps
+            fft_bytes = narr * (nlat * nlon * 8 + nlat * (T + 1) * 16)
+            r = {"ms": total, "stage_ms": {k: v[0] / reps for k, v in prof.items() if v[1]},
+                 "legendre_ms": leg_ms,
+                 "legendre_roofline": {"bound": "hbm", "kernel": "k_leg_*" if prec == "fp64" else "k_tc_gemm",
+                                       "algorithmic_bytes": leg_bytes, "achieved_gbs": leg_bytes / (gemm_ms * 1e6),
+                                       "frac": leg_bytes / (gemm_ms * 1e6) / hbm,
+                                       "tflops": 4.0 * nh * nlm * narr * ntab / (gemm_ms * 1e9)},
+                 "fft_roofline": {"bound": "hbm", "algorithmic_bytes": fft_bytes,
+                                  "achieved_gbs": fft_bytes / (fft_ms * 1e6) if fft_ms > 0 else None,
+                                  "frac": fft_bytes / (fft_ms * 1e6) / hbm if fft_ms > 0 else None}}
+            res[kind] = r
+        p.check()
+        g, b = grid.cpu().numpy(), back.cpu().numpy()
+        if prec == "fp64":
+            ref = {"grid": g, "back": b}
+            res["rel_err_synthesis_vs_fp64"] = 0.0
+        else:
+            res["rel_err_synthesis_vs_fp64"] = float(np.linalg.norm(g - ref["grid"]) / np.linalg.norm(ref["grid"]))
+            res["rel_err_analysis_vs_fp64"] = float(np.linalg.norm(b - ref["back"]) / np.linalg.norm(ref["back"]))
+        out[prec] = res
+        p.close()
+    return out
+
+
+def swe_steps(torch, rexi, configs):
+    """Nonlinear SWE steps (Strang ver1: N by RK2 midpoint for dt/2, REXI L for dt, N for
+    dt/2) on balanced n^-3 states; steps/s, per-stage device times, and the final state's
+    per-field error against the all-FP64 plan after the same steps."""
+    import numpy as np
+    from paper_1805_06557_gb300 import synthetic as syn
+    out = []
+    for (T, nlat, nlon, N, dt, nsteps, variants) in configs:
+        X = rexi.spectrum_bound(T, dt, syn.OMEGA, syn.RADIUS, syn.PHIBAR)
+        p0, Xc = contour(X)
+        U0 = syn.balanced_state(T, 2 if T == 127 else 4)
+        ref = None
+        cfg = {"workload": "nonlinear SWE, T%d on %d x %d Gauss grid, %d poles, dt=%g s, %d steps, "
+                           "balanced n^-3 state (20 m/s rms)" % (T, nlat, nlon, N, dt, nsteps), "variants": {}}
+        for rprec, sprec in variants:
+            p = rexi.SwePlan(T, nlat, nlon, dt, syn.OMEGA, syn.RADIUS, syn.PHIBAR, N, p0, Xc,
+                             rexi_precision=rprec, sh_precision=sprec)
+            u = torch.from_numpy(U0).cuda().contiguous()
+            w = u.clone()
+            p.step(w, 1)                                   # warm-up
+            u2 = u.clone()
+            p.set_profiling(True)
+            p.profile(reset=True)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            p.step(u2, nsteps)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            prof = p.profile(reset=True)
+            p.set_profiling(False)
+            res = u2.cpu().numpy()
+            key = "rexi_%s+sh_%s" % (rprec, sprec)
+            v = {"steps_per_s": nsteps / (ms * 1e-3), "ms_per_step": ms / nsteps,
+                 "stage_ms_per_step": {k: val[0] / nsteps for k, val in prof.items()}}
+            if ref is None:
+                ref = res
+            else:
+                v["rel_err_vs_fp64_after_steps"] = _rel_fields(res, ref, T)
+            cfg["variants"][key] = v
+            p.close()
+        out.append(cfg)
+    return out
+
+
+def _hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
 def serving_run(args):
     import torch
     from paper_1805_06557_gb300 import serving
@@ -391,6 +546,13 @@ def main():
            "d2h_bytes_per_step": bytes_step, "api": "rexi_step_host (pinned host buffers)"}
 
     ens = None if args.no_ensemble else ensemble(torch, rexi, syn, max(3, min(args.steps, 10)))
+    sh = swe = None
+    if not args.no_sh:
+        sh = sh_transforms(torch, rexi)
+        swe = swe_steps(torch, rexi, [
+            (127, 192, 384, 512, 1800.0, 48, [("fp64", "fp64"), ("mixed", "fp64"), ("mixed", "tf32")]),
+            (511, 768, 1536, 2048, 7200.0, 4, [("fp64", "fp64"), ("mixed", "fp64"), ("mixed", "tf32"),
+                                                ("mixed", "bf16")])])
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -414,7 +576,7 @@ def main():
         "speedup_vs_fp64_plain": value / world / (1e3 / statistics.mean(fp64_b1)),
         "plan": {k: info[k] for k in ("n_heavy", "n_groups", "q_slots", "grid_light", "grid_heavy")},
         "alu_peaks_tflops": {"fp64": fp64_tf, "fp32": fp32_tf},
-        "ensemble": ens,
+        "ensemble": ens, "sh_transforms": sh, "swe_step": swe,
         "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
         "gpu_launches": 4 * args.steps,
     }

@@ -69,6 +69,20 @@ int sh_analysis_divcurl(sh_plan* plan, const void* A, const void* B, void* div, 
  * invalid), REXI_ECUDA on a CUDA error, REXI_OK otherwise. */
 int sh_plan_check(sh_plan* plan);
 
+/*
+ * Per-stage timing.  When enabled, every transform records a CUDA event pair on the plan
+ * stream around each kernel it launches; sh_plan_get_profile synchronises the stream and
+ * returns, per stage, the total milliseconds (ms[k]) and the number of launches
+ * (launches[k]) since the last reset (reset = 1 clears them after reading).  Stages:
+ * 0 FP64 Legendre contraction (SH_FP64), 1 operand packing for the tensor cores,
+ * 2 tcgen05 Legendre GEMM, 3 tensor-core epilogue (parity combination in FP64),
+ * 4 longitude FFT.  Arrays hold SH_NSTAGES entries; either may be NULL.  Disabled by
+ * default.  Errors: REXI_EINVAL, REXI_ECUDA.
+ */
+#define SH_NSTAGES 5
+int sh_plan_set_profiling(sh_plan* plan, int enable);
+int sh_plan_get_profile(sh_plan* plan, double* ms, int* launches, int reset);
+
 #ifdef __cplusplus
 }
 #endif

@@ -46,6 +46,18 @@ int swe_step(swe_plan* plan, void* state, int nsteps);
 /* tendency = N(state) (device [3][nlm] complex128 each; no aliasing). */
 int swe_nonlinear(swe_plan* plan, const void* state, void* tendency);
 
+/*
+ * Per-stage timing of swe_step / swe_nonlinear (CUDA events on the plan stream, off by
+ * default; see rexi_plan_get_profile and sh_plan_get_profile).  Stages: 0 REXI linear step
+ * kernels, 1 Legendre contractions (FP64 or tensor-core, with operand packing and
+ * epilogue), 2 longitude FFTs, 3 grid products and spectral assembly of N(U).
+ * swe_plan_get_profile synchronises the stream and returns total ms and launches per stage
+ * since the last reset (reset = 1 clears them).  Errors: REXI_EINVAL, REXI_ECUDA.
+ */
+#define SWE_NSTAGES 4
+int swe_plan_set_profiling(swe_plan* plan, int enable);
+int swe_plan_get_profile(swe_plan* plan, double* ms, int* launches, int reset);
+
 #ifdef __cplusplus
 }
 #endif

@@ -436,6 +436,7 @@ struct sh_plan {
   double2* d_F = nullptr;   // Fourier workspace [2 * max_fields][T+1][nlat]
   FftPlan fp{};
   TcLegendre* tc = nullptr;  // tensor-core Legendre state (SH_TF32 / SH_BF16)
+  StageProf prof;            // per-stage event timing (sh_plan_set_profiling)
 };
 
 static size_t fft_smem(const sh_plan* p) { return sizeof(double2) * 2 * (size_t)p->d.nlon; }
@@ -456,6 +457,7 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
   p->nh = d.nlat / 2;
   p->nlm = (d.T + 1) * (d.T + 2) / 2;
   p->stream = (cudaStream_t)d.stream;
+  p->prof.stream = p->stream;
   auto bail = [&](int code) {
     sh_plan_destroy(p);
     return code;
@@ -493,6 +495,7 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
     int rc = tc_legendre_create(&p->tc, p->d_P, p->d_H, p->d_w, p->d_wq, d.T, d.nlat, d.max_fields,
                                 d.precision == SH_BF16, p->stream);
     if (rc) return bail(rc);
+    tc_legendre_set_prof(p->tc, &p->prof);
   }
   if ((e = cudaStreamSynchronize(p->stream))) return bail(cuda_fail(e, "sh_plan_create: table kernel"));
   *out = p;
@@ -510,6 +513,7 @@ extern "C" int sh_plan_destroy(sh_plan* p) {
   cudaFree(p->d_tw);
   cudaFree(p->d_F);
   tc_legendre_destroy(p->tc);
+  p->prof.release();
   delete p;
   return REXI_OK;
 }
@@ -535,11 +539,19 @@ static double2* fslot(sh_plan* p, int s) {
 }
 
 static int launch_fft_synth(sh_plan* p, const double2* F, double* grid, int nf) {
-  k_fft_synth<<<dim3(p->d.nlat / 2, nf), FTH, fft_smem(p), p->stream>>>(F, grid, p->fp, p->d_tw, p->d.T, p->d.nlat);
+  {
+    const int ph = p->prof.begin(4);
+    k_fft_synth<<<dim3(p->d.nlat / 2, nf), FTH, fft_smem(p), p->stream>>>(F, grid, p->fp, p->d_tw, p->d.T, p->d.nlat);
+    p->prof.end(ph);
+  }
   return REXI_OK;
 }
 static int launch_fft_anal(sh_plan* p, const double* grid, double2* F, int nf) {
-  k_fft_anal<<<dim3(p->d.nlat / 2, nf), FTH, fft_smem(p), p->stream>>>(grid, F, p->fp, p->d_tw, p->d.T, p->d.nlat);
+  {
+    const int ph = p->prof.begin(4);
+    k_fft_anal<<<dim3(p->d.nlat / 2, nf), FTH, fft_smem(p), p->stream>>>(grid, F, p->fp, p->d_tw, p->d.T, p->d.nlat);
+    p->prof.end(ph);
+  }
   return REXI_OK;
 }
 
@@ -551,8 +563,12 @@ extern "C" int sh_synthesis(sh_plan* p, const void* spec, void* grid, int nf) {
     rc = tc_leg_synth(p->tc, (const double2*)spec, F, nf, p->stream);
     if (rc) return rc;
   } else {
-    k_leg_synth<<<dim3(p->d.T + 1, nf, (p->nh + LTH - 1) / LTH), LTH, 0, p->stream>>>(
-        p->d_P, (const double2*)spec, F, p->d.T, p->d.nlat, p->nlm);
+    {
+      const int ph = p->prof.begin(0);
+      k_leg_synth<<<dim3(p->d.T + 1, nf, (p->nh + LTH - 1) / LTH), LTH, 0, p->stream>>>(
+          p->d_P, (const double2*)spec, F, p->d.T, p->d.nlat, p->nlm);
+      p->prof.end(ph);
+    }
   }
   launch_fft_synth(p, F, (double*)grid, nf);
   cudaError_t e = cudaGetLastError();
@@ -568,8 +584,12 @@ extern "C" int sh_analysis(sh_plan* p, const void* grid, void* spec, int nf) {
     rc = tc_leg_anal(p->tc, F, (double2*)spec, nf, p->stream);
     if (rc) return rc;
   } else {
-    k_leg_anal<<<dim3(p->d.T + 1, nf), ATH, sizeof(double2) * 2 * p->nh, p->stream>>>(
-        p->d_P, p->d_w, F, (double2*)spec, p->d.T, p->d.nlat, p->nlm);
+    {
+      const int ph = p->prof.begin(0);
+      k_leg_anal<<<dim3(p->d.T + 1, nf), ATH, sizeof(double2) * 2 * p->nh, p->stream>>>(
+          p->d_P, p->d_w, F, (double2*)spec, p->d.T, p->d.nlat, p->nlm);
+      p->prof.end(ph);
+    }
   }
   cudaError_t e = cudaGetLastError();
   return e ? cuda_fail(e, "sh_analysis") : REXI_OK;
@@ -585,9 +605,13 @@ extern "C" int sh_synthesis_uv(sh_plan* p, const void* psi, const void* chi, voi
     rc = tc_leg_synth_uv(p->tc, (const double2*)psi, (const double2*)chi, FU, FV, nf, 1.0 / p->d.radius, p->stream);
     if (rc) return rc;
   } else {
-    k_leg_synth_uv<<<dim3(p->d.T + 1, nf, (p->nh + LTH - 1) / LTH), LTH, 0, p->stream>>>(
-        p->d_P, p->d_H, (const double2*)psi, (const double2*)chi, FU, FV, p->d.T, p->d.nlat, p->nlm,
-        1.0 / p->d.radius);
+    {
+      const int ph = p->prof.begin(0);
+      k_leg_synth_uv<<<dim3(p->d.T + 1, nf, (p->nh + LTH - 1) / LTH), LTH, 0, p->stream>>>(
+          p->d_P, p->d_H, (const double2*)psi, (const double2*)chi, FU, FV, p->d.T, p->d.nlat, p->nlm,
+          1.0 / p->d.radius);
+      p->prof.end(ph);
+    }
   }
   launch_fft_synth(p, FU, (double*)U, nf);
   launch_fft_synth(p, FV, (double*)V, nf);
@@ -607,9 +631,13 @@ extern "C" int sh_analysis_divcurl(sh_plan* p, const void* A, const void* B, voi
     rc = tc_leg_anal_divcurl(p->tc, FA, FB, (double2*)dv, (double2*)cu, nf, 1.0 / p->d.radius, p->stream);
     if (rc) return rc;
   } else {
-    k_leg_anal_divcurl<<<dim3(p->d.T + 1, nf), ATH, sizeof(double2) * 4 * p->nh, p->stream>>>(
-        p->d_P, p->d_H, p->d_wq, FA, FB, (double2*)dv, (double2*)cu, p->d.T, p->d.nlat, p->nlm,
-        1.0 / p->d.radius);
+    {
+      const int ph = p->prof.begin(0);
+      k_leg_anal_divcurl<<<dim3(p->d.T + 1, nf), ATH, sizeof(double2) * 4 * p->nh, p->stream>>>(
+          p->d_P, p->d_H, p->d_wq, FA, FB, (double2*)dv, (double2*)cu, p->d.T, p->d.nlat, p->nlm,
+          1.0 / p->d.radius);
+      p->prof.end(ph);
+    }
   }
   cudaError_t e = cudaGetLastError();
   return e ? cuda_fail(e, "sh_analysis_divcurl") : REXI_OK;
@@ -623,5 +651,25 @@ extern "C" int sh_plan_check(sh_plan* p) {
   int rc = tc_legendre_error(p->tc, &flag);
   if (rc) return rc;
   if (flag) return fail(REXI_ETIMEOUT, "sh_plan_check: a tensor-core wait timed out (code %d)", flag);
+  return REXI_OK;
+}
+
+extern "C" int sh_plan_set_profiling(sh_plan* p, int enable) {
+  if (!p) return fail(REXI_EINVAL, "sh_plan_set_profiling: null plan");
+  p->prof.on = enable != 0;
+  return REXI_OK;
+}
+
+extern "C" int sh_plan_get_profile(sh_plan* p, double* ms, int* launches, int reset) {
+  if (!p) return fail(REXI_EINVAL, "sh_plan_get_profile: null plan");
+  REXI_CUDA_TRY(p->prof.collect());
+  for (int k = 0; k < StageProf::NSTAGE; ++k) {
+    if (ms) ms[k] = p->prof.ms[k];
+    if (launches) launches[k] = p->prof.n[k];
+    if (reset) {
+      p->prof.ms[k] = 0.0;
+      p->prof.n[k] = 0;
+    }
+  }
   return REXI_OK;
 }

@@ -339,6 +339,7 @@ struct TcLegendre {
   int *dmap_s = nullptr, *dmap_a = nullptr;   // [(m*2+par)*ntile+tile][tab] -> D offset or -1
   int *boff_s = nullptr, *kpad_s = nullptr, *boff_a = nullptr;
   size_t smem_s = 0, smem_a = 0;
+  StageProf* prof = nullptr;
 };
 
 static int tc_fail(const char* what, cudaError_t e) { return cuda_fail(e, what); }
@@ -523,7 +524,11 @@ static int gemm(TcLegendre* t, bool synth, bool both_tabs, int ncols, cudaStream
   g.ncols = ncols;
   g.bf16 = t->bf16;
   g.err = t->err;
-  k_tc_gemm<<<g.njobs, 128, synth ? t->smem_s : t->smem_a, s>>>(g);
+  {
+    const int ph = t->prof ? t->prof->begin(2) : -1;
+    k_tc_gemm<<<g.njobs, 128, synth ? t->smem_s : t->smem_a, s>>>(g);
+    if (t->prof) t->prof->end(ph);
+  }
   cudaError_t e = cudaGetLastError();
   return e ? cuda_fail(e, "k_tc_gemm launch") : REXI_OK;
 }
@@ -535,48 +540,84 @@ static int ncols_for(int nf, int cpf) {
 
 int tc_leg_synth(TcLegendre* t, const double2* spec, double2* F, int nf, cudaStream_t s) {
   const int nc = ncols_for(nf, 2);
-  k_tc_bsynth<<<dim3(t->T + 1, 2), 256, 0, s>>>(spec, spec, t->B, t->boff_s, t->kpad_s, t->T, t->nlm, nf, 2, nc,
-                                                t->bf16);
+  {
+    const int ph = t->prof ? t->prof->begin(1) : -1;
+    k_tc_bsynth<<<dim3(t->T + 1, 2), 256, 0, s>>>(spec, spec, t->B, t->boff_s, t->kpad_s, t->T, t->nlm, nf, 2, nc,
+                                                  t->bf16);
+    if (t->prof) t->prof->end(ph);
+  }
   int rc = gemm(t, true, false, nc, s);
   if (rc) return rc;
-  k_tc_esynth<<<dim3((t->nh + 127) / 128, t->T + 1), 128, 0, s>>>(t->D, t->dmap_s, F, F, t->T, t->nlat, nf, 2, nc,
-                                                                   t->ntile_s, 0, 0.0);
+  {
+    const int ph = t->prof ? t->prof->begin(3) : -1;
+    k_tc_esynth<<<dim3((t->nh + 127) / 128, t->T + 1), 128, 0, s>>>(t->D, t->dmap_s, F, F, t->T, t->nlat, nf, 2, nc,
+                                                                     t->ntile_s, 0, 0.0);
+    if (t->prof) t->prof->end(ph);
+  }
   return REXI_OK;
 }
 
 int tc_leg_synth_uv(TcLegendre* t, const double2* psi, const double2* chi, double2* FU, double2* FV, int nf,
                     double inv_a, cudaStream_t s) {
   const int nc = ncols_for(nf, 4);
-  k_tc_bsynth<<<dim3(t->T + 1, 2), 256, 0, s>>>(psi, chi, t->B, t->boff_s, t->kpad_s, t->T, t->nlm, nf, 4, nc,
-                                                t->bf16);
+  {
+    const int ph = t->prof ? t->prof->begin(1) : -1;
+    k_tc_bsynth<<<dim3(t->T + 1, 2), 256, 0, s>>>(psi, chi, t->B, t->boff_s, t->kpad_s, t->T, t->nlm, nf, 4, nc,
+                                                  t->bf16);
+    if (t->prof) t->prof->end(ph);
+  }
   int rc = gemm(t, true, true, nc, s);
   if (rc) return rc;
-  k_tc_esynth<<<dim3((t->nh + 127) / 128, t->T + 1), 128, 0, s>>>(t->D, t->dmap_s, FU, FV, t->T, t->nlat, nf, 4, nc,
-                                                                   t->ntile_s, 1, inv_a);
+  {
+    const int ph = t->prof ? t->prof->begin(3) : -1;
+    k_tc_esynth<<<dim3((t->nh + 127) / 128, t->T + 1), 128, 0, s>>>(t->D, t->dmap_s, FU, FV, t->T, t->nlat, nf, 4, nc,
+                                                                     t->ntile_s, 1, inv_a);
+    if (t->prof) t->prof->end(ph);
+  }
   return REXI_OK;
 }
 
 int tc_leg_anal(TcLegendre* t, const double2* F, double2* spec, int nf, cudaStream_t s) {
   const int nc = ncols_for(nf, 2);
-  k_tc_banal<<<dim3(t->T + 1, 2), 256, 0, s>>>(F, F, t->w, t->B, t->boff_a, t->kpad_a, t->T, t->nlat, nf, 2, nc,
-                                               t->bf16);
+  {
+    const int ph = t->prof ? t->prof->begin(1) : -1;
+    k_tc_banal<<<dim3(t->T + 1, 2), 256, 0, s>>>(F, F, t->w, t->B, t->boff_a, t->kpad_a, t->T, t->nlat, nf, 2, nc,
+                                                 t->bf16);
+    if (t->prof) t->prof->end(ph);
+  }
   int rc = gemm(t, false, false, nc, s);
   if (rc) return rc;
-  k_tc_eanal<<<dim3((t->T + 1 + 127) / 128, t->T + 1), 128, 0, s>>>(t->D, t->dmap_a, spec, spec, t->T, t->nlm, nf,
-                                                                     2, nc, t->ntile_a, 0, 0.0);
+  {
+    const int ph = t->prof ? t->prof->begin(3) : -1;
+    k_tc_eanal<<<dim3((t->T + 1 + 127) / 128, t->T + 1), 128, 0, s>>>(t->D, t->dmap_a, spec, spec, t->T, t->nlm, nf,
+                                                                       2, nc, t->ntile_a, 0, 0.0);
+    if (t->prof) t->prof->end(ph);
+  }
   return REXI_OK;
 }
 
 int tc_leg_anal_divcurl(TcLegendre* t, const double2* FA, const double2* FB, double2* dv, double2* cu, int nf,
                         double inv_a, cudaStream_t s) {
   const int nc = ncols_for(nf, 4);
-  k_tc_banal<<<dim3(t->T + 1, 2), 256, 0, s>>>(FA, FB, t->wq, t->B, t->boff_a, t->kpad_a, t->T, t->nlat, nf, 4, nc,
-                                               t->bf16);
+  {
+    const int ph = t->prof ? t->prof->begin(1) : -1;
+    k_tc_banal<<<dim3(t->T + 1, 2), 256, 0, s>>>(FA, FB, t->wq, t->B, t->boff_a, t->kpad_a, t->T, t->nlat, nf, 4, nc,
+                                                 t->bf16);
+    if (t->prof) t->prof->end(ph);
+  }
   int rc = gemm(t, false, true, nc, s);
   if (rc) return rc;
-  k_tc_eanal<<<dim3((t->T + 1 + 127) / 128, t->T + 1), 128, 0, s>>>(t->D, t->dmap_a, dv, cu, t->T, t->nlm, nf, 4,
-                                                                     nc, t->ntile_a, 1, inv_a);
+  {
+    const int ph = t->prof ? t->prof->begin(3) : -1;
+    k_tc_eanal<<<dim3((t->T + 1 + 127) / 128, t->T + 1), 128, 0, s>>>(t->D, t->dmap_a, dv, cu, t->T, t->nlm, nf, 4,
+                                                                       nc, t->ntile_a, 1, inv_a);
+    if (t->prof) t->prof->end(ph);
+  }
   return REXI_OK;
+}
+
+void tc_legendre_set_prof(TcLegendre* t, StageProf* prof) {
+  if (t) t->prof = prof;
 }
 
 int tc_legendre_error(TcLegendre* t, int* flag) {

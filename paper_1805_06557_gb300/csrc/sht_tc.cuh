@@ -1,10 +1,76 @@
 // Tensor-core (tcgen05) Legendre contractions for sh_plan precisions SH_TF32 / SH_BF16.
 #pragma once
+#include <vector>
+
 #include "common.cuh"
 
 namespace rexi {
 
+// Per-stage CUDA-event timing of the SH transforms (off unless enabled): a pair of events on
+// the plan stream around every kernel launch, accumulated when collected.
+struct StageProf {
+  static constexpr int NSTAGE = 5;  // FP64 Legendre, TC operand pack, tcgen05 GEMM, TC epilogue, FFT
+  bool on = false;
+  cudaStream_t stream = nullptr;
+  struct Pend {
+    cudaEvent_t a, b;
+    int k;
+  };
+  std::vector<Pend> pending;
+  std::vector<cudaEvent_t> pool;
+  double ms[NSTAGE] = {};
+  int n[NSTAGE] = {};
+  cudaEvent_t take() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  int begin(int k) {
+    if (!on) return -1;
+    Pend q{take(), take(), k};
+    cudaEventRecord(q.a, stream);
+    pending.push_back(q);
+    return (int)pending.size() - 1;
+  }
+  void end(int h) {
+    if (h >= 0) cudaEventRecord(pending[h].b, stream);
+  }
+  // synchronises the stream, adds the pending intervals
+  cudaError_t collect() {
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e) return e;
+    for (auto& q : pending) {
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, q.a, q.b);
+      if (e) return e;
+      ms[q.k] += t;
+      n[q.k] += 1;
+      pool.push_back(q.a);
+      pool.push_back(q.b);
+    }
+    pending.clear();
+    return cudaSuccess;
+  }
+  void release() {
+    cudaStreamSynchronize(stream);
+    for (auto& q : pending) {
+      pool.push_back(q.a);
+      pool.push_back(q.b);
+    }
+    pending.clear();
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    pool.clear();
+  }
+};
+
 struct TcLegendre;
+// stage timer of the owning plan (may be null)
+void tc_legendre_set_prof(TcLegendre* t, StageProf* prof);
 
 int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const double* w,
                        const double* wq, int T, int nlat, int max_fields, bool bf16,

@@ -5,6 +5,7 @@
 #include "../../include/sht.h"
 #include "../../include/swe.h"
 #include "common.cuh"
+#include "sht_tc.cuh"
 
 namespace rexi {
 namespace {
@@ -91,6 +92,7 @@ struct swe_plan {
           *kes = nullptr;
   double *PZ = nullptr, *Ug = nullptr, *Vg = nullptr, *A = nullptr, *B = nullptr, *KE = nullptr,
          *c2 = nullptr;
+  StageProf prof;  // the step's own grid and spectral kernels (stage 0)
 };
 
 extern "C" int swe_plan_destroy(swe_plan* p) {
@@ -98,6 +100,7 @@ extern "C" int swe_plan_destroy(swe_plan* p) {
   cudaStreamSynchronize(p->stream);
   rexi_plan_destroy(p->rp);
   sh_plan_destroy(p->sp);
+  p->prof.release();
   for (void* q : {(void*)p->psi, (void*)p->chi, (void*)p->Um, (void*)p->Ut, (void*)p->dv, (void*)p->cu,
                   (void*)p->kes, (void*)p->PZ, (void*)p->Ug, (void*)p->Vg, (void*)p->A, (void*)p->B,
                   (void*)p->KE, (void*)p->c2})
@@ -115,6 +118,7 @@ extern "C" int swe_plan_create(const swe_plan_desc* desc, swe_plan** out) {
   swe_plan* p = new swe_plan();
   p->d = d;
   p->stream = (cudaStream_t)d.stream;
+  p->prof.stream = p->stream;
   p->nlm = (d.T + 1) * (d.T + 2) / 2;
   p->npt = d.nlat * d.nlon;
   auto bail = [&](int code) {
@@ -170,16 +174,28 @@ extern "C" int swe_plan_create(const swe_plan_desc* desc, swe_plan** out) {
 static int nonlinear_update(swe_plan* p, const double2* U, const double2* base, double tau, double2* out) {
   const int T = p->d.T, nlm = p->nlm;
   const int tb = 256;
-  k_inv_lap<<<(nlm + tb - 1) / tb, tb, 0, p->stream>>>(U, p->psi, p->chi, T, nlm, p->d.radius * p->d.radius);
+  {
+    const int ph = p->prof.begin(0);
+    k_inv_lap<<<(nlm + tb - 1) / tb, tb, 0, p->stream>>>(U, p->psi, p->chi, T, nlm, p->d.radius * p->d.radius);
+    p->prof.end(ph);
+  }
   int rc;
   if ((rc = sh_synthesis(p->sp, U, p->PZ, 2))) return rc;  // Phi', zeta
   if ((rc = sh_synthesis_uv(p->sp, p->psi, p->chi, p->Ug, p->Vg, 1))) return rc;
-  k_swe_products<<<(p->npt + tb - 1) / tb, tb, 0, p->stream>>>(p->PZ, p->Ug, p->Vg, p->c2, p->A, p->B, p->KE,
-                                                              p->d.nlat, p->d.nlon);
+  {
+    const int ph = p->prof.begin(0);
+    k_swe_products<<<(p->npt + tb - 1) / tb, tb, 0, p->stream>>>(p->PZ, p->Ug, p->Vg, p->c2, p->A, p->B, p->KE,
+                                                                p->d.nlat, p->d.nlon);
+    p->prof.end(ph);
+  }
   if ((rc = sh_analysis_divcurl(p->sp, p->A, p->B, p->dv, p->cu, 2))) return rc;
   if ((rc = sh_analysis(p->sp, p->KE, p->kes, 1))) return rc;
-  k_swe_combine<<<(nlm + tb - 1) / tb, tb, 0, p->stream>>>(base, p->dv, p->cu, p->kes, out, tau, T, nlm,
-                                                           1.0 / (p->d.radius * p->d.radius));
+  {
+    const int ph = p->prof.begin(0);
+    k_swe_combine<<<(nlm + tb - 1) / tb, tb, 0, p->stream>>>(base, p->dv, p->cu, p->kes, out, tau, T, nlm,
+                                                             1.0 / (p->d.radius * p->d.radius));
+    p->prof.end(ph);
+  }
   cudaError_t e = cudaGetLastError();
   return e ? cuda_fail(e, "swe nonlinear kernels") : REXI_OK;
 }
@@ -215,6 +231,46 @@ extern "C" int swe_step(swe_plan* p, void* state, int nsteps) {
       if ((rc = rk2_nonlinear(p, p->Ut, dt))) return rc;
       if ((rc = rexi_step(p->rp, p->Ut, U, 1))) return rc;
     }
+  }
+  return REXI_OK;
+}
+
+extern "C" int swe_plan_set_profiling(swe_plan* p, int enable) {
+  if (!p) return fail(REXI_EINVAL, "swe_plan_set_profiling: null plan");
+  p->prof.on = enable != 0;
+  int rc = rexi_plan_set_profiling(p->rp, enable);
+  return rc ? rc : sh_plan_set_profiling(p->sp, enable);
+}
+
+extern "C" int swe_plan_get_profile(swe_plan* p, double* ms, int* launches, int reset) {
+  if (!p) return fail(REXI_EINVAL, "swe_plan_get_profile: null plan");
+  double rm[REXI_NKERNELS], sm[SH_NSTAGES];
+  int rn[REXI_NKERNELS], sn[SH_NSTAGES];
+  int rc = rexi_plan_get_profile(p->rp, rm, rn, reset);
+  if (rc) return rc;
+  if ((rc = sh_plan_get_profile(p->sp, sm, sn, reset))) return rc;
+  REXI_CUDA_TRY(p->prof.collect());
+  double out[SWE_NSTAGES] = {0, 0, 0, 0};
+  int cnt[SWE_NSTAGES] = {0, 0, 0, 0};
+  for (int k = 0; k < REXI_NKERNELS; ++k) {
+    out[0] += rm[k];
+    cnt[0] += rn[k];
+  }
+  for (int k = 0; k < 4; ++k) {
+    out[1] += sm[k];
+    cnt[1] += sn[k];
+  }
+  out[2] = sm[4];
+  cnt[2] = sn[4];
+  out[3] = p->prof.ms[0];
+  cnt[3] = p->prof.n[0];
+  if (reset) {
+    p->prof.ms[0] = 0.0;
+    p->prof.n[0] = 0;
+  }
+  for (int k = 0; k < SWE_NSTAGES; ++k) {
+    if (ms) ms[k] = out[k];
+    if (launches) launches[k] = cnt[k];
   }
   return REXI_OK;
 }

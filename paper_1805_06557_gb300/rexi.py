@@ -359,6 +359,9 @@ _lib.sh_plan_get_grid.argtypes = [ctypes.c_void_p, _dp, _dp]
 for _n in ("sh_synthesis", "sh_analysis"):
     getattr(_lib, _n).argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
 _lib.sh_plan_check.argtypes = [ctypes.c_void_p]
+_lib.sh_plan_set_profiling.argtypes = [ctypes.c_void_p, ctypes.c_int]
+_lib.sh_plan_get_profile.argtypes = [ctypes.c_void_p, _dp, _ip, ctypes.c_int]
+SH_STAGE_NAMES = ("legendre_fp64", "tc_pack", "tc_gemm", "tc_epilogue", "fft")
 for _n in ("sh_synthesis_uv", "sh_analysis_divcurl"):
     getattr(_lib, _n).argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 4 + [ctypes.c_int]
 
@@ -403,6 +406,17 @@ class ShPlan:
         """Synchronise; raise if a device-side bounded wait gave up."""
         _check(_lib.sh_plan_check(self._h))
 
+    def set_profiling(self, enable=True):
+        _check(_lib.sh_plan_set_profiling(self._h, 1 if enable else 0))
+
+    def profile(self, reset=True):
+        """{stage: (total ms, launches)} since the last reset (synchronises the stream)."""
+        ms = np.zeros(len(SH_STAGE_NAMES))
+        n = np.zeros(len(SH_STAGE_NAMES), dtype=np.int32)
+        _check(_lib.sh_plan_get_profile(self._h, ms.ctypes.data_as(_dp), n.ctypes.data_as(_ip),
+                                        1 if reset else 0))
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(SH_STAGE_NAMES)}
+
     def analysis_divcurl(self, A, B, div, curl, nfields=1):
         _check(_lib.sh_analysis_divcurl(self._h, _ptr(A), _ptr(B), _ptr(div), _ptr(curl),
                                         int(nfields)))
@@ -437,6 +451,9 @@ _lib.swe_plan_create.argtypes = [ctypes.POINTER(SweDesc), ctypes.POINTER(ctypes.
 _lib.swe_plan_destroy.argtypes = [ctypes.c_void_p]
 _lib.swe_step.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
 _lib.swe_nonlinear.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+_lib.swe_plan_set_profiling.argtypes = [ctypes.c_void_p, ctypes.c_int]
+_lib.swe_plan_get_profile.argtypes = [ctypes.c_void_p, _dp, _ip, ctypes.c_int]
+SWE_STAGE_NAMES = ("rexi", "legendre", "fft", "grid_products")
 
 
 class SwePlan:
@@ -464,6 +481,17 @@ class SwePlan:
     def nonlinear(self, state, tendency):
         _check(_lib.swe_nonlinear(self._h, _ptr(state), _ptr(tendency)))
         return tendency
+
+    def set_profiling(self, enable=True):
+        _check(_lib.swe_plan_set_profiling(self._h, 1 if enable else 0))
+
+    def profile(self, reset=True):
+        """{stage: (total ms, launches)} since the last reset (synchronises the stream)."""
+        ms = np.zeros(len(SWE_STAGE_NAMES))
+        n = np.zeros(len(SWE_STAGE_NAMES), dtype=np.int32)
+        _check(_lib.swe_plan_get_profile(self._h, ms.ctypes.data_as(_dp), n.ctypes.data_as(_ip),
+                                         1 if reset else 0))
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(SWE_STAGE_NAMES)}
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
