@@ -257,114 +257,145 @@ __global__ void __launch_bounds__(ATH) k_leg_anal_divcurl(const double* __restri
 }
 
 // ---- longitude FFT (Stockham autosort, radix 2 and 3, shared memory) ---------------------
+// Templated on the arithmetic type: FP64 for SH_FP64 plans, FP32 for the tensor-core plans
+// (whose Legendre stage already rounds to TF32 / BF16); grids and Fourier arrays stay FP64.
 struct FftPlan {
   int n, nrad;
   int rad[24];
+  unsigned magic[24];  // ceil(2^32 / Ns) of each pass: j / Ns = umulhi(j, magic) for j < n
 };
 
 constexpr int FTH = 256;
 constexpr double SQRT3_2 = 0.86602540378443864676;  // sin(2 pi / 3)
 
+template <typename C> struct Cx;
+template <> struct Cx<double2> {
+  using R = double;
+  static __device__ __forceinline__ double2 make(double x, double y) { return make_double2(x, y); }
+};
+template <> struct Cx<float2> {
+  using R = float;
+  static __device__ __forceinline__ float2 make(float x, float y) { return make_float2(x, y); }
+};
+template <typename C> __device__ __forceinline__ C c_mul(C a, C b) {
+  return Cx<C>::make(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __device__ __forceinline__ C c_add(C a, C b) { return Cx<C>::make(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C c_sub(C a, C b) { return Cx<C>::make(a.x - b.x, a.y - b.y); }
+
 // in-place on two shared buffers; returns the buffer holding the result.  sign = -1 forward,
 // +1 inverse (no scaling).  tw[k] = e^{-2 pi i k / n}.
-__device__ double2* fft_smem(double2* a, double2* b, const FftPlan& fp, const double2* __restrict__ tw,
-                             int sign) {
+template <typename C>
+__device__ C* fft_smem(C* a, C* b, const FftPlan& fp, const C* __restrict__ tw, int sign) {
+  using R = typename Cx<C>::R;
   const int n = fp.n;
   int Ns = 1;
   for (int s = 0; s < fp.nrad; ++s) {
-    const int R = fp.rad[s];
-    const int nb = n / R;
-    const int stride = n / (Ns * R);
+    const int R_ = fp.rad[s];
+    const int nb = n / R_;
+    const int stride = n / (Ns * R_);
+    const unsigned mg = fp.magic[s];
     for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-      const int jm = j % Ns;
-      double2 v[3];
-      for (int r = 0; r < R; ++r) {
-        double2 x = a[j + r * nb];
-        if (r > 0) {
-          double2 t = tw[(r * jm * stride) % n];
+      const int q = (Ns == 1) ? j : (int)__umulhi((unsigned)j, mg);  // j / Ns
+      const int jm = j - q * Ns;
+      const int idxD = q * Ns * R_ + jm;
+      if (R_ == 2) {
+        const C v0 = a[j];
+        C v1 = a[j + nb];
+        if (jm) {
+          C t = tw[jm * stride];  // jm * stride < n / 2
           if (sign > 0) t.y = -t.y;
-          x = cmul(x, t);
+          v1 = c_mul(v1, t);
         }
-        v[r] = x;
-      }
-      const int idxD = (j / Ns) * Ns * R + jm;
-      if (R == 2) {
-        b[idxD] = cadd(v[0], v[1]);
-        b[idxD + Ns] = make_double2(v[0].x - v[1].x, v[0].y - v[1].y);
+        b[idxD] = c_add(v0, v1);
+        b[idxD + Ns] = c_sub(v0, v1);
       } else {  // R == 3
-        const double2 t1 = cadd(v[1], v[2]);
-        const double2 t2 = make_double2(v[0].x - 0.5 * t1.x, v[0].y - 0.5 * t1.y);
-        const double2 d = make_double2(v[1].x - v[2].x, v[1].y - v[2].y);
-        const double sg = sign * SQRT3_2;
+        const C v0 = a[j];
+        C v1 = a[j + nb], v2 = a[j + 2 * nb];
+        if (jm) {
+          C t1 = tw[jm * stride], t2 = tw[2 * jm * stride];  // 2 jm stride < 2 n / 3
+          if (sign > 0) {
+            t1.y = -t1.y;
+            t2.y = -t2.y;
+          }
+          v1 = c_mul(v1, t1);
+          v2 = c_mul(v2, t2);
+        }
+        const C s1 = c_add(v1, v2);
+        const C t2 = Cx<C>::make(v0.x - R(0.5) * s1.x, v0.y - R(0.5) * s1.y);
+        const C d = c_sub(v1, v2);
+        const R sg = R(sign * SQRT3_2);
         // i * sg * d = (-sg d.y, sg d.x)
-        b[idxD] = cadd(v[0], t1);
-        b[idxD + Ns] = make_double2(t2.x - sg * d.y, t2.y + sg * d.x);
-        b[idxD + 2 * Ns] = make_double2(t2.x + sg * d.y, t2.y - sg * d.x);
+        b[idxD] = c_add(v0, s1);
+        b[idxD + Ns] = Cx<C>::make(t2.x - sg * d.y, t2.y + sg * d.x);
+        b[idxD + 2 * Ns] = Cx<C>::make(t2.x + sg * d.y, t2.y - sg * d.x);
       }
     }
     __syncthreads();
-    double2* t = a;
+    C* t = a;
     a = b;
     b = t;
-    Ns *= R;
+    Ns *= R_;
   }
   return a;
 }
 
 // synthesis: F[field][m][nlat] (m <= T) -> grid[field][nlat][nlon], two latitude rows per block
+template <typename C>
 __global__ void __launch_bounds__(FTH) k_fft_synth(const double2* __restrict__ F, double* __restrict__ grid,
-                                                   FftPlan fp, const double2* __restrict__ tw, int T,
-                                                   int nlat) {
-  extern __shared__ double2 sm2[];
+                                                   FftPlan fp, const C* __restrict__ tw, int T, int nlat) {
+  extern __shared__ __align__(16) unsigned char fsm[];
+  using R = typename Cx<C>::R;
   const int n = fp.n;
   const int f = blockIdx.y;
   const int j0 = 2 * blockIdx.x;
-  double2* a = sm2;
-  double2* b = sm2 + n;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) a[k] = make_double2(0.0, 0.0);
+  C* a = reinterpret_cast<C*>(fsm);
+  C* b = a + n;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) a[k] = Cx<C>::make(R(0), R(0));
   __syncthreads();
   const double2* in = F + (size_t)f * (T + 1) * nlat;
   for (int m = threadIdx.x; m <= T; m += blockDim.x) {
     const double2 A = in[(size_t)m * nlat + j0], B = in[(size_t)m * nlat + j0 + 1];
     if (m == 0) {
-      a[0] = make_double2(A.x, B.x);
+      a[0] = Cx<C>::make(R(A.x), R(B.x));
     } else {
-      a[m] = make_double2(A.x - B.y, A.y + B.x);       // A + i B
-      a[n - m] = make_double2(A.x + B.y, B.x - A.y);   // conj(A) + i conj(B)
+      a[m] = Cx<C>::make(R(A.x - B.y), R(A.y + B.x));      // A + i B
+      a[n - m] = Cx<C>::make(R(A.x + B.y), R(B.x - A.y));  // conj(A) + i conj(B)
     }
   }
   __syncthreads();
-  const double2* z = fft_smem(a, b, fp, tw, +1);
+  const C* z = fft_smem<C>(a, b, fp, tw, +1);
   double* r0 = grid + ((size_t)f * nlat + j0) * n;
   double* r1 = r0 + n;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    r0[k] = z[k].x;
-    r1[k] = z[k].y;
+    r0[k] = (double)z[k].x;
+    r1[k] = (double)z[k].y;
   }
 }
 
 // analysis: grid[field][nlat][nlon] -> F[field][m][nlat] = (2 pi / n) sum_k f e^{-i m lambda_k}
+template <typename C>
 __global__ void __launch_bounds__(FTH) k_fft_anal(const double* __restrict__ grid, double2* __restrict__ F,
-                                                  FftPlan fp, const double2* __restrict__ tw, int T,
-                                                  int nlat) {
-  extern __shared__ double2 sm2[];
+                                                  FftPlan fp, const C* __restrict__ tw, int T, int nlat) {
+  extern __shared__ __align__(16) unsigned char fsm[];
+  using R = typename Cx<C>::R;
   const int n = fp.n;
   const int f = blockIdx.y;
   const int j0 = 2 * blockIdx.x;
-  double2* a = sm2;
-  double2* b = sm2 + n;
+  C* a = reinterpret_cast<C*>(fsm);
+  C* b = a + n;
   const double* r0 = grid + ((size_t)f * nlat + j0) * n;
   const double* r1 = r0 + n;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) a[k] = make_double2(r0[k], r1[k]);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) a[k] = Cx<C>::make(R(r0[k]), R(r1[k]));
   __syncthreads();
-  const double2* z = fft_smem(a, b, fp, tw, -1);
+  const C* z = fft_smem<C>(a, b, fp, tw, -1);
   const double sc = 3.14159265358979323846 / n;  // (2 pi / n) / 2
   double2* out = F + (size_t)f * (T + 1) * nlat;
   for (int m = threadIdx.x; m <= T; m += blockDim.x) {
-    const double2 zm = z[m], zn = z[m == 0 ? 0 : n - m];
+    const C zm = z[m], zn = z[m == 0 ? 0 : n - m];
     // A = (Z_m + conj(Z_{n-m})) / 2,  B = (Z_m - conj(Z_{n-m})) / (2i)
-    out[(size_t)m * nlat + j0] = make_double2(sc * (zm.x + zn.x), sc * (zm.y - zn.y));
-    out[(size_t)m * nlat + j0 + 1] = make_double2(sc * (zm.y + zn.y), -sc * (zm.x - zn.x));
+    out[(size_t)m * nlat + j0] = make_double2(sc * ((double)zm.x + zn.x), sc * ((double)zm.y - zn.y));
+    out[(size_t)m * nlat + j0 + 1] = make_double2(sc * ((double)zm.y + zn.y), -sc * ((double)zm.x - zn.x));
   }
 }
 
@@ -414,6 +445,11 @@ bool fft_factor(int n, FftPlan& fp) {
     fp.rad[fp.nrad++] = 3;
     m /= 3;
   }
+  unsigned long long Ns = 1;
+  for (int s = 0; s < fp.nrad; ++s) {
+    fp.magic[s] = Ns == 1 ? 0u : (unsigned)(((1ULL << 32) + Ns - 1) / Ns);  // ceil(2^32 / Ns); unused for Ns = 1
+    Ns *= fp.rad[s];
+  }
   return m == 1;
 }
 
@@ -433,13 +469,17 @@ struct sh_plan {
   double* d_P = nullptr;    // [nlm][nh]
   double* d_H = nullptr;
   double2* d_tw = nullptr;  // [nlon]
+  float2* d_tw32 = nullptr; // [nlon], FP32 FFT of the tensor-core plans
+  bool fft32 = false;
   double2* d_F = nullptr;   // Fourier workspace [2 * max_fields][T+1][nlat]
   FftPlan fp{};
   TcLegendre* tc = nullptr;  // tensor-core Legendre state (SH_TF32 / SH_BF16)
   StageProf prof;            // per-stage event timing (sh_plan_set_profiling)
 };
 
-static size_t fft_smem(const sh_plan* p) { return sizeof(double2) * 2 * (size_t)p->d.nlon; }
+static size_t fft_smem(const sh_plan* p) {
+  return (p->fft32 ? sizeof(float2) : sizeof(double2)) * 2 * (size_t)p->d.nlon;
+}
 
 extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
   if (!desc || !out) return fail(REXI_EINVAL, "sh_plan_create: null argument");
@@ -458,6 +498,7 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
   p->nlm = (d.T + 1) * (d.T + 2) / 2;
   p->stream = (cudaStream_t)d.stream;
   p->prof.stream = p->stream;
+  p->fft32 = d.precision != SH_FP64;
   auto bail = [&](int code) {
     sh_plan_destroy(p);
     return code;
@@ -468,15 +509,18 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
   std::vector<double> wq(p->nh);
   for (int j = 0; j < p->nh; ++j) wq[j] = p->w[j] / ((1.0 - p->mu[j]) * (1.0 + p->mu[j]));
   std::vector<double2> tw(d.nlon);
+  std::vector<float2> tw32(d.nlon);
   for (int k = 0; k < d.nlon; ++k) {
     const double a = -2.0 * M_PI * k / d.nlon;
     tw[k] = make_double2(std::cos(a), std::sin(a));
+    tw32[k] = make_float2((float)tw[k].x, (float)tw[k].y);
   }
   const size_t tab = (size_t)p->nlm * p->nh;
   cudaError_t e;
   if ((e = cudaMalloc(&p->d_mu, sizeof(double) * p->nh)) || (e = cudaMalloc(&p->d_w, sizeof(double) * p->nh)) ||
       (e = cudaMalloc(&p->d_wq, sizeof(double) * p->nh)) || (e = cudaMalloc(&p->d_P, sizeof(double) * tab)) ||
       (e = cudaMalloc(&p->d_H, sizeof(double) * tab)) || (e = cudaMalloc(&p->d_tw, sizeof(double2) * d.nlon)) ||
+      (e = cudaMalloc(&p->d_tw32, sizeof(float2) * d.nlon)) ||
       (e = cudaMalloc(&p->d_F, sizeof(double2) * 2 * (size_t)d.max_fields * (d.T + 1) * d.nlat))) {
     cudaGetLastError();
     return bail(fail(REXI_ENOMEM, "sh_plan_create: cudaMalloc failed: %s", cudaGetErrorString(e)));
@@ -484,13 +528,19 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
   if ((e = cudaMemcpy(p->d_mu, p->mu.data(), sizeof(double) * p->nh, cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(p->d_w, p->w.data(), sizeof(double) * p->nh, cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(p->d_wq, wq.data(), sizeof(double) * p->nh, cudaMemcpyHostToDevice)) ||
-      (e = cudaMemcpy(p->d_tw, tw.data(), sizeof(double2) * d.nlon, cudaMemcpyHostToDevice)))
+      (e = cudaMemcpy(p->d_tw, tw.data(), sizeof(double2) * d.nlon, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(p->d_tw32, tw32.data(), sizeof(float2) * d.nlon, cudaMemcpyHostToDevice)))
     return bail(cuda_fail(e, "sh_plan_create: cudaMemcpy"));
   k_legendre_table<<<dim3((p->nh + 127) / 128, d.T + 1), 128, 0, p->stream>>>(p->d_mu, p->d_P, p->d_H, d.T, p->nh);
   if ((e = cudaGetLastError())) return bail(cuda_fail(e, "k_legendre_table"));
-  if ((e = cudaFuncSetAttribute(k_fft_synth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p))) ||
-      (e = cudaFuncSetAttribute(k_fft_anal, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p))))
-    return bail(cuda_fail(e, "cudaFuncSetAttribute(fft)"));
+  if (p->fft32) {
+    e = cudaFuncSetAttribute(k_fft_synth<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p));
+    if (!e) e = cudaFuncSetAttribute(k_fft_anal<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p));
+  } else {
+    e = cudaFuncSetAttribute(k_fft_synth<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p));
+    if (!e) e = cudaFuncSetAttribute(k_fft_anal<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p));
+  }
+  if (e) return bail(cuda_fail(e, "cudaFuncSetAttribute(fft)"));
   if (d.precision != SH_FP64) {
     int rc = tc_legendre_create(&p->tc, p->d_P, p->d_H, p->d_w, p->d_wq, d.T, d.nlat, d.max_fields,
                                 d.precision == SH_BF16, p->stream);
@@ -511,6 +561,7 @@ extern "C" int sh_plan_destroy(sh_plan* p) {
   cudaFree(p->d_P);
   cudaFree(p->d_H);
   cudaFree(p->d_tw);
+  cudaFree(p->d_tw32);
   cudaFree(p->d_F);
   tc_legendre_destroy(p->tc);
   p->prof.release();
@@ -539,19 +590,25 @@ static double2* fslot(sh_plan* p, int s) {
 }
 
 static int launch_fft_synth(sh_plan* p, const double2* F, double* grid, int nf) {
-  {
-    const int ph = p->prof.begin(4);
-    k_fft_synth<<<dim3(p->d.nlat / 2, nf), FTH, fft_smem(p), p->stream>>>(F, grid, p->fp, p->d_tw, p->d.T, p->d.nlat);
-    p->prof.end(ph);
-  }
+  const int ph = p->prof.begin(4);
+  if (p->fft32)
+    k_fft_synth<float2><<<dim3(p->d.nlat / 2, nf), FTH, fft_smem(p), p->stream>>>(F, grid, p->fp, p->d_tw32, p->d.T,
+                                                                                p->d.nlat);
+  else
+    k_fft_synth<double2><<<dim3(p->d.nlat / 2, nf), FTH, fft_smem(p), p->stream>>>(F, grid, p->fp, p->d_tw, p->d.T,
+                                                                                 p->d.nlat);
+  p->prof.end(ph);
   return REXI_OK;
 }
 static int launch_fft_anal(sh_plan* p, const double* grid, double2* F, int nf) {
-  {
-    const int ph = p->prof.begin(4);
-    k_fft_anal<<<dim3(p->d.nlat / 2, nf), FTH, fft_smem(p), p->stream>>>(grid, F, p->fp, p->d_tw, p->d.T, p->d.nlat);
-    p->prof.end(ph);
-  }
+  const int ph = p->prof.begin(4);
+  if (p->fft32)
+    k_fft_anal<float2><<<dim3(p->d.nlat / 2, nf), FTH, fft_smem(p), p->stream>>>(grid, F, p->fp, p->d_tw32, p->d.T,
+                                                                               p->d.nlat);
+  else
+    k_fft_anal<double2><<<dim3(p->d.nlat / 2, nf), FTH, fft_smem(p), p->stream>>>(grid, F, p->fp, p->d_tw, p->d.T,
+                                                                                p->d.nlat);
+  p->prof.end(ph);
   return REXI_OK;
 }
 

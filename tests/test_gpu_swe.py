@@ -104,3 +104,39 @@ def test_steady_zonal_flow_splitting_error_second_order(env):
         plan.close()
     rate = math.log2(errs[0] / errs[1])
     assert errs[0] < 1e-2 and 1.6 < rate < 2.6, (errs, rate)
+
+
+# Per-field bounds (Phi', zeta, delta tendencies; relative L2 against the FP64 oracle) of N(U)
+# with tensor-core Legendre contractions at T127.  Each transform carries the input rounding
+# of its precision (unit roundoff 2^-11 for TF32, 2^-8 for BF16; measured transform errors
+# 3e-4 and 2.5e-3), spread over all degrees.  The delta tendency contains -lap(KE): the
+# analysis error of KE at degree n is multiplied by n(n+1)/a^2, up to 1.6e4 times the n = 1
+# factor, while the true tendency's spectrum decays; for the balanced state the tendencies
+# are also small differences of large terms.  Hence the delta tendency is NOT usable in these
+# precisions at T127 (errors of order 1), whereas Phi' and zeta stay within ~10 transform
+# errors.  The bounds are twice the measured errors.
+TC_BOUNDS = {("tf32", "gaussian"): (8e-3, 6e-3, 0.9), ("tf32", "balanced"): (5e-2, 2e-3, 0.5),
+             ("bf16", "gaussian"): (7e-2, 5e-2, 8.0), ("bf16", "balanced"): (0.4, 1e-2, 4.0)}
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("kind", ["gaussian", "balanced"])
+def test_nonlinear_tensor_core_error(env, prec, kind, capsys):
+    """N(U) with the Legendre contractions on the tensor cores (and the FP32 FFT of those
+    plans) against the FP64 oracle at T127, per field, within TC_BOUNDS."""
+    torch, rexi = env
+    T, nlat, nlon = 127, 192, 384
+    U = _state(T, 3) if kind == "balanced" else syn.gaussian_state(T, 3, scales=(1e3, 2e-5, 5e-6))
+    g = osht.Grid(T, nlat, nlon, A)
+    ref = oswe.nonlinear(U, g)
+    p0, Xc = _contour(T, 1800.0)
+    plan = rexi.SwePlan(T, nlat, nlon, 1800.0, OM, A, PB, 64, p0, Xc, sh_precision=prec)
+    u = torch.from_numpy(U).cuda()
+    t = torch.empty_like(u)
+    plan.nonlinear(u, t)
+    torch.cuda.synchronize()
+    err = orx.rel_l2(t.cpu().numpy(), ref, T)
+    with capsys.disabled():
+        print("\nN(U) %s %s per-field rel L2: %s" % (prec, kind, ["%.2e" % e for e in err]))
+    assert np.all(np.isfinite(err)) and np.all(err < np.array(TC_BOUNDS[(prec, kind)])), err
+    plan.close()
