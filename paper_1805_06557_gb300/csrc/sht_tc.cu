@@ -11,9 +11,10 @@
 // Operands are stored in the canonical no-swizzle K-major layout of the tensor cores
 // (8-row x 16-byte core matrices; cores adjacent along K 128 B apart), the tables pre-tiled
 // at plan time so that each K-chunk of A is one contiguous block moved by the bulk-copy
-// engine (cp.async.bulk, completion on an mbarrier) into a 3-stage shared-memory ring.
-// One thread issues the MMAs (accumulator in TMEM, FP32); after the last commit all four
-// warps read the accumulator rows with tcgen05.ld and store D.  Epilogue kernels combine
+// engine (cp.async.bulk, completion on an mbarrier).  The GEMM is a persistent kernel, one
+// CTA per SM, with a copy warp streaming A chunks through a ring of up to 8 stages and the
+// B operands through two buffers, an MMA warp (accumulators in TMEM, FP32, two buffers) and
+// four epilogue warps reading the accumulators with tcgen05.ld.  Epilogue kernels combine
 // the parities (north = even + odd, south = even - odd for P; the opposite sign for H) in
 // FP64.  All mbarrier waits are bounded; on a timeout the kernel records an error flag.
 #include <algorithm>
@@ -27,8 +28,10 @@ namespace rexi {
 
 namespace {
 
-constexpr int TC_STAGES = 3;
+constexpr int TC_MAXSTAGES = 8;     // depth of the A-chunk ring
+constexpr int TC_THREADS = 192;     // warps 0-3 epilogue, warp 4 bulk copies, warp 5 MMA issue
 constexpr int TC_MAXCOL = 32;
+constexpr size_t TC_SMEM_BUDGET = 220 * 1024;
 
 struct Job {
   long long a_off;  // byte offset of the job's first A chunk in its table
@@ -47,100 +50,181 @@ struct GemmArgs {
   float* D;
   const Job* jobs;
   int njobs, ncols, bf16;
+  int stages;       // A ring depth (<= TC_MAXSTAGES)
+  int nb;           // B buffers (2 or 4): B operands are fetched up to nb - 1 jobs ahead
+  uint32_t bslot;   // bytes of one B buffer
   int* err;
 };
 
-__global__ void __launch_bounds__(128) k_tc_gemm(GemmArgs g) {
+// Persistent, warp-specialised GEMM over the job list: CTA c takes jobs c, c + grid, ...
+// (the list is sorted by decreasing length).  Warp 4 streams the A chunks of every job through
+// the S-stage ring without pausing between jobs, and fetches B operands into NB buffers up to
+// NB - 1 jobs ahead (so that a job's MMAs never wait for the latency of its B copy); warp 5
+// issues the MMAs of job i into TMEM accumulator i & 1 and commits: the ring stage (empty),
+// the B buffer (bempty) and the accumulator (tfull); warps 0-3 read accumulator i & 1 (one
+// TMEM lane quarter each), store D, and release it (tempty), so that the MMAs of job i + 1
+// overlap the epilogue of job i.  Every wait is bounded; on a timeout the role records an
+// error code and stops, and teardown drains the copies and MMAs in flight.
+constexpr int TC_MAXNB = 4;
+constexpr int TC_NACC = 4;          // independent accumulators per job (one per k-step of a chunk)
+constexpr uint32_t TC_TMEM_COLS = 2 * TC_NACC * 32;  // two job buffers x TC_NACC x 32 columns
+template <bool BF>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(GemmArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  const int tid = threadIdx.x;
-  const int jid = blockIdx.x;
-  if (jid >= g.njobs) return;
-  const Job jb = g.jobs[jid];
-  const int E = g.bf16 ? 8 : 4, eb = g.bf16 ? 2 : 4, kstep = g.bf16 ? 16 : 8;
-  const int KC = g.bf16 ? 64 : 32;
-  const uint32_t chunk_bytes = 128u * KC * eb;
-  const uint32_t b_bytes = (uint32_t)g.ncols * jb.kpad * eb;
+  // element type constants: 16-byte core-matrix rows hold E elements; a chunk (KC = 128 B of
+  // K per row) is 4 MMA k-steps of 32 B; consecutive k-steps are 2 core matrices (256 B) apart
+  constexpr int E = BF ? 8 : 4, eb = BF ? 2 : 4, KC = BF ? 64 : 32;
+  constexpr uint32_t chunk_bytes = 128u * KC * eb;
+  static_assert(KC * eb == 128, "a chunk row is 128 bytes of K");
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int S = g.stages, NB = g.nb;
   unsigned char* sA = smem;
-  unsigned char* sB = smem + TC_STAGES * chunk_bytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + ((b_bytes + 127) / 128) * 128);
-  // bars: full[0..S), done[0..S), bfull, final ; then the TMEM address
-  uint32_t* taddr_s = reinterpret_cast<uint32_t*>(bars + 2 * TC_STAGES + 2);
-  const uint32_t full0 = tc::smem_u32(bars), done0 = full0 + 8 * TC_STAGES;
-  const uint32_t bfull = full0 + 16 * TC_STAGES, fin = bfull + 8;
-  const uint32_t ncols_alloc = 32;
+  unsigned char* sB = smem + (size_t)S * chunk_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + (size_t)NB * g.bslot);
+  // barriers: full[S], empty[S], bfull[NB], bempty[NB], tfull[2], tempty[2], fin
+  const uint32_t full0 = tc::smem_u32(bars), empty0 = full0 + 8 * S;
+  const uint32_t bfull0 = empty0 + 8 * S, bempty0 = bfull0 + 8 * NB, tfull0 = bempty0 + 8 * NB;
+  const uint32_t tempty0 = tfull0 + 16, fin = tempty0 + 16;
+  uint32_t* taddr_s = reinterpret_cast<uint32_t*>(bars + 2 * S + 2 * NB + 5);
+  // jobs of this CTA: blockIdx.x + i * gridDim.x, i < nj
+  const int nj = blockIdx.x < g.njobs ? (g.njobs - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   if (tid == 0) {
-    for (int i = 0; i < 2 * TC_STAGES + 2; ++i) tc::mbar_init(full0 + 8 * i, 1);
+    for (int i = 0; i < 2 * S + 2 * NB + 2; ++i) tc::mbar_init(full0 + 8 * i, 1);
+    tc::mbar_init(tempty0, 4);
+    tc::mbar_init(tempty0 + 8, 4);
+    tc::mbar_init(fin, 1);
     tc::mbar_fence_init();
   }
   __syncthreads();
-  if (tid < 32) tc::tmem_alloc(tc::smem_u32(taddr_s), ncols_alloc);
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(taddr_s), TC_TMEM_COLS);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *taddr_s;
-  const unsigned char* A = (jb.tab ? g.tabH : g.tabP) + jb.a_off;
-  bool ok = true;
-  if (tid == 0) {
-    const uint32_t idesc = tc::instr_desc(128, g.ncols, g.bf16 ? 1 : 2);
-    const uint32_t sa0 = tc::smem_u32(sA), sb0 = tc::smem_u32(sB);
-    const uint32_t sboA = (uint32_t)(KC / E) * 128u, sboB = (uint32_t)(jb.kpad / E) * 128u;
-    tc::mbar_expect_tx(bfull, b_bytes);
-    tc::bulk_g2s(sb0, g.B + jb.b_off, b_bytes, bfull);
-    const int pre = min(TC_STAGES, jb.nchunk);
-    for (int c = 0; c < pre; ++c) {
-      tc::mbar_expect_tx(full0 + 8 * c, chunk_bytes);
-      tc::bulk_g2s(sa0 + c * chunk_bytes, A + (size_t)c * chunk_bytes, chunk_bytes, full0 + 8 * c);
-    }
-    ok = tc::mbar_wait(bfull, 0);
-    int issued = pre;
-    for (int c = 0; c < jb.nchunk && ok; ++c) {
-      const int s = c % TC_STAGES;
-      ok = tc::mbar_wait(full0 + 8 * s, (c / TC_STAGES) & 1);
-      if (!ok) break;
-      tc::fence_after_sync();
-#pragma unroll 1
-      for (int kk = 0; kk < KC; kk += kstep) {
-        const uint64_t ad = tc::smem_desc(sa0 + s * chunk_bytes + (kk / E) * 128u, 128u, sboA);
-        const uint64_t bd = tc::smem_desc(sb0 + ((c * KC + kk) / E) * 128u, 128u, sboB);
-        const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
-        if (g.bf16) tc::mma_f16(tmem, ad, bd, idesc, acc);
-        else tc::mma_tf32(tmem, ad, bd, idesc, acc);
+  const uint32_t sa0 = tc::smem_u32(sA), sb0 = tc::smem_u32(sB);
+  long long a_issued = 0;  // producer: A fills issued
+  int b_issued = 0;        // producer: B fills issued (jobs 0 .. b_issued - 1)
+
+  if (warp == 4) {
+    if (lane == 0) {
+      bool ok = true;
+      // B operand of job q into buffer q % NB (its previous user, job q - NB, must be done)
+      auto issue_b = [&](int q) {
+        const int b = q % NB, u = q / NB;
+        if (u > 0 && !tc::mbar_wait(bempty0 + 8 * b, (u - 1) & 1)) return false;
+        const Job jq = g.jobs[blockIdx.x + q * gridDim.x];
+        const uint32_t bb = (uint32_t)g.ncols * jq.kpad * eb;
+        tc::mbar_expect_tx(bfull0 + 8 * b, bb);
+        tc::bulk_g2s(sb0 + b * g.bslot, g.B + jq.b_off, bb, bfull0 + 8 * b);
+        ++b_issued;
+        return true;
+      };
+      for (int q = 0; q < NB - 1 && q < nj && ok; ++q) ok = issue_b(q);
+      int s = 0;
+      uint32_t round = 0;  // number of completed passes over the ring
+      for (int i = 0; i < nj && ok; ++i) {
+        const Job jb = g.jobs[blockIdx.x + i * gridDim.x];
+        const unsigned char* A = (jb.tab ? g.tabH : g.tabP) + jb.a_off;
+        for (int c = 0; c < jb.nchunk; ++c) {
+          if (round > 0) ok = tc::mbar_wait(empty0 + 8 * s, (round - 1) & 1);
+          if (!ok) break;
+          tc::mbar_expect_tx(full0 + 8 * s, chunk_bytes);
+          tc::bulk_g2s(sa0 + s * chunk_bytes, A + (size_t)c * chunk_bytes, chunk_bytes, full0 + 8 * s);
+          ++a_issued;
+          if (++s == S) {
+            s = 0;
+            ++round;
+          }
+        }
+        if (ok && i + NB - 1 < nj) ok = issue_b(i + NB - 1);
       }
-      tc::mma_commit(done0 + 8 * s);
-      if (c + TC_STAGES < jb.nchunk) {
-        ok = tc::mbar_wait(done0 + 8 * s, (c / TC_STAGES) & 1);
+      if (!ok) atomicExch(g.err, 3);
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      bool ok = true;
+      const uint32_t idesc = tc::instr_desc(128, g.ncols, BF ? 1 : 2);
+      const uint32_t sboA = (uint32_t)(KC / E) * 128u;
+      int s = 0;
+      uint32_t round = 0;
+      for (int i = 0; i < nj && ok; ++i) {
+        const Job jb = g.jobs[blockIdx.x + i * gridDim.x];
+        const int b = i % NB, ub = i / NB, acc = i & 1, ua = i >> 1;
+        ok = tc::mbar_wait(bfull0 + 8 * b, ub & 1);
+        if (ok && ua > 0) ok = tc::mbar_wait(tempty0 + 8 * acc, (ua - 1) & 1);
         if (!ok) break;
-        tc::mbar_expect_tx(full0 + 8 * s, chunk_bytes);
-        tc::bulk_g2s(sa0 + s * chunk_bytes, A + (size_t)(c + TC_STAGES) * chunk_bytes, chunk_bytes,
-                     full0 + 8 * s);
-        ++issued;
-      }
-    }
-    if (!ok) {
-      // drain: wait (bounded) for every bulk copy issued so far before the block exits
-      for (int c = 0; c < issued; ++c) tc::mbar_wait(full0 + 8 * (c % TC_STAGES), (c / TC_STAGES) & 1, 100000u);
-      atomicExch(g.err, 1);
-    }
-    tc::mma_commit(fin);
-  }
-  __syncwarp();
-  const bool fin_ok = tc::mbar_wait(fin, 0);
-  tc::fence_after_sync();
-  const int w = tid >> 5, lane = tid & 31;
-  if (fin_ok) {
-    float* Dj = g.D + jb.d_off + (size_t)(32 * w + lane) * g.ncols;
-    for (int c = 0; c < g.ncols; c += 8) {
-      float v[8];
-      tc::tmem_ld8(tmem + ((uint32_t)(32 * w) << 16) + c, v);
+        tc::fence_after_sync();
+        // k-step q of every chunk accumulates into accumulator q of job buffer acc, so that
+        // consecutive MMAs do not wait on each other's result
+        const uint32_t dt = tmem + 32u * TC_NACC * acc;
+        const uint64_t bdesc0 = tc::smem_desc(sb0 + b * g.bslot, 128u, (uint32_t)(jb.kpad / E) * 128u);
+        for (int c = 0; c < jb.nchunk; ++c) {
+          ok = tc::mbar_wait(full0 + 8 * s, round & 1);
+          if (!ok) break;
+          tc::fence_after_sync();
+          const uint64_t ad = tc::smem_desc(sa0 + s * chunk_bytes, 128u, sboA);
+          const uint64_t bd = bdesc0 + (uint64_t)(c * ((KC / E) * 128 / 16));  // + c * 1024 B
+          const uint32_t accum = c > 0 ? 1u : 0u;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) Dj[c + i] = v[i];
+          for (int q = 0; q < TC_NACC; ++q) {  // + 256 B per k-step: +16 in the address field
+            if (BF) tc::mma_f16(dt + 32u * q, ad + 16u * q, bd + 16u * q, idesc, accum);
+            else tc::mma_tf32(dt + 32u * q, ad + 16u * q, bd + 16u * q, idesc, accum);
+          }
+          tc::mma_commit(empty0 + 8 * s);
+          if (++s == S) {
+            s = 0;
+            ++round;
+          }
+        }
+        if (!ok) break;
+        tc::mma_commit(bempty0 + 8 * b);
+        tc::mma_commit(tfull0 + 8 * acc);
+      }
+      if (!ok) atomicExch(g.err, 4);
+      tc::mma_commit(fin);  // arrives once every MMA issued above has completed
     }
-  } else if (lane == 0) {
-    atomicExch(g.err, 2);
+  } else {
+    // epilogue: warp w reads TMEM lanes 32 w .. 32 w + 31 (rows of the job's D tile)
+    for (int i = 0; i < nj; ++i) {
+      const Job jb = g.jobs[blockIdx.x + i * gridDim.x];
+      const int acc = i & 1, u = i >> 1;
+      if (!tc::mbar_wait(tfull0 + 8 * acc, u & 1)) {
+        if (lane == 0) atomicExch(g.err, 2);
+        break;
+      }
+      tc::fence_after_sync();
+      float* Dj = g.D + jb.d_off + (size_t)(32 * warp + lane) * g.ncols;
+      for (int c = 0; c < g.ncols; c += 8) {
+        float v[8], w[8];
+        const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + 32u * TC_NACC * acc + c;
+        tc::tmem_ld8(ta, v);
+#pragma unroll
+        for (int a = 1; a < TC_NACC; ++a) {
+          tc::tmem_ld8(ta + 32u * a, w);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) v[q] += w[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) Dj[c + q] = v[q];
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(tempty0 + 8 * acc);
+    }
   }
+  // ---- teardown: no copy may land in, and no MMA may read, a CTA that has exited ----------
+  if (warp == 4 && lane == 0) {
+    // the newest fill of each stage / B buffer: completed fills return at once
+    for (long long q = a_issued - 1; q >= 0 && q >= a_issued - S; --q)
+      tc::mbar_wait(full0 + 8 * (int)(q % S), (uint32_t)((q / S) & 1), 200000u);
+    for (int q = b_issued - 1; q >= 0 && q >= b_issued - NB; --q)
+      tc::mbar_wait(bfull0 + 8 * (q % NB), (q / NB) & 1, 200000u);
+  }
+  if (warp == 5 && lane == 0) tc::mbar_wait(fin, 0, 4000000u);
   tc::fence_before_sync();
   __syncthreads();
-  if (tid < 32) tc::tmem_dealloc(tmem, ncols_alloc);
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, TC_TMEM_COLS);
 }
 
 // ---- canonical layout helpers ---------------------------------------------------------
@@ -338,7 +422,8 @@ struct TcLegendre {
   int njobs_s = 0, njobs_a = 0, njobs_sP = 0, njobs_aP = 0;
   int *dmap_s = nullptr, *dmap_a = nullptr;   // [(m*2+par)*ntile+tile][tab] -> D offset or -1
   int *boff_s = nullptr, *kpad_s = nullptr, *boff_a = nullptr;
-  size_t smem_s = 0, smem_a = 0;
+  int kpad_smax = 0;  // largest K extent of a synthesis B operand
+  int nsm = 0;
   StageProf* prof = nullptr;
 };
 
@@ -484,19 +569,15 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
     tc_legendre_destroy(t);
     return tc_fail("tensor-core Legendre table kernels", e);
   }
-  int kpad_max = 0;
-  for (int v : kpad_s) kpad_max = std::max(kpad_max, v);
-  auto smem_for = [&](int kp) {
-    return (size_t)TC_STAGES * chunk + ((size_t)ncols_max * kp * eb + 127) / 128 * 128 + 8 * (2 * TC_STAGES + 2) + 16;
-  };
-  t->smem_s = smem_for(kpad_max);
-  t->smem_a = smem_for(t->kpad_a);
-  const size_t smax = std::max(t->smem_s, t->smem_a);
-  if (smax > 220 * 1024) {
+  for (int v : kpad_s) t->kpad_smax = std::max(t->kpad_smax, v);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if ((e = cudaDeviceGetAttribute(&t->nsm, cudaDevAttrMultiProcessorCount, dev))) {
     tc_legendre_destroy(t);
-    return fail(REXI_EINVAL, "tensor-core Legendre: shared memory %zu bytes exceeds the limit", smax);
+    return tc_fail("cudaDeviceGetAttribute(SM count)", e);
   }
-  if ((e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax))) {
+  if ((e = cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_BUDGET)) ||
+      (e = cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_BUDGET))) {
     tc_legendre_destroy(t);
     return tc_fail("cudaFuncSetAttribute(k_tc_gemm)", e);
   }
@@ -524,9 +605,20 @@ static int gemm(TcLegendre* t, bool synth, bool both_tabs, int ncols, cudaStream
   g.ncols = ncols;
   g.bf16 = t->bf16;
   g.err = t->err;
+  // two B buffers of the largest B operand of the call, then as many A stages as fit
+  const size_t chunk = 128ull * t->KC * t->eb;
+  const size_t bslot = ((size_t)ncols * (synth ? t->kpad_smax : t->kpad_a) * t->eb + 127) / 128 * 128;
+  auto fixed = [&](int nb) { return nb * bslot + 8 * (2 * TC_MAXSTAGES + 2 * nb + 5) + 16; };
+  g.nb = (fixed(TC_MAXNB) + 4 * chunk <= TC_SMEM_BUDGET) ? TC_MAXNB : 2;
+  if (fixed(g.nb) + 2 * chunk > TC_SMEM_BUDGET) return fail(REXI_EINVAL, "tensor-core Legendre: B operand too large");
+  g.stages = (int)std::min<size_t>(TC_MAXSTAGES, (TC_SMEM_BUDGET - fixed(g.nb)) / chunk);
+  g.bslot = (uint32_t)bslot;
+  const size_t smem = (size_t)g.stages * chunk + g.nb * bslot + 8 * (2 * g.stages + 2 * g.nb + 5) + 16;
+  const int grid = std::max(1, std::min(g.njobs, t->nsm));
   {
     const int ph = t->prof ? t->prof->begin(2) : -1;
-    k_tc_gemm<<<g.njobs, 128, synth ? t->smem_s : t->smem_a, s>>>(g);
+    if (t->bf16) k_tc_gemm<true><<<grid, TC_THREADS, smem, s>>>(g);
+    else k_tc_gemm<false><<<grid, TC_THREADS, smem, s>>>(g);
     if (t->prof) t->prof->end(ph);
   }
   cudaError_t e = cudaGetLastError();
