@@ -52,6 +52,7 @@ struct GemmArgs {
   int njobs, ncols, bf16;
   int stages;       // A ring depth (<= TC_MAXSTAGES)
   int nb;           // B buffers (2 or 4): B operands are fetched up to nb - 1 jobs ahead
+  int nj_max;       // jobs per CTA at most (their descriptors are staged in shared memory)
   uint32_t bslot;   // bytes of one B buffer
   int* err;
 };
@@ -67,7 +68,8 @@ struct GemmArgs {
 // error code and stops, and teardown drains the copies and MMAs in flight.
 constexpr int TC_MAXNB = 4;
 constexpr int TC_NACC = 4;          // independent accumulators per job (one per k-step of a chunk)
-constexpr uint32_t TC_TMEM_COLS = 2 * TC_NACC * 32;  // two job buffers x TC_NACC x 32 columns
+constexpr int TC_NJB = 3;           // job buffers of accumulators in TMEM
+constexpr uint32_t TC_TMEM_COLS = 512;  // >= TC_NJB x TC_NACC x 32 columns, a power of two
 template <bool BF>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(GemmArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -81,17 +83,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(GemmArgs g) {
   unsigned char* sA = smem;
   unsigned char* sB = smem + (size_t)S * chunk_bytes;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sB + (size_t)NB * g.bslot);
-  // barriers: full[S], empty[S], bfull[NB], bempty[NB], tfull[2], tempty[2], fin
+  // barriers: full[S], empty[S], bfull[NB], bempty[NB], tfull[NJB], tempty[NJB], fin
   const uint32_t full0 = tc::smem_u32(bars), empty0 = full0 + 8 * S;
   const uint32_t bfull0 = empty0 + 8 * S, bempty0 = bfull0 + 8 * NB, tfull0 = bempty0 + 8 * NB;
-  const uint32_t tempty0 = tfull0 + 16, fin = tempty0 + 16;
-  uint32_t* taddr_s = reinterpret_cast<uint32_t*>(bars + 2 * S + 2 * NB + 5);
-  // jobs of this CTA: blockIdx.x + i * gridDim.x, i < nj
+  const uint32_t tempty0 = tfull0 + 8 * TC_NJB, fin = tempty0 + 8 * TC_NJB;
+  uint32_t* taddr_s = reinterpret_cast<uint32_t*>(bars + 2 * S + 2 * NB + 2 * TC_NJB + 1);
+  Job* sjobs = reinterpret_cast<Job*>(bars + 2 * S + 2 * NB + 2 * TC_NJB + 2);
+  // jobs of this CTA: blockIdx.x + i * gridDim.x, i < nj; descriptors staged in shared memory
   const int nj = blockIdx.x < g.njobs ? (g.njobs - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  for (int i = tid; i < nj && i < g.nj_max; i += blockDim.x) sjobs[i] = g.jobs[blockIdx.x + i * gridDim.x];
   if (tid == 0) {
-    for (int i = 0; i < 2 * S + 2 * NB + 2; ++i) tc::mbar_init(full0 + 8 * i, 1);
-    tc::mbar_init(tempty0, 4);
-    tc::mbar_init(tempty0 + 8, 4);
+    for (int i = 0; i < 2 * S + 2 * NB + TC_NJB; ++i) tc::mbar_init(full0 + 8 * i, 1);
+    for (int i = 0; i < TC_NJB; ++i) tc::mbar_init(tempty0 + 8 * i, 4);
     tc::mbar_init(fin, 1);
     tc::mbar_fence_init();
   }
@@ -108,22 +111,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(GemmArgs g) {
   if (warp == 4) {
     if (lane == 0) {
       bool ok = true;
-      // B operand of job q into buffer q % NB (its previous user, job q - NB, must be done)
+      // B operand of job q into buffer q % NB once its previous user, job q - NB, is done:
+      // between A chunks whenever that is already so (non-blocking test), and blocking only
+      // when the next job would otherwise lack its operand
+      int nb_next = 0;  // next job whose B operand is not issued
       auto issue_b = [&](int q) {
-        const int b = q % NB, u = q / NB;
-        if (u > 0 && !tc::mbar_wait(bempty0 + 8 * b, (u - 1) & 1)) return false;
-        const Job jq = g.jobs[blockIdx.x + q * gridDim.x];
+        const int b = q % NB;
+        const Job jq = sjobs[q];
         const uint32_t bb = (uint32_t)g.ncols * jq.kpad * eb;
         tc::mbar_expect_tx(bfull0 + 8 * b, bb);
         tc::bulk_g2s(sb0 + b * g.bslot, g.B + jq.b_off, bb, bfull0 + 8 * b);
         ++b_issued;
-        return true;
+        ++nb_next;
       };
-      for (int q = 0; q < NB - 1 && q < nj && ok; ++q) ok = issue_b(q);
+      auto try_b = [&]() {
+        while (nb_next < nj) {
+          const int u = nb_next / NB;
+          if (u > 0 && !tc::mbar_test(bempty0 + 8 * (nb_next % NB), (u - 1) & 1)) return;
+          issue_b(nb_next);
+        }
+      };
+      try_b();
       int s = 0;
       uint32_t round = 0;  // number of completed passes over the ring
       for (int i = 0; i < nj && ok; ++i) {
-        const Job jb = g.jobs[blockIdx.x + i * gridDim.x];
+        if (nb_next <= i) {  // job i's operand must be on its way before its chunks
+          const int u = i / NB;
+          ok = u == 0 || tc::mbar_wait(bempty0 + 8 * (i % NB), (u - 1) & 1);
+          if (!ok) break;
+          issue_b(i);
+        }
+        const Job jb = sjobs[i];
         const unsigned char* A = (jb.tab ? g.tabH : g.tabP) + jb.a_off;
         for (int c = 0; c < jb.nchunk; ++c) {
           if (round > 0) ok = tc::mbar_wait(empty0 + 8 * s, (round - 1) & 1);
@@ -135,8 +153,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(GemmArgs g) {
             s = 0;
             ++round;
           }
+          try_b();
         }
-        if (ok && i + NB - 1 < nj) ok = issue_b(i + NB - 1);
       }
       if (!ok) atomicExch(g.err, 3);
     }
@@ -148,8 +166,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(GemmArgs g) {
       int s = 0;
       uint32_t round = 0;
       for (int i = 0; i < nj && ok; ++i) {
-        const Job jb = g.jobs[blockIdx.x + i * gridDim.x];
-        const int b = i % NB, ub = i / NB, acc = i & 1, ua = i >> 1;
+        const Job jb = sjobs[i];
+        const int b = i % NB, ub = i / NB, acc = i % TC_NJB, ua = i / TC_NJB;
         ok = tc::mbar_wait(bfull0 + 8 * b, ub & 1);
         if (ok && ua > 0) ok = tc::mbar_wait(tempty0 + 8 * acc, (ua - 1) & 1);
         if (!ok) break;
@@ -184,28 +202,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(GemmArgs g) {
       tc::mma_commit(fin);  // arrives once every MMA issued above has completed
     }
   } else {
-    // epilogue: warp w reads TMEM lanes 32 w .. 32 w + 31 (rows of the job's D tile)
+    // epilogue: warp w reads TMEM lanes 32 w .. 32 w + 31 (rows of the job's D tile); all
+    // loads of a 16-column group are issued before one wait
     for (int i = 0; i < nj; ++i) {
-      const Job jb = g.jobs[blockIdx.x + i * gridDim.x];
-      const int acc = i & 1, u = i >> 1;
+      const Job jb = sjobs[i];
+      const int acc = i % TC_NJB, u = i / TC_NJB;
       if (!tc::mbar_wait(tfull0 + 8 * acc, u & 1)) {
         if (lane == 0) atomicExch(g.err, 2);
         break;
       }
       tc::fence_after_sync();
       float* Dj = g.D + jb.d_off + (size_t)(32 * warp + lane) * g.ncols;
-      for (int c = 0; c < g.ncols; c += 8) {
-        float v[8], w[8];
+      for (int c = 0; c < g.ncols; c += 16) {
+        uint32_t r[TC_NACC][16];
         const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + 32u * TC_NACC * acc + c;
-        tc::tmem_ld8(ta, v);
 #pragma unroll
-        for (int a = 1; a < TC_NACC; ++a) {
-          tc::tmem_ld8(ta + 32u * a, w);
-#pragma unroll
-          for (int q = 0; q < 8; ++q) v[q] += w[q];
+        for (int a = 0; a < TC_NACC; ++a) {
+          tc::tmem_ld8_nowait(ta + 32u * a, r[a]);
+          tc::tmem_ld8_nowait(ta + 32u * a + 8, r[a] + 8);
         }
+        tc::tmem_wait_ld();
+        float v[16];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) Dj[c + q] = v[q];
+        for (int q = 0; q < 16; ++q) {
+          v[q] = __uint_as_float(r[0][q]);
+#pragma unroll
+          for (int a = 1; a < TC_NACC; ++a) v[q] += __uint_as_float(r[a][q]);
+        }
+        float4* d4 = reinterpret_cast<float4*>(Dj + c);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
       }
       tc::fence_before_sync();
       __syncwarp();
@@ -608,13 +634,16 @@ static int gemm(TcLegendre* t, bool synth, bool both_tabs, int ncols, cudaStream
   // two B buffers of the largest B operand of the call, then as many A stages as fit
   const size_t chunk = 128ull * t->KC * t->eb;
   const size_t bslot = ((size_t)ncols * (synth ? t->kpad_smax : t->kpad_a) * t->eb + 127) / 128 * 128;
-  auto fixed = [&](int nb) { return nb * bslot + 8 * (2 * TC_MAXSTAGES + 2 * nb + 5) + 16; };
+  const int grid = std::max(1, std::min(g.njobs, t->nsm));
+  g.nj_max = (g.njobs + grid - 1) / grid;
+  const size_t jobs_bytes = sizeof(Job) * (size_t)g.nj_max;
+  auto fixed = [&](int nb) { return nb * bslot + 8 * (2 * TC_MAXSTAGES + 2 * nb + 2 * TC_NJB + 2) + jobs_bytes; };
   g.nb = (fixed(TC_MAXNB) + 4 * chunk <= TC_SMEM_BUDGET) ? TC_MAXNB : 2;
   if (fixed(g.nb) + 2 * chunk > TC_SMEM_BUDGET) return fail(REXI_EINVAL, "tensor-core Legendre: B operand too large");
   g.stages = (int)std::min<size_t>(TC_MAXSTAGES, (TC_SMEM_BUDGET - fixed(g.nb)) / chunk);
   g.bslot = (uint32_t)bslot;
-  const size_t smem = (size_t)g.stages * chunk + g.nb * bslot + 8 * (2 * g.stages + 2 * g.nb + 5) + 16;
-  const int grid = std::max(1, std::min(g.njobs, t->nsm));
+  const size_t smem =
+      (size_t)g.stages * chunk + g.nb * bslot + 8 * (2 * g.stages + 2 * g.nb + 2 * TC_NJB + 2) + jobs_bytes;
   {
     const int ph = t->prof ? t->prof->begin(2) : -1;
     if (t->bf16) k_tc_gemm<true><<<grid, TC_THREADS, smem, s>>>(g);
