@@ -30,6 +30,17 @@ METRIC = "REXI steps/s at T255, batched/mixed vs plain FP64 at ≤1e-8 rel err; 
 T_DEF, N_DEF, DT_DEF, B_DEF = 255, 512, 3600.0, 16
 SAMPLE_M = list(range(0, 256, 2))      # cpu_baseline sample: every second zonal order
 
+# Algorithmic flops (FMA = 2) per chain element and pole of the solve kernels, and the pipe
+# they run on.  Light (FP32 Thomas, FP32 pole sums) and FP64 paths: forward elimination 22,
+# back substitution 8, right-hand side and diagonal 7, weighted pole sums 12.  Heavy (FP32
+# solve + one refinement step): FP32 factor and solve 38, residual r - A x in double-float
+# arithmetic 228 (zeta rows 165, delta rows 291), correction solve 20, double-float pole sums 90.
+KERNEL_FLOPS = {"k_rexi_light": (49.0, "fp32"), "k_rexi_heavy": (376.0, "fp32"),
+                "k_rexi_fp64": (49.0, "fp64")}
+# DRAM bytes (read + write) of one launch from an ncu capture: (bytes, batch of that launch,
+# summary file).  Only for kernels unchanged since the capture.
+TRAFFIC = {"k_rexi_heavy": (8.80e9, 16, "profiles/rexi_solve_T255_B16.md")}
+
 
 def ref_step_m(T):
     """--impl reference: the four zonal orders solved per step (spread over 0..T)."""
@@ -511,29 +522,30 @@ def main():
     fp64_bb = timed(fp64, u0, u1, B, ks, 1)
     mix_b1 = timed(mixed, u0[:1].contiguous(), u1[:1].contiguous(), 1, ks, 2)
 
-    # ---- roofline of the dominant kernel (event times of the timed region) ---------------
+    # ---- rooflines of the solve kernels (event times of the timed region) -----------------
     info = mixed.info()
     n_light = N - info["n_heavy"]
     elems = 2 * nlm * B  # chain elements per pole per launch (two parity chains per m)
-    # algorithmic flops per chain element (FMA = 2): forward elimination 22, back
-    # substitution 8, right-hand side and diagonal 7, weighted pole sums 12
-    FLOPS_SOLVE = 49.0
-    kname, (kms, kn) = max(((k, v) for k, v in prof.items() if v[1] > 0), key=lambda kv: kv[1][0])
-    if kname == "k_rexi_light":
-        flops = FLOPS_SOLVE * elems * n_light
-        peak, ptype = fp32_tf, "fp32"
-    elif kname == "k_rexi_heavy":
-        flops = 14.0 * elems * info["n_heavy"]   # FP64: pole sums 12 + refinement update 2
-        peak, ptype = fp64_tf, "fp64"
-    else:
-        flops = FLOPS_SOLVE * elems * N
-        peak, ptype = fp64_tf, "fp64"
-    avg_s = kms / kn * 1e-3
-    achieved = flops / avg_s / 1e12
-    roof = {"bound": "alu", "kernel": kname, "pipe": ptype, "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-            "peak_source": "measured %s FMA probe (rexi_alu_peaks) in this run" % ptype,
-            "kernel_ms": {k: (v[0] / v[1] if v[1] else None) for k, v in prof.items()}}
+    kernels = {}
+    for kname, (kms, kn) in prof.items():
+        if kn == 0 or kname not in KERNEL_FLOPS:
+            continue
+        fl, pipe = KERNEL_FLOPS[kname]
+        npoles = n_light if kname == "k_rexi_light" else info["n_heavy"]
+        flops = fl * elems * npoles
+        avg_s = kms / kn * 1e-3
+        peak = fp32_tf if pipe == "fp32" else fp64_tf
+        kernels[kname] = {"bound": "alu", "pipe": pipe, "flops_per_chain_element": fl, "poles": npoles,
+                          "ms": kms / kn, "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                          "frac": flops / avg_s / 1e12 / peak}
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    tr = TRAFFIC.get(dom)
+    roof = dict(kernels[dom], kernel=dom,
+                traffic=(tr[0] * B / tr[1]) if tr else None,
+                traffic_source=tr[2] if tr else None,
+                peak_source="measured %s FMA probe (rexi_alu_peaks) in this run" % kernels[dom]["pipe"],
+                kernel_ms={k: (v[0] / v[1] if v[1] else None) for k, v in prof.items()},
+                kernels=kernels)
 
     # ---- end to end through the C ABI with host buffers ---------------------------------
     hin = torch.from_numpy(host).pin_memory()
