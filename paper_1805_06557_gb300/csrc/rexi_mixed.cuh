@@ -24,7 +24,6 @@
 namespace rexi {
 
 constexpr int MIX_WARPS = 4;
-constexpr int SEG = 16;        // transposition block of the heavy path
 constexpr int LTROW = 33;      // padded row (float2) of the light transposition tile
 
 // ---- double-float arithmetic (value = hi + lo, |lo| <= ulp(hi)/2) --------------------
@@ -370,23 +369,122 @@ __device__ __forceinline__ float2 heavy_residual(const MixedArgs& a, const PoleD
   return make_float2(re.hi + re.lo, im.hi + im.lo);
 }
 
-static __global__ void __launch_bounds__(MIX_WARPS * 32)
+// FP32 pivot recurrence of a chain at element k: returns the inverse pivot 1/(d_k - lo_k ct_{k-1})
+// and advances ct to ct_k = up_k / pivot (the LU form of Thomas elimination).
+__device__ __forceinline__ float2 heavy_pivot(const float4 tb, const PoleF& pf, bool isZ, float2& ct) {
+  const float lo = isZ ? tb.y : -tb.y;
+  const float up = isZ ? tb.z : -tb.z;
+  float2 d;
+  if (isZ) d = make_float2(pf.z.x, pf.z.y - tb.x);
+  else d = make_float2(fmaf(tb.w, pf.gz.x, pf.z.x), fmaf(tb.w, pf.gz.y, pf.z.y - tb.x));
+  const float2 den = make_float2(fmaf(-lo, ct.x, d.x), fmaf(-lo, ct.y, d.y));
+  const float2 inv = crcpf(den);
+  ct = make_float2(up * inv.x, up * inv.y);
+  return inv;
+}
+
+// One forward step of the FP32 chain solve at element k: advances (ct, y), returns the pivot.
+__device__ __forceinline__ float2 heavy_fwd(const MixedArgs& a, const PoleF& pf, const Rhs32* rb, int off,
+                                            int toff, int k, int c, float2& ct, float2& y) {
+  const float4 tb = __ldg(a.tab32 + toff + k);
+  const Rhs32 rr = rb[off + k];
+  const bool isZ = ((k & 1) == c);
+  const float lo = isZ ? tb.y : -tb.y;
+  const float2 r = isZ ? rr.bz : cfmaf(pf.iz, rr.qbp, rr.bd);
+  const float2 inv = heavy_pivot(tb, pf, isZ, ct);
+  y = cmulf(make_float2(fmaf(-lo, y.x, r.x), fmaf(-lo, y.y, r.y)), inv);
+  return inv;
+}
+
+constexpr int HSEG = 8;    // heavy: checkpoint interval (segments recomputed in registers)
+constexpr int HBLK = 16;   // heavy: rows per transposition block of the pole sums
+
+// Heavy per-warp scratch in float2 units: checkpoints [nseg][32] float4, then the bottom-up
+// elimination of the correction g[kmax][32], h[kmax][32].
+__host__ __device__ inline size_t heavy_scratch_f2_per_warp(int kmax, int nseg_max) {
+  return (size_t)nseg_max * 32 * 2 + (size_t)kmax * 32 * 2;
+}
+
+// Pole sums of one transposition block: lane (r, h) sums row kb + r over the 16 poles of half
+// h; dfsum: double-float products with the double-float weights (the solution x), else FP32
+// (the small correction); the halves are combined in FP64 by a shuffle and added into the
+// tile's FP64 partial slots (written when first = true).
+__device__ __forceinline__ void heavy_block_sum(const float2* tile, const float4* s_w, const float4* s_wz, int kb,
+                                                int K, int c, int lane, bool dfsum, bool first, double2* part,
+                                                int off, int nlm) {
+  const int r = lane & 15, h = lane >> 4;
+  const int kk = kb + r;
+  const bool valid = kk < K;
+  const bool isD = ((kk & 1) != c);
+  double2 acc = make_double2(0.0, 0.0), acc2 = make_double2(0.0, 0.0);
+  if (valid) {
+    if (dfsum) {
+      float4 f1 = make_float4(0.f, 0.f, 0.f, 0.f), f2 = f1;
+#pragma unroll 4
+      for (int p = 16 * h; p < 16 * h + 16; ++p) {
+        const float2 v = tile[r * LTROW + p];
+        const float4 vv = make_float4(v.x, 0.f, v.y, 0.f);
+        dfc_acc(f1, s_w[p], vv);
+        if (isD) dfc_acc(f2, s_wz[p], vv);
+      }
+      acc = make_double2((double)f1.x + (double)f1.y, (double)f1.z + (double)f1.w);
+      acc2 = make_double2((double)f2.x + (double)f2.y, (double)f2.z + (double)f2.w);
+    } else {
+      float2 g1 = make_float2(0.f, 0.f), g2 = g1;
+#pragma unroll 4
+      for (int p = 16 * h; p < 16 * h + 16; ++p) {
+        const float2 v = tile[r * LTROW + p];
+        const float4 w = s_w[p];
+        g1 = cfmaf(make_float2(w.x, w.z), v, g1);
+        if (isD) {
+          const float4 wz = s_wz[p];
+          g2 = cfmaf(make_float2(wz.x, wz.z), v, g2);
+        }
+      }
+      acc = make_double2((double)g1.x, (double)g1.y);
+      acc2 = make_double2((double)g2.x, (double)g2.y);
+    }
+  }
+  acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
+  acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
+  acc2.x += __shfl_xor_sync(0xffffffffu, acc2.x, 16);
+  acc2.y += __shfl_xor_sync(0xffffffffu, acc2.y, 16);
+  if (h == 0 && valid) {
+    double2* dst = part + (isD ? nlm : 0) + off + kk;
+    *dst = first ? acc : cadd(*dst, acc);
+    if (isD) {
+      double2* dst2 = part + 2 * nlm + off + kk;
+      *dst2 = first ? acc2 : cadd(*dst2, acc2);
+    }
+  }
+}
+
+// Heavy poles: FP32 LU solve with checkpoints (pass A, upward); pass B (downward) recomputes
+// each 8-element segment into a per-warp shared buffer, back-substitutes x, forms the residual
+// r - A x of element k + 1 in double-float once x_k is known, and eliminates the correction
+// system bottom-up (UL form of Thomas: p_k = d_k - up_k g_{k+1}, g_k = lo_k / p_k,
+// h_k = (res_k - up_k h_{k+1}) / p_k), storing g and h; pass C (upward) completes the
+// correction dx_k = h_k - g_k dx_{k-1}.  Pole sums: x in double-float in pass B, dx in FP32
+// in pass C (|dx| ~ 1e-6 |x|).  All loops stay rolled so that the residual's code exists once.
+static __global__ void __launch_bounds__(MIX_WARPS * 32, 4)
 k_rexi_heavy(MixedArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  // transposition tile of 16 rows x 33 (float4: x and its correction, re and im) per warp,
-  // then the pole weights w and w/z in double-float
-  float4* s_tile = reinterpret_cast<float4*>(smem_raw) + wib * (SEG * FP64_TROW);
-  float4* s_w = reinterpret_cast<float4*>(smem_raw) + MIX_WARPS * SEG * FP64_TROW + wib * 64;
+  // per warp: transposition tile [HBLK][LTROW] float2, the double-float weights w, w/z, and
+  // the recomputed segment [HSEG][32] float4 (inverse pivot, forward value)
+  float2* s_tile = reinterpret_cast<float2*>(smem_raw) + wib * (HBLK * LTROW);
+  float4* s_w = reinterpret_cast<float4*>(smem_raw + (size_t)MIX_WARPS * HBLK * LTROW * sizeof(float2)) + wib * 64;
   float4* s_wz = s_w + 32;
+  float4* s_seg = reinterpret_cast<float4*>(smem_raw + (size_t)MIX_WARPS * HBLK * LTROW * sizeof(float2) +
+                                            (size_t)MIX_WARPS * 64 * sizeof(float4)) + wib * (HSEG * 32);
   const int gw = blockIdx.x * MIX_WARPS + wib;
   const int W = gridDim.x * MIX_WARPS;
-  // heavy scratch: after the light checkpoints; per warp S1 [kmax][32] float4, S2 [kmax][32] float2
-  char* base = reinterpret_cast<char*>(a.scratch) +
-               (size_t)a.warps_light * light_ckpt_f4_per_warp(a.nseg_max) * sizeof(float4) +
-               (size_t)gw * a.kmax * 32 * (sizeof(float4) + sizeof(float2));
-  float4* S1 = reinterpret_cast<float4*>(base);
-  float2* S2 = reinterpret_cast<float2*>(base + (size_t)a.kmax * 32 * sizeof(float4));
+  float2* hs = reinterpret_cast<float2*>(reinterpret_cast<char*>(a.scratch) +
+                                         (size_t)a.warps_light * light_ckpt_f4_per_warp(a.nseg_max) * sizeof(float4)) +
+               (size_t)gw * heavy_scratch_f2_per_warp(a.kmax, a.nseg_max);
+  float4* ck = reinterpret_cast<float4*>(hs);
+  float2* Gs = hs + (size_t)a.nseg_max * 64;
+  float2* Hs = Gs + (size_t)a.kmax * 32;
   const int total = a.ntiles_heavy;
 
   for (int round = 0; round * W < total; ++round) {
@@ -407,103 +505,83 @@ k_rexi_heavy(MixedArgs a) {
       __syncwarp();
       s_w[lane] = pq.w;
       s_wz[lane] = pq.wz;
-      // ---- A: FP32 forward, store (inv, y) ------------------------------------------
-      float2 ct = make_float2(0.f, 0.f), y = make_float2(0.f, 0.f);
-#pragma unroll 4
-      for (int k = 0; k < K; ++k) {
-        const float4 tb = __ldg(a.tab32 + toff + k);
-        const Rhs32 rr = rb[off + k];
-        const bool isZ = ((k & 1) == c);
-        const float lo = isZ ? tb.y : -tb.y;
-        const float up = isZ ? tb.z : -tb.z;
-        float2 d, r;
-        if (isZ) {
-          d = make_float2(pf.z.x, pf.z.y - tb.x);
-          r = rr.bz;
-        } else {
-          d = make_float2(fmaf(tb.w, pf.gz.x, pf.z.x), fmaf(tb.w, pf.gz.y, pf.z.y - tb.x));
-          r = cfmaf(pf.iz, rr.qbp, rr.bd);
+      // ---- A: FP32 forward sweep, checkpoint (ct, y) after every full segment ---------------
+      {
+        float2 ct = make_float2(0.f, 0.f), y = make_float2(0.f, 0.f);
+#pragma unroll 1
+        for (int k = 0; k < K; ++k) {
+          heavy_fwd(a, pf, rb, off, toff, k, c, ct, y);
+          if ((k % HSEG) == HSEG - 1 && k + 1 < K)
+            ck[(size_t)(k / HSEG) * 32 + lane] = make_float4(ct.x, ct.y, y.x, y.y);
         }
-        const float2 den = make_float2(fmaf(-lo, ct.x, d.x), fmaf(-lo, ct.y, d.y));
-        const float2 inv = crcpf(den);
-        ct = make_float2(up * inv.x, up * inv.y);
-        y = cmulf(make_float2(fmaf(-lo, y.x, r.x), fmaf(-lo, y.y, r.y)), inv);
-        S1[(size_t)k * 32 + lane] = make_float4(inv.x, inv.y, y.x, y.y);
       }
-      // ---- A: back substitution, store x -------------------------------------------
-      float2 xn = make_float2(0.f, 0.f);
-#pragma unroll 4
-      for (int k = K - 1; k >= 0; --k) {
-        const float4 s = S1[(size_t)k * 32 + lane];
-        const float4 tb = __ldg(a.tab32 + toff + k);
-        const float up = ((k & 1) == c) ? tb.z : -tb.z;
-        const float2 cc = make_float2(up * s.x, up * s.y);
-        const float2 x = make_float2(s.z - fmaf(cc.x, xn.x, -cc.y * xn.y),
-                                     s.w - fmaf(cc.x, xn.y, cc.y * xn.x));
-        S2[(size_t)k * 32 + lane] = x;
-        xn = x;
+      // ---- B: downward; e = -1 only finalises element 0 ----------------------------------
+      float2 x1 = make_float2(0.f, 0.f), x2 = make_float2(0.f, 0.f);  // x_{e+1}, x_{e+2}
+      float2 gU = make_float2(0.f, 0.f), hU = make_float2(0.f, 0.f);  // g, h of element e + 2
+#pragma unroll 1
+      for (int e = K - 1; e >= -1; --e) {
+        float2 x0 = make_float2(0.f, 0.f);
+        if (e >= 0) {
+          const int i = e % HSEG;
+          if (e == K - 1 || i == HSEG - 1) {  // entering a segment from above: recompute it
+            const int s = e / HSEG;
+            float2 cs = make_float2(0.f, 0.f), ys = make_float2(0.f, 0.f);
+            if (s > 0) {
+              const float4 st = ck[(size_t)(s - 1) * 32 + lane];
+              cs = make_float2(st.x, st.y);
+              ys = make_float2(st.z, st.w);
+            }
+#pragma unroll 1
+            for (int k = s * HSEG; k <= e; ++k) {
+              const float2 inv = heavy_fwd(a, pf, rb, off, toff, k, c, cs, ys);
+              s_seg[(k % HSEG) * 32 + lane] = make_float4(inv.x, inv.y, ys.x, ys.y);
+            }
+          }
+          const float4 sv = s_seg[i * 32 + lane];
+          const float4 tb = __ldg(a.tab32 + toff + e);
+          const float up = ((e & 1) == c) ? tb.z : -tb.z;
+          const float2 cc = make_float2(up * sv.x, up * sv.y);
+          x0 = make_float2(sv.z - fmaf(cc.x, x1.x, -cc.y * x1.y), sv.w - fmaf(cc.x, x1.y, cc.y * x1.x));
+          s_tile[(e % HBLK) * LTROW + lane] = x0;
+        }
+        if (e + 1 < K) {  // element k = e + 1: residual with x_{k-1} = x0, x_k = x1, x_{k+1} = x2
+          const int k = e + 1;
+          const float2 res = heavy_residual(a, pq, rbd, off, toff, k, K, c, x0, x1, x2);
+          const float4 tb = __ldg(a.tab32 + toff + k);
+          const bool isZ = ((k & 1) == c);
+          const float lo = isZ ? tb.y : -tb.y;
+          const float up = isZ ? tb.z : -tb.z;
+          float2 d;
+          if (isZ) d = make_float2(pf.z.x, pf.z.y - tb.x);
+          else d = make_float2(fmaf(tb.w, pf.gz.x, pf.z.x), fmaf(tb.w, pf.gz.y, pf.z.y - tb.x));
+          const float2 den = make_float2(fmaf(-up, gU.x, d.x), fmaf(-up, gU.y, d.y));
+          const float2 inv = crcpf(den);
+          gU = make_float2(lo * inv.x, lo * inv.y);
+          hU = cmulf(make_float2(fmaf(-up, hU.x, res.x), fmaf(-up, hU.y, res.y)), inv);
+          Gs[(size_t)k * 32 + lane] = gU;
+          Hs[(size_t)k * 32 + lane] = hU;
+        }
+        if (e >= 0) {
+          if ((e % HBLK) == 0) {
+            __syncwarp();
+            heavy_block_sum(s_tile, s_w, s_wz, e, K, c, lane, true, gi == 0, part, off, nlm);
+            __syncwarp();
+          }
+          x2 = x1;
+          x1 = x0;
+        }
       }
-      // ---- B: double-float residual and forward sweep of the correction ---------------
-      float2 xm = make_float2(0.f, 0.f), x0 = S2[lane];
-      float2 yc = make_float2(0.f, 0.f);
-#pragma unroll 4
+      // ---- C: upward: dx_k = h_k - g_k dx_{k-1}, FP32 pole sums of dx ----------------------
+      float2 dxm = make_float2(0.f, 0.f);
+#pragma unroll 1
       for (int k = 0; k < K; ++k) {
-        const float2 xp = (k + 1 < K) ? S2[(size_t)(k + 1) * 32 + lane] : make_float2(0.f, 0.f);
-        const float2 res = heavy_residual(a, pq, rbd, off, toff, k, K, c, xm, x0, xp);
-        const float4 tb = __ldg(a.tab32 + toff + k);
-        const float lo = ((k & 1) == c) ? tb.y : -tb.y;
-        const float4 s = S1[(size_t)k * 32 + lane];
-        const float2 inv = make_float2(s.x, s.y);
-        yc = cmulf(make_float2(fmaf(-lo, yc.x, res.x), fmaf(-lo, yc.y, res.y)), inv);
-        S1[(size_t)k * 32 + lane] = make_float4(s.x, s.y, yc.x, yc.y);
-        xm = x0;
-        x0 = xp;
-      }
-      // ---- C: back substitution of the correction, weighted sums ---------------------
-      // 16-row blocks: lane (r, h) sums row r over the 16 poles of half h in double-float
-      // (v = x + dx kept as the pair (x, dx)); the halves are converted to FP64 and combined
-      // by a shuffle, then added into the tile's FP64 partial sums.
-      float2 dn = make_float2(0.f, 0.f);
-#pragma unroll 4
-      for (int k = K - 1; k >= 0; --k) {
-        const float4 s = S1[(size_t)k * 32 + lane];
-        const float4 tb = __ldg(a.tab32 + toff + k);
-        const float2 x = S2[(size_t)k * 32 + lane];
-        const float up = ((k & 1) == c) ? tb.z : -tb.z;
-        const float2 cc = make_float2(up * s.x, up * s.y);
-        const float2 dx = make_float2(s.z - fmaf(cc.x, dn.x, -cc.y * dn.y),
-                                      s.w - fmaf(cc.x, dn.y, cc.y * dn.x));
-        dn = dx;
-        s_tile[(k & (SEG - 1)) * FP64_TROW + lane] = make_float4(x.x, dx.x, x.y, dx.y);
-        if ((k & (SEG - 1)) == 0) {
+        const float2 g = Gs[(size_t)k * 32 + lane], h = Hs[(size_t)k * 32 + lane];
+        const float2 dx = make_float2(h.x - fmaf(g.x, dxm.x, -g.y * dxm.y), h.y - fmaf(g.x, dxm.y, g.y * dxm.x));
+        dxm = dx;
+        s_tile[(k % HBLK) * LTROW + lane] = dx;
+        if ((k % HBLK) == HBLK - 1 || k == K - 1) {
           __syncwarp();
-          const int r = lane & 15, h = lane >> 4;
-          const int kk = k + r;
-          const bool valid = kk < K;
-          const bool isD = ((kk & 1) != c);
-          float4 f1 = make_float4(0.f, 0.f, 0.f, 0.f), f2 = f1;
-          if (valid) {
-#pragma unroll 4
-            for (int p = 16 * h; p < 16 * h + 16; ++p) {
-              const float4 v = s_tile[r * FP64_TROW + p];
-              dfc_acc(f1, s_w[p], v);
-              if (isD) dfc_acc(f2, s_wz[p], v);
-            }
-          }
-          double2 acc = make_double2((double)f1.x + (double)f1.y, (double)f1.z + (double)f1.w);
-          double2 acc2 = make_double2((double)f2.x + (double)f2.y, (double)f2.z + (double)f2.w);
-          acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
-          acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
-          acc2.x += __shfl_xor_sync(0xffffffffu, acc2.x, 16);
-          acc2.y += __shfl_xor_sync(0xffffffffu, acc2.y, 16);
-          if (h == 0 && valid) {
-            double2* dst = part + (isD ? nlm : 0) + off + kk;
-            *dst = (gi == 0) ? acc : cadd(*dst, acc);
-            if (isD) {
-              double2* dst2 = part + 2 * nlm + off + kk;
-              *dst2 = (gi == 0) ? acc2 : cadd(*dst2, acc2);
-            }
-          }
+          heavy_block_sum(s_tile, s_w, s_wz, k - (k % HBLK), K, c, lane, false, false, part, off, nlm);
           __syncwarp();
         }
       }
@@ -512,7 +590,8 @@ k_rexi_heavy(MixedArgs a) {
 }
 
 inline size_t heavy_smem_bytes() {
-  return sizeof(float4) * (MIX_WARPS * SEG * FP64_TROW + MIX_WARPS * 64);
+  return sizeof(float2) * MIX_WARPS * HBLK * LTROW + sizeof(float4) * MIX_WARPS * 64 +
+         sizeof(float4) * MIX_WARPS * HSEG * 32;
 }
 
 }  // namespace rexi
