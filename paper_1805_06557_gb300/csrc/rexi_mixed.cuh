@@ -466,7 +466,7 @@ __device__ __forceinline__ void heavy_block_sum(const float2* tile, const float4
 // h_k = (res_k - up_k h_{k+1}) / p_k), storing g and h; pass C (upward) completes the
 // correction dx_k = h_k - g_k dx_{k-1}.  Pole sums: x in double-float in pass B, dx in FP32
 // in pass C (|dx| ~ 1e-6 |x|).  All loops stay rolled so that the residual's code exists once.
-static __global__ void __launch_bounds__(MIX_WARPS * 32, 5)
+static __global__ void __launch_bounds__(MIX_WARPS * 32, 6)
 k_rexi_heavy(MixedArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
