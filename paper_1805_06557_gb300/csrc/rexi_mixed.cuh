@@ -396,13 +396,14 @@ __device__ __forceinline__ float2 heavy_fwd(const MixedArgs& a, const PoleF& pf,
   return inv;
 }
 
-constexpr int HSEG = 8;    // heavy: checkpoint interval (segments recomputed in registers)
+constexpr int HSEG = 8;    // heavy: checkpoint interval (segments recomputed into shared memory)
 constexpr int HBLK = 16;   // heavy: rows per transposition block of the pole sums
 
-// Heavy per-warp scratch in float2 units: checkpoints [nseg][32] float4, then the bottom-up
-// elimination of the correction g[kmax][32], h[kmax][32].
-__host__ __device__ inline size_t heavy_scratch_f2_per_warp(int kmax, int nseg_max) {
-  return (size_t)nseg_max * 32 * 2 + (size_t)kmax * 32 * 2;
+// Heavy per-warp scratch in float2 units: checkpoints [ceil(kmax / HSEG)][32] float4, then the
+// bottom-up elimination of the correction g[kmax][32], h[kmax][32].
+__host__ __device__ inline int heavy_nseg(int kmax) { return (kmax + HSEG - 1) / HSEG; }
+__host__ __device__ inline size_t heavy_scratch_f2_per_warp(int kmax) {
+  return (size_t)heavy_nseg(kmax) * 32 * 2 + (size_t)kmax * 32 * 2;
 }
 
 // Pole sums of one transposition block: lane (r, h) sums row kb + r over the 16 poles of half
@@ -481,9 +482,9 @@ k_rexi_heavy(MixedArgs a) {
   const int W = gridDim.x * MIX_WARPS;
   float2* hs = reinterpret_cast<float2*>(reinterpret_cast<char*>(a.scratch) +
                                          (size_t)a.warps_light * light_ckpt_f4_per_warp(a.nseg_max) * sizeof(float4)) +
-               (size_t)gw * heavy_scratch_f2_per_warp(a.kmax, a.nseg_max);
+               (size_t)gw * heavy_scratch_f2_per_warp(a.kmax);
   float4* ck = reinterpret_cast<float4*>(hs);
-  float2* Gs = hs + (size_t)a.nseg_max * 64;
+  float2* Gs = hs + (size_t)heavy_nseg(a.kmax) * 64;
   float2* Hs = Gs + (size_t)a.kmax * 32;
   const int total = a.ntiles_heavy;
 

@@ -273,7 +273,7 @@ int engine_init(Engine& e, int precision, int Ttab, double omega, double radius,
     e.grid_light = e.nsm * std::max(1, std::min(per_l, 4));
     e.grid_heavy = e.nsm * std::max(1, std::min(per_h, 6));
     e.scratch_bytes = sizeof(float4) * (size_t)e.grid_light * MIX_WARPS * light_ckpt_f4_per_warp(e.nseg_max) +
-                      sizeof(float2) * (size_t)e.grid_heavy * MIX_WARPS * heavy_scratch_f2_per_warp(e.kmax, e.nseg_max);
+                      sizeof(float2) * (size_t)e.grid_heavy * MIX_WARPS * heavy_scratch_f2_per_warp(e.kmax);
     e.rhs_cap = rhs_cap;
     if ((rc = dev_alloc((char**)&e.rhs, rhs32_bytes(rhs_cap) + sizeof(RhsDF) * rhs_cap, &ws))) return rc;
   }
