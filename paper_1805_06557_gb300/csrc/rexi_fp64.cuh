@@ -153,6 +153,9 @@ inline size_t fp64_smem_bytes() {
 
 // U1 = (bPhi S0 - Phibar S_wz, S_zeta, S_delta) for every coefficient of every instance,
 // summing the instance's Q partial slots in order.
+// Partial slots hold FP64 complex sums (DF = false, FP64 plans) or double-float pairs
+// (DF = true, mixed plans: float4 = re.hi, re.lo, im.hi, im.lo, the same 16 bytes per entry).
+template <bool DF>
 static __global__ void k_rexi_finalize(const double2* __restrict__ U0, const double2* __restrict__ partial,
                                        double2* __restrict__ U1, const Inst* __restrict__ insts,
                                        const long long* __restrict__ ecum, int ninst, long long total,
@@ -164,11 +167,38 @@ static __global__ void k_rexi_finalize(const double2* __restrict__ U0, const dou
   const int nlm = I.nlm, idx = (int)(e - ecum[i]);
   double2 sz = make_double2(0, 0), sd = sz, sw = sz;
   const double2* p = partial + I.poff + idx;
-  for (int q = 0; q < I.Q; ++q) {
-    sz = cadd(sz, p[0]);
-    sd = cadd(sd, p[nlm]);
-    sw = cadd(sw, p[2 * nlm]);
-    p += 3 * nlm;
+  if (DF) {
+    // double-float slots summed in double-float (two-sum of the high words, low words added),
+    // in the same fixed order; one conversion to FP64 at the end
+    float4 az = make_float4(0.f, 0.f, 0.f, 0.f), ad = az, aw = az;
+    auto add = [](float4& acc, const double2* q) {
+      const float4 v = *reinterpret_cast<const float4*>(q);
+      float s = acc.x + v.x, bb = s - acc.x;
+      const float ex = (acc.x - (s - bb)) + (v.x - bb);
+      acc.x = s;
+      acc.y += v.y + ex;
+      s = acc.z + v.z;
+      bb = s - acc.z;
+      const float ez = (acc.z - (s - bb)) + (v.z - bb);
+      acc.z = s;
+      acc.w += v.w + ez;
+    };
+    for (int q = 0; q < I.Q; ++q) {
+      add(az, p);
+      add(ad, p + nlm);
+      add(aw, p + 2 * nlm);
+      p += 3 * nlm;
+    }
+    sz = make_double2((double)az.x + (double)az.y, (double)az.z + (double)az.w);
+    sd = make_double2((double)ad.x + (double)ad.y, (double)ad.z + (double)ad.w);
+    sw = make_double2((double)aw.x + (double)aw.y, (double)aw.z + (double)aw.w);
+  } else {
+    for (int q = 0; q < I.Q; ++q) {
+      sz = cadd(sz, p[0]);
+      sd = cadd(sd, p[nlm]);
+      sw = cadd(sw, p[2 * nlm]);
+      p += 3 * nlm;
+    }
   }
   const double2 bp = U0[I.soff + idx];
   double2 phi = cmul(I.S0, bp);

@@ -64,6 +64,17 @@ __device__ __forceinline__ dfc dfc_mul(dfc a, dfc b) {
   return dfc{df_add(df_mul(a.re, b.re), df_neg(df_mul(a.im, b.im))),
              df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
 }
+// Double-float partial slot (re.hi, re.lo, im.hi, im.lo): set, or add a complex value given as
+// a double-float pair per component; the error of each two-sum is kept in the low word.
+__device__ __forceinline__ void dfp_add(float4* dst, float4 v, bool first) {
+  if (first) {
+    *dst = v;
+    return;
+  }
+  float4 o = *dst;
+  const df a = df_two_sum(o.x, v.x), b = df_two_sum(o.z, v.z);
+  *dst = make_float4(a.hi, (o.y + v.y) + a.lo, b.hi, (o.w + v.w) + b.lo);
+}
 __host__ __device__ inline float4 split4(double a, double b) {
   float ah = (float)a, bh = (float)b;
   return make_float4(ah, (float)(a - (double)ah), bh, (float)(b - (double)bh));
@@ -308,22 +319,11 @@ k_rexi_light(MixedArgs a) {
             af.x += __shfl_xor_sync(0xffffffffu, af.x, sh);
             af.y += __shfl_xor_sync(0xffffffffu, af.y, sh);
           }
-          if (h == 0 && valid) {
-            double2* d0 = part + off + k;
-            double2* d1 = d0 + nlm;
-            double2* d2 = d1 + nlm;
-            const double2 vz = make_double2((double)az.x, (double)az.y);
-            const double2 vd = make_double2((double)ad.x, (double)ad.y);
-            const double2 vf = make_double2((double)af.x, (double)af.y);
-            if (gi == 0) {
-              *d0 = vz;
-              *d1 = vd;
-              *d2 = vf;
-            } else {
-              *d0 = cadd(*d0, vz);
-              *d1 = cadd(*d1, vd);
-              *d2 = cadd(*d2, vf);
-            }
+          if (h == 0 && valid) {  // double-float partial slots (no FP64 arithmetic here)
+            float4* d0 = reinterpret_cast<float4*>(part + off + k);
+            dfp_add(d0, make_float4(az.x, 0.f, az.y, 0.f), gi == 0);
+            dfp_add(d0 + nlm, make_float4(ad.x, 0.f, ad.y, 0.f), gi == 0);
+            dfp_add(d0 + 2 * nlm, make_float4(af.x, 0.f, af.y, 0.f), gi == 0);
           }
         }
         __syncwarp();
@@ -417,10 +417,9 @@ __device__ __forceinline__ void heavy_block_sum(const float2* tile, const float4
   const int kk = kb + r;
   const bool valid = kk < K;
   const bool isD = ((kk & 1) != c);
-  double2 acc = make_double2(0.0, 0.0), acc2 = make_double2(0.0, 0.0);
+  float4 f1 = make_float4(0.f, 0.f, 0.f, 0.f), f2 = f1;  // double-float (re.hi, re.lo, im.hi, im.lo)
   if (valid) {
     if (dfsum) {
-      float4 f1 = make_float4(0.f, 0.f, 0.f, 0.f), f2 = f1;
 #pragma unroll 4
       for (int p = 16 * h; p < 16 * h + 16; ++p) {
         const float2 v = tile[r * LTROW + p];
@@ -428,8 +427,6 @@ __device__ __forceinline__ void heavy_block_sum(const float2* tile, const float4
         dfc_acc(f1, s_w[p], vv);
         if (isD) dfc_acc(f2, s_wz[p], vv);
       }
-      acc = make_double2((double)f1.x + (double)f1.y, (double)f1.z + (double)f1.w);
-      acc2 = make_double2((double)f2.x + (double)f2.y, (double)f2.z + (double)f2.w);
     } else {
       float2 g1 = make_float2(0.f, 0.f), g2 = g1;
 #pragma unroll 4
@@ -442,21 +439,31 @@ __device__ __forceinline__ void heavy_block_sum(const float2* tile, const float4
           g2 = cfmaf(make_float2(wz.x, wz.z), v, g2);
         }
       }
-      acc = make_double2((double)g1.x, (double)g1.y);
-      acc2 = make_double2((double)g2.x, (double)g2.y);
+      f1 = make_float4(g1.x, 0.f, g1.y, 0.f);
+      f2 = make_float4(g2.x, 0.f, g2.y, 0.f);
     }
   }
-  acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
-  acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
-  acc2.x += __shfl_xor_sync(0xffffffffu, acc2.x, 16);
-  acc2.y += __shfl_xor_sync(0xffffffffu, acc2.y, 16);
+  // combine the two halves: two-sum of the high words, low words added
+  float4 o1, o2;
+  o1.x = __shfl_xor_sync(0xffffffffu, f1.x, 16);
+  o1.y = __shfl_xor_sync(0xffffffffu, f1.y, 16);
+  o1.z = __shfl_xor_sync(0xffffffffu, f1.z, 16);
+  o1.w = __shfl_xor_sync(0xffffffffu, f1.w, 16);
+  o2.x = __shfl_xor_sync(0xffffffffu, f2.x, 16);
+  o2.y = __shfl_xor_sync(0xffffffffu, f2.y, 16);
+  o2.z = __shfl_xor_sync(0xffffffffu, f2.z, 16);
+  o2.w = __shfl_xor_sync(0xffffffffu, f2.w, 16);
   if (h == 0 && valid) {
-    double2* dst = part + (isD ? nlm : 0) + off + kk;
-    *dst = first ? acc : cadd(*dst, acc);
-    if (isD) {
-      double2* dst2 = part + 2 * nlm + off + kk;
-      *dst2 = first ? acc2 : cadd(*dst2, acc2);
+    float4 s1, s2;
+    {
+      const df a = df_two_sum(f1.x, o1.x), b = df_two_sum(f1.z, o1.z);
+      s1 = make_float4(a.hi, (f1.y + o1.y) + a.lo, b.hi, (f1.w + o1.w) + b.lo);
+      const df c2 = df_two_sum(f2.x, o2.x), d2 = df_two_sum(f2.z, o2.z);
+      s2 = make_float4(c2.hi, (f2.y + o2.y) + c2.lo, d2.hi, (f2.w + o2.w) + d2.lo);
     }
+    float4* dst = reinterpret_cast<float4*>(part + (isD ? nlm : 0) + off + kk);
+    dfp_add(dst, s1, first);
+    if (isD) dfp_add(reinterpret_cast<float4*>(part + 2 * nlm + off + kk), s2, first);
   }
 }
 

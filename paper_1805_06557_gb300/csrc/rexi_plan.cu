@@ -494,8 +494,12 @@ int engine_launch(Engine& e, const LaunchSet& L, const double2* U0, double2* U1)
   cudaError_t ce = cudaGetLastError();
   if (ce != cudaSuccess) return cuda_fail(ce, "solve kernel launch");
   const int hf = prof_begin(e, 4);
-  k_rexi_finalize<<<(unsigned)((L.total + 255) / 256), 256, 0, e.stream>>>(U0, e.partial, U1, L.insts, L.ecum,
-                                                                          L.ninst, L.total, e.phibar);
+  if (e.precision == REXI_FP64)
+    k_rexi_finalize<false><<<(unsigned)((L.total + 255) / 256), 256, 0, e.stream>>>(U0, e.partial, U1, L.insts,
+                                                                                   L.ecum, L.ninst, L.total, e.phibar);
+  else
+    k_rexi_finalize<true><<<(unsigned)((L.total + 255) / 256), 256, 0, e.stream>>>(U0, e.partial, U1, L.insts,
+                                                                                  L.ecum, L.ninst, L.total, e.phibar);
   prof_end(e, hf);
   ce = cudaGetLastError();
   if (ce != cudaSuccess) return cuda_fail(ce, "finalize kernel launch");
