@@ -81,6 +81,26 @@ def exact_step(U0, T, dt, Omega, radius, Phibar):
     return out
 
 
+def exact_phi(U0, T, dt, Omega, radius, Phibar, k):
+    """psi_k(dt L) U0 exactly up to rounding (Sec. 4.3: psi_0 = exp, psi_1, psi_2), through the
+    same energy-weighted eigen-decomposition as exact_step; psi_k of each eigenvalue comes from
+    coeffs.phi_function (Taylor series near 0)."""
+    from .coeffs import phi_function
+    out = np.zeros_like(U0, dtype=np.complex128)
+    for m in range(T + 1):
+        A = linop.operator_m(T, m, Omega, radius, Phibar)
+        W = linop.energy_weights_m(T, m, radius, Phibar)
+        d = np.sqrt(np.where(W > 0, W, 1.0))
+        S = (d[:, None] * A) / d[None, :]
+        Hm = 1j * S
+        Hm = 0.5 * (Hm + Hm.conj().T)
+        lam, Q = np.linalg.eigh(Hm)            # S = -i Q diag(lam) Q^H
+        b = d * linop.split_m(U0, T, m)
+        y = Q @ (phi_function(k, -1j * dt * lam) * (Q.conj().T @ b))
+        linop.merge_m(out, y / d, T, m)
+    return out
+
+
 def exact_step_expm(U0, T, dt, Omega, radius, Phibar):
     """exp(dt L) U0 with scipy.linalg.expm applied in the energy-weighted basis (a second,
     independent route to the exact exponential for the pins)."""

@@ -15,6 +15,9 @@ Time integrators (Sec. 4.1, 4.4; Table 2):
   * ver1 : T(U) = N^{dt/2} o L^{dt} o N^{dt/2} (U), the linear part L = L_g + L_c by REXI
            (method id l_rexi_n_erk_ver1, Coriolis inside REXI).
   * ver0 : T(U) = L^{dt/2} o N^{dt} o L^{dt/2} (U).
+  * etdrk: ETD2RK (Sec. 4.3):  A = psi_0(dt L) U + dt psi_1(dt L) N(U),
+           U+ = A + dt psi_2(dt L) (N(A) - N(U)); every psi_k(dt L) applied by REXI with the
+           psi_k weights of the same poles (method id l_rexi_n_etdrk).
   * rk4  : classical 4th-order Runge-Kutta of the full system, used as the small-step
            reference (the paper's reference solution uses RK4 with a tiny step, Sec. 5).
 """
@@ -68,6 +71,16 @@ def strang_ver0(U, grid, dt, Omega, Phibar, z_half, w_half):
     U1 = rexi.rexi_step(U, T, 0.5 * dt, Omega, a, Phibar, z_half, w_half)
     U2 = rk2_nonlinear(U1, grid, dt)
     return rexi.rexi_step(U2, T, 0.5 * dt, Omega, a, Phibar, z_half, w_half)
+
+
+def etd2rk(U, grid, dt, Omega, Phibar, z, w0, w1, w2, nonlin=None):
+    """One ETD2RK step (Sec. 4.3) with REXI for psi_0, psi_1, psi_2 (weights w0, w1, w2 of the
+    poles z).  nonlin(U) defaults to N(U) on `grid`."""
+    T, a = grid.T, grid.a
+    N_ = (lambda V: nonlinear(V, grid)) if nonlin is None else nonlin
+    NU = N_(U)
+    A = rexi.rexi_step(U, T, dt, Omega, a, Phibar, z, w0) + dt * rexi.rexi_step(NU, T, dt, Omega, a, Phibar, z, w1)
+    return A + dt * rexi.rexi_step(N_(A) - NU, T, dt, Omega, a, Phibar, z, w2)
 
 
 def full_tendency(U, grid, Omega, Phibar):

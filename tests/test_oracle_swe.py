@@ -103,3 +103,79 @@ def test_strang_ver1_second_order():
         errs.append(float(np.max(rexi.rel_l2(U, ref, T))))
     rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert all(1.7 < r < 2.5 for r in rates), (errs, rates)
+
+
+# ---- ETD2RK (Sec. 4.3) ------------------------------------------------------------------
+def _psi_weights(N, p0, Xc):
+    z, w0 = coeffs.rexi_coefficients(N, p0, Xc, k=0)
+    _, w1 = coeffs.rexi_coefficients(N, p0, Xc, k=1)
+    _, w2 = coeffs.rexi_coefficients(N, p0, Xc, k=2)
+    return z, w0, w1, w2
+
+
+def test_exact_phi_defining_identities():
+    """psi_1(K) and psi_2(K) of K = dt L satisfy K psi_1(K) = e^K - I and
+    K psi_2(K) = psi_1(K) - I; psi_0 equals exp."""
+    T, dt = 15, 3600.0
+    U = syn.gaussian_state(T, 21)
+    e = rexi.exact_step(U, T, dt, OM, A, PB)
+    p0_ = rexi.exact_phi(U, T, dt, OM, A, PB, 0)
+    p1 = rexi.exact_phi(U, T, dt, OM, A, PB, 1)
+    p2 = rexi.exact_phi(U, T, dt, OM, A, PB, 2)
+    KL = lambda V: dt * linop.apply_L(V, T, OM, A, PB)
+    assert np.max(rexi.rel_l2(p0_, e, T)) < 1e-12
+    assert np.max(rexi.rel_l2(KL(p1), e - U, T)) < 1e-10
+    assert np.max(rexi.rel_l2(KL(p2), p1 - U, T)) < 1e-10
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_rexi_psi_weights_vs_exact(k):
+    """REXI with the psi_k weights of the same poles applies psi_k(dt L) to within its scalar
+    error (energy norm; the operator is normal in the energy inner product)."""
+    T, dt, N = 15, 3600.0, 128
+    X = rexi.spectrum_bound(T, dt, OM, A, PB)
+    p0, Xc = min(6.0, 1.6 * X), 1.6 * X
+    z, w = coeffs.rexi_coefficients(N, p0, Xc, k=k)
+    x = 1j * np.linspace(-X, X, 4001)
+    x = x[np.abs(x) > 1e-6]
+    ref = (np.expm1(x) / x) if k == 1 else ((np.expm1(x) - x) / x ** 2)
+    es = float(np.max(np.abs(coeffs.rational_eval(z, w, x) - ref)))
+    U = syn.gaussian_state(T, 22)
+    Ur = rexi.rexi_step(U, T, dt, OM, A, PB, z, w)
+    Ue = rexi.exact_phi(U, T, dt, OM, A, PB, k)
+    err = math.sqrt(linop.energy(Ur - Ue, T, A, PB) / linop.energy(U, T, A, PB))
+    assert err <= es + 1e-12, (err, es)
+
+
+def test_etd2rk_exact_for_constant_forcing():
+    """For N(U) = F constant the ETD2RK step is exact: U+ = e^{dt L} U + dt psi_1(dt L) F
+    (the psi_2 term vanishes); checked against the eigen-decomposition."""
+    T, dt, N = 15, 3600.0, 128
+    g = sht.Grid(T, 24, 48, A)
+    X = rexi.spectrum_bound(T, dt, OM, A, PB)
+    z, w0, w1, w2 = _psi_weights(N, min(6.0, 1.6 * X), 1.6 * X)
+    U = syn.gaussian_state(T, 23)
+    F = syn.gaussian_state(T, 24, scales=(1e-2, 1e-10, 1e-10))
+    out = swe.etd2rk(U, g, dt, OM, PB, z, w0, w1, w2, nonlin=lambda V: F)
+    ref = rexi.exact_step(U, T, dt, OM, A, PB) + dt * rexi.exact_phi(F, T, dt, OM, A, PB, 1)
+    assert np.max(rexi.rel_l2(out, ref, T)) < 1e-9
+
+
+def test_etd2rk_second_order():
+    """ETD2RK (l_rexi_n_etdrk) converges at 2nd order to a small-step RK4 reference."""
+    T, nlat, nlon = 15, 24, 48
+    g = sht.Grid(T, nlat, nlon, A)
+    U0 = syn.balanced_state(T, 2, urms=40.0)
+    U0[2] = syn.gaussian_state(T, 8, scales=(0, 0, 2e-6))[2]
+    t_end = 4 * 1800.0
+    ref = swe.rk4_full(U0, g, t_end, 240, OM, PB)
+    errs = []
+    for dt in (1800.0, 900.0, 450.0):
+        X = rexi.spectrum_bound(T, dt, OM, A, PB)
+        z, w0, w1, w2 = _psi_weights(128, min(6.0, 1.6 * X), 1.6 * X)
+        U = U0
+        for _ in range(int(round(t_end / dt))):
+            U = swe.etd2rk(U, g, dt, OM, PB, z, w0, w1, w2)
+        errs.append(float(np.max(rexi.rel_l2(U, ref, T))))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(1.7 < r < 2.6 for r in rates), (errs, rates)
