@@ -40,7 +40,7 @@ KERNEL_FLOPS = {"k_rexi_light": (49.0, "fp32"), "k_rexi_heavy": (376.0, "fp32"),
                 "k_rexi_fp64": (49.0, "fp64")}
 # DRAM bytes (read + write) of one launch from an ncu capture: (bytes, batch of that launch,
 # summary file).  Only for kernels unchanged since the capture.
-TRAFFIC = {}
+TRAFFIC = {"k_rexi_heavy": (3.46e9, 16, "profiles/rexi_solve_T255_B16.md")}
 
 
 def ref_step_m(T):
@@ -366,7 +366,7 @@ def sh_transforms(torch, rexi, fp64_peak, T=511, nlat=768, nlon=1536, nf=2, reps
 
 def swe_steps(torch, rexi, configs):
     """Nonlinear SWE steps (Strang ver1: N by RK2 midpoint for dt/2, REXI L for dt, N for
-    dt/2) on balanced n^-3 states: steps/s and per-stage device times over the timed steps,
+    dt/2; variants may name the ETD2RK scheme instead) on balanced n^-3 states: steps/s and per-stage device times over the timed steps,
     whether the state stayed finite (the explicit RK2 half-steps of N are bound by the
     advective CFL limit, which dt = 7200 s exceeds at T511), and each variant's per-field
     error against the all-FP64 plan after ONE step from the same state."""
@@ -380,9 +380,11 @@ def swe_steps(torch, rexi, configs):
         ref1 = None
         cfg = {"workload": "nonlinear SWE, T%d on %d x %d Gauss grid, %d poles, dt=%g s, %d timed steps, "
                            "balanced n^-3 state (20 m/s rms)" % (T, nlat, nlon, N, dt, nsteps), "variants": {}}
-        for rprec, sprec in variants:
+        for var in variants:
+            rprec, sprec = var[0], var[1]
+            scheme = var[2] if len(var) > 2 else "ver1"
             p = rexi.SwePlan(T, nlat, nlon, dt, syn.OMEGA, syn.RADIUS, syn.PHIBAR, N, p0, Xc,
-                             rexi_precision=rprec, sh_precision=sprec)
+                             rexi_precision=rprec, sh_precision=sprec, scheme=scheme)
             u = torch.from_numpy(U0).cuda().contiguous()
             w1 = u.clone()
             p.step(w1, 1)                                  # one step: error figure and warm-up
@@ -399,12 +401,14 @@ def swe_steps(torch, rexi, configs):
             ms = e0.elapsed_time(e1)
             prof = p.profile(reset=True)
             p.set_profiling(False)
-            key = "rexi_%s+sh_%s" % (rprec, sprec)
+            key = "%srexi_%s+sh_%s" % ("" if scheme == "ver1" else scheme + ":", rprec, sprec)
             v = {"steps_per_s": nsteps / (ms * 1e-3), "ms_per_step": ms / nsteps,
                  "stage_ms_per_step": {k: val[0] / nsteps for k, val in prof.items()},
                  "finite_after_one_step": bool(np.all(np.isfinite(one))),
                  "finite_after_timed_steps": bool(torch.isfinite(u2).all().item())}
-            if ref1 is None:
+            if scheme != "ver1":
+                pass   # another scheme: no error against the ver1 FP64 reference
+            elif ref1 is None:
                 ref1 = one
             elif v["finite_after_one_step"] and np.all(np.isfinite(ref1)):
                 v["rel_err_vs_fp64_one_step"] = _rel_fields(one, ref1, T)
@@ -573,7 +577,8 @@ def main():
     if not args.no_sh:
         sh = sh_transforms(torch, rexi, fp64_tf)
         swe = swe_steps(torch, rexi, [
-            (127, 192, 384, 512, 1800.0, 48, [("fp64", "fp64"), ("mixed", "fp64"), ("mixed", "tf32")]),
+            (127, 192, 384, 512, 1800.0, 48, [("fp64", "fp64"), ("mixed", "fp64"), ("mixed", "tf32"),
+                                              ("fp64", "fp64", "etdrk"), ("mixed", "fp64", "etdrk")]),
             (511, 768, 1536, 2048, 7200.0, 4, [("fp64", "fp64"), ("mixed", "fp64"), ("mixed", "tf32"),
                                                 ("mixed", "bf16")])])
 

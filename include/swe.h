@@ -19,6 +19,11 @@ extern "C" {
 
 #define SWE_L_REXI_N_ERK_VER1 0 /* U+ = N^{dt/2} o L^{dt} o N^{dt/2} (U)  (Sec. 4.4, version 1) */
 #define SWE_L_REXI_N_ERK_VER0 1 /* U+ = L^{dt/2} o N^{dt} o L^{dt/2} (U)  (Sec. 4.4, version 0) */
+/* ETD2RK (Sec. 4.3, method l_rexi_n_etdrk): A = psi_0(dt L) U + dt psi_1(dt L) N(U),
+ * U+ = A + dt psi_2(dt L) (N(A) - N(U)); psi_0 = exp, psi_1(K) = K^-1 (e^K - I),
+ * psi_2(K) = K^-2 (e^K - I - K), each applied by REXI with the psi_k weights of the same poles
+ * (contour p0, Xc for a step of dt). */
+#define SWE_L_REXI_N_ETDRK 2
 
 typedef struct swe_plan swe_plan;
 
@@ -27,14 +32,14 @@ typedef struct swe_plan_desc {
   double dt;                /* time step [s]                                                */
   double omega, radius, phibar;
   int N;                    /* REXI poles                                                   */
-  double p0, Xc;            /* REXI contour for the linear sub-step (dt for ver1, dt/2 ver0) */
+  double p0, Xc;            /* REXI contour for the linear sub-step (dt for ver1 and etdrk, dt/2 ver0) */
   int rexi_precision;       /* REXI_FP64 or REXI_MIXED                                      */
   int sh_precision;         /* SH_FP64, SH_TF32 or SH_BF16                                  */
-  int scheme;               /* SWE_L_REXI_N_ERK_VER1 or SWE_L_REXI_N_ERK_VER0               */
+  int scheme;               /* SWE_L_REXI_N_ERK_VER1, SWE_L_REXI_N_ERK_VER0 or SWE_L_REXI_N_ETDRK */
   void* stream;             /* cudaStream_t                                                  */
 } swe_plan_desc;
 
-/* Creates the REXI plan, the SH plan and all work buffers.
+/* Creates the REXI plan(s: three for etdrk), the SH plan and all work buffers.
  * Errors: REXI_EINVAL, REXI_ENOMEM, REXI_ECUDA. */
 int swe_plan_create(const swe_plan_desc* desc, swe_plan** out);
 int swe_plan_destroy(swe_plan* plan);

@@ -77,6 +77,14 @@ __global__ void k_swe_combine(const double2* __restrict__ base, const double2* _
   out[2 * nlm + i] = make_double2(fma(tau, nD.x, base[2 * nlm + i].x), fma(tau, nD.y, base[2 * nlm + i].y));
 }
 
+// out = a + s * b over n complex entries (ETD2RK combinations)
+__global__ void k_axpy(const double2* __restrict__ a, const double2* __restrict__ b, double s,
+                       double2* __restrict__ out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[i] = make_double2(fma(s, b[i].x, a[i].x), fma(s, b[i].y, a[i].y));
+}
+
 }  // namespace
 }  // namespace rexi
 
@@ -86,8 +94,10 @@ struct swe_plan {
   swe_plan_desc d{};
   int nlm = 0, npt = 0;
   cudaStream_t stream = nullptr;
-  rexi_plan* rp = nullptr;
+  rexi_plan* rp = nullptr;             // REXI of exp (ver1: dt, ver0: dt/2, etdrk: dt)
+  rexi_plan *rp1 = nullptr, *rp2 = nullptr;  // etdrk: REXI of psi_1, psi_2 (same poles)
   sh_plan* sp = nullptr;
+  double2 *NU = nullptr, *A3 = nullptr;      // etdrk: N(U), A
   double2 *psi = nullptr, *chi = nullptr, *Um = nullptr, *Ut = nullptr, *dv = nullptr, *cu = nullptr,
           *kes = nullptr;
   double *PZ = nullptr, *Ug = nullptr, *Vg = nullptr, *A = nullptr, *B = nullptr, *KE = nullptr,
@@ -99,11 +109,13 @@ extern "C" int swe_plan_destroy(swe_plan* p) {
   if (!p) return REXI_OK;
   cudaStreamSynchronize(p->stream);
   rexi_plan_destroy(p->rp);
+  rexi_plan_destroy(p->rp1);
+  rexi_plan_destroy(p->rp2);
   sh_plan_destroy(p->sp);
   p->prof.release();
   for (void* q : {(void*)p->psi, (void*)p->chi, (void*)p->Um, (void*)p->Ut, (void*)p->dv, (void*)p->cu,
                   (void*)p->kes, (void*)p->PZ, (void*)p->Ug, (void*)p->Vg, (void*)p->A, (void*)p->B,
-                  (void*)p->KE, (void*)p->c2})
+                  (void*)p->KE, (void*)p->c2, (void*)p->NU, (void*)p->A3})
     cudaFree(q);
   delete p;
   return REXI_OK;
@@ -113,7 +125,7 @@ extern "C" int swe_plan_create(const swe_plan_desc* desc, swe_plan** out) {
   if (!desc || !out) return fail(REXI_EINVAL, "swe_plan_create: null argument");
   *out = nullptr;
   const swe_plan_desc& d = *desc;
-  if (d.scheme != SWE_L_REXI_N_ERK_VER1 && d.scheme != SWE_L_REXI_N_ERK_VER0)
+  if (d.scheme != SWE_L_REXI_N_ERK_VER1 && d.scheme != SWE_L_REXI_N_ERK_VER0 && d.scheme != SWE_L_REXI_N_ETDRK)
     return fail(REXI_EINVAL, "swe_plan_create: unknown scheme %d", d.scheme);
   swe_plan* p = new swe_plan();
   p->d = d;
@@ -138,7 +150,7 @@ extern "C" int swe_plan_create(const swe_plan_desc* desc, swe_plan** out) {
   rexi_plan_desc rd{};
   rd.T = d.T;
   rd.N = d.N;
-  rd.dt = d.scheme == SWE_L_REXI_N_ERK_VER1 ? d.dt : 0.5 * d.dt;
+  rd.dt = d.scheme == SWE_L_REXI_N_ERK_VER0 ? 0.5 * d.dt : d.dt;
   rd.omega = d.omega;
   rd.radius = d.radius;
   rd.phibar = d.phibar;
@@ -150,6 +162,16 @@ extern "C" int swe_plan_create(const swe_plan_desc* desc, swe_plan** out) {
   rd.stream = d.stream;
   rc = rexi_plan_create(&rd, &p->rp);
   if (rc) return bail(rc);
+  if (d.scheme == SWE_L_REXI_N_ETDRK) {  // psi_1 and psi_2 weights of the same poles
+    std::vector<double> zz(2 * (size_t)d.N), ww(2 * (size_t)d.N);
+    for (int k = 1; k <= 2; ++k) {
+      if ((rc = rexi_coeffs(d.N, d.p0, d.Xc, k, zz.data(), ww.data()))) return bail(rc);
+      rexi_plan_desc rk = rd;
+      rk.z = zz.data();
+      rk.w = ww.data();
+      if ((rc = rexi_plan_create(&rk, k == 1 ? &p->rp1 : &p->rp2))) return bail(rc);
+    }
+  }
   const size_t s3 = sizeof(double2) * 3 * (size_t)p->nlm, s1 = sizeof(double2) * (size_t)p->nlm;
   const size_t g1 = sizeof(double) * (size_t)p->npt;
   cudaError_t e;
@@ -157,7 +179,8 @@ extern "C" int swe_plan_create(const swe_plan_desc* desc, swe_plan** out) {
       (e = cudaMalloc(&p->Ut, s3)) || (e = cudaMalloc(&p->dv, 2 * s1)) || (e = cudaMalloc(&p->cu, 2 * s1)) ||
       (e = cudaMalloc(&p->kes, s1)) || (e = cudaMalloc(&p->PZ, 2 * g1)) || (e = cudaMalloc(&p->Ug, g1)) ||
       (e = cudaMalloc(&p->Vg, g1)) || (e = cudaMalloc(&p->A, 2 * g1)) || (e = cudaMalloc(&p->B, 2 * g1)) ||
-      (e = cudaMalloc(&p->KE, g1)) || (e = cudaMalloc(&p->c2, sizeof(double) * d.nlat))) {
+      (e = cudaMalloc(&p->KE, g1)) || (e = cudaMalloc(&p->c2, sizeof(double) * d.nlat)) ||
+      (d.scheme == SWE_L_REXI_N_ETDRK && ((e = cudaMalloc(&p->NU, s3)) || (e = cudaMalloc(&p->A3, s3))))) {
     cudaGetLastError();
     return bail(fail(REXI_ENOMEM, "swe_plan_create: cudaMalloc failed: %s", cudaGetErrorString(e)));
   }
@@ -226,10 +249,21 @@ extern "C" int swe_step(swe_plan* p, void* state, int nsteps) {
       if ((rc = rexi_step(p->rp, U, p->Ut, 1))) return rc;
       REXI_CUDA_TRY(cudaMemcpyAsync(U, p->Ut, s3, cudaMemcpyDeviceToDevice, p->stream));
       if ((rc = rk2_nonlinear(p, U, 0.5 * dt))) return rc;
-    } else {
+    } else if (p->d.scheme == SWE_L_REXI_N_ERK_VER0) {
       if ((rc = rexi_step(p->rp, U, p->Ut, 1))) return rc;
       if ((rc = rk2_nonlinear(p, p->Ut, dt))) return rc;
       if ((rc = rexi_step(p->rp, p->Ut, U, 1))) return rc;
+    } else {  // ETD2RK
+      const int n3 = 3 * p->nlm, tb = 256, nb = (n3 + tb - 1) / tb;
+      if ((rc = nonlinear_update(p, U, nullptr, 0.0, p->NU))) return rc;          // N(U)
+      if ((rc = rexi_step(p->rp, U, p->Ut, 1))) return rc;                       // psi_0 U
+      if ((rc = rexi_step(p->rp1, p->NU, p->Um, 1))) return rc;                  // psi_1 N(U)
+      k_axpy<<<nb, tb, 0, p->stream>>>(p->Ut, p->Um, dt, p->A3, n3);              // A
+      if ((rc = nonlinear_update(p, p->A3, nullptr, 0.0, p->Ut))) return rc;      // N(A)
+      k_axpy<<<nb, tb, 0, p->stream>>>(p->Ut, p->NU, -1.0, p->Um, n3);            // N(A) - N(U)
+      if ((rc = rexi_step(p->rp2, p->Um, p->Ut, 1))) return rc;                  // psi_2 (...)
+      k_axpy<<<nb, tb, 0, p->stream>>>(p->A3, p->Ut, dt, U, n3);                  // U+
+      REXI_CUDA_TRY(cudaGetLastError());
     }
   }
   return REXI_OK;
@@ -239,6 +273,8 @@ extern "C" int swe_plan_set_profiling(swe_plan* p, int enable) {
   if (!p) return fail(REXI_EINVAL, "swe_plan_set_profiling: null plan");
   p->prof.on = enable != 0;
   int rc = rexi_plan_set_profiling(p->rp, enable);
+  for (rexi_plan* q : {p->rp1, p->rp2})
+    if (!rc && q) rc = rexi_plan_set_profiling(q, enable);
   return rc ? rc : sh_plan_set_profiling(p->sp, enable);
 }
 
@@ -248,6 +284,16 @@ extern "C" int swe_plan_get_profile(swe_plan* p, double* ms, int* launches, int 
   int rn[REXI_NKERNELS], sn[SH_NSTAGES];
   int rc = rexi_plan_get_profile(p->rp, rm, rn, reset);
   if (rc) return rc;
+  for (rexi_plan* q : {p->rp1, p->rp2}) {
+    if (!q) continue;
+    double qm[REXI_NKERNELS];
+    int qn[REXI_NKERNELS];
+    if ((rc = rexi_plan_get_profile(q, qm, qn, reset))) return rc;
+    for (int k = 0; k < REXI_NKERNELS; ++k) {
+      rm[k] += qm[k];
+      rn[k] += qn[k];
+    }
+  }
   if ((rc = sh_plan_get_profile(p->sp, sm, sn, reset))) return rc;
   REXI_CUDA_TRY(p->prof.collect());
   double out[SWE_NSTAGES] = {0, 0, 0, 0};

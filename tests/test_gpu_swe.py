@@ -60,19 +60,27 @@ def test_nonlinear_matches_oracle(env, T, nlat, nlon, kind, tol):
 
 
 @pytest.mark.parametrize("scheme,rprec,tol", [("ver1", "fp64", 1e-10), ("ver0", "fp64", 1e-10),
-                                              ("ver1", "mixed", 1e-8)])
+                                              ("ver1", "mixed", 1e-8), ("etdrk", "fp64", 1e-10),
+                                              ("etdrk", "mixed", 1e-8)])
 def test_strang_steps_match_oracle(env, scheme, rprec, tol):
+    """Strang ver1 / ver0 (Sec. 4.4) and ETD2RK (Sec. 4.3) steps against the oracle."""
     torch, rexi = env
     T, nlat, nlon, dt, N, nsteps = 31, 48, 96, 1800.0, 128, 3
     U0 = _state(T, 4)
     g = osht.Grid(T, nlat, nlon, A)
-    sub = dt if scheme == "ver1" else 0.5 * dt
+    sub = 0.5 * dt if scheme == "ver0" else dt
     p0, Xc = _contour(T, sub)
     z, w = oc.rexi_coefficients(N, p0, Xc)
     ref = U0
     for _ in range(nsteps):
-        ref = (oswe.strang_ver1(ref, g, dt, OM, PB, z, w) if scheme == "ver1"
-               else oswe.strang_ver0(ref, g, dt, OM, PB, z, w))
+        if scheme == "ver1":
+            ref = oswe.strang_ver1(ref, g, dt, OM, PB, z, w)
+        elif scheme == "ver0":
+            ref = oswe.strang_ver0(ref, g, dt, OM, PB, z, w)
+        else:
+            w1 = oc.rexi_coefficients(N, p0, Xc, k=1)[1]
+            w2 = oc.rexi_coefficients(N, p0, Xc, k=2)[1]
+            ref = oswe.etd2rk(ref, g, dt, OM, PB, z, w, w1, w2)
     plan = rexi.SwePlan(T, nlat, nlon, dt, OM, A, PB, N, p0, Xc, rexi_precision=rprec, scheme=scheme)
     u = torch.from_numpy(U0).cuda()
     plan.step(u, nsteps)
