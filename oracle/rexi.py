@@ -101,6 +101,39 @@ def exact_phi(U0, T, dt, Omega, radius, Phibar, k):
     return out
 
 
+def cn_step(U0, T, dt, Omega, radius, Phibar, a=0.5):
+    """Crank-Nicolson (Sec. 4.1, the irk scheme):  U+ = (I - a dt L)^-1 (I + (1 - a) dt L) U0,
+    a = 1/2; the forward-Euler half by linop.apply_L, the backward-Euler half by the pivoted
+    banded LU of every zonal order (the same solver as rexi_step)."""
+    V = U0 + (1.0 - a) * dt * linop.apply_L(U0, T, Omega, radius, Phibar)
+    out = np.zeros_like(U0, dtype=np.complex128)
+    for m in range(T + 1):
+        A = a * dt * linop.operator_m(T, m, Omega, radius, Phibar)
+        ab = _band(-A)
+        ab[4, :] += 1.0
+        linop.merge_m(out, scipy.linalg.solve_banded((4, 4), ab, linop.split_m(V, T, m)), T, m)
+    return out
+
+
+def exact_cayley(U0, T, dt, Omega, radius, Phibar):
+    """(I - dt L / 2)^-1 (I + dt L / 2) U0 through the energy-weighted eigen-decomposition
+    (each eigenvalue lam of dt L maps to (1 + lam/2) / (1 - lam/2)): pins cn_step."""
+    out = np.zeros_like(U0, dtype=np.complex128)
+    for m in range(T + 1):
+        A = linop.operator_m(T, m, Omega, radius, Phibar)
+        W = linop.energy_weights_m(T, m, radius, Phibar)
+        d = np.sqrt(np.where(W > 0, W, 1.0))
+        S = (d[:, None] * A) / d[None, :]
+        Hm = 1j * S
+        Hm = 0.5 * (Hm + Hm.conj().T)
+        lam, Q = np.linalg.eigh(Hm)            # S = -i Q diag(lam) Q^H
+        g = -1j * dt * lam
+        b = d * linop.split_m(U0, T, m)
+        y = Q @ (((1 + 0.5 * g) / (1 - 0.5 * g)) * (Q.conj().T @ b))
+        linop.merge_m(out, y / d, T, m)
+    return out
+
+
 def exact_step_expm(U0, T, dt, Omega, radius, Phibar):
     """exp(dt L) U0 with scipy.linalg.expm applied in the energy-weighted basis (a second,
     independent route to the exact exponential for the pins)."""

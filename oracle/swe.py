@@ -18,6 +18,8 @@ Time integrators (Sec. 4.1, 4.4; Table 2):
   * etdrk: ETD2RK (Sec. 4.3):  A = psi_0(dt L) U + dt psi_1(dt L) N(U),
            U+ = A + dt psi_2(dt L) (N(A) - N(U)); every psi_k(dt L) applied by REXI with the
            psi_k weights of the same poles (method id l_rexi_n_etdrk).
+  * irk  : Crank-Nicolson for the linear part (Sec. 4.1, a = 1/2) inside the Strang ver1 split:
+           N^{dt/2} o CN^{dt} o N^{dt/2}  (method id l_irk_n_erk_ver1, Coriolis in L).
   * rk4  : classical 4th-order Runge-Kutta of the full system, used as the small-step
            reference (the paper's reference solution uses RK4 with a tiny step, Sec. 5).
 """
@@ -71,6 +73,14 @@ def strang_ver0(U, grid, dt, Omega, Phibar, z_half, w_half):
     U1 = rexi.rexi_step(U, T, 0.5 * dt, Omega, a, Phibar, z_half, w_half)
     U2 = rk2_nonlinear(U1, grid, dt)
     return rexi.rexi_step(U2, T, 0.5 * dt, Omega, a, Phibar, z_half, w_half)
+
+
+def cn_ver1(U, grid, dt, Omega, Phibar):
+    """One step of l_irk_n_erk_ver1:  N^{dt/2} o CN^{dt} o N^{dt/2}."""
+    T, a = grid.T, grid.a
+    U1 = rk2_nonlinear(U, grid, 0.5 * dt)
+    U2 = rexi.cn_step(U1, T, dt, Omega, a, Phibar)
+    return rk2_nonlinear(U2, grid, 0.5 * dt)
 
 
 def etd2rk(U, grid, dt, Omega, Phibar, z, w0, w1, w2, nonlin=None):

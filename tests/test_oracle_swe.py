@@ -179,3 +179,46 @@ def test_etd2rk_second_order():
         errs.append(float(np.max(rexi.rel_l2(U, ref, T))))
     rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert all(1.7 < r < 2.6 for r in rates), (errs, rates)
+
+
+# ---- Crank-Nicolson (Sec. 4.1, irk) -------------------------------------------------------
+def test_cn_step_matches_cayley_and_conserves_energy():
+    """CN with a = 1/2 is the Cayley map of dt L: equal to the eigen-decomposition route, and,
+    L being skew-adjoint in the energy inner product, it conserves the linear energy exactly."""
+    T, dt = 15, 3600.0
+    U = syn.gaussian_state(T, 31)
+    cn = rexi.cn_step(U, T, dt, OM, A, PB)
+    ref = rexi.exact_cayley(U, T, dt, OM, A, PB)
+    assert np.max(rexi.rel_l2(cn, ref, T)) < 1e-11
+    E0, E1 = linop.energy(U, T, A, PB), linop.energy(cn, T, A, PB)
+    assert abs(E1 / E0 - 1.0) < 1e-12
+
+
+def test_cn_step_third_order_local_error():
+    """One CN step differs from exp(dt L) by O(dt^3): halving dt divides the gap by ~8."""
+    T = 15
+    U = syn.gaussian_state(T, 32)
+    gaps = []
+    for dt in (400.0, 200.0, 100.0):
+        gaps.append(float(np.max(rexi.rel_l2(rexi.cn_step(U, T, dt, OM, A, PB),
+                                             rexi.exact_step(U, T, dt, OM, A, PB), T))))
+    rates = [math.log2(gaps[i] / gaps[i + 1]) for i in range(2)]
+    assert all(2.7 < r < 3.3 for r in rates), (gaps, rates)
+
+
+def test_cn_ver1_second_order():
+    """l_irk_n_erk_ver1 converges at 2nd order to a small-step RK4 reference."""
+    T, nlat, nlon = 15, 24, 48
+    g = sht.Grid(T, nlat, nlon, A)
+    U0 = syn.balanced_state(T, 2, urms=40.0)
+    U0[2] = syn.gaussian_state(T, 8, scales=(0, 0, 2e-6))[2]
+    t_end = 4 * 1800.0
+    ref = swe.rk4_full(U0, g, t_end, 240, OM, PB)
+    errs = []
+    for dt in (1800.0, 900.0, 450.0):
+        U = U0
+        for _ in range(int(round(t_end / dt))):
+            U = swe.cn_ver1(U, g, dt, OM, PB)
+        errs.append(float(np.max(rexi.rel_l2(U, ref, T))))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(1.7 < r < 2.6 for r in rates), (errs, rates)
