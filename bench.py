@@ -578,7 +578,8 @@ def main():
         sh = sh_transforms(torch, rexi, fp64_tf)
         swe = swe_steps(torch, rexi, [
             (127, 192, 384, 512, 1800.0, 48, [("fp64", "fp64"), ("mixed", "fp64"), ("mixed", "tf32"),
-                                              ("fp64", "fp64", "etdrk"), ("mixed", "fp64", "etdrk")]),
+                                              ("fp64", "fp64", "etdrk"), ("mixed", "fp64", "etdrk"),
+                                              ("fp64", "fp64", "irk")]),
             (511, 768, 1536, 2048, 7200.0, 4, [("fp64", "fp64"), ("mixed", "fp64"), ("mixed", "tf32"),
                                                 ("mixed", "bf16")])])
 

@@ -24,6 +24,11 @@ extern "C" {
  * psi_2(K) = K^-2 (e^K - I - K), each applied by REXI with the psi_k weights of the same poles
  * (contour p0, Xc for a step of dt). */
 #define SWE_L_REXI_N_ETDRK 2
+/* Crank-Nicolson for the linear part inside the Strang ver1 split (Sec. 4.1, irk, a = 1/2;
+ * method l_irk_n_erk_ver1): U+ = N^{dt/2} o CN^{dt} o N^{dt/2} (U) with
+ * CN^{dt} = (I - dt L / 2)^-1 (I + dt L / 2) = 2 (2 - dt L)^-1 (I + dt L / 2), i.e. the banded
+ * solve of one pole z = 2 with weight 2 (FP64); p0 and Xc are not used. */
+#define SWE_L_IRK_N_ERK_VER1 3
 
 typedef struct swe_plan swe_plan;
 
@@ -35,7 +40,7 @@ typedef struct swe_plan_desc {
   double p0, Xc;            /* REXI contour for the linear sub-step (dt for ver1 and etdrk, dt/2 ver0) */
   int rexi_precision;       /* REXI_FP64 or REXI_MIXED                                      */
   int sh_precision;         /* SH_FP64, SH_TF32 or SH_BF16                                  */
-  int scheme;               /* SWE_L_REXI_N_ERK_VER1, SWE_L_REXI_N_ERK_VER0 or SWE_L_REXI_N_ETDRK */
+  int scheme;               /* SWE_L_REXI_N_ERK_VER1 / _VER0, SWE_L_REXI_N_ETDRK, SWE_L_IRK_N_ERK_VER1 */
   void* stream;             /* cudaStream_t                                                  */
 } swe_plan_desc;
 

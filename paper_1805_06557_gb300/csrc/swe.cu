@@ -1,5 +1,6 @@
 // Nonlinear shallow-water step (paper Sec. 3 Eq. 1-3, Sec. 4.4): N(U) on the Gauss grid and
 // the Strang splittings around the REXI linear step.
+#include <cmath>
 #include <vector>
 
 #include "../../include/sht.h"
@@ -77,6 +78,40 @@ __global__ void k_swe_combine(const double2* __restrict__ base, const double2* _
   out[2 * nlm + i] = make_double2(fma(tau, nD.x, base[2 * nlm + i].x), fma(tau, nD.y, base[2 * nlm + i].y));
 }
 
+// out = U + s L U (the forward-Euler half of Crank-Nicolson), one thread per (m, n), with the
+// per-(m, n) table (omega_n, cm_n, cp_n, n(n+1)/a^2) of the spectral operator L_m:
+//   dPhi_n   = -Phibar delta_n
+//   dzeta_n  = i omega_n zeta_n  - (cm_n delta_{n-1} + cp_n delta_{n+1})
+//   ddelta_n = q_n Phi_n + i omega_n delta_n + (cm_n zeta_{n-1} + cp_n zeta_{n+1})
+// (cm_n = 2 Omega (n+1)/n eps_n, cp_n = 2 Omega n/(n+1) eps_{n+1}; entries outside m <= n <= T
+// are zero).
+__global__ void k_apply_L(const double2* __restrict__ U, const double4* __restrict__ tab, double s,
+                          double phibar, double2* __restrict__ out, int T, int nlm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nlm) return;
+  int lo = 0, hi = T;  // m = largest with moff(m) <= i
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (moff(T, mid) <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  const int m = lo, n = m + (i - moff(T, m));
+  const double4 t = tab[i];  // (omega, cm, cp, q)
+  const double2* P = U;
+  const double2* Z = U + nlm;
+  const double2* D = U + 2 * nlm;
+  const double2 zm = n > m ? Z[i - 1] : make_double2(0.0, 0.0), zp = n < T ? Z[i + 1] : make_double2(0.0, 0.0);
+  const double2 dm = n > m ? D[i - 1] : make_double2(0.0, 0.0), dp = n < T ? D[i + 1] : make_double2(0.0, 0.0);
+  const double2 z0 = Z[i], d0 = D[i], p0 = P[i];
+  const double2 lP = make_double2(-phibar * d0.x, -phibar * d0.y);
+  const double2 lZ = make_double2(-t.x * z0.y - (t.y * dm.x + t.z * dp.x), t.x * z0.x - (t.y * dm.y + t.z * dp.y));
+  const double2 lD = make_double2(t.w * p0.x - t.x * d0.y + (t.y * zm.x + t.z * zp.x),
+                                  t.w * p0.y + t.x * d0.x + (t.y * zm.y + t.z * zp.y));
+  out[i] = make_double2(fma(s, lP.x, p0.x), fma(s, lP.y, p0.y));
+  out[nlm + i] = make_double2(fma(s, lZ.x, z0.x), fma(s, lZ.y, z0.y));
+  out[2 * nlm + i] = make_double2(fma(s, lD.x, d0.x), fma(s, lD.y, d0.y));
+}
+
 // out = a + s * b over n complex entries (ETD2RK combinations)
 __global__ void k_axpy(const double2* __restrict__ a, const double2* __restrict__ b, double s,
                        double2* __restrict__ out, int n) {
@@ -98,6 +133,7 @@ struct swe_plan {
   rexi_plan *rp1 = nullptr, *rp2 = nullptr;  // etdrk: REXI of psi_1, psi_2 (same poles)
   sh_plan* sp = nullptr;
   double2 *NU = nullptr, *A3 = nullptr;      // etdrk: N(U), A
+  double4* Ltab = nullptr;                   // irk: (omega, cm, cp, n(n+1)/a^2) per (m, n)
   double2 *psi = nullptr, *chi = nullptr, *Um = nullptr, *Ut = nullptr, *dv = nullptr, *cu = nullptr,
           *kes = nullptr;
   double *PZ = nullptr, *Ug = nullptr, *Vg = nullptr, *A = nullptr, *B = nullptr, *KE = nullptr,
@@ -115,7 +151,7 @@ extern "C" int swe_plan_destroy(swe_plan* p) {
   p->prof.release();
   for (void* q : {(void*)p->psi, (void*)p->chi, (void*)p->Um, (void*)p->Ut, (void*)p->dv, (void*)p->cu,
                   (void*)p->kes, (void*)p->PZ, (void*)p->Ug, (void*)p->Vg, (void*)p->A, (void*)p->B,
-                  (void*)p->KE, (void*)p->c2, (void*)p->NU, (void*)p->A3})
+                  (void*)p->KE, (void*)p->c2, (void*)p->NU, (void*)p->A3, (void*)p->Ltab})
     cudaFree(q);
   delete p;
   return REXI_OK;
@@ -125,7 +161,8 @@ extern "C" int swe_plan_create(const swe_plan_desc* desc, swe_plan** out) {
   if (!desc || !out) return fail(REXI_EINVAL, "swe_plan_create: null argument");
   *out = nullptr;
   const swe_plan_desc& d = *desc;
-  if (d.scheme != SWE_L_REXI_N_ERK_VER1 && d.scheme != SWE_L_REXI_N_ERK_VER0 && d.scheme != SWE_L_REXI_N_ETDRK)
+  if (d.scheme != SWE_L_REXI_N_ERK_VER1 && d.scheme != SWE_L_REXI_N_ERK_VER0 && d.scheme != SWE_L_REXI_N_ETDRK &&
+      d.scheme != SWE_L_IRK_N_ERK_VER1)
     return fail(REXI_EINVAL, "swe_plan_create: unknown scheme %d", d.scheme);
   swe_plan* p = new swe_plan();
   p->d = d;
@@ -160,8 +197,33 @@ extern "C" int swe_plan_create(const swe_plan_desc* desc, swe_plan** out) {
   rd.heavy_tau = -1.0;
   rd.max_batch = 1;
   rd.stream = d.stream;
+  double cn_z[2] = {2.0, 0.0}, cn_w[2] = {2.0, 0.0};  // irk: one pole z = 2, weight 2, FP64
+  if (d.scheme == SWE_L_IRK_N_ERK_VER1) {
+    rd.N = 1;
+    rd.z = cn_z;
+    rd.w = cn_w;
+    rd.precision = REXI_FP64;
+  }
   rc = rexi_plan_create(&rd, &p->rp);
   if (rc) return bail(rc);
+  if (d.scheme == SWE_L_IRK_N_ERK_VER1) {
+    std::vector<double4> t(p->nlm);
+    for (int m = 0; m <= d.T; ++m)
+      for (int n = m; n <= d.T; ++n) {
+        auto eps = [&](int nn) { return nn > m ? std::sqrt((double(nn) * nn - double(m) * m) / (4.0 * nn * nn - 1.0)) : 0.0; };
+        const double nn1 = double(n) * (n + 1);
+        const double om = n > 0 ? 2.0 * d.omega * m / nn1 : 0.0;
+        const double cm = n > m ? 2.0 * d.omega * (n + 1.0) / n * eps(n) : 0.0;
+        const double cp = n > 0 && n < d.T ? 2.0 * d.omega * n / (n + 1.0) * eps(n + 1) : 0.0;
+        t[moff(d.T, m) + (n - m)] = make_double4(om, cm, cp, nn1 / (d.radius * d.radius));
+      }
+    cudaError_t e2;
+    if ((e2 = cudaMalloc(&p->Ltab, sizeof(double4) * p->nlm)) ||
+        (e2 = cudaMemcpy(p->Ltab, t.data(), sizeof(double4) * p->nlm, cudaMemcpyHostToDevice))) {
+      cudaGetLastError();
+      return bail(fail(REXI_ENOMEM, "swe_plan_create: operator table: %s", cudaGetErrorString(e2)));
+    }
+  }
   if (d.scheme == SWE_L_REXI_N_ETDRK) {  // psi_1 and psi_2 weights of the same poles
     std::vector<double> zz(2 * (size_t)d.N), ww(2 * (size_t)d.N);
     for (int k = 1; k <= 2; ++k) {
@@ -253,6 +315,13 @@ extern "C" int swe_step(swe_plan* p, void* state, int nsteps) {
       if ((rc = rexi_step(p->rp, U, p->Ut, 1))) return rc;
       if ((rc = rk2_nonlinear(p, p->Ut, dt))) return rc;
       if ((rc = rexi_step(p->rp, p->Ut, U, 1))) return rc;
+    } else if (p->d.scheme == SWE_L_IRK_N_ERK_VER1) {
+      if ((rc = rk2_nonlinear(p, U, 0.5 * dt))) return rc;
+      k_apply_L<<<(p->nlm + 255) / 256, 256, 0, p->stream>>>(U, p->Ltab, 0.5 * dt, p->d.phibar, p->Ut, p->d.T,
+                                                             p->nlm);
+      REXI_CUDA_TRY(cudaGetLastError());
+      if ((rc = rexi_step(p->rp, p->Ut, U, 1))) return rc;  // 2 (2 - dt L)^-1 (I + dt L / 2) U
+      if ((rc = rk2_nonlinear(p, U, 0.5 * dt))) return rc;
     } else {  // ETD2RK
       const int n3 = 3 * p->nlm, tb = 256, nb = (n3 + tb - 1) / tb;
       if ((rc = nonlinear_update(p, U, nullptr, 0.0, p->NU))) return rc;          // N(U)

@@ -435,7 +435,7 @@ class ShPlan:
 
 
 # ---- nonlinear shallow-water step (include/swe.h) ---------------------------------------
-SWE_VER1, SWE_VER0, SWE_ETDRK = 0, 1, 2
+SWE_VER1, SWE_VER0, SWE_ETDRK, SWE_IRK = 0, 1, 2, 3
 
 
 class SweDesc(ctypes.Structure):
@@ -457,8 +457,8 @@ SWE_STAGE_NAMES = ("rexi", "legendre", "fft", "grid_products")
 
 
 class SwePlan:
-    """Nonlinear SWE step on a Gauss grid: Strang split (l_rexi_n_erk_ver1 / ver0) or ETD2RK
-    (l_rexi_n_etdrk)."""
+    """Nonlinear SWE step on a Gauss grid: Strang split (l_rexi_n_erk_ver1 / ver0), ETD2RK
+    (l_rexi_n_etdrk) or Crank-Nicolson in the Strang split (l_irk_n_erk_ver1)."""
 
     def __init__(self, T, nlat, nlon, dt, omega, radius, phibar, N, p0, Xc, rexi_precision="fp64",
                  sh_precision="fp64", scheme="ver1", stream=None):
@@ -468,7 +468,7 @@ class SwePlan:
         d.N, d.p0, d.Xc = int(N), float(p0), float(Xc)
         d.rexi_precision = _PREC[rexi_precision] if isinstance(rexi_precision, str) else int(rexi_precision)
         d.sh_precision = _SH_PREC[sh_precision] if isinstance(sh_precision, str) else int(sh_precision)
-        d.scheme = ({"ver1": SWE_VER1, "ver0": SWE_VER0, "etdrk": SWE_ETDRK}[scheme]
+        d.scheme = ({"ver1": SWE_VER1, "ver0": SWE_VER0, "etdrk": SWE_ETDRK, "irk": SWE_IRK}[scheme]
                     if isinstance(scheme, str) else int(scheme))
         d.stream = ctypes.c_void_p(_stream_handle(stream))
         h = ctypes.c_void_p()
