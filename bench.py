@@ -79,6 +79,8 @@ def parse():
     ap.add_argument("--no-ensemble", action="store_true", help="skip the ragged-ensemble figure")
     ap.add_argument("--no-sh", action="store_true",
                     help="skip the SH-transform and nonlinear SWE-step figures")
+    ap.add_argument("--dt-sweep", action="store_true",
+                    help="error vs time-step size of the nonlinear schemes instead (T127, 12 h)")
     ap.add_argument("--serving", type=int, default=0,
                     help="run the request-stream workload with this many requests instead")
     return ap.parse_args()
@@ -418,6 +420,58 @@ def swe_steps(torch, rexi, configs):
     return out
 
 
+DT_SWEEP = [15.0, 30.0, 60.0, 120.0, 180.0, 360.0, 480.0, 600.0]   # the paper's REXI time steps
+
+
+def dt_sweep(args):
+    """Error vs time-step size of the nonlinear schemes (Strang ver1 / ver0 with REXI, ETD2RK,
+    Crank-Nicolson Strang) on the balanced n^-3 T127 state (192 x 384 Gauss grid, 512 poles),
+    over 12 h, against Strang ver1 with dt = 5 s: L-infinity of the surface-height error on the
+    grid (Phi' / g, the paper's metric) and the per-field relative L2."""
+    import numpy as np
+    import torch
+    from paper_1805_06557_gb300 import rexi
+    from paper_1805_06557_gb300 import synthetic as syn
+    T, nlat, nlon, N, t_end = 127, 192, 384, 512, 43200.0
+    U0 = syn.balanced_state(T, 2)
+
+    def run(scheme, dt, prec="fp64"):
+        sub = 0.5 * dt if scheme == "ver0" else dt
+        p0, Xc = contour(rexi.spectrum_bound(T, sub, syn.OMEGA, syn.RADIUS, syn.PHIBAR))
+        p = rexi.SwePlan(T, nlat, nlon, dt, syn.OMEGA, syn.RADIUS, syn.PHIBAR, N, p0, Xc,
+                         rexi_precision=prec, scheme=scheme)
+        u = torch.from_numpy(U0).cuda().contiguous()
+        n = int(round(t_end / dt))
+        t0 = time.perf_counter()
+        p.step(u, n)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        p.close()
+        return u, sec
+
+    ref, _ = run("ver1", 5.0)
+    sh = rexi.ShPlan(T, nlat, nlon, syn.RADIUS, "fp64", max_fields=1)
+    grid = torch.empty(1, nlat, nlon, dtype=torch.float64, device="cuda")
+    out = {"workload": "nonlinear SWE, T127 on 192 x 384, 512 poles, balanced n^-3 state (20 m/s rms), "
+                       "12 h; reference: Strang ver1 (FP64) with dt = 5 s", "schemes": {}}
+    r = ref.cpu().numpy()
+    for scheme in ("ver1", "ver0", "etdrk", "irk"):
+        res = {}
+        for dt in DT_SWEEP:
+            u, sec = run(scheme, dt)
+            d = (u - ref)[0:1].contiguous()
+            sh.synthesis(d, grid, 1)
+            torch.cuda.synchronize()
+            linf = float(grid.abs().max().item()) / syn.GRAVITY
+            a = u.cpu().numpy()
+            res["%g" % dt] = {"linf_h_m": linf if np.isfinite(linf) else None,
+                              "rel_l2": _rel_fields(a, r, T) if np.all(np.isfinite(a)) else None,
+                              "wall_s": sec}
+        out["schemes"][scheme] = res
+    sh.close()
+    print(json.dumps(out), flush=True)
+
+
 def _hbm_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -457,6 +511,9 @@ def main():
         return
     if args.serving:
         serving_run(args)
+        return
+    if args.dt_sweep:
+        dt_sweep(args)
         return
 
     import numpy as np
