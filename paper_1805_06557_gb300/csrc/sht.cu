@@ -8,8 +8,8 @@
 //
 // Layouts: Legendre tables [moff(m)+k][nh] (nh = nlat/2, latitude fastest: coalesced over
 // threads that own latitudes); Fourier workspace [field][m][nlat]; grids [field][nlat][nlon].
-// The FFT is a shared-memory Stockham autosort transform with radix-2 and radix-3 passes,
-// two real latitude rows packed into one complex sequence.
+// The FFT is a shared-memory Stockham autosort transform with radix-8, 4, 2 and 3 passes
+// (register butterflies), two real latitude rows packed into one complex sequence.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(ATH) k_leg_anal_divcurl(const double* __restri
   }
 }
 
-// ---- longitude FFT (Stockham autosort, radix 2 and 3, shared memory) ---------------------
+// ---- longitude FFT (Stockham autosort, radix 8, 4, 2 and 3, shared memory) -----------------
 // Templated on the arithmetic type: FP64 for SH_FP64 plans, FP32 for the tensor-core plans
 // (whose Legendre stage already rounds to TF32 / BF16); grids and Fourier arrays stay FP64.
 struct FftPlan {
@@ -283,59 +283,104 @@ template <typename C> __device__ __forceinline__ C c_mul(C a, C b) {
 template <typename C> __device__ __forceinline__ C c_add(C a, C b) { return Cx<C>::make(a.x + b.x, a.y + b.y); }
 template <typename C> __device__ __forceinline__ C c_sub(C a, C b) { return Cx<C>::make(a.x - b.x, a.y - b.y); }
 
+// R-point DFTs in registers, X_k = sum_j v_j w^{jk} with w = e^{sign 2 pi i / R}
+template <typename C> __device__ __forceinline__ C c_mul_i(C a, int sign) {  // (sign i) * a
+  return sign > 0 ? Cx<C>::make(-a.y, a.x) : Cx<C>::make(a.y, -a.x);
+}
+template <typename C> __device__ __forceinline__ void dft2(C& a, C& b) {
+  const C t = c_sub(a, b);
+  a = c_add(a, b);
+  b = t;
+}
+template <typename C> __device__ __forceinline__ void dft4(C& v0, C& v1, C& v2, C& v3, int sign) {
+  const C a0 = c_add(v0, v2), a1 = c_sub(v0, v2), a2 = c_add(v1, v3);
+  const C d = c_mul_i(c_sub(v1, v3), sign);
+  v0 = c_add(a0, a2);
+  v2 = c_sub(a0, a2);
+  v1 = c_add(a1, d);
+  v3 = c_sub(a1, d);
+}
+template <typename C> __device__ __forceinline__ void dft8(C* v, int sign) {
+  using R = typename Cx<C>::R;
+  const R h = R(0.70710678118654752440);  // 1/sqrt(2)
+  dft4(v[0], v[2], v[4], v[6], sign);     // even samples -> E_0..E_3 in v[0], v[2], v[4], v[6]
+  dft4(v[1], v[3], v[5], v[7], sign);     // odd samples  -> O_0..O_3 in v[1], v[3], v[5], v[7]
+  // twiddles w8^k O_k, w8 = (1 + sign i) / sqrt 2
+  const C o1 = Cx<C>::make(h * (v[3].x - sign * v[3].y), h * (v[3].y + sign * v[3].x));
+  const C o2 = c_mul_i(v[5], sign);
+  const C o3 = Cx<C>::make(h * (-v[7].x - sign * v[7].y), h * (-v[7].y + sign * v[7].x));
+  const C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
+  v[0] = c_add(e0, o0);
+  v[4] = c_sub(e0, o0);
+  v[1] = c_add(e1, o1);
+  v[5] = c_sub(e1, o1);
+  v[2] = c_add(e2, o2);
+  v[6] = c_sub(e2, o2);
+  v[3] = c_add(e3, o3);
+  v[7] = c_sub(e3, o3);
+}
+
+// One Stockham pass of radix R (2, 3, 4 or 8): for j < n / R, jm = j mod Ns, q = j / Ns, the
+// R inputs a[j + r n/R] times the twiddles w^{r jm stride} are transformed and written to
+// b[q Ns R + jm + r Ns].
+template <typename C, int R>
+__device__ __forceinline__ void fft_pass(const C* a, C* b, int n, int Ns, unsigned mg, const C* __restrict__ tw,
+                                         int sign) {
+  using Rt = typename Cx<C>::R;
+  const int nb = n / R;
+  const int stride = n / (Ns * R);
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+    const int q = (Ns == 1) ? j : (int)__umulhi((unsigned)j, mg);  // j / Ns
+    const int jm = j - q * Ns;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      v[r] = a[j + r * nb];
+      if (r > 0 && jm) {
+        C t = tw[r * jm * stride];  // r jm stride < n
+        if (sign > 0) t.y = -t.y;
+        v[r] = c_mul(v[r], t);
+      }
+    }
+    if (R == 2) {
+      dft2(v[0], v[1]);
+    } else if (R == 4) {
+      dft4(v[0], v[1], v[2], v[3], sign);
+    } else if (R == 8) {
+      dft8(v, sign);
+    } else {  // R == 3
+      const C s1 = c_add(v[1], v[2]);
+      const C t2 = Cx<C>::make(v[0].x - Rt(0.5) * s1.x, v[0].y - Rt(0.5) * s1.y);
+      const C d = c_sub(v[1], v[2]);
+      const Rt sg = Rt(sign * SQRT3_2);
+      const C x0 = c_add(v[0], s1);
+      v[1] = Cx<C>::make(t2.x - sg * d.y, t2.y + sg * d.x);
+      v[2] = Cx<C>::make(t2.x + sg * d.y, t2.y - sg * d.x);
+      v[0] = x0;
+    }
+    const int base = q * Ns * R + jm;
+#pragma unroll
+    for (int r = 0; r < R; ++r) b[base + r * Ns] = v[r];
+  }
+}
+
 // in-place on two shared buffers; returns the buffer holding the result.  sign = -1 forward,
 // +1 inverse (no scaling).  tw[k] = e^{-2 pi i k / n}.
 template <typename C>
 __device__ C* fft_smem(C* a, C* b, const FftPlan& fp, const C* __restrict__ tw, int sign) {
-  using R = typename Cx<C>::R;
   const int n = fp.n;
   int Ns = 1;
   for (int s = 0; s < fp.nrad; ++s) {
-    const int R_ = fp.rad[s];
-    const int nb = n / R_;
-    const int stride = n / (Ns * R_);
-    const unsigned mg = fp.magic[s];
-    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-      const int q = (Ns == 1) ? j : (int)__umulhi((unsigned)j, mg);  // j / Ns
-      const int jm = j - q * Ns;
-      const int idxD = q * Ns * R_ + jm;
-      if (R_ == 2) {
-        const C v0 = a[j];
-        C v1 = a[j + nb];
-        if (jm) {
-          C t = tw[jm * stride];  // jm * stride < n / 2
-          if (sign > 0) t.y = -t.y;
-          v1 = c_mul(v1, t);
-        }
-        b[idxD] = c_add(v0, v1);
-        b[idxD + Ns] = c_sub(v0, v1);
-      } else {  // R == 3
-        const C v0 = a[j];
-        C v1 = a[j + nb], v2 = a[j + 2 * nb];
-        if (jm) {
-          C t1 = tw[jm * stride], t2 = tw[2 * jm * stride];  // 2 jm stride < 2 n / 3
-          if (sign > 0) {
-            t1.y = -t1.y;
-            t2.y = -t2.y;
-          }
-          v1 = c_mul(v1, t1);
-          v2 = c_mul(v2, t2);
-        }
-        const C s1 = c_add(v1, v2);
-        const C t2 = Cx<C>::make(v0.x - R(0.5) * s1.x, v0.y - R(0.5) * s1.y);
-        const C d = c_sub(v1, v2);
-        const R sg = R(sign * SQRT3_2);
-        // i * sg * d = (-sg d.y, sg d.x)
-        b[idxD] = c_add(v0, s1);
-        b[idxD + Ns] = Cx<C>::make(t2.x - sg * d.y, t2.y + sg * d.x);
-        b[idxD + 2 * Ns] = Cx<C>::make(t2.x + sg * d.y, t2.y - sg * d.x);
-      }
-    }
+    const int R = fp.rad[s];
+    if (R == 8) fft_pass<C, 8>(a, b, n, Ns, fp.magic[s], tw, sign);
+    else if (R == 4) fft_pass<C, 4>(a, b, n, Ns, fp.magic[s], tw, sign);
+    else if (R == 2) fft_pass<C, 2>(a, b, n, Ns, fp.magic[s], tw, sign);
+    else fft_pass<C, 3>(a, b, n, Ns, fp.magic[s], tw, sign);
     __syncthreads();
     C* t = a;
     a = b;
     b = t;
-    Ns *= R_;
+    Ns *= R;
   }
   return a;
 }
@@ -437,6 +482,14 @@ bool fft_factor(int n, FftPlan& fp) {
   fp.n = n;
   fp.nrad = 0;
   int m = n;
+  while (m % 8 == 0 && fp.nrad < 24) {
+    fp.rad[fp.nrad++] = 8;
+    m /= 8;
+  }
+  while (m % 4 == 0 && fp.nrad < 24) {
+    fp.rad[fp.nrad++] = 4;
+    m /= 4;
+  }
   while (m % 2 == 0 && fp.nrad < 24) {
     fp.rad[fp.nrad++] = 2;
     m /= 2;
