@@ -153,14 +153,6 @@ __global__ void __launch_bounds__(LTH) k_leg_synth_uv(const double* __restrict__
 // ---- Legendre analysis -------------------------------------------------------------
 constexpr int ATH = 256;
 
-__device__ __forceinline__ double2 warp_sum2(double2 v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
-  }
-  return v;
-}
 
 __global__ void __launch_bounds__(ATH) k_leg_anal(const double* __restrict__ P,
                                                   const double* __restrict__ w,
@@ -179,19 +171,35 @@ __global__ void __launch_bounds__(ATH) k_leg_anal(const double* __restrict__ P,
     So[j] = make_double2(wj * (a.x - b.x), wj * (a.y - b.y));
   }
   __syncthreads();
+  // one thread per degree: it streams its own table row (32-byte pieces when nh % 4 == 0)
+  // against the shared hemispheric sums; no cross-lane reduction
   const int K = T + 1 - m, base = moff(T, m);
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  for (int k = wp; k < K; k += ATH / 32) {
+  for (int k = threadIdx.x; k < K; k += ATH) {
     const double* Pk = P + (size_t)(base + k) * nh;
     const double2* src = (k & 1) ? So : Se;
     double2 acc = make_double2(0, 0);
-    for (int j = lane; j < nh; j += 32) {
-      const double p = Pk[j];
-      acc.x = fma(p, src[j].x, acc.x);
-      acc.y = fma(p, src[j].y, acc.y);
+    if ((nh & 3) == 0) {
+      const double2* P2 = reinterpret_cast<const double2*>(Pk);
+      for (int j4 = 0; j4 < nh / 4; ++j4) {
+        const double2 pa = __ldg(P2 + 2 * j4), pb = __ldg(P2 + 2 * j4 + 1);  // one 32-byte sector
+        const double2 s0 = src[4 * j4], s1 = src[4 * j4 + 1], s2 = src[4 * j4 + 2], s3 = src[4 * j4 + 3];
+        acc.x = fma(pa.x, s0.x, acc.x);
+        acc.y = fma(pa.x, s0.y, acc.y);
+        acc.x = fma(pa.y, s1.x, acc.x);
+        acc.y = fma(pa.y, s1.y, acc.y);
+        acc.x = fma(pb.x, s2.x, acc.x);
+        acc.y = fma(pb.x, s2.y, acc.y);
+        acc.x = fma(pb.y, s3.x, acc.x);
+        acc.y = fma(pb.y, s3.y, acc.y);
+      }
+    } else {
+      for (int j = 0; j < nh; ++j) {
+        const double p = __ldg(Pk + j);
+        acc.x = fma(p, src[j].x, acc.x);
+        acc.y = fma(p, src[j].y, acc.y);
+      }
     }
-    acc = warp_sum2(acc);
-    if (lane == 0) spec[(size_t)f * nlm + base + k] = acc;
+    spec[(size_t)f * nlm + base + k] = acc;
   }
 }
 
@@ -221,9 +229,9 @@ __global__ void __launch_bounds__(ATH) k_leg_anal_divcurl(const double* __restri
     Bm[j] = make_double2(q * (bn.x - bs.x), q * (bn.y - bs.y));
   }
   __syncthreads();
+  // one thread per degree (see k_leg_anal)
   const int K = T + 1 - m, base = moff(T, m);
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  for (int k = wp; k < K; k += ATH / 32) {
+  for (int k = threadIdx.x; k < K; k += ATH) {
     const double* Pk = P + (size_t)(base + k) * nh;
     const double* Hk = H + (size_t)(base + k) * nh;
     const bool odd = k & 1;
@@ -233,26 +241,34 @@ __global__ void __launch_bounds__(ATH) k_leg_anal_divcurl(const double* __restri
     const double2* AH = odd ? Ap : Am;
     const double2* BH = odd ? Bp : Bm;
     double2 sPA = make_double2(0, 0), sPB = sPA, sHA = sPA, sHB = sPA;
-    for (int j = lane; j < nh; j += 32) {
-      const double p = Pk[j], h = Hk[j];
-      sPA.x = fma(p, AP[j].x, sPA.x);
-      sPA.y = fma(p, AP[j].y, sPA.y);
-      sPB.x = fma(p, BP[j].x, sPB.x);
-      sPB.y = fma(p, BP[j].y, sPB.y);
-      sHA.x = fma(h, AH[j].x, sHA.x);
-      sHA.y = fma(h, AH[j].y, sHA.y);
-      sHB.x = fma(h, BH[j].x, sHB.x);
-      sHB.y = fma(h, BH[j].y, sHB.y);
+    auto step = [&](double p, double h, int j) {
+      const double2 ap = AP[j], bp = BP[j], ah = AH[j], bh = BH[j];
+      sPA.x = fma(p, ap.x, sPA.x);
+      sPA.y = fma(p, ap.y, sPA.y);
+      sPB.x = fma(p, bp.x, sPB.x);
+      sPB.y = fma(p, bp.y, sPB.y);
+      sHA.x = fma(h, ah.x, sHA.x);
+      sHA.y = fma(h, ah.y, sHA.y);
+      sHB.x = fma(h, bh.x, sHB.x);
+      sHB.y = fma(h, bh.y, sHB.y);
+    };
+    if ((nh & 3) == 0) {
+      const double2* P2 = reinterpret_cast<const double2*>(Pk);
+      const double2* H2 = reinterpret_cast<const double2*>(Hk);
+      for (int j4 = 0; j4 < nh / 4; ++j4) {
+        const double2 pa = __ldg(P2 + 2 * j4), pb = __ldg(P2 + 2 * j4 + 1);
+        const double2 ha = __ldg(H2 + 2 * j4), hb = __ldg(H2 + 2 * j4 + 1);
+        step(pa.x, ha.x, 4 * j4);
+        step(pa.y, ha.y, 4 * j4 + 1);
+        step(pb.x, hb.x, 4 * j4 + 2);
+        step(pb.y, hb.y, 4 * j4 + 3);
+      }
+    } else {
+      for (int j = 0; j < nh; ++j) step(__ldg(Pk + j), __ldg(Hk + j), j);
     }
-    sPA = warp_sum2(sPA);
-    sPB = warp_sum2(sPB);
-    sHA = warp_sum2(sHA);
-    sHB = warp_sum2(sHB);
-    if (lane == 0) {
-      const double2 iPA = imul(m, sPA), iPB = imul(m, sPB);
-      dv[(size_t)f * nlm + base + k] = make_double2(inv_a * (iPA.x - sHB.x), inv_a * (iPA.y - sHB.y));
-      cu[(size_t)f * nlm + base + k] = make_double2(inv_a * (iPB.x + sHA.x), inv_a * (iPB.y + sHA.y));
-    }
+    const double2 iPA = imul(m, sPA), iPB = imul(m, sPB);
+    dv[(size_t)f * nlm + base + k] = make_double2(inv_a * (iPA.x - sHB.x), inv_a * (iPA.y - sHB.y));
+    cu[(size_t)f * nlm + base + k] = make_double2(inv_a * (iPB.x + sHA.x), inv_a * (iPB.y + sHA.y));
   }
 }
 
