@@ -38,9 +38,9 @@ struct Job {
   int b_off;        // byte offset of the job's B operand in the B buffer
   int d_off;        // float offset of the job's D tile in the D buffer
   int nchunk;       // K chunks
-  int kpad;         // K extent of B (nchunk * KC)
+  int kpad;         // K extent of B (whole MMA k-steps; (nchunk - 1) * KC + kl)
   int tab;          // 0 = P, 1 = H
-  int pad;
+  int kl;           // K of the last chunk (a multiple of the MMA k-step, <= KC)
 };
 
 struct GemmArgs {
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(GemmArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
   // element type constants: 16-byte core-matrix rows hold E elements; a chunk (KC = 128 B of
   // K per row) is 4 MMA k-steps of 32 B; consecutive k-steps are 2 core matrices (256 B) apart
-  constexpr int E = BF ? 8 : 4, eb = BF ? 2 : 4, KC = BF ? 64 : 32;
+  constexpr int E = BF ? 8 : 4, eb = BF ? 2 : 4, KC = BF ? 64 : 32, KSTEP = BF ? 16 : 8;
   constexpr uint32_t chunk_bytes = 128u * KC * eb;
   static_assert(KC * eb == 128, "a chunk row is 128 bytes of K");
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -146,8 +146,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(GemmArgs g) {
         for (int c = 0; c < jb.nchunk; ++c) {
           if (round > 0) ok = tc::mbar_wait(empty0 + 8 * s, (round - 1) & 1);
           if (!ok) break;
-          tc::mbar_expect_tx(full0 + 8 * s, chunk_bytes);
-          tc::bulk_g2s(sa0 + s * chunk_bytes, A + (size_t)c * chunk_bytes, chunk_bytes, full0 + 8 * s);
+          const uint32_t cb = (c == jb.nchunk - 1) ? 128u * jb.kl * eb : chunk_bytes;
+          tc::mbar_expect_tx(full0 + 8 * s, cb);
+          tc::bulk_g2s(sa0 + s * chunk_bytes, A + (size_t)c * chunk_bytes, cb, full0 + 8 * s);
           ++a_issued;
           if (++s == S) {
             s = 0;
@@ -180,13 +181,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(GemmArgs g) {
           ok = tc::mbar_wait(full0 + 8 * s, round & 1);
           if (!ok) break;
           tc::fence_after_sync();
-          const uint64_t ad = tc::smem_desc(sa0 + s * chunk_bytes, 128u, sboA);
+          // the last chunk may be short: its own core-matrix stride and fewer k-steps
+          const int kc = (c == jb.nchunk - 1) ? jb.kl : KC;
+          const uint64_t ad = tc::smem_desc(sa0 + s * chunk_bytes, 128u, kc == KC ? sboA : (uint32_t)(kc / E) * 128u);
           const uint64_t bd = bdesc0 + (uint64_t)(c * ((KC / E) * 128 / 16));  // + c * 1024 B
           const uint32_t accum = c > 0 ? 1u : 0u;
+          const int nks = kc / KSTEP;
 #pragma unroll
           for (int q = 0; q < TC_NACC; ++q) {  // + 256 B per k-step: +16 in the address field
-            if (BF) tc::mma_f16(dt + 32u * q, ad + 16u * q, bd + 16u * q, idesc, accum);
-            else tc::mma_tf32(dt + 32u * q, ad + 16u * q, bd + 16u * q, idesc, accum);
+            if (q < nks) {
+              if (BF) tc::mma_f16(dt + 32u * q, ad + 16u * q, bd + 16u * q, idesc, accum);
+              else tc::mma_tf32(dt + 32u * q, ad + 16u * q, bd + 16u * q, idesc, accum);
+            }
           }
           tc::mma_commit(empty0 + 8 * s);
           if (++s == S) {
@@ -222,12 +228,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(GemmArgs g) {
           tc::tmem_ld8_nowait(ta + 32u * a + 8, r[a] + 8);
         }
         tc::tmem_wait_ld();
+        // accumulators a < nacc received k-steps (all four unless the job is one short chunk)
+        const int nacc = jb.nchunk > 1 ? TC_NACC : jb.kl / KSTEP;
         float v[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           v[q] = __uint_as_float(r[0][q]);
 #pragma unroll
-          for (int a = 1; a < TC_NACC; ++a) v[q] += __uint_as_float(r[a][q]);
+          for (int a = 1; a < TC_NACC; ++a)
+            if (a < nacc) v[q] += __uint_as_float(r[a][q]);
         }
         float4* d4 = reinterpret_cast<float4*>(Dj + c);
 #pragma unroll
@@ -270,7 +279,7 @@ __device__ __forceinline__ void store_elem(unsigned char* base, size_t off, floa
 // tables: one thread per (job, row), looping over K; src = FP64 table [moff+k][nh]
 struct TabJob {
   long long a_off;
-  int m, par, tile, nchunk;
+  int m, par, tile, nchunk, kl;  // kl: K of the last chunk
 };
 __global__ void k_tc_table(const double* __restrict__ src, unsigned char* __restrict__ dst,
                            const TabJob* __restrict__ jobs, int njobs, int T, int nh, int synth,
@@ -280,12 +289,14 @@ __global__ void k_tc_table(const double* __restrict__ src, unsigned char* __rest
   const TabJob j = jobs[jid];
   const int r = threadIdx.x;  // 0..127
   const int E = bf16 ? 8 : 4, eb = bf16 ? 2 : 4, KC = bf16 ? 64 : 32;
-  const int sbo = (KC / E) * 128;
   const int K = T + 1 - j.m, base = moff(T, j.m);
   unsigned char* out = dst + j.a_off;
   for (int c = 0; c < j.nchunk; ++c) {
+    // every chunk but the last holds KC K-elements per row; the last holds j.kl
+    const int kc = (c == j.nchunk - 1) ? j.kl : KC;
+    const int sbo = (kc / E) * 128;
     unsigned char* ch = out + (size_t)c * 128 * KC * eb;
-    for (int kk = 0; kk < KC; ++kk) {
+    for (int kk = 0; kk < kc; ++kk) {
       float v = 0.f;
       if (synth) {  // rows = latitudes, K = degrees of the parity
         const int lat = j.tile * 128 + r;
@@ -482,24 +493,27 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
   int boff = 0, doff = 0;
   const int ncols_max = TC_MAXCOL;
   std::vector<Job> jsP, jsH;
+  const int kstep = bf16 ? 16 : 8;  // MMA K per instruction
   for (int m = 0; m <= T; ++m)
     for (int par = 0; par < 2; ++par) {
       const int K = T + 1 - m;
       const int kpar = (K - par + 1) / 2;
-      const int nchunk = (kpar + KC - 1) / KC;
+      const int kpad = (kpar + kstep - 1) / kstep * kstep;  // K padded to whole k-steps only
+      const int nchunk = (kpad + KC - 1) / KC;
+      const int kl = kpad - (nchunk - 1) * KC;
       boff_s[m * 2 + par] = boff;
-      kpad_s[m * 2 + par] = nchunk * KC;
-      boff += ncols_max * nchunk * KC * eb;
+      kpad_s[m * 2 + par] = kpad;
+      boff += ncols_max * kpad * eb;
       if (nchunk == 0) continue;
       for (int tile = 0; tile < t->ntile_s; ++tile) {
-        tj.push_back(TabJob{aoff, m, par, tile, nchunk});
+        tj.push_back(TabJob{aoff, m, par, tile, nchunk, kl});
         for (int tab = 0; tab < 2; ++tab) {
-          Job j{aoff, boff_s[m * 2 + par], doff, nchunk, nchunk * KC, tab, 0};
+          Job j{aoff, boff_s[m * 2 + par], doff, nchunk, kpad, tab, kl};
           (tab ? jsH : jsP).push_back(j);
           dmap_s[((m * 2 + par) * t->ntile_s + tile) * 2 + tab] = doff;
           doff += 128 * ncols_max;
         }
-        aoff += (long long)nchunk * chunk;
+        aoff += (long long)(nchunk - 1) * chunk + 128LL * kl * eb;
       }
     }
   const long long tab_s_bytes = aoff;
@@ -513,8 +527,9 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
   js.insert(js.end(), jsH.begin(), jsH.end());
   t->njobs_s = (int)js.size();
   // ---- analysis jobs: (m, par, degree tile, tab), K = northern latitudes ------------------
-  t->kpad_a = (t->nh + KC - 1) / KC * KC;
-  const int nchunk_a = t->kpad_a / KC;
+  t->kpad_a = (t->nh + kstep - 1) / kstep * kstep;
+  const int nchunk_a = (t->kpad_a + KC - 1) / KC;
+  const int kl_a = t->kpad_a - (nchunk_a - 1) * KC;
   int ntile_a = 0;
   for (int m = 0; m <= T; ++m) ntile_a = std::max(ntile_a, ((T + 1 - m + 1) / 2 + 127) / 128);
   t->ntile_a = ntile_a;
@@ -535,16 +550,16 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
       const int kpar = (K - par + 1) / 2;
       const int ntiles = (kpar + 127) / 128;
       for (int tile = 0; tile < ntiles; ++tile) {
-        ta.push_back(TabJob{aoff, m, par, tile, nchunk_a});
+        ta.push_back(TabJob{aoff, m, par, tile, nchunk_a, kl_a});
         for (int tab = 0; tab < 2; ++tab) {
           // P pairs with (N + s S), H with (N - s S), s = (-1)^par: plus for (P, even), (H, odd)
           const int sg = (tab == 0) ? par : 1 - par;
-          Job j{aoff, boff_a[m * 2 + sg], doff, nchunk_a, t->kpad_a, tab, 0};
+          Job j{aoff, boff_a[m * 2 + sg], doff, nchunk_a, t->kpad_a, tab, kl_a};
           (tab ? jaH : jaP).push_back(j);
           dmap_a[((m * 2 + par) * ntile_a + tile) * 2 + tab] = doff;
           doff += 128 * ncols_max;
         }
-        aoff += (long long)nchunk_a * chunk;
+        aoff += (long long)(nchunk_a - 1) * chunk + 128LL * kl_a * eb;
       }
     }
   const long long tab_a_bytes = aoff;
