@@ -73,11 +73,12 @@ constexpr uint32_t TC_TMEM_COLS = 512;  // >= TC_NJB x TC_NACC x 32 columns, a p
 template <bool BF>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(GemmArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  // element type constants: 16-byte core-matrix rows hold E elements; a chunk (KC = 128 B of
-  // K per row) is 4 MMA k-steps of 32 B; consecutive k-steps are 2 core matrices (256 B) apart
-  constexpr int E = BF ? 8 : 4, eb = BF ? 2 : 4, KC = BF ? 64 : 32, KSTEP = BF ? 16 : 8;
+  // element type constants: 16-byte core-matrix rows hold E elements; a chunk (KC = 256 B of
+  // K per row) is 8 MMA k-steps of 32 B; consecutive k-steps are 2 core matrices (256 B) apart
+  constexpr int E = BF ? 8 : 4, eb = BF ? 2 : 4, KC = BF ? 128 : 64, KSTEP = BF ? 16 : 8;
   constexpr uint32_t chunk_bytes = 128u * KC * eb;
-  static_assert(KC * eb == 128, "a chunk row is 128 bytes of K");
+  static_assert(KC * eb == 256, "a chunk row is 256 bytes of K");
+  constexpr int KSTEPS = KC / KSTEP;  // k-steps per full chunk (8)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int S = g.stages, NB = g.nb;
   unsigned char* sA = smem;
@@ -184,14 +185,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(GemmArgs g) {
           // the last chunk may be short: its own core-matrix stride and fewer k-steps
           const int kc = (c == jb.nchunk - 1) ? jb.kl : KC;
           const uint64_t ad = tc::smem_desc(sa0 + s * chunk_bytes, 128u, kc == KC ? sboA : (uint32_t)(kc / E) * 128u);
-          const uint64_t bd = bdesc0 + (uint64_t)(c * ((KC / E) * 128 / 16));  // + c * 1024 B
-          const uint32_t accum = c > 0 ? 1u : 0u;
+          const uint64_t bd = bdesc0 + (uint64_t)(c * ((KC / E) * 128 / 16));  // + c * 2048 B
           const int nks = kc / KSTEP;
 #pragma unroll
-          for (int q = 0; q < TC_NACC; ++q) {  // + 256 B per k-step: +16 in the address field
+          for (int q = 0; q < KSTEPS; ++q) {  // + 256 B per k-step: +16 in the address field
+            // k-step q goes to accumulator q % TC_NACC; its first use initialises it
+            const uint32_t accum = (c > 0 || q >= TC_NACC) ? 1u : 0u;
+            const uint32_t da = dt + 32u * (q % TC_NACC);
             if (q < nks) {
-              if (BF) tc::mma_f16(dt + 32u * q, ad + 16u * q, bd + 16u * q, idesc, accum);
-              else tc::mma_tf32(dt + 32u * q, ad + 16u * q, bd + 16u * q, idesc, accum);
+              if (BF) tc::mma_f16(da, ad + 16u * q, bd + 16u * q, idesc, accum);
+              else tc::mma_tf32(da, ad + 16u * q, bd + 16u * q, idesc, accum);
             }
           }
           tc::mma_commit(empty0 + 8 * s);
@@ -229,7 +232,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(GemmArgs g) {
         }
         tc::tmem_wait_ld();
         // accumulators a < nacc received k-steps (all four unless the job is one short chunk)
-        const int nacc = jb.nchunk > 1 ? TC_NACC : jb.kl / KSTEP;
+        const int nacc = jb.nchunk > 1 ? TC_NACC : min(TC_NACC, jb.kl / KSTEP);
         float v[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
@@ -288,7 +291,7 @@ __global__ void k_tc_table(const double* __restrict__ src, unsigned char* __rest
   if (jid >= njobs) return;
   const TabJob j = jobs[jid];
   const int r = threadIdx.x;  // 0..127
-  const int E = bf16 ? 8 : 4, eb = bf16 ? 2 : 4, KC = bf16 ? 64 : 32;
+  const int E = bf16 ? 8 : 4, eb = bf16 ? 2 : 4, KC = bf16 ? 128 : 64;  // as TcLegendre::KC
   const int K = T + 1 - j.m, base = moff(T, j.m);
   unsigned char* out = dst + j.a_off;
   for (int c = 0; c < j.nchunk; ++c) {
@@ -479,7 +482,7 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
   t->bf16 = bf16 ? 1 : 0;
   t->E = bf16 ? 8 : 4;
   t->eb = bf16 ? 2 : 4;
-  t->KC = bf16 ? 64 : 32;
+  t->KC = bf16 ? 128 : 64;   // 256 bytes of K per chunk row
   t->w = w;
   t->wq = wq;
   const int KC = t->KC, eb = t->eb;
@@ -653,7 +656,7 @@ static int gemm(TcLegendre* t, bool synth, bool both_tabs, int ncols, cudaStream
   g.nj_max = (g.njobs + grid - 1) / grid;
   const size_t jobs_bytes = sizeof(Job) * (size_t)g.nj_max;
   auto fixed = [&](int nb) { return nb * bslot + 8 * (2 * TC_MAXSTAGES + 2 * nb + 2 * TC_NJB + 2) + jobs_bytes; };
-  g.nb = (fixed(TC_MAXNB) + 4 * chunk <= TC_SMEM_BUDGET) ? TC_MAXNB : 2;
+  g.nb = (fixed(TC_MAXNB) + 4 * chunk <= TC_SMEM_BUDGET) ? TC_MAXNB : 2;  // keep >= 4 ring stages
   if (fixed(g.nb) + 2 * chunk > TC_SMEM_BUDGET) return fail(REXI_EINVAL, "tensor-core Legendre: B operand too large");
   g.stages = (int)std::min<size_t>(TC_MAXSTAGES, (TC_SMEM_BUDGET - fixed(g.nb)) / chunk);
   g.bslot = (uint32_t)bslot;
