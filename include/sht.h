@@ -29,7 +29,9 @@ typedef struct sh_plan_desc {
   int nlat, nlon;   /* Gauss grid, nlat even and > T, nlon > 2T, nlon = 2^p 3^q              */
   double radius;    /* sphere radius a [m] (vector transforms)                              */
   int precision;    /* SH_FP64, SH_TF32 or SH_BF16                                          */
-  int max_fields;   /* largest nfields passed to a transform                                */
+  int max_fields;   /* largest nfields passed to a transform; SH_TF32 / SH_BF16: <= 8, and   */
+                    /* the vector analysis operand (8 max_fields rows x nlat/2 latitudes)    */
+                    /* must fit in shared memory (e.g. max_fields <= 4 at nlat = 1536 TF32)  */
   void* stream;     /* cudaStream_t                                                         */
 } sh_plan_desc;
 

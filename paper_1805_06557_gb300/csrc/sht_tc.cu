@@ -30,7 +30,7 @@ namespace {
 
 constexpr int TC_MAXSTAGES = 8;     // depth of the A-chunk ring
 constexpr int TC_THREADS = 192;     // warps 0-3 epilogue, warp 4 bulk copies, warp 5 MMA issue
-constexpr int TC_MAXCOL = 32;
+constexpr int TC_MAXCOL = 32;      // B columns of a synthesis call; analysis uses 2 x ncols
 constexpr size_t TC_SMEM_BUDGET = 220 * 1024;
 
 struct Job {
@@ -51,7 +51,7 @@ struct GemmArgs {
   const Job* jobs;
   int njobs, ncols, bf16;
   int stages;       // A ring depth (<= TC_MAXSTAGES)
-  int nb;           // B buffers (2 or 4): B operands are fetched up to nb - 1 jobs ahead
+  int nb;           // B buffers (1, 2 or 4): B operands are fetched up to nb - 1 jobs ahead
   int nj_max;       // jobs per CTA at most (their descriptors are staged in shared memory)
   uint32_t bslot;   // bytes of one B buffer
   int* err;
@@ -68,8 +68,8 @@ struct GemmArgs {
 // error code and stops, and teardown drains the copies and MMAs in flight.
 constexpr int TC_MAXNB = 4;
 constexpr int TC_NACC = 4;          // independent accumulators per job (one per k-step of a chunk)
-constexpr int TC_NJB = 3;           // job buffers of accumulators in TMEM
-constexpr uint32_t TC_TMEM_COLS = 512;  // >= TC_NJB x TC_NACC x 32 columns, a power of two
+constexpr int TC_NJB = 3;           // job buffers of accumulators in TMEM (at most; 2 when N > 32)
+constexpr uint32_t TC_TMEM_COLS = 512;  // TC_NJB x TC_NACC x 32 (N <= 32) or 2 x TC_NACC x 64 (N <= 64)
 template <bool BF>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(GemmArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -105,6 +105,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(GemmArgs g) {
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *taddr_s;
+  // accumulator column stride (N rounded to 32) and the job buffers that fit in TMEM_COLS
+  const uint32_t cs = (uint32_t)((g.ncols + 31) / 32 * 32);
+  const int njb = min(TC_NJB, (int)(TC_TMEM_COLS / (cs * TC_NACC)));
   const uint32_t sa0 = tc::smem_u32(sA), sb0 = tc::smem_u32(sB);
   long long a_issued = 0;  // producer: A fills issued
   int b_issued = 0;        // producer: B fills issued (jobs 0 .. b_issued - 1)
@@ -169,14 +172,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(GemmArgs g) {
       uint32_t round = 0;
       for (int i = 0; i < nj && ok; ++i) {
         const Job jb = sjobs[i];
-        const int b = i % NB, ub = i / NB, acc = i % TC_NJB, ua = i / TC_NJB;
+        const int b = i % NB, ub = i / NB, acc = i % njb, ua = i / njb;
         ok = tc::mbar_wait(bfull0 + 8 * b, ub & 1);
         if (ok && ua > 0) ok = tc::mbar_wait(tempty0 + 8 * acc, (ua - 1) & 1);
         if (!ok) break;
         tc::fence_after_sync();
-        // k-step q of every chunk accumulates into accumulator q of job buffer acc, so that
-        // consecutive MMAs do not wait on each other's result
-        const uint32_t dt = tmem + 32u * TC_NACC * acc;
+        // k-step q of every chunk accumulates into accumulator q % TC_NACC of job buffer acc,
+        // so that consecutive MMAs do not wait on each other's result
+        const uint32_t dt = tmem + cs * TC_NACC * acc;
         const uint64_t bdesc0 = tc::smem_desc(sb0 + b * g.bslot, 128u, (uint32_t)(jb.kpad / E) * 128u);
         for (int c = 0; c < jb.nchunk; ++c) {
           ok = tc::mbar_wait(full0 + 8 * s, round & 1);
@@ -191,7 +194,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(GemmArgs g) {
           for (int q = 0; q < KSTEPS; ++q) {  // + 256 B per k-step: +16 in the address field
             // k-step q goes to accumulator q % TC_NACC; its first use initialises it
             const uint32_t accum = (c > 0 || q >= TC_NACC) ? 1u : 0u;
-            const uint32_t da = dt + 32u * (q % TC_NACC);
+            const uint32_t da = dt + cs * (q % TC_NACC);
             if (q < nks) {
               if (BF) tc::mma_f16(da, ad + 16u * q, bd + 16u * q, idesc, accum);
               else tc::mma_tf32(da, ad + 16u * q, bd + 16u * q, idesc, accum);
@@ -215,7 +218,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(GemmArgs g) {
     // loads of a 16-column group are issued before one wait
     for (int i = 0; i < nj; ++i) {
       const Job jb = sjobs[i];
-      const int acc = i % TC_NJB, u = i / TC_NJB;
+      const int acc = i % njb, u = i / njb;
       if (!tc::mbar_wait(tfull0 + 8 * acc, u & 1)) {
         if (lane == 0) atomicExch(g.err, 2);
         break;
@@ -224,11 +227,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(GemmArgs g) {
       float* Dj = g.D + jb.d_off + (size_t)(32 * warp + lane) * g.ncols;
       for (int c = 0; c < g.ncols; c += 16) {
         uint32_t r[TC_NACC][16];
-        const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + 32u * TC_NACC * acc + c;
+        const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + cs * TC_NACC * acc + c;
 #pragma unroll
         for (int a = 0; a < TC_NACC; ++a) {
-          tc::tmem_ld8_nowait(ta + 32u * a, r[a]);
-          tc::tmem_ld8_nowait(ta + 32u * a + 8, r[a] + 8);
+          tc::tmem_ld8_nowait(ta + cs * a, r[a]);
+          tc::tmem_ld8_nowait(ta + cs * a + 8, r[a] + 8);
         }
         tc::tmem_wait_ld();
         // accumulators a < nacc received k-steps (all four unless the job is one short chunk)
@@ -305,8 +308,8 @@ __global__ void k_tc_table(const double* __restrict__ src, unsigned char* __rest
         const int lat = j.tile * 128 + r;
         const int k = j.par + 2 * (c * KC + kk);
         if (lat < nh && k < K) v = (float)src[(size_t)(base + k) * nh + lat];
-      } else {      // rows = degrees of the parity, K = latitudes
-        const int k = j.par + 2 * (j.tile * 128 + r);
+      } else {      // rows = degrees (both parities), K = latitudes
+        const int k = j.tile * 128 + r;
         const int lat = c * KC + kk;
         if (lat < nh && k < K) v = (float)src[(size_t)(base + k) * nh + lat];
       }
@@ -350,12 +353,12 @@ __global__ void k_tc_banal(const double2* __restrict__ F0, const double2* __rest
                            const double* __restrict__ wts, unsigned char* __restrict__ B,
                            const int* __restrict__ boff, int kpad, int T, int nlat, int nf, int cpf,
                            int ncols, int bf16) {
+  // B of zonal order m: 2 ncols rows (N + S combinations, then N - S), K = latitudes
   const int m = blockIdx.x, sg = blockIdx.y;  // sg 0: plus, 1: minus
-  const int id = m * 2 + sg;
   const int E = bf16 ? 8 : 4, eb = bf16 ? 2 : 4;
   const int sbo = (kpad / E) * 128;
   const int nh = nlat / 2;
-  unsigned char* out = B + boff[id];
+  unsigned char* out = B + boff[m];
   for (int idx = threadIdx.x; idx < ncols * kpad; idx += blockDim.x) {
     const int col = idx / kpad, j = idx - col * kpad;
     float v = 0.f;
@@ -367,7 +370,7 @@ __global__ void k_tc_banal(const double2* __restrict__ F0, const double2* __rest
       const double re = a.x + s * b.x, im = a.y + s * b.y;
       v = (float)(wts[j] * ((q & 1) ? im : re));
     }
-    store_elem(out, canon_off(col, j, E, eb, sbo), v, bf16);
+    store_elem(out, canon_off(sg * ncols + col, j, E, eb, sbo), v, bf16);
   }
 }
 
@@ -426,10 +429,13 @@ __global__ void k_tc_eanal(const float* __restrict__ D, const int* __restrict__ 
   const int K = T + 1 - m;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= K) return;
-  const int par = k & 1, kk = k >> 1, tile = kk / 128, r = kk % 128;
+  // D rows: degree k of tile k / 128; columns: the N + S block, then the N - S block (ncols
+  // each).  P pairs with N + S for even k - m and N - S for odd; H the other way round.
+  const int par = k & 1, tile = k / 128, r = k % 128;
   auto val = [&](int tab, int col) -> float {
-    const int o = dmap[((m * 2 + par) * ntile + tile) * 2 + tab];
-    return o < 0 ? 0.f : D[o + (size_t)r * ncols + col];
+    const int o = dmap[(m * ntile + tile) * 2 + tab];
+    const int coloff = ((tab == 0) != (par == 1)) ? 0 : ncols;
+    return o < 0 ? 0.f : D[o + (size_t)r * (2 * ncols) + coloff + col];
   };
   const size_t i = moff(T, m) + k;
   for (int f = 0; f < nf; ++f) {
@@ -460,7 +466,7 @@ struct TcLegendre {
   // synthesis jobs (scalar uses the P half), analysis jobs; job lists and D maps per variant
   Job *jobs_s = nullptr, *jobs_a = nullptr;
   int njobs_s = 0, njobs_a = 0, njobs_sP = 0, njobs_aP = 0;
-  int *dmap_s = nullptr, *dmap_a = nullptr;   // [(m*2+par)*ntile+tile][tab] -> D offset or -1
+  int *dmap_s = nullptr, *dmap_a = nullptr;   // synthesis [(m*2+par)*ntile+tile][tab], analysis [m*ntile+tile][tab] -> D offset or -1
   int *boff_s = nullptr, *kpad_s = nullptr, *boff_a = nullptr;
   int kpad_smax = 0;  // largest K extent of a synthesis B operand
   int nsm = 0;
@@ -529,42 +535,37 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
   js = jsP;
   js.insert(js.end(), jsH.begin(), jsH.end());
   t->njobs_s = (int)js.size();
-  // ---- analysis jobs: (m, par, degree tile, tab), K = northern latitudes ------------------
+  // ---- analysis jobs: (m, degree tile, tab), rows = degrees of both parities, K = northern
+  // latitudes; B = [N + S | N - S] of zonal order m (2 ncols columns) ----------------------
   t->kpad_a = (t->nh + kstep - 1) / kstep * kstep;
   const int nchunk_a = (t->kpad_a + KC - 1) / KC;
   const int kl_a = t->kpad_a - (nchunk_a - 1) * KC;
-  int ntile_a = 0;
-  for (int m = 0; m <= T; ++m) ntile_a = std::max(ntile_a, ((T + 1 - m + 1) / 2 + 127) / 128);
+  const int ntile_a = (T + 1 + 127) / 128;
   t->ntile_a = ntile_a;
   std::vector<TabJob> ta;
   std::vector<Job> jaP, jaH;
-  std::vector<int> dmap_a(2 * (T + 1) * 2 * ntile_a, -1), boff_a(2 * (T + 1));
+  std::vector<int> dmap_a((T + 1) * ntile_a * 2, -1), boff_a(T + 1);
   aoff = 0;
   boff = 0;
   doff = 0;
-  for (int m = 0; m <= T; ++m)
-    for (int sg = 0; sg < 2; ++sg) {
-      boff_a[m * 2 + sg] = boff;
-      boff += ncols_max * t->kpad_a * eb;
-    }
-  for (int m = 0; m <= T; ++m)
-    for (int par = 0; par < 2; ++par) {
-      const int K = T + 1 - m;
-      const int kpar = (K - par + 1) / 2;
-      const int ntiles = (kpar + 127) / 128;
-      for (int tile = 0; tile < ntiles; ++tile) {
-        ta.push_back(TabJob{aoff, m, par, tile, nchunk_a, kl_a});
-        for (int tab = 0; tab < 2; ++tab) {
-          // P pairs with (N + s S), H with (N - s S), s = (-1)^par: plus for (P, even), (H, odd)
-          const int sg = (tab == 0) ? par : 1 - par;
-          Job j{aoff, boff_a[m * 2 + sg], doff, nchunk_a, t->kpad_a, tab, kl_a};
-          (tab ? jaH : jaP).push_back(j);
-          dmap_a[((m * 2 + par) * ntile_a + tile) * 2 + tab] = doff;
-          doff += 128 * ncols_max;
-        }
-        aoff += (long long)(nchunk_a - 1) * chunk + 128LL * kl_a * eb;
+  for (int m = 0; m <= T; ++m) {
+    boff_a[m] = boff;
+    boff += 2 * ncols_max * t->kpad_a * eb;
+  }
+  for (int m = 0; m <= T; ++m) {
+    const int K = T + 1 - m;
+    const int ntiles = (K + 127) / 128;
+    for (int tile = 0; tile < ntiles; ++tile) {
+      ta.push_back(TabJob{aoff, m, 0, tile, nchunk_a, kl_a});
+      for (int tab = 0; tab < 2; ++tab) {
+        Job j{aoff, boff_a[m], doff, nchunk_a, t->kpad_a, tab, kl_a};
+        (tab ? jaH : jaP).push_back(j);
+        dmap_a[(m * ntile_a + tile) * 2 + tab] = doff;
+        doff += 128 * 2 * ncols_max;
       }
+      aoff += (long long)(nchunk_a - 1) * chunk + 128LL * kl_a * eb;
     }
+  }
   const long long tab_a_bytes = aoff;
   const int bsz_a = boff;
   const int dsz = std::max(dsz_s, doff);
@@ -572,6 +573,19 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
   std::vector<Job> ja = jaP;
   ja.insert(ja.end(), jaH.begin(), jaH.end());
   t->njobs_a = (int)ja.size();
+  // the largest B operand of any call (analysis of a vector pair: 2 x 4 max_fields columns
+  // over all latitudes) must fit one B buffer and two ring stages in shared memory
+  {
+    auto ncols_of = [](int nf, int cpf) { return std::max(16, (nf * cpf + 15) / 16 * 16); };
+    const size_t bmax = std::max((size_t)ncols_of(max_fields, 4) * t->kpad_a * 2 * eb,
+                                 (size_t)ncols_of(max_fields, 4) * 512 * eb);
+    if (bmax + 2 * chunk + 4096 > TC_SMEM_BUDGET) {
+      tc_legendre_destroy(t);
+      return fail(REXI_EINVAL,
+                  "sh_plan_create: %d latitudes x %d fields exceed the tensor-core shared-memory budget; "
+                  "use fewer fields per call", nlat, max_fields);
+    }
+  }
   // ---- device buffers ---------------------------------------------------------------------
   TabJob *d_tj = nullptr, *d_ta = nullptr;
   cudaError_t e;
@@ -656,7 +670,8 @@ static int gemm(TcLegendre* t, bool synth, bool both_tabs, int ncols, cudaStream
   g.nj_max = (g.njobs + grid - 1) / grid;
   const size_t jobs_bytes = sizeof(Job) * (size_t)g.nj_max;
   auto fixed = [&](int nb) { return nb * bslot + 8 * (2 * TC_MAXSTAGES + 2 * nb + 2 * TC_NJB + 2) + jobs_bytes; };
-  g.nb = (fixed(TC_MAXNB) + 4 * chunk <= TC_SMEM_BUDGET) ? TC_MAXNB : 2;  // keep >= 4 ring stages
+  // B buffers: 4 when that leaves >= 4 ring stages, else 2, else 1 (>= 2 ring stages always)
+  g.nb = (fixed(TC_MAXNB) + 4 * chunk <= TC_SMEM_BUDGET) ? TC_MAXNB : (fixed(2) + 2 * chunk <= TC_SMEM_BUDGET) ? 2 : 1;
   if (fixed(g.nb) + 2 * chunk > TC_SMEM_BUDGET) return fail(REXI_EINVAL, "tensor-core Legendre: B operand too large");
   g.stages = (int)std::min<size_t>(TC_MAXSTAGES, (TC_SMEM_BUDGET - fixed(g.nb)) / chunk);
   g.bslot = (uint32_t)bslot;
@@ -724,7 +739,7 @@ int tc_leg_anal(TcLegendre* t, const double2* F, double2* spec, int nf, cudaStre
                                                  t->bf16);
     if (t->prof) t->prof->end(ph);
   }
-  int rc = gemm(t, false, false, nc, s);
+  int rc = gemm(t, false, false, 2 * nc, s);  // columns: N + S block, N - S block
   if (rc) return rc;
   {
     const int ph = t->prof ? t->prof->begin(3) : -1;
@@ -744,7 +759,7 @@ int tc_leg_anal_divcurl(TcLegendre* t, const double2* FA, const double2* FB, dou
                                                  t->bf16);
     if (t->prof) t->prof->end(ph);
   }
-  int rc = gemm(t, false, true, nc, s);
+  int rc = gemm(t, false, true, 2 * nc, s);  // columns: N + S block, N - S block
   if (rc) return rc;
   {
     const int ph = t->prof ? t->prof->begin(3) : -1;
