@@ -353,24 +353,32 @@ __global__ void k_tc_banal(const double2* __restrict__ F0, const double2* __rest
                            const double* __restrict__ wts, unsigned char* __restrict__ B,
                            const int* __restrict__ boff, int kpad, int T, int nlat, int nf, int cpf,
                            int ncols, int bf16) {
-  // B of zonal order m: 2 ncols rows (N + S combinations, then N - S), K = latitudes
-  const int m = blockIdx.x, sg = blockIdx.y;  // sg 0: plus, 1: minus
+  // B of zonal order m: 2 ncols rows (N + S combinations, then N - S), K = latitudes; one
+  // thread per northern latitude j reads each Fourier coefficient pair (j and its mirror)
+  // once and writes both combinations of every column
+  const int m = blockIdx.x;
   const int E = bf16 ? 8 : 4, eb = bf16 ? 2 : 4;
   const int sbo = (kpad / E) * 128;
   const int nh = nlat / 2;
   unsigned char* out = B + boff[m];
-  for (int idx = threadIdx.x; idx < ncols * kpad; idx += blockDim.x) {
-    const int col = idx / kpad, j = idx - col * kpad;
-    float v = 0.f;
-    const int f = col / cpf, q = col - f * cpf;
-    if (f < nf && j < nh) {
-      const double2* Fq = (q < 2 ? F0 : F1) + ((size_t)f * (T + 1) + m) * nlat;
-      const double2 a = Fq[j], b = Fq[nlat - 1 - j];
-      const double s = sg ? -1.0 : 1.0;
-      const double re = a.x + s * b.x, im = a.y + s * b.y;
-      v = (float)(wts[j] * ((q & 1) ? im : re));
+  for (int j = threadIdx.x; j < kpad; j += blockDim.x) {
+    const double wj = j < nh ? wts[j] : 0.0;
+    for (int col = 0; col < ncols; col += 2) {  // columns come in (re, im) pairs
+      float pr = 0.f, pi = 0.f, mr = 0.f, mi = 0.f;
+      const int f = col / cpf, q = col - f * cpf;
+      if (f < nf && j < nh) {
+        const double2* Fq = (q < 2 ? F0 : F1) + ((size_t)f * (T + 1) + m) * nlat;
+        const double2 a = Fq[j], b = Fq[nlat - 1 - j];
+        pr = (float)(wj * (a.x + b.x));
+        pi = (float)(wj * (a.y + b.y));
+        mr = (float)(wj * (a.x - b.x));
+        mi = (float)(wj * (a.y - b.y));
+      }
+      store_elem(out, canon_off(col, j, E, eb, sbo), pr, bf16);
+      store_elem(out, canon_off(col + 1, j, E, eb, sbo), pi, bf16);
+      store_elem(out, canon_off(ncols + col, j, E, eb, sbo), mr, bf16);
+      store_elem(out, canon_off(ncols + col + 1, j, E, eb, sbo), mi, bf16);
     }
-    store_elem(out, canon_off(sg * ncols + col, j, E, eb, sbo), v, bf16);
   }
 }
 
@@ -735,7 +743,7 @@ int tc_leg_anal(TcLegendre* t, const double2* F, double2* spec, int nf, cudaStre
   const int nc = ncols_for(nf, 2);
   {
     const int ph = t->prof ? t->prof->begin(1) : -1;
-    k_tc_banal<<<dim3(t->T + 1, 2), 256, 0, s>>>(F, F, t->w, t->B, t->boff_a, t->kpad_a, t->T, t->nlat, nf, 2, nc,
+    k_tc_banal<<<t->T + 1, 128, 0, s>>>(F, F, t->w, t->B, t->boff_a, t->kpad_a, t->T, t->nlat, nf, 2, nc,
                                                  t->bf16);
     if (t->prof) t->prof->end(ph);
   }
@@ -755,7 +763,7 @@ int tc_leg_anal_divcurl(TcLegendre* t, const double2* FA, const double2* FB, dou
   const int nc = ncols_for(nf, 4);
   {
     const int ph = t->prof ? t->prof->begin(1) : -1;
-    k_tc_banal<<<dim3(t->T + 1, 2), 256, 0, s>>>(FA, FB, t->wq, t->B, t->boff_a, t->kpad_a, t->T, t->nlat, nf, 4, nc,
+    k_tc_banal<<<t->T + 1, 128, 0, s>>>(FA, FB, t->wq, t->B, t->boff_a, t->kpad_a, t->T, t->nlat, nf, 4, nc,
                                                  t->bf16);
     if (t->prof) t->prof->end(ph);
   }
