@@ -22,6 +22,8 @@ linop   : spectral form of the linear operator L = L_g + L_c per zonal order (Se
           and the L_g / L_c split), its grid-space form, the linear energy.
 rexi    : the REXI step  U(dt) ~ sum_n beta_n (dt L + alpha_n)^-1 U(0)  (Eq. rexi), solved per
           pole and zonal order with a pivoted banded LU, plus the exact exponential.
+rexi_lg : REXI of the gravity operator L_g alone (the lg_* methods of Table 2): a per-degree
+          2 x 2 solve per pole, and its closed-form exponential.
 swe     : nonlinear term N(U) on the Gauss grid (Sec. 3, the N column of the split), RK2, RK4,
           and the Strang ver1 step  N^{dt/2} o L^{dt} o N^{dt/2}  (Sec. 4.4).
 """

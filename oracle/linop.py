@@ -26,9 +26,14 @@ import numpy as np
 from . import sht
 
 
-def operator_m(T, m, Omega, radius, Phibar):
+def operator_m(T, m, Omega, radius, Phibar, part="L"):
     """Dense 3K x 3K matrix of L restricted to zonal order m, K = T + 1 - m, with the
-    unknowns interleaved as (Phi_n, zeta_n, delta_n) for n = m..T (bandwidth 4 / 4)."""
+    unknowns interleaved as (Phi_n, zeta_n, delta_n) for n = m..T (bandwidth 4 / 4).
+    part = "Lg" keeps only the gravity terms (-Phibar delta_n, n(n+1)/a^2 Phi_n), "Lc" only
+    the Coriolis terms (i w_n, the eps couplings); "L" is their sum."""
+    if part not in ("L", "Lg", "Lc"):
+        raise ValueError(part)
+    grav, cor = part in ("L", "Lg"), part in ("L", "Lc")
     K = T + 1 - m
     A = np.zeros((3 * K, 3 * K), dtype=np.complex128)
     a2 = radius * radius
@@ -37,11 +42,14 @@ def operator_m(T, m, Omega, radius, Phibar):
         iP, iZ, iD = 3 * k, 3 * k + 1, 3 * k + 2
         if n == 0:
             continue
+        if grav:
+            A[iP, iD] = -Phibar
+            A[iD, iP] = n * (n + 1.0) / a2
+        if not cor:
+            continue
         wn = 2.0 * Omega * m / (n * (n + 1.0))
-        A[iP, iD] = -Phibar
         A[iZ, iZ] = 1j * wn
         A[iD, iD] = 1j * wn
-        A[iD, iP] = n * (n + 1.0) / a2
         if k > 0 and n - 1 > 0:
             cm = 2.0 * Omega * (n + 1.0) / n * float(sht.eps(n, m))
             A[iZ, 3 * (k - 1) + 2] = -cm
@@ -72,11 +80,12 @@ def merge_m(out, v, T, m):
     out[2, o: o + K] = v[2::3]
 
 
-def apply_L(U, T, Omega, radius, Phibar):
-    """L U for U[3, nlm] (fields Phi', zeta, delta), spectral route."""
+def apply_L(U, T, Omega, radius, Phibar, part="L"):
+    """L U (or L_g U, L_c U with part = "Lg", "Lc") for U[3, nlm] (fields Phi', zeta, delta),
+    spectral route."""
     out = np.zeros_like(U, dtype=np.complex128)
     for m in range(T + 1):
-        merge_m(out, operator_m(T, m, Omega, radius, Phibar) @ split_m(U, T, m), T, m)
+        merge_m(out, operator_m(T, m, Omega, radius, Phibar, part) @ split_m(U, T, m), T, m)
     return out
 
 

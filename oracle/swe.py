@@ -22,10 +22,15 @@ Time integrators (Sec. 4.1, 4.4; Table 2):
            N^{dt/2} o CN^{dt} o N^{dt/2}  (method id l_irk_n_erk_ver1, Coriolis in L).
   * rk4  : classical 4th-order Runge-Kutta of the full system, used as the small-step
            reference (the paper's reference solution uses RK4 with a tiny step, Sec. 5).
+  * lg   : the lg_rexi_lc_n_* identifiers of Table 2: only the gravity operator L_g goes to
+           REXI (a diagonal solve, oracle.rexi_lg), the Coriolis term L_c joins N in the
+           explicit part:  N'(U) = L_c U + N(U).  lg ver1 is N'^{dt/2} o L_g^{dt} o N'^{dt/2}
+           (lg_rexi_lc_n_erk_ver1, the paper's best REXI method, Sec. 5.2); lg etdrk is
+           ETD2RK with (L_g, N') in place of (L, N) (lg_rexi_lc_n_etdrk).
 """
 import numpy as np
 
-from . import linop, rexi, sht
+from . import linop, rexi, rexi_lg, sht
 
 
 def nonlinear(U, grid):
@@ -51,11 +56,41 @@ def nonlinear(U, grid):
     return out
 
 
+def rk2(U, f, tau):
+    """Integrate dU/dt = f(U) over tau with the midpoint rule (erk, 2nd order)."""
+    k1 = f(U)
+    k2 = f(U + 0.5 * tau * k1)
+    return U + tau * k2
+
+
 def rk2_nonlinear(U, grid, tau):
     """Integrate dU/dt = N(U) over tau with the midpoint rule (erk, 2nd order)."""
-    k1 = nonlinear(U, grid)
-    k2 = nonlinear(U + 0.5 * tau * k1, grid)
-    return U + tau * k2
+    return rk2(U, lambda V: nonlinear(V, grid), tau)
+
+
+def nonlinear_lc(U, grid, Omega):
+    """N'(U) = L_c U + N(U): the explicit part of the lg schemes (Coriolis with N)."""
+    return linop.apply_L(U, grid.T, Omega, grid.a, 0.0, part="Lc") + nonlinear(U, grid)
+
+
+def strang_lg_ver1(U, grid, dt, Omega, Phibar, z, w):
+    """One step of lg_rexi_lc_n_erk_ver1:  N'^{dt/2} o L_g^{dt} o N'^{dt/2}  (Sec. 4.4 version 1
+    with the Coriolis term in the explicit part)."""
+    T, a = grid.T, grid.a
+    f = lambda V: nonlinear_lc(V, grid, Omega)
+    U1 = rk2(U, f, 0.5 * dt)
+    U2 = rexi_lg.rexi_step_lg(U1, T, dt, a, Phibar, z, w)
+    return rk2(U2, f, 0.5 * dt)
+
+
+def etd2rk_lg(U, grid, dt, Omega, Phibar, z, w0, w1, w2):
+    """One ETD2RK step (Sec. 4.3) of lg_rexi_lc_n_etdrk: psi_k(dt L_g) by the diagonal REXI
+    with the psi_k weights of the poles z, nonlinear part N' = L_c + N."""
+    T, a = grid.T, grid.a
+    R = lambda V, w: rexi_lg.rexi_step_lg(V, T, dt, a, Phibar, z, w)
+    NU = nonlinear_lc(U, grid, Omega)
+    A = R(U, w0) + dt * R(NU, w1)
+    return A + dt * R(nonlinear_lc(A, grid, Omega) - NU, w2)
 
 
 def strang_ver1(U, grid, dt, Omega, Phibar, z, w):
