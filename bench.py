@@ -366,6 +366,45 @@ def sh_transforms(torch, rexi, fp64_peak, T=511, nlat=768, nlon=1536, nf=2, reps
     return out
 
 
+def lg_rexi(torch, rexi, fp64_peak, T=511, N=2048, dt=7200.0, batch=32, reps=20):
+    """The gravity-only REXI step (the lg_rexi_* methods: L_g alone, a per-degree 2 x 2 pole sum
+    applied in one pass) on a batch of T511 states, 2048 poles, dt = 7200 s: device time per
+    launch over `reps` launches with CUDA events (input and output 2 x 201 MB, larger than
+    L2), against the HBM roof (algorithmic bytes: 3 fields read and written, 96 B per
+    coefficient) and the FP64 pipe (14 flops per coefficient triple with real sums)."""
+    import numpy as np
+    from paper_1805_06557_gb300 import synthetic as syn
+    X = dt * np.sqrt(syn.PHIBAR * T * (T + 1.0)) / syn.RADIUS
+    p0, Xc = contour(X)
+    nlm = (T + 1) * (T + 2) // 2
+    base = np.stack([syn.gaussian_state(T, 500 + i) for i in range(4)])
+    u0 = torch.from_numpy(np.ascontiguousarray(np.tile(base, (batch // 4, 1, 1)))).cuda()
+    u1 = torch.empty_like(u0)
+    p = rexi.LgPlan(T, N, dt, syn.RADIUS, syn.PHIBAR, p0=p0, Xc=Xc, max_batch=batch)
+    for _ in range(3):
+        p.step(u0, u1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        p.step(u0, u1)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    _, real = p.operator()
+    p.close()
+    hbm = _hbm_peak()
+    nbytes = 2 * 3 * 16 * nlm * batch
+    flops = (14 if real else 28) * nlm * batch
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    return {"workload": "gravity-only REXI step, T%d, %d poles, dt=%g s, batch %d states" % (T, N, dt, batch),
+            "ms_per_launch": ms, "states_per_s": batch / (ms * 1e-3), "real_sums": real,
+            "roofline": {"bound": "hbm", "kernel": "k_lg_apply", "algorithmic_bytes": nbytes,
+                         "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                         "fp64_tflops": flops / (ms * 1e-3) / 1e12,
+                         "fp64_frac": flops / (ms * 1e-3) / 1e12 / fp64_peak if fp64_peak else None}}
+
+
 def swe_steps(torch, rexi, configs):
     """Nonlinear SWE steps (Strang ver1: N by RK2 midpoint for dt/2, REXI L for dt, N for
     dt/2; variants may name the ETD2RK scheme instead) on balanced n^-3 states: steps/s and per-stage device times over the timed steps,
@@ -425,7 +464,8 @@ DT_SWEEP = [15.0, 30.0, 60.0, 120.0, 180.0, 360.0, 480.0, 600.0]   # the paper's
 
 def dt_sweep(args):
     """Error vs time-step size of the nonlinear schemes (Strang ver1 / ver0 with REXI, ETD2RK,
-    Crank-Nicolson Strang) on the balanced n^-3 T127 state (192 x 384 Gauss grid, 512 poles),
+    Crank-Nicolson Strang, and the lg ver1 / lg ETD2RK schemes with Coriolis in the explicit
+    part) on the balanced n^-3 T127 state (192 x 384 Gauss grid, 512 poles),
     over 12 h, against Strang ver1 with dt = 5 s: L-infinity of the surface-height error on the
     grid (Phi' / g, the paper's metric) and the per-field relative L2."""
     import numpy as np
@@ -455,7 +495,7 @@ def dt_sweep(args):
     out = {"workload": "nonlinear SWE, T127 on 192 x 384, 512 poles, balanced n^-3 state (20 m/s rms), "
                        "12 h; reference: Strang ver1 (FP64) with dt = 5 s", "schemes": {}}
     r = ref.cpu().numpy()
-    for scheme in ("ver1", "ver0", "etdrk", "irk"):
+    for scheme in ("ver1", "ver0", "etdrk", "irk", "lg_ver1", "lg_etdrk"):
         res = {}
         for dt in DT_SWEEP:
             u, sec = run(scheme, dt)
@@ -630,15 +670,18 @@ def main():
            "d2h_bytes_per_step": bytes_step, "api": "rexi_step_host (pinned host buffers)"}
 
     ens = None if args.no_ensemble else ensemble(torch, rexi, syn, max(3, min(args.steps, 10)))
-    sh = swe = None
+    sh = swe = lg = None
     if not args.no_sh:
         sh = sh_transforms(torch, rexi, fp64_tf)
         swe = swe_steps(torch, rexi, [
             (127, 192, 384, 512, 1800.0, 48, [("fp64", "fp64"), ("mixed", "fp64"), ("mixed", "tf32"),
                                               ("fp64", "fp64", "etdrk"), ("mixed", "fp64", "etdrk"),
-                                              ("fp64", "fp64", "irk")]),
+                                              ("fp64", "fp64", "irk"), ("fp64", "fp64", "lg_ver1"),
+                                              ("fp64", "fp64", "lg_etdrk"), ("fp64", "tf32", "lg_ver1")]),
             (511, 768, 1536, 2048, 7200.0, 4, [("fp64", "fp64"), ("mixed", "fp64"), ("mixed", "tf32"),
-                                                ("mixed", "bf16")])])
+                                                ("mixed", "bf16"), ("fp64", "fp64", "lg_ver1"),
+                                                ("fp64", "tf32", "lg_ver1")])])
+        lg = lg_rexi(torch, rexi, fp64_tf)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -662,7 +705,7 @@ def main():
         "speedup_vs_fp64_plain": value / world / (1e3 / statistics.mean(fp64_b1)),
         "plan": {k: info[k] for k in ("n_heavy", "n_groups", "q_slots", "grid_light", "grid_heavy")},
         "alu_peaks_tflops": {"fp64": fp64_tf, "fp32": fp32_tf},
-        "ensemble": ens, "sh_transforms": sh, "swe_step": swe,
+        "ensemble": ens, "sh_transforms": sh, "swe_step": swe, "lg_rexi": lg,
         "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
         "gpu_launches": 4 * args.steps,
     }

@@ -150,6 +150,60 @@ int rexi_plan_get_info(const rexi_plan* plan, rexi_plan_info* info);
 int rexi_plan_get_poles(const rexi_plan* plan, double* z, double* w, int* heavy);
 
 /*
+ * Gravity-only REXI plans (the lg_rexi_* method identifiers of Table 2: only L_g goes to REXI,
+ * the Coriolis term L_c is left to the explicit part; Sec. 3 split, Sec. 5.3).  Without
+ * Coriolis the operator couples neither degrees nor zonal orders; for degree n >= 1, with
+ * q_n = n(n+1)/a^2,
+ *     dPhi_n/dt = -Phibar delta_n,   dzeta_n/dt = 0,   ddelta_n/dt = q_n Phi_n,
+ * so each REXI term (z_p - dt L_g)^-1 is a 2 x 2 solve on (Phi_n, delta_n) (determinant
+ * z_p^2 + dt^2 Phibar q_n) and a division of zeta_n by z_p, and the pole sum
+ *     M_n = sum_p w_p (z_p - dt L_g,n)^-1
+ * is a 2 x 2 matrix on (Phi_n, delta_n) and the scalar sum_p w_p / z_p on zeta_n, the same for
+ * every zonal order.  Degree 0 (a zero row of the operator) gets sum_p w_p / z_p on all three
+ * fields.  Plan creation evaluates M_n on the device in FP64 (one thread per degree, poles in
+ * order); rexi_lg_step applies it: one pass over the state.  When the pole set is closed under
+ * conjugation (pole p and pole N-1-p conjugate, weights too, to 1e-13 relative, as rexi_coeffs
+ * makes them), M_n is real up to rounding and only its real part is applied.
+ */
+typedef struct rexi_lg_plan rexi_lg_plan;
+
+typedef struct rexi_lg_desc {
+  int T;              /* triangular truncation, 1 <= T <= 1023                           */
+  int N;              /* number of poles, 1 <= N <= 8192                                 */
+  double dt;          /* time step [s]                                                   */
+  double radius;      /* sphere radius a [m]                                             */
+  double phibar;      /* mean geopotential Phibar [m^2/s^2]                              */
+  double p0, Xc;      /* contour (used when z == NULL)                                   */
+  const double* z;    /* optional host array, 2N doubles: poles z_p                      */
+  const double* w;    /* optional host array, 2N doubles: weights w_p                    */
+  int phi;            /* z == NULL: 0, 1, 2 for the psi_0, psi_1, psi_2 weights (rexi_coeffs) */
+  int max_batch;      /* largest batch passed to rexi_lg_step, >= 1                      */
+  void* stream;       /* cudaStream_t the plan launches on (NULL: legacy default stream) */
+} rexi_lg_desc;
+
+/* Allocates the per-degree table ((T+1) x 64 bytes) and computes it.
+ * Errors: REXI_EINVAL, REXI_ENOMEM, REXI_ECUDA. */
+int rexi_lg_create(const rexi_lg_desc* desc, rexi_lg_plan** out);
+/* Frees the plan (NULL allowed).  Synchronises the plan stream. */
+int rexi_lg_destroy(rexi_lg_plan* plan);
+/*
+ * U1 = sum_p w_p (z_p - dt L_g)^-1 U0 for `batch` states, [batch][3][nlm] complex128 device
+ * arrays (caller-owned).  U0 == U1 (in place) is allowed; any other overlap is REXI_EINVAL.
+ * 1 <= batch <= max_batch.  Asynchronous on the plan stream, no allocation, one kernel launch.
+ * Errors: REXI_EINVAL, REXI_ECUDA.
+ */
+int rexi_lg_step(rexi_lg_plan* plan, const void* U0, void* U1, int batch);
+/* Synchronises the plan stream; reports errors of device work since the last call. */
+int rexi_lg_sync(rexi_lg_plan* plan);
+/*
+ * Copies the per-degree pole sums to a host array of (T+1) x 8 doubles:
+ * per degree (M_PhiPhi, M_PhiDelta, M_DeltaPhi, M_ZetaZeta) as (re, im) pairs
+ * (M_DeltaDelta = M_PhiPhi).  *real_only (may be NULL) is 1 if the step applies real parts.
+ * Synchronous.  Errors: REXI_EINVAL, REXI_ECUDA.
+ */
+int rexi_lg_get_operator(const rexi_lg_plan* plan, double* M, int* real_only);
+
+/*
  * Ragged plans -- one launch over instances of different truncation T, time step dt and pole
  * count N (uneven per-m chain lengths from many states; the ensemble and serving forms).
  * Each instance gets its own Cauchy pole set; the tiles of all instances are sorted by cost

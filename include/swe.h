@@ -29,6 +29,16 @@ extern "C" {
  * CN^{dt} = (I - dt L / 2)^-1 (I + dt L / 2) = 2 (2 - dt L)^-1 (I + dt L / 2), i.e. the banded
  * solve of one pole z = 2 with weight 2 (FP64); p0 and Xc are not used. */
 #define SWE_L_IRK_N_ERK_VER1 3
+/* Coriolis in the explicit part (Table 2 lg_rexi_lc_n_*; Sec. 5.2 names lg_rexi_lc_n_erk_ver1 the
+ * best REXI method by wallclock time to error): only the gravity operator L_g goes to REXI, by
+ * the diagonal gravity-only plan of rexi.h (rexi_lg_*, FP64; rexi_precision is not used), and
+ * the explicit part is N'(U) = L_c U + N(U), L_c evaluated spectrally:
+ *   zeta_n: i w_n zeta_n - 2 Omega [(n+1)/n eps_n delta_{n-1} + n/(n+1) eps_{n+1} delta_{n+1}]
+ *   delta_n: i w_n delta_n + 2 Omega [(n+1)/n eps_n zeta_{n-1} + n/(n+1) eps_{n+1} zeta_{n+1}]
+ * LG_..._VER1: U+ = N'^{dt/2} o L_g^{dt} o N'^{dt/2} (U).
+ * LG_..._ETDRK: ETD2RK with (L_g, N') in place of (L, N), psi_k(dt L_g) by the diagonal REXI. */
+#define SWE_LG_REXI_LC_N_ERK_VER1 4
+#define SWE_LG_REXI_LC_N_ETDRK 5
 
 typedef struct swe_plan swe_plan;
 
@@ -40,11 +50,12 @@ typedef struct swe_plan_desc {
   double p0, Xc;            /* REXI contour for the linear sub-step (dt for ver1 and etdrk, dt/2 ver0) */
   int rexi_precision;       /* REXI_FP64 or REXI_MIXED                                      */
   int sh_precision;         /* SH_FP64, SH_TF32 or SH_BF16                                  */
-  int scheme;               /* SWE_L_REXI_N_ERK_VER1 / _VER0, SWE_L_REXI_N_ETDRK, SWE_L_IRK_N_ERK_VER1 */
+  int scheme;               /* one of the SWE_* scheme identifiers above                    */
   void* stream;             /* cudaStream_t                                                  */
 } swe_plan_desc;
 
-/* Creates the REXI plan(s: three for etdrk), the SH plan and all work buffers.
+/* Creates the REXI plan(s: three for etdrk, gravity-only plans for lg), the SH plan and all
+ * work buffers.
  * Errors: REXI_EINVAL, REXI_ENOMEM, REXI_ECUDA. */
 int swe_plan_create(const swe_plan_desc* desc, swe_plan** out);
 int swe_plan_destroy(swe_plan* plan);

@@ -62,16 +62,32 @@ def phi_function(k, z):
 def rexi_coefficients(N, p0, X, k=0):
     """Poles z_n and weights w_n of  psi_k(x) ~ sum_n w_n / (z_n - x)  (Eq. cauchy_alpha/beta).
 
-    Returns complex128 arrays z (= -alpha_n) and w (= -beta_n) of length N."""
+    Returns complex128 arrays z (= -alpha_n) and w (= -beta_n) of length N.
+
+    The circle is symmetric about the real axis and theta_{N+1-n} = 2 pi - theta_n, so node
+    N+1-n is the conjugate of node n (psi_k has real Taylor coefficients: psi_k(conj z) =
+    conj psi_k(z)).  The nodes n <= N/2 are evaluated and the others set to their exact
+    conjugates; for odd N the middle node (theta = pi) is real.  Evaluating every node on its
+    own would break the pairing by rounding (the weights carry a relative error of about
+    |z| eps through e^z), and the contour's cancellation (|w_n| up to 1e5 summing to O(1))
+    would turn that into a spurious imaginary part of the sums."""
     if N < 1:
         raise ValueError("N must be positive")
     R, mu = contour(p0, X)
-    n = np.arange(1, N + 1, dtype=np.float64)
+    h = N // 2
+    n = np.arange(1, h + 1, dtype=np.float64)
     theta = 2.0 * np.pi * (n - 0.5) / N
     ring = R * np.exp(1j * theta)
-    z = ring + mu
-    w = ring * phi_function(k, z) / N
-    return z, w
+    zh = ring + mu
+    wh = ring * phi_function(k, zh) / N
+    parts_z, parts_w = [zh], [wh]
+    if N % 2:
+        zm = np.array([mu - R], dtype=np.complex128)
+        parts_z.append(zm)
+        parts_w.append((-R * phi_function(k, zm) / N).real.astype(np.complex128))
+    parts_z.append(np.conj(zh[::-1]))
+    parts_w.append(np.conj(wh[::-1]))
+    return np.concatenate(parts_z), np.concatenate(parts_w)
 
 
 def rational_eval(z, w, x):

@@ -34,11 +34,15 @@ def degrees(T):
     return n
 
 
-def rexi_step_lg(U0, T, dt, radius, Phibar, z, w):
+def rexi_step_lg(U0, T, dt, radius, Phibar, z, w, idx=None):
     """sum_p w_p (z_p - dt L_g)^-1 U0 for U0[3, nlm] (Phi', zeta, delta): the diagonal solve
-    of every pole written out per coefficient, poles summed in order."""
+    of every pole written out per coefficient, poles summed in order.  idx (optional) restricts
+    the computation to those coefficient indices; the result then has shape [3, len(idx)]."""
     U0 = np.asarray(U0, dtype=np.complex128)
     n = degrees(T).astype(np.float64)
+    if idx is not None:
+        n = n[idx]
+        U0 = U0[:, idx]
     q = n * (n + 1.0) / (radius * radius)
     bP, bZ, bD = U0[0], U0[1], U0[2]
     g = n > 0

@@ -61,11 +61,20 @@ static void contour_coeffs(int N, double p0, double Xc, int k, std::vector<cplx>
   const double mu = p0 - R;
   z.resize(N);
   w.resize(N);
-  for (int n = 1; n <= N; ++n) {
+  // node N+1-n is the conjugate of node n (the circle is symmetric about the real axis and
+  // psi_k(conj z) = conj psi_k(z)): evaluate n <= N/2 and mirror, so that the pairs are exact
+  // and conjugate sums have no imaginary part from rounding; odd N: the middle node is real
+  for (int n = 1; n <= N / 2; ++n) {
     const double th = 2.0 * M_PI * (n - 0.5) / N;
     const cplx ring = R * cplx(std::cos(th), std::sin(th));
     z[n - 1] = ring + mu;
     w[n - 1] = ring * psi(k, z[n - 1]) / double(N);
+    z[N - n] = std::conj(z[n - 1]);
+    w[N - n] = std::conj(w[n - 1]);
+  }
+  if (N % 2) {
+    z[N / 2] = cplx(mu - R, 0.0);
+    w[N / 2] = cplx((-R * psi(k, z[N / 2]) / double(N)).real(), 0.0);
   }
 }
 

@@ -49,9 +49,13 @@ __global__ void k_swe_products(const double* __restrict__ PZ, const double* __re
 }
 
 // out = base + tau * N,  N = (-div(Phi V), -div(zeta V), curl(zeta V) + n(n+1)/a^2 KE_s);
-// the n = 0 vorticity and divergence tendencies are 0 (global means).
+// the n = 0 vorticity and divergence tendencies are 0 (global means).  With a Coriolis table
+// (the lg schemes) the tendency is N' = L_c U + N, L_c U evaluated spectrally from U:
+//   zeta_n: i omega_n zeta_n - (cm_n delta_{n-1} + cp_n delta_{n+1})
+//   delta_n: i omega_n delta_n + (cm_n zeta_{n-1} + cp_n zeta_{n+1})
 __global__ void k_swe_combine(const double2* __restrict__ base, const double2* __restrict__ dv,
                               const double2* __restrict__ cu, const double2* __restrict__ kes,
+                              const double2* __restrict__ U, const D4* __restrict__ ctab,
                               double2* __restrict__ out, double tau, int T, int nlm, double inv_a2) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nlm) return;
@@ -66,6 +70,19 @@ __global__ void k_swe_combine(const double2* __restrict__ base, const double2* _
   double2 nZ = make_double2(-dv[nlm + i].x, -dv[nlm + i].y);
   const double l = double(n) * (n + 1) * inv_a2;
   double2 nD = make_double2(cu[nlm + i].x + l * kes[i].x, cu[nlm + i].y + l * kes[i].y);
+  if (ctab) {
+    const int m = lo;
+    const D4 t = ctab[i];  // (omega, cm, cp, -)
+    const double2* Z = U + nlm;
+    const double2* D = U + 2 * nlm;
+    const double2 zm = n > m ? Z[i - 1] : make_double2(0.0, 0.0), zp = n < T ? Z[i + 1] : make_double2(0.0, 0.0);
+    const double2 dm = n > m ? D[i - 1] : make_double2(0.0, 0.0), dp = n < T ? D[i + 1] : make_double2(0.0, 0.0);
+    const double2 z0 = Z[i], d0 = D[i];
+    nZ.x += -t.x * z0.y - (t.y * dm.x + t.z * dp.x);
+    nZ.y += t.x * z0.x - (t.y * dm.y + t.z * dp.y);
+    nD.x += -t.x * d0.y + (t.y * zm.x + t.z * zp.x);
+    nD.y += t.x * d0.x + (t.y * zm.y + t.z * zp.y);
+  }
   if (i == 0) nZ = nD = make_double2(0.0, 0.0);
   if (tau == 0.0) {  // plain tendency
     out[i] = nP;
@@ -85,7 +102,7 @@ __global__ void k_swe_combine(const double2* __restrict__ base, const double2* _
 //   ddelta_n = q_n Phi_n + i omega_n delta_n + (cm_n zeta_{n-1} + cp_n zeta_{n+1})
 // (cm_n = 2 Omega (n+1)/n eps_n, cp_n = 2 Omega n/(n+1) eps_{n+1}; entries outside m <= n <= T
 // are zero).
-__global__ void k_apply_L(const double2* __restrict__ U, const double4* __restrict__ tab, double s,
+__global__ void k_apply_L(const double2* __restrict__ U, const D4* __restrict__ tab, double s,
                           double phibar, double2* __restrict__ out, int T, int nlm) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nlm) return;
@@ -96,7 +113,7 @@ __global__ void k_apply_L(const double2* __restrict__ U, const double4* __restri
     else hi = mid - 1;
   }
   const int m = lo, n = m + (i - moff(T, m));
-  const double4 t = tab[i];  // (omega, cm, cp, q)
+  const D4 t = tab[i];  // (omega, cm, cp, q)
   const double2* P = U;
   const double2* Z = U + nlm;
   const double2* D = U + 2 * nlm;
@@ -133,7 +150,9 @@ struct swe_plan {
   rexi_plan *rp1 = nullptr, *rp2 = nullptr;  // etdrk: REXI of psi_1, psi_2 (same poles)
   sh_plan* sp = nullptr;
   double2 *NU = nullptr, *A3 = nullptr;      // etdrk: N(U), A
-  double4* Ltab = nullptr;                   // irk: (omega, cm, cp, n(n+1)/a^2) per (m, n)
+  D4* Ltab = nullptr;                        // irk, lg: (omega, cm, cp, n(n+1)/a^2) per (m, n)
+  rexi_lg_plan* lg[3] = {nullptr, nullptr, nullptr};  // lg: REXI of psi_0, psi_1, psi_2 of dt L_g
+  bool is_lg = false;
   double2 *psi = nullptr, *chi = nullptr, *Um = nullptr, *Ut = nullptr, *dv = nullptr, *cu = nullptr,
           *kes = nullptr;
   double *PZ = nullptr, *Ug = nullptr, *Vg = nullptr, *A = nullptr, *B = nullptr, *KE = nullptr,
@@ -147,6 +166,7 @@ extern "C" int swe_plan_destroy(swe_plan* p) {
   rexi_plan_destroy(p->rp);
   rexi_plan_destroy(p->rp1);
   rexi_plan_destroy(p->rp2);
+  for (rexi_lg_plan* q : p->lg) rexi_lg_destroy(q);
   sh_plan_destroy(p->sp);
   p->prof.release();
   for (void* q : {(void*)p->psi, (void*)p->chi, (void*)p->Um, (void*)p->Ut, (void*)p->dv, (void*)p->cu,
@@ -161,11 +181,11 @@ extern "C" int swe_plan_create(const swe_plan_desc* desc, swe_plan** out) {
   if (!desc || !out) return fail(REXI_EINVAL, "swe_plan_create: null argument");
   *out = nullptr;
   const swe_plan_desc& d = *desc;
-  if (d.scheme != SWE_L_REXI_N_ERK_VER1 && d.scheme != SWE_L_REXI_N_ERK_VER0 && d.scheme != SWE_L_REXI_N_ETDRK &&
-      d.scheme != SWE_L_IRK_N_ERK_VER1)
+  if (d.scheme < SWE_L_REXI_N_ERK_VER1 || d.scheme > SWE_LG_REXI_LC_N_ETDRK)
     return fail(REXI_EINVAL, "swe_plan_create: unknown scheme %d", d.scheme);
   swe_plan* p = new swe_plan();
   p->d = d;
+  p->is_lg = d.scheme == SWE_LG_REXI_LC_N_ERK_VER1 || d.scheme == SWE_LG_REXI_LC_N_ETDRK;
   p->stream = (cudaStream_t)d.stream;
   p->prof.stream = p->stream;
   p->nlm = (d.T + 1) * (d.T + 2) / 2;
@@ -204,22 +224,40 @@ extern "C" int swe_plan_create(const swe_plan_desc* desc, swe_plan** out) {
     rd.w = cn_w;
     rd.precision = REXI_FP64;
   }
-  rc = rexi_plan_create(&rd, &p->rp);
-  if (rc) return bail(rc);
-  if (d.scheme == SWE_L_IRK_N_ERK_VER1) {
-    std::vector<double4> t(p->nlm);
+  if (p->is_lg) {  // L_g by the diagonal REXI (FP64), psi_1 and psi_2 too for ETD2RK
+    const int nk = d.scheme == SWE_LG_REXI_LC_N_ETDRK ? 3 : 1;
+    for (int k = 0; k < nk; ++k) {
+      rexi_lg_desc ld{};
+      ld.T = d.T;
+      ld.N = d.N;
+      ld.dt = d.dt;
+      ld.radius = d.radius;
+      ld.phibar = d.phibar;
+      ld.p0 = d.p0;
+      ld.Xc = d.Xc;
+      ld.phi = k;
+      ld.max_batch = 1;
+      ld.stream = d.stream;
+      if ((rc = rexi_lg_create(&ld, &p->lg[k]))) return bail(rc);
+    }
+  } else {
+    rc = rexi_plan_create(&rd, &p->rp);
+    if (rc) return bail(rc);
+  }
+  if (d.scheme == SWE_L_IRK_N_ERK_VER1 || p->is_lg) {
+    std::vector<D4> t(p->nlm);
     for (int m = 0; m <= d.T; ++m)
       for (int n = m; n <= d.T; ++n) {
         auto eps = [&](int nn) { return nn > m ? std::sqrt((double(nn) * nn - double(m) * m) / (4.0 * nn * nn - 1.0)) : 0.0; };
         const double nn1 = double(n) * (n + 1);
         const double om = n > 0 ? 2.0 * d.omega * m / nn1 : 0.0;
-        const double cm = n > m ? 2.0 * d.omega * (n + 1.0) / n * eps(n) : 0.0;
+        const double cm = n > m && n - 1 > 0 ? 2.0 * d.omega * (n + 1.0) / n * eps(n) : 0.0;
         const double cp = n > 0 && n < d.T ? 2.0 * d.omega * n / (n + 1.0) * eps(n + 1) : 0.0;
-        t[moff(d.T, m) + (n - m)] = make_double4(om, cm, cp, nn1 / (d.radius * d.radius));
+        t[moff(d.T, m) + (n - m)] = D4{om, cm, cp, nn1 / (d.radius * d.radius)};
       }
     cudaError_t e2;
-    if ((e2 = cudaMalloc(&p->Ltab, sizeof(double4) * p->nlm)) ||
-        (e2 = cudaMemcpy(p->Ltab, t.data(), sizeof(double4) * p->nlm, cudaMemcpyHostToDevice))) {
+    if ((e2 = cudaMalloc(&p->Ltab, sizeof(D4) * p->nlm)) ||
+        (e2 = cudaMemcpy(p->Ltab, t.data(), sizeof(D4) * p->nlm, cudaMemcpyHostToDevice))) {
       cudaGetLastError();
       return bail(fail(REXI_ENOMEM, "swe_plan_create: operator table: %s", cudaGetErrorString(e2)));
     }
@@ -242,7 +280,8 @@ extern "C" int swe_plan_create(const swe_plan_desc* desc, swe_plan** out) {
       (e = cudaMalloc(&p->kes, s1)) || (e = cudaMalloc(&p->PZ, 2 * g1)) || (e = cudaMalloc(&p->Ug, g1)) ||
       (e = cudaMalloc(&p->Vg, g1)) || (e = cudaMalloc(&p->A, 2 * g1)) || (e = cudaMalloc(&p->B, 2 * g1)) ||
       (e = cudaMalloc(&p->KE, g1)) || (e = cudaMalloc(&p->c2, sizeof(double) * d.nlat)) ||
-      (d.scheme == SWE_L_REXI_N_ETDRK && ((e = cudaMalloc(&p->NU, s3)) || (e = cudaMalloc(&p->A3, s3))))) {
+      ((d.scheme == SWE_L_REXI_N_ETDRK || d.scheme == SWE_LG_REXI_LC_N_ETDRK) &&
+       ((e = cudaMalloc(&p->NU, s3)) || (e = cudaMalloc(&p->A3, s3))))) {
     cudaGetLastError();
     return bail(fail(REXI_ENOMEM, "swe_plan_create: cudaMalloc failed: %s", cudaGetErrorString(e)));
   }
@@ -255,8 +294,9 @@ extern "C" int swe_plan_create(const swe_plan_desc* desc, swe_plan** out) {
   return REXI_OK;
 }
 
-// out = base + tau * N(U)   (tau = 0: out = N(U))
-static int nonlinear_update(swe_plan* p, const double2* U, const double2* base, double tau, double2* out) {
+// out = base + tau * N(U)   (tau = 0: out = N(U)); with ctab, N' = L_c U + N(U) instead
+static int nonlinear_update(swe_plan* p, const double2* U, const double2* base, double tau, double2* out,
+                            const D4* ctab = nullptr) {
   const int T = p->d.T, nlm = p->nlm;
   const int tb = 256;
   {
@@ -277,19 +317,28 @@ static int nonlinear_update(swe_plan* p, const double2* U, const double2* base, 
   if ((rc = sh_analysis(p->sp, p->KE, p->kes, 1))) return rc;
   {
     const int ph = p->prof.begin(0);
-    k_swe_combine<<<(nlm + tb - 1) / tb, tb, 0, p->stream>>>(base, p->dv, p->cu, p->kes, out, tau, T, nlm,
-                                                             1.0 / (p->d.radius * p->d.radius));
+    k_swe_combine<<<(nlm + tb - 1) / tb, tb, 0, p->stream>>>(base, p->dv, p->cu, p->kes, U, ctab, out, tau, T,
+                                                             nlm, 1.0 / (p->d.radius * p->d.radius));
     p->prof.end(ph);
   }
   cudaError_t e = cudaGetLastError();
   return e ? cuda_fail(e, "swe nonlinear kernels") : REXI_OK;
 }
 
-// U <- U + tau N(U + tau/2 N(U))   (explicit midpoint rule)
+// U <- U + tau N(U + tau/2 N(U))   (explicit midpoint rule; N' = L_c + N for the lg schemes)
 static int rk2_nonlinear(swe_plan* p, double2* U, double tau) {
-  int rc = nonlinear_update(p, U, U, 0.5 * tau, p->Um);
+  const D4* ctab = p->is_lg ? p->Ltab : nullptr;
+  int rc = nonlinear_update(p, U, U, 0.5 * tau, p->Um, ctab);
   if (rc) return rc;
-  return nonlinear_update(p, p->Um, U, tau, U);
+  return nonlinear_update(p, p->Um, U, tau, U, ctab);
+}
+
+// the gravity-only REXI step, timed as part of the REXI stage
+static int lg_step(swe_plan* p, int k, const double2* in, double2* out) {
+  const int ph = p->prof.begin(1);
+  int rc = rexi_lg_step(p->lg[k], in, out, 1);
+  p->prof.end(ph);
+  return rc;
 }
 
 extern "C" int swe_nonlinear(swe_plan* p, const void* state, void* tend) {
@@ -322,6 +371,21 @@ extern "C" int swe_step(swe_plan* p, void* state, int nsteps) {
       REXI_CUDA_TRY(cudaGetLastError());
       if ((rc = rexi_step(p->rp, p->Ut, U, 1))) return rc;  // 2 (2 - dt L)^-1 (I + dt L / 2) U
       if ((rc = rk2_nonlinear(p, U, 0.5 * dt))) return rc;
+    } else if (p->d.scheme == SWE_LG_REXI_LC_N_ERK_VER1) {
+      if ((rc = rk2_nonlinear(p, U, 0.5 * dt))) return rc;
+      if ((rc = lg_step(p, 0, U, U))) return rc;  // in place
+      if ((rc = rk2_nonlinear(p, U, 0.5 * dt))) return rc;
+    } else if (p->d.scheme == SWE_LG_REXI_LC_N_ETDRK) {
+      const int n3 = 3 * p->nlm, tb = 256, nb = (n3 + tb - 1) / tb;
+      if ((rc = nonlinear_update(p, U, nullptr, 0.0, p->NU, p->Ltab))) return rc;  // N'(U)
+      if ((rc = lg_step(p, 0, U, p->Ut))) return rc;                              // psi_0 U
+      if ((rc = lg_step(p, 1, p->NU, p->Um))) return rc;                          // psi_1 N'(U)
+      k_axpy<<<nb, tb, 0, p->stream>>>(p->Ut, p->Um, dt, p->A3, n3);               // A
+      if ((rc = nonlinear_update(p, p->A3, nullptr, 0.0, p->Ut, p->Ltab))) return rc;  // N'(A)
+      k_axpy<<<nb, tb, 0, p->stream>>>(p->Ut, p->NU, -1.0, p->Um, n3);             // N'(A) - N'(U)
+      if ((rc = lg_step(p, 2, p->Um, p->Ut))) return rc;                          // psi_2 (...)
+      k_axpy<<<nb, tb, 0, p->stream>>>(p->A3, p->Ut, dt, U, n3);                   // U+
+      REXI_CUDA_TRY(cudaGetLastError());
     } else {  // ETD2RK
       const int n3 = 3 * p->nlm, tb = 256, nb = (n3 + tb - 1) / tb;
       if ((rc = nonlinear_update(p, U, nullptr, 0.0, p->NU))) return rc;          // N(U)
@@ -341,7 +405,7 @@ extern "C" int swe_step(swe_plan* p, void* state, int nsteps) {
 extern "C" int swe_plan_set_profiling(swe_plan* p, int enable) {
   if (!p) return fail(REXI_EINVAL, "swe_plan_set_profiling: null plan");
   p->prof.on = enable != 0;
-  int rc = rexi_plan_set_profiling(p->rp, enable);
+  int rc = p->rp ? rexi_plan_set_profiling(p->rp, enable) : REXI_OK;
   for (rexi_plan* q : {p->rp1, p->rp2})
     if (!rc && q) rc = rexi_plan_set_profiling(q, enable);
   return rc ? rc : sh_plan_set_profiling(p->sp, enable);
@@ -349,9 +413,9 @@ extern "C" int swe_plan_set_profiling(swe_plan* p, int enable) {
 
 extern "C" int swe_plan_get_profile(swe_plan* p, double* ms, int* launches, int reset) {
   if (!p) return fail(REXI_EINVAL, "swe_plan_get_profile: null plan");
-  double rm[REXI_NKERNELS], sm[SH_NSTAGES];
-  int rn[REXI_NKERNELS], sn[SH_NSTAGES];
-  int rc = rexi_plan_get_profile(p->rp, rm, rn, reset);
+  double rm[REXI_NKERNELS] = {}, sm[SH_NSTAGES];
+  int rn[REXI_NKERNELS] = {}, sn[SH_NSTAGES];
+  int rc = p->rp ? rexi_plan_get_profile(p->rp, rm, rn, reset) : REXI_OK;
   if (rc) return rc;
   for (rexi_plan* q : {p->rp1, p->rp2}) {
     if (!q) continue;
@@ -377,12 +441,15 @@ extern "C" int swe_plan_get_profile(swe_plan* p, double* ms, int* launches, int 
   }
   out[2] = sm[4];
   cnt[2] = sn[4];
+  out[0] += p->prof.ms[1];  // gravity-only REXI launches (lg schemes)
+  cnt[0] += p->prof.n[1];
   out[3] = p->prof.ms[0];
   cnt[3] = p->prof.n[0];
-  if (reset) {
-    p->prof.ms[0] = 0.0;
-    p->prof.n[0] = 0;
-  }
+  if (reset)
+    for (int k = 0; k < 2; ++k) {
+      p->prof.ms[k] = 0.0;
+      p->prof.n[k] = 0;
+    }
   for (int k = 0; k < SWE_NSTAGES; ++k) {
     if (ms) ms[k] = out[k];
     if (launches) launches[k] = cnt[k];

@@ -342,6 +342,84 @@ class Plan:
             pass
 
 
+# ---- gravity-only REXI plans (include/rexi.h, rexi_lg_*) ---------------------------------
+class LgDesc(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int), ("N", ctypes.c_int), ("dt", ctypes.c_double),
+                ("radius", ctypes.c_double), ("phibar", ctypes.c_double), ("p0", ctypes.c_double),
+                ("Xc", ctypes.c_double), ("z", _dp), ("w", _dp), ("phi", ctypes.c_int),
+                ("max_batch", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+_lib.rexi_lg_create.argtypes = [ctypes.POINTER(LgDesc), ctypes.POINTER(ctypes.c_void_p)]
+_lib.rexi_lg_destroy.argtypes = [ctypes.c_void_p]
+_lib.rexi_lg_step.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+_lib.rexi_lg_sync.argtypes = [ctypes.c_void_p]
+_lib.rexi_lg_get_operator.argtypes = [ctypes.c_void_p, _dp, _ip]
+
+
+class LgPlan:
+    """Gravity-only REXI plan: U1 = sum_p w_p (z_p - dt L_g)^-1 U0 (the lg_rexi_* methods)."""
+
+    def __init__(self, T, N, dt, radius, phibar, p0=None, Xc=None, z=None, w=None, phi=0,
+                 max_batch=1, stream=None):
+        d = LgDesc()
+        d.T, d.N, d.dt = int(T), int(N), float(dt)
+        d.radius, d.phibar = float(radius), float(phibar)
+        d.p0 = float(p0) if p0 is not None else 0.0
+        d.Xc = float(Xc) if Xc is not None else 0.0
+        self._zw = None
+        if z is not None:
+            zz = np.ascontiguousarray(np.asarray(z, dtype=np.complex128)).view(np.float64)
+            ww = np.ascontiguousarray(np.asarray(w, dtype=np.complex128)).view(np.float64)
+            self._zw = (zz, ww)
+            d.z = zz.ctypes.data_as(_dp)
+            d.w = ww.ctypes.data_as(_dp)
+        d.phi = int(phi)
+        d.max_batch = int(max_batch)
+        d.stream = ctypes.c_void_p(_stream_handle(stream))
+        h = ctypes.c_void_p()
+        _check(_lib.rexi_lg_create(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+        self.T, self.N, self.nlm, self.max_batch = int(T), int(N), nlm(T), int(max_batch)
+
+    def step(self, U0, U1, batch=None):
+        """U0, U1: CUDA complex128 tensors [batch, 3, nlm] (or [3, nlm]); U1 may be U0."""
+        if batch is None:
+            batch = 1 if U0.dim() == 2 else U0.shape[0]
+        for t in (U0, U1):
+            if not (t.is_cuda and t.is_contiguous()) or t.numel() != batch * 3 * self.nlm:
+                raise ValueError("need contiguous CUDA complex128 tensors of %d x 3 x %d"
+                                 % (batch, self.nlm))
+        _check(_lib.rexi_lg_step(self._h, ctypes.c_void_p(U0.data_ptr()),
+                                 ctypes.c_void_p(U1.data_ptr()), int(batch)))
+        return U1
+
+    def step_raw(self, U0_ptr, U1_ptr, batch):
+        return _lib.rexi_lg_step(self._h, ctypes.c_void_p(U0_ptr), ctypes.c_void_p(U1_ptr), int(batch))
+
+    def sync(self):
+        _check(_lib.rexi_lg_sync(self._h))
+
+    def operator(self):
+        """Per-degree pole sums [T+1, 4] complex (M_PhiPhi, M_PhiDelta, M_DeltaPhi, M_ZetaZeta)
+        and whether the step applies their real parts."""
+        M = np.empty(8 * (self.T + 1))
+        r = ctypes.c_int()
+        _check(_lib.rexi_lg_get_operator(self._h, M.ctypes.data_as(_dp), ctypes.byref(r)))
+        return M.view(np.complex128).reshape(self.T + 1, 4), bool(r.value)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.rexi_lg_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ---- spherical-harmonic transforms (include/sht.h) ------------------------------------
 SH_FP64, SH_TF32, SH_BF16 = 0, 1, 2
 _SH_PREC = {"fp64": SH_FP64, "tf32": SH_TF32, "bf16": SH_BF16}
@@ -435,7 +513,9 @@ class ShPlan:
 
 
 # ---- nonlinear shallow-water step (include/swe.h) ---------------------------------------
-SWE_VER1, SWE_VER0, SWE_ETDRK, SWE_IRK = 0, 1, 2, 3
+SWE_VER1, SWE_VER0, SWE_ETDRK, SWE_IRK, SWE_LG_VER1, SWE_LG_ETDRK = 0, 1, 2, 3, 4, 5
+SWE_SCHEMES = {"ver1": SWE_VER1, "ver0": SWE_VER0, "etdrk": SWE_ETDRK, "irk": SWE_IRK,
+               "lg_ver1": SWE_LG_VER1, "lg_etdrk": SWE_LG_ETDRK}
 
 
 class SweDesc(ctypes.Structure):
@@ -458,7 +538,8 @@ SWE_STAGE_NAMES = ("rexi", "legendre", "fft", "grid_products")
 
 class SwePlan:
     """Nonlinear SWE step on a Gauss grid: Strang split (l_rexi_n_erk_ver1 / ver0), ETD2RK
-    (l_rexi_n_etdrk) or Crank-Nicolson in the Strang split (l_irk_n_erk_ver1)."""
+    (l_rexi_n_etdrk), Crank-Nicolson in the Strang split (l_irk_n_erk_ver1), or the Coriolis
+    term in the explicit part (lg_rexi_lc_n_erk_ver1 "lg_ver1", lg_rexi_lc_n_etdrk "lg_etdrk")."""
 
     def __init__(self, T, nlat, nlon, dt, omega, radius, phibar, N, p0, Xc, rexi_precision="fp64",
                  sh_precision="fp64", scheme="ver1", stream=None):
@@ -468,8 +549,7 @@ class SwePlan:
         d.N, d.p0, d.Xc = int(N), float(p0), float(Xc)
         d.rexi_precision = _PREC[rexi_precision] if isinstance(rexi_precision, str) else int(rexi_precision)
         d.sh_precision = _SH_PREC[sh_precision] if isinstance(sh_precision, str) else int(sh_precision)
-        d.scheme = ({"ver1": SWE_VER1, "ver0": SWE_VER0, "etdrk": SWE_ETDRK, "irk": SWE_IRK}[scheme]
-                    if isinstance(scheme, str) else int(scheme))
+        d.scheme = SWE_SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
         d.stream = ctypes.c_void_p(_stream_handle(stream))
         h = ctypes.c_void_p()
         _check(_lib.swe_plan_create(ctypes.byref(d), ctypes.byref(h)))

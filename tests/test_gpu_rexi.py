@@ -128,6 +128,24 @@ def test_T255_N512_batched_sampled(env, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("T,N,dt,ms", [
+    (511, 2048, 7200.0, [0, 1, 2, 255, 510, 511]),      # the high-resolution configuration
+    (1023, 1024, 3600.0, [0, 1, 511, 1022, 1023]),      # the largest truncation a plan accepts
+])
+def test_largest_sizes_sampled(env, prec, T, N, dt, ms):
+    """T511 with 2048 poles at dt = 7200 s and T1023 (the plan's maximum truncation, chains of
+    up to 512 elements per parity): sampled zonal orders, first and last included."""
+    p0, Xc, X = contour(T, dt, N)
+    U0 = syn.gaussian_state(T, 7)
+    z, w = oc.rexi_coefficients(N, p0, Xc)
+    ref = orx.rexi_step(U0, T, dt, OM, A, PB, z, w, m_list=ms)
+    out, info = run_plan(env, T, N, dt, U0, prec, p0, Xc)
+    err = masked_rel(out, ref, T, ms)
+    tol = fp64_tol(z, w, X) if prec == "fp64" else 1e-8
+    assert np.all(err < tol), (err, tol, info)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_batch_matches_single_and_is_deterministic(env, prec):
     torch, rexi = env
     T, N, dt = 63, 256, 3600.0
