@@ -133,25 +133,36 @@ def test_nonconjugate_poles_use_complex_sums(env):
 
 
 def test_operator_is_the_oracle_on_unit_inputs(env):
-    """M_n read back from the plan equals the oracle's response to unit coefficients."""
+    """M_n read back from the plan equals the oracle's response to unit coefficients, each entry
+    to 64 eps times the sum of the magnitudes of its terms (the rounding bound of the pole
+    sum: M_PP from w z / det, M_PD and M_DP from w / det scaled by dt Phibar and dt q_n,
+    M_ZZ from w / z)."""
     T, N, dt = 15, 64, 3600.0
     p0, Xc, X = contour(T, dt)
     z, w = oc.rexi_coefficients(N, p0, Xc)
     _, (M, real) = run(env, T, N, dt, syn.gaussian_state(T, 1), p0=p0, Xc=Xc)
     nlm = (T + 1) * (T + 2) // 2
+    eps = 2.0 ** -53
+    se = np.sum(np.abs(w / z))
     for n in (0, 1, 7, 15):
+        q = n * (n + 1.0) / A ** 2
+        det = z * z + dt * dt * PB * q
+        s1 = np.sum(np.abs(w * z / det)) if n else se
+        s0 = np.sum(np.abs(w / det))
         i = n  # m = 0 block: index n
-        for f in (0, 2, 1):
+        resp = {}
+        for f in (0, 1, 2):
             U = np.zeros((3, nlm), complex)
             U[f, i] = 1.0
-            r = olg.rexi_step_lg(U, T, dt, A, PB, z, w)[:, i]
-            scale = np.sum(np.abs(w)) * 1e-13
-            if f == 0:      # Phi in: (M_PP, M_DP)
-                assert abs(r[0] - M[n, 0]) < scale and abs(r[2] - M[n, 2]) < scale
-            elif f == 2:    # delta in: (M_PD, M_DD = M_PP)
-                assert abs(r[0] - M[n, 1]) < scale and abs(r[2] - M[n, 0]) < scale
-            else:           # zeta in: M_ZZ
-                assert abs(r[1] - M[n, 3]) < scale
+            resp[f] = olg.rexi_step_lg(U, T, dt, A, PB, z, w)[:, i]
+        checks = [(resp[0][0], M[n, 0], s1), (resp[2][2], M[n, 0], s1), (resp[1][1], M[n, 3], se)]
+        if n:
+            checks += [(resp[2][0], M[n, 1], dt * PB * s0), (resp[0][2], M[n, 2], dt * q * s0)]
+        else:
+            checks += [(resp[2][0], M[n, 1], se), (resp[0][2], M[n, 2], se)]
+        for got, ref, scale in checks:
+            assert abs(got - ref) <= 64 * eps * scale, (n, got, ref, scale)
+    assert real
 
 
 def test_errors(env):
