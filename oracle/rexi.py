@@ -101,14 +101,15 @@ def exact_phi(U0, T, dt, Omega, radius, Phibar, k):
     return out
 
 
-def cn_step(U0, T, dt, Omega, radius, Phibar, a=0.5):
+def cn_step(U0, T, dt, Omega, radius, Phibar, a=0.5, part="L"):
     """Crank-Nicolson (Sec. 4.1, the irk scheme):  U+ = (I - a dt L)^-1 (I + (1 - a) dt L) U0,
     a = 1/2; the forward-Euler half by linop.apply_L, the backward-Euler half by the pivoted
-    banded LU of every zonal order (the same solver as rexi_step)."""
-    V = U0 + (1.0 - a) * dt * linop.apply_L(U0, T, Omega, radius, Phibar)
+    banded LU of every zonal order (the same solver as rexi_step).  part = "Lg" applies it to
+    the gravity operator alone (the lg_irk_* methods of Table 2)."""
+    V = U0 + (1.0 - a) * dt * linop.apply_L(U0, T, Omega, radius, Phibar, part)
     out = np.zeros_like(U0, dtype=np.complex128)
     for m in range(T + 1):
-        A = a * dt * linop.operator_m(T, m, Omega, radius, Phibar)
+        A = a * dt * linop.operator_m(T, m, Omega, radius, Phibar, part)
         ab = _band(-A)
         ab[4, :] += 1.0
         linop.merge_m(out, scipy.linalg.solve_banded((4, 4), ab, linop.split_m(V, T, m)), T, m)

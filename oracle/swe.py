@@ -26,7 +26,9 @@ Time integrators (Sec. 4.1, 4.4; Table 2):
            REXI (a diagonal solve, oracle.rexi_lg), the Coriolis term L_c joins N in the
            explicit part:  N'(U) = L_c U + N(U).  lg ver1 is N'^{dt/2} o L_g^{dt} o N'^{dt/2}
            (lg_rexi_lc_n_erk_ver1, the paper's best REXI method, Sec. 5.2); lg etdrk is
-           ETD2RK with (L_g, N') in place of (L, N) (lg_rexi_lc_n_etdrk).
+           ETD2RK with (L_g, N') in place of (L, N) (lg_rexi_lc_n_etdrk).  lg irk ver0 is
+           CN_g^{dt/2} o N'^{dt} o CN_g^{dt/2} with Crank-Nicolson for L_g (lg_irk_lc_n_erk_ver0,
+           the paper's best implicit method).
 """
 import numpy as np
 
@@ -81,6 +83,16 @@ def strang_lg_ver1(U, grid, dt, Omega, Phibar, z, w):
     U1 = rk2(U, f, 0.5 * dt)
     U2 = rexi_lg.rexi_step_lg(U1, T, dt, a, Phibar, z, w)
     return rk2(U2, f, 0.5 * dt)
+
+
+def cn_lg_ver0(U, grid, dt, Omega, Phibar):
+    """One step of lg_irk_lc_n_erk_ver0 (the paper's best implicit method, Sec. 5.2):
+    CN_g^{dt/2} o N'^{dt} o CN_g^{dt/2}, CN_g the Crank-Nicolson step of the gravity operator
+    alone and N' = L_c + N by RK2 (Sec. 4.4 version 0)."""
+    T, a = grid.T, grid.a
+    U1 = rexi.cn_step(U, T, 0.5 * dt, Omega, a, Phibar, part="Lg")
+    U2 = rk2(U1, lambda V: nonlinear_lc(V, grid, Omega), dt)
+    return rexi.cn_step(U2, T, 0.5 * dt, Omega, a, Phibar, part="Lg")
 
 
 def etd2rk_lg(U, grid, dt, Omega, Phibar, z, w0, w1, w2):

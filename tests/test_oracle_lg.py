@@ -9,6 +9,8 @@ Sec. 5.3 diagonal solve; Table 2 lg_rexi_lc_n_erk_ver1 and lg_rexi_lc_n_etdrk).
   Omega = 0 (no Coriolis: L = L_g), and lies within the scalar error of the closed form.
 * psi_1 / psi_2 weights of the same poles apply psi_k(dt L_g) (Sec. 4.3).
 * lg ver1 and lg ETD2RK converge at 2nd order to a small-step RK4 reference of the same PDE.
+* Crank-Nicolson of L_g alone is the Cayley map of dt L_g (eigen route at Omega = 0) and its
+  ver0 split (lg_irk_lc_n_erk_ver0) converges at 2nd order.
 """
 import math
 
@@ -134,3 +136,17 @@ def test_etd2rk_lg_second_order():
         w2 = coeffs.rexi_coefficients(128, p0, Xc, k=2)[1]
         return swe.etd2rk_lg(U, g, dt, OM, PB, z, w0, w1, w2)
     _converges(step)
+
+
+def test_cn_of_lg_is_the_cayley_map():
+    T, dt = 15, 3600.0
+    U = syn.gaussian_state(T, 46)
+    cn = rexi.cn_step(U, T, dt, OM, A, PB, part="Lg")
+    ref = rexi.exact_cayley(U, T, dt, 0.0, A, PB)
+    assert np.max(rexi.rel_l2(cn, ref, T)) < 1e-12
+    # L_g has no zeta terms: zeta passes through unchanged
+    assert np.max(np.abs(cn[1] - U[1])) == 0.0
+
+
+def test_cn_lg_ver0_second_order():
+    _converges(lambda U, g, dt, X: swe.cn_lg_ver0(U, g, dt, OM, PB))
