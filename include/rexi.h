@@ -177,6 +177,9 @@ typedef struct rexi_lg_desc {
   const double* z;    /* optional host array, 2N doubles: poles z_p                      */
   const double* w;    /* optional host array, 2N doubles: weights w_p                    */
   int phi;            /* z == NULL: 0, 1, 2 for the psi_0, psi_1, psi_2 weights (rexi_coeffs) */
+  double ident;       /* coefficient c0 of a polynomial part: the plan applies              */
+                      /* c0 I + sum_p w_p (z_p - dt L_g)^-1 (0 for REXI; Crank-Nicolson of   */
+                      /* L_g over dt is 4 (2 - dt L_g)^-1 - I: one pole z = 2, w = 4, c0 = -1) */
   int max_batch;      /* largest batch passed to rexi_lg_step, >= 1                      */
   void* stream;       /* cudaStream_t the plan launches on (NULL: legacy default stream) */
 } rexi_lg_desc;

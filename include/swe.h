@@ -39,6 +39,12 @@ extern "C" {
  * LG_..._ETDRK: ETD2RK with (L_g, N') in place of (L, N), psi_k(dt L_g) by the diagonal REXI. */
 #define SWE_LG_REXI_LC_N_ERK_VER1 4
 #define SWE_LG_REXI_LC_N_ETDRK 5
+/* The paper's best implicit method (Sec. 5.2, lg_irk_lc_n_erk_ver0): Crank-Nicolson of L_g alone
+ * inside the ver0 split, U+ = CN_g^{dt/2} o N'^{dt} o CN_g^{dt/2} (U), N' = L_c + N by RK2;
+ * CN_g over a step h is (I - h L_g / 2)^-1 (I + h L_g / 2) = 4 (2 - h L_g)^-1 - I, a gravity-only
+ * plan with one pole z = 2, weight 4 and ident = -1 (FP64); N, p0, Xc and rexi_precision are
+ * not used. */
+#define SWE_LG_IRK_LC_N_ERK_VER0 6
 
 typedef struct swe_plan swe_plan;
 

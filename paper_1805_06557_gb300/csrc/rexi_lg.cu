@@ -30,9 +30,10 @@ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
 
 // One thread per degree n: S1 = sum w z / det, S0 = sum w / det, E = sum w / z with
 // det = z^2 + dt^2 Phibar q_n; M_PP = S1, M_PD = -dt Phibar S0, M_DP = dt q_n S0, M_ZZ = E.
-// Degree 0 (zero operator row): every field gets E.
+// Degree 0 (zero operator row): every field gets E.  A polynomial part c0 I is added to the
+// diagonal (M_PP, M_DD, M_ZZ).
 __global__ void k_lg_sums(const double2* __restrict__ z, const double2* __restrict__ w, int N, int T,
-                          double dt, double phibar, double inv_a2, LgM* __restrict__ M) {
+                          double dt, double phibar, double inv_a2, double ident, LgM* __restrict__ M) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n > T) return;
   const double q = double(n) * (n + 1) * inv_a2;
@@ -56,6 +57,8 @@ __global__ void k_lg_sums(const double2* __restrict__ z, const double2* __restri
     r.dp = make_double2(dt * q * s0.x, dt * q * s0.y);
   }
   r.zz = e;
+  r.pp.x += ident;  // polynomial part c0 I (M_DD = M_PP carries it too)
+  r.zz.x += ident;
   M[n] = r;
 }
 
@@ -138,8 +141,8 @@ extern "C" int rexi_lg_create(const rexi_lg_desc* desc, rexi_lg_plan** out) {
   const rexi_lg_desc& d = *desc;
   if (d.T < 1 || d.T > 1023) return fail(REXI_EINVAL, "rexi_lg_create: T must be in [1, 1023] (got %d)", d.T);
   if (d.N < 1 || d.N > 8192) return fail(REXI_EINVAL, "rexi_lg_create: N must be in [1, 8192] (got %d)", d.N);
-  if (!(d.dt > 0) || !(d.radius > 0) || !(d.phibar > 0))
-    return fail(REXI_EINVAL, "rexi_lg_create: need dt > 0, radius > 0, phibar > 0");
+  if (!(d.dt > 0) || !(d.radius > 0) || !(d.phibar > 0) || !std::isfinite(d.ident))
+    return fail(REXI_EINVAL, "rexi_lg_create: need dt > 0, radius > 0, phibar > 0, finite ident");
   if (d.max_batch < 1) return fail(REXI_EINVAL, "rexi_lg_create: max_batch must be >= 1");
   if ((d.z == nullptr) != (d.w == nullptr)) return fail(REXI_EINVAL, "rexi_lg_create: give both z and w or neither");
   if (!d.z && (!(d.p0 > 0) || !(d.Xc > 0) || d.phi < 0 || d.phi > 2))
@@ -191,7 +194,8 @@ extern "C" int rexi_lg_create(const rexi_lg_desc* desc, rexi_lg_plan** out) {
     return bail(cuda_fail(e, "rexi_lg_create: cudaMemcpy"));
   }
   const int tb = 128, nb = (d.T + 1 + tb - 1) / tb;
-  k_lg_sums<<<nb, tb, 0, p->stream>>>(dz, dw, d.N, d.T, d.dt, d.phibar, 1.0 / (d.radius * d.radius), p->M);
+  k_lg_sums<<<nb, tb, 0, p->stream>>>(dz, dw, d.N, d.T, d.dt, d.phibar, 1.0 / (d.radius * d.radius), d.ident,
+                                      p->M);
   k_lg_pack_real<<<nb, tb, 0, p->stream>>>(p->M, p->R, d.T);
   e = cudaGetLastError();
   if (!e) e = cudaStreamSynchronize(p->stream);

@@ -181,11 +181,12 @@ extern "C" int swe_plan_create(const swe_plan_desc* desc, swe_plan** out) {
   if (!desc || !out) return fail(REXI_EINVAL, "swe_plan_create: null argument");
   *out = nullptr;
   const swe_plan_desc& d = *desc;
-  if (d.scheme < SWE_L_REXI_N_ERK_VER1 || d.scheme > SWE_LG_REXI_LC_N_ETDRK)
+  if (d.scheme < SWE_L_REXI_N_ERK_VER1 || d.scheme > SWE_LG_IRK_LC_N_ERK_VER0)
     return fail(REXI_EINVAL, "swe_plan_create: unknown scheme %d", d.scheme);
   swe_plan* p = new swe_plan();
   p->d = d;
-  p->is_lg = d.scheme == SWE_LG_REXI_LC_N_ERK_VER1 || d.scheme == SWE_LG_REXI_LC_N_ETDRK;
+  p->is_lg = d.scheme == SWE_LG_REXI_LC_N_ERK_VER1 || d.scheme == SWE_LG_REXI_LC_N_ETDRK ||
+             d.scheme == SWE_LG_IRK_LC_N_ERK_VER0;
   p->stream = (cudaStream_t)d.stream;
   p->prof.stream = p->stream;
   p->nlm = (d.T + 1) * (d.T + 2) / 2;
@@ -224,6 +225,7 @@ extern "C" int swe_plan_create(const swe_plan_desc* desc, swe_plan** out) {
     rd.w = cn_w;
     rd.precision = REXI_FP64;
   }
+  double cn_w4[2] = {4.0, 0.0};
   if (p->is_lg) {  // L_g by the diagonal REXI (FP64), psi_1 and psi_2 too for ETD2RK
     const int nk = d.scheme == SWE_LG_REXI_LC_N_ETDRK ? 3 : 1;
     for (int k = 0; k < nk; ++k) {
@@ -238,6 +240,13 @@ extern "C" int swe_plan_create(const swe_plan_desc* desc, swe_plan** out) {
       ld.phi = k;
       ld.max_batch = 1;
       ld.stream = d.stream;
+      if (d.scheme == SWE_LG_IRK_LC_N_ERK_VER0) {  // CN_g over dt/2: 4 (2 - (dt/2) L_g)^-1 - I
+        ld.N = 1;
+        ld.dt = 0.5 * d.dt;
+        ld.z = cn_z;
+        ld.w = cn_w4;
+        ld.ident = -1.0;
+      }
       if ((rc = rexi_lg_create(&ld, &p->lg[k]))) return bail(rc);
     }
   } else {
@@ -375,6 +384,10 @@ extern "C" int swe_step(swe_plan* p, void* state, int nsteps) {
       if ((rc = rk2_nonlinear(p, U, 0.5 * dt))) return rc;
       if ((rc = lg_step(p, 0, U, U))) return rc;  // in place
       if ((rc = rk2_nonlinear(p, U, 0.5 * dt))) return rc;
+    } else if (p->d.scheme == SWE_LG_IRK_LC_N_ERK_VER0) {
+      if ((rc = lg_step(p, 0, U, U))) return rc;  // CN_g^{dt/2}, in place
+      if ((rc = rk2_nonlinear(p, U, dt))) return rc;
+      if ((rc = lg_step(p, 0, U, U))) return rc;
     } else if (p->d.scheme == SWE_LG_REXI_LC_N_ETDRK) {
       const int n3 = 3 * p->nlm, tb = 256, nb = (n3 + tb - 1) / tb;
       if ((rc = nonlinear_update(p, U, nullptr, 0.0, p->NU, p->Ltab))) return rc;  // N'(U)

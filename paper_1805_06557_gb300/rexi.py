@@ -347,7 +347,7 @@ class LgDesc(ctypes.Structure):
     _fields_ = [("T", ctypes.c_int), ("N", ctypes.c_int), ("dt", ctypes.c_double),
                 ("radius", ctypes.c_double), ("phibar", ctypes.c_double), ("p0", ctypes.c_double),
                 ("Xc", ctypes.c_double), ("z", _dp), ("w", _dp), ("phi", ctypes.c_int),
-                ("max_batch", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("ident", ctypes.c_double), ("max_batch", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 _lib.rexi_lg_create.argtypes = [ctypes.POINTER(LgDesc), ctypes.POINTER(ctypes.c_void_p)]
@@ -361,7 +361,7 @@ class LgPlan:
     """Gravity-only REXI plan: U1 = sum_p w_p (z_p - dt L_g)^-1 U0 (the lg_rexi_* methods)."""
 
     def __init__(self, T, N, dt, radius, phibar, p0=None, Xc=None, z=None, w=None, phi=0,
-                 max_batch=1, stream=None):
+                 ident=0.0, max_batch=1, stream=None):
         d = LgDesc()
         d.T, d.N, d.dt = int(T), int(N), float(dt)
         d.radius, d.phibar = float(radius), float(phibar)
@@ -375,6 +375,7 @@ class LgPlan:
             d.z = zz.ctypes.data_as(_dp)
             d.w = ww.ctypes.data_as(_dp)
         d.phi = int(phi)
+        d.ident = float(ident)
         d.max_batch = int(max_batch)
         d.stream = ctypes.c_void_p(_stream_handle(stream))
         h = ctypes.c_void_p()
@@ -513,9 +514,9 @@ class ShPlan:
 
 
 # ---- nonlinear shallow-water step (include/swe.h) ---------------------------------------
-SWE_VER1, SWE_VER0, SWE_ETDRK, SWE_IRK, SWE_LG_VER1, SWE_LG_ETDRK = 0, 1, 2, 3, 4, 5
+SWE_VER1, SWE_VER0, SWE_ETDRK, SWE_IRK, SWE_LG_VER1, SWE_LG_ETDRK, SWE_LG_IRK_VER0 = range(7)
 SWE_SCHEMES = {"ver1": SWE_VER1, "ver0": SWE_VER0, "etdrk": SWE_ETDRK, "irk": SWE_IRK,
-               "lg_ver1": SWE_LG_VER1, "lg_etdrk": SWE_LG_ETDRK}
+               "lg_ver1": SWE_LG_VER1, "lg_etdrk": SWE_LG_ETDRK, "lg_irk_ver0": SWE_LG_IRK_VER0}
 
 
 class SweDesc(ctypes.Structure):
@@ -539,7 +540,8 @@ SWE_STAGE_NAMES = ("rexi", "legendre", "fft", "grid_products")
 class SwePlan:
     """Nonlinear SWE step on a Gauss grid: Strang split (l_rexi_n_erk_ver1 / ver0), ETD2RK
     (l_rexi_n_etdrk), Crank-Nicolson in the Strang split (l_irk_n_erk_ver1), or the Coriolis
-    term in the explicit part (lg_rexi_lc_n_erk_ver1 "lg_ver1", lg_rexi_lc_n_etdrk "lg_etdrk")."""
+    term in the explicit part (lg_rexi_lc_n_erk_ver1 "lg_ver1", lg_rexi_lc_n_etdrk "lg_etdrk",
+    lg_irk_lc_n_erk_ver0 "lg_irk_ver0")."""
 
     def __init__(self, T, nlat, nlon, dt, omega, radius, phibar, N, p0, Xc, rexi_precision="fp64",
                  sh_precision="fp64", scheme="ver1", stream=None):

@@ -117,6 +117,17 @@ def test_psi_weights(env, k):
     assert np.all(orx.rel_l2(out, ref, T) < tol(z, w, X))
 
 
+def test_crank_nicolson_as_one_pole_plus_identity(env):
+    """ident = -1 with the single pole z = 2, w = 4 is Crank-Nicolson of L_g:
+    (I - dt L_g / 2)^-1 (I + dt L_g / 2) = 4 (2 - dt L_g)^-1 - I (Sec. 4.1, lg_irk)."""
+    T, dt = 63, 1800.0
+    U0 = syn.gaussian_state(T, 95)
+    ref = orx.cn_step(U0, T, dt, 0.0, A, PB, part="Lg")
+    out, (M, real) = run(env, T, 1, dt, U0, z=[2.0], w=[4.0], ident=-1.0)
+    assert real
+    assert np.all(orx.rel_l2(out, ref, T) < 1e-13)
+
+
 def test_nonconjugate_poles_use_complex_sums(env):
     """A pole set that is not closed under conjugation (the upper half of a contour) keeps the
     complex per-degree sums."""

@@ -62,7 +62,8 @@ def test_nonlinear_matches_oracle(env, T, nlat, nlon, kind, tol):
 @pytest.mark.parametrize("scheme,rprec,tol", [("ver1", "fp64", 1e-10), ("ver0", "fp64", 1e-10),
                                               ("ver1", "mixed", 1e-8), ("etdrk", "fp64", 1e-10),
                                               ("etdrk", "mixed", 1e-8), ("irk", "fp64", 1e-10),
-                                              ("lg_ver1", "fp64", 1e-10), ("lg_etdrk", "fp64", 1e-10)])
+                                              ("lg_ver1", "fp64", 1e-10), ("lg_etdrk", "fp64", 1e-10),
+                                              ("lg_irk_ver0", "fp64", 1e-10)])
 def test_strang_steps_match_oracle(env, scheme, rprec, tol):
     """Strang ver1 / ver0 (Sec. 4.4), ETD2RK (Sec. 4.3), the Crank-Nicolson Strang step
     (Sec. 4.1) and the lg schemes (Coriolis in the explicit part, Table 2) against the oracle."""
@@ -83,6 +84,8 @@ def test_strang_steps_match_oracle(env, scheme, rprec, tol):
             ref = oswe.cn_ver1(ref, g, dt, OM, PB)
         elif scheme == "lg_ver1":
             ref = oswe.strang_lg_ver1(ref, g, dt, OM, PB, z, w)
+        elif scheme == "lg_irk_ver0":
+            ref = oswe.cn_lg_ver0(ref, g, dt, OM, PB)
         elif scheme == "lg_etdrk":
             w1 = oc.rexi_coefficients(N, p0, Xc, k=1)[1]
             w2 = oc.rexi_coefficients(N, p0, Xc, k=2)[1]
