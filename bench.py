@@ -579,7 +579,8 @@ def main():
     fp64_tf, fp32_tf = rexi.alu_peaks()
     kw = dict(omega=syn.OMEGA, radius=syn.RADIUS, phibar=syn.PHIBAR, p0=p0, Xc=Xc)
     mixed = rexi.Plan(T, N, dt, precision="mixed", max_batch=B, **kw)
-    fp64 = rexi.Plan(T, N, dt, precision="fp64", max_batch=B, **kw)
+    fp64 = rexi.Plan(T, N, dt, precision="fp64", max_batch=B, **kw)            # every pole
+    fp64p = rexi.Plan(T, N, dt, precision="fp64", max_batch=B, prune_tau=2.0 ** -70, **kw)
 
     def timed(plan, a, b, nb, steps, warmup):
         for _ in range(warmup):
@@ -629,10 +630,20 @@ def main():
     fp64_b1 = timed(fp64, u0[:1].contiguous(), u1[:1].contiguous(), 1, ks, 2)
     fp64_bb = timed(fp64, u0, u1, B, ks, 1)
     mix_b1 = timed(mixed, u0[:1].contiguous(), u1[:1].contiguous(), 1, ks, 2)
+    # FP64 with the same pole pruning as the mixed plan (summed gain of the poles left out
+    # <= 2^-70): separates the pruning from the mixed-precision gain
+    p64 = torch.empty_like(u0)
+    fp64p.step(u0, p64, B)
+    torch.cuda.synchronize()
+    ap = p64.cpu().numpy()
+    err_p64 = [float(np.sqrt(np.sum(wts * np.abs(ap[:, f] - r[:, f]) ** 2)) /
+                     np.sqrt(np.sum(wts * np.abs(r[:, f]) ** 2))) for f in range(3)]
+    fp64p_b1 = timed(fp64p, u0[:1].contiguous(), u1[:1].contiguous(), 1, ks, 2)
+    fp64p_bb = timed(fp64p, u0, u1, B, ks, 1)
 
     # ---- rooflines of the solve kernels (event times of the timed region) -----------------
     info = mixed.info()
-    n_light = N - info["n_heavy"]
+    n_light = N - info["n_pruned"] - info["n_heavy"]
     elems = 2 * nlm * B  # chain elements per pole per launch (two parity chains per m)
     kernels = {}
     for kname, (kms, kn) in prof.items():
@@ -704,7 +715,11 @@ def main():
         "fp64_batched_steps_per_s": B * 1e3 / statistics.mean(fp64_bb),
         "mixed_single_steps_per_s": 1e3 / statistics.mean(mix_b1),
         "speedup_vs_fp64_plain": value / world / (1e3 / statistics.mean(fp64_b1)),
-        "plan": {k: info[k] for k in ("n_heavy", "n_groups", "q_slots", "grid_light", "grid_heavy")},
+        "fp64_pruned": {"single_steps_per_s": 1e3 / statistics.mean(fp64p_b1),
+                        "batched_steps_per_s": B * 1e3 / statistics.mean(fp64p_bb),
+                        "n_pruned": fp64p.info()["n_pruned"], "rel_err_vs_fp64_plain": err_p64},
+        "plan": {k: info[k] for k in ("n_heavy", "n_pruned", "pruned_gain", "n_groups", "q_slots", "grid_light",
+                                      "grid_heavy")},
         "alu_peaks_tflops": {"fp64": fp64_tf, "fp32": fp32_tf},
         "ensemble": ens, "sh_transforms": sh, "swe_step": swe, "lg_rexi": lg,
         "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
@@ -714,6 +729,7 @@ def main():
         print(json.dumps(line), flush=True)
     mixed.close()
     fp64.close()
+    fp64p.close()
     if dist is not None:
         dist.destroy_process_group()
 

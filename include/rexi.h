@@ -86,6 +86,11 @@ typedef struct rexi_plan_desc {
                       /* exceeds heavy_tau is refined and summed in FP64; < 0: 1e-3      */
   int max_batch;      /* largest batch passed to rexi_step, >= 1                         */
   void* stream;       /* cudaStream_t the plan launches on (NULL: legacy default stream) */
+  double prune_tau;   /* pole pruning: the poles of smallest gain |w_n| / dist(z_n, [-iX, iX]) */
+                      /* (a bound on the energy-norm size of their term relative to U0, dt L */
+                      /* being skew-adjoint in that norm) are left out while their summed    */
+                      /* gain stays <= prune_tau, conjugate pairs together; 0: default    */
+                      /* (REXI_MIXED 2^-70, REXI_FP64 none: every pole is solved); < 0: none */
 } rexi_plan_desc;
 
 /*
@@ -139,14 +144,17 @@ typedef struct rexi_plan_info {
   int q_slots;            /* pole ranges summed separately before the final sum          */
   int grid_fp64, grid_light, grid_heavy;   /* persistent grid sizes (blocks)            */
   long long workspace_bytes;               /* device memory owned by the plan           */
-  double s0_re, s0_im;    /* sum_n w_n / z_n                                             */
+  double s0_re, s0_im;    /* sum_n w_n / z_n over the poles solved                       */
   double X;               /* covered half-width used for the heavy classification        */
+  int n_pruned;           /* poles left out by pruning                                   */
+  double pruned_gain;     /* their summed gain (bound on the relative energy-norm change) */
 } rexi_plan_info;
 
 int rexi_plan_get_info(const rexi_plan* plan, rexi_plan_info* info);
 
-/* Copies the plan's poles and weights (in the plan's internal order, 2*N doubles each)
- * and the per-pole heavy flags (N ints) to host arrays; any pointer may be NULL. */
+/* Copies the plan's poles and weights (2*N doubles each: the solved poles in the plan's
+ * internal order, then the pruned ones) and per-pole classes (N ints: 1 heavy, 0 light,
+ * -1 pruned) to host arrays; any pointer may be NULL. */
 int rexi_plan_get_poles(const rexi_plan* plan, double* z, double* w, int* heavy);
 
 /*
@@ -224,6 +232,7 @@ typedef struct rexi_ragged_desc {
   int precision;       /* REXI_FP64 or REXI_MIXED                                            */
   double heavy_tau;    /* as in rexi_plan_desc                                               */
   void* stream;        /* cudaStream_t (graph capture needs a non-default stream)            */
+  double prune_tau;    /* as in rexi_plan_desc, per instance pole set                        */
 } rexi_ragged_desc;
 
 typedef struct rexi_instance {

@@ -43,34 +43,76 @@ int dev_alloc(P** p, size_t bytes, long long* acc) {
 // ---- pole sets (host) -----------------------------------------------------------------
 struct PoleSet {
   int T = 0, N = 0, Npad = 0, ngroups = 0, n_heavy = 0, g_light = 0, g_heavy = 0;
+  int n_pruned = 0;         // poles left out (their summed gain is <= the pruning threshold)
+  double pruned_gain = 0;   // sum of the gains of the poles left out
   double dt = 0, X = 0;
   cplx S0 = 0;
   std::vector<cplx> z, w;   // internal order, padded, unscaled
   std::vector<int> heavy;
+  std::vector<cplx> zp, wp; // poles left out (reported by rexi_plan_get_poles)
   int pole0 = -1;           // position in the device arena (-1: not uploaded)
 };
 
-// Orders (and pads) the poles.  FP64: given order, padding at the end.  MIXED: light poles
-// first, heavy ones (largest gain |w| / dist(z, [-iX, iX]), padded to whole groups) last.
+// Default pruning threshold of mixed plans: the summed gain of the poles left out is at most
+// 2^-70 (the change of the result in the energy norm, relative to the state).
+constexpr double PRUNE_TAU_MIXED = 8.470329472543003e-22;
+
+// Orders (and pads) the poles.  Every pole n has the gain g_n = |w_n| / dist(z_n, [-iX, iX]),
+// a bound on the energy-norm size of its term w_n (z_n - dt L)^-1 U0 relative to U0 (dt L is
+// skew-adjoint in the energy inner product with its spectrum in [-iX, iX]).  Pruning: the
+// poles of smallest gain are left out while their summed gain stays <= prune_tau (conjugate
+// pairs, which have equal gains, stay together); prune_tau = 0 selects the default (mixed:
+// 2^-70, FP64: no pruning), prune_tau < 0 no pruning.  FP64: the kept poles in the given
+// order, padding at the end.
+// MIXED: light poles first, heavy ones (gain > heavy_tau, padded to whole groups) last.
 int make_poleset(PoleSet& ps, int precision, int T, int N, double dt, double X, const cplx* z,
-                 const cplx* w, double heavy_tau) {
+                 const cplx* w, double heavy_tau, double prune_tau) {
   ps.T = T;
   ps.N = N;
   ps.dt = dt;
   ps.X = X;
   for (int n = 0; n < N; ++n)
     if (std::abs(z[n]) < 1e-12) return fail(REXI_EINVAL, "pole %d is zero", n);
-  cplx s = 0, comp = 0;  // S0 = sum w/z, compensated
+  std::vector<double> gain(N);
   for (int n = 0; n < N; ++n) {
+    const double yi = std::min(std::max(z[n].imag(), -X), X);
+    gain[n] = std::abs(w[n]) / std::max(std::abs(z[n] - cplx(0.0, yi)), 1e-300);
+  }
+  std::vector<int> by_gain(N);
+  std::iota(by_gain.begin(), by_gain.end(), 0);
+  std::stable_sort(by_gain.begin(), by_gain.end(), [&](int a, int b) { return gain[a] > gain[b]; });
+  const double ptau = prune_tau > 0 ? prune_tau : (prune_tau == 0 && precision == REXI_MIXED ? PRUNE_TAU_MIXED : -1.0);
+  int nkeep = N;
+  ps.pruned_gain = 0.0;
+  if (ptau >= 0) {
+    double tail = 0.0;  // summed gain of by_gain[nkeep..N)
+    while (nkeep > 1 && tail + gain[by_gain[nkeep - 1]] <= ptau) tail += gain[by_gain[--nkeep]];
+    while (nkeep < N && nkeep > 0 && gain[by_gain[nkeep]] == gain[by_gain[nkeep - 1]])  // keep pairs whole
+      tail -= gain[by_gain[nkeep++]];
+    ps.pruned_gain = std::max(tail, 0.0);
+  }
+  std::vector<char> keep(N, 0);
+  for (int i = 0; i < nkeep; ++i) keep[by_gain[i]] = 1;
+  ps.n_pruned = N - nkeep;
+  ps.zp.clear();
+  ps.wp.clear();
+  for (int n = 0; n < N; ++n)
+    if (!keep[n]) {
+      ps.zp.push_back(z[n]);
+      ps.wp.push_back(w[n]);
+    }
+  cplx s = 0, comp = 0;  // S0 = sum w/z over the kept poles, compensated
+  for (int n = 0; n < N; ++n) {
+    if (!keep[n]) continue;
     const cplx yv = w[n] / z[n] - comp;
     const cplx t = s + yv;
     comp = (t - s) - yv;
     s = t;
   }
   ps.S0 = s;
-  ps.Npad = (N + 31) / 32 * 32;
+  ps.Npad = (nkeep + 31) / 32 * 32;
   ps.ngroups = ps.Npad / 32;
-  const int npad = ps.Npad - N;
+  const int npad = ps.Npad - nkeep;
   ps.z.clear();
   ps.w.clear();
   ps.heavy.clear();
@@ -79,38 +121,26 @@ int make_poleset(PoleSet& ps, int precision, int T, int N, double dt, double X, 
     ps.w.push_back(ww);
     ps.heavy.push_back(h);
   };
-  if (precision == REXI_FP64) {
-    for (int n = 0; n < N; ++n) push(z[n], w[n], 1);
+  auto all_heavy = [&]() {
+    for (int n = 0; n < N; ++n)
+      if (keep[n]) push(z[n], w[n], 1);
     for (int i = 0; i < npad; ++i) push(1.0, 0.0, 1);
-    ps.n_heavy = N;
+    ps.n_heavy = nkeep;
     ps.g_light = 0;
     ps.g_heavy = ps.ngroups;
     return REXI_OK;
-  }
+  };
+  if (precision == REXI_FP64) return all_heavy();
   const double tau = heavy_tau < 0 ? 1e-3 : heavy_tau;
-  std::vector<double> gain(N);
   int nh = 0;
-  for (int n = 0; n < N; ++n) {
-    const double yi = std::min(std::max(z[n].imag(), -X), X);
-    gain[n] = std::abs(w[n]) / std::max(std::abs(z[n] - cplx(0.0, yi)), 1e-300);
-    if (gain[n] > tau) ++nh;
-  }
-  const int nh_pad = std::min((nh + 31) / 32 * 32, N);
-  if (nh_pad == N && N % 32 != 0) {  // everything heavy, padding at the end
-    for (int n = 0; n < N; ++n) push(z[n], w[n], 1);
-    for (int i = 0; i < npad; ++i) push(1.0, 0.0, 1);
-    ps.n_heavy = N;
-    ps.g_light = 0;
-    ps.g_heavy = ps.ngroups;
-    return REXI_OK;
-  }
-  std::vector<int> by_gain(N);
-  std::iota(by_gain.begin(), by_gain.end(), 0);
-  std::stable_sort(by_gain.begin(), by_gain.end(), [&](int a, int b) { return gain[a] > gain[b]; });
+  for (int i = 0; i < nkeep; ++i)
+    if (gain[by_gain[i]] > tau) ++nh;
+  const int nh_pad = std::min((nh + 31) / 32 * 32, nkeep);
+  if (nh_pad == nkeep && nkeep % 32 != 0) return all_heavy();  // everything heavy, padding at the end
   std::vector<int> hv(N, 0);
   for (int i = 0; i < nh_pad; ++i) hv[by_gain[i]] = 1;
   for (int n = 0; n < N; ++n)
-    if (!hv[n]) push(z[n], w[n], 0);
+    if (keep[n] && !hv[n]) push(z[n], w[n], 0);
   for (int i = 0; i < npad; ++i) push(1.0, 0.0, 0);
   for (int n = 0; n < N; ++n)
     if (hv[n]) push(z[n], w[n], 1);
@@ -121,7 +151,7 @@ int make_poleset(PoleSet& ps, int precision, int T, int N, double dt, double X, 
 }
 
 int make_poleset_from_contour(PoleSet& ps, int precision, int T, int N, double dt, double X, double p0,
-                              double Xc, double heavy_tau) {
+                              double Xc, double heavy_tau, double prune_tau) {
   std::vector<double> zz(2 * N), ww(2 * N);
   int rc = rexi_coeffs(N, p0, Xc, 0, zz.data(), ww.data());
   if (rc) return rc;
@@ -130,7 +160,7 @@ int make_poleset_from_contour(PoleSet& ps, int precision, int T, int N, double d
     z[n] = cplx(zz[2 * n], zz[2 * n + 1]);
     w[n] = cplx(ww[2 * n], ww[2 * n + 1]);
   }
-  return make_poleset(ps, precision, T, N, dt, X, z.data(), w.data(), heavy_tau);
+  return make_poleset(ps, precision, T, N, dt, X, z.data(), w.data(), heavy_tau, prune_tau);
 }
 
 int ranges_used(int G, int Q) {
@@ -578,9 +608,9 @@ extern "C" int rexi_plan_create(const rexi_plan_desc* desc, rexi_plan** out) {
       z[n] = cplx(d.z[2 * n], d.z[2 * n + 1]);
       w[n] = cplx(d.w[2 * n], d.w[2 * n + 1]);
     }
-    rc = make_poleset(p->ps, d.precision, d.T, d.N, d.dt, X, z.data(), w.data(), d.heavy_tau);
+    rc = make_poleset(p->ps, d.precision, d.T, d.N, d.dt, X, z.data(), w.data(), d.heavy_tau, d.prune_tau);
   } else {
-    rc = make_poleset_from_contour(p->ps, d.precision, d.T, d.N, d.dt, X, d.p0, d.Xc, d.heavy_tau);
+    rc = make_poleset_from_contour(p->ps, d.precision, d.T, d.N, d.dt, X, d.p0, d.Xc, d.heavy_tau, d.prune_tau);
   }
   if (rc) return bail(rc);
   rc = engine_init(p->e, d.precision, d.T, d.omega, d.radius, d.phibar, (cudaStream_t)d.stream, p->ps.Npad, 0,
@@ -696,6 +726,8 @@ extern "C" int rexi_plan_get_info(const rexi_plan* p, rexi_plan_info* info) {
   info->s0_re = p->ps.S0.real();
   info->s0_im = p->ps.S0.imag();
   info->X = p->ps.X;
+  info->n_pruned = p->ps.n_pruned;
+  info->pruned_gain = p->ps.pruned_gain;
   return REXI_OK;
 }
 
@@ -714,6 +746,17 @@ extern "C" int rexi_plan_get_poles(const rexi_plan* p, double* z, double* w, int
     }
     if (heavy) heavy[k] = p->ps.heavy[i];
     ++k;
+  }
+  for (size_t i = 0; i < p->ps.zp.size() && k < p->ps.N; ++i, ++k) {  // poles left out
+    if (z) {
+      z[2 * k] = p->ps.zp[i].real();
+      z[2 * k + 1] = p->ps.zp[i].imag();
+    }
+    if (w) {
+      w[2 * k] = p->ps.wp[i].real();
+      w[2 * k + 1] = p->ps.wp[i].imag();
+    }
+    if (heavy) heavy[k] = -1;
   }
   return REXI_OK;
 }
@@ -825,7 +868,8 @@ extern "C" int rexi_ragged_set(rexi_ragged* r, int ninst, const rexi_instance* i
     }
     PoleSet ps;
     const double X = rexi_spectrum_bound(q.T, q.dt, r->d.omega, r->d.radius, r->d.phibar);
-    int rc = make_poleset_from_contour(ps, r->d.precision, q.T, q.N, q.dt, X, q.p0, q.Xc, r->d.heavy_tau);
+    int rc = make_poleset_from_contour(ps, r->d.precision, q.T, q.N, q.dt, X, q.p0, q.Xc, r->d.heavy_tau,
+                                       r->d.prune_tau);
     if (rc) return rc;
     if (r->e.pole_used + ps.Npad > r->e.pole_cap) return REXI_EBUSY;
     rc = engine_upload_poles(r->e, ps);

@@ -44,7 +44,7 @@ class PlanDesc(ctypes.Structure):
                 ("phibar", ctypes.c_double), ("p0", ctypes.c_double), ("Xc", ctypes.c_double),
                 ("z", _dp), ("w", _dp), ("precision", ctypes.c_int),
                 ("heavy_tau", ctypes.c_double), ("max_batch", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("prune_tau", ctypes.c_double)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -53,7 +53,8 @@ class PlanInfo(ctypes.Structure):
                 ("n_groups", ctypes.c_int), ("n_tiles", ctypes.c_int), ("q_slots", ctypes.c_int),
                 ("grid_fp64", ctypes.c_int), ("grid_light", ctypes.c_int),
                 ("grid_heavy", ctypes.c_int), ("workspace_bytes", ctypes.c_longlong),
-                ("s0_re", ctypes.c_double), ("s0_im", ctypes.c_double), ("X", ctypes.c_double)]
+                ("s0_re", ctypes.c_double), ("s0_im", ctypes.c_double), ("X", ctypes.c_double),
+                ("n_pruned", ctypes.c_int), ("pruned_gain", ctypes.c_double)]
 
 
 _lib.rexi_last_error.restype = ctypes.c_char_p
@@ -94,7 +95,7 @@ class RaggedDesc(ctypes.Structure):
                 ("max_elems", ctypes.c_longlong), ("omega", ctypes.c_double),
                 ("radius", ctypes.c_double), ("phibar", ctypes.c_double),
                 ("precision", ctypes.c_int), ("heavy_tau", ctypes.c_double),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("prune_tau", ctypes.c_double)]
 
 
 class Instance(ctypes.Structure):
@@ -119,12 +120,13 @@ class RaggedPlan:
     """One REXI launch over states of different truncation, time step and pole count."""
 
     def __init__(self, Tmax, max_inst, max_poles, max_elems, omega, radius, phibar,
-                 precision="mixed", heavy_tau=-1.0, stream=None):
+                 precision="mixed", heavy_tau=-1.0, prune_tau=0.0, stream=None):
         d = RaggedDesc()
         d.Tmax, d.max_inst, d.max_poles, d.max_elems = int(Tmax), int(max_inst), int(max_poles), int(max_elems)
         d.omega, d.radius, d.phibar = float(omega), float(radius), float(phibar)
         d.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
         d.heavy_tau = float(heavy_tau)
+        d.prune_tau = float(prune_tau)
         d.stream = ctypes.c_void_p(_stream_handle(stream))
         h = ctypes.c_void_p()
         _check(_lib.rexi_ragged_create(ctypes.byref(d), ctypes.byref(h)))
@@ -252,7 +254,7 @@ class Plan:
     """REXI plan: U1 = sum_n w_n (z_n - dt L)^-1 U0 for batches of spectral states."""
 
     def __init__(self, T, N, dt, omega, radius, phibar, p0=None, Xc=None, z=None, w=None,
-                 precision="fp64", heavy_tau=-1.0, max_batch=1, stream=None):
+                 precision="fp64", heavy_tau=-1.0, max_batch=1, stream=None, prune_tau=0.0):
         d = PlanDesc()
         d.T, d.N, d.dt = int(T), int(N), float(dt)
         d.omega, d.radius, d.phibar = float(omega), float(radius), float(phibar)
@@ -269,6 +271,7 @@ class Plan:
         d.heavy_tau = float(heavy_tau)
         d.max_batch = int(max_batch)
         d.stream = ctypes.c_void_p(_stream_handle(stream))
+        d.prune_tau = float(prune_tau)
         h = ctypes.c_void_p()
         _check(_lib.rexi_plan_create(ctypes.byref(d), ctypes.byref(h)))
         self._h = h
@@ -312,12 +315,14 @@ class Plan:
         return {k: getattr(i, k) for k, _ in PlanInfo._fields_}
 
     def poles(self):
+        """(z, w, cls): the solved poles in internal order, then the pruned ones; cls is 1 for
+        heavy, 0 for light and -1 for pruned poles."""
         z = np.empty(2 * self.N)
         w = np.empty(2 * self.N)
         hv = np.empty(self.N, dtype=np.int32)
         _check(_lib.rexi_plan_get_poles(self._h, z.ctypes.data_as(_dp), w.ctypes.data_as(_dp),
                                         hv.ctypes.data_as(_ip)))
-        return z.view(np.complex128), w.view(np.complex128), hv.astype(bool)
+        return z.view(np.complex128), w.view(np.complex128), hv
 
     def set_profiling(self, enable=True):
         _check(_lib.rexi_plan_set_profiling(self._h, 1 if enable else 0))

@@ -145,6 +145,21 @@ def test_largest_sizes_sampled(env, prec, T, N, dt, ms):
     assert np.all(err < tol), (err, tol, info)
 
 
+@pytest.mark.parametrize("T,N,dt", [(63, 256, 3600.0), (255, 512, 3600.0)])
+def test_fp64_pruned_matches_full_oracle(env, T, N, dt):
+    """An FP64 plan that leaves out poles of summed gain <= 2^-70 stays within the FP64
+    tolerance of the oracle's sum over all N poles."""
+    p0, Xc, X = contour(T, dt, N)
+    U0 = syn.gaussian_state(T, 400 + T)
+    z, w = oc.rexi_coefficients(N, p0, Xc)
+    ms = [0, 1, T // 2, T]
+    ref = orx.rexi_step(U0, T, dt, OM, A, PB, z, w, m_list=ms)
+    out, info = run_plan(env, T, N, dt, U0, "fp64", p0, Xc, prune_tau=2.0 ** -70)
+    assert info["n_pruned"] > 0 and info["pruned_gain"] <= 2.0 ** -70
+    err = masked_rel(out, ref, T, ms)
+    assert np.all(err < fp64_tol(z, w, X)), (err, info)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_batch_matches_single_and_is_deterministic(env, prec):
     torch, rexi = env
@@ -221,16 +236,34 @@ def test_errors(env):
     plan.close()
 
 
-def test_mixed_heavy_classification(env):
+def test_mixed_heavy_classification_and_pruning(env):
+    """Heavy poles have the largest gains; pruned poles the smallest, their summed gain within
+    the default 2^-70; conjugate pairs are kept or pruned together."""
     torch, rexi = env
     T, N, dt = 255, 512, 3600.0
     p0, Xc, X = contour(T, dt, N)
     plan = rexi.Plan(T, N, dt, OM, A, PB, p0=p0, Xc=Xc, precision="mixed")
-    z, w, heavy = plan.poles()
+    z, w, cls = plan.poles()
     info = plan.info()
     assert info["n_heavy"] % 32 == 0 and 0 < info["n_heavy"] < N
     yi = np.clip(z.imag, -X, X)
     gain = np.abs(w) / np.abs(z - 1j * yi)
-    assert gain[heavy].min() >= gain[~heavy].max()
+    heavy, light, pruned = cls == 1, cls == 0, cls == -1
+    assert gain[heavy].min() >= gain[light].max()
     assert np.sum(gain > 1e-3) <= info["n_heavy"]
+    assert info["n_pruned"] == pruned.sum() > 0
+    assert gain[light].min() >= gain[pruned].max()
+    assert gain[pruned].sum() <= 2.0 ** -70 and abs(gain[pruned].sum() - info["pruned_gain"]) <= 1e-30
+    assert np.array_equal(np.sort_complex(z[pruned]), np.sort_complex(np.conj(z[pruned])))
+    # the oracle's sum over the solved poles alone differs from the full sum by <= the bound
+    U = syn.gaussian_state(T, 3)
+    zo, wo = oc.rexi_coefficients(N, p0, Xc)
+    ref_all = orx.rexi_step(U, T, dt, OM, A, PB, zo, wo, m_list=[0, 200])
+    keep = ~pruned
+    ref_kept = orx.rexi_step(U, T, dt, OM, A, PB, z[keep], w[keep], m_list=[0, 200])
+    # (both FP64 sums, in different pole orders: rounding of order amp * 2^-53)
+    assert np.max(masked_rel(ref_kept, ref_all, T, [0, 200])) < fp64_tol(zo, wo, X)
     plan.close()
+    fp = rexi.Plan(T, N, dt, OM, A, PB, p0=p0, Xc=Xc, precision="fp64")
+    assert fp.info()["n_pruned"] == 0          # FP64 plans solve every pole by default
+    fp.close()
