@@ -81,26 +81,25 @@ __host__ __device__ inline float4 split4(double a, double b) {
 }
 __device__ __forceinline__ dfc dfc_of(float4 v) { return dfc{df{v.x, v.y}, df{v.z, v.w}}; }
 
-// (ah, al) += (wh + wl) * (xh + xl), with the rounding error of wh * xh recovered by FMA and that
-// of the sum by two-sum.  xl is the refinement correction of xh; wl * xl is dropped, which like
-// the FP32 rounding of wh * xl is 2^-24 |xl / xh| of the product, far below the error the one
-// refinement step leaves in xh + xl.  al is left unnormalised over the 16 terms.
-__device__ __forceinline__ void df_acc(float& ah, float& al, float wh, float wl, float xh, float xl) {
-  const float p = wh * xh;
-  float e = fmaf(wh, xh, -p);
-  e = fmaf(wh, xl, fmaf(wl, xh, e));
-  const float s = ah + p;
-  const float bb = s - ah;
-  al += ((ah - (s - bb)) + (p - bb)) + e;
-  ah = s;
+// ---- packed (FP32x2) double-float accumulation ------------------------------------------
+// Blackwell issues two FP32 operations per thread with one FADD2 / FMUL2 / FFMA2 instruction;
+// each component is rounded exactly as by the scalar instruction.
+__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
+// (AH, AL) += W * X per component, W = Wh + Wl in double-float, X in FP32: the product's rounding
+// error is recovered by FMA and the sum's by two-sum; AL is left unnormalised.
+__device__ __forceinline__ void df2_acc(float2& AH, float2& AL, float2 Wh, float2 Wl, float2 X) {
+  const float2 P = __fmul2_rn(Wh, X);
+  float2 E = __ffma2_rn(Wh, X, f2neg(P));
+  E = __ffma2_rn(Wl, X, E);
+  const float2 S = __fadd2_rn(AH, P);
+  const float2 BB = __fadd2_rn(S, f2neg(AH));
+  const float2 err = __fadd2_rn(__fadd2_rn(AH, f2neg(__fadd2_rn(S, f2neg(BB)))), __fadd2_rn(P, f2neg(BB)));
+  AL = __fadd2_rn(AL, __fadd2_rn(err, E));
+  AH = S;
 }
-// complex (acc.re, acc.im) += w * v; w = (re.hi, re.lo, im.hi, im.lo), v likewise
-__device__ __forceinline__ void dfc_acc(float4& acc, const float4 w, const float4 v) {
-  df_acc(acc.x, acc.y, w.x, w.y, v.x, v.y);
-  df_acc(acc.x, acc.y, -w.z, -w.w, v.z, v.w);
-  df_acc(acc.z, acc.w, w.x, w.y, v.z, v.w);
-  df_acc(acc.z, acc.w, w.z, w.w, v.x, v.y);
-}
+// Weight in the packed shared-memory layout (re.hi, im.hi, re.lo, im.lo) from a double-float
+// complex (re.hi, re.lo, im.hi, im.lo).
+__device__ __forceinline__ float4 w_packed(float4 w) { return make_float4(w.x, w.z, w.y, w.w); }
 
 // per-(m,n) table in double-float: (dt w, cm), (cp, q) as (hi, lo) pairs
 struct TabDF {
@@ -406,10 +405,28 @@ __host__ __device__ inline size_t heavy_scratch_f2_per_warp(int kmax) {
   return (size_t)heavy_nseg(kmax) * 32 * 2 + (size_t)kmax * 32 * 2;
 }
 
+// sum over 16 poles of w_p x_p in double-float (w in the packed layout, x in FP32), returned
+// as (re.hi, re.lo, im.hi, im.lo): two packed accumulators, sum_p (w.re x.re, w.im x.re) and
+// sum_p (w.re x.im, w.im x.im), combined once: re = first.re - second.im, im = second.re + first.im
+__device__ __forceinline__ float4 heavy_dfsum16(const float2* x, const float4* w) {
+  const float2 z2 = make_float2(0.f, 0.f);
+  float2 a1h = z2, a1l = z2, a2h = z2, a2l = z2;
+#pragma unroll 4
+  for (int p = 0; p < 16; ++p) {
+    const float2 v = x[p];
+    const float4 wp = w[p];
+    df2_acc(a1h, a1l, make_float2(wp.x, wp.y), make_float2(wp.z, wp.w), make_float2(v.x, v.x));
+    df2_acc(a2h, a2l, make_float2(wp.x, wp.y), make_float2(wp.z, wp.w), make_float2(v.y, v.y));
+  }
+  const df re = df_add(df{a1h.x, a1l.x}, df{-a2h.y, -a2l.y}), im = df_add(df{a2h.x, a2l.x}, df{a1h.y, a1l.y});
+  return make_float4(re.hi, re.lo, im.hi, im.lo);
+}
+
 // Pole sums of one transposition block: lane (r, h) sums row kb + r over the 16 poles of half
 // h; dfsum: double-float products with the double-float weights (the solution x), else FP32
-// (the small correction); the halves are combined in FP64 by a shuffle and added into the
-// tile's FP64 partial slots (written when first = true).
+// (the small correction); the halves are combined by a shuffle and added into the tile's
+// double-float partial slots (written when first = true).  Weights are in the packed layout
+// (re.hi, im.hi, re.lo, im.lo).
 __device__ __forceinline__ void heavy_block_sum(const float2* tile, const float4* s_w, const float4* s_wz, int kb,
                                                 int K, int c, int lane, bool dfsum, bool first, double2* part,
                                                 int off, int nlm) {
@@ -420,23 +437,18 @@ __device__ __forceinline__ void heavy_block_sum(const float2* tile, const float4
   float4 f1 = make_float4(0.f, 0.f, 0.f, 0.f), f2 = f1;  // double-float (re.hi, re.lo, im.hi, im.lo)
   if (valid) {
     if (dfsum) {
-#pragma unroll 4
-      for (int p = 16 * h; p < 16 * h + 16; ++p) {
-        const float2 v = tile[r * LTROW + p];
-        const float4 vv = make_float4(v.x, 0.f, v.y, 0.f);
-        dfc_acc(f1, s_w[p], vv);
-        if (isD) dfc_acc(f2, s_wz[p], vv);
-      }
+      f1 = heavy_dfsum16(tile + r * LTROW + 16 * h, s_w + 16 * h);
+      if (isD) f2 = heavy_dfsum16(tile + r * LTROW + 16 * h, s_wz + 16 * h);
     } else {
       float2 g1 = make_float2(0.f, 0.f), g2 = g1;
 #pragma unroll 4
       for (int p = 16 * h; p < 16 * h + 16; ++p) {
         const float2 v = tile[r * LTROW + p];
         const float4 w = s_w[p];
-        g1 = cfmaf(make_float2(w.x, w.z), v, g1);
+        g1 = cfmaf(make_float2(w.x, w.y), v, g1);
         if (isD) {
           const float4 wz = s_wz[p];
-          g2 = cfmaf(make_float2(wz.x, wz.z), v, g2);
+          g2 = cfmaf(make_float2(wz.x, wz.y), v, g2);
         }
       }
       f1 = make_float4(g1.x, 0.f, g1.y, 0.f);
@@ -511,8 +523,8 @@ k_rexi_heavy(MixedArgs a) {
       const PoleF pf = a.p32[pidx];
       const PoleDF pq = a.pdf[pidx];
       __syncwarp();
-      s_w[lane] = pq.w;
-      s_wz[lane] = pq.wz;
+      s_w[lane] = w_packed(pq.w);
+      s_wz[lane] = w_packed(pq.wz);
       // ---- A: FP32 forward sweep, checkpoint (ct, y) after every full segment ---------------
       {
         float2 ct = make_float2(0.f, 0.f), y = make_float2(0.f, 0.f);
