@@ -397,6 +397,12 @@ __device__ __forceinline__ float2 heavy_fwd(const MixedArgs& a, const PoleF& pf,
 
 constexpr int HSEG = 8;    // heavy: checkpoint interval (segments recomputed into shared memory)
 constexpr int HBLK = 16;   // heavy: rows per transposition block of the pole sums
+static_assert((HSEG & (HSEG - 1)) == 0 && (HBLK & (HBLK - 1)) == 0, "powers of two: indices use masks");
+// element index k >= 0 within its segment / block, and its segment (masks and shifts instead of
+// the signed division of int)
+__device__ __forceinline__ int hseg_pos(int k) { return k & (HSEG - 1); }
+__device__ __forceinline__ int hseg_of(int k) { return (int)((unsigned)k / HSEG); }
+__device__ __forceinline__ int hblk_pos(int k) { return k & (HBLK - 1); }
 
 // Heavy per-warp scratch in float2 units: checkpoints [ceil(kmax / HSEG)][32] float4, then the
 // bottom-up elimination of the correction g[kmax][32], h[kmax][32].
@@ -531,8 +537,8 @@ k_rexi_heavy(MixedArgs a) {
 #pragma unroll 1
         for (int k = 0; k < K; ++k) {
           heavy_fwd(a, pf, rb, off, toff, k, c, ct, y);
-          if ((k % HSEG) == HSEG - 1 && k + 1 < K)
-            ck[(size_t)(k / HSEG) * 32 + lane] = make_float4(ct.x, ct.y, y.x, y.y);
+          if (hseg_pos(k) == HSEG - 1 && k + 1 < K)
+            ck[(size_t)hseg_of(k) * 32 + lane] = make_float4(ct.x, ct.y, y.x, y.y);
         }
       }
       // ---- B: downward; e = -1 only finalises element 0 ----------------------------------
@@ -542,9 +548,9 @@ k_rexi_heavy(MixedArgs a) {
       for (int e = K - 1; e >= -1; --e) {
         float2 x0 = make_float2(0.f, 0.f);
         if (e >= 0) {
-          const int i = e % HSEG;
+          const int i = hseg_pos(e);
           if (e == K - 1 || i == HSEG - 1) {  // entering a segment from above: recompute it
-            const int s = e / HSEG;
+            const int s = hseg_of(e);
             float2 cs = make_float2(0.f, 0.f), ys = make_float2(0.f, 0.f);
             if (s > 0) {
               const float4 st = ck[(size_t)(s - 1) * 32 + lane];
@@ -554,7 +560,7 @@ k_rexi_heavy(MixedArgs a) {
 #pragma unroll 1
             for (int k = s * HSEG; k <= e; ++k) {
               const float2 inv = heavy_fwd(a, pf, rb, off, toff, k, c, cs, ys);
-              s_seg[(k % HSEG) * 32 + lane] = make_float4(inv.x, inv.y, ys.x, ys.y);
+              s_seg[hseg_pos(k) * 32 + lane] = make_float4(inv.x, inv.y, ys.x, ys.y);
             }
           }
           const float4 sv = s_seg[i * 32 + lane];
@@ -562,7 +568,7 @@ k_rexi_heavy(MixedArgs a) {
           const float up = ((e & 1) == c) ? tb.z : -tb.z;
           const float2 cc = make_float2(up * sv.x, up * sv.y);
           x0 = make_float2(sv.z - fmaf(cc.x, x1.x, -cc.y * x1.y), sv.w - fmaf(cc.x, x1.y, cc.y * x1.x));
-          s_tile[(e % HBLK) * LTROW + lane] = x0;
+          s_tile[hblk_pos(e) * LTROW + lane] = x0;
         }
         if (e + 1 < K) {  // element k = e + 1: residual with x_{k-1} = x0, x_k = x1, x_{k+1} = x2
           const int k = e + 1;
@@ -582,7 +588,7 @@ k_rexi_heavy(MixedArgs a) {
           Hs[(size_t)k * 32 + lane] = hU;
         }
         if (e >= 0) {
-          if ((e % HBLK) == 0) {
+          if (hblk_pos(e) == 0) {
             __syncwarp();
             heavy_block_sum(s_tile, s_w, s_wz, e, K, c, lane, true, gi == 0, part, off, nlm);
             __syncwarp();
@@ -598,10 +604,10 @@ k_rexi_heavy(MixedArgs a) {
         const float2 g = Gs[(size_t)k * 32 + lane], h = Hs[(size_t)k * 32 + lane];
         const float2 dx = make_float2(h.x - fmaf(g.x, dxm.x, -g.y * dxm.y), h.y - fmaf(g.x, dxm.y, g.y * dxm.x));
         dxm = dx;
-        s_tile[(k % HBLK) * LTROW + lane] = dx;
-        if ((k % HBLK) == HBLK - 1 || k == K - 1) {
+        s_tile[hblk_pos(k) * LTROW + lane] = dx;
+        if (hblk_pos(k) == HBLK - 1 || k == K - 1) {
           __syncwarp();
-          heavy_block_sum(s_tile, s_w, s_wz, k - (k % HBLK), K, c, lane, false, false, part, off, nlm);
+          heavy_block_sum(s_tile, s_w, s_wz, k - hblk_pos(k), K, c, lane, false, false, part, off, nlm);
           __syncwarp();
         }
       }
