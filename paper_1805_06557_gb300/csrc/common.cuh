@@ -81,9 +81,10 @@ struct PoleF {
 };
 
 // One unit of work: instance, zonal order m, parity chain (2 = both chains, light tiles), a range of 32-pole groups of the
-// instance's pole set, and the slot of the partial sums it owns.  Sorted by decreasing cost.
+// instance's pole set, and the slot of the partial sums it owns.  Sorted by decreasing cost.  Heavy tiles may carry a
+// second instance inst2 of the same truncation and pole set (-1: none), solved with the same pivots.
 struct Tile {
-  int m, chain, g0, ng, q, heavy, cost, inst;
+  int m, chain, g0, ng, q, heavy, cost, inst, inst2;
 };
 
 // One state of a launch.  Offsets are relative to the launch's base pointers.

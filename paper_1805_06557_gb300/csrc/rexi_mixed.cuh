@@ -332,38 +332,49 @@ k_rexi_light(MixedArgs a) {
 }
 
 // ---- heavy kernel ------------------------------------------------------------------
-// residual of chain row k in double-float:  r_k - d_k x_k - lo_k x_{k-1} - up_k x_{k+1}
-__device__ __forceinline__ float2 heavy_residual(const MixedArgs& a, const PoleDF& pq,
-                                                 const RhsDF* rb, int off, int toff, int k, int K,
-                                                 int c, float2 xm, float2 x0, float2 xp) {
+// Row k of a heavy chain in double-float: the diagonal d_k and the off-diagonals lo_k, up_k.
+// They depend on the pole and the matrix only, so a tile that carries two states forms them once.
+struct HeavyRow {
+  dfc d;
+  df lo, up;
+};
+__device__ __forceinline__ HeavyRow heavy_row(const MixedArgs& a, const PoleDF& pq, int toff, int k, bool isZ) {
   const TabDF tb = a.tabdf[toff + k];
-  const bool isZ = ((k & 1) == c);
   const df hw{tb.a.x, tb.a.y}, cm{tb.a.z, tb.a.w}, cp{tb.b.x, tb.b.y}, q{tb.b.z, tb.b.w};
-  const RhsDF rr = rb[off + k];
   const dfc z = dfc_of(pq.z);
-  dfc d, r;
+  HeavyRow R;
   if (isZ) {
-    d = dfc{z.re, df_add(z.im, df_neg(hw))};
-    r = dfc_of(rr.bz);
+    R.d = dfc{z.re, df_add(z.im, df_neg(hw))};
   } else {
     const dfc gz = dfc_of(pq.gz);
-    d = dfc{df_add(z.re, df_mul(q, gz.re)), df_add(df_add(z.im, df_neg(hw)), df_mul(q, gz.im))};
+    R.d = dfc{df_add(z.re, df_mul(q, gz.re)), df_add(df_add(z.im, df_neg(hw)), df_mul(q, gz.im))};
+  }
+  R.lo = isZ ? cm : df_neg(cm);
+  R.up = isZ ? cp : df_neg(cp);
+  return R;
+}
+
+// residual of one state's chain row k in double-float:  r_k - d_k x_k - lo_k x_{k-1} - up_k x_{k+1}
+__device__ __forceinline__ float2 heavy_residual(const HeavyRow& R, const PoleDF& pq, const RhsDF& rr, bool isZ,
+                                                 bool has_m, bool has_p, float2 xm, float2 x0, float2 xp) {
+  dfc r;
+  if (isZ) {
+    r = dfc_of(rr.bz);
+  } else {
     const dfc t = dfc_mul(dfc_of(pq.iz), dfc_of(rr.qbp));
     const dfc bd = dfc_of(rr.bd);
     r = dfc{df_add(bd.re, t.re), df_add(bd.im, t.im)};
   }
-  const df lo = isZ ? cm : df_neg(cm);
-  const df up = isZ ? cp : df_neg(cp);
   // acc = r - d x
-  df re = df_add(r.re, df_neg(df_add(df_mulf(d.re, x0.x), df_neg(df_mulf(d.im, x0.y)))));
-  df im = df_add(r.im, df_neg(df_add(df_mulf(d.re, x0.y), df_mulf(d.im, x0.x))));
-  if (k > 0) {
-    re = df_add(re, df_neg(df_mulf(lo, xm.x)));
-    im = df_add(im, df_neg(df_mulf(lo, xm.y)));
+  df re = df_add(r.re, df_neg(df_add(df_mulf(R.d.re, x0.x), df_neg(df_mulf(R.d.im, x0.y)))));
+  df im = df_add(r.im, df_neg(df_add(df_mulf(R.d.re, x0.y), df_mulf(R.d.im, x0.x))));
+  if (has_m) {
+    re = df_add(re, df_neg(df_mulf(R.lo, xm.x)));
+    im = df_add(im, df_neg(df_mulf(R.lo, xm.y)));
   }
-  if (k + 1 < K) {
-    re = df_add(re, df_neg(df_mulf(up, xp.x)));
-    im = df_add(im, df_neg(df_mulf(up, xp.y)));
+  if (has_p) {
+    re = df_add(re, df_neg(df_mulf(R.up, xp.x)));
+    im = df_add(im, df_neg(df_mulf(R.up, xp.y)));
   }
   return make_float2(re.hi + re.lo, im.hi + im.lo);
 }
@@ -382,33 +393,26 @@ __device__ __forceinline__ float2 heavy_pivot(const float4 tb, const PoleF& pf, 
   return inv;
 }
 
-// One forward step of the FP32 chain solve at element k: advances (ct, y), returns the pivot.
-__device__ __forceinline__ float2 heavy_fwd(const MixedArgs& a, const PoleF& pf, const Rhs32* rb, int off,
-                                            int toff, int k, int c, float2& ct, float2& y) {
-  const float4 tb = __ldg(a.tab32 + toff + k);
-  const Rhs32 rr = rb[off + k];
-  const bool isZ = ((k & 1) == c);
-  const float lo = isZ ? tb.y : -tb.y;
+// One state's forward value at element k: y_k = (r_k - lo_k y_{k-1}) / pivot_k.
+__device__ __forceinline__ float2 heavy_y(const PoleF& pf, const Rhs32& rr, bool isZ, float lo, float2 inv, float2 y) {
   const float2 r = isZ ? rr.bz : cfmaf(pf.iz, rr.qbp, rr.bd);
-  const float2 inv = heavy_pivot(tb, pf, isZ, ct);
-  y = cmulf(make_float2(fmaf(-lo, y.x, r.x), fmaf(-lo, y.y, r.y)), inv);
-  return inv;
+  return cmulf(make_float2(fmaf(-lo, y.x, r.x), fmaf(-lo, y.y, r.y)), inv);
 }
 
-constexpr int HSEG = 8;    // heavy: checkpoint interval (segments recomputed into shared memory)
-constexpr int HBLK = 16;   // heavy: rows per transposition block of the pole sums
-static_assert((HSEG & (HSEG - 1)) == 0 && (HBLK & (HBLK - 1)) == 0, "powers of two: indices use masks");
-// element index k >= 0 within its segment / block, and its segment (masks and shifts instead of
-// the signed division of int)
-__device__ __forceinline__ int hseg_pos(int k) { return k & (HSEG - 1); }
-__device__ __forceinline__ int hseg_of(int k) { return (int)((unsigned)k / HSEG); }
+constexpr int HBLK = 16;     // heavy: rows per transposition block of the pole sums
+constexpr int HSEG_MIN = 4;  // heavy: shortest checkpoint interval (sizes the checkpoint scratch)
+// checkpoint interval of a heavy tile carrying G states (segments recomputed into shared memory)
+template <int G>
+__host__ __device__ constexpr int heavy_seg() { return G == 2 ? 4 : 8; }
+static_assert((HBLK & (HBLK - 1)) == 0, "power of two: block positions use masks");
 __device__ __forceinline__ int hblk_pos(int k) { return k & (HBLK - 1); }
 
-// Heavy per-warp scratch in float2 units: checkpoints [ceil(kmax / HSEG)][32] float4, then the
-// bottom-up elimination of the correction g[kmax][32], h[kmax][32].
-__host__ __device__ inline int heavy_nseg(int kmax) { return (kmax + HSEG - 1) / HSEG; }
+// Heavy per-warp scratch in float2 units, sized for the shortest interval and two states:
+// forward checkpoints [ceil(kmax / HSEG_MIN)][32][3] (ct, y of each state), the correction's
+// factor g[kmax][32] (shared by the states of a tile), and h[2][kmax][32].
+__host__ __device__ inline int heavy_nseg(int kmax) { return (kmax + HSEG_MIN - 1) / HSEG_MIN; }
 __host__ __device__ inline size_t heavy_scratch_f2_per_warp(int kmax) {
-  return (size_t)heavy_nseg(kmax) * 32 * 2 + (size_t)kmax * 32 * 2;
+  return (size_t)heavy_nseg(kmax) * 32 * 3 + (size_t)kmax * 32 * 3;
 }
 
 // sum over 16 poles of w_p x_p in double-float (w in the packed layout, x in FP32), returned
@@ -486,46 +490,60 @@ __device__ __forceinline__ void heavy_block_sum(const float2* tile, const float4
 }
 
 // Heavy poles: FP32 LU solve with checkpoints (pass A, upward); pass B (downward) recomputes
-// each 8-element segment into a per-warp shared buffer, back-substitutes x, forms the residual
-// r - A x of element k + 1 in double-float once x_k is known, and eliminates the correction
-// system bottom-up (UL form of Thomas: p_k = d_k - up_k g_{k+1}, g_k = lo_k / p_k,
+// each segment into a per-warp shared buffer, back-substitutes x, forms the residual r - A x of
+// element k + 1 in double-float once x_k is known, and eliminates the correction system
+// bottom-up (UL form of Thomas: p_k = d_k - up_k g_{k+1}, g_k = lo_k / p_k,
 // h_k = (res_k - up_k h_{k+1}) / p_k), storing g and h; pass C (upward) completes the
 // correction dx_k = h_k - g_k dx_{k-1}.  Pole sums: x in double-float in pass B, dx in FP32
-// in pass C (|dx| ~ 1e-6 |x|).  All loops stay rolled so that the residual's code exists once.
-static __global__ void __launch_bounds__(MIX_WARPS * 32, 6)
-k_rexi_heavy(MixedArgs a) {
+// in pass C (|dx| ~ 1e-6 |x|).  A tile carries G states of the same truncation and pole set
+// (G = 2 pairs the states of a batch): the pivots, the correction's factor g, the double-float
+// diagonal and every table load are formed once for both; right-hand sides, x, residuals, h
+// and the pole sums are per state.  All loops stay rolled so that the residual's code exists
+// once per state.
+template <int G>
+static __global__ void __launch_bounds__(MIX_WARPS * 32, G == 2 ? 4 : 6)
+k_rexi_heavy(MixedArgs a, int t0, int nt) {
+  constexpr int SEG = heavy_seg<G>();
+  constexpr int SW = 1 + G;  // float2 per lane and element in the segment buffer: inv, y of each state
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  // per warp: transposition tile [HBLK][LTROW] float2, the double-float weights w, w/z, and
-  // the recomputed segment [HSEG][32] float4 (inverse pivot, forward value)
-  float2* s_tile = reinterpret_cast<float2*>(smem_raw) + wib * (HBLK * LTROW);
-  float4* s_w = reinterpret_cast<float4*>(smem_raw + (size_t)MIX_WARPS * HBLK * LTROW * sizeof(float2)) + wib * 64;
+  // per warp: transposition tiles [G][HBLK][LTROW] float2, the double-float weights w, w/z,
+  // and the recomputed segment [SEG][32][SW] float2
+  float2* s_tile = reinterpret_cast<float2*>(smem_raw) + wib * (G * HBLK * LTROW);
+  float4* s_w = reinterpret_cast<float4*>(smem_raw + (size_t)MIX_WARPS * G * HBLK * LTROW * sizeof(float2)) + wib * 64;
   float4* s_wz = s_w + 32;
-  float4* s_seg = reinterpret_cast<float4*>(smem_raw + (size_t)MIX_WARPS * HBLK * LTROW * sizeof(float2) +
-                                            (size_t)MIX_WARPS * 64 * sizeof(float4)) + wib * (HSEG * 32);
+  float2* s_seg = reinterpret_cast<float2*>(smem_raw + (size_t)MIX_WARPS * G * HBLK * LTROW * sizeof(float2) +
+                                            (size_t)MIX_WARPS * 64 * sizeof(float4)) + wib * (SEG * 32 * SW);
   const int gw = blockIdx.x * MIX_WARPS + wib;
   const int W = gridDim.x * MIX_WARPS;
   float2* hs = reinterpret_cast<float2*>(reinterpret_cast<char*>(a.scratch) +
                                          (size_t)a.warps_light * light_ckpt_f4_per_warp(a.nseg_max) * sizeof(float4)) +
                (size_t)gw * heavy_scratch_f2_per_warp(a.kmax);
-  float4* ck = reinterpret_cast<float4*>(hs);
-  float2* Gs = hs + (size_t)heavy_nseg(a.kmax) * 64;
-  float2* Hs = Gs + (size_t)a.kmax * 32;
-  const int total = a.ntiles_heavy;
+  float2* ck = hs;                                              // [nseg][32][SW]
+  float2* Gs = hs + (size_t)heavy_nseg(a.kmax) * 32 * 3;        // [kmax][32]
+  float2* Hs = Gs + (size_t)a.kmax * 32;                        // [G][kmax][32]
 
-  for (int round = 0; round * W < total; ++round) {
+  for (int round = 0; round * W < nt; ++round) {
     const int t = round * W + ((round & 1) ? (W - 1 - gw) : gw);
-    if (t >= total) continue;
-    const Tile tl = a.tiles[a.ntiles_light + t];
-    const Inst I = a.insts[tl.inst];
-    const int T = I.T, nlm = I.nlm;
+    if (t >= nt) continue;
+    const Tile tl = a.tiles[t0 + t];
+    Inst I[G];
+    I[0] = a.insts[tl.inst];
+    if (G == 2) I[G - 1] = a.insts[tl.inst2];
+    const int T = I[0].T, nlm = I[0].nlm;
     const int m = tl.m, c = tl.chain, K = T + 1 - m, off = moff(T, m), toff = moff(a.Ttab, m);
-    const Rhs32* rb = a.rhs32 + I.roff;
-    const RhsDF* rbd = a.rhsdf + I.roff;
-    double2* part = a.partial + I.poff + (size_t)tl.q * 3 * nlm;
+    const Rhs32* rb[G];
+    const RhsDF* rbd[G];
+    double2* part[G];
+#pragma unroll
+    for (int s = 0; s < G; ++s) {
+      rb[s] = a.rhs32 + I[s].roff + off;
+      rbd[s] = a.rhsdf + I[s].roff + off;
+      part[s] = a.partial + I[s].poff + (size_t)tl.q * 3 * nlm;
+    }
 
     for (int gi = 0; gi < tl.ng; ++gi) {
-      const int pidx = I.pole0 + (tl.g0 + gi) * 32 + lane;
+      const int pidx = I[0].pole0 + (tl.g0 + gi) * 32 + lane;
       const PoleF pf = a.p32[pidx];
       const PoleDF pq = a.pdf[pidx];
       __syncwarp();
@@ -533,46 +551,76 @@ k_rexi_heavy(MixedArgs a) {
       s_wz[lane] = w_packed(pq.wz);
       // ---- A: FP32 forward sweep, checkpoint (ct, y) after every full segment ---------------
       {
-        float2 ct = make_float2(0.f, 0.f), y = make_float2(0.f, 0.f);
+        float2 ct = make_float2(0.f, 0.f), y[G];
+#pragma unroll
+        for (int s = 0; s < G; ++s) y[s] = make_float2(0.f, 0.f);
 #pragma unroll 1
         for (int k = 0; k < K; ++k) {
-          heavy_fwd(a, pf, rb, off, toff, k, c, ct, y);
-          if (hseg_pos(k) == HSEG - 1 && k + 1 < K)
-            ck[(size_t)hseg_of(k) * 32 + lane] = make_float4(ct.x, ct.y, y.x, y.y);
+          const float4 tb = __ldg(a.tab32 + toff + k);
+          const bool isZ = ((k & 1) == c);
+          const float lo = isZ ? tb.y : -tb.y;
+          const float2 inv = heavy_pivot(tb, pf, isZ, ct);
+#pragma unroll
+          for (int s = 0; s < G; ++s) y[s] = heavy_y(pf, rb[s][k], isZ, lo, inv, y[s]);
+          if ((k & (SEG - 1)) == SEG - 1 && k + 1 < K) {
+            float2* cp = ck + ((size_t)(k / SEG) * 32 + lane) * SW;
+            cp[0] = ct;
+#pragma unroll
+            for (int s = 0; s < G; ++s) cp[1 + s] = y[s];
+          }
         }
       }
       // ---- B: downward; e = -1 only finalises element 0 ----------------------------------
-      float2 x1 = make_float2(0.f, 0.f), x2 = make_float2(0.f, 0.f);  // x_{e+1}, x_{e+2}
-      float2 gU = make_float2(0.f, 0.f), hU = make_float2(0.f, 0.f);  // g, h of element e + 2
+      float2 x0[G], x1[G], x2[G], hU[G];  // x_e, x_{e+1}, x_{e+2}; h of element e + 2
+#pragma unroll
+      for (int s = 0; s < G; ++s) x1[s] = x2[s] = hU[s] = make_float2(0.f, 0.f);
+      float2 gU = make_float2(0.f, 0.f);  // g of element e + 2
 #pragma unroll 1
       for (int e = K - 1; e >= -1; --e) {
-        float2 x0 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int s = 0; s < G; ++s) x0[s] = make_float2(0.f, 0.f);
         if (e >= 0) {
-          const int i = hseg_pos(e);
-          if (e == K - 1 || i == HSEG - 1) {  // entering a segment from above: recompute it
-            const int s = hseg_of(e);
-            float2 cs = make_float2(0.f, 0.f), ys = make_float2(0.f, 0.f);
-            if (s > 0) {
-              const float4 st = ck[(size_t)(s - 1) * 32 + lane];
-              cs = make_float2(st.x, st.y);
-              ys = make_float2(st.z, st.w);
+          const int i = e & (SEG - 1);
+          if (e == K - 1 || i == SEG - 1) {  // entering a segment from above: recompute it
+            const int sg = e / SEG;
+            float2 cs = make_float2(0.f, 0.f), ys[G];
+#pragma unroll
+            for (int s = 0; s < G; ++s) ys[s] = make_float2(0.f, 0.f);
+            if (sg > 0) {
+              const float2* cp = ck + ((size_t)(sg - 1) * 32 + lane) * SW;
+              cs = cp[0];
+#pragma unroll
+              for (int s = 0; s < G; ++s) ys[s] = cp[1 + s];
             }
 #pragma unroll 1
-            for (int k = s * HSEG; k <= e; ++k) {
-              const float2 inv = heavy_fwd(a, pf, rb, off, toff, k, c, cs, ys);
-              s_seg[hseg_pos(k) * 32 + lane] = make_float4(inv.x, inv.y, ys.x, ys.y);
+            for (int k = sg * SEG; k <= e; ++k) {
+              const float4 tb = __ldg(a.tab32 + toff + k);
+              const bool isZ = ((k & 1) == c);
+              const float lo = isZ ? tb.y : -tb.y;
+              const float2 inv = heavy_pivot(tb, pf, isZ, cs);
+              float2* sp = s_seg + ((k & (SEG - 1)) * 32 + lane) * SW;
+              sp[0] = inv;
+#pragma unroll
+              for (int s = 0; s < G; ++s) {
+                ys[s] = heavy_y(pf, rb[s][k], isZ, lo, inv, ys[s]);
+                sp[1 + s] = ys[s];
+              }
             }
           }
-          const float4 sv = s_seg[i * 32 + lane];
+          const float2* sp = s_seg + (i * 32 + lane) * SW;
           const float4 tb = __ldg(a.tab32 + toff + e);
           const float up = ((e & 1) == c) ? tb.z : -tb.z;
-          const float2 cc = make_float2(up * sv.x, up * sv.y);
-          x0 = make_float2(sv.z - fmaf(cc.x, x1.x, -cc.y * x1.y), sv.w - fmaf(cc.x, x1.y, cc.y * x1.x));
-          s_tile[hblk_pos(e) * LTROW + lane] = x0;
+          const float2 cc = make_float2(up * sp[0].x, up * sp[0].y);
+#pragma unroll
+          for (int s = 0; s < G; ++s) {
+            const float2 yv = sp[1 + s];
+            x0[s] = make_float2(yv.x - fmaf(cc.x, x1[s].x, -cc.y * x1[s].y),
+                                yv.y - fmaf(cc.x, x1[s].y, cc.y * x1[s].x));
+            s_tile[(s * HBLK + hblk_pos(e)) * LTROW + lane] = x0[s];
+          }
         }
         if (e + 1 < K) {  // element k = e + 1: residual with x_{k-1} = x0, x_k = x1, x_{k+1} = x2
           const int k = e + 1;
-          const float2 res = heavy_residual(a, pq, rbd, off, toff, k, K, c, x0, x1, x2);
           const float4 tb = __ldg(a.tab32 + toff + k);
           const bool isZ = ((k & 1) == c);
           const float lo = isZ ? tb.y : -tb.y;
@@ -583,31 +631,51 @@ k_rexi_heavy(MixedArgs a) {
           const float2 den = make_float2(fmaf(-up, gU.x, d.x), fmaf(-up, gU.y, d.y));
           const float2 inv = crcpf(den);
           gU = make_float2(lo * inv.x, lo * inv.y);
-          hU = cmulf(make_float2(fmaf(-up, hU.x, res.x), fmaf(-up, hU.y, res.y)), inv);
           Gs[(size_t)k * 32 + lane] = gU;
-          Hs[(size_t)k * 32 + lane] = hU;
+          const HeavyRow R = heavy_row(a, pq, toff, k, isZ);
+#pragma unroll
+          for (int s = 0; s < G; ++s) {
+            const float2 res = heavy_residual(R, pq, rbd[s][k], isZ, k > 0, k + 1 < K, x0[s], x1[s], x2[s]);
+            hU[s] = cmulf(make_float2(fmaf(-up, hU[s].x, res.x), fmaf(-up, hU[s].y, res.y)), inv);
+            Hs[((size_t)s * a.kmax + k) * 32 + lane] = hU[s];
+          }
         }
         if (e >= 0) {
           if (hblk_pos(e) == 0) {
             __syncwarp();
-            heavy_block_sum(s_tile, s_w, s_wz, e, K, c, lane, true, gi == 0, part, off, nlm);
+#pragma unroll
+            for (int s = 0; s < G; ++s)
+              heavy_block_sum(s_tile + s * HBLK * LTROW, s_w, s_wz, e, K, c, lane, true, gi == 0, part[s], off, nlm);
             __syncwarp();
           }
-          x2 = x1;
-          x1 = x0;
+#pragma unroll
+          for (int s = 0; s < G; ++s) {
+            x2[s] = x1[s];
+            x1[s] = x0[s];
+          }
         }
       }
       // ---- C: upward: dx_k = h_k - g_k dx_{k-1}, FP32 pole sums of dx ----------------------
-      float2 dxm = make_float2(0.f, 0.f);
+      float2 dxm[G];
+#pragma unroll
+      for (int s = 0; s < G; ++s) dxm[s] = make_float2(0.f, 0.f);
 #pragma unroll 1
       for (int k = 0; k < K; ++k) {
-        const float2 g = Gs[(size_t)k * 32 + lane], h = Hs[(size_t)k * 32 + lane];
-        const float2 dx = make_float2(h.x - fmaf(g.x, dxm.x, -g.y * dxm.y), h.y - fmaf(g.x, dxm.y, g.y * dxm.x));
-        dxm = dx;
-        s_tile[hblk_pos(k) * LTROW + lane] = dx;
+        const float2 g = Gs[(size_t)k * 32 + lane];
+#pragma unroll
+        for (int s = 0; s < G; ++s) {
+          const float2 h = Hs[((size_t)s * a.kmax + k) * 32 + lane];
+          const float2 dx = make_float2(h.x - fmaf(g.x, dxm[s].x, -g.y * dxm[s].y),
+                                        h.y - fmaf(g.x, dxm[s].y, g.y * dxm[s].x));
+          dxm[s] = dx;
+          s_tile[(s * HBLK + hblk_pos(k)) * LTROW + lane] = dx;
+        }
         if (hblk_pos(k) == HBLK - 1 || k == K - 1) {
           __syncwarp();
-          heavy_block_sum(s_tile, s_w, s_wz, k - hblk_pos(k), K, c, lane, false, false, part, off, nlm);
+#pragma unroll
+          for (int s = 0; s < G; ++s)
+            heavy_block_sum(s_tile + s * HBLK * LTROW, s_w, s_wz, k - hblk_pos(k), K, c, lane, false, false, part[s],
+                            off, nlm);
           __syncwarp();
         }
       }
@@ -615,9 +683,10 @@ k_rexi_heavy(MixedArgs a) {
   }
 }
 
+template <int G>
 inline size_t heavy_smem_bytes() {
-  return sizeof(float2) * MIX_WARPS * HBLK * LTROW + sizeof(float4) * MIX_WARPS * 64 +
-         sizeof(float4) * MIX_WARPS * HSEG * 32;
+  return sizeof(float2) * MIX_WARPS * G * HBLK * LTROW + sizeof(float4) * MIX_WARPS * 64 +
+         sizeof(float2) * MIX_WARPS * heavy_seg<G>() * 32 * (1 + G);
 }
 
 }  // namespace rexi

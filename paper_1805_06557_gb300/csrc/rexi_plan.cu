@@ -189,7 +189,7 @@ struct Engine {
   size_t rhs_cap = 0;  // elements
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
-  int grid_fp64 = 0, grid_light = 0, grid_heavy = 0;
+  int grid_fp64 = 0, grid_light = 0, grid_heavy = 0, grid_heavy2 = 0;  // heavy: single-state and paired tiles
   int max_q = 0;  // cap on pole ranges per class and instance (0: none)
   long long workspace = 0;
   // profiling
@@ -209,7 +209,7 @@ struct LaunchSet {
   Inst* insts = nullptr;
   Tile* tiles = nullptr;
   long long* ecum = nullptr;
-  int ninst = 0, ntiles = 0, ntiles_light = 0;
+  int ninst = 0, ntiles = 0, ntiles_light = 0, ntiles_heavy2 = 0;
   long long total = 0, partial_elems = 0;
 };
 
@@ -292,18 +292,23 @@ int engine_init(Engine& e, int precision, int Ttab, double omega, double radius,
       return cuda_fail(ce, "cudaMemcpy(tables)");
     if ((rc = dev_alloc(&e.p32, sizeof(PoleF) * pole_cap, &ws))) return rc;
     if ((rc = dev_alloc(&e.pdf, sizeof(PoleDF) * pole_cap, &ws))) return rc;
-    const size_t hsm = heavy_smem_bytes();
-    if ((ce = cudaFuncSetAttribute(k_rexi_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm)))
+    const size_t hsm = heavy_smem_bytes<1>(), hsm2 = heavy_smem_bytes<2>();
+    if ((ce = cudaFuncSetAttribute(k_rexi_heavy<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm)) ||
+        (ce = cudaFuncSetAttribute(k_rexi_heavy<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm2)))
       return cuda_fail(ce, "cudaFuncSetAttribute(k_rexi_heavy)");
     int per_l = 0, per_h = 0;
     if ((ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_l, k_rexi_light, MIX_WARPS * 32, 0)))
       return cuda_fail(ce, "occupancy(k_rexi_light)");
-    if ((ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_h, k_rexi_heavy, MIX_WARPS * 32, hsm)))
+    int per_h2 = 0;
+    if ((ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_h, k_rexi_heavy<1>, MIX_WARPS * 32, hsm)) ||
+        (ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_h2, k_rexi_heavy<2>, MIX_WARPS * 32, hsm2)))
       return cuda_fail(ce, "occupancy(k_rexi_heavy)");
     e.grid_light = e.nsm * std::max(1, std::min(per_l, 4));
     e.grid_heavy = e.nsm * std::max(1, std::min(per_h, 6));
+    e.grid_heavy2 = e.nsm * std::max(1, std::min(per_h2, 4));
     e.scratch_bytes = sizeof(float4) * (size_t)e.grid_light * MIX_WARPS * light_ckpt_f4_per_warp(e.nseg_max) +
-                      sizeof(float2) * (size_t)e.grid_heavy * MIX_WARPS * heavy_scratch_f2_per_warp(e.kmax);
+                      sizeof(float2) * (size_t)std::max(e.grid_heavy, e.grid_heavy2) * MIX_WARPS *
+                          heavy_scratch_f2_per_warp(e.kmax);
     e.rhs_cap = rhs_cap;
     if ((rc = dev_alloc((char**)&e.rhs, rhs32_bytes(rhs_cap) + sizeof(RhsDF) * rhs_cap, &ws))) return rc;
   }
@@ -349,28 +354,49 @@ struct InstReq {
 // into ranges so that the launch has about qmul tiles per resident warp.
 void build_launch(const Engine& e, const std::vector<InstReq>& req, std::vector<Inst>& insts,
                   std::vector<Tile>& tiles, std::vector<long long>& ecum, int& ntiles_light,
-                  long long& partial_elems, int qmul = 4) {
+                  long long& partial_elems, int& ntiles_heavy2, int qmul = 4) {
   insts.clear();
   tiles.clear();
   ecum.clear();
+  // heavy tiles of two instances with the same pole set (same truncation, same poles) are paired:
+  // partner[i] = the instance solved together with i (set on the first of the pair), -1 otherwise
+  std::vector<int> partner(req.size(), -1);
+  std::vector<char> second(req.size(), 0);
+  if (e.precision == REXI_MIXED) {
+    std::map<const PoleSet*, int> open;  // pole set -> an unpaired instance waiting for a partner
+    for (size_t i = 0; i < req.size(); ++i) {
+      auto it = open.find(req[i].ps);
+      if (it == open.end()) {
+        open[req[i].ps] = (int)i;
+      } else {
+        partner[it->second] = (int)i;
+        second[i] = 1;
+        open.erase(it);
+      }
+    }
+  }
   // units = tiles per pole range: (m, chain) pairs; a light tile holds both chains of its m
-  long long units = 0;
-  for (auto& r : req) units += 2LL * (r.ps->T + 1);
+  long long units = 0, units_h = 0;
+  for (size_t i = 0; i < req.size(); ++i) {
+    units += 2LL * (req[i].ps->T + 1);
+    if (!second[i]) units_h += 2LL * (req[i].ps->T + 1);
+  }
   units = std::max<long long>(units, 1);
+  units_h = std::max<long long>(units_h, 1);
   const long long units_l = std::max<long long>(units / 2, 1);
   int Ql_glob = 1, Qh_glob = 1;
   if (e.precision == REXI_FP64) {
     Qh_glob = (int)std::max<long long>(1, (qmul * (long long)e.grid_fp64 * FP64_WARPS + units - 1) / units);
   } else {
     Ql_glob = (int)std::max<long long>(1, (qmul * (long long)e.grid_light * MIX_WARPS + units_l - 1) / units_l);
-    Qh_glob = (int)std::max<long long>(1, (qmul * (long long)e.grid_heavy * MIX_WARPS + units - 1) / units);
+    Qh_glob = (int)std::max<long long>(1, (qmul * (long long)e.grid_heavy * MIX_WARPS + units_h - 1) / units_h);
   }
   if (e.max_q > 0) {
     Ql_glob = std::min(Ql_glob, e.max_q);
     Qh_glob = std::min(Qh_glob, e.max_q);
   }
   long long poff = 0, roff = 0, ec = 0;
-  std::vector<Tile> light, heavy;
+  std::vector<Tile> light, heavy, heavy2;
   for (size_t i = 0; i < req.size(); ++i) {
     const PoleSet& ps = *req[i].ps;
     const int T = ps.T, nlm = (T + 1) * (T + 2) / 2;
@@ -388,7 +414,7 @@ void build_launch(const Engine& e, const std::vector<InstReq>& req, std::vector<
     I.S0 = make_double2(ps.S0.real(), ps.S0.imag());
     insts.push_back(I);
     ecum.push_back(ec);
-    auto add = [&](int gbase, int G, int Q, int qbase, int hv, std::vector<Tile>& out) {
+    auto add = [&](int gbase, int G, int Q, int qbase, int hv, int inst2, std::vector<Tile>& out) {
       if (G == 0) return;
       const int per = (G + Q - 1) / Q;
       int q = qbase;
@@ -396,18 +422,18 @@ void build_launch(const Engine& e, const std::vector<InstReq>& req, std::vector<
         const int ng = std::min(per, G - g);
         for (int m = 0; m <= T; ++m) {
           if (!hv && e.precision != REXI_FP64) {  // light: both chains in one tile (chain = 2)
-            out.push_back(Tile{m, 2, gbase + g, ng, q, 0, 2 * (T + 1 - m) * ng, (int)i});
+            out.push_back(Tile{m, 2, gbase + g, ng, q, 0, 2 * (T + 1 - m) * ng, (int)i, -1});
             continue;
           }
           for (int c = 0; c < 2; ++c) {
-            const int w = (hv && e.precision != REXI_FP64) ? 3 : 1;
-            out.push_back(Tile{m, c, gbase + g, ng, q, hv, (T + 1 - m) * ng * w, (int)i});
+            const int w = (hv && e.precision != REXI_FP64) ? (inst2 >= 0 ? 6 : 3) : 1;
+            out.push_back(Tile{m, c, gbase + g, ng, q, hv, (T + 1 - m) * ng * w, (int)i, inst2});
           }
         }
       }
     };
-    add(0, ps.g_light, Ql, 0, 0, light);
-    add(ps.g_light, ps.g_heavy, Qh, ql, 1, heavy);
+    add(0, ps.g_light, Ql, 0, 0, -1, light);
+    if (!second[i]) add(ps.g_light, ps.g_heavy, Qh, ql, 1, partner[i], partner[i] >= 0 ? heavy2 : heavy);
     poff += (long long)I.Q * 3 * nlm;
     roff += nlm;
     ec += nlm;
@@ -415,15 +441,18 @@ void build_launch(const Engine& e, const std::vector<InstReq>& req, std::vector<
   ecum.push_back(ec);
   auto bycost = [](const Tile& a, const Tile& b) { return a.cost > b.cost; };
   std::stable_sort(light.begin(), light.end(), bycost);
+  std::stable_sort(heavy2.begin(), heavy2.end(), bycost);
   std::stable_sort(heavy.begin(), heavy.end(), bycost);
   ntiles_light = (int)light.size();
-  tiles = light;
+  ntiles_heavy2 = (int)heavy2.size();
+  tiles = light;  // light, then paired heavy, then single heavy tiles
+  tiles.insert(tiles.end(), heavy2.begin(), heavy2.end());
   tiles.insert(tiles.end(), heavy.begin(), heavy.end());
   partial_elems = poff;
 }
 
 int upload_launch(LaunchSet& L, const std::vector<Inst>& insts, const std::vector<Tile>& tiles,
-                  const std::vector<long long>& ecum, int ntiles_light, long long partial_elems) {
+                  const std::vector<long long>& ecum, int ntiles_light, int ntiles_heavy2, long long partial_elems) {
   free_launch(L);
   cudaError_t ce;
   if ((ce = cudaMalloc(&L.insts, sizeof(Inst) * std::max<size_t>(insts.size(), 1))) ||
@@ -439,6 +468,7 @@ int upload_launch(LaunchSet& L, const std::vector<Inst>& insts, const std::vecto
   L.ninst = (int)insts.size();
   L.ntiles = (int)tiles.size();
   L.ntiles_light = ntiles_light;
+  L.ntiles_heavy2 = ntiles_heavy2;
   L.total = ecum.back();
   L.partial_elems = partial_elems;
   return REXI_OK;
@@ -515,9 +545,15 @@ int engine_launch(Engine& e, const LaunchSet& L, const double2* U0, double2* U1)
       k_rexi_light<<<e.grid_light, MIX_WARPS * 32, 0, e.stream>>>(a);
       prof_end(e, h);
     }
-    if (a.ntiles_heavy) {
+    const int nh2 = L.ntiles_heavy2, nh1 = a.ntiles_heavy - L.ntiles_heavy2;
+    if (nh2) {  // tiles carrying two states
       h = prof_begin(e, 3);
-      k_rexi_heavy<<<e.grid_heavy, MIX_WARPS * 32, heavy_smem_bytes(), e.stream>>>(a);
+      k_rexi_heavy<2><<<e.grid_heavy2, MIX_WARPS * 32, heavy_smem_bytes<2>(), e.stream>>>(a, L.ntiles_light, nh2);
+      prof_end(e, h);
+    }
+    if (nh1) {
+      h = prof_begin(e, 3);
+      k_rexi_heavy<1><<<e.grid_heavy, MIX_WARPS * 32, heavy_smem_bytes<1>(), e.stream>>>(a, L.ntiles_light + nh2, nh1);
       prof_end(e, h);
     }
   }
@@ -624,9 +660,9 @@ extern "C" int rexi_plan_create(const rexi_plan_desc* desc, rexi_plan** out) {
     std::vector<Inst> I;
     std::vector<Tile> Tl;
     std::vector<long long> ec;
-    int ntl;
+    int ntl, nth2;
     long long pe;
-    build_launch(p->e, req, I, Tl, ec, ntl, pe);
+    build_launch(p->e, req, I, Tl, ec, ntl, pe, nth2);
     maxp = std::max(maxp, (size_t)pe);
   }
   cudaFree(p->e.partial);
@@ -659,11 +695,11 @@ static int plan_launchset(rexi_plan* p, int B, LaunchSet** out) {
     std::vector<Inst> I;
     std::vector<Tile> Tl;
     std::vector<long long> ec;
-    int ntl;
+    int ntl, nth2;
     long long pe;
-    build_launch(p->e, req, I, Tl, ec, ntl, pe);
+    build_launch(p->e, req, I, Tl, ec, ntl, pe, nth2);
     LaunchSet L;
-    int rc = upload_launch(L, I, Tl, ec, ntl, pe);
+    int rc = upload_launch(L, I, Tl, ec, ntl, nth2, pe);
     if (rc) {
       free_launch(L);
       return rc;
@@ -832,11 +868,11 @@ static int ragged_rebuild(rexi_ragged* r) {
   std::vector<Inst> I;
   std::vector<Tile> Tl;
   std::vector<long long> ec;
-  int ntl;
+  int ntl, nth2;
   long long pe;
-  build_launch(r->e, req, I, Tl, ec, ntl, pe, r->qmul);
+  build_launch(r->e, req, I, Tl, ec, ntl, pe, nth2, r->qmul);
   if (pe > (long long)r->e.partial_cap) return fail(REXI_EBUSY, "rexi_ragged: partial-sum workspace exceeded");
-  return upload_launch(r->L, I, Tl, ec, ntl, pe);
+  return upload_launch(r->L, I, Tl, ec, ntl, nth2, pe);
 }
 
 extern "C" int rexi_ragged_set(rexi_ragged* r, int ninst, const rexi_instance* inst) {
