@@ -415,8 +415,11 @@ __global__ void __launch_bounds__(FTH) k_fft_synth(const double2* __restrict__ F
   for (int k = threadIdx.x; k < n; k += blockDim.x) a[k] = Cx<C>::make(R(0), R(0));
   __syncthreads();
   const double2* in = F + (size_t)f * (T + 1) * nlat;
+#pragma unroll 2
   for (int m = threadIdx.x; m <= T; m += blockDim.x) {
-    const double2 A = in[(size_t)m * nlat + j0], B = in[(size_t)m * nlat + j0 + 1];
+    // latitudes j0, j0 + 1 of order m: one aligned 32-byte load (j0 even, rows of nlat even)
+    const D4 AB = *reinterpret_cast<const D4*>(in + (size_t)m * nlat + j0);
+    const double2 A = make_double2(AB.x, AB.y), B = make_double2(AB.z, AB.w);
     if (m == 0) {
       a[0] = Cx<C>::make(R(A.x), R(B.x));
     } else {
@@ -447,16 +450,18 @@ __global__ void __launch_bounds__(FTH) k_fft_anal(const double* __restrict__ gri
   C* b = a + n;
   const double* r0 = grid + ((size_t)f * nlat + j0) * n;
   const double* r1 = r0 + n;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) a[k] = Cx<C>::make(R(r0[k]), R(r1[k]));
+#pragma unroll 4
+  for (int k = threadIdx.x; k < n; k += blockDim.x) a[k] = Cx<C>::make(R(__ldg(r0 + k)), R(__ldg(r1 + k)));
   __syncthreads();
   const C* z = fft_smem<C>(a, b, fp, tw, -1);
   const double sc = 3.14159265358979323846 / n;  // (2 pi / n) / 2
   double2* out = F + (size_t)f * (T + 1) * nlat;
   for (int m = threadIdx.x; m <= T; m += blockDim.x) {
     const C zm = z[m], zn = z[m == 0 ? 0 : n - m];
-    // A = (Z_m + conj(Z_{n-m})) / 2,  B = (Z_m - conj(Z_{n-m})) / (2i)
-    out[(size_t)m * nlat + j0] = make_double2(sc * ((double)zm.x + zn.x), sc * ((double)zm.y - zn.y));
-    out[(size_t)m * nlat + j0 + 1] = make_double2(sc * ((double)zm.y + zn.y), -sc * ((double)zm.x - zn.x));
+    // A = (Z_m + conj(Z_{n-m})) / 2,  B = (Z_m - conj(Z_{n-m})) / (2i); one aligned 32-byte store
+    *reinterpret_cast<D4*>(out + (size_t)m * nlat + j0) =
+        D4{sc * ((double)zm.x + zn.x), sc * ((double)zm.y - zn.y), sc * ((double)zm.y + zn.y),
+           -sc * ((double)zm.x - zn.x)};
   }
 }
 
