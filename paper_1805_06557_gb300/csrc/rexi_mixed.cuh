@@ -554,7 +554,7 @@ k_rexi_heavy(MixedArgs a, int t0, int nt) {
         float2 ct = make_float2(0.f, 0.f), y[G];
 #pragma unroll
         for (int s = 0; s < G; ++s) y[s] = make_float2(0.f, 0.f);
-#pragma unroll 1
+#pragma unroll 4  // loads of four elements in flight
         for (int k = 0; k < K; ++k) {
           const float4 tb = __ldg(a.tab32 + toff + k);
           const bool isZ = ((k & 1) == c);
@@ -592,7 +592,7 @@ k_rexi_heavy(MixedArgs a, int t0, int nt) {
 #pragma unroll
               for (int s = 0; s < G; ++s) ys[s] = cp[1 + s];
             }
-#pragma unroll 1
+#pragma unroll
             for (int k = sg * SEG; k <= e; ++k) {
               const float4 tb = __ldg(a.tab32 + toff + k);
               const bool isZ = ((k & 1) == c);
@@ -659,7 +659,7 @@ k_rexi_heavy(MixedArgs a, int t0, int nt) {
       float2 dxm[G];
 #pragma unroll
       for (int s = 0; s < G; ++s) dxm[s] = make_float2(0.f, 0.f);
-#pragma unroll 1
+#pragma unroll 4  // loads of four elements in flight
       for (int k = 0; k < K; ++k) {
         const float2 g = Gs[(size_t)k * 32 + lane];
 #pragma unroll
