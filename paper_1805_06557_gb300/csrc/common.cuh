@@ -81,10 +81,12 @@ struct PoleF {
 };
 
 // One unit of work: instance, zonal order m, parity chain (2 = both chains, light tiles), a range of 32-pole groups of the
-// instance's pole set, and the slot of the partial sums it owns.  Sorted by decreasing cost.  Heavy tiles may carry a
-// second instance inst2 of the same truncation and pole set (-1: none), solved with the same pivots.
+// instance's pole set, and the slot of the partial sums it owns.  Sorted by decreasing cost.  Heavy tiles of state
+// pairs carry two pairs of instances of the same truncation and pole set, (inst, inst2) on lanes 0-15 and
+// (inst3, inst4) on lanes 16-31 (inst3 = -1: the second half repeats the first and writes nothing); g0 is then a
+// pole offset and ng counts 16-pole groups.  Other tiles have inst2 = inst3 = inst4 = -1.
 struct Tile {
-  int m, chain, g0, ng, q, heavy, cost, inst, inst2;
+  int m, chain, g0, ng, q, heavy, cost, inst, inst2, inst3, inst4;
 };
 
 // One state of a launch.  Offsets are relative to the launch's base pointers.

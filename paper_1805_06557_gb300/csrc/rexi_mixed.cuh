@@ -437,9 +437,12 @@ __device__ __forceinline__ float4 heavy_dfsum16(const float2* x, const float4* w
 // (the small correction); the halves are combined by a shuffle and added into the tile's
 // double-float partial slots (written when first = true).  Weights are in the packed layout
 // (re.hi, im.hi, re.lo, im.lo).
+// HALVES (tiles of state pairs): the two half-warps hold different states on the same 16 poles,
+// so each half writes its own row sums (when wr) and nothing is combined across halves.
+template <bool HALVES>
 __device__ __forceinline__ void heavy_block_sum(const float2* tile, const float4* s_w, const float4* s_wz, int kb,
                                                 int K, int c, int lane, bool dfsum, bool first, double2* part,
-                                                int off, int nlm) {
+                                                int off, int nlm, bool wr = true) {
   const int r = lane & 15, h = lane >> 4;
   const int kk = kb + r;
   const bool valid = kk < K;
@@ -464,6 +467,13 @@ __device__ __forceinline__ void heavy_block_sum(const float2* tile, const float4
       f1 = make_float4(g1.x, 0.f, g1.y, 0.f);
       f2 = make_float4(g2.x, 0.f, g2.y, 0.f);
     }
+  }
+  if (HALVES) {
+    if (valid && wr) {
+      dfp_add(reinterpret_cast<float4*>(part + (isD ? nlm : 0) + off + kk), f1, first);
+      if (isD) dfp_add(reinterpret_cast<float4*>(part + 2 * nlm + off + kk), f2, first);
+    }
+    return;
   }
   // combine the two halves: two-sum of the high words, low words added
   float4 o1, o2;
@@ -527,9 +537,14 @@ k_rexi_heavy(MixedArgs a, int t0, int nt) {
     const int t = round * W + ((round & 1) ? (W - 1 - gw) : gw);
     if (t >= nt) continue;
     const Tile tl = a.tiles[t0 + t];
+    // tiles of state pairs: half-warp h solves pair h on the same 16 poles; a missing second pair
+    // (inst3 < 0) is replaced by the first, whose results that half then does not write
+    const int half = lane >> 4;
+    const bool second = G == 2 && half && tl.inst3 >= 0;
+    const bool wr = G == 1 || !half || second;
     Inst I[G];
-    I[0] = a.insts[tl.inst];
-    if (G == 2) I[G - 1] = a.insts[tl.inst2];
+    I[0] = a.insts[second ? tl.inst3 : tl.inst];
+    if (G == 2) I[G - 1] = a.insts[second ? tl.inst4 : tl.inst2];
     const int T = I[0].T, nlm = I[0].nlm;
     const int m = tl.m, c = tl.chain, K = T + 1 - m, off = moff(T, m), toff = moff(a.Ttab, m);
     const Rhs32* rb[G];
@@ -543,7 +558,8 @@ k_rexi_heavy(MixedArgs a, int t0, int nt) {
     }
 
     for (int gi = 0; gi < tl.ng; ++gi) {
-      const int pidx = I[0].pole0 + (tl.g0 + gi) * 32 + lane;
+      // one state: 32 poles of the 32-pole group g0 + gi; state pairs: 16 poles from pole offset g0
+      const int pidx = G == 2 ? I[0].pole0 + tl.g0 + 16 * gi + (lane & 15) : I[0].pole0 + (tl.g0 + gi) * 32 + lane;
       const PoleF pf = a.p32[pidx];
       const PoleDF pq = a.pdf[pidx];
       __syncwarp();
@@ -645,7 +661,8 @@ k_rexi_heavy(MixedArgs a, int t0, int nt) {
             __syncwarp();
 #pragma unroll
             for (int s = 0; s < G; ++s)
-              heavy_block_sum(s_tile + s * HBLK * LTROW, s_w, s_wz, e, K, c, lane, true, gi == 0, part[s], off, nlm);
+              heavy_block_sum<G == 2>(s_tile + s * HBLK * LTROW, s_w, s_wz, e, K, c, lane, true, gi == 0, part[s], off,
+                                      nlm, wr);
             __syncwarp();
           }
 #pragma unroll
@@ -674,8 +691,8 @@ k_rexi_heavy(MixedArgs a, int t0, int nt) {
           __syncwarp();
 #pragma unroll
           for (int s = 0; s < G; ++s)
-            heavy_block_sum(s_tile + s * HBLK * LTROW, s_w, s_wz, k - hblk_pos(k), K, c, lane, false, false, part[s],
-                            off, nlm);
+            heavy_block_sum<G == 2>(s_tile + s * HBLK * LTROW, s_w, s_wz, k - hblk_pos(k), K, c, lane, false, false,
+                                    part[s], off, nlm, wr);
           __syncwarp();
         }
       }

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <array>
 #include <map>
 #include <numeric>
 #include <tuple>
@@ -43,6 +44,7 @@ int dev_alloc(P** p, size_t bytes, long long* acc) {
 // ---- pole sets (host) -----------------------------------------------------------------
 struct PoleSet {
   int T = 0, N = 0, Npad = 0, ngroups = 0, n_heavy = 0, g_light = 0, g_heavy = 0;
+  int g_heavy16 = 0;        // heavy poles in 16-pole groups (tiles of state pairs); g_heavy counts 32-pole groups
   int n_pruned = 0;         // poles left out (their summed gain is <= the pruning threshold)
   double pruned_gain = 0;   // sum of the gains of the poles left out
   double dt = 0, X = 0;
@@ -128,6 +130,7 @@ int make_poleset(PoleSet& ps, int precision, int T, int N, double dt, double X, 
     ps.n_heavy = nkeep;
     ps.g_light = 0;
     ps.g_heavy = ps.ngroups;
+    ps.g_heavy16 = 2 * ps.ngroups;
     return REXI_OK;
   };
   if (precision == REXI_FP64) return all_heavy();
@@ -135,18 +138,28 @@ int make_poleset(PoleSet& ps, int precision, int T, int N, double dt, double X, 
   int nh = 0;
   for (int i = 0; i < nkeep; ++i)
     if (gain[by_gain[i]] > tau) ++nh;
-  const int nh_pad = std::min((nh + 31) / 32 * 32, nkeep);
-  if (nh_pad == nkeep && nkeep % 32 != 0) return all_heavy();  // everything heavy, padding at the end
+  // heavy class: whole 16-pole groups of the largest gains (tiles of state pairs take 16 poles
+  // per half-warp); the pole array pads it to 32 for tiles of one state
+  const int nh16 = std::min((nh + 15) / 16 * 16, nkeep);
+  if (nh16 == nkeep && nkeep % 16 != 0) return all_heavy();  // everything heavy, padding at the end
+  const int nl = nkeep - nh16, lpad = (nl + 31) / 32 * 32, hpad = (nh16 + 31) / 32 * 32;
+  ps.Npad = lpad + hpad;
+  ps.ngroups = ps.Npad / 32;
+  ps.z.clear();
+  ps.w.clear();
+  ps.heavy.clear();
   std::vector<int> hv(N, 0);
-  for (int i = 0; i < nh_pad; ++i) hv[by_gain[i]] = 1;
+  for (int i = 0; i < nh16; ++i) hv[by_gain[i]] = 1;
   for (int n = 0; n < N; ++n)
     if (keep[n] && !hv[n]) push(z[n], w[n], 0);
-  for (int i = 0; i < npad; ++i) push(1.0, 0.0, 0);
+  for (int i = nl; i < lpad; ++i) push(1.0, 0.0, 0);
   for (int n = 0; n < N; ++n)
     if (hv[n]) push(z[n], w[n], 1);
-  ps.n_heavy = nh_pad;
-  ps.g_light = (ps.Npad - nh_pad) / 32;
-  ps.g_heavy = nh_pad / 32;
+  for (int i = nh16; i < hpad; ++i) push(1.0, 0.0, 1);
+  ps.n_heavy = nh16;
+  ps.g_light = lpad / 32;
+  ps.g_heavy = hpad / 32;
+  ps.g_heavy16 = nh16 / 16;
   return REXI_OK;
 }
 
@@ -358,28 +371,34 @@ void build_launch(const Engine& e, const std::vector<InstReq>& req, std::vector<
   insts.clear();
   tiles.clear();
   ecum.clear();
-  // heavy tiles of two instances with the same pole set (same truncation, same poles) are paired:
-  // partner[i] = the instance solved together with i (set on the first of the pair), -1 otherwise
-  std::vector<int> partner(req.size(), -1);
-  std::vector<char> second(req.size(), 0);
+  // Heavy tiles of instances with the same pole set (same truncation, same poles): instances are
+  // paired, and pairs grouped by two into one tile (one pair per half-warp).  group[i] lists the
+  // (up to four) instances led by i; led[i] = 1 when i leads a group, 2 when i joined one.
+  std::vector<std::array<int, 4>> group(req.size(), std::array<int, 4>{-1, -1, -1, -1});
+  std::vector<char> led(req.size(), 0);
   if (e.precision == REXI_MIXED) {
-    std::map<const PoleSet*, int> open;  // pole set -> an unpaired instance waiting for a partner
-    for (size_t i = 0; i < req.size(); ++i) {
-      auto it = open.find(req[i].ps);
-      if (it == open.end()) {
-        open[req[i].ps] = (int)i;
-      } else {
-        partner[it->second] = (int)i;
-        second[i] = 1;
-        open.erase(it);
+    std::map<const PoleSet*, std::vector<int>> by_set;  // instances of each pole set, in order
+    for (size_t i = 0; i < req.size(); ++i) by_set[req[i].ps].push_back((int)i);
+    for (auto& kv : by_set) {
+      const std::vector<int>& v = kv.second;
+      size_t k = 0;
+      while (k + 1 < v.size()) {  // a pair is left: four together if there are four, else a lone pair
+        const size_t take = v.size() - k >= 4 ? 4 : 2;
+        std::array<int, 4> gr{-1, -1, -1, -1};
+        for (size_t j = 0; j < take; ++j) gr[j] = v[k + j];
+        group[v[k]] = gr;
+        led[v[k]] = 1;
+        for (size_t j = 1; j < take; ++j) led[v[k + j]] = 2;
+        k += take;
       }
+      // a last odd instance keeps tiles of one state
     }
   }
   // units = tiles per pole range: (m, chain) pairs; a light tile holds both chains of its m
   long long units = 0, units_h = 0;
   for (size_t i = 0; i < req.size(); ++i) {
     units += 2LL * (req[i].ps->T + 1);
-    if (!second[i]) units_h += 2LL * (req[i].ps->T + 1);
+    if (led[i] != 2) units_h += 2LL * (req[i].ps->T + 1);
   }
   units = std::max<long long>(units, 1);
   units_h = std::max<long long>(units_h, 1);
@@ -400,9 +419,11 @@ void build_launch(const Engine& e, const std::vector<InstReq>& req, std::vector<
   for (size_t i = 0; i < req.size(); ++i) {
     const PoleSet& ps = *req[i].ps;
     const int T = ps.T, nlm = (T + 1) * (T + 2) / 2;
+    const bool grouped = led[i] != 0;  // heavy work in tiles of state pairs (16-pole groups)
+    const int Gh = grouped ? ps.g_heavy16 : ps.g_heavy;
     const int Ql = ps.g_light ? std::min(Ql_glob, ps.g_light) : 1;
-    const int Qh = ps.g_heavy ? std::min(Qh_glob, ps.g_heavy) : 1;
-    const int ql = ranges_used(ps.g_light, Ql), qh = ranges_used(ps.g_heavy, Qh);
+    const int Qh = Gh ? std::min(Qh_glob, Gh) : 1;
+    const int ql = ranges_used(ps.g_light, Ql), qh = ranges_used(Gh, Qh);
     Inst I;
     I.soff = req[i].soff;
     I.poff = poff;
@@ -414,7 +435,7 @@ void build_launch(const Engine& e, const std::vector<InstReq>& req, std::vector<
     I.S0 = make_double2(ps.S0.real(), ps.S0.imag());
     insts.push_back(I);
     ecum.push_back(ec);
-    auto add = [&](int gbase, int G, int Q, int qbase, int hv, int inst2, std::vector<Tile>& out) {
+    auto add = [&](int gbase, int G, int Q, int qbase, int hv, std::vector<Tile>& out) {
       if (G == 0) return;
       const int per = (G + Q - 1) / Q;
       int q = qbase;
@@ -422,18 +443,31 @@ void build_launch(const Engine& e, const std::vector<InstReq>& req, std::vector<
         const int ng = std::min(per, G - g);
         for (int m = 0; m <= T; ++m) {
           if (!hv && e.precision != REXI_FP64) {  // light: both chains in one tile (chain = 2)
-            out.push_back(Tile{m, 2, gbase + g, ng, q, 0, 2 * (T + 1 - m) * ng, (int)i, -1});
+            out.push_back(Tile{m, 2, gbase + g, ng, q, 0, 2 * (T + 1 - m) * ng, (int)i, -1, -1, -1});
             continue;
           }
           for (int c = 0; c < 2; ++c) {
-            const int w = (hv && e.precision != REXI_FP64) ? (inst2 >= 0 ? 6 : 3) : 1;
-            out.push_back(Tile{m, c, gbase + g, ng, q, hv, (T + 1 - m) * ng * w, (int)i, inst2});
+            const int w = (hv && e.precision != REXI_FP64) ? 3 : 1;
+            out.push_back(Tile{m, c, gbase + g, ng, q, hv, (T + 1 - m) * ng * w, (int)i, -1, -1, -1});
           }
         }
       }
     };
-    add(0, ps.g_light, Ql, 0, 0, -1, light);
-    if (!second[i]) add(ps.g_light, ps.g_heavy, Qh, ql, 1, partner[i], partner[i] >= 0 ? heavy2 : heavy);
+    add(0, ps.g_light, Ql, 0, 0, light);
+    if (!grouped) {
+      add(ps.g_light, ps.g_heavy, Qh, ql, 1, heavy);
+    } else if (led[i] == 1) {  // tiles of the group led by i: g0 = pole offset, ng = 16-pole groups
+      const std::array<int, 4>& gr = group[i];
+      const int per = (Gh + Qh - 1) / Qh;
+      int q = ql;
+      for (int g = 0; g < Gh; g += per, ++q) {
+        const int ng = std::min(per, Gh - g);
+        for (int m = 0; m <= T; ++m)
+          for (int c = 0; c < 2; ++c)
+            heavy2.push_back(Tile{m, c, 32 * ps.g_light + 16 * g, ng, q, 1, (T + 1 - m) * ng * 6, gr[0], gr[1],
+                                  gr[2], gr[3]});
+      }
+    }
     poff += (long long)I.Q * 3 * nlm;
     roff += nlm;
     ec += nlm;

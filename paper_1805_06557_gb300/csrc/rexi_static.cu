@@ -137,7 +137,7 @@ __global__ void k_static_setup(D4* tab, PoleD* poles, Tile* tiles, Inst* inst, l
     t.heavy = 1;
     t.cost = (T + 1 - m) * t.ng;
     t.inst = 0;
-    t.inst2 = -1;
+    t.inst2 = t.inst3 = t.inst4 = -1;
     tiles[i] = t;
   }
 }

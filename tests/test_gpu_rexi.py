@@ -245,7 +245,7 @@ def test_mixed_heavy_classification_and_pruning(env):
     plan = rexi.Plan(T, N, dt, OM, A, PB, p0=p0, Xc=Xc, precision="mixed")
     z, w, cls = plan.poles()
     info = plan.info()
-    assert info["n_heavy"] % 32 == 0 and 0 < info["n_heavy"] < N
+    assert info["n_heavy"] % 16 == 0 and 0 < info["n_heavy"] < N
     yi = np.clip(z.imag, -X, X)
     gain = np.abs(w) / np.abs(z - 1j * yi)
     heavy, light, pruned = cls == 1, cls == 0, cls == -1
