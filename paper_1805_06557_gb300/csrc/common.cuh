@@ -81,10 +81,10 @@ struct PoleF {
 };
 
 // One unit of work: instance, zonal order m, parity chain (2 = both chains, light tiles), a range of 32-pole groups of the
-// instance's pole set, and the slot of the partial sums it owns.  Sorted by decreasing cost.  Heavy tiles of state
-// pairs carry two pairs of instances of the same truncation and pole set, (inst, inst2) on lanes 0-15 and
-// (inst3, inst4) on lanes 16-31 (inst3 = -1: the second half repeats the first and writes nothing); g0 is then a
-// pole offset and ng counts 16-pole groups.  Other tiles have inst2 = inst3 = inst4 = -1.
+// instance's pole set, and the slot of the partial sums it owns.  Sorted by decreasing cost.  Heavy tiles may carry a
+// pair of instances of the same truncation and pole set (inst, inst2) on 32-pole groups, or two such pairs, (inst,
+// inst2) on lanes 0-15 and (inst3, inst4) on lanes 16-31, on 16-pole groups (g0 is then a pole offset and ng counts
+// 16-pole groups).  Unused instance fields are -1.
 struct Tile {
   int m, chain, g0, ng, q, heavy, cost, inst, inst2, inst3, inst4;
 };

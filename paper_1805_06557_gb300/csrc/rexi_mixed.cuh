@@ -510,9 +510,10 @@ __device__ __forceinline__ void heavy_block_sum(const float2* tile, const float4
 // diagonal and every table load are formed once for both; right-hand sides, x, residuals, h
 // and the pole sums are per state.  All loops stay rolled so that the residual's code exists
 // once per state.
-template <int G>
+template <int G, bool HALVES>
 static __global__ void __launch_bounds__(MIX_WARPS * 32, G == 2 ? 4 : 6)
 k_rexi_heavy(MixedArgs a, int t0, int nt) {
+  static_assert(G == 2 || !HALVES, "half-warp tiles carry state pairs");
   constexpr int SEG = heavy_seg<G>();
   constexpr int SW = 1 + G;  // float2 per lane and element in the segment buffer: inv, y of each state
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -537,11 +538,11 @@ k_rexi_heavy(MixedArgs a, int t0, int nt) {
     const int t = round * W + ((round & 1) ? (W - 1 - gw) : gw);
     if (t >= nt) continue;
     const Tile tl = a.tiles[t0 + t];
-    // tiles of state pairs: half-warp h solves pair h on the same 16 poles; a missing second pair
-    // (inst3 < 0) is replaced by the first, whose results that half then does not write
+    // HALVES: half-warp h solves pair h on the same 16 poles; a missing second pair (inst3 < 0)
+    // is replaced by the first, whose results that half then does not write
     const int half = lane >> 4;
-    const bool second = G == 2 && half && tl.inst3 >= 0;
-    const bool wr = G == 1 || !half || second;
+    const bool second = HALVES && half && tl.inst3 >= 0;
+    const bool wr = !HALVES || !half || second;
     Inst I[G];
     I[0] = a.insts[second ? tl.inst3 : tl.inst];
     if (G == 2) I[G - 1] = a.insts[second ? tl.inst4 : tl.inst2];
@@ -558,8 +559,8 @@ k_rexi_heavy(MixedArgs a, int t0, int nt) {
     }
 
     for (int gi = 0; gi < tl.ng; ++gi) {
-      // one state: 32 poles of the 32-pole group g0 + gi; state pairs: 16 poles from pole offset g0
-      const int pidx = G == 2 ? I[0].pole0 + tl.g0 + 16 * gi + (lane & 15) : I[0].pole0 + (tl.g0 + gi) * 32 + lane;
+      // 32 poles of the 32-pole group g0 + gi; HALVES: 16 poles from the pole offset g0 + 16 gi
+      const int pidx = HALVES ? I[0].pole0 + tl.g0 + 16 * gi + (lane & 15) : I[0].pole0 + (tl.g0 + gi) * 32 + lane;
       const PoleF pf = a.p32[pidx];
       const PoleDF pq = a.pdf[pidx];
       __syncwarp();
@@ -661,7 +662,7 @@ k_rexi_heavy(MixedArgs a, int t0, int nt) {
             __syncwarp();
 #pragma unroll
             for (int s = 0; s < G; ++s)
-              heavy_block_sum<G == 2>(s_tile + s * HBLK * LTROW, s_w, s_wz, e, K, c, lane, true, gi == 0, part[s], off,
+              heavy_block_sum<HALVES>(s_tile + s * HBLK * LTROW, s_w, s_wz, e, K, c, lane, true, gi == 0, part[s], off,
                                       nlm, wr);
             __syncwarp();
           }
@@ -691,7 +692,7 @@ k_rexi_heavy(MixedArgs a, int t0, int nt) {
           __syncwarp();
 #pragma unroll
           for (int s = 0; s < G; ++s)
-            heavy_block_sum<G == 2>(s_tile + s * HBLK * LTROW, s_w, s_wz, k - hblk_pos(k), K, c, lane, false, false,
+            heavy_block_sum<HALVES>(s_tile + s * HBLK * LTROW, s_w, s_wz, k - hblk_pos(k), K, c, lane, false, false,
                                     part[s], off, nlm, wr);
           __syncwarp();
         }

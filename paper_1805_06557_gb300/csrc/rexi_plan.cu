@@ -68,7 +68,7 @@ constexpr double PRUNE_TAU_MIXED = 8.470329472543003e-22;
 // order, padding at the end.
 // MIXED: light poles first, heavy ones (gain > heavy_tau, padded to whole groups) last.
 int make_poleset(PoleSet& ps, int precision, int T, int N, double dt, double X, const cplx* z,
-                 const cplx* w, double heavy_tau, double prune_tau) {
+                 const cplx* w, double heavy_tau, double prune_tau, int heavy_align) {
   ps.T = T;
   ps.N = N;
   ps.dt = dt;
@@ -138,9 +138,10 @@ int make_poleset(PoleSet& ps, int precision, int T, int N, double dt, double X, 
   int nh = 0;
   for (int i = 0; i < nkeep; ++i)
     if (gain[by_gain[i]] > tau) ++nh;
-  // heavy class: whole 16-pole groups of the largest gains (tiles of state pairs take 16 poles
-  // per half-warp); the pole array pads it to 32 for tiles of one state
-  const int nh16 = std::min((nh + 15) / 16 * 16, nkeep);
+  // heavy class: the poles of largest gain, rounded up to heavy_align (16 where tiles of state
+  // pairs take 16 poles per half-warp, 32 where most tiles carry one state) with the next-largest
+  // gains; the pole array pads it to 32 for tiles of one state
+  const int nh16 = std::min((nh + heavy_align - 1) / heavy_align * heavy_align, nkeep);
   if (nh16 == nkeep && nkeep % 16 != 0) return all_heavy();  // everything heavy, padding at the end
   const int nl = nkeep - nh16, lpad = (nl + 31) / 32 * 32, hpad = (nh16 + 31) / 32 * 32;
   ps.Npad = lpad + hpad;
@@ -164,7 +165,7 @@ int make_poleset(PoleSet& ps, int precision, int T, int N, double dt, double X, 
 }
 
 int make_poleset_from_contour(PoleSet& ps, int precision, int T, int N, double dt, double X, double p0,
-                              double Xc, double heavy_tau, double prune_tau) {
+                              double Xc, double heavy_tau, double prune_tau, int heavy_align) {
   std::vector<double> zz(2 * N), ww(2 * N);
   int rc = rexi_coeffs(N, p0, Xc, 0, zz.data(), ww.data());
   if (rc) return rc;
@@ -173,7 +174,7 @@ int make_poleset_from_contour(PoleSet& ps, int precision, int T, int N, double d
     z[n] = cplx(zz[2 * n], zz[2 * n + 1]);
     w[n] = cplx(ww[2 * n], ww[2 * n + 1]);
   }
-  return make_poleset(ps, precision, T, N, dt, X, z.data(), w.data(), heavy_tau, prune_tau);
+  return make_poleset(ps, precision, T, N, dt, X, z.data(), w.data(), heavy_tau, prune_tau, heavy_align);
 }
 
 int ranges_used(int G, int Q) {
@@ -202,7 +203,7 @@ struct Engine {
   size_t rhs_cap = 0;  // elements
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
-  int grid_fp64 = 0, grid_light = 0, grid_heavy = 0, grid_heavy2 = 0;  // heavy: single-state and paired tiles
+  int grid_fp64 = 0, grid_light = 0, grid_heavy = 0, grid_heavy2 = 0;  // heavy: tiles of one state, of state pairs
   int max_q = 0;  // cap on pole ranges per class and instance (0: none)
   long long workspace = 0;
   // profiling
@@ -222,7 +223,7 @@ struct LaunchSet {
   Inst* insts = nullptr;
   Tile* tiles = nullptr;
   long long* ecum = nullptr;
-  int ninst = 0, ntiles = 0, ntiles_light = 0, ntiles_heavy2 = 0;
+  int ninst = 0, ntiles = 0, ntiles_light = 0, ntiles_quad = 0, ntiles_pair = 0;
   long long total = 0, partial_elems = 0;
 };
 
@@ -306,16 +307,20 @@ int engine_init(Engine& e, int precision, int Ttab, double omega, double radius,
     if ((rc = dev_alloc(&e.p32, sizeof(PoleF) * pole_cap, &ws))) return rc;
     if ((rc = dev_alloc(&e.pdf, sizeof(PoleDF) * pole_cap, &ws))) return rc;
     const size_t hsm = heavy_smem_bytes<1>(), hsm2 = heavy_smem_bytes<2>();
-    if ((ce = cudaFuncSetAttribute(k_rexi_heavy<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm)) ||
-        (ce = cudaFuncSetAttribute(k_rexi_heavy<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm2)))
+    if ((ce = cudaFuncSetAttribute(k_rexi_heavy<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm)) ||
+        (ce = cudaFuncSetAttribute(k_rexi_heavy<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm2)) ||
+        (ce = cudaFuncSetAttribute(k_rexi_heavy<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm2)))
       return cuda_fail(ce, "cudaFuncSetAttribute(k_rexi_heavy)");
     int per_l = 0, per_h = 0;
     if ((ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_l, k_rexi_light, MIX_WARPS * 32, 0)))
       return cuda_fail(ce, "occupancy(k_rexi_light)");
     int per_h2 = 0;
-    if ((ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_h, k_rexi_heavy<1>, MIX_WARPS * 32, hsm)) ||
-        (ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_h2, k_rexi_heavy<2>, MIX_WARPS * 32, hsm2)))
+    int per_h2b = 0;
+    if ((ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_h, k_rexi_heavy<1, false>, MIX_WARPS * 32, hsm)) ||
+        (ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_h2, k_rexi_heavy<2, false>, MIX_WARPS * 32, hsm2)) ||
+        (ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_h2b, k_rexi_heavy<2, true>, MIX_WARPS * 32, hsm2)))
       return cuda_fail(ce, "occupancy(k_rexi_heavy)");
+    per_h2 = std::min(per_h2, per_h2b);  // one grid size serves both tile forms of state pairs
     e.grid_light = e.nsm * std::max(1, std::min(per_l, 4));
     e.grid_heavy = e.nsm * std::max(1, std::min(per_h, 6));
     e.grid_heavy2 = e.nsm * std::max(1, std::min(per_h2, 4));
@@ -367,7 +372,7 @@ struct InstReq {
 // into ranges so that the launch has about qmul tiles per resident warp.
 void build_launch(const Engine& e, const std::vector<InstReq>& req, std::vector<Inst>& insts,
                   std::vector<Tile>& tiles, std::vector<long long>& ecum, int& ntiles_light,
-                  long long& partial_elems, int& ntiles_heavy2, int qmul = 4) {
+                  long long& partial_elems, int& ntiles_quad, int& ntiles_pair, int qmul = 4) {
   insts.clear();
   tiles.clear();
   ecum.clear();
@@ -375,7 +380,7 @@ void build_launch(const Engine& e, const std::vector<InstReq>& req, std::vector<
   // paired, and pairs grouped by two into one tile (one pair per half-warp).  group[i] lists the
   // (up to four) instances led by i; led[i] = 1 when i leads a group, 2 when i joined one.
   std::vector<std::array<int, 4>> group(req.size(), std::array<int, 4>{-1, -1, -1, -1});
-  std::vector<char> led(req.size(), 0);
+  std::vector<char> led(req.size(), 0), in_quad(req.size(), 0);
   if (e.precision == REXI_MIXED) {
     std::map<const PoleSet*, std::vector<int>> by_set;  // instances of each pole set, in order
     for (size_t i = 0; i < req.size(); ++i) by_set[req[i].ps].push_back((int)i);
@@ -389,6 +394,7 @@ void build_launch(const Engine& e, const std::vector<InstReq>& req, std::vector<
         group[v[k]] = gr;
         led[v[k]] = 1;
         for (size_t j = 1; j < take; ++j) led[v[k + j]] = 2;
+        for (size_t j = 0; j < take; ++j) in_quad[v[k + j]] = take == 4;
         k += take;
       }
       // a last odd instance keeps tiles of one state
@@ -415,12 +421,15 @@ void build_launch(const Engine& e, const std::vector<InstReq>& req, std::vector<
     Qh_glob = std::min(Qh_glob, e.max_q);
   }
   long long poff = 0, roff = 0, ec = 0;
-  std::vector<Tile> light, heavy, heavy2;
+  std::vector<Tile> light, heavy, heavyQ, heavyP;
   for (size_t i = 0; i < req.size(); ++i) {
     const PoleSet& ps = *req[i].ps;
     const int T = ps.T, nlm = (T + 1) * (T + 2) / 2;
-    const bool grouped = led[i] != 0;  // heavy work in tiles of state pairs (16-pole groups)
-    const int Gh = grouped ? ps.g_heavy16 : ps.g_heavy;
+    // heavy work of an instance grouped by four runs on 16-pole groups (tiles of two pairs); a
+    // lone pair and a single instance run on 32-pole groups
+    const int lead = led[i] == 1 ? (int)i : -1;
+    const bool quad = in_quad[i];
+    const int Gh = quad ? ps.g_heavy16 : ps.g_heavy;
     const int Ql = ps.g_light ? std::min(Ql_glob, ps.g_light) : 1;
     const int Qh = Gh ? std::min(Qh_glob, Gh) : 1;
     const int ql = ranges_used(ps.g_light, Ql), qh = ranges_used(Gh, Qh);
@@ -454,18 +463,22 @@ void build_launch(const Engine& e, const std::vector<InstReq>& req, std::vector<
       }
     };
     add(0, ps.g_light, Ql, 0, 0, light);
-    if (!grouped) {
+    if (!led[i]) {
       add(ps.g_light, ps.g_heavy, Qh, ql, 1, heavy);
-    } else if (led[i] == 1) {  // tiles of the group led by i: g0 = pole offset, ng = 16-pole groups
+    } else if (lead >= 0) {  // tiles of the group led by i
       const std::array<int, 4>& gr = group[i];
       const int per = (Gh + Qh - 1) / Qh;
       int q = ql;
       for (int g = 0; g < Gh; g += per, ++q) {
         const int ng = std::min(per, Gh - g);
         for (int m = 0; m <= T; ++m)
-          for (int c = 0; c < 2; ++c)
-            heavy2.push_back(Tile{m, c, 32 * ps.g_light + 16 * g, ng, q, 1, (T + 1 - m) * ng * 6, gr[0], gr[1],
-                                  gr[2], gr[3]});
+          for (int c = 0; c < 2; ++c) {
+            if (quad)  // g0 = pole offset, ng = 16-pole groups
+              heavyQ.push_back(Tile{m, c, 32 * ps.g_light + 16 * g, ng, q, 1, (T + 1 - m) * ng * 6, gr[0], gr[1],
+                                    gr[2], gr[3]});
+            else  // lone pair: g0, ng in 32-pole groups
+              heavyP.push_back(Tile{m, c, ps.g_light + g, ng, q, 1, (T + 1 - m) * ng * 6, gr[0], gr[1], -1, -1});
+          }
       }
     }
     poff += (long long)I.Q * 3 * nlm;
@@ -475,18 +488,22 @@ void build_launch(const Engine& e, const std::vector<InstReq>& req, std::vector<
   ecum.push_back(ec);
   auto bycost = [](const Tile& a, const Tile& b) { return a.cost > b.cost; };
   std::stable_sort(light.begin(), light.end(), bycost);
-  std::stable_sort(heavy2.begin(), heavy2.end(), bycost);
+  std::stable_sort(heavyQ.begin(), heavyQ.end(), bycost);
+  std::stable_sort(heavyP.begin(), heavyP.end(), bycost);
   std::stable_sort(heavy.begin(), heavy.end(), bycost);
   ntiles_light = (int)light.size();
-  ntiles_heavy2 = (int)heavy2.size();
-  tiles = light;  // light, then paired heavy, then single heavy tiles
-  tiles.insert(tiles.end(), heavy2.begin(), heavy2.end());
+  ntiles_quad = (int)heavyQ.size();
+  ntiles_pair = (int)heavyP.size();
+  tiles = light;  // light, then heavy tiles of two pairs, of one pair, of one state
+  tiles.insert(tiles.end(), heavyQ.begin(), heavyQ.end());
+  tiles.insert(tiles.end(), heavyP.begin(), heavyP.end());
   tiles.insert(tiles.end(), heavy.begin(), heavy.end());
   partial_elems = poff;
 }
 
 int upload_launch(LaunchSet& L, const std::vector<Inst>& insts, const std::vector<Tile>& tiles,
-                  const std::vector<long long>& ecum, int ntiles_light, int ntiles_heavy2, long long partial_elems) {
+                  const std::vector<long long>& ecum, int ntiles_light, int ntiles_quad, int ntiles_pair,
+                  long long partial_elems) {
   free_launch(L);
   cudaError_t ce;
   if ((ce = cudaMalloc(&L.insts, sizeof(Inst) * std::max<size_t>(insts.size(), 1))) ||
@@ -502,7 +519,8 @@ int upload_launch(LaunchSet& L, const std::vector<Inst>& insts, const std::vecto
   L.ninst = (int)insts.size();
   L.ntiles = (int)tiles.size();
   L.ntiles_light = ntiles_light;
-  L.ntiles_heavy2 = ntiles_heavy2;
+  L.ntiles_quad = ntiles_quad;
+  L.ntiles_pair = ntiles_pair;
   L.total = ecum.back();
   L.partial_elems = partial_elems;
   return REXI_OK;
@@ -579,15 +597,23 @@ int engine_launch(Engine& e, const LaunchSet& L, const double2* U0, double2* U1)
       k_rexi_light<<<e.grid_light, MIX_WARPS * 32, 0, e.stream>>>(a);
       prof_end(e, h);
     }
-    const int nh2 = L.ntiles_heavy2, nh1 = a.ntiles_heavy - L.ntiles_heavy2;
-    if (nh2) {  // tiles carrying two states
+    const int nq = L.ntiles_quad, np = L.ntiles_pair, n1 = a.ntiles_heavy - nq - np;
+    int t0 = L.ntiles_light;
+    if (nq) {  // tiles of two state pairs (half-warps, 16-pole groups)
       h = prof_begin(e, 3);
-      k_rexi_heavy<2><<<e.grid_heavy2, MIX_WARPS * 32, heavy_smem_bytes<2>(), e.stream>>>(a, L.ntiles_light, nh2);
+      k_rexi_heavy<2, true><<<e.grid_heavy2, MIX_WARPS * 32, heavy_smem_bytes<2>(), e.stream>>>(a, t0, nq);
       prof_end(e, h);
+      t0 += nq;
     }
-    if (nh1) {
+    if (np) {  // tiles of one state pair (32-pole groups)
       h = prof_begin(e, 3);
-      k_rexi_heavy<1><<<e.grid_heavy, MIX_WARPS * 32, heavy_smem_bytes<1>(), e.stream>>>(a, L.ntiles_light + nh2, nh1);
+      k_rexi_heavy<2, false><<<e.grid_heavy2, MIX_WARPS * 32, heavy_smem_bytes<2>(), e.stream>>>(a, t0, np);
+      prof_end(e, h);
+      t0 += np;
+    }
+    if (n1) {
+      h = prof_begin(e, 3);
+      k_rexi_heavy<1, false><<<e.grid_heavy, MIX_WARPS * 32, heavy_smem_bytes<1>(), e.stream>>>(a, t0, n1);
       prof_end(e, h);
     }
   }
@@ -671,6 +697,8 @@ extern "C" int rexi_plan_create(const rexi_plan_desc* desc, rexi_plan** out) {
     return code;
   };
   const double X = rexi_spectrum_bound(d.T, d.dt, d.omega, d.radius, d.phibar);
+  // batches of four or more run heavy tiles of two state pairs on 16-pole groups
+  const int halign = d.max_batch >= 4 ? 16 : 32;
   int rc;
   if (d.z) {
     std::vector<cplx> z(d.N), w(d.N);
@@ -678,9 +706,10 @@ extern "C" int rexi_plan_create(const rexi_plan_desc* desc, rexi_plan** out) {
       z[n] = cplx(d.z[2 * n], d.z[2 * n + 1]);
       w[n] = cplx(d.w[2 * n], d.w[2 * n + 1]);
     }
-    rc = make_poleset(p->ps, d.precision, d.T, d.N, d.dt, X, z.data(), w.data(), d.heavy_tau, d.prune_tau);
+    rc = make_poleset(p->ps, d.precision, d.T, d.N, d.dt, X, z.data(), w.data(), d.heavy_tau, d.prune_tau, halign);
   } else {
-    rc = make_poleset_from_contour(p->ps, d.precision, d.T, d.N, d.dt, X, d.p0, d.Xc, d.heavy_tau, d.prune_tau);
+    rc = make_poleset_from_contour(p->ps, d.precision, d.T, d.N, d.dt, X, d.p0, d.Xc, d.heavy_tau, d.prune_tau,
+                                   halign);
   }
   if (rc) return bail(rc);
   rc = engine_init(p->e, d.precision, d.T, d.omega, d.radius, d.phibar, (cudaStream_t)d.stream, p->ps.Npad, 0,
@@ -694,9 +723,9 @@ extern "C" int rexi_plan_create(const rexi_plan_desc* desc, rexi_plan** out) {
     std::vector<Inst> I;
     std::vector<Tile> Tl;
     std::vector<long long> ec;
-    int ntl, nth2;
+    int ntl, ntq, ntp;
     long long pe;
-    build_launch(p->e, req, I, Tl, ec, ntl, pe, nth2);
+    build_launch(p->e, req, I, Tl, ec, ntl, pe, ntq, ntp);
     maxp = std::max(maxp, (size_t)pe);
   }
   cudaFree(p->e.partial);
@@ -729,11 +758,11 @@ static int plan_launchset(rexi_plan* p, int B, LaunchSet** out) {
     std::vector<Inst> I;
     std::vector<Tile> Tl;
     std::vector<long long> ec;
-    int ntl, nth2;
+    int ntl, ntq, ntp;
     long long pe;
-    build_launch(p->e, req, I, Tl, ec, ntl, pe, nth2);
+    build_launch(p->e, req, I, Tl, ec, ntl, pe, ntq, ntp);
     LaunchSet L;
-    int rc = upload_launch(L, I, Tl, ec, ntl, nth2, pe);
+    int rc = upload_launch(L, I, Tl, ec, ntl, ntq, ntp, pe);
     if (rc) {
       free_launch(L);
       return rc;
@@ -902,11 +931,11 @@ static int ragged_rebuild(rexi_ragged* r) {
   std::vector<Inst> I;
   std::vector<Tile> Tl;
   std::vector<long long> ec;
-  int ntl, nth2;
+  int ntl, ntq, ntp;
   long long pe;
-  build_launch(r->e, req, I, Tl, ec, ntl, pe, nth2, r->qmul);
+  build_launch(r->e, req, I, Tl, ec, ntl, pe, ntq, ntp, r->qmul);
   if (pe > (long long)r->e.partial_cap) return fail(REXI_EBUSY, "rexi_ragged: partial-sum workspace exceeded");
-  return upload_launch(r->L, I, Tl, ec, ntl, nth2, pe);
+  return upload_launch(r->L, I, Tl, ec, ntl, ntq, ntp, pe);
 }
 
 extern "C" int rexi_ragged_set(rexi_ragged* r, int ninst, const rexi_instance* inst) {
@@ -938,8 +967,9 @@ extern "C" int rexi_ragged_set(rexi_ragged* r, int ninst, const rexi_instance* i
     }
     PoleSet ps;
     const double X = rexi_spectrum_bound(q.T, q.dt, r->d.omega, r->d.radius, r->d.phibar);
+    // ragged sets: most instances have a pole set of their own and run tiles of one state
     int rc = make_poleset_from_contour(ps, r->d.precision, q.T, q.N, q.dt, X, q.p0, q.Xc, r->d.heavy_tau,
-                                       r->d.prune_tau);
+                                       r->d.prune_tau, 32);
     if (rc) return rc;
     if (r->e.pole_used + ps.Npad > r->e.pole_cap) return REXI_EBUSY;
     rc = engine_upload_poles(r->e, ps);
