@@ -90,7 +90,7 @@ typedef struct rexi_plan_desc {
                       /* (a bound on the energy-norm size of their term relative to U0, dt L */
                       /* being skew-adjoint in that norm) are left out while their summed    */
                       /* gain stays <= prune_tau, conjugate pairs together; 0: default    */
-                      /* (REXI_MIXED 2^-70, REXI_FP64 none: every pole is solved); < 0: none */
+                      /* (REXI_MIXED 2^-60, REXI_FP64 none: every pole is solved); < 0: none */
 } rexi_plan_desc;
 
 /*

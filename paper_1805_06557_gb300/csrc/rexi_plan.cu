@@ -56,15 +56,16 @@ struct PoleSet {
 };
 
 // Default pruning threshold of mixed plans: the summed gain of the poles left out is at most
-// 2^-70 (the change of the result in the energy norm, relative to the state).
-constexpr double PRUNE_TAU_MIXED = 8.470329472543003e-22;
+// 2^-60 (the change of the result in the energy norm, relative to the state: 1/128 of one FP64
+// unit roundoff).
+constexpr double PRUNE_TAU_MIXED = 8.673617379884035e-19;
 
 // Orders (and pads) the poles.  Every pole n has the gain g_n = |w_n| / dist(z_n, [-iX, iX]),
 // a bound on the energy-norm size of its term w_n (z_n - dt L)^-1 U0 relative to U0 (dt L is
 // skew-adjoint in the energy inner product with its spectrum in [-iX, iX]).  Pruning: the
 // poles of smallest gain are left out while their summed gain stays <= prune_tau (conjugate
 // pairs, which have equal gains, stay together); prune_tau = 0 selects the default (mixed:
-// 2^-70, FP64: no pruning), prune_tau < 0 no pruning.  FP64: the kept poles in the given
+// 2^-60, FP64: no pruning), prune_tau < 0 no pruning.  FP64: the kept poles in the given
 // order, padding at the end.
 // MIXED: light poles first, heavy ones (gain > heavy_tau, padded to whole groups) last.
 int make_poleset(PoleSet& ps, int precision, int T, int N, double dt, double X, const cplx* z,
