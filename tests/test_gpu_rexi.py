@@ -184,6 +184,33 @@ def test_batch_matches_single_and_is_deterministic(env, prec):
     plan.close()
 
 
+@pytest.mark.parametrize("B", [2, 3, 6, 7])
+def test_heavy_tile_forms(env, B):
+    """Batches that exercise every form of heavy tile: a lone pair (B = 2), a pair and a single
+    state (3), two pairs on half-warps and a lone pair (6), and all three (7).  Every state
+    matches its one-state result, and the last state of B = 7 the oracle."""
+    torch, rexi = env
+    T, N, dt = 63, 256, 3600.0
+    p0, Xc, X = contour(T, dt, N)
+    U0 = np.stack([syn.gaussian_state(T, 500 + i) for i in range(B)])
+    plan = rexi.Plan(T, N, dt, OM, A, PB, p0=p0, Xc=Xc, precision="mixed", max_batch=8)
+    u0 = torch.from_numpy(U0).cuda()
+    u1 = torch.empty_like(u0)
+    plan.step(u0, u1)
+    one = torch.empty_like(u0[:1])
+    for b in range(B):
+        plan.step(u0[b:b + 1].contiguous(), one)
+        plan.sync()
+        err = orx.rel_l2(u1[b].cpu().numpy(), one[0].cpu().numpy(), T)
+        assert np.all(err < 1e-9), (B, b, err)
+    if B == 7:
+        z, w = oc.rexi_coefficients(N, p0, Xc)
+        ms = [0, 1, 31, 63]
+        ref = orx.rexi_step(U0[6], T, dt, OM, A, PB, z, w, m_list=ms)
+        assert np.all(masked_rel(u1[6].cpu().numpy(), ref, T, ms) < 1e-8)
+    plan.close()
+
+
 def test_step_host_matches_device(env):
     torch, rexi = env
     T, N, dt = 31, 64, 3600.0
