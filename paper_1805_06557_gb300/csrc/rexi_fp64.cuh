@@ -183,6 +183,7 @@ static __global__ void k_rexi_finalize(const double2* __restrict__ U0, const dou
       acc.z = s;
       acc.w += v.w + ez;
     };
+#pragma unroll 4  // loads of several slots in flight; the order of the sums is unchanged
     for (int q = 0; q < I.Q; ++q) {
       add(az, p);
       add(ad, p + nlm);
