@@ -30,8 +30,9 @@ typedef struct sh_plan_desc {
   double radius;    /* sphere radius a [m] (vector transforms)                              */
   int precision;    /* SH_FP64, SH_TF32 or SH_BF16                                          */
   int max_fields;   /* largest nfields passed to a transform; SH_TF32 / SH_BF16: <= 8, and   */
-                    /* the vector analysis operand (8 max_fields rows x nlat/2 latitudes)    */
-                    /* must fit in shared memory (e.g. max_fields <= 4 at nlat = 1536 TF32)  */
+                    /* the vector operands (8 max_fields columns x nlat/2 latitudes for      */
+                    /* analysis, x T+1 degrees for synthesis) must fit in shared memory      */
+                    /* (e.g. max_fields <= 4 at T = 1023, nlat = 1536, TF32)                 */
   void* stream;     /* cudaStream_t                                                         */
 } sh_plan_desc;
 
@@ -77,7 +78,7 @@ int sh_plan_check(sh_plan* plan);
  * returns, per stage, the total milliseconds (ms[k]) and the number of launches
  * (launches[k]) since the last reset (reset = 1 clears them after reading).  Stages:
  * 0 FP64 Legendre contraction (SH_FP64), 1 operand packing for the tensor cores,
- * 2 tcgen05 Legendre GEMM, 3 tensor-core epilogue (parity combination in FP64),
+ * 2 tcgen05 Legendre GEMM, 3 tensor-core epilogue (hemisphere and parity combination in FP64),
  * 4 longitude FFT.  Arrays hold SH_NSTAGES entries; either may be NULL.  Disabled by
  * default.  Errors: REXI_EINVAL, REXI_ECUDA.
  */

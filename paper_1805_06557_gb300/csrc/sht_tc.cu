@@ -30,7 +30,7 @@ namespace {
 
 constexpr int TC_MAXSTAGES = 8;     // depth of the A-chunk ring
 constexpr int TC_THREADS = 192;     // warps 0-3 epilogue, warp 4 bulk copies, warp 5 MMA issue
-constexpr int TC_MAXCOL = 32;      // B columns of a synthesis call; analysis uses 2 x ncols
+constexpr int TC_MAXCOL = 32;      // B columns of one half of a B operand (synthesis: north | south; analysis: N + S | N - S)
 constexpr size_t TC_SMEM_BUDGET = 220 * 1024;
 
 struct Job {
@@ -304,9 +304,9 @@ __global__ void k_tc_table(const double* __restrict__ src, unsigned char* __rest
     unsigned char* ch = out + (size_t)c * 128 * KC * eb;
     for (int kk = 0; kk < kc; ++kk) {
       float v = 0.f;
-      if (synth) {  // rows = latitudes, K = degrees of the parity
+      if (synth) {  // rows = latitudes of the northern half, K = all degrees n = m + k
         const int lat = j.tile * 128 + r;
-        const int k = j.par + 2 * (c * KC + kk);
+        const int k = c * KC + kk;
         if (lat < nh && k < K) v = (float)src[(size_t)(base + k) * nh + lat];
       } else {      // rows = degrees (both parities), K = latitudes
         const int k = j.tile * 128 + r;
@@ -318,31 +318,33 @@ __global__ void k_tc_table(const double* __restrict__ src, unsigned char* __rest
   }
 }
 
-// synthesis B operand of (m, par): column col = f * cpf + q, K index kk <-> k = par + 2 kk.
-// q in [0, cpf): scalar (cpf = 2): re, im of spec f; vector (cpf = 4): psi re, psi im, chi re,
-// chi im.
+// synthesis B operand of zonal order m: K index k = n - m over all degrees; columns
+// [0, nr): coefficient (f, q) of column col = f * cpf + q (north: P_n(mu) of the northern
+// latitude); [nr, 2 nr): the same times (-1)^k (south: P_n(-mu) = (-1)^(n-m) P_n(mu)); the rest 0;
+// nr = nf * cpf.  q in [0, cpf): scalar (cpf = 2): re, im of spec f; vector (cpf = 4): psi re,
+// psi im, chi re, chi im.
 __global__ void k_tc_bsynth(const double2* __restrict__ s0, const double2* __restrict__ s1,
                             unsigned char* __restrict__ B, const int* __restrict__ boff,
                             const int* __restrict__ kpad, int T, int nlm, int nf, int cpf, int ncols,
                             int bf16) {
-  const int m = blockIdx.x, par = blockIdx.y;
-  const int id = m * 2 + par;
-  const int kp = kpad[id];
+  const int m = blockIdx.x;
+  const int kp = kpad[m];
   if (kp == 0) return;
   const int E = bf16 ? 8 : 4, eb = bf16 ? 2 : 4;
   const int sbo = (kp / E) * 128;
-  const int K = T + 1 - m, base = moff(T, m);
-  unsigned char* out = B + boff[id];
+  const int K = T + 1 - m, base = moff(T, m), nr = nf * cpf;
+  unsigned char* out = B + boff[m];
   for (int idx = threadIdx.x; idx < ncols * kp; idx += blockDim.x) {
-    const int col = idx / kp, kk = idx - col * kp;
-    const int k = par + 2 * kk;
+    const int col = idx / kp, k = idx - col * kp;
     float v = 0.f;
-    const int f = col / cpf, q = col - f * cpf;
-    if (f < nf && k < K) {
+    if (col < 2 * nr && k < K) {
+      const int cc = col < nr ? col : col - nr;
+      const int f = cc / cpf, q = cc - f * cpf;
       const double2 c = (q < 2 ? s0 : s1)[(size_t)f * nlm + base + k];
-      v = (float)((q & 1) ? c.y : c.x);
+      const double x = (q & 1) ? c.y : c.x;
+      v = (float)((col >= nr && (k & 1)) ? -x : x);
     }
-    store_elem(out, canon_off(col, kk, E, eb, sbo), v, bf16);
+    store_elem(out, canon_off(col, k, E, eb, sbo), v, bf16);
   }
 }
 
@@ -384,7 +386,9 @@ __global__ void k_tc_banal(const double2* __restrict__ F0, const double2* __rest
 
 __device__ __forceinline__ double2 imul_d(int m, double2 v) { return make_double2(-m * v.y, m * v.x); }
 
-// synthesis epilogue: thread per (m, northern latitude); jobs indexed jid(m, par, tile, tab)
+// synthesis epilogue: thread per (m, northern latitude); D rows of job (m, tile, tab) hold the
+// northern values in columns [0, nr) and the southern ones in [nr, 2 nr) (H: minus the sum, since
+// H_n(-mu) = -(-1)^(n-m) H_n(mu)); row stride ncols
 __global__ void k_tc_esynth(const float* __restrict__ D, const int* __restrict__ dmap, double2* __restrict__ F0,
                             double2* __restrict__ F1, int T, int nlat, int nf, int cpf, int ncols, int ntile,
                             int vector, double inv_a) {
@@ -392,34 +396,25 @@ __global__ void k_tc_esynth(const float* __restrict__ D, const int* __restrict__
   const int nh = nlat / 2;
   const int lat = blockIdx.x * blockDim.x + threadIdx.x;
   if (lat >= nh) return;
-  const int tile = lat / 128, r = lat % 128;
-  auto val = [&](int par, int tab, int col) -> float {
-    const int o = dmap[((m * 2 + par) * ntile + tile) * 2 + tab];
-    return o < 0 ? 0.f : D[o + (size_t)r * ncols + col];
+  const int tile = lat / 128, r = lat % 128, nr = nf * cpf;
+  auto val = [&](int tab, int hemi, int col) -> double {
+    const int o = dmap[(m * ntile + tile) * 2 + tab];
+    return o < 0 ? 0.0 : (double)D[o + (size_t)r * ncols + hemi * nr + col];
   };
   for (int f = 0; f < nf; ++f) {
     const int c0 = f * cpf;
     double2* o0 = F0 + ((size_t)f * (T + 1) + m) * nlat;
     if (!vector) {
-      const double2 e = make_double2(val(0, 0, c0), val(0, 0, c0 + 1));
-      const double2 od = make_double2(val(1, 0, c0), val(1, 0, c0 + 1));
-      o0[lat] = make_double2(e.x + od.x, e.y + od.y);
-      o0[nlat - 1 - lat] = make_double2(e.x - od.x, e.y - od.y);
+      o0[lat] = make_double2(val(0, 0, c0), val(0, 0, c0 + 1));
+      o0[nlat - 1 - lat] = make_double2(val(0, 1, c0), val(0, 1, c0 + 1));
     } else {
       double2* o1 = F1 + ((size_t)f * (T + 1) + m) * nlat;
-      double2 Pps[2], Pch[2], Hps[2], Hch[2];
-      for (int par = 0; par < 2; ++par) {
-        Pps[par] = make_double2(val(par, 0, c0), val(par, 0, c0 + 1));
-        Pch[par] = make_double2(val(par, 0, c0 + 2), val(par, 0, c0 + 3));
-        Hps[par] = make_double2(val(par, 1, c0), val(par, 1, c0 + 1));
-        Hch[par] = make_double2(val(par, 1, c0 + 2), val(par, 1, c0 + 3));
-      }
       for (int hemi = 0; hemi < 2; ++hemi) {
-        const double so = hemi ? -1.0 : 1.0, sh = hemi ? -1.0 : 1.0;
-        auto cb = [&](const double2* v, double sa) {
-          return make_double2(sa * (v[0].x + so * v[1].x), sa * (v[0].y + so * v[1].y));
-        };
-        const double2 pps = cb(Pps, 1.0), pch = cb(Pch, 1.0), hps = cb(Hps, sh), hch = cb(Hch, sh);
+        const double sh = hemi ? -1.0 : 1.0;  // H of the southern latitude
+        const double2 pps = make_double2(val(0, hemi, c0), val(0, hemi, c0 + 1));
+        const double2 pch = make_double2(val(0, hemi, c0 + 2), val(0, hemi, c0 + 3));
+        const double2 hps = make_double2(sh * val(1, hemi, c0), sh * val(1, hemi, c0 + 1));
+        const double2 hch = make_double2(sh * val(1, hemi, c0 + 2), sh * val(1, hemi, c0 + 3));
         const double2 ich = imul_d(m, pch), ips = imul_d(m, pps);
         const int jj = hemi ? nlat - 1 - lat : lat;
         o0[jj] = make_double2(inv_a * (-hps.x + ich.x), inv_a * (-hps.y + ich.y));
@@ -474,7 +469,7 @@ struct TcLegendre {
   // synthesis jobs (scalar uses the P half), analysis jobs; job lists and D maps per variant
   Job *jobs_s = nullptr, *jobs_a = nullptr;
   int njobs_s = 0, njobs_a = 0, njobs_sP = 0, njobs_aP = 0;
-  int *dmap_s = nullptr, *dmap_a = nullptr;   // synthesis [(m*2+par)*ntile+tile][tab], analysis [m*ntile+tile][tab] -> D offset or -1
+  int *dmap_s = nullptr, *dmap_a = nullptr;   // [m*ntile+tile][tab] -> D offset or -1 (synthesis, analysis)
   int *boff_s = nullptr, *kpad_s = nullptr, *boff_a = nullptr;
   int kpad_smax = 0;  // largest K extent of a synthesis B operand
   int nsm = 0;
@@ -502,37 +497,35 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
   const int KC = t->KC, eb = t->eb;
   const size_t chunk = 128ull * KC * eb;
   t->ntile_s = (t->nh + 127) / 128;
-  // ---- synthesis jobs: (m, par, tile, tab), K = degrees of the parity ----------------------
+  // ---- synthesis jobs: (m, tile, tab); rows = northern latitudes of the tile, K = all degrees
+  // of m; B = [c | (-1)^(n-m) c] gives the northern and the southern values in one job -------
   std::vector<TabJob> tj;
   std::vector<Job> js;
-  std::vector<int> dmap_s(2 * (T + 1) * 2 * t->ntile_s, -1), boff_s(2 * (T + 1)), kpad_s(2 * (T + 1));
+  std::vector<int> dmap_s((T + 1) * t->ntile_s * 2, -1), boff_s(T + 1), kpad_s(T + 1);
   long long aoff = 0;
   int boff = 0, doff = 0;
   const int ncols_max = TC_MAXCOL;
   std::vector<Job> jsP, jsH;
   const int kstep = bf16 ? 16 : 8;  // MMA K per instruction
-  for (int m = 0; m <= T; ++m)
-    for (int par = 0; par < 2; ++par) {
-      const int K = T + 1 - m;
-      const int kpar = (K - par + 1) / 2;
-      const int kpad = (kpar + kstep - 1) / kstep * kstep;  // K padded to whole k-steps only
-      const int nchunk = (kpad + KC - 1) / KC;
-      const int kl = kpad - (nchunk - 1) * KC;
-      boff_s[m * 2 + par] = boff;
-      kpad_s[m * 2 + par] = kpad;
-      boff += ncols_max * kpad * eb;
-      if (nchunk == 0) continue;
-      for (int tile = 0; tile < t->ntile_s; ++tile) {
-        tj.push_back(TabJob{aoff, m, par, tile, nchunk, kl});
-        for (int tab = 0; tab < 2; ++tab) {
-          Job j{aoff, boff_s[m * 2 + par], doff, nchunk, kpad, tab, kl};
-          (tab ? jsH : jsP).push_back(j);
-          dmap_s[((m * 2 + par) * t->ntile_s + tile) * 2 + tab] = doff;
-          doff += 128 * ncols_max;
-        }
-        aoff += (long long)(nchunk - 1) * chunk + 128LL * kl * eb;
+  for (int m = 0; m <= T; ++m) {
+    const int K = T + 1 - m;
+    const int kpad = (K + kstep - 1) / kstep * kstep;  // K padded to whole k-steps only
+    const int nchunk = (kpad + KC - 1) / KC;
+    const int kl = kpad - (nchunk - 1) * KC;
+    boff_s[m] = boff;
+    kpad_s[m] = kpad;
+    boff += 2 * ncols_max * kpad * eb;
+    for (int tile = 0; tile < t->ntile_s; ++tile) {
+      tj.push_back(TabJob{aoff, m, 0, tile, nchunk, kl});
+      for (int tab = 0; tab < 2; ++tab) {
+        Job j{aoff, boff_s[m], doff, nchunk, kpad, tab, kl};
+        (tab ? jsH : jsP).push_back(j);
+        dmap_s[(m * t->ntile_s + tile) * 2 + tab] = doff;
+        doff += 128 * 2 * ncols_max;
       }
+      aoff += (long long)(nchunk - 1) * chunk + 128LL * kl * eb;
     }
+  }
   const long long tab_s_bytes = aoff;
   const int bsz_s = boff;
   const int dsz_s = doff;
@@ -585,8 +578,10 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
   // over all latitudes) must fit one B buffer and two ring stages in shared memory
   {
     auto ncols_of = [](int nf, int cpf) { return std::max(16, (nf * cpf + 15) / 16 * 16); };
+    int kpad_smax = 0;
+    for (int v : kpad_s) kpad_smax = std::max(kpad_smax, v);
     const size_t bmax = std::max((size_t)ncols_of(max_fields, 4) * t->kpad_a * 2 * eb,
-                                 (size_t)ncols_of(max_fields, 4) * 512 * eb);
+                                 (size_t)ncols_of(2 * max_fields, 4) * kpad_smax * eb);
     if (bmax + 2 * chunk + 4096 > TC_SMEM_BUDGET) {
       tc_legendre_destroy(t);
       return fail(REXI_EINVAL,
@@ -701,11 +696,10 @@ static int ncols_for(int nf, int cpf) {
 }
 
 int tc_leg_synth(TcLegendre* t, const double2* spec, double2* F, int nf, cudaStream_t s) {
-  const int nc = ncols_for(nf, 2);
+  const int nc = ncols_for(2 * nf, 2);  // northern and southern columns
   {
     const int ph = t->prof ? t->prof->begin(1) : -1;
-    k_tc_bsynth<<<dim3(t->T + 1, 2), 256, 0, s>>>(spec, spec, t->B, t->boff_s, t->kpad_s, t->T, t->nlm, nf, 2, nc,
-                                                  t->bf16);
+    k_tc_bsynth<<<t->T + 1, 256, 0, s>>>(spec, spec, t->B, t->boff_s, t->kpad_s, t->T, t->nlm, nf, 2, nc, t->bf16);
     if (t->prof) t->prof->end(ph);
   }
   int rc = gemm(t, true, false, nc, s);
@@ -721,11 +715,10 @@ int tc_leg_synth(TcLegendre* t, const double2* spec, double2* F, int nf, cudaStr
 
 int tc_leg_synth_uv(TcLegendre* t, const double2* psi, const double2* chi, double2* FU, double2* FV, int nf,
                     double inv_a, cudaStream_t s) {
-  const int nc = ncols_for(nf, 4);
+  const int nc = ncols_for(2 * nf, 4);  // northern and southern columns
   {
     const int ph = t->prof ? t->prof->begin(1) : -1;
-    k_tc_bsynth<<<dim3(t->T + 1, 2), 256, 0, s>>>(psi, chi, t->B, t->boff_s, t->kpad_s, t->T, t->nlm, nf, 4, nc,
-                                                  t->bf16);
+    k_tc_bsynth<<<t->T + 1, 256, 0, s>>>(psi, chi, t->B, t->boff_s, t->kpad_s, t->T, t->nlm, nf, 4, nc, t->bf16);
     if (t->prof) t->prof->end(ph);
   }
   int rc = gemm(t, true, true, nc, s);
