@@ -78,7 +78,7 @@ int sh_plan_check(sh_plan* plan);
  * returns, per stage, the total milliseconds (ms[k]) and the number of launches
  * (launches[k]) since the last reset (reset = 1 clears them after reading).  Stages:
  * 0 FP64 Legendre contraction (SH_FP64), 1 operand packing for the tensor cores,
- * 2 tcgen05 Legendre GEMM, 3 tensor-core epilogue (hemisphere and parity combination in FP64),
+ * 2 tcgen05 Legendre GEMM with its fused FP64 epilogue, 3 unused (always 0),
  * 4 longitude FFT.  Arrays hold SH_NSTAGES entries; either may be NULL.  Disabled by
  * default.  Errors: REXI_EINVAL, REXI_ECUDA.
  */

@@ -1,22 +1,25 @@
 // Tensor-core (tcgen05) Legendre contractions for sh_plan precisions SH_TF32 / SH_BF16
 // (paper Sec. 3.2: the dense Legendre contraction per zonal order m of the SH transforms).
 //
-// Every contraction is a set of GEMM jobs D[128 x Ncols] = A[128 x K] B[K x Ncols]:
-//   synthesis, per (m, parity of n - m, 128-latitude tile, table P or H):
-//       A = table^T (rows = northern latitudes, K = degrees of that parity),
-//       B = spectral coefficients (columns = fields x re/im [x psi/chi])
-//   analysis, per (m, parity, 128-degree tile, table P or H):
-//       A = table (rows = degrees of that parity, K = northern latitudes),
-//       B = weighted hemispheric sums / differences of the Fourier coefficients.
+// Every contraction is a set of GEMM jobs [128 x Ncols] = A[128 x K] B[K x Ncols]:
+//   synthesis, per (m, 128-latitude tile, table P or H):
+//       A = table^T (rows = northern latitudes, K = all degrees n = m + k),
+//       B = spectral coefficients c_n beside (-1)^k c_n (columns: the northern and the
+//           mirrored southern value of each field x re/im [x psi/chi])
+//   analysis, per (m, 128-degree tile, table P or H):
+//       A = table (rows = degrees, K = northern latitudes),
+//       B = weighted hemispheric sums and differences of the Fourier coefficients.
 // Operands are stored in the canonical no-swizzle K-major layout of the tensor cores
 // (8-row x 16-byte core matrices; cores adjacent along K 128 B apart), the tables pre-tiled
 // at plan time so that each K-chunk of A is one contiguous block moved by the bulk-copy
 // engine (cp.async.bulk, completion on an mbarrier).  The GEMM is a persistent kernel, one
-// CTA per SM, with a copy warp streaming A chunks through a ring of up to 8 stages and the
-// B operands through two buffers, an MMA warp (accumulators in TMEM, FP32, two buffers) and
-// four epilogue warps reading the accumulators with tcgen05.ld.  Epilogue kernels combine
-// the parities (north = even + odd, south = even - odd for P; the opposite sign for H) in
-// FP64.  All mbarrier waits are bounded; on a timeout the kernel records an error flag.
+// CTA per SM, each with its own list of jobs (longest first, assigned to the least-loaded CTA
+// at plan time): a copy warp streams A chunks through a ring of up to 8 stages and the B
+// operands through up to four buffers, an MMA warp accumulates in TMEM (FP32), and four
+// epilogue warps read the accumulators with tcgen05.ld and write the FP64 results directly
+// (hemisphere and parity combination, and for vector transforms the P and H sums of one
+// (m, tile), which run as consecutive jobs of one CTA).  All mbarrier waits are bounded; on a
+// timeout the kernel records an error flag.
 #include <algorithm>
 #include <cuda_bf16.h>
 #include <vector>
@@ -30,26 +33,34 @@ namespace {
 
 constexpr int TC_MAXSTAGES = 8;     // depth of the A-chunk ring
 constexpr int TC_THREADS = 192;     // warps 0-3 epilogue, warp 4 bulk copies, warp 5 MMA issue
-constexpr int TC_MAXCOL = 32;      // B columns of one half of a B operand (synthesis: north | south; analysis: N + S | N - S)
+constexpr int TC_MAXCOL = 32;      // B operands are allocated 2 x TC_MAXCOL columns per m (8 fields x 2 x 4)
 constexpr size_t TC_SMEM_BUDGET = 220 * 1024;
 
 struct Job {
   long long a_off;  // byte offset of the job's first A chunk in its table
   int b_off;        // byte offset of the job's B operand in the B buffer
-  int d_off;        // float offset of the job's D tile in the D buffer
+  int m, tile;      // zonal order and 128-row tile (latitudes or degrees k = n - m)
   int nchunk;       // K chunks
   int kpad;         // K extent of B (whole MMA k-steps; (nchunk - 1) * KC + kl)
   int tab;          // 0 = P, 1 = H
   int kl;           // K of the last chunk (a multiple of the MMA k-step, <= KC)
+  int rows;         // A rows stored for the job (the valid rows rounded up to 8, <= 128): a
+                    // chunk holds rows x KC elements; the MMA reads all 128 rows of a ring
+                    // stage, and the D rows past `rows` hold stale sums that no epilogue reads
 };
 
 struct GemmArgs {
   const unsigned char* tabP;
   const unsigned char* tabH;
   const unsigned char* B;
-  float* D;
-  const Job* jobs;
-  int njobs, ncols, bf16;
+  const Job* jobs;      // per-CTA lists: CTA c runs jobs[cta_off[c] .. cta_off[c + 1])
+  const int* cta_off;
+  int ncols, bf16;
+  int synth, pair;      // pair: (P, H) jobs of one (m, tile) follow each other (vector transforms)
+  double2* out0;        // synthesis: Fourier coefficients [nf][T+1][nlat] (U for vector)
+  double2* out1;        //   (V); analysis: spectral [nf][nlm] (div; curl for vector)
+  int T, nlat, nlm, nf, cpf;
+  double inv_a;
   int stages;       // A ring depth (<= TC_MAXSTAGES)
   int nb;           // B buffers (1, 2 or 4): B operands are fetched up to nb - 1 jobs ahead
   int nj_max;       // jobs per CTA at most (their descriptors are staged in shared memory)
@@ -57,21 +68,104 @@ struct GemmArgs {
   int* err;
 };
 
-// Persistent, warp-specialised GEMM over the job list: CTA c takes jobs c, c + grid, ...
-// (the list is sorted by decreasing length).  Warp 4 streams the A chunks of every job through
+// Persistent, warp-specialised GEMM over per-CTA job lists (longest first).  Warp 4 streams the A chunks of every job through
 // the S-stage ring without pausing between jobs, and fetches B operands into NB buffers up to
 // NB - 1 jobs ahead (so that a job's MMAs never wait for the latency of its B copy); warp 5
-// issues the MMAs of job i into TMEM accumulator i & 1 and commits: the ring stage (empty),
-// the B buffer (bempty) and the accumulator (tfull); warps 0-3 read accumulator i & 1 (one
-// TMEM lane quarter each), store D, and release it (tempty), so that the MMAs of job i + 1
-// overlap the epilogue of job i.  Every wait is bounded; on a timeout the role records an
-// error code and stops, and teardown drains the copies and MMAs in flight.
+// issues the MMAs of job i into TMEM job buffer i % njb and commits: the ring stage (empty),
+// the B buffer (bempty) and the accumulator (tfull); warps 0-3 read the buffer (one TMEM lane
+// quarter each), write the FP64 results, and release it (tempty), so that the MMAs of the next
+// jobs overlap the epilogue.  Every wait is bounded; on a timeout the role records an error
+// code and stops, and teardown drains the copies and MMAs in flight.
 constexpr int TC_MAXNB = 4;
 constexpr int TC_NACC = 4;          // independent accumulators per job (one per k-step of a chunk)
 constexpr int TC_NJB = 3;           // job buffers of accumulators in TMEM (at most; 2 when N > 32)
 constexpr uint32_t TC_TMEM_COLS = 512;  // TC_NJB x TC_NACC x 32 (N <= 32) or 2 x TC_NACC x 64 (N <= 64)
+
+// 8 columns of this warp's 32 TMEM lanes: the sum of the first nacc of the TC_NACC
+// accumulators (accumulator a at column offset a * cs), in order a = 0, 1, ...
+__device__ __forceinline__ void tmem_sum8(uint32_t ta, uint32_t cs, int nacc, float* v) {
+  uint32_t r[TC_NACC][8];
+#pragma unroll
+  for (int a = 0; a < TC_NACC; ++a) tc::tmem_ld8_nowait(ta + cs * a, r[a]);
+  tc::tmem_wait_ld();
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    float x = __uint_as_float(r[0][q]);
+#pragma unroll
+    for (int a = 1; a < TC_NACC; ++a)
+      if (a < nacc) x += __uint_as_float(r[a][q]);
+    v[q] = x;
+  }
+}
+
+// Results of one row (synthesis: northern latitude `row`; analysis: k = n - m = row) from the
+// 8-column group gq of the sums P (and H for vector transforms), combined in FP64.  Columns are
+// interleaved per field (2 cpf columns each), so a group is two scalar fields or one vector
+// field:
+//   synthesis scalar  (N re, N im, S re, S im): northern latitude and its mirror;
+//   synthesis vector  (N: psi re, psi im, chi re, chi im; S: the same): U = (-H psi + i m P chi)/a,
+//                     V = (i m P psi + H chi)/a, with the southern H sums negated
+//                     (H_n(-mu) = -(-1)^(n-m) H_n(mu); the B operand carries (-1)^(n-m));
+//   analysis scalar   (N+S re, N+S im, N-S re, N-S im): P pairs with N + S for even k, N - S odd;
+//   analysis vector   (N+S: A re, A im, B re, B im; N-S: the same), H with the other block:
+//                     div = (i m P.A - H.B)/a, curl = (i m P.B + H.A)/a.
+__device__ __forceinline__ void epilogue8(const GemmArgs& g, int m, int row, int gq, const float* P,
+                                          const float* H) {
+  const double ia = g.inv_a, dm = (double)m;
+  if (g.synth) {
+    if (row >= g.nlat / 2) return;
+    const int lat = row, lats = g.nlat - 1 - row;
+    if (!g.pair) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int f = 2 * gq + h;
+        if (f >= g.nf) break;
+        double2* o = g.out0 + ((size_t)f * (g.T + 1) + m) * g.nlat;
+        o[lat] = make_double2(P[4 * h], P[4 * h + 1]);
+        o[lats] = make_double2(P[4 * h + 2], P[4 * h + 3]);
+      }
+    } else {
+      const size_t o = ((size_t)gq * (g.T + 1) + m) * g.nlat;
+#pragma unroll
+      for (int hs = 0; hs < 2; ++hs) {
+        const float* p = P + 4 * hs;
+        const float* q = H + 4 * hs;
+        const double sh = hs ? -1.0 : 1.0;
+        const int j = hs ? lats : lat;
+        g.out0[o + j] = make_double2(ia * (-sh * (double)q[0] - dm * (double)p[3]),
+                                     ia * (-sh * (double)q[1] + dm * (double)p[2]));
+        g.out1[o + j] = make_double2(ia * (-dm * (double)p[1] + sh * (double)q[2]),
+                                     ia * (dm * (double)p[0] + sh * (double)q[3]));
+      }
+    }
+  } else {
+    if (row >= g.T + 1 - m) return;
+    const int par = row & 1;
+    const size_t i = (size_t)moff(g.T, m) + row;
+    if (!g.pair) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int f = 2 * gq + h;
+        if (f >= g.nf) break;
+        g.out0[(size_t)f * g.nlm + i] = par ? make_double2(P[4 * h + 2], P[4 * h + 3])
+                                            : make_double2(P[4 * h], P[4 * h + 1]);
+      }
+    } else {
+      double p[4], q[4];  // register selects (no indexing by the parity)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        p[c] = par ? P[4 + c] : P[c];
+        q[c] = par ? H[c] : H[4 + c];
+      }
+      const size_t o = (size_t)gq * g.nlm + i;
+      g.out0[o] = make_double2(ia * (-dm * p[1] - q[2]), ia * (dm * p[0] - q[3]));
+      g.out1[o] = make_double2(ia * (-dm * p[3] + q[0]), ia * (dm * p[2] + q[1]));
+    }
+  }
+}
+
 template <bool BF>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(GemmArgs g) {
+__global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant__ GemmArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
   // element type constants: 16-byte core-matrix rows hold E elements; a chunk (KC = 256 B of
   // K per row) is 8 MMA k-steps of 32 B; consecutive k-steps are 2 core matrices (256 B) apart
@@ -90,9 +184,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(GemmArgs g) {
   const uint32_t tempty0 = tfull0 + 8 * TC_NJB, fin = tempty0 + 8 * TC_NJB;
   uint32_t* taddr_s = reinterpret_cast<uint32_t*>(bars + 2 * S + 2 * NB + 2 * TC_NJB + 1);
   Job* sjobs = reinterpret_cast<Job*>(bars + 2 * S + 2 * NB + 2 * TC_NJB + 2);
-  // jobs of this CTA: blockIdx.x + i * gridDim.x, i < nj; descriptors staged in shared memory
-  const int nj = blockIdx.x < g.njobs ? (g.njobs - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-  for (int i = tid; i < nj && i < g.nj_max; i += blockDim.x) sjobs[i] = g.jobs[blockIdx.x + i * gridDim.x];
+  // jobs of this CTA, descriptors staged in shared memory
+  const int j0 = g.cta_off[blockIdx.x];
+  const int nj = min(g.cta_off[blockIdx.x + 1] - j0, g.nj_max);
+  for (int i = tid; i < nj; i += blockDim.x) sjobs[i] = g.jobs[j0 + i];
   if (tid == 0) {
     for (int i = 0; i < 2 * S + 2 * NB + TC_NJB; ++i) tc::mbar_init(full0 + 8 * i, 1);
     for (int i = 0; i < TC_NJB; ++i) tc::mbar_init(tempty0 + 8 * i, 4);
@@ -147,12 +242,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(GemmArgs g) {
         }
         const Job jb = sjobs[i];
         const unsigned char* A = (jb.tab ? g.tabH : g.tabP) + jb.a_off;
+        // rows / 8 core-matrix row groups: a prefix of the stage's canonical layout
+        const uint32_t jchunk = (uint32_t)jb.rows * KC * eb;
         for (int c = 0; c < jb.nchunk; ++c) {
           if (round > 0) ok = tc::mbar_wait(empty0 + 8 * s, (round - 1) & 1);
           if (!ok) break;
-          const uint32_t cb = (c == jb.nchunk - 1) ? 128u * jb.kl * eb : chunk_bytes;
+          const uint32_t cb = (c == jb.nchunk - 1) ? (uint32_t)jb.rows * jb.kl * eb : jchunk;
           tc::mbar_expect_tx(full0 + 8 * s, cb);
-          tc::bulk_g2s(sa0 + s * chunk_bytes, A + (size_t)c * chunk_bytes, cb, full0 + 8 * s);
+          tc::bulk_g2s(sa0 + s * chunk_bytes, A + (size_t)c * jchunk, cb, full0 + 8 * s);
           ++a_issued;
           if (++s == S) {
             s = 0;
@@ -214,43 +311,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(GemmArgs g) {
       tc::mma_commit(fin);  // arrives once every MMA issued above has completed
     }
   } else {
-    // epilogue: warp w reads TMEM lanes 32 w .. 32 w + 31 (rows of the job's D tile); all
-    // loads of a 16-column group are issued before one wait
-    for (int i = 0; i < nj; ++i) {
+    // epilogue warps 0-3: warp w holds rows 32 w .. 32 w + 31 of every job (its TMEM lane
+    // quarter); the jobs of a vector transform come in (P, H) pairs, released together
+    const int step = g.pair ? 2 : 1;
+    const int ngrp = (2 * g.nf * g.cpf + 7) / 8;  // 8-column groups holding results
+    for (int i = 0; i + step <= nj; i += step) {
       const Job jb = sjobs[i];
-      const int acc = i % njb, u = i / njb;
-      if (!tc::mbar_wait(tfull0 + 8 * acc, u & 1)) {
+      const int acc0 = i % njb, acc1 = (i + 1) % njb;
+      bool ok = tc::mbar_wait(tfull0 + 8 * acc0, (i / njb) & 1);
+      if (ok && g.pair) ok = tc::mbar_wait(tfull0 + 8 * acc1, ((i + 1) / njb) & 1);
+      if (!ok) {
         if (lane == 0) atomicExch(g.err, 2);
         break;
       }
       tc::fence_after_sync();
-      float* Dj = g.D + jb.d_off + (size_t)(32 * warp + lane) * g.ncols;
-      for (int c = 0; c < g.ncols; c += 16) {
-        uint32_t r[TC_NACC][16];
-        const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + cs * TC_NACC * acc + c;
-#pragma unroll
-        for (int a = 0; a < TC_NACC; ++a) {
-          tc::tmem_ld8_nowait(ta + cs * a, r[a]);
-          tc::tmem_ld8_nowait(ta + cs * a + 8, r[a] + 8);
-        }
-        tc::tmem_wait_ld();
+      if (32 * warp < jb.rows) {  // warp-uniform: tcgen05.ld is collective
         // accumulators a < nacc received k-steps (all four unless the job is one short chunk)
         const int nacc = jb.nchunk > 1 ? TC_NACC : min(TC_NACC, jb.kl / KSTEP);
-        float v[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          v[q] = __uint_as_float(r[0][q]);
-#pragma unroll
-          for (int a = 1; a < TC_NACC; ++a)
-            if (a < nacc) v[q] += __uint_as_float(r[a][q]);
+        const uint32_t lq = (uint32_t)(32 * warp) << 16;
+        const uint32_t ta0 = tmem + lq + cs * TC_NACC * acc0, ta1 = tmem + lq + cs * TC_NACC * acc1;
+        const int row = jb.tile * 128 + 32 * warp + lane;
+        for (int gq = 0; gq < ngrp; ++gq) {
+          float P[8], H[8];
+          tmem_sum8(ta0 + 8 * gq, cs, nacc, P);
+          if (g.pair) tmem_sum8(ta1 + 8 * gq, cs, nacc, H);
+          epilogue8(g, jb.m, row, gq, P, H);
         }
-        float4* d4 = reinterpret_cast<float4*>(Dj + c);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
       }
       tc::fence_before_sync();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(tempty0 + 8 * acc);
+      if (lane == 0) {
+        tc::mbar_arrive(tempty0 + 8 * acc0);
+        if (g.pair) tc::mbar_arrive(tempty0 + 8 * acc1);
+      }
     }
   }
   // ---- teardown: no copy may land in, and no MMA may read, a CTA that has exited ----------
@@ -285,7 +378,7 @@ __device__ __forceinline__ void store_elem(unsigned char* base, size_t off, floa
 // tables: one thread per (job, row), looping over K; src = FP64 table [moff+k][nh]
 struct TabJob {
   long long a_off;
-  int m, par, tile, nchunk, kl;  // kl: K of the last chunk
+  int m, rows, tile, nchunk, kl;  // rows: stored rows (<= 128); kl: K of the last chunk
 };
 __global__ void k_tc_table(const double* __restrict__ src, unsigned char* __restrict__ dst,
                            const TabJob* __restrict__ jobs, int njobs, int T, int nh, int synth,
@@ -294,6 +387,7 @@ __global__ void k_tc_table(const double* __restrict__ src, unsigned char* __rest
   if (jid >= njobs) return;
   const TabJob j = jobs[jid];
   const int r = threadIdx.x;  // 0..127
+  if (r >= j.rows) return;
   const int E = bf16 ? 8 : 4, eb = bf16 ? 2 : 4, KC = bf16 ? 128 : 64;  // as TcLegendre::KC
   const int K = T + 1 - j.m, base = moff(T, j.m);
   unsigned char* out = dst + j.a_off;
@@ -301,7 +395,7 @@ __global__ void k_tc_table(const double* __restrict__ src, unsigned char* __rest
     // every chunk but the last holds KC K-elements per row; the last holds j.kl
     const int kc = (c == j.nchunk - 1) ? j.kl : KC;
     const int sbo = (kc / E) * 128;
-    unsigned char* ch = out + (size_t)c * 128 * KC * eb;
+    unsigned char* ch = out + (size_t)c * j.rows * KC * eb;
     for (int kk = 0; kk < kc; ++kk) {
       float v = 0.f;
       if (synth) {  // rows = latitudes of the northern half, K = all degrees n = m + k
@@ -318,158 +412,141 @@ __global__ void k_tc_table(const double* __restrict__ src, unsigned char* __rest
   }
 }
 
-// synthesis B operand of zonal order m: K index k = n - m over all degrees; columns
-// [0, nr): coefficient (f, q) of column col = f * cpf + q (north: P_n(mu) of the northern
-// latitude); [nr, 2 nr): the same times (-1)^k (south: P_n(-mu) = (-1)^(n-m) P_n(mu)); the rest 0;
-// nr = nf * cpf.  q in [0, cpf): scalar (cpf = 2): re, im of spec f; vector (cpf = 4): psi re,
-// psi im, chi re, chi im.
+// One 16-byte core-matrix row of a B operand: E consecutive K elements of column c of the
+// K group whose first byte is `grp` (column c at (c >> 3) * sbo + (c & 7) * 16), rounded to
+// TF32 (cvt.rna) or BF16 (round to nearest even)
+template <bool BF>
+__device__ __forceinline__ void store_row16(unsigned char* grp, int c, int sbo, const float* v) {
+  uint4 u;
+  uint32_t* w = reinterpret_cast<uint32_t*>(&u);
+  if (BF) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+      w[e] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w[e]) : "f"(v[e]));
+  }
+  *reinterpret_cast<uint4*>(grp + (size_t)(c >> 3) * sbo + (c & 7) * 16) = u;
+}
+
+// Padding columns of a B operand (past the real ones, up to the MMA's N) are never written:
+// each D column depends on its own B column only, and no epilogue reads a padding column.
+
+// synthesis B operand of zonal order m: K index k = n - m over all degrees; field f owns the
+// 2 cpf columns from 2 cpf f: first coefficient q of the field in column 2 cpf f + q (north:
+// P_n(mu) of the northern latitude), then the same times (-1)^k in column 2 cpf f + cpf + q
+// (south: P_n(-mu) = (-1)^(n-m) P_n(mu)).  q in [0, cpf): scalar (cpf = 2): re, im of spec f;
+// vector (cpf = 4): psi re, psi im, chi re, chi im.  Thread per (K group of E degrees, column
+// pair p < nf cpf / 2): reads the E coefficients of its pair once and writes the northern and
+// the southern (re, im) rows.
+template <bool BF>
 __global__ void k_tc_bsynth(const double2* __restrict__ s0, const double2* __restrict__ s1,
                             unsigned char* __restrict__ B, const int* __restrict__ boff,
-                            const int* __restrict__ kpad, int T, int nlm, int nf, int cpf, int ncols,
-                            int bf16) {
-  const int m = blockIdx.x;
+                            const int* __restrict__ kpad, int T, int nlm, int nf, int cpf) {
+  constexpr int E = BF ? 8 : 4;
+  const int m = blockIdx.y;
+  const int np = nf * cpf / 2;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = idx / np, p = idx - g * np;
   const int kp = kpad[m];
-  if (kp == 0) return;
-  const int E = bf16 ? 8 : 4, eb = bf16 ? 2 : 4;
+  if (g * E >= kp) return;
   const int sbo = (kp / E) * 128;
-  const int K = T + 1 - m, base = moff(T, m), nr = nf * cpf;
-  unsigned char* out = B + boff[m];
-  for (int idx = threadIdx.x; idx < ncols * kp; idx += blockDim.x) {
-    const int col = idx / kp, k = idx - col * kp;
-    float v = 0.f;
-    if (col < 2 * nr && k < K) {
-      const int cc = col < nr ? col : col - nr;
-      const int f = cc / cpf, q = cc - f * cpf;
-      const double2 c = (q < 2 ? s0 : s1)[(size_t)f * nlm + base + k];
-      const double x = (q & 1) ? c.y : c.x;
-      v = (float)((col >= nr && (k & 1)) ? -x : x);
-    }
-    store_elem(out, canon_off(col, k, E, eb, sbo), v, bf16);
+  unsigned char* grp = B + boff[m] + (size_t)g * 128;
+  const int K = T + 1 - m;
+  const int f = (2 * p) / cpf, q = 2 * p - f * cpf;
+  const double2* src = (q < 2 ? s0 : s1) + (size_t)f * nlm + moff(T, m);
+  double2 c[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int k = g * E + e;
+    c[e] = k < K ? src[k] : make_double2(0.0, 0.0);
   }
+  float re[E], im[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    re[e] = (float)c[e].x;
+    im[e] = (float)c[e].y;
+  }
+  const int cn = 2 * cpf * f + q;  // northern column; the southern one is cpf further
+  store_row16<BF>(grp, cn, sbo, re);
+  store_row16<BF>(grp, cn + 1, sbo, im);
+#pragma unroll
+  for (int e = 1; e < E; e += 2) {  // g * E is even: the parity of k is that of e
+    re[e] = -re[e];
+    im[e] = -im[e];
+  }
+  store_row16<BF>(grp, cn + cpf, sbo, re);
+  store_row16<BF>(grp, cn + cpf + 1, sbo, im);
 }
 
-// analysis B operand of (m, sign): K index = latitude j of the northern half,
-//   scalar (cpf = 2):  w_j (F_N +- F_S)           columns (re, im) per field
-//   vector (cpf = 4):  wq_j (A_N +- A_S), wq_j (B_N +- B_S)   columns (A re, A im, B re, B im)
+// analysis B operand: for each zonal order m, K = northern latitudes j (padded to kpad);
+// field f owns the 2 cpf columns from 2 cpf f: the N + S combinations, then the N - S ones:
+//   scalar (cpf = 2):  w_j (F_N +- F_S)           (re, im)
+//   vector (cpf = 4):  wq_j (A_N +- A_S), wq_j (B_N +- B_S)   (A re, A im, B re, B im)
+// Thread per (K group of E latitudes, column pair p < nr / 2): reads the E northern and
+// mirrored southern Fourier coefficients of its pair once and writes four rows.
+template <bool BF>
 __global__ void k_tc_banal(const double2* __restrict__ F0, const double2* __restrict__ F1,
                            const double* __restrict__ wts, unsigned char* __restrict__ B,
-                           const int* __restrict__ boff, int kpad, int T, int nlat, int nf, int cpf,
-                           int ncols, int bf16) {
-  // B of zonal order m: 2 ncols rows (N + S combinations, then N - S), K = latitudes; one
-  // thread per northern latitude j reads each Fourier coefficient pair (j and its mirror)
-  // once and writes both combinations of every column
-  const int m = blockIdx.x;
-  const int E = bf16 ? 8 : 4, eb = bf16 ? 2 : 4;
+                           const int* __restrict__ boff, int kpad, int T, int nlat, int nf, int cpf) {
+  constexpr int E = BF ? 8 : 4;
+  const int m = blockIdx.y;
+  const int np = nf * cpf / 2;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = idx / np, p = idx - g * np;
+  if (g * E >= kpad) return;
   const int sbo = (kpad / E) * 128;
   const int nh = nlat / 2;
-  unsigned char* out = B + boff[m];
-  for (int j = threadIdx.x; j < kpad; j += blockDim.x) {
-    const double wj = j < nh ? wts[j] : 0.0;
-    for (int col = 0; col < ncols; col += 2) {  // columns come in (re, im) pairs
-      float pr = 0.f, pi = 0.f, mr = 0.f, mi = 0.f;
-      const int f = col / cpf, q = col - f * cpf;
-      if (f < nf && j < nh) {
-        const double2* Fq = (q < 2 ? F0 : F1) + ((size_t)f * (T + 1) + m) * nlat;
-        const double2 a = Fq[j], b = Fq[nlat - 1 - j];
-        pr = (float)(wj * (a.x + b.x));
-        pi = (float)(wj * (a.y + b.y));
-        mr = (float)(wj * (a.x - b.x));
-        mi = (float)(wj * (a.y - b.y));
-      }
-      store_elem(out, canon_off(col, j, E, eb, sbo), pr, bf16);
-      store_elem(out, canon_off(col + 1, j, E, eb, sbo), pi, bf16);
-      store_elem(out, canon_off(ncols + col, j, E, eb, sbo), mr, bf16);
-      store_elem(out, canon_off(ncols + col + 1, j, E, eb, sbo), mi, bf16);
-    }
+  const int f = (2 * p) / cpf, q = 2 * p - f * cpf;
+  const double2* Fq = (q < 2 ? F0 : F1) + ((size_t)f * (T + 1) + m) * nlat;
+  double2 a[E], b[E];
+  double w[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int j = g * E + e;
+    const bool in = j < nh;
+    a[e] = in ? Fq[j] : make_double2(0.0, 0.0);
+    b[e] = in ? Fq[nlat - 1 - j] : make_double2(0.0, 0.0);
+    w[e] = in ? wts[j] : 0.0;
   }
-}
-
-__device__ __forceinline__ double2 imul_d(int m, double2 v) { return make_double2(-m * v.y, m * v.x); }
-
-// synthesis epilogue: thread per (m, northern latitude); D rows of job (m, tile, tab) hold the
-// northern values in columns [0, nr) and the southern ones in [nr, 2 nr) (H: minus the sum, since
-// H_n(-mu) = -(-1)^(n-m) H_n(mu)); row stride ncols
-__global__ void k_tc_esynth(const float* __restrict__ D, const int* __restrict__ dmap, double2* __restrict__ F0,
-                            double2* __restrict__ F1, int T, int nlat, int nf, int cpf, int ncols, int ntile,
-                            int vector, double inv_a) {
-  const int m = blockIdx.y;
-  const int nh = nlat / 2;
-  const int lat = blockIdx.x * blockDim.x + threadIdx.x;
-  if (lat >= nh) return;
-  const int tile = lat / 128, r = lat % 128, nr = nf * cpf;
-  auto val = [&](int tab, int hemi, int col) -> double {
-    const int o = dmap[(m * ntile + tile) * 2 + tab];
-    return o < 0 ? 0.0 : (double)D[o + (size_t)r * ncols + hemi * nr + col];
-  };
-  for (int f = 0; f < nf; ++f) {
-    const int c0 = f * cpf;
-    double2* o0 = F0 + ((size_t)f * (T + 1) + m) * nlat;
-    if (!vector) {
-      o0[lat] = make_double2(val(0, 0, c0), val(0, 0, c0 + 1));
-      o0[nlat - 1 - lat] = make_double2(val(0, 1, c0), val(0, 1, c0 + 1));
-    } else {
-      double2* o1 = F1 + ((size_t)f * (T + 1) + m) * nlat;
-      for (int hemi = 0; hemi < 2; ++hemi) {
-        const double sh = hemi ? -1.0 : 1.0;  // H of the southern latitude
-        const double2 pps = make_double2(val(0, hemi, c0), val(0, hemi, c0 + 1));
-        const double2 pch = make_double2(val(0, hemi, c0 + 2), val(0, hemi, c0 + 3));
-        const double2 hps = make_double2(sh * val(1, hemi, c0), sh * val(1, hemi, c0 + 1));
-        const double2 hch = make_double2(sh * val(1, hemi, c0 + 2), sh * val(1, hemi, c0 + 3));
-        const double2 ich = imul_d(m, pch), ips = imul_d(m, pps);
-        const int jj = hemi ? nlat - 1 - lat : lat;
-        o0[jj] = make_double2(inv_a * (-hps.x + ich.x), inv_a * (-hps.y + ich.y));
-        o1[jj] = make_double2(inv_a * (ips.x + hch.x), inv_a * (ips.y + hch.y));
-      }
-    }
+  float pr[E], pi[E], mr[E], mi[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    pr[e] = (float)(w[e] * (a[e].x + b[e].x));
+    pi[e] = (float)(w[e] * (a[e].y + b[e].y));
+    mr[e] = (float)(w[e] * (a[e].x - b[e].x));
+    mi[e] = (float)(w[e] * (a[e].y - b[e].y));
   }
-}
-
-// analysis epilogue: thread per (m, k)
-__global__ void k_tc_eanal(const float* __restrict__ D, const int* __restrict__ dmap, double2* __restrict__ s0,
-                           double2* __restrict__ s1, int T, int nlm, int nf, int cpf, int ncols, int ntile,
-                           int vector, double inv_a) {
-  const int m = blockIdx.y;
-  const int K = T + 1 - m;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= K) return;
-  // D rows: degree k of tile k / 128; columns: the N + S block, then the N - S block (ncols
-  // each).  P pairs with N + S for even k - m and N - S for odd; H the other way round.
-  const int par = k & 1, tile = k / 128, r = k % 128;
-  auto val = [&](int tab, int col) -> float {
-    const int o = dmap[(m * ntile + tile) * 2 + tab];
-    const int coloff = ((tab == 0) != (par == 1)) ? 0 : ncols;
-    return o < 0 ? 0.f : D[o + (size_t)r * (2 * ncols) + coloff + col];
-  };
-  const size_t i = moff(T, m) + k;
-  for (int f = 0; f < nf; ++f) {
-    const int c0 = f * cpf;
-    if (!vector) {
-      s0[(size_t)f * nlm + i] = make_double2(val(0, c0), val(0, c0 + 1));
-    } else {
-      const double2 PA = make_double2(val(0, c0), val(0, c0 + 1)), PB = make_double2(val(0, c0 + 2), val(0, c0 + 3));
-      const double2 HA = make_double2(val(1, c0), val(1, c0 + 1)), HB = make_double2(val(1, c0 + 2), val(1, c0 + 3));
-      const double2 iPA = imul_d(m, PA), iPB = imul_d(m, PB);
-      s0[(size_t)f * nlm + i] = make_double2(inv_a * (iPA.x - HB.x), inv_a * (iPA.y - HB.y));
-      s1[(size_t)f * nlm + i] = make_double2(inv_a * (iPB.x + HA.x), inv_a * (iPB.y + HA.y));
-    }
-  }
+  unsigned char* grp = B + boff[m] + (size_t)g * 128;
+  const int cn = 2 * cpf * f + q;  // N + S column; the N - S one is cpf further
+  store_row16<BF>(grp, cn, sbo, pr);
+  store_row16<BF>(grp, cn + 1, sbo, pi);
+  store_row16<BF>(grp, cn + cpf, sbo, mr);
+  store_row16<BF>(grp, cn + cpf + 1, sbo, mi);
 }
 
 }  // namespace
 
 // ---------------------------------------------------------------------------------------
+// A GEMM launch plan: per-CTA job lists, flattened (CTA c: jobs[off[c] .. off[c + 1])).
+struct Sched {
+  Job* jobs = nullptr;
+  int* off = nullptr;
+  int grid = 0, nj_max = 0;
+};
+
 struct TcLegendre {
   int T = 0, nlat = 0, nh = 0, nlm = 0, max_fields = 0, bf16 = 0, E = 4, eb = 4, KC = 32;
   int ntile_s = 0, ntile_a = 0, kpad_a = 0;
   unsigned char *tabPs = nullptr, *tabHs = nullptr, *tabPa = nullptr, *tabHa = nullptr;
   unsigned char* B = nullptr;
-  float* D = nullptr;
   int* err = nullptr;
   const double *w = nullptr, *wq = nullptr;
-  // synthesis jobs (scalar uses the P half), analysis jobs; job lists and D maps per variant
-  Job *jobs_s = nullptr, *jobs_a = nullptr;
-  int njobs_s = 0, njobs_a = 0, njobs_sP = 0, njobs_aP = 0;
-  int *dmap_s = nullptr, *dmap_a = nullptr;   // [m*ntile+tile][tab] -> D offset or -1 (synthesis, analysis)
+  // launch plans: [synthesis, analysis][scalar (P jobs), vector ((P, H) pairs)]
+  Sched sched[2][2];
   int *boff_s = nullptr, *kpad_s = nullptr, *boff_a = nullptr;
   int kpad_smax = 0;  // largest K extent of a synthesis B operand
   int nsm = 0;
@@ -477,6 +554,46 @@ struct TcLegendre {
 };
 
 static int tc_fail(const char* what, cudaError_t e) { return cuda_fail(e, what); }
+
+// Assigns units (one job, or a (P, H) pair when H is given; cost = A bytes, rows x K) to
+// min(units, nsm) CTAs: longest first, each to the least-loaded CTA so far; a CTA runs its
+// units in that order.
+static cudaError_t make_sched(const std::vector<Job>& P, const std::vector<Job>* H, int nsm, Sched& sc) {
+  const int nu = (int)P.size();
+  const int grid = std::max(1, std::min(nu, nsm));
+  auto cost = [&](int u) { return (long long)P[u].rows * P[u].kpad; };
+  std::vector<int> order(nu);
+  for (int u = 0; u < nu; ++u) order[u] = u;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+  std::vector<long long> load(grid, 0);
+  std::vector<std::vector<int>> per(grid);
+  for (int u : order) {
+    const int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    per[c].push_back(u);
+    load[c] += cost(u);
+  }
+  std::vector<Job> jobs;
+  std::vector<int> off(grid + 1);
+  sc.nj_max = 0;
+  for (int c = 0; c < grid; ++c) {
+    off[c] = (int)jobs.size();
+    for (int u : per[c]) {
+      jobs.push_back(P[u]);
+      if (H) jobs.push_back((*H)[u]);
+    }
+    sc.nj_max = std::max(sc.nj_max, (int)jobs.size() - off[c]);
+  }
+  off[grid] = (int)jobs.size();
+  sc.grid = grid;
+  cudaError_t e;
+  if ((e = cudaMalloc(&sc.jobs, sizeof(Job) * std::max<size_t>(1, jobs.size()))) ||
+      (e = cudaMalloc(&sc.off, sizeof(int) * off.size())))
+    return e;
+  if ((e = cudaMemcpy(sc.jobs, jobs.data(), sizeof(Job) * jobs.size(), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(sc.off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice)))
+    return e;
+  return cudaSuccess;
+}
 
 int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const double* w, const double* wq,
                        int T, int nlat, int max_fields, bool bf16, cudaStream_t stream) {
@@ -496,17 +613,25 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
   t->wq = wq;
   const int KC = t->KC, eb = t->eb;
   const size_t chunk = 128ull * KC * eb;
+  cudaError_t e;
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if ((e = cudaDeviceGetAttribute(&t->nsm, cudaDevAttrMultiProcessorCount, dev))) {
+      tc_legendre_destroy(t);
+      return tc_fail("cudaDeviceGetAttribute(SM count)", e);
+    }
+  }
   t->ntile_s = (t->nh + 127) / 128;
+  const int ncols_max = TC_MAXCOL;
+  const int kstep = bf16 ? 16 : 8;  // MMA K per instruction
   // ---- synthesis jobs: (m, tile, tab); rows = northern latitudes of the tile, K = all degrees
   // of m; B = [c | (-1)^(n-m) c] gives the northern and the southern values in one job -------
   std::vector<TabJob> tj;
-  std::vector<Job> js;
-  std::vector<int> dmap_s((T + 1) * t->ntile_s * 2, -1), boff_s(T + 1), kpad_s(T + 1);
+  std::vector<Job> jsP, jsH;  // aligned: entry u of both is the same (m, tile)
+  std::vector<int> boff_s(T + 1), kpad_s(T + 1);
   long long aoff = 0;
-  int boff = 0, doff = 0;
-  const int ncols_max = TC_MAXCOL;
-  std::vector<Job> jsP, jsH;
-  const int kstep = bf16 ? 16 : 8;  // MMA K per instruction
+  int boff = 0;
   for (int m = 0; m <= T; ++m) {
     const int K = T + 1 - m;
     const int kpad = (K + kstep - 1) / kstep * kstep;  // K padded to whole k-steps only
@@ -516,39 +641,26 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
     kpad_s[m] = kpad;
     boff += 2 * ncols_max * kpad * eb;
     for (int tile = 0; tile < t->ntile_s; ++tile) {
-      tj.push_back(TabJob{aoff, m, 0, tile, nchunk, kl});
-      for (int tab = 0; tab < 2; ++tab) {
-        Job j{aoff, boff_s[m], doff, nchunk, kpad, tab, kl};
-        (tab ? jsH : jsP).push_back(j);
-        dmap_s[(m * t->ntile_s + tile) * 2 + tab] = doff;
-        doff += 128 * 2 * ncols_max;
-      }
-      aoff += (long long)(nchunk - 1) * chunk + 128LL * kl * eb;
+      const int rows = std::min(128, (t->nh - 128 * tile + 7) / 8 * 8);
+      tj.push_back(TabJob{aoff, m, rows, tile, nchunk, kl});
+      jsP.push_back(Job{aoff, boff_s[m], m, tile, nchunk, kpad, 0, kl, rows});
+      jsH.push_back(Job{aoff, boff_s[m], m, tile, nchunk, kpad, 1, kl, rows});
+      aoff += (long long)rows * ((nchunk - 1) * KC + kl) * eb;
     }
   }
   const long long tab_s_bytes = aoff;
   const int bsz_s = boff;
-  const int dsz_s = doff;
-  auto bylen = [](const Job& a, const Job& b) { return a.nchunk > b.nchunk; };
-  std::stable_sort(jsP.begin(), jsP.end(), bylen);
-  std::stable_sort(jsH.begin(), jsH.end(), bylen);
-  t->njobs_sP = (int)jsP.size();
-  js = jsP;
-  js.insert(js.end(), jsH.begin(), jsH.end());
-  t->njobs_s = (int)js.size();
   // ---- analysis jobs: (m, degree tile, tab), rows = degrees of both parities, K = northern
-  // latitudes; B = [N + S | N - S] of zonal order m (2 ncols columns) ----------------------
+  // latitudes; B = [N + S | N - S] of each field of zonal order m --------------------------
   t->kpad_a = (t->nh + kstep - 1) / kstep * kstep;
   const int nchunk_a = (t->kpad_a + KC - 1) / KC;
   const int kl_a = t->kpad_a - (nchunk_a - 1) * KC;
-  const int ntile_a = (T + 1 + 127) / 128;
-  t->ntile_a = ntile_a;
+  t->ntile_a = (T + 1 + 127) / 128;
   std::vector<TabJob> ta;
   std::vector<Job> jaP, jaH;
-  std::vector<int> dmap_a((T + 1) * ntile_a * 2, -1), boff_a(T + 1);
+  std::vector<int> boff_a(T + 1);
   aoff = 0;
   boff = 0;
-  doff = 0;
   for (int m = 0; m <= T; ++m) {
     boff_a[m] = boff;
     boff += 2 * ncols_max * t->kpad_a * eb;
@@ -557,31 +669,21 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
     const int K = T + 1 - m;
     const int ntiles = (K + 127) / 128;
     for (int tile = 0; tile < ntiles; ++tile) {
-      ta.push_back(TabJob{aoff, m, 0, tile, nchunk_a, kl_a});
-      for (int tab = 0; tab < 2; ++tab) {
-        Job j{aoff, boff_a[m], doff, nchunk_a, t->kpad_a, tab, kl_a};
-        (tab ? jaH : jaP).push_back(j);
-        dmap_a[(m * ntile_a + tile) * 2 + tab] = doff;
-        doff += 128 * 2 * ncols_max;
-      }
-      aoff += (long long)(nchunk_a - 1) * chunk + 128LL * kl_a * eb;
+      const int rows = std::min(128, (K - 128 * tile + 7) / 8 * 8);
+      ta.push_back(TabJob{aoff, m, rows, tile, nchunk_a, kl_a});
+      jaP.push_back(Job{aoff, boff_a[m], m, tile, nchunk_a, t->kpad_a, 0, kl_a, rows});
+      jaH.push_back(Job{aoff, boff_a[m], m, tile, nchunk_a, t->kpad_a, 1, kl_a, rows});
+      aoff += (long long)rows * ((nchunk_a - 1) * KC + kl_a) * eb;
     }
   }
   const long long tab_a_bytes = aoff;
   const int bsz_a = boff;
-  const int dsz = std::max(dsz_s, doff);
-  t->njobs_aP = (int)jaP.size();
-  std::vector<Job> ja = jaP;
-  ja.insert(ja.end(), jaH.begin(), jaH.end());
-  t->njobs_a = (int)ja.size();
-  // the largest B operand of any call (analysis of a vector pair: 2 x 4 max_fields columns
-  // over all latitudes) must fit one B buffer and two ring stages in shared memory
+  for (int v : kpad_s) t->kpad_smax = std::max(t->kpad_smax, v);
+  // the largest B operand of any call (a vector pair: 2 x 4 max_fields columns over all
+  // latitudes or all degrees) must fit one B buffer and two ring stages in shared memory
   {
     auto ncols_of = [](int nf, int cpf) { return std::max(16, (nf * cpf + 15) / 16 * 16); };
-    int kpad_smax = 0;
-    for (int v : kpad_s) kpad_smax = std::max(kpad_smax, v);
-    const size_t bmax = std::max((size_t)ncols_of(max_fields, 4) * t->kpad_a * 2 * eb,
-                                 (size_t)ncols_of(2 * max_fields, 4) * kpad_smax * eb);
+    const size_t bmax = (size_t)ncols_of(2 * max_fields, 4) * std::max(t->kpad_a, t->kpad_smax) * eb;
     if (bmax + 2 * chunk + 4096 > TC_SMEM_BUDGET) {
       tc_legendre_destroy(t);
       return fail(REXI_EINVAL,
@@ -589,20 +691,17 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
                   "use fewer fields per call", nlat, max_fields);
     }
   }
-  // ---- device buffers ---------------------------------------------------------------------
+  // ---- device buffers and launch plans ------------------------------------------------------
   TabJob *d_tj = nullptr, *d_ta = nullptr;
-  cudaError_t e;
   if ((e = cudaMalloc(&t->tabPs, tab_s_bytes)) || (e = cudaMalloc(&t->tabHs, tab_s_bytes)) ||
       (e = cudaMalloc(&t->tabPa, tab_a_bytes)) || (e = cudaMalloc(&t->tabHa, tab_a_bytes)) ||
-      (e = cudaMalloc(&t->B, std::max(bsz_s, bsz_a))) || (e = cudaMalloc(&t->D, sizeof(float) * (size_t)dsz)) ||
-      (e = cudaMalloc(&t->err, sizeof(int))) || (e = cudaMalloc(&t->jobs_s, sizeof(Job) * js.size())) ||
-      (e = cudaMalloc(&t->jobs_a, sizeof(Job) * ja.size())) ||
-      (e = cudaMalloc(&t->dmap_s, sizeof(int) * dmap_s.size())) ||
-      (e = cudaMalloc(&t->dmap_a, sizeof(int) * dmap_a.size())) ||
+      (e = cudaMalloc(&t->B, std::max(bsz_s, bsz_a))) || (e = cudaMalloc(&t->err, sizeof(int))) ||
       (e = cudaMalloc(&t->boff_s, sizeof(int) * boff_s.size())) ||
       (e = cudaMalloc(&t->kpad_s, sizeof(int) * kpad_s.size())) ||
       (e = cudaMalloc(&t->boff_a, sizeof(int) * boff_a.size())) ||
-      (e = cudaMalloc(&d_tj, sizeof(TabJob) * tj.size())) || (e = cudaMalloc(&d_ta, sizeof(TabJob) * ta.size()))) {
+      (e = cudaMalloc(&d_tj, sizeof(TabJob) * tj.size())) || (e = cudaMalloc(&d_ta, sizeof(TabJob) * ta.size())) ||
+      (e = make_sched(jsP, nullptr, t->nsm, t->sched[0][0])) || (e = make_sched(jsP, &jsH, t->nsm, t->sched[0][1])) ||
+      (e = make_sched(jaP, nullptr, t->nsm, t->sched[1][0])) || (e = make_sched(jaP, &jaH, t->nsm, t->sched[1][1]))) {
     cudaGetLastError();
     tc_legendre_destroy(t);
     cudaFree(d_tj);
@@ -610,10 +709,6 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
     return fail(REXI_ENOMEM, "tensor-core Legendre tables: cudaMalloc failed: %s", cudaGetErrorString(e));
   }
   cudaMemset(t->err, 0, sizeof(int));
-  cudaMemcpy(t->jobs_s, js.data(), sizeof(Job) * js.size(), cudaMemcpyHostToDevice);
-  cudaMemcpy(t->jobs_a, ja.data(), sizeof(Job) * ja.size(), cudaMemcpyHostToDevice);
-  cudaMemcpy(t->dmap_s, dmap_s.data(), sizeof(int) * dmap_s.size(), cudaMemcpyHostToDevice);
-  cudaMemcpy(t->dmap_a, dmap_a.data(), sizeof(int) * dmap_a.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(t->boff_s, boff_s.data(), sizeof(int) * boff_s.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(t->kpad_s, kpad_s.data(), sizeof(int) * kpad_s.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(t->boff_a, boff_a.data(), sizeof(int) * boff_a.size(), cudaMemcpyHostToDevice);
@@ -630,13 +725,6 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
     tc_legendre_destroy(t);
     return tc_fail("tensor-core Legendre table kernels", e);
   }
-  for (int v : kpad_s) t->kpad_smax = std::max(t->kpad_smax, v);
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if ((e = cudaDeviceGetAttribute(&t->nsm, cudaDevAttrMultiProcessorCount, dev))) {
-    tc_legendre_destroy(t);
-    return tc_fail("cudaDeviceGetAttribute(SM count)", e);
-  }
   if ((e = cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_BUDGET)) ||
       (e = cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_BUDGET))) {
     tc_legendre_destroy(t);
@@ -648,29 +736,47 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
 
 void tc_legendre_destroy(TcLegendre* t) {
   if (!t) return;
-  for (void* p : {(void*)t->tabPs, (void*)t->tabHs, (void*)t->tabPa, (void*)t->tabHa, (void*)t->B, (void*)t->D,
-                  (void*)t->err, (void*)t->jobs_s, (void*)t->jobs_a, (void*)t->dmap_s, (void*)t->dmap_a,
+  for (void* p : {(void*)t->tabPs, (void*)t->tabHs, (void*)t->tabPa, (void*)t->tabHa, (void*)t->B, (void*)t->err,
                   (void*)t->boff_s, (void*)t->kpad_s, (void*)t->boff_a})
     cudaFree(p);
+  for (auto& row : t->sched)
+    for (Sched& sc : row) {
+      cudaFree(sc.jobs);
+      cudaFree(sc.off);
+    }
   delete t;
 }
 
-static int gemm(TcLegendre* t, bool synth, bool both_tabs, int ncols, cudaStream_t s) {
+// One GEMM launch with the fused epilogue: ncols = MMA N (the real columns 2 nf cpf, padded to
+// a multiple of 16; the padding columns of B are never written and their sums never read).
+static int gemm(TcLegendre* t, bool synth, bool vector, int nf, double2* out0, double2* out1, double inv_a,
+                cudaStream_t s) {
+  const int cpf = vector ? 4 : 2;
+  const int ncols = std::max(16, (2 * nf * cpf + 15) / 16 * 16);
+  const Sched& sc = t->sched[synth ? 0 : 1][vector ? 1 : 0];
   GemmArgs g;
   g.tabP = synth ? t->tabPs : t->tabPa;
   g.tabH = synth ? t->tabHs : t->tabHa;
   g.B = t->B;
-  g.D = t->D;
-  g.jobs = synth ? t->jobs_s : t->jobs_a;
-  g.njobs = both_tabs ? (synth ? t->njobs_s : t->njobs_a) : (synth ? t->njobs_sP : t->njobs_aP);
+  g.jobs = sc.jobs;
+  g.cta_off = sc.off;
   g.ncols = ncols;
   g.bf16 = t->bf16;
+  g.synth = synth ? 1 : 0;
+  g.pair = vector ? 1 : 0;
+  g.out0 = out0;
+  g.out1 = out1;
+  g.T = t->T;
+  g.nlat = t->nlat;
+  g.nlm = t->nlm;
+  g.nf = nf;
+  g.cpf = cpf;
+  g.inv_a = inv_a;
   g.err = t->err;
-  // two B buffers of the largest B operand of the call, then as many A stages as fit
+  g.nj_max = sc.nj_max;
+  // B buffers of the largest B operand of the call, then as many A stages as fit
   const size_t chunk = 128ull * t->KC * t->eb;
   const size_t bslot = ((size_t)ncols * (synth ? t->kpad_smax : t->kpad_a) * t->eb + 127) / 128 * 128;
-  const int grid = std::max(1, std::min(g.njobs, t->nsm));
-  g.nj_max = (g.njobs + grid - 1) / grid;
   const size_t jobs_bytes = sizeof(Job) * (size_t)g.nj_max;
   auto fixed = [&](int nb) { return nb * bslot + 8 * (2 * TC_MAXSTAGES + 2 * nb + 2 * TC_NJB + 2) + jobs_bytes; };
   // B buffers: 4 when that leaves >= 4 ring stages, else 2, else 1 (>= 2 ring stages always)
@@ -682,93 +788,53 @@ static int gemm(TcLegendre* t, bool synth, bool both_tabs, int ncols, cudaStream
       (size_t)g.stages * chunk + g.nb * bslot + 8 * (2 * g.stages + 2 * g.nb + 2 * TC_NJB + 2) + jobs_bytes;
   {
     const int ph = t->prof ? t->prof->begin(2) : -1;
-    if (t->bf16) k_tc_gemm<true><<<grid, TC_THREADS, smem, s>>>(g);
-    else k_tc_gemm<false><<<grid, TC_THREADS, smem, s>>>(g);
+    if (t->bf16) k_tc_gemm<true><<<sc.grid, TC_THREADS, smem, s>>>(g);
+    else k_tc_gemm<false><<<sc.grid, TC_THREADS, smem, s>>>(g);
     if (t->prof) t->prof->end(ph);
   }
   cudaError_t e = cudaGetLastError();
   return e ? cuda_fail(e, "k_tc_gemm launch") : REXI_OK;
 }
 
-static int ncols_for(int nf, int cpf) {
-  const int c = nf * cpf;
-  return std::max(16, (c + 15) / 16 * 16);
+// B packing launches: a thread per (K group of E elements, real column pair), 128 per block
+static void pack_synth(TcLegendre* t, const double2* s0, const double2* s1, int nf, int cpf, cudaStream_t s) {
+  const int np = nf * cpf / 2, groups = t->kpad_smax / t->E;
+  const dim3 grid((groups * np + 127) / 128, t->T + 1);
+  const int ph = t->prof ? t->prof->begin(1) : -1;
+  if (t->bf16) k_tc_bsynth<true><<<grid, 128, 0, s>>>(s0, s1, t->B, t->boff_s, t->kpad_s, t->T, t->nlm, nf, cpf);
+  else k_tc_bsynth<false><<<grid, 128, 0, s>>>(s0, s1, t->B, t->boff_s, t->kpad_s, t->T, t->nlm, nf, cpf);
+  if (t->prof) t->prof->end(ph);
+}
+static void pack_anal(TcLegendre* t, const double2* F0, const double2* F1, const double* wts, int nf, int cpf,
+                      cudaStream_t s) {
+  const int np = nf * cpf / 2, groups = t->kpad_a / t->E;
+  const dim3 grid((groups * np + 127) / 128, t->T + 1);
+  const int ph = t->prof ? t->prof->begin(1) : -1;
+  if (t->bf16) k_tc_banal<true><<<grid, 128, 0, s>>>(F0, F1, wts, t->B, t->boff_a, t->kpad_a, t->T, t->nlat, nf, cpf);
+  else k_tc_banal<false><<<grid, 128, 0, s>>>(F0, F1, wts, t->B, t->boff_a, t->kpad_a, t->T, t->nlat, nf, cpf);
+  if (t->prof) t->prof->end(ph);
 }
 
 int tc_leg_synth(TcLegendre* t, const double2* spec, double2* F, int nf, cudaStream_t s) {
-  const int nc = ncols_for(2 * nf, 2);  // northern and southern columns
-  {
-    const int ph = t->prof ? t->prof->begin(1) : -1;
-    k_tc_bsynth<<<t->T + 1, 256, 0, s>>>(spec, spec, t->B, t->boff_s, t->kpad_s, t->T, t->nlm, nf, 2, nc, t->bf16);
-    if (t->prof) t->prof->end(ph);
-  }
-  int rc = gemm(t, true, false, nc, s);
-  if (rc) return rc;
-  {
-    const int ph = t->prof ? t->prof->begin(3) : -1;
-    k_tc_esynth<<<dim3((t->nh + 127) / 128, t->T + 1), 128, 0, s>>>(t->D, t->dmap_s, F, F, t->T, t->nlat, nf, 2, nc,
-                                                                     t->ntile_s, 0, 0.0);
-    if (t->prof) t->prof->end(ph);
-  }
-  return REXI_OK;
+  pack_synth(t, spec, spec, nf, 2, s);
+  return gemm(t, true, false, nf, F, F, 0.0, s);
 }
 
 int tc_leg_synth_uv(TcLegendre* t, const double2* psi, const double2* chi, double2* FU, double2* FV, int nf,
                     double inv_a, cudaStream_t s) {
-  const int nc = ncols_for(2 * nf, 4);  // northern and southern columns
-  {
-    const int ph = t->prof ? t->prof->begin(1) : -1;
-    k_tc_bsynth<<<t->T + 1, 256, 0, s>>>(psi, chi, t->B, t->boff_s, t->kpad_s, t->T, t->nlm, nf, 4, nc, t->bf16);
-    if (t->prof) t->prof->end(ph);
-  }
-  int rc = gemm(t, true, true, nc, s);
-  if (rc) return rc;
-  {
-    const int ph = t->prof ? t->prof->begin(3) : -1;
-    k_tc_esynth<<<dim3((t->nh + 127) / 128, t->T + 1), 128, 0, s>>>(t->D, t->dmap_s, FU, FV, t->T, t->nlat, nf, 4, nc,
-                                                                     t->ntile_s, 1, inv_a);
-    if (t->prof) t->prof->end(ph);
-  }
-  return REXI_OK;
+  pack_synth(t, psi, chi, nf, 4, s);
+  return gemm(t, true, true, nf, FU, FV, inv_a, s);
 }
 
 int tc_leg_anal(TcLegendre* t, const double2* F, double2* spec, int nf, cudaStream_t s) {
-  const int nc = ncols_for(nf, 2);
-  {
-    const int ph = t->prof ? t->prof->begin(1) : -1;
-    k_tc_banal<<<t->T + 1, 128, 0, s>>>(F, F, t->w, t->B, t->boff_a, t->kpad_a, t->T, t->nlat, nf, 2, nc,
-                                                 t->bf16);
-    if (t->prof) t->prof->end(ph);
-  }
-  int rc = gemm(t, false, false, 2 * nc, s);  // columns: N + S block, N - S block
-  if (rc) return rc;
-  {
-    const int ph = t->prof ? t->prof->begin(3) : -1;
-    k_tc_eanal<<<dim3((t->T + 1 + 127) / 128, t->T + 1), 128, 0, s>>>(t->D, t->dmap_a, spec, spec, t->T, t->nlm, nf,
-                                                                       2, nc, t->ntile_a, 0, 0.0);
-    if (t->prof) t->prof->end(ph);
-  }
-  return REXI_OK;
+  pack_anal(t, F, F, t->w, nf, 2, s);
+  return gemm(t, false, false, nf, spec, spec, 0.0, s);
 }
 
 int tc_leg_anal_divcurl(TcLegendre* t, const double2* FA, const double2* FB, double2* dv, double2* cu, int nf,
                         double inv_a, cudaStream_t s) {
-  const int nc = ncols_for(nf, 4);
-  {
-    const int ph = t->prof ? t->prof->begin(1) : -1;
-    k_tc_banal<<<t->T + 1, 128, 0, s>>>(FA, FB, t->wq, t->B, t->boff_a, t->kpad_a, t->T, t->nlat, nf, 4, nc,
-                                                 t->bf16);
-    if (t->prof) t->prof->end(ph);
-  }
-  int rc = gemm(t, false, true, 2 * nc, s);  // columns: N + S block, N - S block
-  if (rc) return rc;
-  {
-    const int ph = t->prof ? t->prof->begin(3) : -1;
-    k_tc_eanal<<<dim3((t->T + 1 + 127) / 128, t->T + 1), 128, 0, s>>>(t->D, t->dmap_a, dv, cu, t->T, t->nlm, nf, 4,
-                                                                       nc, t->ntile_a, 1, inv_a);
-    if (t->prof) t->prof->end(ph);
-  }
-  return REXI_OK;
+  pack_anal(t, FA, FB, t->wq, nf, 4, s);
+  return gemm(t, false, true, nf, dv, cu, inv_a, s);
 }
 
 void tc_legendre_set_prof(TcLegendre* t, StageProf* prof) {
