@@ -12,10 +12,13 @@
 // (register butterflies), two real latitude rows packed into one complex sequence.
 #include <algorithm>
 #include <cmath>
+#include <initializer_list>
+#include <tuple>
 #include <vector>
 
 #include "../../include/sht.h"
 #include "common.cuh"
+#include "sht_fused.cuh"
 #include "sht_tc.cuh"
 
 namespace rexi {
@@ -336,12 +339,25 @@ template <typename C> __device__ __forceinline__ void dft8(C* v, int sign) {
   v[7] = c_sub(e3, o3);
 }
 
+// Segments of one FFT launch: blockIdx.y in [start[s], start[s + 1]) is field y - start[s] of
+// segment s, whose Fourier coefficients are F[s] ([nf_s][T+1][nlat]) and grid rows g[s]
+// ([nf_s][nlat][nlon]); unused segments have start[s] = start[s + 1] = the field total.
+struct FftSegs {
+  double2* F[3];
+  double* g[3];
+  int start[4];
+};
+
+// padded shared-memory index: one spare slot per 8 elements, so that the stride-R stores of
+// the early passes spread over the banks
+__device__ __forceinline__ int fpad(int i) { return i + (i >> 3); }
+__host__ __device__ constexpr int fft_padded(int n) { return n + (n >> 3) + 1; }
+
 // One Stockham pass of radix R (2, 3, 4 or 8): for j < n / R, jm = j mod Ns, q = j / Ns, the
-// R inputs a[j + r n/R] times the twiddles w^{r jm stride} are transformed and written to
-// b[q Ns R + jm + r Ns].
-template <typename C, int R>
-__device__ __forceinline__ void fft_pass(const C* a, C* b, int n, int Ns, unsigned mg, const C* __restrict__ tw,
-                                         int sign) {
+// R inputs src(j + r n/R) times the twiddles w^{r jm stride} are transformed and written to
+// dst(q Ns R + jm + r Ns).
+template <typename C, int R, typename Src, typename Dst>
+__device__ __forceinline__ void fft_pass(Src src, Dst dst, int n, int Ns, unsigned mg, const C* tw, int sign) {
   using Rt = typename Cx<C>::R;
   const int nb = n / R;
   const int stride = n / (Ns * R);
@@ -350,9 +366,10 @@ __device__ __forceinline__ void fft_pass(const C* a, C* b, int n, int Ns, unsign
     const int jm = j - q * Ns;
     C v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      v[r] = a[j + r * nb];
-      if (r > 0 && jm) {
+    for (int r = 0; r < R; ++r) v[r] = src(j + r * nb);
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      if (jm) {
         C t = tw[r * jm * stride];  // r jm stride < n
         if (sign > 0) t.y = -t.y;
         v[r] = c_mul(v[r], t);
@@ -376,93 +393,142 @@ __device__ __forceinline__ void fft_pass(const C* a, C* b, int n, int Ns, unsign
     }
     const int base = q * Ns * R + jm;
 #pragma unroll
-    for (int r = 0; r < R; ++r) b[base + r * Ns] = v[r];
+    for (int r = 0; r < R; ++r) dst(base + r * Ns, v[r]);
   }
 }
 
-// in-place on two shared buffers; returns the buffer holding the result.  sign = -1 forward,
-// +1 inverse (no scaling).  tw[k] = e^{-2 pi i k / n}.
-template <typename C>
-__device__ C* fft_smem(C* a, C* b, const FftPlan& fp, const C* __restrict__ tw, int sign) {
-  const int n = fp.n;
+template <typename C, typename Src, typename Dst>
+__device__ __forceinline__ void fft_pass_r(int R, Src src, Dst dst, int n, int Ns, unsigned mg, const C* tw,
+                                           int sign) {
+  if (R == 8) fft_pass<C, 8>(src, dst, n, Ns, mg, tw, sign);
+  else if (R == 4) fft_pass<C, 4>(src, dst, n, Ns, mg, tw, sign);
+  else if (R == 2) fft_pass<C, 2>(src, dst, n, Ns, mg, tw, sign);
+  else fft_pass<C, 3>(src, dst, n, Ns, mg, tw, sign);
+}
+
+// All passes of one length-n transform (sign = -1 forward, +1 inverse, no scaling; tw[k] =
+// e^{-2 pi i k / n}).  The first pass reads its inputs through src (global memory); the passes
+// in between go through the padded shared buffers a and b; the last pass writes through dst,
+// or, with LAST_SMEM, into a shared buffer whose address is returned (padded indices).
+template <typename C, bool LAST_SMEM, typename Src, typename Dst>
+__device__ C* fft_run(Src src, Dst dst, C* a, C* b, const FftPlan& fp, const C* tw, int sign) {
+  const int n = fp.n, S = fp.nrad;
+  C* cur = a;  // holds the input of the next pass (after the first)
+  C* nxt = b;
   int Ns = 1;
-  for (int s = 0; s < fp.nrad; ++s) {
+  for (int s = 0; s < S; ++s) {
     const int R = fp.rad[s];
-    if (R == 8) fft_pass<C, 8>(a, b, n, Ns, fp.magic[s], tw, sign);
-    else if (R == 4) fft_pass<C, 4>(a, b, n, Ns, fp.magic[s], tw, sign);
-    else if (R == 2) fft_pass<C, 2>(a, b, n, Ns, fp.magic[s], tw, sign);
-    else fft_pass<C, 3>(a, b, n, Ns, fp.magic[s], tw, sign);
+    const unsigned mg = fp.magic[s];
+    C* const rb = cur;
+    C* const wb = nxt;
+    auto rd = [rb](int i) { return rb[fpad(i)]; };
+    auto wr = [wb](int i, C v) { wb[fpad(i)] = v; };
+    const bool last = s == S - 1;
+    if (s == 0) {
+      if (last && !LAST_SMEM) fft_pass_r<C>(R, src, dst, n, Ns, mg, tw, sign);
+      else fft_pass_r<C>(R, src, wr, n, Ns, mg, tw, sign);
+    } else {
+      if (last && !LAST_SMEM) fft_pass_r<C>(R, rd, dst, n, Ns, mg, tw, sign);
+      else fft_pass_r<C>(R, rd, wr, n, Ns, mg, tw, sign);
+    }
     __syncthreads();
-    C* t = a;
-    a = b;
-    b = t;
+    cur = wb;
+    nxt = rb;
     Ns *= R;
   }
-  return a;
+  return cur;
+}
+
+__device__ __forceinline__ int fft_seg(const FftSegs& sg, int y) {
+  return (y >= sg.start[1]) + (y >= sg.start[2]);
 }
 
 // synthesis: F[field][m][nlat] (m <= T) -> grid[field][nlat][nlon], two latitude rows per block
+// (row j0 in the real part, j0 + 1 in the imaginary part of one complex sequence)
 template <typename C>
-__global__ void __launch_bounds__(FTH) k_fft_synth(const double2* __restrict__ F, double* __restrict__ grid,
-                                                   FftPlan fp, const C* __restrict__ tw, int T, int nlat) {
+__device__ __forceinline__ void fft_synth_block(const FftSegs& sg, const FftPlan& fp, const C* __restrict__ tw, int T,
+                                                int nlat) {
   extern __shared__ __align__(16) unsigned char fsm[];
   using R = typename Cx<C>::R;
-  const int n = fp.n;
-  const int f = blockIdx.y;
-  const int j0 = 2 * blockIdx.x;
+  const int n = fp.n, np = fft_padded(n);
   C* a = reinterpret_cast<C*>(fsm);
-  C* b = a + n;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) a[k] = Cx<C>::make(R(0), R(0));
-  __syncthreads();
-  const double2* in = F + (size_t)f * (T + 1) * nlat;
-#pragma unroll 2
+  C* b = a + np;
+  const int s = fft_seg(sg, blockIdx.y), f = blockIdx.y - sg.start[s];
+  const int j0 = 2 * blockIdx.x;
+  const double2* in = sg.F[s] + (size_t)f * (T + 1) * nlat;
+  double* r0 = sg.g[s] + ((size_t)f * nlat + j0) * n;
+  double* r1 = r0 + n;
+  // input element k: A + i B of order m = k (k <= T), conj(A) + i conj(B) of m = n - k
+  // (k >= n - T), else 0; A, B = latitudes j0, j0 + 1 of order m, one aligned 32-byte load per
+  // m for both entries.  Filled into the padded buffer b, which the first pass reads.
   for (int m = threadIdx.x; m <= T; m += blockDim.x) {
-    // latitudes j0, j0 + 1 of order m: one aligned 32-byte load (j0 even, rows of nlat even)
     const D4 AB = *reinterpret_cast<const D4*>(in + (size_t)m * nlat + j0);
-    const double2 A = make_double2(AB.x, AB.y), B = make_double2(AB.z, AB.w);
     if (m == 0) {
-      a[0] = Cx<C>::make(R(A.x), R(B.x));
+      b[0] = Cx<C>::make(R(AB.x), R(AB.z));
     } else {
-      a[m] = Cx<C>::make(R(A.x - B.y), R(A.y + B.x));      // A + i B
-      a[n - m] = Cx<C>::make(R(A.x + B.y), R(B.x - A.y));  // conj(A) + i conj(B)
+      b[fpad(m)] = Cx<C>::make(R(AB.x - AB.w), R(AB.y + AB.z));
+      b[fpad(n - m)] = Cx<C>::make(R(AB.x + AB.w), R(AB.z - AB.y));
     }
   }
+  for (int k = T + 1 + threadIdx.x; k < n - T; k += blockDim.x) b[fpad(k)] = Cx<C>::make(R(0), R(0));
   __syncthreads();
-  const C* z = fft_smem<C>(a, b, fp, tw, +1);
-  double* r0 = grid + ((size_t)f * nlat + j0) * n;
-  double* r1 = r0 + n;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    r0[k] = (double)z[k].x;
-    r1[k] = (double)z[k].y;
-  }
+  const C* bin = b;
+  auto src = [bin](int k) -> C { return bin[fpad(k)]; };
+  auto dst = [r0, r1](int k, C v) {
+    r0[k] = (double)v.x;
+    r1[k] = (double)v.y;
+  };
+  fft_run<C, false>(src, dst, b, a, fp, tw, +1);  // the first pass reads b and writes a
 }
 
 // analysis: grid[field][nlat][nlon] -> F[field][m][nlat] = (2 pi / n) sum_k f e^{-i m lambda_k}
 template <typename C>
-__global__ void __launch_bounds__(FTH) k_fft_anal(const double* __restrict__ grid, double2* __restrict__ F,
-                                                  FftPlan fp, const C* __restrict__ tw, int T, int nlat) {
+__device__ __forceinline__ void fft_anal_block(const FftSegs& sg, const FftPlan& fp, const C* __restrict__ tw, int T,
+                                               int nlat) {
   extern __shared__ __align__(16) unsigned char fsm[];
   using R = typename Cx<C>::R;
-  const int n = fp.n;
-  const int f = blockIdx.y;
-  const int j0 = 2 * blockIdx.x;
+  const int n = fp.n, np = fft_padded(n);
   C* a = reinterpret_cast<C*>(fsm);
-  C* b = a + n;
-  const double* r0 = grid + ((size_t)f * nlat + j0) * n;
+  C* b = a + np;
+  const int s = fft_seg(sg, blockIdx.y), f = blockIdx.y - sg.start[s];
+  const int j0 = 2 * blockIdx.x;
+  const double* r0 = sg.g[s] + ((size_t)f * nlat + j0) * n;
   const double* r1 = r0 + n;
-#pragma unroll 4
-  for (int k = threadIdx.x; k < n; k += blockDim.x) a[k] = Cx<C>::make(R(__ldg(r0 + k)), R(__ldg(r1 + k)));
-  __syncthreads();
-  const C* z = fft_smem<C>(a, b, fp, tw, -1);
+  auto src = [r0, r1](int k) -> C { return Cx<C>::make(R(__ldg(r0 + k)), R(__ldg(r1 + k))); };
+  auto none = [](int, C) {};
+  const C* z = fft_run<C, true>(src, none, a, b, fp, tw, -1);
   const double sc = 3.14159265358979323846 / n;  // (2 pi / n) / 2
-  double2* out = F + (size_t)f * (T + 1) * nlat;
+  double2* out = sg.F[s] + (size_t)f * (T + 1) * nlat;
   for (int m = threadIdx.x; m <= T; m += blockDim.x) {
-    const C zm = z[m], zn = z[m == 0 ? 0 : n - m];
+    const C zm = z[fpad(m)], zn = z[fpad(m == 0 ? 0 : n - m)];
     // A = (Z_m + conj(Z_{n-m})) / 2,  B = (Z_m - conj(Z_{n-m})) / (2i); one aligned 32-byte store
     *reinterpret_cast<D4*>(out + (size_t)m * nlat + j0) =
         D4{sc * ((double)zm.x + zn.x), sc * ((double)zm.y - zn.y), sc * ((double)zm.y + zn.y),
            -sc * ((double)zm.x - zn.x)};
   }
+}
+
+// FP32 transforms (tensor-core plans) keep six blocks per SM resident; FP64 ones are bound by
+// the FP64 pipe and keep their registers
+__global__ void __launch_bounds__(FTH, 6) k_fft_synth32(const __grid_constant__ FftSegs sg,
+                                                        const __grid_constant__ FftPlan fp,
+                                                        const float2* __restrict__ tw, int T, int nlat) {
+  fft_synth_block<float2>(sg, fp, tw, T, nlat);
+}
+__global__ void __launch_bounds__(FTH) k_fft_synth64(const __grid_constant__ FftSegs sg,
+                                                     const __grid_constant__ FftPlan fp,
+                                                     const double2* __restrict__ tw, int T, int nlat) {
+  fft_synth_block<double2>(sg, fp, tw, T, nlat);
+}
+__global__ void __launch_bounds__(FTH, 6) k_fft_anal32(const __grid_constant__ FftSegs sg,
+                                                       const __grid_constant__ FftPlan fp,
+                                                       const float2* __restrict__ tw, int T, int nlat) {
+  fft_anal_block<float2>(sg, fp, tw, T, nlat);
+}
+__global__ void __launch_bounds__(FTH) k_fft_anal64(const __grid_constant__ FftSegs sg,
+                                                    const __grid_constant__ FftPlan fp,
+                                                    const double2* __restrict__ tw, int T, int nlat) {
+  fft_anal_block<double2>(sg, fp, tw, T, nlat);
 }
 
 // Gauss-Legendre nodes (north to south) and weights: Newton iteration on P_n
@@ -551,8 +617,9 @@ struct sh_plan {
   StageProf prof;            // per-stage event timing (sh_plan_set_profiling)
 };
 
+// two padded work buffers
 static size_t fft_smem(const sh_plan* p) {
-  return (p->fft32 ? sizeof(float2) : sizeof(double2)) * 2 * (size_t)p->d.nlon;
+  return (p->fft32 ? sizeof(float2) : sizeof(double2)) * 2 * (size_t)fft_padded(p->d.nlon);
 }
 
 extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
@@ -608,11 +675,11 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
   k_legendre_table<<<dim3((p->nh + 127) / 128, d.T + 1), 128, 0, p->stream>>>(p->d_mu, p->d_P, p->d_H, d.T, p->nh);
   if ((e = cudaGetLastError())) return bail(cuda_fail(e, "k_legendre_table"));
   if (p->fft32) {
-    e = cudaFuncSetAttribute(k_fft_synth<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p));
-    if (!e) e = cudaFuncSetAttribute(k_fft_anal<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p));
+    e = cudaFuncSetAttribute(k_fft_synth32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p));
+    if (!e) e = cudaFuncSetAttribute(k_fft_anal32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p));
   } else {
-    e = cudaFuncSetAttribute(k_fft_synth<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p));
-    if (!e) e = cudaFuncSetAttribute(k_fft_anal<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p));
+    e = cudaFuncSetAttribute(k_fft_synth64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p));
+    if (!e) e = cudaFuncSetAttribute(k_fft_anal64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p));
   }
   if (e) return bail(cuda_fail(e, "cudaFuncSetAttribute(fft)"));
   if (d.precision != SH_FP64) {
@@ -658,72 +725,99 @@ static int check_call(sh_plan* p, const void* a, const void* b, int nf, const ch
   return REXI_OK;
 }
 
-// Fourier buffer slots: slot 0 = first nf fields, slot 1 = second
-static double2* fslot(sh_plan* p, int s) {
-  return p->d_F + (size_t)s * p->d.max_fields * (p->d.T + 1) * p->d.nlat;
+
+// FFT segments: up to three (Fourier, grid) array pairs of nf_s fields each
+static FftSegs make_segs(std::initializer_list<std::tuple<double2*, double*, int>> list) {
+  FftSegs sg{};
+  int k = 0, tot = 0;
+  sg.start[0] = 0;
+  for (const auto& e : list) {
+    sg.F[k] = std::get<0>(e);
+    sg.g[k] = std::get<1>(e);
+    tot += std::get<2>(e);
+    sg.start[++k] = tot;
+  }
+  for (; k < 3; ++k) sg.start[k + 1] = tot;
+  return sg;
 }
 
-static int launch_fft_synth(sh_plan* p, const double2* F, double* grid, int nf) {
+static void launch_fft_synth(sh_plan* p, const FftSegs& sg) {
   const int ph = p->prof.begin(4);
+  const dim3 grid(p->d.nlat / 2, sg.start[3]);
   if (p->fft32)
-    k_fft_synth<float2><<<dim3(p->d.nlat / 2, nf), FTH, fft_smem(p), p->stream>>>(F, grid, p->fp, p->d_tw32, p->d.T,
-                                                                                p->d.nlat);
+    k_fft_synth32<<<grid, FTH, fft_smem(p), p->stream>>>(sg, p->fp, p->d_tw32, p->d.T, p->d.nlat);
   else
-    k_fft_synth<double2><<<dim3(p->d.nlat / 2, nf), FTH, fft_smem(p), p->stream>>>(F, grid, p->fp, p->d_tw, p->d.T,
-                                                                                 p->d.nlat);
+    k_fft_synth64<<<grid, FTH, fft_smem(p), p->stream>>>(sg, p->fp, p->d_tw, p->d.T, p->d.nlat);
+  p->prof.end(ph);
+}
+static void launch_fft_anal(sh_plan* p, const FftSegs& sg) {
+  const int ph = p->prof.begin(4);
+  const dim3 grid(p->d.nlat / 2, sg.start[3]);
+  if (p->fft32)
+    k_fft_anal32<<<grid, FTH, fft_smem(p), p->stream>>>(sg, p->fp, p->d_tw32, p->d.T, p->d.nlat);
+  else
+    k_fft_anal64<<<grid, FTH, fft_smem(p), p->stream>>>(sg, p->fp, p->d_tw, p->d.T, p->d.nlat);
+  p->prof.end(ph);
+}
+
+// Legendre stages (FP64 kernels or the tensor-core path) between spectra and Fourier arrays
+static int leg_synth(sh_plan* p, const double2* spec, double2* F, int nf) {
+  if (p->tc) return tc_leg_synth(p->tc, spec, F, nf, p->stream);
+  const int ph = p->prof.begin(0);
+  k_leg_synth<<<dim3(p->d.T + 1, nf, (p->nh + LTH - 1) / LTH), LTH, 0, p->stream>>>(p->d_P, spec, F, p->d.T,
+                                                                                  p->d.nlat, p->nlm);
   p->prof.end(ph);
   return REXI_OK;
 }
-static int launch_fft_anal(sh_plan* p, const double* grid, double2* F, int nf) {
-  const int ph = p->prof.begin(4);
-  if (p->fft32)
-    k_fft_anal<float2><<<dim3(p->d.nlat / 2, nf), FTH, fft_smem(p), p->stream>>>(grid, F, p->fp, p->d_tw32, p->d.T,
-                                                                               p->d.nlat);
-  else
-    k_fft_anal<double2><<<dim3(p->d.nlat / 2, nf), FTH, fft_smem(p), p->stream>>>(grid, F, p->fp, p->d_tw, p->d.T,
-                                                                                p->d.nlat);
+static int leg_synth_uv(sh_plan* p, const double2* psi, const double2* chi, double2* FU, double2* FV, int nf) {
+  if (p->tc) return tc_leg_synth_uv(p->tc, psi, chi, FU, FV, nf, 1.0 / p->d.radius, p->stream);
+  const int ph = p->prof.begin(0);
+  k_leg_synth_uv<<<dim3(p->d.T + 1, nf, (p->nh + LTH - 1) / LTH), LTH, 0, p->stream>>>(
+      p->d_P, p->d_H, psi, chi, FU, FV, p->d.T, p->d.nlat, p->nlm, 1.0 / p->d.radius);
   p->prof.end(ph);
   return REXI_OK;
+}
+static int leg_anal(sh_plan* p, const double2* F, double2* spec, int nf) {
+  if (p->tc) return tc_leg_anal(p->tc, F, spec, nf, p->stream);
+  const int ph = p->prof.begin(0);
+  k_leg_anal<<<dim3(p->d.T + 1, nf), ATH, sizeof(double2) * 2 * p->nh, p->stream>>>(p->d_P, p->d_w, F, spec,
+                                                                                    p->d.T, p->d.nlat, p->nlm);
+  p->prof.end(ph);
+  return REXI_OK;
+}
+static int leg_anal_divcurl(sh_plan* p, const double2* FA, const double2* FB, double2* dv, double2* cu, int nf) {
+  if (p->tc) return tc_leg_anal_divcurl(p->tc, FA, FB, dv, cu, nf, 1.0 / p->d.radius, p->stream);
+  const int ph = p->prof.begin(0);
+  k_leg_anal_divcurl<<<dim3(p->d.T + 1, nf), ATH, sizeof(double2) * 4 * p->nh, p->stream>>>(
+      p->d_P, p->d_H, p->d_wq, FA, FB, dv, cu, p->d.T, p->d.nlat, p->nlm, 1.0 / p->d.radius);
+  p->prof.end(ph);
+  return REXI_OK;
+}
+
+// Fourier work slot k (one field) of the plan's buffer of 2 max_fields slots
+static double2* fslot(sh_plan* p, int k) { return p->d_F + (size_t)k * (p->d.T + 1) * p->d.nlat; }
+
+static int launched(const char* who) {
+  cudaError_t e = cudaGetLastError();
+  return e ? cuda_fail(e, who) : REXI_OK;
 }
 
 extern "C" int sh_synthesis(sh_plan* p, const void* spec, void* grid, int nf) {
   int rc = check_call(p, spec, grid, nf, "sh_synthesis");
   if (rc) return rc;
   double2* F = fslot(p, 0);
-  if (p->tc) {
-    rc = tc_leg_synth(p->tc, (const double2*)spec, F, nf, p->stream);
-    if (rc) return rc;
-  } else {
-    {
-      const int ph = p->prof.begin(0);
-      k_leg_synth<<<dim3(p->d.T + 1, nf, (p->nh + LTH - 1) / LTH), LTH, 0, p->stream>>>(
-          p->d_P, (const double2*)spec, F, p->d.T, p->d.nlat, p->nlm);
-      p->prof.end(ph);
-    }
-  }
-  launch_fft_synth(p, F, (double*)grid, nf);
-  cudaError_t e = cudaGetLastError();
-  return e ? cuda_fail(e, "sh_synthesis") : REXI_OK;
+  if ((rc = leg_synth(p, (const double2*)spec, F, nf))) return rc;
+  launch_fft_synth(p, make_segs({{F, (double*)grid, nf}}));
+  return launched("sh_synthesis");
 }
 
 extern "C" int sh_analysis(sh_plan* p, const void* grid, void* spec, int nf) {
   int rc = check_call(p, grid, spec, nf, "sh_analysis");
   if (rc) return rc;
   double2* F = fslot(p, 0);
-  launch_fft_anal(p, (const double*)grid, F, nf);
-  if (p->tc) {
-    rc = tc_leg_anal(p->tc, F, (double2*)spec, nf, p->stream);
-    if (rc) return rc;
-  } else {
-    {
-      const int ph = p->prof.begin(0);
-      k_leg_anal<<<dim3(p->d.T + 1, nf), ATH, sizeof(double2) * 2 * p->nh, p->stream>>>(
-          p->d_P, p->d_w, F, (double2*)spec, p->d.T, p->d.nlat, p->nlm);
-      p->prof.end(ph);
-    }
-  }
-  cudaError_t e = cudaGetLastError();
-  return e ? cuda_fail(e, "sh_analysis") : REXI_OK;
+  launch_fft_anal(p, make_segs({{F, (double*)grid, nf}}));
+  if ((rc = leg_anal(p, F, (double2*)spec, nf))) return rc;
+  return launched("sh_analysis");
 }
 
 extern "C" int sh_synthesis_uv(sh_plan* p, const void* psi, const void* chi, void* U, void* V, int nf) {
@@ -731,23 +825,10 @@ extern "C" int sh_synthesis_uv(sh_plan* p, const void* psi, const void* chi, voi
   if (rc) return rc;
   if (!U || !V) return fail(REXI_EINVAL, "sh_synthesis_uv: null output");
   double2* FU = fslot(p, 0);
-  double2* FV = fslot(p, 1);
-  if (p->tc) {
-    rc = tc_leg_synth_uv(p->tc, (const double2*)psi, (const double2*)chi, FU, FV, nf, 1.0 / p->d.radius, p->stream);
-    if (rc) return rc;
-  } else {
-    {
-      const int ph = p->prof.begin(0);
-      k_leg_synth_uv<<<dim3(p->d.T + 1, nf, (p->nh + LTH - 1) / LTH), LTH, 0, p->stream>>>(
-          p->d_P, p->d_H, (const double2*)psi, (const double2*)chi, FU, FV, p->d.T, p->d.nlat, p->nlm,
-          1.0 / p->d.radius);
-      p->prof.end(ph);
-    }
-  }
-  launch_fft_synth(p, FU, (double*)U, nf);
-  launch_fft_synth(p, FV, (double*)V, nf);
-  cudaError_t e = cudaGetLastError();
-  return e ? cuda_fail(e, "sh_synthesis_uv") : REXI_OK;
+  double2* FV = fslot(p, p->d.max_fields);
+  if ((rc = leg_synth_uv(p, (const double2*)psi, (const double2*)chi, FU, FV, nf))) return rc;
+  launch_fft_synth(p, make_segs({{FU, (double*)U, nf}, {FV, (double*)V, nf}}));
+  return launched("sh_synthesis_uv");
 }
 
 extern "C" int sh_analysis_divcurl(sh_plan* p, const void* A, const void* B, void* dv, void* cu, int nf) {
@@ -755,23 +836,38 @@ extern "C" int sh_analysis_divcurl(sh_plan* p, const void* A, const void* B, voi
   if (rc) return rc;
   if (!dv || !cu) return fail(REXI_EINVAL, "sh_analysis_divcurl: null output");
   double2* FA = fslot(p, 0);
-  double2* FB = fslot(p, 1);
-  launch_fft_anal(p, (const double*)A, FA, nf);
-  launch_fft_anal(p, (const double*)B, FB, nf);
-  if (p->tc) {
-    rc = tc_leg_anal_divcurl(p->tc, FA, FB, (double2*)dv, (double2*)cu, nf, 1.0 / p->d.radius, p->stream);
-    if (rc) return rc;
-  } else {
-    {
-      const int ph = p->prof.begin(0);
-      k_leg_anal_divcurl<<<dim3(p->d.T + 1, nf), ATH, sizeof(double2) * 4 * p->nh, p->stream>>>(
-          p->d_P, p->d_H, p->d_wq, FA, FB, (double2*)dv, (double2*)cu, p->d.T, p->d.nlat, p->nlm,
-          1.0 / p->d.radius);
-      p->prof.end(ph);
-    }
-  }
-  cudaError_t e = cudaGetLastError();
-  return e ? cuda_fail(e, "sh_analysis_divcurl") : REXI_OK;
+  double2* FB = fslot(p, p->d.max_fields);
+  launch_fft_anal(p, make_segs({{FA, (double*)A, nf}, {FB, (double*)B, nf}}));
+  if ((rc = leg_anal_divcurl(p, FA, FB, (double2*)dv, (double2*)cu, nf))) return rc;
+  return launched("sh_analysis_divcurl");
+}
+
+int sh_synth_fused(sh_plan* p, const double2* S, int nf, double* G, const double2* psi, const double2* chi, int nfv,
+                   double* U, double* V) {
+  if (!p || nf < 1 || nfv < 1 || nf > p->d.max_fields || nfv > p->d.max_fields || nf + 2 * nfv > 2 * p->d.max_fields)
+    return fail(REXI_EINVAL, "fused synthesis: %d scalar + 2 x %d vector fields exceed the plan's work slots", nf, nfv);
+  double2* F = fslot(p, 0);
+  double2* FU = fslot(p, nf);
+  double2* FV = fslot(p, nf + nfv);
+  int rc;
+  if ((rc = leg_synth(p, S, F, nf))) return rc;
+  if ((rc = leg_synth_uv(p, psi, chi, FU, FV, nfv))) return rc;
+  launch_fft_synth(p, make_segs({{F, G, nf}, {FU, U, nfv}, {FV, V, nfv}}));
+  return launched("fused synthesis");
+}
+
+int sh_anal_fused(sh_plan* p, const double* A, const double* B, int nfv, double2* dv, double2* cu, const double* G,
+                  int nf, double2* S) {
+  if (!p || nf < 1 || nfv < 1 || nf > p->d.max_fields || nfv > p->d.max_fields || nf + 2 * nfv > 2 * p->d.max_fields)
+    return fail(REXI_EINVAL, "fused analysis: 2 x %d vector + %d scalar fields exceed the plan's work slots", nfv, nf);
+  double2* FA = fslot(p, 0);
+  double2* FB = fslot(p, nfv);
+  double2* FG = fslot(p, 2 * nfv);
+  launch_fft_anal(p, make_segs({{FA, (double*)A, nfv}, {FB, (double*)B, nfv}, {FG, (double*)G, nf}}));
+  int rc;
+  if ((rc = leg_anal_divcurl(p, FA, FB, dv, cu, nfv))) return rc;
+  if ((rc = leg_anal(p, FG, S, nf))) return rc;
+  return launched("fused analysis");
 }
 
 extern "C" int sh_plan_check(sh_plan* p) {

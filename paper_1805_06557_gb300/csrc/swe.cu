@@ -6,6 +6,7 @@
 #include "../../include/sht.h"
 #include "../../include/swe.h"
 #include "common.cuh"
+#include "sht_fused.cuh"
 #include "sht_tc.cuh"
 
 namespace rexi {
@@ -201,7 +202,7 @@ extern "C" int swe_plan_create(const swe_plan_desc* desc, swe_plan** out) {
   sd.nlon = d.nlon;
   sd.radius = d.radius;
   sd.precision = d.sh_precision;
-  sd.max_fields = 2;
+  sd.max_fields = 3;  // Fourier work slots for the fused analysis: A, B (2 each) and KE
   sd.stream = d.stream;
   int rc = sh_plan_create(&sd, &p->sp);
   if (rc) return bail(rc);
@@ -314,16 +315,16 @@ static int nonlinear_update(swe_plan* p, const double2* U, const double2* base, 
     p->prof.end(ph);
   }
   int rc;
-  if ((rc = sh_synthesis(p->sp, U, p->PZ, 2))) return rc;  // Phi', zeta
-  if ((rc = sh_synthesis_uv(p->sp, p->psi, p->chi, p->Ug, p->Vg, 1))) return rc;
+  // Phi', zeta and U, V: one FFT launch for the four fields
+  if ((rc = sh_synth_fused(p->sp, U, 2, p->PZ, p->psi, p->chi, 1, p->Ug, p->Vg))) return rc;
   {
     const int ph = p->prof.begin(0);
     k_swe_products<<<(p->npt + tb - 1) / tb, tb, 0, p->stream>>>(p->PZ, p->Ug, p->Vg, p->c2, p->A, p->B, p->KE,
                                                                 p->d.nlat, p->d.nlon);
     p->prof.end(ph);
   }
-  if ((rc = sh_analysis_divcurl(p->sp, p->A, p->B, p->dv, p->cu, 2))) return rc;
-  if ((rc = sh_analysis(p->sp, p->KE, p->kes, 1))) return rc;
+  // div / curl of A, B (two fields each) and KE: one FFT launch for the five fields
+  if ((rc = sh_anal_fused(p->sp, p->A, p->B, 2, p->dv, p->cu, p->KE, 1, p->kes))) return rc;
   {
     const int ph = p->prof.begin(0);
     k_swe_combine<<<(nlm + tb - 1) / tb, tb, 0, p->stream>>>(base, p->dv, p->cu, p->kes, U, ctab, out, tau, T,
