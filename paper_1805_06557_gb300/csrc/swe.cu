@@ -12,9 +12,10 @@
 namespace rexi {
 namespace {
 
-// psi = lap^-1 zeta, chi = lap^-1 delta with lap Y_n = -n(n+1)/a^2 Y_n; n = 0 -> 0
+// psi = lap^-1 zeta, chi = lap^-1 delta with lap Y_n = -n(n+1)/a^2 Y_n; n = 0 -> 0.
+// ilap[n] = -a^2 / (n(n+1)) (0 for n = 0), formed on the host.
 __global__ void k_inv_lap(const double2* __restrict__ U, double2* __restrict__ psi,
-                          double2* __restrict__ chi, int T, int nlm, double a2) {
+                          double2* __restrict__ chi, int T, int nlm, const double* __restrict__ ilap) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nlm) return;
   int m = 0;
@@ -27,26 +28,28 @@ __global__ void k_inv_lap(const double2* __restrict__ U, double2* __restrict__ p
   }
   m = lo;
   const int n = m + (i - moff(T, m));
-  const double s = n > 0 ? -a2 / (double(n) * (n + 1)) : 0.0;
+  const double s = ilap[n];
   const double2 z = U[nlm + i], d = U[2 * nlm + i];
   psi[i] = make_double2(s * z.x, s * z.y);
   chi[i] = make_double2(s * d.x, s * d.y);
 }
 
-// grid products: A = (Phi U, zeta U), B = (Phi V, zeta V), KE = (U^2 + V^2) / (2 cos^2)
+// grid products: A = (Phi U, zeta U), B = (Phi V, zeta V), KE = (U^2 + V^2) / (2 cos^2);
+// block row blockIdx.y = latitude j, ikc[j] = 1 / (2 cos^2 of latitude j), formed on the host
 __global__ void k_swe_products(const double* __restrict__ PZ, const double* __restrict__ Ug,
-                               const double* __restrict__ Vg, const double* __restrict__ c2,
+                               const double* __restrict__ Vg, const double* __restrict__ ikc,
                                double* __restrict__ A, double* __restrict__ B, double* __restrict__ KE,
                                int nlat, int nlon) {
   const int npt = nlat * nlon;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= npt) return;
+  const int j = blockIdx.y, k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nlon) return;
+  const int i = j * nlon + k;
   const double u = Ug[i], v = Vg[i], ph = PZ[i], ze = PZ[npt + i];
   A[i] = ph * u;
   A[npt + i] = ze * u;
   B[i] = ph * v;
   B[npt + i] = ze * v;
-  KE[i] = (u * u + v * v) / (2.0 * c2[i / nlon]);
+  KE[i] = (u * u + v * v) * ikc[j];
 }
 
 // out = base + tau * N,  N = (-div(Phi V), -div(zeta V), curl(zeta V) + n(n+1)/a^2 KE_s);
@@ -157,7 +160,7 @@ struct swe_plan {
   double2 *psi = nullptr, *chi = nullptr, *Um = nullptr, *Ut = nullptr, *dv = nullptr, *cu = nullptr,
           *kes = nullptr;
   double *PZ = nullptr, *Ug = nullptr, *Vg = nullptr, *A = nullptr, *B = nullptr, *KE = nullptr,
-         *c2 = nullptr;
+         *ikc = nullptr, *ilap = nullptr;
   StageProf prof;  // the step's own grid and spectral kernels (stage 0)
 };
 
@@ -172,7 +175,7 @@ extern "C" int swe_plan_destroy(swe_plan* p) {
   p->prof.release();
   for (void* q : {(void*)p->psi, (void*)p->chi, (void*)p->Um, (void*)p->Ut, (void*)p->dv, (void*)p->cu,
                   (void*)p->kes, (void*)p->PZ, (void*)p->Ug, (void*)p->Vg, (void*)p->A, (void*)p->B,
-                  (void*)p->KE, (void*)p->c2, (void*)p->NU, (void*)p->A3, (void*)p->Ltab})
+                  (void*)p->KE, (void*)p->ikc, (void*)p->ilap, (void*)p->NU, (void*)p->A3, (void*)p->Ltab})
     cudaFree(q);
   delete p;
   return REXI_OK;
@@ -289,16 +292,19 @@ extern "C" int swe_plan_create(const swe_plan_desc* desc, swe_plan** out) {
       (e = cudaMalloc(&p->Ut, s3)) || (e = cudaMalloc(&p->dv, 2 * s1)) || (e = cudaMalloc(&p->cu, 2 * s1)) ||
       (e = cudaMalloc(&p->kes, s1)) || (e = cudaMalloc(&p->PZ, 2 * g1)) || (e = cudaMalloc(&p->Ug, g1)) ||
       (e = cudaMalloc(&p->Vg, g1)) || (e = cudaMalloc(&p->A, 2 * g1)) || (e = cudaMalloc(&p->B, 2 * g1)) ||
-      (e = cudaMalloc(&p->KE, g1)) || (e = cudaMalloc(&p->c2, sizeof(double) * d.nlat)) ||
+      (e = cudaMalloc(&p->KE, g1)) || (e = cudaMalloc(&p->ikc, sizeof(double) * d.nlat)) ||
+      (e = cudaMalloc(&p->ilap, sizeof(double) * (d.T + 1))) ||
       ((d.scheme == SWE_L_REXI_N_ETDRK || d.scheme == SWE_LG_REXI_LC_N_ETDRK) &&
        ((e = cudaMalloc(&p->NU, s3)) || (e = cudaMalloc(&p->A3, s3))))) {
     cudaGetLastError();
     return bail(fail(REXI_ENOMEM, "swe_plan_create: cudaMalloc failed: %s", cudaGetErrorString(e)));
   }
-  std::vector<double> mu(d.nlat), c2(d.nlat);
+  std::vector<double> mu(d.nlat), ikc(d.nlat), ilap(d.T + 1, 0.0);
   sh_plan_get_grid(p->sp, mu.data(), nullptr);
-  for (int j = 0; j < d.nlat; ++j) c2[j] = (1.0 - mu[j]) * (1.0 + mu[j]);
-  if ((e = cudaMemcpy(p->c2, c2.data(), sizeof(double) * d.nlat, cudaMemcpyHostToDevice)))
+  for (int j = 0; j < d.nlat; ++j) ikc[j] = 1.0 / (2.0 * ((1.0 - mu[j]) * (1.0 + mu[j])));
+  for (int n = 1; n <= d.T; ++n) ilap[n] = -(d.radius * d.radius) / (double(n) * (n + 1));
+  if ((e = cudaMemcpy(p->ikc, ikc.data(), sizeof(double) * d.nlat, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(p->ilap, ilap.data(), sizeof(double) * (d.T + 1), cudaMemcpyHostToDevice)))
     return bail(cuda_fail(e, "swe_plan_create: cudaMemcpy"));
   *out = p;
   return REXI_OK;
@@ -311,7 +317,7 @@ static int nonlinear_update(swe_plan* p, const double2* U, const double2* base, 
   const int tb = 256;
   {
     const int ph = p->prof.begin(0);
-    k_inv_lap<<<(nlm + tb - 1) / tb, tb, 0, p->stream>>>(U, p->psi, p->chi, T, nlm, p->d.radius * p->d.radius);
+    k_inv_lap<<<(nlm + tb - 1) / tb, tb, 0, p->stream>>>(U, p->psi, p->chi, T, nlm, p->ilap);
     p->prof.end(ph);
   }
   int rc;
@@ -319,7 +325,8 @@ static int nonlinear_update(swe_plan* p, const double2* U, const double2* base, 
   if ((rc = sh_synth_fused(p->sp, U, 2, p->PZ, p->psi, p->chi, 1, p->Ug, p->Vg))) return rc;
   {
     const int ph = p->prof.begin(0);
-    k_swe_products<<<(p->npt + tb - 1) / tb, tb, 0, p->stream>>>(p->PZ, p->Ug, p->Vg, p->c2, p->A, p->B, p->KE,
+    k_swe_products<<<dim3((p->d.nlon + tb - 1) / tb, p->d.nlat), tb, 0, p->stream>>>(p->PZ, p->Ug, p->Vg, p->ikc,
+                                                                                  p->A, p->B, p->KE,
                                                                 p->d.nlat, p->d.nlon);
     p->prof.end(ph);
   }
