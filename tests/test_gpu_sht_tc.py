@@ -95,3 +95,57 @@ def test_tc_vector(env, prec, T, nlat, nlon):
         print("%s T%d uv/divcurl" % (prec, T), ["%.2e" % e for e in errs])
         assert max(errs) < BOUND[prec], errs
     p.close()
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("nf", [1, 3, 5, 8])
+def test_tc_field_counts_scalar(env, prec, nf):
+    """Field counts up to max_fields = 8 on a plan sized for 8: the fused epilogue takes the
+    fields two per 8-column group (an odd count leaves the last group half used), and a call
+    writes only its own fields (the rest of the output keeps a sentinel)."""
+    torch, rexi = env
+    T, nlat, nlon = 63, 96, 192
+    og = osht.Grid(T, nlat, nlon, A)
+    p = rexi.ShPlan(T, nlat, nlon, A, prec, max_fields=8)
+    c = _spec(T, 30 + nf, nf)
+    g = torch.full((8, nlat, nlon), 7.0, dtype=torch.float64, device="cuda")
+    p.synthesis(torch.from_numpy(c).cuda(), g, nf)
+    grids = np.stack([og.synth(c[f]) for f in range(nf)])
+    s = torch.full((8, osht.nlm(T)), 7.0 + 0j, dtype=torch.complex128, device="cuda")
+    p.analysis(torch.from_numpy(grids).cuda(), s, nf)
+    p.check()
+    G, S = g.cpu().numpy(), s.cpu().numpy()
+    for f in range(nf):
+        es, ea = _rel(G[f], grids[f]), _rel(S[f], og.analys(grids[f]))
+        assert es < BOUND[prec] and ea < BOUND[prec], (f, es, ea)
+    assert np.all(G[nf:] == 7.0) and np.all(S[nf:] == 7.0)
+    p.close()
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("nf", [1, 3, 4])
+def test_tc_field_counts_vector(env, prec, nf):
+    """Vector field counts: one 8-column group per field, the (P, H) job pairs of every
+    (m, tile) combined in the epilogue, nf = 4 filling 64 columns (T = 63, 96 x 192 grid)."""
+    torch, rexi = env
+    T, nlat, nlon = 63, 96, 192
+    og = osht.Grid(T, nlat, nlon, A)
+    p = rexi.ShPlan(T, nlat, nlon, A, prec, max_fields=4)
+    psi, chi = _spec(T, 40 + nf, nf), _spec(T, 50 + nf, nf)
+    psi[:, 0] = chi[:, 0] = 0
+    U = torch.empty(nf, nlat, nlon, dtype=torch.float64, device="cuda")
+    V = torch.empty_like(U)
+    p.synthesis_uv(torch.from_numpy(psi).cuda(), torch.from_numpy(chi).cuda(), U, V, nf)
+    Ag = np.stack([og.synth(_spec(T, 60 + f)[0]) for f in range(nf)])
+    Bg = np.stack([og.synth(_spec(T, 70 + f)[0]) for f in range(nf)])
+    dv = torch.empty(nf, osht.nlm(T), dtype=torch.complex128, device="cuda")
+    cu = torch.empty_like(dv)
+    p.analysis_divcurl(torch.from_numpy(Ag).cuda(), torch.from_numpy(Bg).cuda(), dv, cu, nf)
+    p.check()
+    for f in range(nf):
+        Uo, Vo = og.synth_uv(psi[f], chi[f])
+        do, co = og.analys_divcurl(Ag[f], Bg[f])
+        errs = [_rel(U.cpu().numpy()[f], Uo), _rel(V.cpu().numpy()[f], Vo),
+                _rel(dv.cpu().numpy()[f], do), _rel(cu.cpu().numpy()[f], co)]
+        assert max(errs) < BOUND[prec], (f, errs)
+    p.close()
