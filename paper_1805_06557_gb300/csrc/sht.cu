@@ -463,11 +463,13 @@ __device__ __forceinline__ void fft_synth_block(const FftSegs& sg, const FftPlan
   // m for both entries.  Filled into the padded buffer b, which the first pass reads.
   for (int m = threadIdx.x; m <= T; m += blockDim.x) {
     const D4 AB = *reinterpret_cast<const D4*>(in + (size_t)m * nlat + j0);
+    // in the transform's own precision: FP32 plans convert first and combine in FP32
+    const R ax = R(AB.x), ay = R(AB.y), bx = R(AB.z), by = R(AB.w);
     if (m == 0) {
-      b[0] = Cx<C>::make(R(AB.x), R(AB.z));
+      b[0] = Cx<C>::make(ax, bx);
     } else {
-      b[fpad(m)] = Cx<C>::make(R(AB.x - AB.w), R(AB.y + AB.z));
-      b[fpad(n - m)] = Cx<C>::make(R(AB.x + AB.w), R(AB.z - AB.y));
+      b[fpad(m)] = Cx<C>::make(ax - by, ay + bx);
+      b[fpad(n - m)] = Cx<C>::make(ax + by, bx - ay);
     }
   }
   for (int k = T + 1 + threadIdx.x; k < n - T; k += blockDim.x) b[fpad(k)] = Cx<C>::make(R(0), R(0));
@@ -497,14 +499,14 @@ __device__ __forceinline__ void fft_anal_block(const FftSegs& sg, const FftPlan&
   auto src = [r0, r1](int k) -> C { return Cx<C>::make(R(__ldg(r0 + k)), R(__ldg(r1 + k))); };
   auto none = [](int, C) {};
   const C* z = fft_run<C, true>(src, none, a, b, fp, tw, -1);
-  const double sc = 3.14159265358979323846 / n;  // (2 pi / n) / 2
+  const R sc = R(3.14159265358979323846 / n);  // (2 pi / n) / 2, in the transform's precision
   double2* out = sg.F[s] + (size_t)f * (T + 1) * nlat;
   for (int m = threadIdx.x; m <= T; m += blockDim.x) {
     const C zm = z[fpad(m)], zn = z[fpad(m == 0 ? 0 : n - m)];
     // A = (Z_m + conj(Z_{n-m})) / 2,  B = (Z_m - conj(Z_{n-m})) / (2i); one aligned 32-byte store
     *reinterpret_cast<D4*>(out + (size_t)m * nlat + j0) =
-        D4{sc * ((double)zm.x + zn.x), sc * ((double)zm.y - zn.y), sc * ((double)zm.y + zn.y),
-           -sc * ((double)zm.x - zn.x)};
+        D4{(double)(sc * (zm.x + zn.x)), (double)(sc * (zm.y - zn.y)), (double)(sc * (zm.y + zn.y)),
+           (double)(-sc * (zm.x - zn.x))};
   }
 }
 

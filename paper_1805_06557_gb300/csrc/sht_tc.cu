@@ -99,7 +99,9 @@ __device__ __forceinline__ void tmem_sum8(uint32_t ta, uint32_t cs, int nacc, fl
 }
 
 // Results of one row (synthesis: northern latitude `row`; analysis: k = n - m = row) from the
-// 8-column group gq of the sums P (and H for vector transforms), combined in FP64.  Columns are
+// 8-column group gq of the sums P (and H for vector transforms), combined in FP32 (the sums
+// carry TF32 / BF16 operand rounding; FP64 arithmetic is a scarce pipe on this GPU) and stored
+// as FP64.  Columns are
 // interleaved per field (2 cpf columns each), so a group is two scalar fields or one vector
 // field:
 //   synthesis scalar  (N re, N im, S re, S im): northern latitude and its mirror;
@@ -111,7 +113,7 @@ __device__ __forceinline__ void tmem_sum8(uint32_t ta, uint32_t cs, int nacc, fl
 //                     div = (i m P.A - H.B)/a, curl = (i m P.B + H.A)/a.
 __device__ __forceinline__ void epilogue8(const GemmArgs& g, int m, int row, int gq, const float* P,
                                           const float* H) {
-  const double ia = g.inv_a, dm = (double)m;
+  const float ia = (float)g.inv_a, fm = (float)m;
   if (g.synth) {
     if (row >= g.nlat / 2) return;
     const int lat = row, lats = g.nlat - 1 - row;
@@ -130,12 +132,10 @@ __device__ __forceinline__ void epilogue8(const GemmArgs& g, int m, int row, int
       for (int hs = 0; hs < 2; ++hs) {
         const float* p = P + 4 * hs;
         const float* q = H + 4 * hs;
-        const double sh = hs ? -1.0 : 1.0;
+        const float sh = hs ? -1.f : 1.f;
         const int j = hs ? lats : lat;
-        g.out0[o + j] = make_double2(ia * (-sh * (double)q[0] - dm * (double)p[3]),
-                                     ia * (-sh * (double)q[1] + dm * (double)p[2]));
-        g.out1[o + j] = make_double2(ia * (-dm * (double)p[1] + sh * (double)q[2]),
-                                     ia * (dm * (double)p[0] + sh * (double)q[3]));
+        g.out0[o + j] = make_double2(ia * (-sh * q[0] - fm * p[3]), ia * (-sh * q[1] + fm * p[2]));
+        g.out1[o + j] = make_double2(ia * (-fm * p[1] + sh * q[2]), ia * (fm * p[0] + sh * q[3]));
       }
     }
   } else {
@@ -151,15 +151,15 @@ __device__ __forceinline__ void epilogue8(const GemmArgs& g, int m, int row, int
                                             : make_double2(P[4 * h], P[4 * h + 1]);
       }
     } else {
-      double p[4], q[4];  // register selects (no indexing by the parity)
+      float p[4], q[4];  // register selects (no indexing by the parity)
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         p[c] = par ? P[4 + c] : P[c];
         q[c] = par ? H[c] : H[4 + c];
       }
       const size_t o = (size_t)gq * g.nlm + i;
-      g.out0[o] = make_double2(ia * (-dm * p[1] - q[2]), ia * (dm * p[0] - q[3]));
-      g.out1[o] = make_double2(ia * (-dm * p[3] + q[0]), ia * (dm * p[2] + q[1]));
+      g.out0[o] = make_double2(ia * (-fm * p[1] - q[2]), ia * (fm * p[0] - q[3]));
+      g.out1[o] = make_double2(ia * (-fm * p[3] + q[0]), ia * (fm * p[2] + q[1]));
     }
   }
 }
@@ -512,13 +512,17 @@ __global__ void k_tc_banal(const double2* __restrict__ F0, const double2* __rest
     b[e] = in ? Fq[nlat - 1 - j] : make_double2(0.0, 0.0);
     w[e] = in ? wts[j] : 0.0;
   }
+  // the combinations in FP32 (the operand is rounded to TF32 / BF16 next; FP64 arithmetic is
+  // a scarce pipe on this GPU): only the conversions of the inputs touch FP64 values
   float pr[E], pi[E], mr[E], mi[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
-    pr[e] = (float)(w[e] * (a[e].x + b[e].x));
-    pi[e] = (float)(w[e] * (a[e].y + b[e].y));
-    mr[e] = (float)(w[e] * (a[e].x - b[e].x));
-    mi[e] = (float)(w[e] * (a[e].y - b[e].y));
+    const float ax = (float)a[e].x, ay = (float)a[e].y, bx = (float)b[e].x, by = (float)b[e].y;
+    const float we = (float)w[e];
+    pr[e] = we * (ax + bx);
+    pi[e] = we * (ay + by);
+    mr[e] = we * (ax - bx);
+    mi[e] = we * (ay - by);
   }
   unsigned char* grp = B + boff[m] + (size_t)g * 128;
   const int cn = 2 * cpf * f + q;  // N + S column; the N - S one is cpf further
