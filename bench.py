@@ -156,6 +156,98 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------------------
+def thomas_rexi_step(U0, T, dt, omega, radius, phibar, z, w, chunk=64, threads=None):
+    """Vectorised FP64 CPU REXI step, the fair CPU baseline (not the oracle): for every pole
+    z_p and zonal order m, Phi is eliminated from (z_p - dt L_m) u = b (Phi_n = (b_Phi,n -
+    dt Phibar delta_n) / z_p) and the zeta/delta coupling splits into two tridiagonal chains by
+    the parity of n - m, solved by Thomas elimination without pivoting.  Arrays are [row j of
+    the chain (n = m + j)][pole][m], so one elimination step is one contiguous numpy operation
+    over `chunk` poles and all zonal orders; pole chunks run in `threads` threads (numpy
+    releases the interpreter lock inside its array operations); U1 = sum_p w_p u_p.
+    U0: [3, nlm] complex128 (Phi', zeta, delta), m-major."""
+    import numpy as np
+    from concurrent.futures import ThreadPoolExecutor
+    M = T + 1
+    jj, mm = np.meshgrid(np.arange(M), np.arange(M), indexing="ij")  # [j, m], n = m + j
+    n = (mm + jj).astype(float)
+    valid = (mm + jj) <= T
+    off = mm * (2 * T + 3 - mm) // 2
+    idx = np.where(valid, off + jj, 0)
+    b = [np.where(valid, U0[f][idx], 0.0) for f in range(3)]
+    nz = valid & (n > 0)
+    nn = np.where(nz, n, 1.0)
+    eps = lambda k: np.sqrt(np.clip((k * k - mm * mm) / (4.0 * k * k - 1.0), 0.0, None))
+    om = np.where(nz, 2.0 * omega * mm / (nn * (nn + 1.0)), 0.0)
+    q = np.where(nz, n * (n + 1.0) / (radius * radius), 0.0)
+    # couplings of row n to n - 1 and n + 1 (times dt); dropped at n - 1 = 0 and beyond T
+    cm = np.where(nz & (jj > 0) & (n - 1 > 0), dt * 2.0 * omega * (nn + 1.0) / nn * eps(nn), 0.0)
+    cp = np.where(valid & (mm + jj + 1 <= T), dt * 2.0 * omega * n / (n + 1.0) * eps(n + 1.0), 0.0)
+    zs = np.asarray(z, dtype=np.complex128)
+    ws = np.asarray(w, dtype=np.complex128)
+
+    def solve(p0):
+        Z = zs[p0:p0 + chunk][None, :, None]  # [1, P, 1]
+        W = ws[p0:p0 + chunk]
+        dZ = np.where(nz[:, None, :], Z - 1j * dt * om[:, None, :], Z)
+        dD = np.where(nz[:, None, :], dZ + dt * dt * phibar * q[:, None, :] / Z, Z)
+        rD = np.where(nz[:, None, :], b[2][:, None, :] + dt * q[:, None, :] * b[0][:, None, :] / Z,
+                      b[2][:, None, :])
+        zeta = np.empty(dZ.shape, dtype=np.complex128)
+        delta = np.empty(dZ.shape, dtype=np.complex128)
+        for c in (0, 1):  # chain c: zeta rows where j % 2 == c, delta rows elsewhere
+            cpr = np.empty(dZ.shape, dtype=np.complex128)
+            y = np.empty(dZ.shape, dtype=np.complex128)
+            cprev = np.zeros(dZ.shape[1:], dtype=np.complex128)
+            yprev = np.zeros(dZ.shape[1:], dtype=np.complex128)
+            for j in range(M):
+                isZ = (j % 2) == c
+                sg = 1.0 if isZ else -1.0
+                d = np.where(valid[j], dZ[j] if isZ else dD[j], 1.0)
+                r = np.where(valid[j], b[1][j] if isZ else rD[j], 0.0)
+                lo, up = sg * cm[j], sg * cp[j]
+                piv = d - lo * cprev
+                cprev = up / piv
+                yprev = (r - lo * yprev) / piv
+                cpr[j] = cprev
+                y[j] = yprev
+            xn = np.zeros(dZ.shape[1:], dtype=np.complex128)
+            for j in range(M - 1, -1, -1):
+                xn = y[j] - cpr[j] * xn
+                if (j % 2) == c:
+                    zeta[j] = xn
+                else:
+                    delta[j] = xn
+        phi = np.where(nz[:, None, :], (b[0][:, None, :] - dt * phibar * delta) / Z, b[0][:, None, :] / Z)
+        return [np.einsum("p,jpm->jm", W, v) for v in (phi, zeta, delta)]
+
+    starts = list(range(0, len(zs), chunk))
+    nthr = threads or min(len(starts), os.cpu_count() or 1)
+    with ThreadPoolExecutor(max_workers=nthr) as ex:
+        parts = list(ex.map(solve, starts))
+    U1 = np.zeros((3, (T + 1) * (T + 2) // 2), dtype=np.complex128)
+    for f in range(3):
+        acc = parts[0][f].copy()
+        for pr in parts[1:]:  # pole chunks summed in their fixed order
+            acc += pr[f]
+        U1[f][idx[valid]] = acc[valid]
+    return U1
+
+
+def cpu_thomas_rate(T, N, dt, states):
+    """The vectorised numpy Thomas baseline over whole steps of the given states: (steps/s,
+    seconds)."""
+    from paper_1805_06557_gb300 import rexi
+    from paper_1805_06557_gb300 import synthetic as syn
+    X = rexi.spectrum_bound(T, dt, syn.OMEGA, syn.RADIUS, syn.PHIBAR)
+    p0, Xc = contour(X)
+    z, w = rexi.coeffs(N, p0, Xc)
+    t0 = time.perf_counter()
+    for U in states:
+        thomas_rexi_step(U, T, dt, syn.OMEGA, syn.RADIUS, syn.PHIBAR, z, w)
+    sec = time.perf_counter() - t0
+    return len(states) / sec, sec
+
+
 def cpu_oracle_rate(T, N, dt, m_list, states):
     """Oracle (pivoted banded LU per pole and zonal order, FP64 sum) on the zonal orders
     m_list of each state; returns (state-steps/s extrapolated to the full step, seconds)."""
@@ -695,7 +787,7 @@ def main():
                                                 ("fp64", "tf32", "lg_ver1")])])
         lg = lg_rexi(torch, rexi, fp64_tf)
 
-    cpu = None
+    cpu = cpu_fair = None
     if rank == 0 and world == 1 and not args.no_cpu:
         import multiprocessing as mp  # noqa: F401  (the oracle runs in this process)
         rate, sec = cpu_oracle_rate(T, N, dt, SAMPLE_M, [host[i] for i in range(min(SAMPLE_STATES, B))])
@@ -703,6 +795,11 @@ def main():
                "seconds": sec,
                "sample": "pivoted banded LU oracle, all %d zonal orders of %d states (full steps)"
                          % (len(SAMPLE_M), min(SAMPLE_STATES, B))}
+        nthr = os.cpu_count() or 1
+        rate_t, sec_t = cpu_thomas_rate(T, N, dt, [host[0]])
+        cpu_fair = {"value": rate_t, "unit": "steps/s", "cores": nthr, "seconds": sec_t,
+                    "kind": "vectorised numpy FP64 Thomas (two parity chains per pole and zonal order)",
+                    "sample": "one full step of one state, pole chunks of 64 on %d threads" % nthr}
 
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
@@ -722,7 +819,7 @@ def main():
                                       "grid_heavy")},
         "alu_peaks_tflops": {"fp64": fp64_tf, "fp32": fp32_tf},
         "ensemble": ens, "sh_transforms": sh, "swe_step": swe, "lg_rexi": lg,
-        "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+        "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "cpu_thomas": cpu_fair, "clocks": clocks,
         "gpu_launches": 4 * args.steps,
     }
     if rank == 0:
