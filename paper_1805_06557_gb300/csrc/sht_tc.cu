@@ -46,7 +46,8 @@ struct Job {
   int kl;           // K of the last chunk (a multiple of the MMA k-step, <= KC)
   int rows;         // A rows stored for the job (the valid rows rounded up to 8, <= 128): a
                     // chunk holds rows x KC elements; the MMA reads all 128 rows of a ring
-                    // stage, and the D rows past `rows` hold stale sums that no epilogue reads
+                    // stage, and the accumulator rows past `rows` hold stale sums that the
+                    // epilogue never stores
 };
 
 struct GemmArgs {
@@ -433,7 +434,8 @@ __device__ __forceinline__ void store_row16(unsigned char* grp, int c, int sbo, 
 }
 
 // Padding columns of a B operand (past the real ones, up to the MMA's N) are never written:
-// each D column depends on its own B column only, and no epilogue reads a padding column.
+// each accumulator column depends on its own B column only, and the epilogue never reads a
+// padding column.
 
 // synthesis B operand of zonal order m: K index k = n - m over all degrees; field f owns the
 // 2 cpf columns from 2 cpf f: first coefficient q of the field in column 2 cpf f + q (north:
@@ -544,7 +546,7 @@ struct Sched {
 
 struct TcLegendre {
   int T = 0, nlat = 0, nh = 0, nlm = 0, max_fields = 0, bf16 = 0, E = 4, eb = 4, KC = 32;
-  int ntile_s = 0, ntile_a = 0, kpad_a = 0;
+  int ntile_s = 0, kpad_a = 0;
   unsigned char *tabPs = nullptr, *tabHs = nullptr, *tabPa = nullptr, *tabHa = nullptr;
   unsigned char* B = nullptr;
   int* err = nullptr;
@@ -659,7 +661,6 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
   t->kpad_a = (t->nh + kstep - 1) / kstep * kstep;
   const int nchunk_a = (t->kpad_a + KC - 1) / KC;
   const int kl_a = t->kpad_a - (nchunk_a - 1) * KC;
-  t->ntile_a = (T + 1 + 127) / 128;
   std::vector<TabJob> ta;
   std::vector<Job> jaP, jaH;
   std::vector<int> boff_a(T + 1);
