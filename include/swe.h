@@ -57,7 +57,8 @@ typedef struct swe_plan_desc {
   int rexi_precision;       /* REXI_FP64 or REXI_MIXED                                      */
   int sh_precision;         /* SH_FP64, SH_TF32 or SH_BF16                                  */
   int scheme;               /* one of the SWE_* scheme identifiers above                    */
-  void* stream;             /* cudaStream_t                                                  */
+  void* stream;             /* cudaStream_t; NULL (the legacy default stream): the plan makes */
+                            /* its own blocking stream, implicitly ordered with the default  */
 } swe_plan_desc;
 
 /* Creates the REXI plan(s: three for etdrk, gravity-only plans for lg), the SH plan and all
@@ -67,7 +68,10 @@ int swe_plan_create(const swe_plan_desc* desc, swe_plan** out);
 int swe_plan_destroy(swe_plan* plan);
 
 /* Advances `state` (device, [3][nlm] complex128) in place by nsteps steps of the scheme.
- * Asynchronous on the plan stream; no allocation.  Errors: REXI_EINVAL, REXI_ECUDA. */
+ * Asynchronous on the plan stream.  With nsteps >= 2 and profiling off, the first step runs
+ * eagerly and the kernels of one step are captured into a CUDA graph that replays the rest
+ * (kept per state address: a call on another state recaptures; a stream that cannot capture
+ * runs every step eagerly).  Errors: REXI_EINVAL, REXI_ECUDA. */
 int swe_step(swe_plan* plan, void* state, int nsteps);
 
 /* tendency = N(state) (device [3][nlm] complex128 each; no aliasing). */

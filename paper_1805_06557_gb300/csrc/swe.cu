@@ -150,6 +150,10 @@ struct swe_plan {
   swe_plan_desc d{};
   int nlm = 0, npt = 0;
   cudaStream_t stream = nullptr;
+  bool own_stream = false;             // made here because the caller gave the legacy stream
+  cudaGraphExec_t step_graph = nullptr;  // one step's kernels, replayed by swe_step
+  const void* graph_state = nullptr;   // the state address the graph was captured for
+  bool no_graph = false;               // the stream could not capture: steps run eagerly
   rexi_plan* rp = nullptr;             // REXI of exp (ver1: dt, ver0: dt/2, etdrk: dt)
   rexi_plan *rp1 = nullptr, *rp2 = nullptr;  // etdrk: REXI of psi_1, psi_2 (same poles)
   sh_plan* sp = nullptr;
@@ -167,6 +171,7 @@ struct swe_plan {
 extern "C" int swe_plan_destroy(swe_plan* p) {
   if (!p) return REXI_OK;
   cudaStreamSynchronize(p->stream);
+  if (p->step_graph) cudaGraphExecDestroy(p->step_graph);
   rexi_plan_destroy(p->rp);
   rexi_plan_destroy(p->rp1);
   rexi_plan_destroy(p->rp2);
@@ -177,6 +182,7 @@ extern "C" int swe_plan_destroy(swe_plan* p) {
                   (void*)p->kes, (void*)p->PZ, (void*)p->Ug, (void*)p->Vg, (void*)p->A, (void*)p->B,
                   (void*)p->KE, (void*)p->ikc, (void*)p->ilap, (void*)p->NU, (void*)p->A3, (void*)p->Ltab})
     cudaFree(q);
+  if (p->own_stream) cudaStreamDestroy(p->stream);
   delete p;
   return REXI_OK;
 }
@@ -192,6 +198,14 @@ extern "C" int swe_plan_create(const swe_plan_desc* desc, swe_plan** out) {
   p->is_lg = d.scheme == SWE_LG_REXI_LC_N_ERK_VER1 || d.scheme == SWE_LG_REXI_LC_N_ETDRK ||
              d.scheme == SWE_LG_IRK_LC_N_ERK_VER0;
   p->stream = (cudaStream_t)d.stream;
+  if (!p->stream) {  // the legacy stream cannot capture graphs; a blocking stream orders with it
+    cudaError_t es = cudaStreamCreate(&p->stream);
+    if (es) {
+      delete p;
+      return cuda_fail(es, "swe_plan_create: cudaStreamCreate");
+    }
+    p->own_stream = true;
+  }
   p->prof.stream = p->stream;
   p->nlm = (d.T + 1) * (d.T + 2) / 2;
   p->npt = d.nlat * d.nlon;
@@ -206,7 +220,7 @@ extern "C" int swe_plan_create(const swe_plan_desc* desc, swe_plan** out) {
   sd.radius = d.radius;
   sd.precision = d.sh_precision;
   sd.max_fields = 3;  // Fourier work slots for the fused analysis: A, B (2 each) and KE
-  sd.stream = d.stream;
+  sd.stream = p->stream;
   int rc = sh_plan_create(&sd, &p->sp);
   if (rc) return bail(rc);
   rexi_plan_desc rd{};
@@ -221,7 +235,7 @@ extern "C" int swe_plan_create(const swe_plan_desc* desc, swe_plan** out) {
   rd.precision = d.rexi_precision;
   rd.heavy_tau = -1.0;
   rd.max_batch = 1;
-  rd.stream = d.stream;
+  rd.stream = p->stream;
   double cn_z[2] = {2.0, 0.0}, cn_w[2] = {2.0, 0.0};  // irk: one pole z = 2, weight 2, FP64
   if (d.scheme == SWE_L_IRK_N_ERK_VER1) {
     rd.N = 1;
@@ -243,7 +257,7 @@ extern "C" int swe_plan_create(const swe_plan_desc* desc, swe_plan** out) {
       ld.Xc = d.Xc;
       ld.phi = k;
       ld.max_batch = 1;
-      ld.stream = d.stream;
+      ld.stream = p->stream;
       if (d.scheme == SWE_LG_IRK_LC_N_ERK_VER0) {  // CN_g over dt/2: 4 (2 - (dt/2) L_g)^-1 - I
         ld.N = 1;
         ld.dt = 0.5 * d.dt;
@@ -364,13 +378,11 @@ extern "C" int swe_nonlinear(swe_plan* p, const void* state, void* tend) {
   return nonlinear_update(p, (const double2*)state, nullptr, 0.0, (double2*)tend);
 }
 
-extern "C" int swe_step(swe_plan* p, void* state, int nsteps) {
-  if (!p || !state) return fail(REXI_EINVAL, "swe_step: null argument");
-  if (nsteps < 0) return fail(REXI_EINVAL, "swe_step: nsteps < 0");
-  double2* U = (double2*)state;
+// One step of the plan's scheme on U: kernels and device copies on the plan stream only.
+static int step_once(swe_plan* p, double2* U) {
   const size_t s3 = sizeof(double2) * 3 * (size_t)p->nlm;
   const double dt = p->d.dt;
-  for (int s = 0; s < nsteps; ++s) {
+  {
     int rc;
     if (p->d.scheme == SWE_L_REXI_N_ERK_VER1) {
       if ((rc = rk2_nonlinear(p, U, 0.5 * dt))) return rc;
@@ -418,6 +430,60 @@ extern "C" int swe_step(swe_plan* p, void* state, int nsteps) {
       if ((rc = rexi_step(p->rp2, p->Um, p->Ut, 1))) return rc;                  // psi_2 (...)
       k_axpy<<<nb, tb, 0, p->stream>>>(p->A3, p->Ut, dt, U, n3);                  // U+
       REXI_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  return REXI_OK;
+}
+
+// Records one step on U into p->step_graph (stream capture: nothing runs).  A stream or a call
+// that cannot be captured leaves no graph and sets no_graph; steps then run eagerly.
+static void capture_step(swe_plan* p, double2* U) {
+  if (p->step_graph) {
+    cudaGraphExecDestroy(p->step_graph);
+    p->step_graph = nullptr;
+    p->graph_state = nullptr;
+  }
+  if (cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    p->no_graph = true;
+    return;
+  }
+  const int rc = step_once(p, U);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(p->stream, &g);
+  cudaGraphExec_t x = nullptr;
+  if (rc || e != cudaSuccess || !g || cudaGraphInstantiate(&x, g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    p->no_graph = true;
+    x = nullptr;
+  }
+  if (g) cudaGraphDestroy(g);
+  p->step_graph = x;
+  p->graph_state = x ? U : nullptr;
+}
+
+extern "C" int swe_step(swe_plan* p, void* state, int nsteps) {
+  if (!p || !state) return fail(REXI_EINVAL, "swe_step: null argument");
+  if (nsteps < 0) return fail(REXI_EINVAL, "swe_step: nsteps < 0");
+  double2* U = (double2*)state;
+  // a step is ~50 dependent kernels (most of them short at moderate truncations): replaying a
+  // captured graph removes their per-launch host work and shortens the gaps between them.  The
+  // first step of a new state runs eagerly, so that anything a sub-plan builds on first use
+  // exists before the capture; profiling (host-collected event pairs) always runs eagerly.
+  const bool graphs = !p->prof.on && !p->no_graph && nsteps >= 2;
+  int s = 0;
+  if (graphs && (!p->step_graph || p->graph_state != U)) {
+    int rc = step_once(p, U);
+    if (rc) return rc;
+    ++s;
+    capture_step(p, U);
+  }
+  for (; s < nsteps; ++s) {
+    if (graphs && p->step_graph && p->graph_state == U) {
+      REXI_CUDA_TRY(cudaGraphLaunch(p->step_graph, p->stream));
+    } else {
+      int rc = step_once(p, U);
+      if (rc) return rc;
     }
   }
   return REXI_OK;

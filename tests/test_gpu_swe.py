@@ -161,3 +161,30 @@ def test_nonlinear_tensor_core_error(env, prec, kind, capsys):
         print("\nN(U) %s %s per-field rel L2: %s" % (prec, kind, ["%.2e" % e for e in err]))
     assert np.all(np.isfinite(err)) and np.all(err < np.array(TC_BOUNDS[(prec, kind)])), err
     plan.close()
+
+
+@pytest.mark.parametrize("scheme,sprec", [("ver1", "fp64"), ("lg_etdrk", "fp64"), ("ver1", "tf32")])
+def test_graph_replay_equals_eager_steps(env, scheme, sprec):
+    """swe_step with nsteps >= 2 replays a captured graph of one step: the result equals the
+    same steps run one call at a time (eager) bit for bit; a second state recaptures; steps
+    with profiling on (always eager) agree as well."""
+    torch, rexi = env
+    T, nlat, nlon, N, dt = 31, 48, 96, 128, 1800.0
+    p0, Xc = _contour(T, dt)
+    plan = rexi.SwePlan(T, nlat, nlon, dt, OM, A, PB, N, p0, Xc, sh_precision=sprec, scheme=scheme)
+    U0 = torch.from_numpy(syn.balanced_state(T, 2, urms=20.0)).cuda()
+    a, b, c = U0.clone(), U0.clone(), U0.clone()
+    plan.step(a, 5)          # 1 eager + capture + 4 replays
+    for _ in range(5):
+        plan.step(b, 1)      # eager
+    plan.step(c, 3)          # another state address: recapture
+    plan.step(c, 2)          # replays of that capture
+    d = U0.clone()
+    plan.set_profiling(True)
+    plan.step(d, 5)          # eager (profiling)
+    plan.set_profiling(False)
+    torch.cuda.synchronize()
+    assert torch.isfinite(a).all()
+    assert torch.equal(a, b) and torch.equal(a, c) and torch.equal(a, d)
+    assert not torch.equal(a, U0)
+    plan.close()
