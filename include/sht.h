@@ -77,8 +77,8 @@ int sh_plan_check(sh_plan* plan);
  * stream around each kernel it launches; sh_plan_get_profile synchronises the stream and
  * returns, per stage, the total milliseconds (ms[k]) and the number of launches
  * (launches[k]) since the last reset (reset = 1 clears them after reading).  Stages:
- * 0 FP64 Legendre contraction (SH_FP64), 1 operand packing for the tensor cores,
- * 2 tcgen05 Legendre GEMM with its fused FP64 epilogue, 3 unused (always 0),
+ * 0 FP64 Legendre contraction (SH_FP64), 1 unused (always 0), 2 tcgen05 Legendre GEMM
+ * (its B operands built and its FP64 results written inside the kernel), 3 unused,
  * 4 longitude FFT.  Arrays hold SH_NSTAGES entries; either may be NULL.  Disabled by
  * default.  Errors: REXI_EINVAL, REXI_ECUDA.
  */

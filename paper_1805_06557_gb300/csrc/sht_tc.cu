@@ -14,8 +14,9 @@
 // at plan time so that each K-chunk of A is one contiguous block moved by the bulk-copy
 // engine (cp.async.bulk, completion on an mbarrier).  The GEMM is a persistent kernel, one
 // CTA per SM, each with its own list of jobs (longest first, assigned to the least-loaded CTA
-// at plan time): a copy warp streams A chunks through a ring of up to 8 stages and the B
-// operands through up to four buffers, an MMA warp accumulates in TMEM (FP32), and four
+// at plan time): a copy warp streams A chunks through a ring of up to 8 stages; the B
+// operands go through up to four shared-memory buffers that eight builder warps fill from the
+// spectral or Fourier coefficients, an MMA warp accumulates in TMEM (FP32), and four
 // epilogue warps read the accumulators with tcgen05.ld and write the FP64 results directly
 // (hemisphere and parity combination, and for vector transforms the P and H sums of one
 // (m, tile), which run as consecutive jobs of one CTA).  All mbarrier waits are bounded; on a
@@ -32,13 +33,14 @@ namespace rexi {
 namespace {
 
 constexpr int TC_MAXSTAGES = 8;     // depth of the A-chunk ring
-constexpr int TC_THREADS = 192;     // warps 0-3 epilogue, warp 4 bulk copies, warp 5 MMA issue
-constexpr int TC_MAXCOL = 32;      // B operands are allocated 2 x TC_MAXCOL columns per m (8 fields x 2 x 4)
+constexpr int TC_BUILD0 = 6;        // first of the warps that build the B operands
+constexpr int TC_NBUILD = 8;        // builder warps
+constexpr int TC_THREADS = 32 * (TC_BUILD0 + TC_NBUILD);  // warps 0-3 epilogue, 4 A copies, 5 MMA
+                                                         // issue, 6-13 B operands
 constexpr size_t TC_SMEM_BUDGET = 220 * 1024;
 
 struct Job {
   long long a_off;  // byte offset of the job's first A chunk in its table
-  int b_off;        // byte offset of the job's B operand in the B buffer
   int m, tile;      // zonal order and 128-row tile (latitudes or degrees k = n - m)
   int nchunk;       // K chunks
   int kpad;         // K extent of B (whole MMA k-steps; (nchunk - 1) * KC + kl)
@@ -53,7 +55,12 @@ struct Job {
 struct GemmArgs {
   const unsigned char* tabP;
   const unsigned char* tabH;
-  const unsigned char* B;
+  // sources of the B operands: synthesis: spectra in0 (scalar; psi for vector) and in1 (chi),
+  // [nf][nlm]; analysis: Fourier coefficients in0 (A for vector), in1 (B), [nf][T+1][nlat],
+  // with the quadrature weights wts[nh] (w, or w / (1 - mu^2) for vector transforms)
+  const double2* in0;
+  const double2* in1;
+  const double* wts;
   const Job* jobs;      // per-CTA lists: CTA c runs jobs[cta_off[c] .. cta_off[c + 1])
   const int* cta_off;
   int ncols, bf16;
@@ -69,9 +76,10 @@ struct GemmArgs {
   int* err;
 };
 
-// Persistent, warp-specialised GEMM over per-CTA job lists (longest first).  Warp 4 streams the A chunks of every job through
-// the S-stage ring without pausing between jobs, and fetches B operands into NB buffers up to
-// NB - 1 jobs ahead (so that a job's MMAs never wait for the latency of its B copy); warp 5
+// Persistent, warp-specialised GEMM over per-CTA job lists (longest first).  Warp 4 streams
+// the A chunks of every job through the S-stage ring without pausing between jobs; warps 6-13
+// build the B operands into NB buffers up to NB - 1 jobs ahead (so that a job's MMAs never
+// wait for its operand); warp 5
 // issues the MMAs of job i into TMEM job buffer i % njb and commits: the ring stage (empty),
 // the B buffer (bempty) and the accumulator (tfull); warps 0-3 read the buffer (one TMEM lane
 // quarter each), write the FP64 results, and release it (tempty), so that the MMAs of the next
@@ -165,6 +173,108 @@ __device__ __forceinline__ void epilogue8(const GemmArgs& g, int m, int row, int
   }
 }
 
+// One 16-byte core-matrix row of a B operand: E consecutive K elements of column c of the
+// K group whose first byte is `grp` (column c at (c >> 3) * sbo + (c & 7) * 16), rounded to
+// TF32 (cvt.rna) or BF16 (round to nearest even)
+template <bool BF>
+__device__ __forceinline__ void store_row16(unsigned char* grp, int c, int sbo, const float* v) {
+  uint4 u;
+  uint32_t* w = reinterpret_cast<uint32_t*>(&u);
+  if (BF) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+      w[e] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w[e]) : "f"(v[e]));
+  }
+  *reinterpret_cast<uint4*>(grp + (size_t)(c >> 3) * sbo + (c & 7) * 16) = u;
+}
+
+// B operand of job (m, kpad) written into shared memory at `base` by the threads of the
+// builder warps (bt = thread index among them), in the tensor cores' canonical K-major layout
+// (K group g of E elements at g * 128 B, column c at (c >> 3) * sbo + (c & 7) * 16).  Field f
+// owns the 2 cpf columns from 2 cpf f.  Columns past 2 nf cpf are never written: each
+// accumulator column depends on its own B column only, and the epilogue never reads them.
+//   synthesis (K = degrees k = n - m): coefficient q of field f in column 2 cpf f + q (the
+//     northern latitude's P_n(mu)), times (-1)^k in column 2 cpf f + cpf + q (the southern
+//     one: P_n(-mu) = (-1)^(n-m) P_n(mu)); scalar q: re, im; vector q: psi re, im, chi re, im.
+//   analysis (K = northern latitudes j): w_j (F_N + F_S) in column 2 cpf f + q, w_j (F_N - F_S)
+//     in column 2 cpf f + cpf + q; scalar q: re, im; vector q: A re, im, B re, im.
+// One item = (K group, column pair p < nf cpf / 2): E loads of its pair, four 16-byte rows.
+template <bool BF>
+__device__ __forceinline__ void build_b(const GemmArgs& g, int m, int kpad, unsigned char* base, int bt) {
+  constexpr int E = BF ? 8 : 4;
+  const int cpf = g.cpf, np = g.nf * cpf / 2;
+  const int sbo = (kpad / E) * 128;
+  const int nitems = (kpad / E) * np;
+  for (int it = bt; it < nitems; it += TC_NBUILD * 32) {
+    const int gk = it / np, p = it - gk * np;
+    const int f = (2 * p) / cpf, q = 2 * p - f * cpf;
+    const int cn = 2 * cpf * f + q;  // the first column; the second block is cpf further
+    unsigned char* grp = base + (size_t)gk * 128;
+    float v0[E], v1[E], v2[E], v3[E];
+    if (g.synth) {
+      const int K = g.T + 1 - m;
+      const double2* src = (q < 2 ? g.in0 : g.in1) + (size_t)f * g.nlm + moff(g.T, m);
+      double2 c[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int k = gk * E + e;
+        c[e] = k < K ? src[k] : make_double2(0.0, 0.0);
+      }
+#pragma unroll
+      for (int e = 0; e < E; ++e) {  // gk * E is even: the parity of k is that of e
+        v0[e] = (float)c[e].x;
+        v1[e] = (float)c[e].y;
+        v2[e] = (e & 1) ? -v0[e] : v0[e];
+        v3[e] = (e & 1) ? -v1[e] : v1[e];
+      }
+    } else {
+      const int nh = g.nlat / 2;
+      const double2* Fq = (q < 2 ? g.in0 : g.in1) + ((size_t)f * (g.T + 1) + m) * g.nlat;
+      double2 a[E], b[E];
+      double w[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int j = gk * E + e;
+        const bool in = j < nh;
+        a[e] = in ? Fq[j] : make_double2(0.0, 0.0);
+        b[e] = in ? Fq[g.nlat - 1 - j] : make_double2(0.0, 0.0);
+        w[e] = in ? g.wts[j] : 0.0;
+      }
+      // combinations in FP32 (the operand is rounded to TF32 / BF16 next; FP64 arithmetic is a
+      // scarce pipe on this GPU): only the conversions of the inputs touch FP64 values
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const float ax = (float)a[e].x, ay = (float)a[e].y, bx = (float)b[e].x, by = (float)b[e].y;
+        const float we = (float)w[e];
+        v0[e] = we * (ax + bx);
+        v1[e] = we * (ay + by);
+        v2[e] = we * (ax - bx);
+        v3[e] = we * (ay - by);
+      }
+    }
+    store_row16<BF>(grp, cn, sbo, v0);
+    store_row16<BF>(grp, cn + 1, sbo, v1);
+    store_row16<BF>(grp, cn + cpf, sbo, v2);
+    store_row16<BF>(grp, cn + cpf + 1, sbo, v3);
+  }
+}
+
+// and-reduction of v over the threads of the builder warps (named barrier 1)
+__device__ __forceinline__ bool builders_all(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(TC_NBUILD * 32)
+      : "memory");
+  return r != 0;
+}
+
 template <bool BF>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant__ GemmArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -206,41 +316,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
   const int njb = min(TC_NJB, (int)(TC_TMEM_COLS / (cs * TC_NACC)));
   const uint32_t sa0 = tc::smem_u32(sA), sb0 = tc::smem_u32(sB);
   long long a_issued = 0;  // producer: A fills issued
-  int b_issued = 0;        // producer: B fills issued (jobs 0 .. b_issued - 1)
 
   if (warp == 4) {
     if (lane == 0) {
       bool ok = true;
-      // B operand of job q into buffer q % NB once its previous user, job q - NB, is done:
-      // between A chunks whenever that is already so (non-blocking test), and blocking only
-      // when the next job would otherwise lack its operand
-      int nb_next = 0;  // next job whose B operand is not issued
-      auto issue_b = [&](int q) {
-        const int b = q % NB;
-        const Job jq = sjobs[q];
-        const uint32_t bb = (uint32_t)g.ncols * jq.kpad * eb;
-        tc::mbar_expect_tx(bfull0 + 8 * b, bb);
-        tc::bulk_g2s(sb0 + b * g.bslot, g.B + jq.b_off, bb, bfull0 + 8 * b);
-        ++b_issued;
-        ++nb_next;
-      };
-      auto try_b = [&]() {
-        while (nb_next < nj) {
-          const int u = nb_next / NB;
-          if (u > 0 && !tc::mbar_test(bempty0 + 8 * (nb_next % NB), (u - 1) & 1)) return;
-          issue_b(nb_next);
-        }
-      };
-      try_b();
       int s = 0;
       uint32_t round = 0;  // number of completed passes over the ring
       for (int i = 0; i < nj && ok; ++i) {
-        if (nb_next <= i) {  // job i's operand must be on its way before its chunks
-          const int u = i / NB;
-          ok = u == 0 || tc::mbar_wait(bempty0 + 8 * (i % NB), (u - 1) & 1);
-          if (!ok) break;
-          issue_b(i);
-        }
         const Job jb = sjobs[i];
         const unsigned char* A = (jb.tab ? g.tabH : g.tabP) + jb.a_off;
         // rows / 8 core-matrix row groups: a prefix of the stage's canonical layout
@@ -256,10 +338,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
             s = 0;
             ++round;
           }
-          try_b();
         }
       }
       if (!ok) atomicExch(g.err, 3);
+    }
+  } else if (warp >= TC_BUILD0) {
+    // B operand of job q into buffer (q / bstep) % NB once its previous user has released it
+    // (its MMAs completed): written with ordinary shared-memory stores, made visible to the
+    // tensor cores' (async) proxy by a proxy fence, then announced on bfull by one thread
+    // (every thread of the builder warps takes the same path: the outcome of the bounded
+    // wait is and-reduced over them, so that a timeout ends the loop for all at once)
+    const int bt = tid - TC_BUILD0 * 32;
+    const int bstep = g.pair ? 2 : 1;  // the (P, H) jobs of a vector transform share a B buffer
+    for (int q = 0; q < nj; q += bstep) {
+      const int b = (q / bstep) % NB, u = (q / bstep) / NB;
+      const bool ok = builders_all(u == 0 || tc::mbar_wait(bempty0 + 8 * b, (u - 1) & 1));
+      if (!ok) {
+        if (bt == 0) atomicExch(g.err, 5);
+        break;
+      }
+      const Job jq = sjobs[q];
+      build_b<BF>(g, jq.m, jq.kpad, sB + (size_t)b * g.bslot, bt);
+      tc::fence_proxy_async();
+      builders_all(true);  // every row of the operand is written and fenced
+      if (bt == 0) tc::mbar_arrive(bfull0 + 8 * b);
     }
   } else if (warp == 5) {
     if (lane == 0) {
@@ -268,10 +370,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
       const uint32_t sboA = (uint32_t)(KC / E) * 128u;
       int s = 0;
       uint32_t round = 0;
+      // B buffer of job i: (i / bstep) % NB; the (P, H) jobs of a vector transform share theirs
+      const int bstep = g.pair ? 2 : 1;
       for (int i = 0; i < nj && ok; ++i) {
         const Job jb = sjobs[i];
-        const int b = i % NB, ub = i / NB, acc = i % njb, ua = i / njb;
-        ok = tc::mbar_wait(bfull0 + 8 * b, ub & 1);
+        const int bi = i / bstep, b = bi % NB, ub = bi / NB, acc = i % njb, ua = i / njb;
+        const bool first_of_b = i % bstep == 0, last_of_b = i % bstep == bstep - 1;
+        if (first_of_b) ok = tc::mbar_wait(bfull0 + 8 * b, ub & 1);
         if (ok && ua > 0) ok = tc::mbar_wait(tempty0 + 8 * acc, (ua - 1) & 1);
         if (!ok) break;
         tc::fence_after_sync();
@@ -305,7 +410,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
           }
         }
         if (!ok) break;
-        tc::mma_commit(bempty0 + 8 * b);
+        if (last_of_b) tc::mma_commit(bempty0 + 8 * b);
         tc::mma_commit(tfull0 + 8 * acc);
       }
       if (!ok) atomicExch(g.err, 4);
@@ -352,8 +457,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
     // the newest fill of each stage / B buffer: completed fills return at once
     for (long long q = a_issued - 1; q >= 0 && q >= a_issued - S; --q)
       tc::mbar_wait(full0 + 8 * (int)(q % S), (uint32_t)((q / S) & 1), 200000u);
-    for (int q = b_issued - 1; q >= 0 && q >= b_issued - NB; --q)
-      tc::mbar_wait(bfull0 + 8 * (q % NB), (q / NB) & 1, 200000u);
   }
   if (warp == 5 && lane == 0) tc::mbar_wait(fin, 0, 4000000u);
   tc::fence_before_sync();
@@ -413,127 +516,6 @@ __global__ void k_tc_table(const double* __restrict__ src, unsigned char* __rest
   }
 }
 
-// One 16-byte core-matrix row of a B operand: E consecutive K elements of column c of the
-// K group whose first byte is `grp` (column c at (c >> 3) * sbo + (c & 7) * 16), rounded to
-// TF32 (cvt.rna) or BF16 (round to nearest even)
-template <bool BF>
-__device__ __forceinline__ void store_row16(unsigned char* grp, int c, int sbo, const float* v) {
-  uint4 u;
-  uint32_t* w = reinterpret_cast<uint32_t*>(&u);
-  if (BF) {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
-      w[e] = *reinterpret_cast<const uint32_t*>(&h);
-    }
-  } else {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w[e]) : "f"(v[e]));
-  }
-  *reinterpret_cast<uint4*>(grp + (size_t)(c >> 3) * sbo + (c & 7) * 16) = u;
-}
-
-// Padding columns of a B operand (past the real ones, up to the MMA's N) are never written:
-// each accumulator column depends on its own B column only, and the epilogue never reads a
-// padding column.
-
-// synthesis B operand of zonal order m: K index k = n - m over all degrees; field f owns the
-// 2 cpf columns from 2 cpf f: first coefficient q of the field in column 2 cpf f + q (north:
-// P_n(mu) of the northern latitude), then the same times (-1)^k in column 2 cpf f + cpf + q
-// (south: P_n(-mu) = (-1)^(n-m) P_n(mu)).  q in [0, cpf): scalar (cpf = 2): re, im of spec f;
-// vector (cpf = 4): psi re, psi im, chi re, chi im.  Thread per (K group of E degrees, column
-// pair p < nf cpf / 2): reads the E coefficients of its pair once and writes the northern and
-// the southern (re, im) rows.
-template <bool BF>
-__global__ void k_tc_bsynth(const double2* __restrict__ s0, const double2* __restrict__ s1,
-                            unsigned char* __restrict__ B, const int* __restrict__ boff,
-                            const int* __restrict__ kpad, int T, int nlm, int nf, int cpf) {
-  constexpr int E = BF ? 8 : 4;
-  const int m = blockIdx.y;
-  const int np = nf * cpf / 2;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  const int g = idx / np, p = idx - g * np;
-  const int kp = kpad[m];
-  if (g * E >= kp) return;
-  const int sbo = (kp / E) * 128;
-  unsigned char* grp = B + boff[m] + (size_t)g * 128;
-  const int K = T + 1 - m;
-  const int f = (2 * p) / cpf, q = 2 * p - f * cpf;
-  const double2* src = (q < 2 ? s0 : s1) + (size_t)f * nlm + moff(T, m);
-  double2 c[E];
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int k = g * E + e;
-    c[e] = k < K ? src[k] : make_double2(0.0, 0.0);
-  }
-  float re[E], im[E];
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    re[e] = (float)c[e].x;
-    im[e] = (float)c[e].y;
-  }
-  const int cn = 2 * cpf * f + q;  // northern column; the southern one is cpf further
-  store_row16<BF>(grp, cn, sbo, re);
-  store_row16<BF>(grp, cn + 1, sbo, im);
-#pragma unroll
-  for (int e = 1; e < E; e += 2) {  // g * E is even: the parity of k is that of e
-    re[e] = -re[e];
-    im[e] = -im[e];
-  }
-  store_row16<BF>(grp, cn + cpf, sbo, re);
-  store_row16<BF>(grp, cn + cpf + 1, sbo, im);
-}
-
-// analysis B operand: for each zonal order m, K = northern latitudes j (padded to kpad);
-// field f owns the 2 cpf columns from 2 cpf f: the N + S combinations, then the N - S ones:
-//   scalar (cpf = 2):  w_j (F_N +- F_S)           (re, im)
-//   vector (cpf = 4):  wq_j (A_N +- A_S), wq_j (B_N +- B_S)   (A re, A im, B re, B im)
-// Thread per (K group of E latitudes, column pair p < nr / 2): reads the E northern and
-// mirrored southern Fourier coefficients of its pair once and writes four rows.
-template <bool BF>
-__global__ void k_tc_banal(const double2* __restrict__ F0, const double2* __restrict__ F1,
-                           const double* __restrict__ wts, unsigned char* __restrict__ B,
-                           const int* __restrict__ boff, int kpad, int T, int nlat, int nf, int cpf) {
-  constexpr int E = BF ? 8 : 4;
-  const int m = blockIdx.y;
-  const int np = nf * cpf / 2;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  const int g = idx / np, p = idx - g * np;
-  if (g * E >= kpad) return;
-  const int sbo = (kpad / E) * 128;
-  const int nh = nlat / 2;
-  const int f = (2 * p) / cpf, q = 2 * p - f * cpf;
-  const double2* Fq = (q < 2 ? F0 : F1) + ((size_t)f * (T + 1) + m) * nlat;
-  double2 a[E], b[E];
-  double w[E];
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int j = g * E + e;
-    const bool in = j < nh;
-    a[e] = in ? Fq[j] : make_double2(0.0, 0.0);
-    b[e] = in ? Fq[nlat - 1 - j] : make_double2(0.0, 0.0);
-    w[e] = in ? wts[j] : 0.0;
-  }
-  // the combinations in FP32 (the operand is rounded to TF32 / BF16 next; FP64 arithmetic is
-  // a scarce pipe on this GPU): only the conversions of the inputs touch FP64 values
-  float pr[E], pi[E], mr[E], mi[E];
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const float ax = (float)a[e].x, ay = (float)a[e].y, bx = (float)b[e].x, by = (float)b[e].y;
-    const float we = (float)w[e];
-    pr[e] = we * (ax + bx);
-    pi[e] = we * (ay + by);
-    mr[e] = we * (ax - bx);
-    mi[e] = we * (ay - by);
-  }
-  unsigned char* grp = B + boff[m] + (size_t)g * 128;
-  const int cn = 2 * cpf * f + q;  // N + S column; the N - S one is cpf further
-  store_row16<BF>(grp, cn, sbo, pr);
-  store_row16<BF>(grp, cn + 1, sbo, pi);
-  store_row16<BF>(grp, cn + cpf, sbo, mr);
-  store_row16<BF>(grp, cn + cpf + 1, sbo, mi);
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------------------------------
@@ -548,12 +530,10 @@ struct TcLegendre {
   int T = 0, nlat = 0, nh = 0, nlm = 0, max_fields = 0, bf16 = 0, E = 4, eb = 4, KC = 32;
   int ntile_s = 0, kpad_a = 0;
   unsigned char *tabPs = nullptr, *tabHs = nullptr, *tabPa = nullptr, *tabHa = nullptr;
-  unsigned char* B = nullptr;
   int* err = nullptr;
   const double *w = nullptr, *wq = nullptr;
   // launch plans: [synthesis, analysis][scalar (P jobs), vector ((P, H) pairs)]
   Sched sched[2][2];
-  int *boff_s = nullptr, *kpad_s = nullptr, *boff_a = nullptr;
   int kpad_smax = 0;  // largest K extent of a synthesis B operand
   int nsm = 0;
   StageProf* prof = nullptr;
@@ -629,33 +609,27 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
     }
   }
   t->ntile_s = (t->nh + 127) / 128;
-  const int ncols_max = TC_MAXCOL;
   const int kstep = bf16 ? 16 : 8;  // MMA K per instruction
   // ---- synthesis jobs: (m, tile, tab); rows = northern latitudes of the tile, K = all degrees
   // of m; B = [c | (-1)^(n-m) c] gives the northern and the southern values in one job -------
   std::vector<TabJob> tj;
   std::vector<Job> jsP, jsH;  // aligned: entry u of both is the same (m, tile)
-  std::vector<int> boff_s(T + 1), kpad_s(T + 1);
   long long aoff = 0;
-  int boff = 0;
   for (int m = 0; m <= T; ++m) {
     const int K = T + 1 - m;
     const int kpad = (K + kstep - 1) / kstep * kstep;  // K padded to whole k-steps only
     const int nchunk = (kpad + KC - 1) / KC;
     const int kl = kpad - (nchunk - 1) * KC;
-    boff_s[m] = boff;
-    kpad_s[m] = kpad;
-    boff += 2 * ncols_max * kpad * eb;
+    t->kpad_smax = std::max(t->kpad_smax, kpad);
     for (int tile = 0; tile < t->ntile_s; ++tile) {
       const int rows = std::min(128, (t->nh - 128 * tile + 7) / 8 * 8);
       tj.push_back(TabJob{aoff, m, rows, tile, nchunk, kl});
-      jsP.push_back(Job{aoff, boff_s[m], m, tile, nchunk, kpad, 0, kl, rows});
-      jsH.push_back(Job{aoff, boff_s[m], m, tile, nchunk, kpad, 1, kl, rows});
+      jsP.push_back(Job{aoff, m, tile, nchunk, kpad, 0, kl, rows});
+      jsH.push_back(Job{aoff, m, tile, nchunk, kpad, 1, kl, rows});
       aoff += (long long)rows * ((nchunk - 1) * KC + kl) * eb;
     }
   }
   const long long tab_s_bytes = aoff;
-  const int bsz_s = boff;
   // ---- analysis jobs: (m, degree tile, tab), rows = degrees of both parities, K = northern
   // latitudes; B = [N + S | N - S] of each field of zonal order m --------------------------
   t->kpad_a = (t->nh + kstep - 1) / kstep * kstep;
@@ -663,27 +637,19 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
   const int kl_a = t->kpad_a - (nchunk_a - 1) * KC;
   std::vector<TabJob> ta;
   std::vector<Job> jaP, jaH;
-  std::vector<int> boff_a(T + 1);
   aoff = 0;
-  boff = 0;
-  for (int m = 0; m <= T; ++m) {
-    boff_a[m] = boff;
-    boff += 2 * ncols_max * t->kpad_a * eb;
-  }
   for (int m = 0; m <= T; ++m) {
     const int K = T + 1 - m;
     const int ntiles = (K + 127) / 128;
     for (int tile = 0; tile < ntiles; ++tile) {
       const int rows = std::min(128, (K - 128 * tile + 7) / 8 * 8);
       ta.push_back(TabJob{aoff, m, rows, tile, nchunk_a, kl_a});
-      jaP.push_back(Job{aoff, boff_a[m], m, tile, nchunk_a, t->kpad_a, 0, kl_a, rows});
-      jaH.push_back(Job{aoff, boff_a[m], m, tile, nchunk_a, t->kpad_a, 1, kl_a, rows});
+      jaP.push_back(Job{aoff, m, tile, nchunk_a, t->kpad_a, 0, kl_a, rows});
+      jaH.push_back(Job{aoff, m, tile, nchunk_a, t->kpad_a, 1, kl_a, rows});
       aoff += (long long)rows * ((nchunk_a - 1) * KC + kl_a) * eb;
     }
   }
   const long long tab_a_bytes = aoff;
-  const int bsz_a = boff;
-  for (int v : kpad_s) t->kpad_smax = std::max(t->kpad_smax, v);
   // the largest B operand of any call (a vector pair: 2 x 4 max_fields columns over all
   // latitudes or all degrees) must fit one B buffer and two ring stages in shared memory
   {
@@ -700,10 +666,7 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
   TabJob *d_tj = nullptr, *d_ta = nullptr;
   if ((e = cudaMalloc(&t->tabPs, tab_s_bytes)) || (e = cudaMalloc(&t->tabHs, tab_s_bytes)) ||
       (e = cudaMalloc(&t->tabPa, tab_a_bytes)) || (e = cudaMalloc(&t->tabHa, tab_a_bytes)) ||
-      (e = cudaMalloc(&t->B, std::max(bsz_s, bsz_a))) || (e = cudaMalloc(&t->err, sizeof(int))) ||
-      (e = cudaMalloc(&t->boff_s, sizeof(int) * boff_s.size())) ||
-      (e = cudaMalloc(&t->kpad_s, sizeof(int) * kpad_s.size())) ||
-      (e = cudaMalloc(&t->boff_a, sizeof(int) * boff_a.size())) ||
+      (e = cudaMalloc(&t->err, sizeof(int))) ||
       (e = cudaMalloc(&d_tj, sizeof(TabJob) * tj.size())) || (e = cudaMalloc(&d_ta, sizeof(TabJob) * ta.size())) ||
       (e = make_sched(jsP, nullptr, t->nsm, t->sched[0][0])) || (e = make_sched(jsP, &jsH, t->nsm, t->sched[0][1])) ||
       (e = make_sched(jaP, nullptr, t->nsm, t->sched[1][0])) || (e = make_sched(jaP, &jaH, t->nsm, t->sched[1][1]))) {
@@ -714,9 +677,6 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
     return fail(REXI_ENOMEM, "tensor-core Legendre tables: cudaMalloc failed: %s", cudaGetErrorString(e));
   }
   cudaMemset(t->err, 0, sizeof(int));
-  cudaMemcpy(t->boff_s, boff_s.data(), sizeof(int) * boff_s.size(), cudaMemcpyHostToDevice);
-  cudaMemcpy(t->kpad_s, kpad_s.data(), sizeof(int) * kpad_s.size(), cudaMemcpyHostToDevice);
-  cudaMemcpy(t->boff_a, boff_a.data(), sizeof(int) * boff_a.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(d_tj, tj.data(), sizeof(TabJob) * tj.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(d_ta, ta.data(), sizeof(TabJob) * ta.size(), cudaMemcpyHostToDevice);
   k_tc_table<<<(int)tj.size(), 128, 0, stream>>>(P, t->tabPs, d_tj, (int)tj.size(), T, t->nh, 1, t->bf16);
@@ -741,8 +701,7 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
 
 void tc_legendre_destroy(TcLegendre* t) {
   if (!t) return;
-  for (void* p : {(void*)t->tabPs, (void*)t->tabHs, (void*)t->tabPa, (void*)t->tabHa, (void*)t->B, (void*)t->err,
-                  (void*)t->boff_s, (void*)t->kpad_s, (void*)t->boff_a})
+  for (void* p : {(void*)t->tabPs, (void*)t->tabHs, (void*)t->tabPa, (void*)t->tabHa, (void*)t->err})
     cudaFree(p);
   for (auto& row : t->sched)
     for (Sched& sc : row) {
@@ -754,15 +713,17 @@ void tc_legendre_destroy(TcLegendre* t) {
 
 // One GEMM launch with the fused epilogue: ncols = MMA N (the real columns 2 nf cpf, padded to
 // a multiple of 16; the padding columns of B are never written and their sums never read).
-static int gemm(TcLegendre* t, bool synth, bool vector, int nf, double2* out0, double2* out1, double inv_a,
-                cudaStream_t s) {
+static int gemm(TcLegendre* t, bool synth, bool vector, int nf, const double2* in0, const double2* in1,
+                const double* wts, double2* out0, double2* out1, double inv_a, cudaStream_t s) {
   const int cpf = vector ? 4 : 2;
   const int ncols = std::max(16, (2 * nf * cpf + 15) / 16 * 16);
   const Sched& sc = t->sched[synth ? 0 : 1][vector ? 1 : 0];
   GemmArgs g;
   g.tabP = synth ? t->tabPs : t->tabPa;
   g.tabH = synth ? t->tabHs : t->tabHa;
-  g.B = t->B;
+  g.in0 = in0;
+  g.in1 = in1;
+  g.wts = wts;
   g.jobs = sc.jobs;
   g.cta_off = sc.off;
   g.ncols = ncols;
@@ -801,45 +762,22 @@ static int gemm(TcLegendre* t, bool synth, bool vector, int nf, double2* out0, d
   return e ? cuda_fail(e, "k_tc_gemm launch") : REXI_OK;
 }
 
-// B packing launches: a thread per (K group of E elements, real column pair), 128 per block
-static void pack_synth(TcLegendre* t, const double2* s0, const double2* s1, int nf, int cpf, cudaStream_t s) {
-  const int np = nf * cpf / 2, groups = t->kpad_smax / t->E;
-  const dim3 grid((groups * np + 127) / 128, t->T + 1);
-  const int ph = t->prof ? t->prof->begin(1) : -1;
-  if (t->bf16) k_tc_bsynth<true><<<grid, 128, 0, s>>>(s0, s1, t->B, t->boff_s, t->kpad_s, t->T, t->nlm, nf, cpf);
-  else k_tc_bsynth<false><<<grid, 128, 0, s>>>(s0, s1, t->B, t->boff_s, t->kpad_s, t->T, t->nlm, nf, cpf);
-  if (t->prof) t->prof->end(ph);
-}
-static void pack_anal(TcLegendre* t, const double2* F0, const double2* F1, const double* wts, int nf, int cpf,
-                      cudaStream_t s) {
-  const int np = nf * cpf / 2, groups = t->kpad_a / t->E;
-  const dim3 grid((groups * np + 127) / 128, t->T + 1);
-  const int ph = t->prof ? t->prof->begin(1) : -1;
-  if (t->bf16) k_tc_banal<true><<<grid, 128, 0, s>>>(F0, F1, wts, t->B, t->boff_a, t->kpad_a, t->T, t->nlat, nf, cpf);
-  else k_tc_banal<false><<<grid, 128, 0, s>>>(F0, F1, wts, t->B, t->boff_a, t->kpad_a, t->T, t->nlat, nf, cpf);
-  if (t->prof) t->prof->end(ph);
-}
-
 int tc_leg_synth(TcLegendre* t, const double2* spec, double2* F, int nf, cudaStream_t s) {
-  pack_synth(t, spec, spec, nf, 2, s);
-  return gemm(t, true, false, nf, F, F, 0.0, s);
+  return gemm(t, true, false, nf, spec, spec, nullptr, F, F, 0.0, s);
 }
 
 int tc_leg_synth_uv(TcLegendre* t, const double2* psi, const double2* chi, double2* FU, double2* FV, int nf,
                     double inv_a, cudaStream_t s) {
-  pack_synth(t, psi, chi, nf, 4, s);
-  return gemm(t, true, true, nf, FU, FV, inv_a, s);
+  return gemm(t, true, true, nf, psi, chi, nullptr, FU, FV, inv_a, s);
 }
 
 int tc_leg_anal(TcLegendre* t, const double2* F, double2* spec, int nf, cudaStream_t s) {
-  pack_anal(t, F, F, t->w, nf, 2, s);
-  return gemm(t, false, false, nf, spec, spec, 0.0, s);
+  return gemm(t, false, false, nf, F, F, t->w, spec, spec, 0.0, s);
 }
 
 int tc_leg_anal_divcurl(TcLegendre* t, const double2* FA, const double2* FB, double2* dv, double2* cu, int nf,
                         double inv_a, cudaStream_t s) {
-  pack_anal(t, FA, FB, t->wq, nf, 4, s);
-  return gemm(t, false, true, nf, dv, cu, inv_a, s);
+  return gemm(t, false, true, nf, FA, FB, t->wq, dv, cu, inv_a, s);
 }
 
 void tc_legendre_set_prof(TcLegendre* t, StageProf* prof) {
