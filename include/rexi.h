@@ -124,9 +124,12 @@ int rexi_plan_destroy(rexi_plan* plan);
 int rexi_step(rexi_plan* plan, const void* U0, void* U1, int batch);
 
 /*
- * rexi_step_host -- rexi_step on HOST buffers: copies U0 to plan-owned device staging
- * memory, runs the step and copies U1 back, all on the plan stream, then synchronises it.
- * U0/U1: host arrays of batch*3*nlm complex128 (pinned memory gives full copy bandwidth).
+ * rexi_step_host -- rexi_step on HOST buffers, on the plan stream, then synchronises it.
+ * FP64 plans, and any plan given pageable memory: U0 is copied to plan-owned device staging
+ * memory, the step runs there and U1 is copied back.  Mixed plans given pinned (mapped)
+ * buffers: the step's kernels read U0 and write U1 in host memory directly over the host link
+ * (each is touched once), without staging copies.
+ * U0/U1: host arrays of batch*3*nlm complex128 (pinned memory gives full bandwidth).
  * Errors: REXI_EINVAL, REXI_ECUDA.
  */
 int rexi_step_host(rexi_plan* plan, const double* U0, double* U1, int batch);

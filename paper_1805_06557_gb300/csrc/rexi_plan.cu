@@ -786,11 +786,35 @@ extern "C" int rexi_step(rexi_plan* p, const void* U0, void* U1, int batch) {
   return engine_launch(p->e, *L, (const double2*)U0, (double2*)U1);
 }
 
+// Device address of page-locked host memory mapped into the device's address space (pinned
+// allocations are, with unified addressing), else null.
+static void* mapped_host(const void* h) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return (a.type == cudaMemoryTypeHost && a.devicePointer) ? a.devicePointer : nullptr;
+}
+
 extern "C" int rexi_step_host(rexi_plan* p, const double* U0, double* U1, int batch) {
   if (!p || !U0 || !U1) return fail(REXI_EINVAL, "rexi_step_host: null argument");
   if (batch < 1 || batch > p->d.max_batch)
     return fail(REXI_EINVAL, "rexi_step_host: batch %d outside [1, %d]", batch, p->d.max_batch);
   const size_t bytes = sizeof(double2) * 3 * (size_t)p->nlm * batch;
+  if (p->d.precision == REXI_MIXED) {
+    // a mixed step reads U0 once (the right-hand-side pre-pass, and Phi in the finalize) and
+    // writes U1 once (the finalize): with mapped pinned buffers those kernels use the host
+    // memory in place over the host link, without the staging copies
+    const void* d0 = mapped_host(U0);
+    void* d1 = mapped_host(U1);
+    if (d0 && d1) {
+      int rc = rexi_step(p, d0, d1, batch);
+      if (rc) return rc;
+      REXI_CUDA_TRY(cudaStreamSynchronize(p->e.stream));
+      return REXI_OK;
+    }
+  }
   REXI_CUDA_TRY(cudaMemcpyAsync(p->stage_in, U0, bytes, cudaMemcpyHostToDevice, p->e.stream));
   int rc = rexi_step(p, p->stage_in, p->stage_out, batch);
   if (rc) return rc;

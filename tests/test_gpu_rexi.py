@@ -226,6 +226,27 @@ def test_step_host_matches_device(env):
     plan.close()
 
 
+def test_step_host_mixed_pinned_and_pageable(env):
+    """Mixed plans read and write pinned (mapped) host buffers in place over the host link and
+    stage pageable ones through device copies: both equal the device step bit for bit."""
+    torch, rexi = env
+    T, N, dt, B = 63, 256, 3600.0, 5
+    p0, Xc, _ = contour(T, dt, N)
+    U0 = np.stack([syn.gaussian_state(T, 310 + i) for i in range(B)])
+    plan = rexi.Plan(T, N, dt, OM, A, PB, p0=p0, Xc=Xc, precision="mixed", max_batch=B)
+    u0 = torch.from_numpy(U0).cuda()
+    u1 = torch.empty_like(u0)
+    plan.step(u0, u1, B)
+    plan.sync()
+    ref = u1.cpu().numpy()
+    hin = torch.from_numpy(U0).pin_memory()
+    hout = torch.zeros_like(hin).pin_memory()
+    plan.step_host_ptr(hin.data_ptr(), hout.data_ptr(), B)  # pinned: in place
+    assert np.array_equal(hout.numpy(), ref)
+    assert np.array_equal(plan.step_host(U0), ref)            # pageable: staged
+    plan.close()
+
+
 def test_explicit_poles_and_zero_input(env):
     """Poles given explicitly (the oracle's) give the same result; a zero state stays zero."""
     torch, rexi = env
