@@ -22,6 +22,7 @@
 // (m, tile), which run as consecutive jobs of one CTA).  All mbarrier waits are bounded; on a
 // timeout the kernel records an error flag.
 #include <algorithm>
+#include <map>
 #include <cuda_bf16.h>
 #include <vector>
 
@@ -50,6 +51,7 @@ struct Job {
                     // chunk holds rows x KC elements; the MMA reads all 128 rows of a ring
                     // stage, and the accumulator rows past `rows` hold stale sums that the
                     // epilogue never stores
+  int newb;         // 1: the job starts a B group (consecutive jobs of one m share a B operand)
 };
 
 struct GemmArgs {
@@ -343,15 +345,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
       if (!ok) atomicExch(g.err, 3);
     }
   } else if (warp >= TC_BUILD0) {
-    // B operand of job q into buffer (q / bstep) % NB once its previous user has released it
+    // B operand of B group bg (first job q) into buffer bg % NB once its previous group has
+    // released it
     // (its MMAs completed): written with ordinary shared-memory stores, made visible to the
     // tensor cores' (async) proxy by a proxy fence, then announced on bfull by one thread
     // (every thread of the builder warps takes the same path: the outcome of the bounded
     // wait is and-reduced over them, so that a timeout ends the loop for all at once)
     const int bt = tid - TC_BUILD0 * 32;
-    const int bstep = g.pair ? 2 : 1;  // the (P, H) jobs of a vector transform share a B buffer
-    for (int q = 0; q < nj; q += bstep) {
-      const int b = (q / bstep) % NB, u = (q / bstep) / NB;
+    int bg = -1;  // B group of the job: the jobs of one group (one m) share the buffer
+    for (int q = 0; q < nj; ++q) {
+      if (!sjobs[q].newb) continue;
+      ++bg;
+      const int b = bg % NB, u = bg / NB;
       const bool ok = builders_all(u == 0 || tc::mbar_wait(bempty0 + 8 * b, (u - 1) & 1));
       if (!ok) {
         if (bt == 0) atomicExch(g.err, 5);
@@ -370,13 +375,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
       const uint32_t sboA = (uint32_t)(KC / E) * 128u;
       int s = 0;
       uint32_t round = 0;
-      // B buffer of job i: (i / bstep) % NB; the (P, H) jobs of a vector transform share theirs
-      const int bstep = g.pair ? 2 : 1;
+      // B group bg (jobs from one with newb to the next) uses buffer bg % NB
+      int bg = -1;
       for (int i = 0; i < nj && ok; ++i) {
         const Job jb = sjobs[i];
-        const int bi = i / bstep, b = bi % NB, ub = bi / NB, acc = i % njb, ua = i / njb;
-        const bool first_of_b = i % bstep == 0, last_of_b = i % bstep == bstep - 1;
-        if (first_of_b) ok = tc::mbar_wait(bfull0 + 8 * b, ub & 1);
+        if (jb.newb) ++bg;
+        const int b = bg % NB, ub = bg / NB, acc = i % njb, ua = i / njb;
+        const bool last_of_b = i + 1 == nj || sjobs[i + 1].newb;
+        if (jb.newb) ok = tc::mbar_wait(bfull0 + 8 * b, ub & 1);
         if (ok && ua > 0) ok = tc::mbar_wait(tempty0 + 8 * acc, (ua - 1) & 1);
         if (!ok) break;
         tc::fence_after_sync();
@@ -541,31 +547,67 @@ struct TcLegendre {
 
 static int tc_fail(const char* what, cudaError_t e) { return cuda_fail(e, what); }
 
-// Assigns units (one job, or a (P, H) pair when H is given; cost = A bytes, rows x K) to
-// min(units, nsm) CTAs: longest first, each to the least-loaded CTA so far; a CTA runs its
-// units in that order.
+// Per-CTA job lists.  A unit is all jobs of one zonal order m (the tiles of m; with H given,
+// each tile's (P, H) pair), which then run back to back and share one B operand (the first job
+// of a unit starts a B group, `newb`); a unit heavier than half the mean CTA load is split into
+// its tiles, so that the heaviest zonal orders still balance.  Units go longest first (cost =
+// A bytes, rows x K), each to the least-loaded CTA so far.
 static cudaError_t make_sched(const std::vector<Job>& P, const std::vector<Job>* H, int nsm, Sched& sc) {
-  const int nu = (int)P.size();
+  auto cost = [&](int u) { return (long long)P[u].rows * P[u].kpad * (H ? 2 : 1); };
+  std::vector<std::vector<int>> units;
+  {
+    std::map<int, std::vector<int>> by_m;
+    long long total = 0;
+    for (int u = 0; u < (int)P.size(); ++u) {
+      by_m[P[u].m].push_back(u);
+      total += cost(u);
+    }
+    const long long cap = std::max<long long>(1, total / std::max(1, nsm) / 2);
+    for (auto& kv : by_m) {
+      long long c = 0;
+      for (int u : kv.second) c += cost(u);
+      if (c > cap && kv.second.size() > 1) {
+        for (int u : kv.second) units.push_back({u});
+      } else {
+        units.push_back(kv.second);
+      }
+    }
+  }
+  const int nu = (int)units.size();
   const int grid = std::max(1, std::min(nu, nsm));
-  auto cost = [&](int u) { return (long long)P[u].rows * P[u].kpad; };
+  auto ucost = [&](int k) {
+    long long c = 0;
+    for (int u : units[k]) c += cost(u);
+    return c;
+  };
   std::vector<int> order(nu);
-  for (int u = 0; u < nu; ++u) order[u] = u;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+  for (int k = 0; k < nu; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ucost(a) > ucost(b); });
   std::vector<long long> load(grid, 0);
   std::vector<std::vector<int>> per(grid);
-  for (int u : order) {
+  for (int k : order) {
     const int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-    per[c].push_back(u);
-    load[c] += cost(u);
+    per[c].push_back(k);
+    load[c] += ucost(k);
   }
   std::vector<Job> jobs;
   std::vector<int> off(grid + 1);
   sc.nj_max = 0;
   for (int c = 0; c < grid; ++c) {
     off[c] = (int)jobs.size();
-    for (int u : per[c]) {
-      jobs.push_back(P[u]);
-      if (H) jobs.push_back((*H)[u]);
+    for (int k : per[c]) {
+      bool first = true;
+      for (int u : units[k]) {
+        Job jp = P[u];
+        jp.newb = first ? 1 : 0;
+        first = false;
+        jobs.push_back(jp);
+        if (H) {
+          Job jh = (*H)[u];
+          jh.newb = 0;
+          jobs.push_back(jh);
+        }
+      }
     }
     sc.nj_max = std::max(sc.nj_max, (int)jobs.size() - off[c]);
   }
