@@ -191,6 +191,11 @@ struct Engine {
   int precision = 0, Ttab = 0, device = 0, nsm = 0, kmax = 0, nseg_max = 0;
   double omega = 0, radius = 0, phibar = 0;
   cudaStream_t stream = nullptr;
+  // mixed plans: the light kernel runs on `side`, forked after the right-hand-side pre-pass and
+  // joined before the finalize, beside the heavy kernels on `stream` (the two write disjoint
+  // partial slots and scratch regions)
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
   D4* tab64 = nullptr;
   float4* tab32 = nullptr;
   TabDF* tabdf = nullptr;
@@ -212,6 +217,7 @@ struct Engine {
   struct Pend {
     cudaEvent_t a, b;
     int kid;
+    cudaStream_t st;  // the stream the pair is recorded on
   };
   std::vector<Pend> pending;
   std::vector<cudaEvent_t> event_pool;
@@ -249,6 +255,14 @@ void engine_free(Engine& e) {
   for (auto ev : e.event_pool) cudaEventDestroy(ev);
   e.pending.clear();
   e.event_pool.clear();
+  if (e.side) {
+    cudaStreamSynchronize(e.side);
+    cudaStreamDestroy(e.side);
+  }
+  if (e.fork) cudaEventDestroy(e.fork);
+  if (e.join) cudaEventDestroy(e.join);
+  e.side = nullptr;
+  e.fork = e.join = nullptr;
 }
 
 size_t rhs32_bytes(size_t elems) { return (sizeof(Rhs32) * elems + 255) / 256 * 256; }
@@ -262,6 +276,13 @@ int engine_init(Engine& e, int precision, int Ttab, double omega, double radius,
   e.radius = radius;
   e.phibar = phibar;
   e.stream = stream;
+  if (precision == REXI_MIXED) {
+    cudaError_t es;
+    if ((es = cudaStreamCreateWithFlags(&e.side, cudaStreamNonBlocking)) ||
+        (es = cudaEventCreateWithFlags(&e.fork, cudaEventDisableTiming)) ||
+        (es = cudaEventCreateWithFlags(&e.join, cudaEventDisableTiming)))
+      return cuda_fail(es, "engine side stream");
+  }
   e.kmax = Ttab + 1;
   e.nseg_max = (e.kmax + LSEG - 1) / LSEG;
   if (cudaGetDevice(&e.device) != cudaSuccess) return fail(REXI_ECUDA, "no CUDA device");
@@ -537,15 +558,16 @@ cudaEvent_t take_event(Engine& e) {
   cudaEventCreate(&ev);
   return ev;
 }
-int prof_begin(Engine& e, int kid) {
+int prof_begin(Engine& e, int kid, cudaStream_t st = nullptr) {
   if (!e.profiling) return -1;
   Engine::Pend q{take_event(e), take_event(e), kid};
-  cudaEventRecord(q.a, e.stream);
+  q.st = st ? st : e.stream;
+  cudaEventRecord(q.a, q.st);
   e.pending.push_back(q);
   return (int)e.pending.size() - 1;
 }
 void prof_end(Engine& e, int h) {
-  if (h >= 0) cudaEventRecord(e.pending[h].b, e.stream);
+  if (h >= 0) cudaEventRecord(e.pending[h].b, e.pending[h].st);
 }
 
 // Launches one REXI step of the launch set.  No allocation.
@@ -593,12 +615,15 @@ int engine_launch(Engine& e, const LaunchSet& L, const double2* U0, double2* U1)
     a.kmax = e.kmax;
     a.nseg_max = e.nseg_max;
     a.warps_light = e.grid_light * MIX_WARPS;
-    if (a.ntiles_light) {
-      h = prof_begin(e, 2);
-      k_rexi_light<<<e.grid_light, MIX_WARPS * 32, 0, e.stream>>>(a);
-      prof_end(e, h);
-    }
     const int nq = L.ntiles_quad, np = L.ntiles_pair, n1 = a.ntiles_heavy - nq - np;
+    // light beside heavy: the heavy kernels are launched first and take the SMs; light blocks
+    // fill what the heavy grid leaves (its tail, or the warps without tiles of a small launch)
+    const bool both = a.ntiles_light && a.ntiles_heavy && e.side;
+    cudaStream_t ls = both ? e.side : e.stream;
+    if (both) {
+      cudaEventRecord(e.fork, e.stream);
+      cudaStreamWaitEvent(e.side, e.fork, 0);
+    }
     int t0 = L.ntiles_light;
     if (nq) {  // tiles of two state pairs (half-warps, 16-pole groups)
       h = prof_begin(e, 3);
@@ -616,6 +641,15 @@ int engine_launch(Engine& e, const LaunchSet& L, const double2* U0, double2* U1)
       h = prof_begin(e, 3);
       k_rexi_heavy<1, false><<<e.grid_heavy, MIX_WARPS * 32, heavy_smem_bytes<1>(), e.stream>>>(a, t0, n1);
       prof_end(e, h);
+    }
+    if (a.ntiles_light) {
+      h = prof_begin(e, 2, ls);
+      k_rexi_light<<<e.grid_light, MIX_WARPS * 32, 0, ls>>>(a);
+      prof_end(e, h);
+    }
+    if (both) {
+      cudaEventRecord(e.join, e.side);
+      cudaStreamWaitEvent(e.stream, e.join, 0);
     }
   }
   cudaError_t ce = cudaGetLastError();
