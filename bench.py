@@ -753,7 +753,13 @@ def main():
         kernels[kname] = {"bound": "alu", "pipe": pipe, "flops_per_chain_element": fl, "poles": npoles,
                           "ms": kms / kn, "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                           "frac": flops / avg_s / 1e12 / peak}
-    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    # the dominant kernel is the one with the most algorithmic work (the heavy kernel: 85 % of the
+    # launch list); the light kernel runs beside the heavy ones on a side stream, so its event
+    # interval spans its wait for SM room and event times do not rank the kernels
+    dom = max(kernels, key=lambda k: kernels[k]["achieved"] * kernels[k]["ms"])
+    if "k_rexi_light" in kernels:
+        kernels["k_rexi_light"]["note"] = ("launched beside the heavy kernels on a side stream: the event "
+                                           "interval includes the wait for SM room")
     tr = TRAFFIC.get(dom)
     roof = dict(kernels[dom], kernel=dom,
                 traffic=(tr[0] * B / tr[1]) if tr else None,
