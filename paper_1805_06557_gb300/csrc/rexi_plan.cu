@@ -616,9 +616,13 @@ int engine_launch(Engine& e, const LaunchSet& L, const double2* U0, double2* U1)
     a.nseg_max = e.nseg_max;
     a.warps_light = e.grid_light * MIX_WARPS;
     const int nq = L.ntiles_quad, np = L.ntiles_pair, n1 = a.ntiles_heavy - nq - np;
-    // light beside heavy: the heavy kernels are launched first and take the SMs; light blocks
-    // fill what the heavy grid leaves (its tail, or the warps without tiles of a small launch)
-    const bool both = a.ntiles_light && a.ntiles_heavy && e.side;
+    // light beside heavy, when the heavy tiles do not fill the heavy grid's resident warps (a
+    // latency-bound launch, e.g. one state): the light blocks then run in the room the idle
+    // heavy warps leave.  A batched launch fills every SM with heavy warps, so light would only
+    // share the tail, and the order in which the two become resident is not fixed: it stays
+    // after heavy on the plan stream.
+    const bool both = a.ntiles_light && a.ntiles_heavy && e.side &&
+                      a.ntiles_heavy < (long long)std::max(e.grid_heavy, e.grid_heavy2) * MIX_WARPS;
     cudaStream_t ls = both ? e.side : e.stream;
     if (both) {
       cudaEventRecord(e.fork, e.stream);
