@@ -123,14 +123,15 @@ def test_tc_field_counts_scalar(env, prec, nf):
 
 
 @pytest.mark.parametrize("prec", ["tf32", "bf16"])
-@pytest.mark.parametrize("nf", [1, 3, 4])
+@pytest.mark.parametrize("nf", [1, 3, 4, 8])
 def test_tc_field_counts_vector(env, prec, nf):
     """Vector field counts: one 8-column group per field, the (P, H) job pairs of every
-    (m, tile) combined in the epilogue, nf = 4 filling 64 columns (T = 63, 96 x 192 grid)."""
+    (m, tile) combined in the epilogue; nf = 8 fills 64 columns (two accumulator buffers in
+    TMEM) (T = 63, 96 x 192 grid)."""
     torch, rexi = env
     T, nlat, nlon = 63, 96, 192
     og = osht.Grid(T, nlat, nlon, A)
-    p = rexi.ShPlan(T, nlat, nlon, A, prec, max_fields=4)
+    p = rexi.ShPlan(T, nlat, nlon, A, prec, max_fields=max(nf, 4))
     psi, chi = _spec(T, 40 + nf, nf), _spec(T, 50 + nf, nf)
     psi[:, 0] = chi[:, 0] = 0
     U = torch.empty(nf, nlat, nlon, dtype=torch.float64, device="cuda")
