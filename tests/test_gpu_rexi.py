@@ -79,6 +79,21 @@ def test_config_T63_N256(env, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_golden_step_on_paper_contour(env, golden_step, prec):
+    """The stored T7 step of tests/golden/ (written from the oracle) on the contour that Sec. 5
+    starts from: p0 = 10, p_{+-1} = +-30i, N = 128, dt = 21600 s."""
+    k, U0, U1 = golden_step("rexi_step_T7_N128.txt")
+    assert (k["Omega"], k["radius"], k["Phibar"]) == (OM, A, PB)
+    T, N, dt = int(k["T"]), int(k["N"]), k["dt"]
+    z, w = oc.rexi_coefficients(N, k["p0"], k["Xc"])
+    X = orx.spectrum_bound(T, dt, OM, A, PB)
+    out, info = run_plan(env, T, N, dt, U0, prec, k["p0"], k["Xc"])
+    err = orx.rel_l2(out, U1, T)
+    tol = fp64_tol(z, w, X) if prec == "fp64" else 1e-8
+    assert np.all(err < tol), (err, tol, info)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("T,N", [(1, 8), (2, 40), (5, 33), (17, 96), (40, 64), (47, 200)])
 def test_small_and_ragged(env, prec, T, N):
     """Tiny truncations (single-element chains), pole counts that are not a multiple of 32,
