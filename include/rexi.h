@@ -90,7 +90,9 @@ typedef struct rexi_plan_desc {
                       /* (a bound on the energy-norm size of their term relative to U0, dt L */
                       /* being skew-adjoint in that norm) are left out while their summed    */
                       /* gain stays <= prune_tau, conjugate pairs together; 0: default    */
-                      /* (REXI_MIXED 2^-60, REXI_FP64 none: every pole is solved); < 0: none */
+                      /* (REXI_MIXED 1e-10, REXI_FP64 none: every pole is solved); < 0: none */
+                      /* REXI_MIXED then completes the last 32-pole light group with the    */
+                      /* largest pruned poles (pairs whole), so fewer may be left out       */
 } rexi_plan_desc;
 
 /*

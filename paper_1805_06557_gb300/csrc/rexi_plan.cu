@@ -56,16 +56,18 @@ struct PoleSet {
 };
 
 // Default pruning threshold of mixed plans: the summed gain of the poles left out is at most
-// 2^-60 (the change of the result in the energy norm, relative to the state: 1/128 of one FP64
-// unit roundoff).
-constexpr double PRUNE_TAU_MIXED = 8.673617379884035e-19;
+// 1e-10, the change of the result in the energy norm relative to the state: 1/100 of the 1e-8
+// relative error the mixed path is held to.  The far poles that pruning removes act on U0
+// nearly as the scalar w/z, so each field changes by about the same relative amount.
+constexpr double PRUNE_TAU_MIXED = 1e-10;
 
 // Orders (and pads) the poles.  Every pole n has the gain g_n = |w_n| / dist(z_n, [-iX, iX]),
 // a bound on the energy-norm size of its term w_n (z_n - dt L)^-1 U0 relative to U0 (dt L is
 // skew-adjoint in the energy inner product with its spectrum in [-iX, iX]).  Pruning: the
 // poles of smallest gain are left out while their summed gain stays <= prune_tau (conjugate
 // pairs, which have equal gains, stay together); prune_tau = 0 selects the default (mixed:
-// 2^-60, FP64: no pruning), prune_tau < 0 no pruning.  FP64: the kept poles in the given
+// 1e-10, FP64: no pruning), prune_tau < 0 no pruning; mixed plans then refill the last light
+// group's idle lanes with the largest pruned poles.  FP64: the kept poles in the given
 // order, padding at the end.
 // MIXED: light poles first, heavy ones (gain > heavy_tau, padded to whole groups) last.
 int make_poleset(PoleSet& ps, int precision, int T, int N, double dt, double X, const cplx* z,
@@ -92,7 +94,22 @@ int make_poleset(PoleSet& ps, int precision, int T, int N, double dt, double X, 
     while (nkeep > 1 && tail + gain[by_gain[nkeep - 1]] <= ptau) tail += gain[by_gain[--nkeep]];
     while (nkeep < N && nkeep > 0 && gain[by_gain[nkeep]] == gain[by_gain[nkeep - 1]])  // keep pairs whole
       tail -= gain[by_gain[nkeep++]];
-    ps.pruned_gain = std::max(tail, 0.0);
+    if (precision == REXI_MIXED) {
+      // light poles are solved 32 to a warp: the largest pruned poles fill the last light
+      // group's idle lanes (conjugate pairs whole), at no cost and with a smaller pruned gain
+      const double tau = heavy_tau < 0 ? 1e-3 : heavy_tau;
+      int nh = 0;
+      for (int i = 0; i < nkeep; ++i) nh += gain[by_gain[i]] > tau;
+      const int nh16 = std::min((nh + heavy_align - 1) / heavy_align * heavy_align, nkeep);
+      int room = nh16 < nkeep ? (nkeep - nh16 + 31) / 32 * 32 - (nkeep - nh16) : 0;
+      while (room > 0 && nkeep < N) {
+        const int take = nkeep + 1 < N && gain[by_gain[nkeep + 1]] == gain[by_gain[nkeep]] ? 2 : 1;
+        if (take > room) break;
+        nkeep += take;
+        room -= take;
+      }
+    }
+    for (int i = N - 1; i >= nkeep; --i) ps.pruned_gain += gain[by_gain[i]];  // smallest first
   }
   std::vector<char> keep(N, 0);
   for (int i = 0; i < nkeep; ++i) keep[by_gain[i]] = 1;
