@@ -756,7 +756,7 @@ def main():
         kernels[kname] = {"bound": "alu", "pipe": pipe, "flops_per_chain_element": fl, "poles": npoles,
                           "ms": kms / kn, "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                           "frac": flops / avg_s / 1e12 / peak}
-    # the dominant kernel is the one with the most algorithmic work (the heavy kernel: 85 % of the
+    # the dominant kernel is the one with the most algorithmic work (the heavy kernel: 90 % of the
     # launch list).  Where the heavy tiles leave resident warps idle (one-state steps) the light
     # kernel runs beside them on a side stream, and its event interval then spans its wait for
     # SM room, so event times alone do not rank the kernels; batched steps run it after them
