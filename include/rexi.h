@@ -65,6 +65,22 @@ int rexi_coeffs(int N, double p0, double Xc, int phi, double* z_out, double* w_o
  */
 int rexi_contour_select(double X, int N, double* p0, double* Xc);
 
+/*
+ * rexi_select_poles -- the pole classes a plan would use, computed on the host (no GPU).
+ *   precision    REXI_FP64 or REXI_MIXED
+ *   z, w         N poles and weights, caller-owned host arrays of 2N doubles (re, im)
+ *   X            half-width of the spectrum [-iX, iX] (rexi_spectrum_bound)
+ *   heavy_tau, prune_tau   as in rexi_plan_desc (< 0 / 0 select the defaults)
+ *   heavy_align  16 (plans with max_batch >= 4: state pairs on half-warps) or 32
+ *   cls          caller-owned array of N ints: 1 heavy (FP32 solve refined with a double-float
+ *                residual; every solved pole of an FP64 plan), 0 light, -1 pruned
+ *   pruned_gain  optional: summed gain of the pruned poles (bound on the relative energy-norm
+ *                change of the result, Sec. 4.2 contour sum with those terms left out)
+ * The gain of pole n is |w_n| / dist(z_n, [-iX, iX]).  Errors: REXI_EINVAL (bad arguments or a
+ * zero pole). */
+int rexi_select_poles(int precision, int N, const double* z, const double* w, double X, double heavy_tau,
+                      double prune_tau, int heavy_align, int* cls, double* pruned_gain);
+
 /* X = dt (sqrt(phibar T (T+1)) / radius + 2 omega): bound on |dt lambda| over the spectrum
  * of dt L (gravity-wave frequency of degree T plus the largest Coriolis frequency). */
 double rexi_spectrum_bound(int T, double dt, double omega, double radius, double phibar);

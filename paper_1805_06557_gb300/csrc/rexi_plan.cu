@@ -52,6 +52,7 @@ struct PoleSet {
   std::vector<cplx> z, w;   // internal order, padded, unscaled
   std::vector<int> heavy;
   std::vector<cplx> zp, wp; // poles left out (reported by rexi_plan_get_poles)
+  std::vector<int> cls;     // per input pole: 1 heavy, 0 light, -1 pruned
   int pole0 = -1;           // position in the device arena (-1: not uploaded)
 };
 
@@ -146,6 +147,9 @@ int make_poleset(PoleSet& ps, int precision, int T, int N, double dt, double X, 
       if (keep[n]) push(z[n], w[n], 1);
     for (int i = 0; i < npad; ++i) push(1.0, 0.0, 1);
     ps.n_heavy = nkeep;
+    ps.cls.assign(N, -1);
+    for (int n = 0; n < N; ++n)
+      if (keep[n]) ps.cls[n] = 1;
     ps.g_light = 0;
     ps.g_heavy = ps.ngroups;
     ps.g_heavy16 = 2 * ps.ngroups;
@@ -176,6 +180,9 @@ int make_poleset(PoleSet& ps, int precision, int T, int N, double dt, double X, 
     if (hv[n]) push(z[n], w[n], 1);
   for (int i = nh16; i < hpad; ++i) push(1.0, 0.0, 1);
   ps.n_heavy = nh16;
+  ps.cls.assign(N, -1);
+  for (int n = 0; n < N; ++n)
+    if (keep[n]) ps.cls[n] = hv[n];
   ps.g_light = lpad / 32;
   ps.g_heavy = hpad / 32;
   ps.g_heavy16 = nh16 / 16;
@@ -937,6 +944,28 @@ extern "C" int rexi_plan_get_poles(const rexi_plan* p, double* z, double* w, int
     }
     if (heavy) heavy[k] = -1;
   }
+  return REXI_OK;
+}
+
+extern "C" int rexi_select_poles(int precision, int N, const double* z, const double* w, double X,
+                                 double heavy_tau, double prune_tau, int heavy_align, int* cls,
+                                 double* pruned_gain) {
+  if (N < 1 || !z || !w || !cls) return fail(REXI_EINVAL, "rexi_select_poles: need N >= 1 and z, w, cls");
+  if (precision != REXI_FP64 && precision != REXI_MIXED)
+    return fail(REXI_EINVAL, "rexi_select_poles: unknown precision %d", precision);
+  if (heavy_align != 16 && heavy_align != 32)
+    return fail(REXI_EINVAL, "rexi_select_poles: heavy_align must be 16 or 32");
+  if (!(X >= 0.0) || !std::isfinite(X)) return fail(REXI_EINVAL, "rexi_select_poles: need finite X >= 0");
+  std::vector<cplx> zz(N), ww(N);
+  for (int n = 0; n < N; ++n) {
+    zz[n] = cplx(z[2 * n], z[2 * n + 1]);
+    ww[n] = cplx(w[2 * n], w[2 * n + 1]);
+  }
+  PoleSet ps;
+  const int rc = make_poleset(ps, precision, 0, N, 0.0, X, zz.data(), ww.data(), heavy_tau, prune_tau, heavy_align);
+  if (rc) return rc;
+  std::copy(ps.cls.begin(), ps.cls.end(), cls);
+  if (pruned_gain) *pruned_gain = ps.pruned_gain;
   return REXI_OK;
 }
 

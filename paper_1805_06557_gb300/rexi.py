@@ -60,6 +60,8 @@ class PlanInfo(ctypes.Structure):
 _lib.rexi_last_error.restype = ctypes.c_char_p
 _lib.rexi_coeffs.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp]
 _lib.rexi_contour_select.argtypes = [ctypes.c_double, ctypes.c_int, _dp, _dp]
+_lib.rexi_select_poles.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_int, _ip, _dp]
 _lib.rexi_spectrum_bound.argtypes = [ctypes.c_int] + [ctypes.c_double] * 4
 _lib.rexi_spectrum_bound.restype = ctypes.c_double
 _lib.rexi_plan_create.argtypes = [ctypes.POINTER(PlanDesc), ctypes.POINTER(ctypes.c_void_p)]
@@ -231,6 +233,21 @@ def contour_select(X, N):
     Xc = ctypes.c_double()
     _check(_lib.rexi_contour_select(float(X), int(N), ctypes.byref(p0), ctypes.byref(Xc)))
     return p0.value, Xc.value
+
+
+def select_poles(z, w, X, precision="mixed", heavy_tau=-1.0, prune_tau=0.0, heavy_align=16):
+    """(cls, pruned_gain): per pole 1 heavy, 0 light, -1 pruned, as a plan would classify them
+    (host only)."""
+    z = np.ascontiguousarray(np.asarray(z, dtype=np.complex128))
+    w = np.ascontiguousarray(np.asarray(w, dtype=np.complex128))
+    if z.shape != w.shape or z.ndim != 1:
+        raise ValueError("z and w must be 1-D arrays of the same length")
+    cls = np.empty(len(z), dtype=np.int32)
+    pg = ctypes.c_double()
+    _check(_lib.rexi_select_poles(_PREC[precision], len(z), z.ctypes.data_as(_dp), w.ctypes.data_as(_dp),
+                                  float(X), float(heavy_tau), float(prune_tau), int(heavy_align),
+                                  cls.ctypes.data_as(_ip), ctypes.byref(pg)))
+    return cls, pg.value
 
 
 def spectrum_bound(T, dt, omega, radius, phibar):

@@ -51,3 +51,68 @@ def test_spectrum_bound_and_contour_select(rexi):
         es = ocoeffs.scalar_error(z, w, X, npts=2001)
         amp = ocoeffs.amplification(z, w, X)
         assert max(es, amp * 1.1e-16) < 1e-8
+
+
+def _gains(z, w, X):
+    return np.abs(w) / np.abs(z - 1j * np.clip(z.imag, -X, X))
+
+
+def _pairs_share_class(z, cls):
+    for c in (-1, 0, 1):
+        s = z[cls == c]
+        s = s[np.abs(s.imag) > 0]
+        if not np.array_equal(np.sort_complex(s), np.sort_complex(np.conj(s))):
+            return False
+    return True
+
+
+@pytest.mark.parametrize("align,nheavy", [(16, 80), (32, 96)])
+def test_select_poles_mixed_default(rexi, align, nheavy):
+    """Mixed classes at T255, N = 512, dt = 3600 s: heavy poles have the largest gains (every
+    gain > 1e-3 among them, rounded up to the alignment), pruned poles the smallest with summed
+    gain <= 1e-10, and the largest pruned poles fill the last 32-pole light group."""
+    from oracle import rexi as orx
+    from paper_1805_06557_gb300 import synthetic as syn
+    X = orx.spectrum_bound(255, 3600.0, syn.OMEGA, syn.RADIUS, syn.PHIBAR)
+    p0, Xc = rexi.contour_select(X, 512)
+    z, w = ocoeffs.rexi_coefficients(512, p0, Xc)
+    cls, pg = rexi.select_poles(z, w, X, "mixed", heavy_align=align)
+    g = _gains(z, w, X)
+    heavy, light, pruned = cls == 1, cls == 0, cls == -1
+    assert heavy.sum() == nheavy and light.sum() == 32 and pruned.sum() == 512 - nheavy - 32
+    assert np.all(g[g > 1e-3] >= g[light].max()) and np.sum(g > 1e-3) <= heavy.sum()
+    assert g[heavy].min() >= g[light].max() >= g[light].min() >= g[pruned].max()
+    assert g[pruned].sum() <= 1e-10 and abs(g[pruned].sum() - pg) <= 1e-12 * 1e-10
+    # without the refill the 1e-10 budget would leave the last light group partly idle
+    order = np.sort(g)
+    assert np.sum(np.cumsum(order) <= 1e-10) > pruned.sum()
+    assert _pairs_share_class(z, cls)
+
+
+def test_select_poles_fp64_and_options(rexi):
+    z, w = ocoeffs.rexi_coefficients(256, 6.0, 18.8)
+    X = 11.0
+    g = _gains(z, w, X)
+    cls, pg = rexi.select_poles(z, w, X, "fp64")
+    assert np.all(cls == 1) and pg == 0.0                      # FP64 solves every pole by default
+    cls, pg = rexi.select_poles(z, w, X, "fp64", prune_tau=1e-12)
+    assert 0 < np.sum(cls == -1) and g[cls == -1].sum() <= 1e-12 and not np.any(cls == 0)
+    cls, _ = rexi.select_poles(z, w, X, "mixed", prune_tau=-1.0)
+    assert not np.any(cls == -1)                               # pruning off
+    cls, _ = rexi.select_poles(z, w, X, "mixed", heavy_tau=0.1, prune_tau=-1.0)
+    assert np.all(g[cls == 1].min() >= g[cls == 0].max()) and np.sum(g > 0.1) <= np.sum(cls == 1)
+    assert _pairs_share_class(z, cls)
+
+
+def test_select_poles_reject_bad_arguments(rexi):
+    z, w = ocoeffs.rexi_coefficients(16, 3.0, 5.0)
+    for kw in (dict(heavy_align=8), dict(precision="fp64", X=-1.0)):
+        args = dict(precision="mixed", X=4.0)
+        args.update(kw)
+        with pytest.raises(rexi.RexiError) as e:
+            rexi.select_poles(z, w, args.pop("X"), **args)
+        assert e.value.code == rexi.REXI_EINVAL
+    z0 = z.copy()
+    z0[3] = 0.0
+    with pytest.raises(rexi.RexiError):
+        rexi.select_poles(z0, w, 4.0)
