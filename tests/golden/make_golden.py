@@ -1,6 +1,6 @@
 """Writes the stored expected values under tests/golden/ from the FP64 oracle alone.
 
-    python tests/golden/make_golden.py
+    python tests/golden/make_golden.py [output directory, default: this directory]
 
 rexi_step_T7_N128.txt: one REXI step (Eq. rexi with the Cauchy-contour poles of
 Eq. cauchy_alpha / cauchy_beta) of the linear SWE operator at T7, on the contour that Sec. 5
@@ -22,7 +22,7 @@ from paper_1805_06557_gb300 import synthetic as syn  # noqa: E402
 T, N, P0, XC, DT, SEED = 7, 128, 10.0, 30.0, 21600.0, 2018
 
 
-def main():
+def main(outdir=HERE):
     z, w = oc.rexi_coefficients(N, P0, XC)
     U0 = syn.gaussian_state(T, SEED)
     U1 = orx.rexi_step(U0, T, DT, syn.OMEGA, syn.RADIUS, syn.PHIBAR, z, w)
@@ -38,9 +38,9 @@ def main():
         for i in range(U0.shape[1]):
             lines.append("%d %d %.17g %.17g %.17g %.17g" % (f, i, U0[f, i].real, U0[f, i].imag,
                                                          U1[f, i].real, U1[f, i].imag))
-    with open(os.path.join(HERE, "rexi_step_T7_N128.txt"), "w") as fh:
+    with open(os.path.join(outdir, "rexi_step_T7_N128.txt"), "w") as fh:
         fh.write("\n".join(lines) + "\n")
 
 
 if __name__ == "__main__":
-    main()
+    main(sys.argv[1] if len(sys.argv) > 1 else HERE)

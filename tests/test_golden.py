@@ -5,6 +5,8 @@ p_{+-1} = +-30i (the parameters Sec. 5 starts from), radius 50 and centre -40.
 rexi_step_T7_N128.txt is one REXI step on that contour, written by make_golden.py from the
 oracle; replaying it guards the oracle against silent changes, and its distance to the exact
 exponential bounds the REXI error of that contour."""
+import os
+
 import numpy as np
 
 from oracle import coeffs as oc
@@ -58,3 +60,17 @@ def test_stored_step_near_exact_exponential(golden_step):
     z, w = oc.rexi_coefficients(int(k["N"]), k["p0"], k["Xc"])
     exact = orx.exact_step(U0, *args)
     assert np.all(orx.rel_l2(U1, exact, T) < oc.scalar_error(z, w, X))
+
+
+def test_stored_step_is_what_the_script_writes(tmp_path, golden_step):
+    """The committed fixture is the output of tests/golden/make_golden.py (oracle only): same
+    parameters, same input, and the same result up to the rounding of the host's LAPACK."""
+    import subprocess
+    import sys
+    from conftest import GOLDEN
+    subprocess.run([sys.executable, os.path.join(GOLDEN, "make_golden.py"), str(tmp_path)], check=True)
+    k, U0, U1 = golden_step("rexi_step_T7_N128.txt")
+    k2, V0, V1 = golden_step(str(tmp_path / "rexi_step_T7_N128.txt"))
+    assert k == k2
+    assert np.max(np.abs(V0 - U0)) <= 1e-15 * np.max(np.abs(U0))
+    assert np.all(orx.rel_l2(V1, U1, int(k["T"])) < 1e-13)
