@@ -314,9 +314,11 @@ int rexi_plan_get_profile(rexi_plan* plan, double* ms, int* launches, int reset)
  * allocating routine.
  *   T <= 63, N <= 1024 (REXI_EINVAL beyond); U0, U1 device pointers of 3*nlm complex128,
  *   not overlapping; stream: cudaStream_t (NULL = legacy default stream).
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * and sets the solve kernel's shared-memory limit: make that first call before any stream
- * capture.  Every call reuses the same array and leaves the last call's contents in it
+ * Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress) and sets the solve kernel's shared-memory limit, so the address stays
+ * valid after cudaDeviceReset; the first call on a device also loads the library's module
+ * there: make that first call before any stream capture.  Every call reuses the same array
+ * and leaves the last call's contents in it
  * (everything a call reads is written by it first); calls that overlap on the GPU (two
  * streams, or two host threads) race on that array and must be serialised by the caller.
  * Asynchronous on `stream`.  Errors: REXI_EINVAL, REXI_ECUDA.

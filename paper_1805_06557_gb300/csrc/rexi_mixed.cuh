@@ -8,14 +8,15 @@
 //
 //  * light poles (k_rexi_light): FP32 Thomas elimination, weighted sums in FP32 over the 32
 //    poles of a warp, added into the FP64 partial sums.  The forward coefficients are not
-//    stored: the sweep keeps a checkpoint of the recurrence state every 16 elements and the
-//    backward pass recomputes each 16-element segment in registers, so the kernel needs no
+//    stored: the sweep keeps a checkpoint of the recurrence state every LSEG = 8 elements and
+//    the backward pass recomputes each 8-element segment in registers, so the kernel needs no
 //    per-element scratch traffic.
-//  * heavy poles (k_rexi_heavy): FP32 solve, one step of iterative refinement whose
-//    residual r - A x is evaluated in double-float arithmetic (pairs of FP32 numbers,
-//    error-free products by FMA, Knuth's two-sum), FP32 solve of the correction with the
-//    same factorisation, and weighted sums over poles in double-float arithmetic (16 poles at a
-//    time), added in FP64 across the pole halves and tiles.
+//  * heavy poles (k_rexi_heavy): FP32 solve (checkpoints every heavy_seg() elements: 8 for one
+//    state, 4 for state pairs), one step of iterative refinement whose residual r - A x is
+//    evaluated in double-float arithmetic (pairs of FP32 numbers, error-free products by FMA,
+//    Knuth's two-sum), FP32 solve of the correction by bottom-up (UL) elimination, and
+//    weighted sums over poles in double-float arithmetic (16 poles at a time), added in FP64
+//    across the pole halves and tiles.
 // Both kernels share the tile scheme and chain equations of the FP64 kernel.
 #pragma once
 #include "common.cuh"

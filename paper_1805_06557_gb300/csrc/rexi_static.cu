@@ -10,7 +10,6 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
-#include <mutex>
 
 #include "common.cuh"
 #include "rexi_fp64.cuh"
@@ -44,28 +43,21 @@ constexpr size_t OFF_ECUM = al(OFF_INST + sizeof(Inst));
 constexpr size_t ST_BYTES = al(OFF_ECUM + 2 * sizeof(long long));
 
 // The scratch.  In host code this name is only a stand-in for the symbol: the device
-// address comes from cudaGetSymbolAddress (once per device, in static_setup).
+// address comes from cudaGetSymbolAddress, with the caller's device current.
 static __device__ __align__(256) unsigned char g_rexi_static[ST_BYTES];
 
-constexpr int MAX_DEV = 64;
-std::mutex g_mu;
-unsigned char* g_ptr[MAX_DEV] = {nullptr};
-
+// Looks the array's address up and sets the solve kernel's shared-memory limit on every call.
+// Both are cheap host calls that allocate nothing; doing them per call (instead of caching
+// the address per device index) keeps the address valid after cudaDeviceReset or a new
+// primary context, which reload the module.
 int static_setup(unsigned char** out) {
-  int dev = 0;
-  REXI_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= MAX_DEV) return fail(REXI_EINVAL, "device index %d out of range", dev);
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_rexi_static);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_rexi_static)");
-    e = cudaFuncSetAttribute(k_rexi_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)fp64_smem_bytes());
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_rexi_fp64)");
-    g_ptr[dev] = static_cast<unsigned char*>(p);
-  }
-  *out = g_ptr[dev];
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_rexi_static);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_rexi_static)");
+  e = cudaFuncSetAttribute(k_rexi_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)fp64_smem_bytes());
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_rexi_fp64)");
+  *out = static_cast<unsigned char*>(p);
   return REXI_OK;
 }
 

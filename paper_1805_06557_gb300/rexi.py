@@ -79,11 +79,36 @@ _lib.rexi_step_fp64_static.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.c_d
 _lib.rexi_static_scratch_bytes.restype = ctypes.c_longlong
 
 
+def _dev_tensor(t, numel, dtype, what, at_least=False):
+    """Checks that `t` is a contiguous CUDA tensor of `dtype` on the current device holding
+    `numel` elements (at least `numel` with at_least) before its address reaches a kernel:
+    a wrong size, stride or device would make the kernel read or write outside the buffer."""
+    import torch
+    dt = getattr(torch, dtype)
+    if not isinstance(t, torch.Tensor):
+        raise ValueError("%s: need a torch tensor, got %s" % (what, type(t).__name__))
+    if t.dtype != dt:
+        raise ValueError("%s: need dtype %s, got %s" % (what, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s: need a contiguous tensor" % what)
+    if (t.numel() < numel) if at_least else (t.numel() != numel):
+        raise ValueError("%s: need %s%d elements, got %d" % (what, "at least " if at_least else "",
+                                                           numel, t.numel()))
+    if not t.is_cuda:
+        raise ValueError("%s: need a CUDA tensor, got one on %s" % (what, t.device))
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError("%s: tensor on %s, current device is cuda:%d"
+                         % (what, t.device, torch.cuda.current_device()))
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def step_fp64_static(T, N, dt, omega, radius, phibar, p0, Xc, U0, U1, stream=None):
     """Allocation-free FP64 REXI step on one state (CUDA complex128 tensors [3, nlm])."""
+    n = 3 * nlm(int(T)) if int(T) >= 0 else 0
+    p0_ = _dev_tensor(U0, n, "complex128", "U0")
+    p1_ = _dev_tensor(U1, n, "complex128", "U1")
     _check(_lib.rexi_step_fp64_static(int(T), int(N), float(dt), float(omega), float(radius),
-                                      float(phibar), float(p0), float(Xc),
-                                      ctypes.c_void_p(U0.data_ptr()), ctypes.c_void_p(U1.data_ptr()),
+                                      float(phibar), float(p0), float(Xc), p0_, p1_,
                                       ctypes.c_void_p(_stream_handle(stream))))
     return U1
 
@@ -152,17 +177,23 @@ class RaggedPlan:
         _check(_lib.rexi_ragged_offsets(self._h, o))
         return [int(v) for v in o]
 
+    def _states(self, U0, U1):
+        n = self.offsets()[-1]
+        return (_dev_tensor(U0, n, "complex128", "U0", at_least=True),
+                _dev_tensor(U1, n, "complex128", "U1", at_least=True))
+
     def step(self, U0, U1):
-        _check(_lib.rexi_ragged_step(self._h, _ptr(U0), _ptr(U1)))
+        _check(_lib.rexi_ragged_step(self._h, *self._states(U0, U1)))
         return U1
 
     def capture(self, U0, U1):
-        _check(_lib.rexi_ragged_capture(self._h, _ptr(U0), _ptr(U1)))
+        _check(_lib.rexi_ragged_capture(self._h, *self._states(U0, U1)))
 
     def tune(self, U0, U1, reps=3):
         q = ctypes.c_int()
         ms = ctypes.c_double()
-        _check(_lib.rexi_ragged_tune(self._h, _ptr(U0), _ptr(U1), int(reps), ctypes.byref(q), ctypes.byref(ms)))
+        _check(_lib.rexi_ragged_tune(self._h, *self._states(U0, U1), int(reps), ctypes.byref(q),
+                                     ctypes.byref(ms)))
         return q.value, ms.value
 
     def sync(self):
@@ -298,12 +329,9 @@ class Plan:
         """U0, U1: CUDA complex128 tensors of shape [batch, 3, nlm] (or [3, nlm])."""
         if batch is None:
             batch = 1 if U0.dim() == 2 else U0.shape[0]
-        for t in (U0, U1):
-            if not (t.is_cuda and t.is_contiguous()) or t.numel() != batch * 3 * self.nlm:
-                raise ValueError("need contiguous CUDA complex128 tensors of %d x 3 x %d"
-                                 % (batch, self.nlm))
-        _check(_lib.rexi_step(self._h, ctypes.c_void_p(U0.data_ptr()),
-                              ctypes.c_void_p(U1.data_ptr()), int(batch)))
+        a0 = _dev_tensor(U0, batch * 3 * self.nlm, "complex128", "U0")
+        a1 = _dev_tensor(U1, batch * 3 * self.nlm, "complex128", "U1")
+        _check(_lib.rexi_step(self._h, a0, a1, int(batch)))
         return U1
 
     def step_raw(self, U0_ptr, U1_ptr, batch):
@@ -409,12 +437,9 @@ class LgPlan:
         """U0, U1: CUDA complex128 tensors [batch, 3, nlm] (or [3, nlm]); U1 may be U0."""
         if batch is None:
             batch = 1 if U0.dim() == 2 else U0.shape[0]
-        for t in (U0, U1):
-            if not (t.is_cuda and t.is_contiguous()) or t.numel() != batch * 3 * self.nlm:
-                raise ValueError("need contiguous CUDA complex128 tensors of %d x 3 x %d"
-                                 % (batch, self.nlm))
-        _check(_lib.rexi_lg_step(self._h, ctypes.c_void_p(U0.data_ptr()),
-                                 ctypes.c_void_p(U1.data_ptr()), int(batch)))
+        a0 = _dev_tensor(U0, batch * 3 * self.nlm, "complex128", "U0")
+        a1 = _dev_tensor(U1, batch * 3 * self.nlm, "complex128", "U1")
+        _check(_lib.rexi_lg_step(self._h, a0, a1, int(batch)))
         return U1
 
     def step_raw(self, U0_ptr, U1_ptr, batch):
@@ -491,16 +516,25 @@ class ShPlan:
         _check(_lib.sh_plan_get_grid(self._h, mu.ctypes.data_as(_dp), w.ctypes.data_as(_dp)))
         return mu, w
 
+    def _spec(self, t, nfields, what):
+        return _dev_tensor(t, int(nfields) * self.nlm, "complex128", what, at_least=True)
+
+    def _grid(self, t, nfields, what):
+        return _dev_tensor(t, int(nfields) * self.nlat * self.nlon, "float64", what, at_least=True)
+
     def synthesis(self, spec, grid, nfields=1):
-        _check(_lib.sh_synthesis(self._h, _ptr(spec), _ptr(grid), int(nfields)))
+        _check(_lib.sh_synthesis(self._h, self._spec(spec, nfields, "spec"),
+                                 self._grid(grid, nfields, "grid"), int(nfields)))
         return grid
 
     def analysis(self, grid, spec, nfields=1):
-        _check(_lib.sh_analysis(self._h, _ptr(grid), _ptr(spec), int(nfields)))
+        _check(_lib.sh_analysis(self._h, self._grid(grid, nfields, "grid"),
+                                self._spec(spec, nfields, "spec"), int(nfields)))
         return spec
 
     def synthesis_uv(self, psi, chi, U, V, nfields=1):
-        _check(_lib.sh_synthesis_uv(self._h, _ptr(psi), _ptr(chi), _ptr(U), _ptr(V), int(nfields)))
+        _check(_lib.sh_synthesis_uv(self._h, self._spec(psi, nfields, "psi"), self._spec(chi, nfields, "chi"),
+                                    self._grid(U, nfields, "U"), self._grid(V, nfields, "V"), int(nfields)))
         return U, V
 
     def check(self):
@@ -519,7 +553,8 @@ class ShPlan:
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(SH_STAGE_NAMES)}
 
     def analysis_divcurl(self, A, B, div, curl, nfields=1):
-        _check(_lib.sh_analysis_divcurl(self._h, _ptr(A), _ptr(B), _ptr(div), _ptr(curl),
+        _check(_lib.sh_analysis_divcurl(self._h, self._grid(A, nfields, "A"), self._grid(B, nfields, "B"),
+                                        self._spec(div, nfields, "div"), self._spec(curl, nfields, "curl"),
                                         int(nfields)))
         return div, curl
 
@@ -581,11 +616,12 @@ class SwePlan:
         self.T, self.nlm = int(T), nlm(T)
 
     def step(self, state, nsteps=1):
-        _check(_lib.swe_step(self._h, _ptr(state), int(nsteps)))
+        _check(_lib.swe_step(self._h, _dev_tensor(state, 3 * self.nlm, "complex128", "state"), int(nsteps)))
         return state
 
     def nonlinear(self, state, tendency):
-        _check(_lib.swe_nonlinear(self._h, _ptr(state), _ptr(tendency)))
+        _check(_lib.swe_nonlinear(self._h, _dev_tensor(state, 3 * self.nlm, "complex128", "state"),
+                                  _dev_tensor(tendency, 3 * self.nlm, "complex128", "tendency")))
         return tendency
 
     def set_profiling(self, enable=True):

@@ -116,3 +116,21 @@ def test_select_poles_reject_bad_arguments(rexi):
     z0[3] = 0.0
     with pytest.raises(rexi.RexiError):
         rexi.select_poles(z0, w, 4.0)
+
+
+def test_binding_rejects_wrong_tensors_before_the_call(rexi):
+    """The binding checks size, dtype, contiguity and device of every state tensor before its
+    address reaches a kernel (no GPU needed: every case fails on the host)."""
+    import torch
+    T = 15
+    n = rexi.nlm(T)
+    good_cpu = torch.zeros(3, n, dtype=torch.complex128)
+    cases = [torch.zeros(3, n - 1, dtype=torch.complex128),          # too small
+             torch.zeros(3, 2 * n, dtype=torch.complex128)[:, ::2],  # strided view
+             torch.zeros(3, n, dtype=torch.complex64),               # wrong dtype
+             good_cpu]                                               # right shape, on the host
+    for bad in cases:
+        with pytest.raises(ValueError):
+            rexi.step_fp64_static(T, 64, 3600.0, 7.292e-5, 6.37122e6, 9.80616e4, 6.0, 10.0, bad, bad)
+    with pytest.raises(ValueError, match="elements"):
+        rexi.step_fp64_static(T, 64, 3600.0, 7.292e-5, 6.37122e6, 9.80616e4, 6.0, 10.0, cases[0], good_cpu)
