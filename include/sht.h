@@ -21,6 +21,13 @@ extern "C" {
 #define SH_FP64 0  /* Legendre contraction in FP64 on CUDA cores                           */
 #define SH_TF32 1  /* Legendre contraction on tcgen05 tensor cores, TF32 inputs, FP32 sums    */
 #define SH_BF16 2  /* Legendre contraction on tcgen05 tensor cores, BF16 inputs, FP32 sums    */
+/* Split TF32 on tcgen05 tensor cores: every operand x is carried as x_hi + x_lo with
+ * x_hi = tf32(x), x_lo = tf32(x - x_hi), and each product as a_hi b_lo + a_lo b_hi + a_hi b_hi
+ * (three MMAs into one FP32 accumulator).  The operand unit is about 3 * 2^-22 instead of
+ * TF32's 2^-11, so that the derivatives of N(U) (the Laplacian of the kinetic energy, the
+ * divergence of the fluxes) keep a usable accuracy; table bytes are those of FP64 (hi and lo
+ * words), still streamed through the tensor cores. */
+#define SH_TF32X3 3
 
 typedef struct sh_plan sh_plan;
 
@@ -28,8 +35,8 @@ typedef struct sh_plan_desc {
   int T;            /* triangular truncation, 1 <= T <= 1023                                */
   int nlat, nlon;   /* Gauss grid, nlat even and > T, nlon > 2T, nlon = 2^p 3^q              */
   double radius;    /* sphere radius a [m] (vector transforms)                              */
-  int precision;    /* SH_FP64, SH_TF32 or SH_BF16                                          */
-  int max_fields;   /* largest nfields passed to a transform; SH_TF32 / SH_BF16: <= 8, and   */
+  int precision;    /* SH_FP64, SH_TF32, SH_BF16 or SH_TF32X3                               */
+  int max_fields;   /* largest nfields passed to a transform; tensor-core precisions: <= 8,  */
                     /* the vector operands (8 max_fields columns x nlat/2 latitudes for      */
                     /* analysis, x T+1 degrees for synthesis) must fit in shared memory      */
                     /* (e.g. max_fields <= 4 at T = 1023, nlat = 1536, TF32)                 */

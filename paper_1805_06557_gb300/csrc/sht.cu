@@ -615,7 +615,7 @@ struct sh_plan {
   bool fft32 = false;
   double2* d_F = nullptr;   // Fourier workspace [2 * max_fields][T+1][nlat]
   FftPlan fp{};
-  TcLegendre* tc = nullptr;  // tensor-core Legendre state (SH_TF32 / SH_BF16)
+  TcLegendre* tc = nullptr;  // tensor-core Legendre state (SH_TF32 / SH_BF16 / SH_TF32X3)
   StageProf prof;            // per-stage event timing (sh_plan_set_profiling)
 };
 
@@ -633,7 +633,7 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
     return fail(REXI_EINVAL, "sh_plan_create: nlat must be even and > T (got %d)", d.nlat);
   if (d.nlon <= 2 * d.T) return fail(REXI_EINVAL, "sh_plan_create: nlon must exceed 2T");
   if (!(d.radius > 0) || d.max_fields < 1) return fail(REXI_EINVAL, "sh_plan_create: radius > 0, max_fields >= 1");
-  if (d.precision != SH_FP64 && d.precision != SH_TF32 && d.precision != SH_BF16)
+  if (d.precision != SH_FP64 && d.precision != SH_TF32 && d.precision != SH_BF16 && d.precision != SH_TF32X3)
     return fail(REXI_EINVAL, "sh_plan_create: unknown precision %d", d.precision);
   sh_plan* p = new sh_plan();
   p->d = d;
@@ -686,7 +686,7 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
   if (e) return bail(cuda_fail(e, "cudaFuncSetAttribute(fft)"));
   if (d.precision != SH_FP64) {
     int rc = tc_legendre_create(&p->tc, p->d_P, p->d_H, p->d_w, p->d_wq, d.T, d.nlat, d.max_fields,
-                                d.precision == SH_BF16, p->stream);
+                                d.precision, p->stream);
     if (rc) return bail(rc);
     tc_legendre_set_prof(p->tc, &p->prof);
   }

@@ -1,5 +1,6 @@
-// Tensor-core (tcgen05) Legendre contractions for sh_plan precisions SH_TF32 / SH_BF16
-// (paper Sec. 3.2: the dense Legendre contraction per zonal order m of the SH transforms).
+// Tensor-core (tcgen05) Legendre contractions for sh_plan precisions SH_TF32, SH_BF16 and
+// SH_TF32X3 (paper Sec. 3.2: the dense Legendre contraction per zonal order m of the SH
+// transforms).
 //
 // Every contraction is a set of GEMM jobs [128 x Ncols] = A[128 x K] B[K x Ncols]:
 //   synthesis, per (m, 128-latitude tile, table P or H):
@@ -21,11 +22,19 @@
 // (hemisphere and parity combination, and for vector transforms the P and H sums of one
 // (m, tile), which run as consecutive jobs of one CTA).  All mbarrier waits are bounded; on a
 // timeout the kernel records an error flag.
+//
+// SH_TF32X3 (split TF32): every operand x is carried as x_hi + x_lo, x_hi = tf32(x) and
+// x_lo = tf32(x - x_hi), and each k-step issues three MMAs into the same FP32 accumulator,
+// a_hi b_lo + a_lo b_hi + a_hi b_hi; the dropped a_lo b_lo and the rounding of the lo parts
+// leave a relative error of about 3 * 2^-22 per product instead of 2^-10.  A table chunk row
+// holds 32 hi elements of K beside the same 32 lo elements (still 256 bytes), the B operand a
+// hi and a lo copy.
 #include <algorithm>
 #include <map>
 #include <cuda_bf16.h>
 #include <vector>
 
+#include "../../include/sht.h"
 #include "sht_tc.cuh"
 #include "tc_common.cuh"
 
@@ -54,6 +63,9 @@ struct Job {
   int newb;         // 1: the job starts a B group (consecutive jobs of one m share a B operand)
 };
 
+// precision modes of the GEMM (template parameter PM)
+constexpr int PM_TF32 = 0, PM_BF16 = 1, PM_TF32X3 = 2;
+
 struct GemmArgs {
   const unsigned char* tabP;
   const unsigned char* tabH;
@@ -75,6 +87,7 @@ struct GemmArgs {
   int nb;           // B buffers (1, 2 or 4): B operands are fetched up to nb - 1 jobs ahead
   int nj_max;       // jobs per CTA at most (their descriptors are staged in shared memory)
   uint32_t bslot;   // bytes of one B buffer
+  uint32_t blo;     // PM_TF32X3: byte offset of the lo copy of B in its buffer (else 0)
   int* err;
 };
 
@@ -175,24 +188,41 @@ __device__ __forceinline__ void epilogue8(const GemmArgs& g, int m, int row, int
   }
 }
 
+__device__ __forceinline__ uint32_t tf32_rna(float v) {
+  uint32_t t;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(v));
+  return t;
+}
+
 // One 16-byte core-matrix row of a B operand: E consecutive K elements of column c of the
 // K group whose first byte is `grp` (column c at (c >> 3) * sbo + (c & 7) * 16), rounded to
-// TF32 (cvt.rna) or BF16 (round to nearest even)
-template <bool BF>
-__device__ __forceinline__ void store_row16(unsigned char* grp, int c, int sbo, const float* v) {
+// TF32 (cvt.rna) or BF16 (round to nearest even); PM_TF32X3 also writes the lo parts
+// tf32(v - tf32(v)) at grp + blo (v - tf32(v) is exact in FP32)
+template <int PM>
+__device__ __forceinline__ void store_row16(unsigned char* grp, int c, int sbo, uint32_t blo, const float* v) {
   uint4 u;
   uint32_t* w = reinterpret_cast<uint32_t*>(&u);
-  if (BF) {
+  const size_t off = (size_t)(c >> 3) * sbo + (c & 7) * 16;
+  if (PM == PM_BF16) {
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
       w[e] = *reinterpret_cast<const uint32_t*>(&h);
     }
+  } else if (PM == PM_TF32X3) {
+    uint4 l;
+    uint32_t* wl = reinterpret_cast<uint32_t*>(&l);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      w[e] = tf32_rna(v[e]);
+      wl[e] = tf32_rna(v[e] - __uint_as_float(w[e]));
+    }
+    *reinterpret_cast<uint4*>(grp + blo + off) = l;
   } else {
 #pragma unroll
-    for (int e = 0; e < 4; ++e) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w[e]) : "f"(v[e]));
+    for (int e = 0; e < 4; ++e) w[e] = tf32_rna(v[e]);
   }
-  *reinterpret_cast<uint4*>(grp + (size_t)(c >> 3) * sbo + (c & 7) * 16) = u;
+  *reinterpret_cast<uint4*>(grp + off) = u;
 }
 
 // B operand of job (m, kpad) written into shared memory at `base` by the threads of the
@@ -206,9 +236,9 @@ __device__ __forceinline__ void store_row16(unsigned char* grp, int c, int sbo, 
 //   analysis (K = northern latitudes j): w_j (F_N + F_S) in column 2 cpf f + q, w_j (F_N - F_S)
 //     in column 2 cpf f + cpf + q; scalar q: re, im; vector q: A re, im, B re, im.
 // One item = (K group, column pair p < nf cpf / 2): E loads of its pair, four 16-byte rows.
-template <bool BF>
+template <int PM>
 __device__ __forceinline__ void build_b(const GemmArgs& g, int m, int kpad, unsigned char* base, int bt) {
-  constexpr int E = BF ? 8 : 4;
+  constexpr int E = PM == PM_BF16 ? 8 : 4;
   const int cpf = g.cpf, np = g.nf * cpf / 2;
   const int sbo = (kpad / E) * 128;
   const int nitems = (kpad / E) * np;
@@ -259,10 +289,10 @@ __device__ __forceinline__ void build_b(const GemmArgs& g, int m, int kpad, unsi
         v3[e] = we * (ay - by);
       }
     }
-    store_row16<BF>(grp, cn, sbo, v0);
-    store_row16<BF>(grp, cn + 1, sbo, v1);
-    store_row16<BF>(grp, cn + cpf, sbo, v2);
-    store_row16<BF>(grp, cn + cpf + 1, sbo, v3);
+    store_row16<PM>(grp, cn, sbo, g.blo, v0);
+    store_row16<PM>(grp, cn + 1, sbo, g.blo, v1);
+    store_row16<PM>(grp, cn + cpf, sbo, g.blo, v2);
+    store_row16<PM>(grp, cn + cpf + 1, sbo, g.blo, v3);
   }
 }
 
@@ -277,15 +307,18 @@ __device__ __forceinline__ bool builders_all(bool v) {
   return r != 0;
 }
 
-template <bool BF>
+template <int PM>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant__ GemmArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
   // element type constants: 16-byte core-matrix rows hold E elements; a chunk (KC = 256 B of
-  // K per row) is 8 MMA k-steps of 32 B; consecutive k-steps are 2 core matrices (256 B) apart
+  // K per row) is 8 MMA k-steps of 32 B; consecutive k-steps are 2 core matrices (256 B) apart.
+  // PM_TF32X3: a chunk row holds KCK = 32 hi elements of K, then the same 32 lo elements
+  constexpr bool BF = PM == PM_BF16, SPLIT = PM == PM_TF32X3;
   constexpr int E = BF ? 8 : 4, eb = BF ? 2 : 4, KC = BF ? 128 : 64, KSTEP = BF ? 16 : 8;
+  constexpr int KCK = SPLIT ? KC / 2 : KC;  // K covered by one chunk
   constexpr uint32_t chunk_bytes = 128u * KC * eb;
   static_assert(KC * eb == 256, "a chunk row is 256 bytes of K");
-  constexpr int KSTEPS = KC / KSTEP;  // k-steps per full chunk (8)
+  constexpr int KSTEPS = KCK / KSTEP;  // k-steps per full chunk (8; 4 split)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int S = g.stages, NB = g.nb;
   unsigned char* sA = smem;
@@ -332,7 +365,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
         for (int c = 0; c < jb.nchunk; ++c) {
           if (round > 0) ok = tc::mbar_wait(empty0 + 8 * s, (round - 1) & 1);
           if (!ok) break;
-          const uint32_t cb = (c == jb.nchunk - 1) ? (uint32_t)jb.rows * jb.kl * eb : jchunk;
+          const uint32_t cb = (c == jb.nchunk - 1) ? (uint32_t)jb.rows * jb.kl * eb * (SPLIT ? 2 : 1) : jchunk;
           tc::mbar_expect_tx(full0 + 8 * s, cb);
           tc::bulk_g2s(sa0 + s * chunk_bytes, A + (size_t)c * jchunk, cb, full0 + 8 * s);
           ++a_issued;
@@ -363,7 +396,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
         break;
       }
       const Job jq = sjobs[q];
-      build_b<BF>(g, jq.m, jq.kpad, sB + (size_t)b * g.bslot, bt);
+      build_b<PM>(g, jq.m, jq.kpad, sB + (size_t)b * g.bslot, bt);
       tc::fence_proxy_async();
       builders_all(true);  // every row of the operand is written and fenced
       if (bt == 0) tc::mbar_arrive(bfull0 + 8 * b);
@@ -395,9 +428,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
           if (!ok) break;
           tc::fence_after_sync();
           // the last chunk may be short: its own core-matrix stride and fewer k-steps
-          const int kc = (c == jb.nchunk - 1) ? jb.kl : KC;
-          const uint64_t ad = tc::smem_desc(sa0 + s * chunk_bytes, 128u, kc == KC ? sboA : (uint32_t)(kc / E) * 128u);
-          const uint64_t bd = bdesc0 + (uint64_t)(c * ((KC / E) * 128 / 16));  // + c * 2048 B
+          const int kc = (c == jb.nchunk - 1) ? jb.kl : KCK;
+          const int kw = SPLIT ? 2 * kc : kc;  // K width of the stored chunk
+          const uint64_t ad = tc::smem_desc(sa0 + s * chunk_bytes, 128u, kw == KC ? sboA : (uint32_t)(kw / E) * 128u);
+          const uint64_t bd = bdesc0 + (uint64_t)(c * ((KCK / E) * 128 / 16));  // + c * KCK K elements
           const int nks = kc / KSTEP;
 #pragma unroll
           for (int q = 0; q < KSTEPS; ++q) {  // + 256 B per k-step: +16 in the address field
@@ -405,8 +439,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
             const uint32_t accum = (c > 0 || q >= TC_NACC) ? 1u : 0u;
             const uint32_t da = dt + cs * (q % TC_NACC);
             if (q < nks) {
-              if (BF) tc::mma_f16(da, ad + 16u * q, bd + 16u * q, idesc, accum);
-              else tc::mma_tf32(da, ad + 16u * q, bd + 16u * q, idesc, accum);
+              if (BF) {
+                tc::mma_f16(da, ad + 16u * q, bd + 16u * q, idesc, accum);
+              } else if (SPLIT) {
+                // the small products first: a_hi b_lo, a_lo b_hi (lo half of the chunk), a_hi b_hi
+                const uint64_t alo = ad + (uint64_t)((kc / E) * 128 / 16);
+                const uint64_t blo = bd + (uint64_t)(g.blo >> 4);
+                tc::mma_tf32(da, ad + 16u * q, blo + 16u * q, idesc, accum);
+                tc::mma_tf32(da, alo + 16u * q, bd + 16u * q, idesc, 1u);
+                tc::mma_tf32(da, ad + 16u * q, bd + 16u * q, idesc, 1u);
+              } else {
+                tc::mma_tf32(da, ad + 16u * q, bd + 16u * q, idesc, accum);
+              }
             }
           }
           tc::mma_commit(empty0 + 8 * s);
@@ -479,45 +523,53 @@ __device__ __forceinline__ void store_elem(unsigned char* base, size_t off, floa
   if (bf16) {
     *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(v);
   } else {
-    uint32_t t;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(v));
-    *reinterpret_cast<uint32_t*>(base + off) = t;
+    *reinterpret_cast<uint32_t*>(base + off) = tf32_rna(v);
   }
 }
 
-// tables: one thread per (job, row), looping over K; src = FP64 table [moff+k][nh]
+// tables: one thread per (job, row), looping over K; src = FP64 table [moff+k][nh];
+// pm = PM_TF32 / PM_BF16 / PM_TF32X3 (a chunk then holds kc hi elements, then kc lo elements)
 struct TabJob {
   long long a_off;
   int m, rows, tile, nchunk, kl;  // rows: stored rows (<= 128); kl: K of the last chunk
 };
 __global__ void k_tc_table(const double* __restrict__ src, unsigned char* __restrict__ dst,
                            const TabJob* __restrict__ jobs, int njobs, int T, int nh, int synth,
-                           int bf16) {
+                           int pm) {
   const int jid = blockIdx.x;
   if (jid >= njobs) return;
   const TabJob j = jobs[jid];
   const int r = threadIdx.x;  // 0..127
   if (r >= j.rows) return;
+  const int bf16 = pm == PM_BF16, split = pm == PM_TF32X3;
   const int E = bf16 ? 8 : 4, eb = bf16 ? 2 : 4, KC = bf16 ? 128 : 64;  // as TcLegendre::KC
+  const int KCK = split ? KC / 2 : KC;                                     // K per chunk
   const int K = T + 1 - j.m, base = moff(T, j.m);
   unsigned char* out = dst + j.a_off;
   for (int c = 0; c < j.nchunk; ++c) {
-    // every chunk but the last holds KC K-elements per row; the last holds j.kl
-    const int kc = (c == j.nchunk - 1) ? j.kl : KC;
-    const int sbo = (kc / E) * 128;
+    // every chunk but the last covers KCK K-elements per row; the last covers j.kl
+    const int kc = (c == j.nchunk - 1) ? j.kl : KCK;
+    const int sbo = ((split ? 2 * kc : kc) / E) * 128;
     unsigned char* ch = out + (size_t)c * j.rows * KC * eb;
     for (int kk = 0; kk < kc; ++kk) {
-      float v = 0.f;
+      double x = 0.0;
       if (synth) {  // rows = latitudes of the northern half, K = all degrees n = m + k
         const int lat = j.tile * 128 + r;
-        const int k = c * KC + kk;
-        if (lat < nh && k < K) v = (float)src[(size_t)(base + k) * nh + lat];
+        const int k = c * KCK + kk;
+        if (lat < nh && k < K) x = src[(size_t)(base + k) * nh + lat];
       } else {      // rows = degrees (both parities), K = latitudes
         const int k = j.tile * 128 + r;
-        const int lat = c * KC + kk;
-        if (lat < nh && k < K) v = (float)src[(size_t)(base + k) * nh + lat];
+        const int lat = c * KCK + kk;
+        if (lat < nh && k < K) x = src[(size_t)(base + k) * nh + lat];
       }
-      store_elem(ch, canon_off(r, kk, E, eb, sbo), v, bf16);
+      if (split) {
+        const uint32_t hi = tf32_rna((float)x);
+        const uint32_t lo = tf32_rna((float)(x - (double)__uint_as_float(hi)));
+        *reinterpret_cast<uint32_t*>(ch + canon_off(r, kk, E, eb, sbo)) = hi;
+        *reinterpret_cast<uint32_t*>(ch + canon_off(r, kc + kk, E, eb, sbo)) = lo;
+      } else {
+        store_elem(ch, canon_off(r, kk, E, eb, sbo), (float)x, bf16);
+      }
     }
   }
 }
@@ -534,6 +586,7 @@ struct Sched {
 
 struct TcLegendre {
   int T = 0, nlat = 0, nh = 0, nlm = 0, max_fields = 0, bf16 = 0, E = 4, eb = 4, KC = 32;
+  int pm = PM_TF32, KCK = 64;  // precision mode; K covered by one chunk (KC, or KC / 2 split)
   int ntile_s = 0, kpad_a = 0;
   unsigned char *tabPs = nullptr, *tabHs = nullptr, *tabPa = nullptr, *tabHa = nullptr;
   int* err = nullptr;
@@ -624,9 +677,10 @@ static cudaError_t make_sched(const std::vector<Job>& P, const std::vector<Job>*
 }
 
 int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const double* w, const double* wq,
-                       int T, int nlat, int max_fields, bool bf16, cudaStream_t stream) {
+                       int T, int nlat, int max_fields, int mode, cudaStream_t stream) {
   *out = nullptr;
   if (max_fields > 8) return fail(REXI_EINVAL, "sh_plan_create: tensor-core precisions support max_fields <= 8");
+  const bool bf16 = mode == SH_BF16, split = mode == SH_TF32X3;
   TcLegendre* t = new TcLegendre();
   t->T = T;
   t->nlat = nlat;
@@ -634,12 +688,14 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
   t->nlm = (T + 1) * (T + 2) / 2;
   t->max_fields = max_fields;
   t->bf16 = bf16 ? 1 : 0;
+  t->pm = bf16 ? PM_BF16 : split ? PM_TF32X3 : PM_TF32;
   t->E = bf16 ? 8 : 4;
   t->eb = bf16 ? 2 : 4;
   t->KC = bf16 ? 128 : 64;   // 256 bytes of K per chunk row
+  t->KCK = split ? t->KC / 2 : t->KC;
   t->w = w;
   t->wq = wq;
-  const int KC = t->KC, eb = t->eb;
+  const int KC = t->KC, KCK = t->KCK, eb = t->eb, kw = split ? 2 : 1;
   const size_t chunk = 128ull * KC * eb;
   cudaError_t e;
   {
@@ -660,23 +716,23 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
   for (int m = 0; m <= T; ++m) {
     const int K = T + 1 - m;
     const int kpad = (K + kstep - 1) / kstep * kstep;  // K padded to whole k-steps only
-    const int nchunk = (kpad + KC - 1) / KC;
-    const int kl = kpad - (nchunk - 1) * KC;
+    const int nchunk = (kpad + KCK - 1) / KCK;
+    const int kl = kpad - (nchunk - 1) * KCK;
     t->kpad_smax = std::max(t->kpad_smax, kpad);
     for (int tile = 0; tile < t->ntile_s; ++tile) {
       const int rows = std::min(128, (t->nh - 128 * tile + 7) / 8 * 8);
       tj.push_back(TabJob{aoff, m, rows, tile, nchunk, kl});
       jsP.push_back(Job{aoff, m, tile, nchunk, kpad, 0, kl, rows});
       jsH.push_back(Job{aoff, m, tile, nchunk, kpad, 1, kl, rows});
-      aoff += (long long)rows * ((nchunk - 1) * KC + kl) * eb;
+      aoff += (long long)rows * ((nchunk - 1) * KC + kw * kl) * eb;
     }
   }
   const long long tab_s_bytes = aoff;
   // ---- analysis jobs: (m, degree tile, tab), rows = degrees of both parities, K = northern
   // latitudes; B = [N + S | N - S] of each field of zonal order m --------------------------
   t->kpad_a = (t->nh + kstep - 1) / kstep * kstep;
-  const int nchunk_a = (t->kpad_a + KC - 1) / KC;
-  const int kl_a = t->kpad_a - (nchunk_a - 1) * KC;
+  const int nchunk_a = (t->kpad_a + KCK - 1) / KCK;
+  const int kl_a = t->kpad_a - (nchunk_a - 1) * KCK;
   std::vector<TabJob> ta;
   std::vector<Job> jaP, jaH;
   aoff = 0;
@@ -688,7 +744,7 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
       ta.push_back(TabJob{aoff, m, rows, tile, nchunk_a, kl_a});
       jaP.push_back(Job{aoff, m, tile, nchunk_a, t->kpad_a, 0, kl_a, rows});
       jaH.push_back(Job{aoff, m, tile, nchunk_a, t->kpad_a, 1, kl_a, rows});
-      aoff += (long long)rows * ((nchunk_a - 1) * KC + kl_a) * eb;
+      aoff += (long long)rows * ((nchunk_a - 1) * KC + kw * kl_a) * eb;
     }
   }
   const long long tab_a_bytes = aoff;
@@ -696,7 +752,7 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
   // latitudes or all degrees) must fit one B buffer and two ring stages in shared memory
   {
     auto ncols_of = [](int nf, int cpf) { return std::max(16, (nf * cpf + 15) / 16 * 16); };
-    const size_t bmax = (size_t)ncols_of(2 * max_fields, 4) * std::max(t->kpad_a, t->kpad_smax) * eb;
+    const size_t bmax = (size_t)kw * ncols_of(2 * max_fields, 4) * std::max(t->kpad_a, t->kpad_smax) * eb;
     if (bmax + 2 * chunk + 4096 > TC_SMEM_BUDGET) {
       tc_legendre_destroy(t);
       return fail(REXI_EINVAL,
@@ -721,10 +777,10 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
   cudaMemset(t->err, 0, sizeof(int));
   cudaMemcpy(d_tj, tj.data(), sizeof(TabJob) * tj.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(d_ta, ta.data(), sizeof(TabJob) * ta.size(), cudaMemcpyHostToDevice);
-  k_tc_table<<<(int)tj.size(), 128, 0, stream>>>(P, t->tabPs, d_tj, (int)tj.size(), T, t->nh, 1, t->bf16);
-  k_tc_table<<<(int)tj.size(), 128, 0, stream>>>(H, t->tabHs, d_tj, (int)tj.size(), T, t->nh, 1, t->bf16);
-  k_tc_table<<<(int)ta.size(), 128, 0, stream>>>(P, t->tabPa, d_ta, (int)ta.size(), T, t->nh, 0, t->bf16);
-  k_tc_table<<<(int)ta.size(), 128, 0, stream>>>(H, t->tabHa, d_ta, (int)ta.size(), T, t->nh, 0, t->bf16);
+  k_tc_table<<<(int)tj.size(), 128, 0, stream>>>(P, t->tabPs, d_tj, (int)tj.size(), T, t->nh, 1, t->pm);
+  k_tc_table<<<(int)tj.size(), 128, 0, stream>>>(H, t->tabHs, d_tj, (int)tj.size(), T, t->nh, 1, t->pm);
+  k_tc_table<<<(int)ta.size(), 128, 0, stream>>>(P, t->tabPa, d_ta, (int)ta.size(), T, t->nh, 0, t->pm);
+  k_tc_table<<<(int)ta.size(), 128, 0, stream>>>(H, t->tabHa, d_ta, (int)ta.size(), T, t->nh, 0, t->pm);
   e = cudaStreamSynchronize(stream);
   cudaFree(d_tj);
   cudaFree(d_ta);
@@ -732,8 +788,9 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
     tc_legendre_destroy(t);
     return tc_fail("tensor-core Legendre table kernels", e);
   }
-  if ((e = cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_BUDGET)) ||
-      (e = cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_BUDGET))) {
+  if ((e = cudaFuncSetAttribute(k_tc_gemm<PM_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_BUDGET)) ||
+      (e = cudaFuncSetAttribute(k_tc_gemm<PM_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_BUDGET)) ||
+      (e = cudaFuncSetAttribute(k_tc_gemm<PM_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_BUDGET))) {
     tc_legendre_destroy(t);
     return tc_fail("cudaFuncSetAttribute(k_tc_gemm)", e);
   }
@@ -784,7 +841,9 @@ static int gemm(TcLegendre* t, bool synth, bool vector, int nf, const double2* i
   g.nj_max = sc.nj_max;
   // B buffers of the largest B operand of the call, then as many A stages as fit
   const size_t chunk = 128ull * t->KC * t->eb;
-  const size_t bslot = ((size_t)ncols * (synth ? t->kpad_smax : t->kpad_a) * t->eb + 127) / 128 * 128;
+  // one B copy, rounded to 128 bytes; PM_TF32X3 keeps the lo copy behind the hi copy
+  const size_t bcopy = ((size_t)ncols * (synth ? t->kpad_smax : t->kpad_a) * t->eb + 127) / 128 * 128;
+  const size_t bslot = t->pm == PM_TF32X3 ? 2 * bcopy : bcopy;
   const size_t jobs_bytes = sizeof(Job) * (size_t)g.nj_max;
   auto fixed = [&](int nb) { return nb * bslot + 8 * (2 * TC_MAXSTAGES + 2 * nb + 2 * TC_NJB + 2) + jobs_bytes; };
   // B buffers: 4 when that leaves >= 4 ring stages, else 2, else 1 (>= 2 ring stages always)
@@ -792,12 +851,14 @@ static int gemm(TcLegendre* t, bool synth, bool vector, int nf, const double2* i
   if (fixed(g.nb) + 2 * chunk > TC_SMEM_BUDGET) return fail(REXI_EINVAL, "tensor-core Legendre: B operand too large");
   g.stages = (int)std::min<size_t>(TC_MAXSTAGES, (TC_SMEM_BUDGET - fixed(g.nb)) / chunk);
   g.bslot = (uint32_t)bslot;
+  g.blo = t->pm == PM_TF32X3 ? (uint32_t)bcopy : 0u;
   const size_t smem =
       (size_t)g.stages * chunk + g.nb * bslot + 8 * (2 * g.stages + 2 * g.nb + 2 * TC_NJB + 2) + jobs_bytes;
   {
     const int ph = t->prof ? t->prof->begin(2) : -1;
-    if (t->bf16) k_tc_gemm<true><<<sc.grid, TC_THREADS, smem, s>>>(g);
-    else k_tc_gemm<false><<<sc.grid, TC_THREADS, smem, s>>>(g);
+    if (t->pm == PM_BF16) k_tc_gemm<PM_BF16><<<sc.grid, TC_THREADS, smem, s>>>(g);
+    else if (t->pm == PM_TF32X3) k_tc_gemm<PM_TF32X3><<<sc.grid, TC_THREADS, smem, s>>>(g);
+    else k_tc_gemm<PM_TF32><<<sc.grid, TC_THREADS, smem, s>>>(g);
     if (t->prof) t->prof->end(ph);
   }
   cudaError_t e = cudaGetLastError();

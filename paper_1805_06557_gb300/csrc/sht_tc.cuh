@@ -1,4 +1,5 @@
-// Tensor-core (tcgen05) Legendre contractions for sh_plan precisions SH_TF32 / SH_BF16.
+// Tensor-core (tcgen05) Legendre contractions for sh_plan precisions SH_TF32, SH_BF16 and
+// SH_TF32X3.
 #pragma once
 #include <vector>
 
@@ -72,8 +73,9 @@ struct TcLegendre;
 // stage timer of the owning plan (may be null)
 void tc_legendre_set_prof(TcLegendre* t, StageProf* prof);
 
+// mode: SH_TF32, SH_BF16 or SH_TF32X3
 int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const double* w,
-                       const double* wq, int T, int nlat, int max_fields, bool bf16,
+                       const double* wq, int T, int nlat, int max_fields, int mode,
                        cudaStream_t stream);
 void tc_legendre_destroy(TcLegendre* t);
 int tc_leg_synth(TcLegendre* t, const double2* spec, double2* F, int nf, cudaStream_t s);

@@ -469,8 +469,8 @@ class LgPlan:
 
 
 # ---- spherical-harmonic transforms (include/sht.h) ------------------------------------
-SH_FP64, SH_TF32, SH_BF16 = 0, 1, 2
-_SH_PREC = {"fp64": SH_FP64, "tf32": SH_TF32, "bf16": SH_BF16}
+SH_FP64, SH_TF32, SH_BF16, SH_TF32X3 = 0, 1, 2, 3
+_SH_PREC = {"fp64": SH_FP64, "tf32": SH_TF32, "bf16": SH_BF16, "tf32x3": SH_TF32X3}
 
 
 class ShDesc(ctypes.Structure):
