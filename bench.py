@@ -497,28 +497,69 @@ def lg_rexi(torch, rexi, fp64_peak, T=511, N=2048, dt=7200.0, batch=32, reps=20)
                          "fp64_frac": flops / (ms * 1e-3) / 1e12 / fp64_peak if fp64_peak else None}}
 
 
+def _max_wind(torch, rexi, U0, T, nlat, nlon):
+    """Largest wind speed |V| [m/s] of a spectral state on its Gauss grid (FP64 vector synthesis
+    of psi = lap^-1 zeta, chi = lap^-1 delta through the library)."""
+    import numpy as np
+    from paper_1805_06557_gb300 import synthetic as syn
+    a = syn.RADIUS
+    sh = rexi.ShPlan(T, nlat, nlon, a, "fp64", max_fields=1)
+    nn = np.concatenate([np.arange(m, T + 1) for m in range(T + 1)]).astype(float)
+    ilap = np.where(nn > 0, -a * a / np.maximum(nn * (nn + 1), 1.0), 0.0)
+    psi = torch.from_numpy((U0[1] * ilap)[None].copy()).cuda()
+    chi = torch.from_numpy((U0[2] * ilap)[None].copy()).cuda()
+    Ug = torch.empty(1, nlat, nlon, dtype=torch.float64, device="cuda")
+    Vg = torch.empty_like(Ug)
+    sh.synthesis_uv(psi, chi, Ug, Vg, 1)
+    mu, _ = sh.grid()
+    cos = torch.from_numpy(np.sqrt((1.0 - mu) * (1.0 + mu))).cuda()[None, :, None]
+    umax = float(torch.sqrt((Ug / cos) ** 2 + (Vg / cos) ** 2).max())
+    sh.close()
+    return umax
+
+
 def swe_steps(torch, rexi, configs):
     """Nonlinear SWE steps (Strang ver1: N by RK2 midpoint for dt/2, REXI L for dt, N for
-    dt/2; variants may name the ETD2RK scheme instead) on balanced n^-3 states: steps/s (timed
-    without profiling) and per-stage device times (a second, profiled run of the same steps),
-    whether the state stayed finite (the explicit RK2 half-steps of N are bound by the
-    advective CFL limit, which dt = 7200 s exceeds at T511), and each variant's per-field
-    error against the all-FP64 plan after ONE step from the same state."""
+    dt/2; variants may name another scheme) on balanced n^-3 states: steps/s (timed without
+    profiling), per-stage device times (a second, profiled run of the same steps), whether the
+    state stayed finite, and each variant's per-field error against the all-FP64 plan after one
+    step and after all timed steps from the same state.
+
+    A configuration may carry a time-step treatment (a dict): "contour": "select" (the
+    library's contour search, rexi_contour_select, instead of the fixed rule), "courant": c
+    (sub-steps of the explicit part from swe_substeps with the state's largest wind), and
+    "efold_s": t (del^4 hyper-diffusion whose truncation degree e-folds in t seconds)."""
     import numpy as np
     from paper_1805_06557_gb300 import synthetic as syn
     out = []
-    for (T, nlat, nlon, N, dt, nsteps, variants) in configs:
+    for cfg_in in configs:
+        (T, nlat, nlon, N, dt, nsteps, variants) = cfg_in[:7]
+        treat = cfg_in[7] if len(cfg_in) > 7 else {}
         X = rexi.spectrum_bound(T, dt, syn.OMEGA, syn.RADIUS, syn.PHIBAR)
-        p0, Xc = contour(X)
+        p0, Xc = rexi.contour_select(X, N) if treat.get("contour") == "select" else contour(X)
         U0 = syn.balanced_state(T, 2 if T == 127 else 4)
-        ref1 = None
+        nsub, visc = 1, 0.0
+        if "courant" in treat:
+            umax = _max_wind(torch, rexi, U0, T, nlat, nlon)
+            nsub = rexi.swe_substeps(T, 0.5 * dt, umax, syn.RADIUS, treat["courant"])
+        if "efold_s" in treat:
+            visc = 1.0 / (treat["efold_s"] * (T * (T + 1.0) / syn.RADIUS ** 2) ** 2)
         cfg = {"workload": "nonlinear SWE, T%d on %d x %d Gauss grid, %d poles, dt=%g s, %d timed steps, "
-                           "balanced n^-3 state (20 m/s rms)" % (T, nlat, nlon, N, dt, nsteps), "variants": {}}
+                           "balanced n^-3 state (20 m/s rms)" % (T, nlat, nlon, N, dt, nsteps),
+               "contour": {"p0": p0, "Xc": Xc, "X": X}, "nsub": nsub, "visc_del4": visc,
+               "variants": {}}
+        if "courant" in treat:
+            cfg["max_wind_ms"] = umax
+            cfg["courant"] = treat["courant"]
+        if "efold_s" in treat:
+            cfg["efold_truncation_s"] = treat["efold_s"]
+        ref1 = refn = None
         for var in variants:
             rprec, sprec = var[0], var[1]
             scheme = var[2] if len(var) > 2 else "ver1"
             p = rexi.SwePlan(T, nlat, nlon, dt, syn.OMEGA, syn.RADIUS, syn.PHIBAR, N, p0, Xc,
-                             rexi_precision=rprec, sh_precision=sprec, scheme=scheme)
+                             rexi_precision=rprec, sh_precision=sprec, scheme=scheme, nsub=nsub,
+                             visc=visc, visc_order=2)
             u = torch.from_numpy(U0).cuda().contiguous()
             w1 = u.clone()
             p.step(w1, 1)                                  # one step: error figure and warm-up
@@ -531,6 +572,7 @@ def swe_steps(torch, rexi, configs):
             e1.record()
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
+            last = u2.cpu().numpy()
             # stage times from a separate profiled run of the same steps from the same state
             u3 = u.clone()
             p.set_profiling(True)
@@ -542,13 +584,16 @@ def swe_steps(torch, rexi, configs):
             v = {"steps_per_s": nsteps / (ms * 1e-3), "ms_per_step": ms / nsteps,
                  "stage_ms_per_step": {k: val[0] / nsteps for k, val in prof.items()},
                  "finite_after_one_step": bool(np.all(np.isfinite(one))),
-                 "finite_after_timed_steps": bool(torch.isfinite(u2).all().item())}
+                 "finite_after_timed_steps": bool(np.all(np.isfinite(last)))}
             if scheme != "ver1":
                 pass   # another scheme: no error against the ver1 FP64 reference
             elif ref1 is None:
-                ref1 = one
-            elif v["finite_after_one_step"] and np.all(np.isfinite(ref1)):
-                v["rel_err_vs_fp64_one_step"] = _rel_fields(one, ref1, T)
+                ref1, refn = one, last
+            else:
+                if v["finite_after_one_step"] and np.all(np.isfinite(ref1)):
+                    v["rel_err_vs_fp64_one_step"] = _rel_fields(one, ref1, T)
+                if v["finite_after_timed_steps"] and np.all(np.isfinite(refn)):
+                    v["rel_err_vs_fp64_after_timed_steps"] = _rel_fields(last, refn, T)
             cfg["variants"][key] = v
             p.close()
         out.append(cfg)
@@ -788,14 +833,18 @@ def main():
     if not args.no_sh:
         sh = sh_transforms(torch, rexi, fp64_tf)
         swe = swe_steps(torch, rexi, [
-            (127, 192, 384, 512, 1800.0, 48, [("fp64", "fp64"), ("mixed", "fp64"), ("mixed", "tf32"),
-                                              ("fp64", "fp64", "etdrk"), ("mixed", "fp64", "etdrk"),
-                                              ("fp64", "fp64", "irk"), ("fp64", "fp64", "lg_ver1"),
-                                              ("fp64", "fp64", "lg_etdrk"), ("fp64", "fp64", "lg_irk_ver0"),
-                                              ("fp64", "tf32", "lg_ver1")]),
-            (511, 768, 1536, 2048, 7200.0, 4, [("fp64", "fp64"), ("mixed", "fp64"), ("mixed", "tf32"),
-                                                ("mixed", "bf16"), ("fp64", "fp64", "lg_ver1"),
-                                                ("fp64", "tf32", "lg_ver1")])])
+            (127, 192, 384, 512, 1800.0, 48, [("fp64", "fp64"), ("mixed", "fp64"), ("mixed", "tf32x3"),
+                                              ("mixed", "tf32"), ("fp64", "fp64", "etdrk"),
+                                              ("mixed", "fp64", "etdrk"), ("fp64", "fp64", "irk"),
+                                              ("fp64", "fp64", "lg_ver1"), ("fp64", "fp64", "lg_etdrk"),
+                                              ("fp64", "fp64", "lg_irk_ver0"), ("fp64", "tf32x3", "lg_ver1")]),
+            # T511, dt = 7200 s: the library's contour search (the fixed rule leaves a scalar error
+            # of 2e5 at X = 182), the explicit part sub-stepped at Courant 0.5 under the state's
+            # largest wind, del^4 diffusion with the truncation degree e-folding in 900 s
+            (511, 768, 1536, 2048, 7200.0, 12, [("fp64", "fp64"), ("mixed", "fp64"), ("mixed", "tf32x3"),
+                                                 ("mixed", "tf32"), ("mixed", "bf16"),
+                                                 ("fp64", "tf32x3", "lg_ver1")],
+             {"contour": "select", "courant": 0.5, "efold_s": 900.0})])
         lg = lg_rexi(torch, rexi, fp64_tf)
 
     cpu = cpu_fair = None

@@ -59,7 +59,30 @@ typedef struct swe_plan_desc {
   int scheme;               /* one of the SWE_* scheme identifiers above                    */
   void* stream;             /* cudaStream_t; NULL (the legacy default stream): the plan makes */
                             /* its own blocking stream, implicitly ordered with the default  */
+  int nsub;                 /* explicit sub-steps: every RK2 integration of the nonlinear part */
+                            /* over an interval tau (the Strang halves of ver1 / irk / lg ver1,  */
+                            /* the N step of ver0 / lg irk ver0) takes nsub midpoint steps of    */
+                            /* tau / nsub; 0 or 1: one step (the paper's scheme); <= 4096.  The  */
+                            /* linear part keeps its full step.  swe_substeps() gives the count */
+                            /* for an advective Courant limit.  ETD2RK schemes ignore it.       */
+  double visc;              /* hyper-diffusion coefficient nu >= 0 (0: none, the paper's       */
+                            /* inviscid runs): the term (-1)^(q+1) nu lap^q on Phi', zeta,      */
+                            /* delta, integrated exactly in spectral space (degree n decays by  */
+                            /* exp(-t nu (n(n+1)/a^2)^q)) as half steps around every step of    */
+                            /* the scheme: U+ = D^{dt/2} o step o D^{dt/2} (U)                  */
+  int visc_order;           /* q in [1, 8]; 0: 2 (del^4)                                      */
 } swe_plan_desc;
+
+/*
+ * swe_substeps -- explicit sub-steps for the nonlinear part over an interval tau (reading of
+ * Sec. 2.3 and 4.4: the explicitly treated nonlinear terms limit the time step, the REXI
+ * linear step does not): the smallest n >= 1 with
+ *     (tau / n) * umax * sqrt(T (T+1)) / radius <= courant,
+ * i.e. the advective phase change of the highest resolved degree under the largest wind speed
+ * umax [m/s] stays within `courant` radians per midpoint step.  Host only.  Returns n, or
+ * REXI_EINVAL for T < 1, tau < 0, umax < 0, radius <= 0 or courant <= 0 (n is capped at 4096).
+ */
+int swe_substeps(int T, double tau, double umax, double radius, double courant);
 
 /* Creates the REXI plan(s: three for etdrk, gravity-only plans for lg), the SH plan and all
  * work buffers.

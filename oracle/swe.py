@@ -11,7 +11,12 @@ on the Gauss grid, divergence / curl / Laplacian by analysis.
 
 Time integrators (Sec. 4.1, 4.4; Table 2):
   * erk  : 2nd-order explicit Runge-Kutta.  Reading taken (the paper does not name the
-           variant): the midpoint rule.
+           variant): the midpoint rule.  Every scheme below that integrates N by erk over an
+           interval tau takes `nsub` midpoint steps of tau / nsub (default 1, the paper's
+           single step).  Reading taken: the paper treats N explicitly and notes that
+           explicitly treated nonlinearities limit the time step (Sec. 2.3); at T511 with
+           dt = 7200 s one midpoint step over dt/2 exceeds the advective stability limit, so
+           the explicit part is sub-stepped while the linear part keeps the full REXI step.
   * ver1 : T(U) = N^{dt/2} o L^{dt} o N^{dt/2} (U), the linear part L = L_g + L_c by REXI
            (method id l_rexi_n_erk_ver1, Coriolis inside REXI).
   * ver0 : T(U) = L^{dt/2} o N^{dt} o L^{dt/2} (U).
@@ -65,9 +70,11 @@ def rk2(U, f, tau):
     return U + tau * k2
 
 
-def rk2_nonlinear(U, grid, tau):
-    """Integrate dU/dt = N(U) over tau with the midpoint rule (erk, 2nd order)."""
-    return rk2(U, lambda V: nonlinear(V, grid), tau)
+def rk2_nonlinear(U, grid, tau, nsub=1):
+    """Integrate dU/dt = N(U) over tau with nsub midpoint steps of tau / nsub (erk, 2nd order)."""
+    for _ in range(nsub):
+        U = rk2(U, lambda V: nonlinear(V, grid), tau / nsub)
+    return U
 
 
 def nonlinear_lc(U, grid, Omega):
@@ -75,23 +82,30 @@ def nonlinear_lc(U, grid, Omega):
     return linop.apply_L(U, grid.T, Omega, grid.a, 0.0, part="Lc") + nonlinear(U, grid)
 
 
-def strang_lg_ver1(U, grid, dt, Omega, Phibar, z, w):
+def rk2_sub(U, f, tau, nsub):
+    """nsub midpoint steps of tau / nsub for dU/dt = f(U)."""
+    for _ in range(nsub):
+        U = rk2(U, f, tau / nsub)
+    return U
+
+
+def strang_lg_ver1(U, grid, dt, Omega, Phibar, z, w, nsub=1):
     """One step of lg_rexi_lc_n_erk_ver1:  N'^{dt/2} o L_g^{dt} o N'^{dt/2}  (Sec. 4.4 version 1
     with the Coriolis term in the explicit part)."""
     T, a = grid.T, grid.a
     f = lambda V: nonlinear_lc(V, grid, Omega)
-    U1 = rk2(U, f, 0.5 * dt)
+    U1 = rk2_sub(U, f, 0.5 * dt, nsub)
     U2 = rexi_lg.rexi_step_lg(U1, T, dt, a, Phibar, z, w)
-    return rk2(U2, f, 0.5 * dt)
+    return rk2_sub(U2, f, 0.5 * dt, nsub)
 
 
-def cn_lg_ver0(U, grid, dt, Omega, Phibar):
+def cn_lg_ver0(U, grid, dt, Omega, Phibar, nsub=1):
     """One step of lg_irk_lc_n_erk_ver0 (the paper's best implicit method, Sec. 5.2):
     CN_g^{dt/2} o N'^{dt} o CN_g^{dt/2}, CN_g the Crank-Nicolson step of the gravity operator
     alone and N' = L_c + N by RK2 (Sec. 4.4 version 0)."""
     T, a = grid.T, grid.a
     U1 = rexi.cn_step(U, T, 0.5 * dt, Omega, a, Phibar, part="Lg")
-    U2 = rk2(U1, lambda V: nonlinear_lc(V, grid, Omega), dt)
+    U2 = rk2_sub(U1, lambda V: nonlinear_lc(V, grid, Omega), dt, nsub)
     return rexi.cn_step(U2, T, 0.5 * dt, Omega, a, Phibar, part="Lg")
 
 
@@ -105,29 +119,30 @@ def etd2rk_lg(U, grid, dt, Omega, Phibar, z, w0, w1, w2):
     return A + dt * R(nonlinear_lc(A, grid, Omega) - NU, w2)
 
 
-def strang_ver1(U, grid, dt, Omega, Phibar, z, w):
-    """One step of l_rexi_n_erk_ver1:  N^{dt/2} o L^{dt} o N^{dt/2}  (Sec. 4.4, version 1)."""
+def strang_ver1(U, grid, dt, Omega, Phibar, z, w, nsub=1):
+    """One step of l_rexi_n_erk_ver1:  N^{dt/2} o L^{dt} o N^{dt/2}  (Sec. 4.4, version 1);
+    each N^{dt/2} by nsub midpoint steps."""
     T, a = grid.T, grid.a
-    U1 = rk2_nonlinear(U, grid, 0.5 * dt)
+    U1 = rk2_nonlinear(U, grid, 0.5 * dt, nsub)
     U2 = rexi.rexi_step(U1, T, dt, Omega, a, Phibar, z, w)
-    return rk2_nonlinear(U2, grid, 0.5 * dt)
+    return rk2_nonlinear(U2, grid, 0.5 * dt, nsub)
 
 
-def strang_ver0(U, grid, dt, Omega, Phibar, z_half, w_half):
+def strang_ver0(U, grid, dt, Omega, Phibar, z_half, w_half, nsub=1):
     """One step of l_rexi_n_erk_ver0:  L^{dt/2} o N^{dt} o L^{dt/2}  (Sec. 4.4, version 0);
     z_half, w_half are REXI coefficients for a step of dt/2."""
     T, a = grid.T, grid.a
     U1 = rexi.rexi_step(U, T, 0.5 * dt, Omega, a, Phibar, z_half, w_half)
-    U2 = rk2_nonlinear(U1, grid, dt)
+    U2 = rk2_nonlinear(U1, grid, dt, nsub)
     return rexi.rexi_step(U2, T, 0.5 * dt, Omega, a, Phibar, z_half, w_half)
 
 
-def cn_ver1(U, grid, dt, Omega, Phibar):
+def cn_ver1(U, grid, dt, Omega, Phibar, nsub=1):
     """One step of l_irk_n_erk_ver1:  N^{dt/2} o CN^{dt} o N^{dt/2}."""
     T, a = grid.T, grid.a
-    U1 = rk2_nonlinear(U, grid, 0.5 * dt)
+    U1 = rk2_nonlinear(U, grid, 0.5 * dt, nsub)
     U2 = rexi.cn_step(U1, T, dt, Omega, a, Phibar)
-    return rk2_nonlinear(U2, grid, 0.5 * dt)
+    return rk2_nonlinear(U2, grid, 0.5 * dt, nsub)
 
 
 def etd2rk(U, grid, dt, Omega, Phibar, z, w0, w1, w2, nonlin=None):
@@ -138,6 +153,21 @@ def etd2rk(U, grid, dt, Omega, Phibar, z, w0, w1, w2, nonlin=None):
     NU = N_(U)
     A = rexi.rexi_step(U, T, dt, Omega, a, Phibar, z, w0) + dt * rexi.rexi_step(NU, T, dt, Omega, a, Phibar, z, w1)
     return A + dt * rexi.rexi_step(N_(A) - NU, T, dt, Omega, a, Phibar, z, w2)
+
+
+def diffuse(U, T, radius, tau, nu, q=2):
+    """Exact flow over tau of the hyper-diffusion term (-1)^(q+1) nu lap^q on all three fields:
+    lap Y_n = -n(n+1)/a^2 Y_n, so each degree n decays by exp(-tau nu (n(n+1)/a^2)^q).  Not in
+    the paper's benchmarks (which run inviscid); the T511 configuration needs it (see strang
+    steps with diffusion below)."""
+    lam = -sht.laplacian_eig(T, radius)
+    return U * np.exp(-tau * nu * lam ** q)[None, :]
+
+
+def with_diffusion(step, U, T, radius, dt, nu, q=2):
+    """D^{dt/2} o step o D^{dt/2} (U): a time step with the diffusion flow D split off
+    symmetrically (2nd order like the Strang step itself)."""
+    return diffuse(step(diffuse(U, T, radius, 0.5 * dt, nu, q)), T, radius, 0.5 * dt, nu, q)
 
 
 def full_tendency(U, grid, Omega, Phibar):

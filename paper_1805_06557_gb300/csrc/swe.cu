@@ -133,6 +133,25 @@ __global__ void k_apply_L(const double2* __restrict__ U, const D4* __restrict__ 
   out[2 * nlm + i] = make_double2(fma(s, lD.x, d0.x), fma(s, lD.y, d0.y));
 }
 
+// U <- fac[n] U on all three fields: the exact factor exp(-tau nu (n(n+1)/a^2)^q) of the
+// hyper-diffusion term, fac formed on the host per degree (fac[0] = 1)
+__global__ void k_diffuse(double2* __restrict__ U, const double* __restrict__ fac, int T, int nlm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nlm) return;
+  int lo = 0, hi = T;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (moff(T, mid) <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  const double f = fac[lo + (i - moff(T, lo))];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double2 u = U[(size_t)k * nlm + i];
+    U[(size_t)k * nlm + i] = make_double2(f * u.x, f * u.y);
+  }
+}
+
 // out = a + s * b over n complex entries (ETD2RK combinations)
 __global__ void k_axpy(const double2* __restrict__ a, const double2* __restrict__ b, double s,
                        double2* __restrict__ out, int n) {
@@ -165,6 +184,7 @@ struct swe_plan {
           *kes = nullptr;
   double *PZ = nullptr, *Ug = nullptr, *Vg = nullptr, *A = nullptr, *B = nullptr, *KE = nullptr,
          *ikc = nullptr, *ilap = nullptr;
+  double* dfac = nullptr;  // hyper-diffusion factor per degree over dt/2 (nullptr: none)
   StageProf prof;  // the step's own grid and spectral kernels (stage 0)
 };
 
@@ -180,7 +200,8 @@ extern "C" int swe_plan_destroy(swe_plan* p) {
   p->prof.release();
   for (void* q : {(void*)p->psi, (void*)p->chi, (void*)p->Um, (void*)p->Ut, (void*)p->dv, (void*)p->cu,
                   (void*)p->kes, (void*)p->PZ, (void*)p->Ug, (void*)p->Vg, (void*)p->A, (void*)p->B,
-                  (void*)p->KE, (void*)p->ikc, (void*)p->ilap, (void*)p->NU, (void*)p->A3, (void*)p->Ltab})
+                  (void*)p->KE, (void*)p->ikc, (void*)p->ilap, (void*)p->NU, (void*)p->A3, (void*)p->Ltab,
+                  (void*)p->dfac})
     cudaFree(q);
   if (p->own_stream) cudaStreamDestroy(p->stream);
   delete p;
@@ -193,6 +214,9 @@ extern "C" int swe_plan_create(const swe_plan_desc* desc, swe_plan** out) {
   const swe_plan_desc& d = *desc;
   if (d.scheme < SWE_L_REXI_N_ERK_VER1 || d.scheme > SWE_LG_IRK_LC_N_ERK_VER0)
     return fail(REXI_EINVAL, "swe_plan_create: unknown scheme %d", d.scheme);
+  if (d.nsub < 0 || d.nsub > 4096) return fail(REXI_EINVAL, "swe_plan_create: nsub = %d outside [0, 4096]", d.nsub);
+  if (!(d.visc >= 0) || d.visc_order < 0 || d.visc_order > 8)
+    return fail(REXI_EINVAL, "swe_plan_create: need visc >= 0 and visc_order in [0, 8]");
   swe_plan* p = new swe_plan();
   p->d = d;
   p->is_lg = d.scheme == SWE_LG_REXI_LC_N_ERK_VER1 || d.scheme == SWE_LG_REXI_LC_N_ETDRK ||
@@ -320,6 +344,17 @@ extern "C" int swe_plan_create(const swe_plan_desc* desc, swe_plan** out) {
   if ((e = cudaMemcpy(p->ikc, ikc.data(), sizeof(double) * d.nlat, cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(p->ilap, ilap.data(), sizeof(double) * (d.T + 1), cudaMemcpyHostToDevice)))
     return bail(cuda_fail(e, "swe_plan_create: cudaMemcpy"));
+  if (d.visc > 0) {  // exp(-(dt/2) nu (n(n+1)/a^2)^q) per degree
+    const int q = d.visc_order > 0 ? d.visc_order : 2;
+    std::vector<double> f(d.T + 1);
+    for (int n = 0; n <= d.T; ++n)
+      f[n] = std::exp(-0.5 * d.dt * d.visc * std::pow(double(n) * (n + 1) / (d.radius * d.radius), q));
+    if ((e = cudaMalloc(&p->dfac, sizeof(double) * (d.T + 1))) ||
+        (e = cudaMemcpy(p->dfac, f.data(), sizeof(double) * (d.T + 1), cudaMemcpyHostToDevice))) {
+      cudaGetLastError();
+      return bail(fail(REXI_ENOMEM, "swe_plan_create: diffusion table: %s", cudaGetErrorString(e)));
+    }
+  }
   *out = p;
   return REXI_OK;
 }
@@ -356,12 +391,18 @@ static int nonlinear_update(swe_plan* p, const double2* U, const double2* base, 
   return e ? cuda_fail(e, "swe nonlinear kernels") : REXI_OK;
 }
 
-// U <- U + tau N(U + tau/2 N(U))   (explicit midpoint rule; N' = L_c + N for the lg schemes)
+// U <- U + h N(U + h/2 N(U)), h = tau / nsub, nsub times   (explicit midpoint rule; N' = L_c + N
+// for the lg schemes)
 static int rk2_nonlinear(swe_plan* p, double2* U, double tau) {
   const D4* ctab = p->is_lg ? p->Ltab : nullptr;
-  int rc = nonlinear_update(p, U, U, 0.5 * tau, p->Um, ctab);
-  if (rc) return rc;
-  return nonlinear_update(p, p->Um, U, tau, U, ctab);
+  const int ns = p->d.nsub > 1 ? p->d.nsub : 1;
+  const double h = tau / ns;
+  for (int i = 0; i < ns; ++i) {
+    int rc = nonlinear_update(p, U, U, 0.5 * h, p->Um, ctab);
+    if (rc) return rc;
+    if ((rc = nonlinear_update(p, p->Um, U, h, U, ctab))) return rc;
+  }
+  return REXI_OK;
 }
 
 // the gravity-only REXI step, timed as part of the REXI stage
@@ -372,14 +413,43 @@ static int lg_step(swe_plan* p, int k, const double2* in, double2* out) {
   return rc;
 }
 
+extern "C" int swe_substeps(int T, double tau, double umax, double radius, double courant) {
+  if (T < 1 || !(tau >= 0) || !(umax >= 0) || !(radius > 0) || !(courant > 0))
+    return fail(REXI_EINVAL, "swe_substeps: need T >= 1, tau >= 0, umax >= 0, radius > 0, courant > 0");
+  const double c = tau * umax * std::sqrt(double(T) * (T + 1.0)) / (radius * courant);
+  if (!(c <= 4096.0)) return 4096;
+  const int n = (int)std::ceil(c);
+  return n < 1 ? 1 : n;
+}
+
 extern "C" int swe_nonlinear(swe_plan* p, const void* state, void* tend) {
   if (!p || !state || !tend) return fail(REXI_EINVAL, "swe_nonlinear: null argument");
   if (state == tend) return fail(REXI_EINVAL, "swe_nonlinear: state and tendency alias");
   return nonlinear_update(p, (const double2*)state, nullptr, 0.0, (double2*)tend);
 }
 
-// One step of the plan's scheme on U: kernels and device copies on the plan stream only.
+static int scheme_step(swe_plan* p, double2* U);
+
+// the hyper-diffusion factor over dt/2 (no-op without diffusion)
+static int diffuse_half(swe_plan* p, double2* U) {
+  if (!p->dfac) return REXI_OK;
+  const int ph = p->prof.begin(0);
+  k_diffuse<<<(p->nlm + 255) / 256, 256, 0, p->stream>>>(U, p->dfac, p->d.T, p->nlm);
+  p->prof.end(ph);
+  REXI_CUDA_TRY(cudaGetLastError());
+  return REXI_OK;
+}
+
+// One step on U: D^{dt/2} o (the scheme's step) o D^{dt/2} with D the exact hyper-diffusion
+// flow (identity without diffusion); kernels and device copies on the plan stream only.
 static int step_once(swe_plan* p, double2* U) {
+  int rc;
+  if ((rc = diffuse_half(p, U))) return rc;
+  if ((rc = scheme_step(p, U))) return rc;
+  return diffuse_half(p, U);
+}
+
+static int scheme_step(swe_plan* p, double2* U) {
   const size_t s3 = sizeof(double2) * 3 * (size_t)p->nlm;
   const double dt = p->d.dt;
   {

@@ -582,7 +582,8 @@ class SweDesc(ctypes.Structure):
                 ("phibar", ctypes.c_double), ("N", ctypes.c_int), ("p0", ctypes.c_double),
                 ("Xc", ctypes.c_double), ("rexi_precision", ctypes.c_int),
                 ("sh_precision", ctypes.c_int), ("scheme", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("nsub", ctypes.c_int), ("visc", ctypes.c_double),
+                ("visc_order", ctypes.c_int)]
 
 
 _lib.swe_plan_create.argtypes = [ctypes.POINTER(SweDesc), ctypes.POINTER(ctypes.c_void_p)]
@@ -590,6 +591,14 @@ _lib.swe_plan_destroy.argtypes = [ctypes.c_void_p]
 _lib.swe_step.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
 _lib.swe_nonlinear.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
 _lib.swe_plan_set_profiling.argtypes = [ctypes.c_void_p, ctypes.c_int]
+_lib.swe_substeps.argtypes = [ctypes.c_int] + [ctypes.c_double] * 4
+
+
+def swe_substeps(T, tau, umax, radius, courant=1.0):
+    """Explicit midpoint sub-steps over tau so that the advective phase change of degree T under
+    the wind umax stays within `courant` radians per sub-step (include/swe.h)."""
+    n = _lib.swe_substeps(int(T), float(tau), float(umax), float(radius), float(courant))
+    return _check(n) if n < 0 else int(n)
 _lib.swe_plan_get_profile.argtypes = [ctypes.c_void_p, _dp, _ip, ctypes.c_int]
 SWE_STAGE_NAMES = ("rexi", "legendre", "fft", "grid_products")
 
@@ -601,7 +610,7 @@ class SwePlan:
     lg_irk_lc_n_erk_ver0 "lg_irk_ver0")."""
 
     def __init__(self, T, nlat, nlon, dt, omega, radius, phibar, N, p0, Xc, rexi_precision="fp64",
-                 sh_precision="fp64", scheme="ver1", stream=None):
+                 sh_precision="fp64", scheme="ver1", stream=None, nsub=1, visc=0.0, visc_order=2):
         d = SweDesc()
         d.T, d.nlat, d.nlon, d.dt = int(T), int(nlat), int(nlon), float(dt)
         d.omega, d.radius, d.phibar = float(omega), float(radius), float(phibar)
@@ -610,6 +619,8 @@ class SwePlan:
         d.sh_precision = _SH_PREC[sh_precision] if isinstance(sh_precision, str) else int(sh_precision)
         d.scheme = SWE_SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
         d.stream = ctypes.c_void_p(_stream_handle(stream))
+        d.nsub = int(nsub)
+        d.visc, d.visc_order = float(visc), int(visc_order)
         h = ctypes.c_void_p()
         _check(_lib.swe_plan_create(ctypes.byref(d), ctypes.byref(h)))
         self._h = h

@@ -134,3 +134,24 @@ def test_binding_rejects_wrong_tensors_before_the_call(rexi):
             rexi.step_fp64_static(T, 64, 3600.0, 7.292e-5, 6.37122e6, 9.80616e4, 6.0, 10.0, bad, bad)
     with pytest.raises(ValueError, match="elements"):
         rexi.step_fp64_static(T, 64, 3600.0, 7.292e-5, 6.37122e6, 9.80616e4, 6.0, 10.0, cases[0], good_cpu)
+
+
+def test_swe_substeps_rule(rexi):
+    """Explicit sub-steps of the nonlinear part: the smallest n >= 1 with
+    (tau / n) umax sqrt(T (T+1)) / a <= courant (include/swe.h)."""
+    a = 6.37122e6
+    c = 3600.0 * 40.0 * math.sqrt(511 * 512) / a
+    assert rexi.swe_substeps(511, 3600.0, 40.0, a, 1.0) == math.ceil(c) == 12
+    assert rexi.swe_substeps(511, 3600.0, 40.0, a, 0.5) == math.ceil(2 * c)
+    assert rexi.swe_substeps(127, 900.0, 38.9, a, 1.0) == 1
+    assert rexi.swe_substeps(63, 0.0, 40.0, a, 1.0) == 1
+    # an exact multiple is not rounded up
+    T = 3
+    tau = 2.0 * a / math.sqrt(T * (T + 1.0))
+    assert rexi.swe_substeps(T, tau, 1.0, a, 1.0) in (2, 3)
+    assert rexi.swe_substeps(T, 4.0 * tau, 1.0, a, 8.0) in (1, 2)
+    assert rexi.swe_substeps(1023, 1e9, 1e3, a, 1e-3) == 4096
+    for args in [(0, 1.0, 1.0, a, 1.0), (5, -1.0, 1.0, a, 1.0), (5, 1.0, -1.0, a, 1.0),
+                 (5, 1.0, 1.0, 0.0, 1.0), (5, 1.0, 1.0, a, 0.0)]:
+        with pytest.raises(rexi.RexiError):
+            rexi.swe_substeps(*args)

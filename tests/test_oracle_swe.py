@@ -105,6 +105,120 @@ def test_strang_ver1_second_order():
     assert all(1.7 < r < 2.5 for r in rates), (errs, rates)
 
 
+def _rk4_nonlinear(U, g, tau, n):
+    """n classical RK4 steps of dU/dt = N(U) over tau: an independent reference for the
+    sub-stepped midpoint rule."""
+    h = tau / n
+    for _ in range(n):
+        k1 = swe.nonlinear(U, g)
+        k2 = swe.nonlinear(U + 0.5 * h * k1, g)
+        k3 = swe.nonlinear(U + 0.5 * h * k2, g)
+        k4 = swe.nonlinear(U + h * k3, g)
+        U = U + (h / 6.0) * (k1 + 2 * k2 + 2 * k3 + k4)
+    return U
+
+
+def test_substepped_erk_second_order_in_substep():
+    """N^{tau} by nsub midpoint steps of tau / nsub converges at 2nd order in tau / nsub to the
+    exact nonlinear flow (RK4 with many steps): doubling nsub divides the error by ~4.  A
+    sub-step that used tau instead of tau / nsub, or left the loop after one pass, fails."""
+    T, nlat, nlon = 15, 24, 48
+    g = sht.Grid(T, nlat, nlon, A)
+    U0 = syn.balanced_state(T, 2, urms=40.0)
+    U0[2] = syn.gaussian_state(T, 8, scales=(0, 0, 2e-6))[2]
+    tau = 6 * 3600.0
+    ref = _rk4_nonlinear(U0, g, tau, 96)
+    errs = [float(np.max(rexi.rel_l2(swe.rk2_nonlinear(U0, g, tau, n), ref, T))) for n in (2, 4, 8)]
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(1.8 < r < 2.3 for r in rates), (errs, rates)
+
+
+def test_strang_ver1_substepped_second_order():
+    """l_rexi_n_erk_ver1 with N sub-stepped (nsub = 3 midpoint steps per half step) still
+    converges at 2nd order in dt to a small-step RK4 reference, and its sub-steps make the
+    explicit part closer to the exact N flow than one midpoint step at the largest dt."""
+    T, nlat, nlon = 15, 24, 48
+    g = sht.Grid(T, nlat, nlon, A)
+    U0 = syn.balanced_state(T, 2, urms=40.0)
+    U0[2] = syn.gaussian_state(T, 8, scales=(0, 0, 2e-6))[2]
+    t_end = 4 * 1800.0
+    ref = swe.rk4_full(U0, g, t_end, 240, OM, PB)
+    errs = []
+    for dt in (1800.0, 900.0, 450.0):
+        X = rexi.spectrum_bound(T, dt, OM, A, PB)
+        z, w = coeffs.rexi_coefficients(128, min(6.0, 1.6 * X), 1.6 * X)
+        U = U0
+        for _ in range(int(round(t_end / dt))):
+            U = swe.strang_ver1(U, g, dt, OM, PB, z, w, nsub=3)
+        errs.append(float(np.max(rexi.rel_l2(U, ref, T))))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(1.7 < r < 2.5 for r in rates), (errs, rates)
+    tau = 1800.0
+    exact = _rk4_nonlinear(U0, g, tau, 64)
+    e1 = float(np.max(rexi.rel_l2(swe.rk2_nonlinear(U0, g, tau, 1), exact, T)))
+    e3 = float(np.max(rexi.rel_l2(swe.rk2_nonlinear(U0, g, tau, 3), exact, T)))
+    assert e3 < e1 / 6, (e1, e3)
+
+
+def _grid_laplacian(c, g):
+    """lap f by the grid route: V = grad f from the vector synthesis (psi = 0, chi = f), then
+    the divergence analysis; independent of the spectral eigenvalues -n(n+1)/a^2."""
+    U, V = g.synth_uv(np.zeros_like(c), c)
+    div, _ = g.analys_divcurl(U, V)
+    return div
+
+
+def test_diffusion_generator_is_grid_bilaplacian():
+    """The exact diffusion flow over a short tau moves U by -tau nu lap^2 U to first order:
+    checked against lap applied twice on the Gauss grid (q = 2), and for q = 1 against one
+    grid Laplacian.  n = 0 stays unchanged and no coefficient grows."""
+    T, nlat, nlon = 15, 24, 48
+    g = sht.Grid(T, nlat, nlon, A)
+    U = syn.gaussian_state(T, 41)
+    # central differences over +-tau: the generator to O((tau nu k^4)^2), tau nu k_T^4 ~ 1e-4
+    nu4, tau = 1e15, 3000.0
+    gen = (swe.diffuse(U, T, A, tau, nu4, 2) - swe.diffuse(U, T, A, -tau, nu4, 2)) / (2 * tau)
+    for f in range(3):
+        ref = -nu4 * _grid_laplacian(_grid_laplacian(U[f], g), g)
+        assert np.linalg.norm(gen[f] - ref) < 1e-7 * np.linalg.norm(ref)
+    nu2 = 1e2
+    gen1 = (swe.diffuse(U, T, A, tau, nu2, 1) - swe.diffuse(U, T, A, -tau, nu2, 1)) / (2 * tau)
+    ref1 = nu2 * _grid_laplacian(U[1], g)
+    assert np.linalg.norm(gen1[1] - ref1) < 1e-7 * np.linalg.norm(ref1)
+    big = swe.diffuse(U, T, A, 3600.0, nu4, 2)
+    assert np.all(np.abs(big) <= np.abs(U) + 1e-300)
+    assert np.array_equal(big[:, 0], U[:, 0])
+
+
+def test_strang_ver1_with_diffusion_second_order():
+    """D^{dt/2} o (N^{dt/2} L^{dt} N^{dt/2} with nsub = 2) o D^{dt/2} converges at 2nd order
+    to a small-step RK4 solution of dU/dt = L U + N(U) - nu lap^2 U."""
+    T, nlat, nlon = 15, 24, 48
+    g = sht.Grid(T, nlat, nlon, A)
+    U0 = syn.balanced_state(T, 2, urms=40.0)
+    U0[2] = syn.gaussian_state(T, 8, scales=(0, 0, 2e-6))[2]
+    lam2 = sht.laplacian_eig(T, A) ** 2
+    nu = 0.3 / (3600.0 * (T * (T + 1) / A ** 2) ** 2)   # degree T e-folds in about 3 h
+    t_end = 4 * 1800.0
+    h, U = t_end / 240, U0
+    for _ in range(240):
+        f = lambda V: swe.full_tendency(V, g, OM, PB) - nu * lam2[None, :] * V
+        k1 = f(U); k2 = f(U + 0.5 * h * k1); k3 = f(U + 0.5 * h * k2); k4 = f(U + h * k3)
+        U = U + (h / 6.0) * (k1 + 2 * k2 + 2 * k3 + k4)
+    ref = U
+    errs = []
+    for dt in (1800.0, 900.0, 450.0):
+        X = rexi.spectrum_bound(T, dt, OM, A, PB)
+        z, w = coeffs.rexi_coefficients(128, min(6.0, 1.6 * X), 1.6 * X)
+        U = U0
+        step = lambda V: swe.strang_ver1(V, g, dt, OM, PB, z, w, nsub=2)
+        for _ in range(int(round(t_end / dt))):
+            U = swe.with_diffusion(step, U, T, A, dt, nu)
+        errs.append(float(np.max(rexi.rel_l2(U, ref, T))))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(1.7 < r < 2.5 for r in rates), (errs, rates)
+
+
 # ---- ETD2RK (Sec. 4.3) ------------------------------------------------------------------
 def _psi_weights(N, p0, Xc):
     z, w0 = coeffs.rexi_coefficients(N, p0, Xc, k=0)
