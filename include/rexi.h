@@ -33,6 +33,9 @@ extern "C" {
 #define REXI_EBUSY (-5)    /* resource busy (serving slots / memory budget exhausted)    */
 
 #define REXI_FP64 0   /* every solve and sum in FP64                                         */
+#define REXI_PART_NONE 0   /* the plan computes the whole step                                 */
+#define REXI_PART_POLES 1  /* the plan sums only its rank's share of the poles                 */
+#define REXI_PART_M 2      /* the plan computes only its rank's zonal orders, zeros elsewhere  */
 #define REXI_MIXED 1  /* FP32 solves; poles with large weight refined (double-float residual) */
                       /* and summed in FP64; the others summed in FP32                        */
 
@@ -81,6 +84,18 @@ int rexi_contour_select(double X, int N, double* p0, double* Xc);
 int rexi_select_poles(int precision, int N, const double* z, const double* w, double X, double heavy_tau,
                       double prune_tau, int heavy_align, int* cls, double* pruned_gain);
 
+/*
+ * rexi_partition -- which poles or zonal orders rank `rank` of `size` owns (host only).
+ *   REXI_PART_POLES: owned[n] for the N contour poles n = 0..N-1: the conjugate pair
+ *     {k, N-1-k} (rexi_coeffs places the conjugate of node n at N-1-n; the middle node of an
+ *     odd N is alone) goes to rank k mod size, so that the large-weight poles near both ends of
+ *     the node list spread over the ranks.
+ *   REXI_PART_M: owned[m] for m = 0..T: the orders pair as (m, T-m), chains of total length
+ *     T + 2, and pair min(m, T-m) goes to rank min(m, T-m) mod size.
+ * owned: caller-owned int array (N or T+1 entries), 1 owned, 0 not.  Errors: REXI_EINVAL.
+ */
+int rexi_partition(int mode, int T, int N, int rank, int size, int* owned);
+
 /* X = dt (sqrt(phibar T (T+1)) / radius + 2 omega): bound on |dt lambda| over the spectrum
  * of dt L (gravity-wave frequency of degree T plus the largest Coriolis frequency). */
 double rexi_spectrum_bound(int T, double dt, double omega, double radius, double phibar);
@@ -109,6 +124,15 @@ typedef struct rexi_plan_desc {
                       /* (REXI_MIXED 1e-10, REXI_FP64 none: every pole is solved); < 0: none */
                       /* REXI_MIXED then completes the last 32-pole light group with the    */
                       /* largest pruned poles (pairs whole), so fewer may be left out       */
+  int part_mode;      /* work partition over part_size devices (paper Sec. 5.3-5.4: REXI     */
+  int part_rank;      /* terms spread over MPI ranks, U0 broadcast, the sum reduced):        */
+  int part_size;      /* REXI_PART_NONE (0), REXI_PART_POLES or REXI_PART_M; rexi_partition  */
+                      /* says which poles / orders rank part_rank owns.  POLES: the plan's   */
+                      /* pole set is its share of the N poles, pruned within prune_tau /     */
+                      /* part_size; U1 holds the partial sum over those poles (Phi included). */
+                      /* M: U1 holds the full result on the owned orders and 0 elsewhere.    */
+                      /* Either way the element-wise sum of U1 over the ranks (one all-reduce */
+                      /* of 3 nlm complex128 per state) is the whole step                    */
 } rexi_plan_desc;
 
 /*

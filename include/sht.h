@@ -41,6 +41,11 @@ typedef struct sh_plan_desc {
                     /* analysis, x T+1 degrees for synthesis) must fit in shared memory      */
                     /* (e.g. max_fields <= 4 at T = 1023, nlat = 1536, TF32)                 */
   void* stream;     /* cudaStream_t                                                         */
+  int epilogue_wait_polls;  /* 0 (normal use).  For tests of the timeout path of the tensor-core */
+                    /* precisions: n > 0 makes the GEMM's epilogue give up waiting for an    */
+                    /* accumulator after n non-blocking polls (the copy and MMA roles still  */
+                    /* drain everything they issued); that transform's results are invalid  */
+                    /* and sh_plan_check then returns REXI_ETIMEOUT                          */
 } sh_plan_desc;
 
 /* Builds the Gauss grid (Newton iteration on P_nlat), the orthonormal associated Legendre

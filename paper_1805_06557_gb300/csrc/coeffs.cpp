@@ -103,25 +103,34 @@ extern "C" double rexi_spectrum_bound(int T, double dt, double omega, double rad
 }
 
 // Score of a contour: max over x in [0, X] of |r(ix) - e^{ix}| and of the rounding growth
-// sum_n |w_n| / |z_n - ix| times 2^-53 (conjugate symmetry covers [-X, 0]).
-static double contour_score(int N, double p0, double Xc, double X) {
+// sum_n |w_n| / |z_n - ix| times 2^-53 (conjugate symmetry covers [-X, 0]).  The points go
+// from the band edge x = X inward, where both terms peak, and the evaluation stops once the
+// partial maximum reaches `stop` (the best score so far): such a contour cannot win, so the
+// search's choice is the same as with full evaluations.  The conjugate pairs of the node
+// list are summed together (w/(z - ix) + conj(w)/(conj(z) - ix)).
+static double contour_score(int N, double p0, double Xc, double X, double stop) {
   std::vector<cplx> z, w;
   contour_coeffs(N, p0, Xc, 0, z, w);
-  const int npts = 201;
-  double es = 0, amp = 0;
-  for (int j = 0; j < npts; ++j) {
+  const int npts = 201, half = N / 2;
+  double score = 0;
+  for (int j = npts - 1; j >= 0; --j) {
     const cplx x(0.0, X * j / (npts - 1));
     cplx r = 0.0;
     double a = 0.0;
-    for (int n = 0; n < N; ++n) {
-      const cplx t = w[n] / (z[n] - x);
+    for (int n = 0; n < half; ++n) {
+      const cplx t = w[n] / (z[n] - x), u = w[N - 1 - n] / (z[N - 1 - n] - x);
+      r += t + u;
+      a += std::abs(t) + std::abs(u);
+    }
+    if (N % 2) {
+      const cplx t = w[half] / (z[half] - x);
       r += t;
       a += std::abs(t);
     }
-    es = std::max(es, std::abs(r - std::exp(x)));
-    amp = std::max(amp, a);
+    score = std::max(score, std::max(std::abs(r - std::exp(x)), a * 1.1102230246251565e-16));
+    if (score >= stop) break;
   }
-  return std::max(es, amp * 1.1102230246251565e-16);
+  return score;
 }
 
 extern "C" int rexi_contour_select(double X, int N, double* p0_out, double* Xc_out) {
@@ -134,7 +143,7 @@ extern "C" int rexi_contour_select(double X, int N, double* p0_out, double* Xc_o
     const double Xc = mg * X;
     for (double p : p0s) {
       const double pp = std::min(p, Xc);  // the circle must not pass near the origin
-      const double s = contour_score(N, pp, Xc, X);
+      const double s = contour_score(N, pp, Xc, X, best);
       if (s < best) {
         best = s;
         bp = pp;

@@ -96,7 +96,13 @@ struct Inst {
   long long roff;  // element offset of its right-hand-side pieces [nlm]
   int T, nlm, Q, pole0;  // truncation, coefficients per field, pole ranges, first pole
   double2 S0;      // sum_n w_n / z_n of its pole set
+  int mrank = 0, msize = 0;  // zonal-order partition: with msize > 1 the state owns the orders m
+                             // with m_pair(T, m) % msize == mrank; the others are written as 0
 };
+
+// pair index of zonal order m when the orders are dealt in pairs (m, T - m), which have equal
+// total chain length T + 2
+__host__ __device__ __forceinline__ int m_pair(int T, int m) { return m < T - m ? m : T - m; }
 
 // index of the instance owning global element e: largest i with ecum[i] <= e
 __host__ __device__ __forceinline__ int inst_of(const long long* ecum, int ninst, long long e) {

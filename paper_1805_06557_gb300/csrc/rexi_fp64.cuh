@@ -166,6 +166,13 @@ static __global__ void k_rexi_finalize(const double2* __restrict__ U0, const dou
   const Inst I = insts[i];
   const int nlm = I.nlm, idx = (int)(e - ecum[i]);
   double2 sz = make_double2(0, 0), sd = sz, sw = sz;
+  if (I.msize > 1 && m_pair(I.T, m_of(I.T, idx)) % I.msize != I.mrank) {  // another rank's order
+    double2* o = U1 + I.soff + idx;
+    o[0] = sz;
+    o[nlm] = sz;
+    o[2 * nlm] = sz;
+    return;
+  }
   const double2* p = partial + I.poff + idx;
   if (DF) {
     // double-float slots summed in double-float (two-sum of the high words, low words added),

@@ -54,6 +54,8 @@ struct PoleSet {
   std::vector<cplx> zp, wp; // poles left out (reported by rexi_plan_get_poles)
   std::vector<int> cls;     // per input pole: 1 heavy, 0 light, -1 pruned
   int pole0 = -1;           // position in the device arena (-1: not uploaded)
+  int mrank = 0, msize = 0; // zonal-order partition (msize > 1): only the owned orders get tiles
+  bool owns(int m) const { return msize <= 1 || m_pair(T, m) % msize == mrank; }
 };
 
 // Default pruning threshold of mixed plans: the summed gain of the poles left out is at most
@@ -488,6 +490,8 @@ void build_launch(const Engine& e, const std::vector<InstReq>& req, std::vector<
     I.Q = ql + qh;
     I.pole0 = ps.pole0;
     I.S0 = make_double2(ps.S0.real(), ps.S0.imag());
+    I.mrank = ps.mrank;
+    I.msize = ps.msize;
     insts.push_back(I);
     ecum.push_back(ec);
     auto add = [&](int gbase, int G, int Q, int qbase, int hv, std::vector<Tile>& out) {
@@ -497,6 +501,7 @@ void build_launch(const Engine& e, const std::vector<InstReq>& req, std::vector<
       for (int g = 0; g < G; g += per, ++q) {
         const int ng = std::min(per, G - g);
         for (int m = 0; m <= T; ++m) {
+          if (!ps.owns(m)) continue;
           if (!hv && e.precision != REXI_FP64) {  // light: both chains in one tile (chain = 2)
             out.push_back(Tile{m, 2, gbase + g, ng, q, 0, 2 * (T + 1 - m) * ng, (int)i, -1, -1, -1});
             continue;
@@ -518,7 +523,7 @@ void build_launch(const Engine& e, const std::vector<InstReq>& req, std::vector<
       for (int g = 0; g < Gh; g += per, ++q) {
         const int ng = std::min(per, Gh - g);
         for (int m = 0; m <= T; ++m)
-          for (int c = 0; c < 2; ++c) {
+          for (int c = 0; c < 2 && ps.owns(m); ++c) {
             if (quad)  // g0 = pole offset, ng = 16-pole groups
               heavyQ.push_back(Tile{m, c, 32 * ps.g_light + 16 * g, ng, q, 1, (T + 1 - m) * ng * 6, gr[0], gr[1],
                                     gr[2], gr[3]});
@@ -751,6 +756,10 @@ extern "C" int rexi_plan_create(const rexi_plan_desc* desc, rexi_plan** out) {
   if (d.max_batch < 1) return fail(REXI_EINVAL, "max_batch must be >= 1");
   if ((d.z == nullptr) != (d.w == nullptr)) return fail(REXI_EINVAL, "give both z and w or neither");
   if (!d.z && (!(d.p0 > 0) || !(d.Xc > 0))) return fail(REXI_EINVAL, "need p0 > 0 and Xc > 0");
+  if (d.part_mode != REXI_PART_NONE && d.part_mode != REXI_PART_POLES && d.part_mode != REXI_PART_M)
+    return fail(REXI_EINVAL, "part_mode must be REXI_PART_NONE, REXI_PART_POLES or REXI_PART_M");
+  if (d.part_mode != REXI_PART_NONE && (d.part_size < 1 || d.part_rank < 0 || d.part_rank >= d.part_size))
+    return fail(REXI_EINVAL, "partition rank %d of %d", d.part_rank, d.part_size);
   rexi_plan* p = new rexi_plan();
   p->d = d;
   p->d.z = p->d.w = nullptr;
@@ -763,18 +772,46 @@ extern "C" int rexi_plan_create(const rexi_plan_desc* desc, rexi_plan** out) {
   // batches of four or more run heavy tiles of two state pairs on 16-pole groups
   const int halign = d.max_batch >= 4 ? 16 : 32;
   int rc;
+  std::vector<cplx> z(d.N), w(d.N);
   if (d.z) {
-    std::vector<cplx> z(d.N), w(d.N);
     for (int n = 0; n < d.N; ++n) {
       z[n] = cplx(d.z[2 * n], d.z[2 * n + 1]);
       w[n] = cplx(d.w[2 * n], d.w[2 * n + 1]);
     }
-    rc = make_poleset(p->ps, d.precision, d.T, d.N, d.dt, X, z.data(), w.data(), d.heavy_tau, d.prune_tau, halign);
   } else {
-    rc = make_poleset_from_contour(p->ps, d.precision, d.T, d.N, d.dt, X, d.p0, d.Xc, d.heavy_tau, d.prune_tau,
-                                   halign);
+    std::vector<double> zz(2 * (size_t)d.N), ww(2 * (size_t)d.N);
+    if ((rc = rexi_coeffs(d.N, d.p0, d.Xc, 0, zz.data(), ww.data()))) return bail(rc);
+    for (int n = 0; n < d.N; ++n) {
+      z[n] = cplx(zz[2 * n], zz[2 * n + 1]);
+      w[n] = cplx(ww[2 * n], ww[2 * n + 1]);
+    }
   }
+  double prune_tau = d.prune_tau;
+  if (d.part_mode == REXI_PART_POLES && d.part_size > 1) {
+    // this rank's conjugate pairs; each rank prunes within 1/part_size of the pruning budget, so
+    // the poles left out over all ranks still sum to at most the plan's threshold
+    std::vector<int> own(d.N);
+    rexi_partition(REXI_PART_POLES, d.T, d.N, d.part_rank, d.part_size, own.data());
+    std::vector<cplx> zs, ws;
+    for (int n = 0; n < d.N; ++n)
+      if (own[n]) {
+        zs.push_back(z[n]);
+        ws.push_back(w[n]);
+      }
+    if (zs.empty()) return bail(fail(REXI_EINVAL, "partition rank %d of %d owns no pole of %d", d.part_rank,
+                                     d.part_size, d.N));
+    z.swap(zs);
+    w.swap(ws);
+    p->d.N = (int)z.size();
+    const double base = prune_tau > 0 ? prune_tau : (prune_tau == 0 && d.precision == REXI_MIXED ? 1e-10 : -1.0);
+    prune_tau = base > 0 ? base / d.part_size : base;
+  }
+  rc = make_poleset(p->ps, d.precision, d.T, p->d.N, d.dt, X, z.data(), w.data(), d.heavy_tau, prune_tau, halign);
   if (rc) return bail(rc);
+  if (d.part_mode == REXI_PART_M && d.part_size > 1) {
+    p->ps.mrank = d.part_rank;
+    p->ps.msize = d.part_size;
+  }
   rc = engine_init(p->e, d.precision, d.T, d.omega, d.radius, d.phibar, (cudaStream_t)d.stream, p->ps.Npad, 0,
                    (size_t)p->nlm * d.max_batch);
   if (rc) return bail(rc);
@@ -943,6 +980,20 @@ extern "C" int rexi_plan_get_poles(const rexi_plan* p, double* z, double* w, int
       w[2 * k + 1] = p->ps.wp[i].imag();
     }
     if (heavy) heavy[k] = -1;
+  }
+  return REXI_OK;
+}
+
+extern "C" int rexi_partition(int mode, int T, int N, int rank, int size, int* owned) {
+  if (!owned || size < 1 || rank < 0 || rank >= size || T < 1 || N < 1)
+    return fail(REXI_EINVAL, "rexi_partition: bad arguments");
+  if (mode == REXI_PART_POLES) {
+    // conjugate pair k = {k, N - 1 - k} (the middle pole of an odd N alone), dealt round robin
+    for (int n = 0; n < N; ++n) owned[n] = std::min(n, N - 1 - n) % size == rank;
+  } else if (mode == REXI_PART_M) {
+    for (int m = 0; m <= T; ++m) owned[m] = m_pair(T, m) % size == rank;
+  } else {
+    return fail(REXI_EINVAL, "rexi_partition: mode must be REXI_PART_POLES or REXI_PART_M");
   }
   return REXI_OK;
 }

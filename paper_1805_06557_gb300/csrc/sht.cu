@@ -633,6 +633,7 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
     return fail(REXI_EINVAL, "sh_plan_create: nlat must be even and > T (got %d)", d.nlat);
   if (d.nlon <= 2 * d.T) return fail(REXI_EINVAL, "sh_plan_create: nlon must exceed 2T");
   if (!(d.radius > 0) || d.max_fields < 1) return fail(REXI_EINVAL, "sh_plan_create: radius > 0, max_fields >= 1");
+  if (d.epilogue_wait_polls < 0) return fail(REXI_EINVAL, "sh_plan_create: epilogue_wait_polls < 0");
   if (d.precision != SH_FP64 && d.precision != SH_TF32 && d.precision != SH_BF16 && d.precision != SH_TF32X3)
     return fail(REXI_EINVAL, "sh_plan_create: unknown precision %d", d.precision);
   sh_plan* p = new sh_plan();
@@ -689,6 +690,7 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
                                 d.precision, p->stream);
     if (rc) return bail(rc);
     tc_legendre_set_prof(p->tc, &p->prof);
+    tc_legendre_set_epilogue_polls(p->tc, d.epilogue_wait_polls);
   }
   if ((e = cudaStreamSynchronize(p->stream))) return bail(cuda_fail(e, "sh_plan_create: table kernel"));
   *out = p;

@@ -88,6 +88,8 @@ struct GemmArgs {
   int nj_max;       // jobs per CTA at most (their descriptors are staged in shared memory)
   uint32_t bslot;   // bytes of one B buffer
   uint32_t blo;     // PM_TF32X3: byte offset of the lo copy of B in its buffer (else 0)
+  uint32_t epi_polls;  // 0: the epilogue waits for its accumulators with the normal bound; n > 0:
+                       // it gives up after n non-blocking polls (a test of the timeout path)
   int* err;
 };
 
@@ -474,8 +476,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
     for (int i = 0; i + step <= nj; i += step) {
       const Job jb = sjobs[i];
       const int acc0 = i % njb, acc1 = (i + 1) % njb;
-      bool ok = tc::mbar_wait(tfull0 + 8 * acc0, (i / njb) & 1);
-      if (ok && g.pair) ok = tc::mbar_wait(tfull0 + 8 * acc1, ((i + 1) / njb) & 1);
+      auto wait_acc = [&](int acc, uint32_t parity) {
+        if (!g.epi_polls) return tc::mbar_wait(tfull0 + 8 * acc, parity);
+        for (uint32_t it = 0; it < g.epi_polls; ++it)
+          if (tc::mbar_test(tfull0 + 8 * acc, parity)) return true;
+        return false;
+      };
+      bool ok = wait_acc(acc0, (i / njb) & 1);
+      if (ok && g.pair) ok = wait_acc(acc1, ((i + 1) / njb) & 1);
       if (!ok) {
         if (lane == 0) atomicExch(g.err, 2);
         break;
@@ -587,6 +595,7 @@ struct Sched {
 struct TcLegendre {
   int T = 0, nlat = 0, nh = 0, nlm = 0, max_fields = 0, bf16 = 0, E = 4, eb = 4, KC = 32;
   int pm = PM_TF32, KCK = 64;  // precision mode; K covered by one chunk (KC, or KC / 2 split)
+  uint32_t epi_polls = 0;      // see GemmArgs::epi_polls
   int ntile_s = 0, kpad_a = 0;
   unsigned char *tabPs = nullptr, *tabHs = nullptr, *tabPa = nullptr, *tabHa = nullptr;
   int* err = nullptr;
@@ -852,6 +861,7 @@ static int gemm(TcLegendre* t, bool synth, bool vector, int nf, const double2* i
   g.stages = (int)std::min<size_t>(TC_MAXSTAGES, (TC_SMEM_BUDGET - fixed(g.nb)) / chunk);
   g.bslot = (uint32_t)bslot;
   g.blo = t->pm == PM_TF32X3 ? (uint32_t)bcopy : 0u;
+  g.epi_polls = t->epi_polls;
   const size_t smem =
       (size_t)g.stages * chunk + g.nb * bslot + 8 * (2 * g.stages + 2 * g.nb + 2 * TC_NJB + 2) + jobs_bytes;
   {
@@ -885,6 +895,10 @@ int tc_leg_anal_divcurl(TcLegendre* t, const double2* FA, const double2* FB, dou
 
 void tc_legendre_set_prof(TcLegendre* t, StageProf* prof) {
   if (t) t->prof = prof;
+}
+
+void tc_legendre_set_epilogue_polls(TcLegendre* t, int polls) {
+  if (t) t->epi_polls = polls > 0 ? (uint32_t)polls : 0u;
 }
 
 int tc_legendre_error(TcLegendre* t, int* flag) {

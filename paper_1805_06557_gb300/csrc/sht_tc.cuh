@@ -72,6 +72,8 @@ struct StageProf {
 struct TcLegendre;
 // stage timer of the owning plan (may be null)
 void tc_legendre_set_prof(TcLegendre* t, StageProf* prof);
+// test of the timeout path: the epilogue gives up after `polls` non-blocking polls (0: normal)
+void tc_legendre_set_epilogue_polls(TcLegendre* t, int polls);
 
 // mode: SH_TF32, SH_BF16 or SH_TF32X3
 int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const double* w,

@@ -20,6 +20,8 @@ _lib = ctypes.CDLL(LIB_PATH)
 REXI_OK, REXI_EINVAL, REXI_ENOMEM, REXI_ECUDA, REXI_ETIMEOUT, REXI_EBUSY = 0, -1, -2, -3, -4, -5
 REXI_FP64, REXI_MIXED = 0, 1
 _PREC = {"fp64": REXI_FP64, "mixed": REXI_MIXED}
+REXI_PART_NONE, REXI_PART_POLES, REXI_PART_M = 0, 1, 2
+_PART = {None: REXI_PART_NONE, "none": REXI_PART_NONE, "poles": REXI_PART_POLES, "m": REXI_PART_M}
 
 
 class RexiError(RuntimeError):
@@ -44,7 +46,8 @@ class PlanDesc(ctypes.Structure):
                 ("phibar", ctypes.c_double), ("p0", ctypes.c_double), ("Xc", ctypes.c_double),
                 ("z", _dp), ("w", _dp), ("precision", ctypes.c_int),
                 ("heavy_tau", ctypes.c_double), ("max_batch", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("prune_tau", ctypes.c_double)]
+                ("stream", ctypes.c_void_p), ("prune_tau", ctypes.c_double),
+                ("part_mode", ctypes.c_int), ("part_rank", ctypes.c_int), ("part_size", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -72,6 +75,27 @@ _lib.rexi_sync.argtypes = [ctypes.c_void_p]
 _lib.rexi_plan_get_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(PlanInfo)]
 _lib.rexi_plan_get_poles.argtypes = [ctypes.c_void_p, _dp, _dp, _ip]
 _lib.rexi_alu_peaks.argtypes = [_dp, _dp]
+_lib.rexi_partition.argtypes = [ctypes.c_int] * 5 + [_ip]
+
+
+def partition(mode, T, N, rank, size):
+    """Which poles (mode "poles": N entries) or zonal orders (mode "m": T + 1 entries) rank
+    `rank` of `size` owns, as a boolean array (include/rexi.h rexi_partition)."""
+    n = int(N) if mode == "poles" else int(T) + 1
+    own = np.zeros(n, dtype=np.int32)
+    _check(_lib.rexi_partition(_PART[mode], int(T), int(N), int(rank), int(size), own.ctypes.data_as(_ip)))
+    return own.astype(bool)
+
+
+def step_allreduce(plan, U0, U1, group=None):
+    """One step of a partitioned plan on every rank, completed by a sum all-reduce of U1 over the
+    ranks of `group` (torch.distributed; NCCL on GPUs): each rank's U1 holds its share (a partial
+    pole sum, or its zonal orders and zeros), and the sum is the whole step."""
+    import torch
+    import torch.distributed as dist
+    plan.step(U0, U1)
+    dist.all_reduce(torch.view_as_real(U1), op=dist.ReduceOp.SUM, group=group)
+    return U1
 _lib.rexi_plan_set_profiling.argtypes = [ctypes.c_void_p, ctypes.c_int]
 _lib.rexi_plan_get_profile.argtypes = [ctypes.c_void_p, _dp, _ip, ctypes.c_int]
 _lib.rexi_step_fp64_static.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 6 + \
@@ -302,7 +326,10 @@ class Plan:
     """REXI plan: U1 = sum_n w_n (z_n - dt L)^-1 U0 for batches of spectral states."""
 
     def __init__(self, T, N, dt, omega, radius, phibar, p0=None, Xc=None, z=None, w=None,
-                 precision="fp64", heavy_tau=-1.0, max_batch=1, stream=None, prune_tau=0.0):
+                 precision="fp64", heavy_tau=-1.0, max_batch=1, stream=None, prune_tau=0.0,
+                 partition=None):
+        """partition: None, or (mode, rank, size) with mode "poles" or "m": this plan computes
+        rank's share of the step (include/rexi.h part_mode); step_allreduce completes it."""
         d = PlanDesc()
         d.T, d.N, d.dt = int(T), int(N), float(dt)
         d.omega, d.radius, d.phibar = float(omega), float(radius), float(phibar)
@@ -320,6 +347,9 @@ class Plan:
         d.max_batch = int(max_batch)
         d.stream = ctypes.c_void_p(_stream_handle(stream))
         d.prune_tau = float(prune_tau)
+        if partition is not None:
+            mode, rank, size = partition
+            d.part_mode, d.part_rank, d.part_size = _PART[mode], int(rank), int(size)
         h = ctypes.c_void_p()
         _check(_lib.rexi_plan_create(ctypes.byref(d), ctypes.byref(h)))
         self._h = h
@@ -476,7 +506,8 @@ _SH_PREC = {"fp64": SH_FP64, "tf32": SH_TF32, "bf16": SH_BF16, "tf32x3": SH_TF32
 class ShDesc(ctypes.Structure):
     _fields_ = [("T", ctypes.c_int), ("nlat", ctypes.c_int), ("nlon", ctypes.c_int),
                 ("radius", ctypes.c_double), ("precision", ctypes.c_int),
-                ("max_fields", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("max_fields", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("epilogue_wait_polls", ctypes.c_int)]
 
 
 _lib.sh_plan_create.argtypes = [ctypes.POINTER(ShDesc), ctypes.POINTER(ctypes.c_void_p)]
@@ -499,12 +530,14 @@ def _ptr(t):
 class ShPlan:
     """Spherical-harmonic transforms on a Gauss grid (nlat x nlon), truncation T."""
 
-    def __init__(self, T, nlat, nlon, radius, precision="fp64", max_fields=1, stream=None):
+    def __init__(self, T, nlat, nlon, radius, precision="fp64", max_fields=1, stream=None,
+                 epilogue_wait_polls=0):
         d = ShDesc()
         d.T, d.nlat, d.nlon, d.radius = int(T), int(nlat), int(nlon), float(radius)
         d.precision = _SH_PREC[precision] if isinstance(precision, str) else int(precision)
         d.max_fields = int(max_fields)
         d.stream = ctypes.c_void_p(_stream_handle(stream))
+        d.epilogue_wait_polls = int(epilogue_wait_polls)
         h = ctypes.c_void_p()
         _check(_lib.sh_plan_create(ctypes.byref(d), ctypes.byref(h)))
         self._h = h

@@ -23,11 +23,24 @@ from . import rexi
 OK, REJECTED = "ok", "rejected"
 
 
-def contour(T, dt, omega, radius, phibar):
+_CONTOURS = {}  # (N, quantised X) -> (p0, Xc) from the library's contour search
+
+
+def contour(T, dt, omega, radius, phibar, N=None):
     """Default contour for a request: the covered half-width X of dt L, then (p0, Xc) with
-    p0 <= Xc (Xc = 1.6 X below X = 20, else p0 = 14, Xc = 1.4 X)."""
+    p0 <= Xc.  Below X = 20: Xc = 1.6 X, p0 = min(6, 1.6 X).  From X = 20 on, a fixed p0 fails:
+    with p0 = 14 and 2048 poles the scalar REXI error is 2e5 at X = 182, so the contour comes from
+    rexi_contour_select for the request's pole count, evaluated at X rounded up to a 5 % grid
+    (X_q >= X covers the request's spectrum) and memoised, so that a stream of requests with
+    continuous time steps costs a few hundred searches at most."""
     X = rexi.spectrum_bound(T, dt, omega, radius, phibar)
-    return (min(6.0, 1.6 * X), 1.6 * X) if X < 20 else (14.0, 1.4 * X)
+    if X < 20 or N is None:
+        return (min(6.0, 1.6 * X), 1.6 * X) if X < 20 else (14.0, 1.4 * X)
+    q = math.ceil(math.log(X / 20.0) / math.log(1.05))
+    key = (int(N), q)
+    if key not in _CONTOURS:
+        _CONTOURS[key] = rexi.contour_select(20.0 * 1.05 ** q, int(N))
+    return _CONTOURS[key]
 
 
 class Request:
@@ -136,7 +149,7 @@ class ServingEngine:
             self.done.append(r)
             return r
         if r.p0 is None:
-            r.p0, r.Xc = contour(r.T, r.dt, self.omega, self.radius, self.phibar)
+            r.p0, r.Xc = contour(r.T, r.dt, self.omega, self.radius, self.phibar, r.N)
         self.queue.append(r)
         return r
 
@@ -252,7 +265,7 @@ def one_at_a_time(requests, precision="fp64", Tmax=511, clock=time.perf_counter)
         while clock() < arrival:
             time.sleep(max(0.0, min(0.01, arrival - clock())))
         if r.p0 is None:
-            r.p0, r.Xc = contour(r.T, r.dt, syn.OMEGA, syn.RADIUS, syn.PHIBAR)
+            r.p0, r.Xc = contour(r.T, r.dt, syn.OMEGA, syn.RADIUS, syn.PHIBAR, r.N)
         n = 3 * r.nlm
         U0[:n].copy_(torch.from_numpy(r.state.reshape(-1)))
         plan.set([(r.T, r.N, r.dt, r.p0, r.Xc, 0)])

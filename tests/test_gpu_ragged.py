@@ -115,3 +115,34 @@ def test_ragged_errors(env):
         r.set([(31, 64, 3600.0, 6.0, 10.0)] * 3)      # more than max_inst
     assert e.value.code == rexi.REXI_EBUSY
     r.close()
+
+
+INST_LARGE = [(127, 512, 3600.0)] * 4 + [(255, 512, 3600.0)] * 2 + [(63, 256, 3600.0), (191, 512, 1800.0),
+                                                                      (255, 512, 2400.0)]
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", None), ("mixed", 1e-8)])
+def test_ragged_config_sizes_sampled(env, prec, tol):
+    """Ensemble sizes (T63-T255, 256-512 poles) in one ragged launch, with four instances of one
+    pole set (heavy tiles of two state pairs) and two of another (a lone pair), against the
+    oracle on sampled zonal orders; the launch configuration of the ensemble benchmark."""
+    torch, rexi = env
+    r, off, states, u0, u1 = _run(env, prec, INST_LARGE)
+    out = u1.cpu().numpy()
+    for i in (0, 3, 4, 5, 6, 7, 8):
+        t, n, dt = INST_LARGE[i]
+        p0, Xc = contour(t, dt)
+        z, w = oc.rexi_coefficients(n, p0, Xc)
+        ms = [0, 1, t // 2, t]
+        ref = orx.rexi_step(states[i], t, dt, OM, A, PB, z, w, m_list=ms)
+        got = out[off[i]: off[i + 1]].reshape(3, -1)
+        mask = np.zeros(got.shape[-1], bool)
+        for m in ms:
+            o = m * (2 * t + 3 - m) // 2
+            mask[o: o + t + 1 - m] = True
+        wgt = np.where(np.arange(mask.size) <= t, 1.0, 2.0)[mask]
+        num = np.sqrt(np.sum(wgt * np.abs(got[:, mask] - ref[:, mask]) ** 2, axis=-1))
+        den = np.sqrt(np.sum(wgt * np.abs(ref[:, mask]) ** 2, axis=-1))
+        bound = tol if tol else max(1e-11, 8 * oc.amplification(z, w, orx.spectrum_bound(t, dt, OM, A, PB)) * 2.0 ** -53)
+        assert np.all(num / den < bound), (i, num / den, bound)
+    r.close()

@@ -332,3 +332,41 @@ def test_mixed_heavy_classification_and_pruning(env):
     fp = rexi.Plan(T, N, dt, OM, A, PB, p0=p0, Xc=Xc, precision="fp64")
     assert fp.info()["n_pruned"] == 0          # FP64 plans solve every pole by default
     fp.close()
+
+
+_PART_REF = []  # the oracle's whole steps of the four states below, computed once
+
+
+@pytest.mark.parametrize("mode", ["poles", "m"])
+@pytest.mark.parametrize("prec,size", [("fp64", 2), ("fp64", 3), ("mixed", 2), ("mixed", 3)])
+def test_partitioned_plans_sum_to_the_whole_step(env, mode, prec, size):
+    """The multi-GPU partition of one step (paper Sec. 5.3-5.4), run rank by rank on one GPU:
+    the sum of the ranks' outputs (what the all-reduce forms) equals the oracle's whole step
+    within the precision's tolerance, every rank of the m partition writes exact zeros on the
+    orders it does not own, and a batch of 4 (heavy tiles of state pairs) works the same."""
+    torch, rexi = env
+    T, N, dt, B = 63, 256, 3600.0, 4
+    p0, Xc, X = contour(T, dt, N)
+    z, w = oc.rexi_coefficients(N, p0, Xc)
+    U0 = np.stack([syn.gaussian_state(T, 60 + b) for b in range(B)])
+    if not _PART_REF:
+        _PART_REF.extend(orx.rexi_step(U0[b], T, dt, OM, A, PB, z, w) for b in range(B))
+    u0 = torch.from_numpy(U0).cuda()
+    total = torch.zeros_like(u0)
+    for r in range(size):
+        plan = rexi.Plan(T, N, dt, OM, A, PB, p0=p0, Xc=Xc, precision=prec, max_batch=B,
+                         partition=(mode, r, size))
+        u1 = torch.full_like(u0, float("nan"))
+        plan.step(u0, u1)
+        plan.sync()
+        if mode == "m":
+            own = rexi.partition("m", T, N, r, size)
+            mask = torch.from_numpy(np.concatenate([np.full(T + 1 - m, own[m]) for m in range(T + 1)])).cuda()
+            assert bool((u1[..., ~mask] == 0).all())
+        total += u1
+        plan.close()
+    tot = total.cpu().numpy()
+    for b in range(B):
+        err = orx.rel_l2(tot[b], _PART_REF[b], T)
+        tol = fp64_tol(z, w, X) if prec == "fp64" else 1e-8
+        assert np.all(err < tol), (b, err, tol)

@@ -33,9 +33,9 @@ def _requests(serving, arrivals=None):
 
 
 def _alone(rexi, serving, r, precision="mixed"):
+    """The request stepped alone by a uniform plan on the contour the engine chose for it."""
     import torch
-    p0, Xc = serving.contour(r.T, r.dt, syn.OMEGA, syn.RADIUS, syn.PHIBAR)
-    plan = rexi.Plan(r.T, r.N, r.dt, syn.OMEGA, syn.RADIUS, syn.PHIBAR, p0=p0, Xc=Xc, precision=precision)
+    plan = rexi.Plan(r.T, r.N, r.dt, syn.OMEGA, syn.RADIUS, syn.PHIBAR, p0=r.p0, Xc=r.Xc, precision=precision)
     a = torch.from_numpy(r.state).cuda().reshape(1, 3, -1).contiguous()
     b = torch.empty_like(a)
     plan.step(a, b)
@@ -90,4 +90,38 @@ def test_memory_budget_admission(env):
     for r in eng.done:
         if r.rid < len(SPEC):
             assert np.all(orx.rel_l2(r.result, _alone(rexi, serving, r), r.T) < 1e-9)
+    eng.close()
+
+
+SPEC_LARGE = [(255, 3600.0, 512), (511, 1800.0, 1024), (127, 1800.0, 512), (300, 2400.0, 512),
+              (63, 3600.0, 256), (255, 3600.0, 512), (400, 1200.0, 1024)]
+
+
+def test_alone_equals_in_mix_up_to_T511(env):
+    """The serving sizes (Tmax = 511): requests of T63-T511, two of them identical in
+    (T, dt, N) so that the ragged launch pairs their heavy tiles; each result equals the request
+    stepped alone within the mixed-precision bound of 1e-8, and the T255 request matches the
+    oracle on sampled zonal orders."""
+    torch, rexi, serving = env
+    from oracle import coeffs as oc
+    eng = serving.ServingEngine(Tmax=511, max_slots=16, hbm_bytes=1 << 30, max_poles=1 << 15)
+    reqs = [serving.Request(k, 1e-3 * k, T, dt, N, syn.gaussian_state(T, 900 + k))
+            for k, (T, dt, N) in enumerate(SPEC_LARGE)]
+    stats = eng.run(reqs)
+    assert stats["completed"] == len(SPEC_LARGE) and stats["rejected"] == 0
+    for r in eng.done:
+        err = orx.rel_l2(r.result, _alone(rexi, serving, r), r.T)
+        assert np.all(err < 1e-8), (r.rid, r.T, err)
+    r0 = [r for r in eng.done if r.rid == 0][0]
+    z, w = oc.rexi_coefficients(r0.N, r0.p0, r0.Xc)
+    ms = [0, 1, 128, 255]
+    ref = orx.rexi_step(r0.state, r0.T, r0.dt, syn.OMEGA, syn.RADIUS, syn.PHIBAR, z, w, m_list=ms)
+    mask = np.zeros(r0.result.shape[-1], bool)
+    for m in ms:
+        o = m * (2 * r0.T + 3 - m) // 2
+        mask[o: o + r0.T + 1 - m] = True
+    wgt = np.where(np.arange(mask.size) <= r0.T, 1.0, 2.0)[mask]
+    num = np.sqrt(np.sum(wgt * np.abs(r0.result[:, mask] - ref[:, mask]) ** 2, axis=-1))
+    den = np.sqrt(np.sum(wgt * np.abs(ref[:, mask]) ** 2, axis=-1))
+    assert np.all(num / den < 1e-8), num / den
     eng.close()

@@ -155,3 +155,30 @@ def test_tc_field_counts_vector(env, prec, nf):
                 _rel(dv.cpu().numpy()[f], do), _rel(cu.cpu().numpy()[f], co)]
         assert max(errs) < BOUND[prec], (f, errs)
     p.close()
+
+
+@pytest.mark.parametrize("prec", ["tf32", "tf32x3"])
+def test_tc_gemm_timeout_path_reports_etimeout(env, prec):
+    """The bounded-wait error path of the tensor-core GEMM, run for real: a plan whose epilogue
+    gives up after one non-blocking poll of its accumulator barrier (the MMAs cannot have
+    completed by then: the B operand and the first A chunk are still in flight) records the
+    error, the kernel still ends (copies and MMAs drain with their full bounds; with one job
+    per CTA the MMA warp never waits for the epilogue), sh_plan_check reports REXI_ETIMEOUT,
+    and a following plan of the same precision transforms correctly."""
+    torch, rexi = env
+    T, nlat, nlon, nf = 15, 24, 48, 1
+    c = _spec(T, 7, nf)
+    cs = torch.from_numpy(c).cuda()
+    g = torch.empty(nf, nlat, nlon, dtype=torch.float64, device="cuda")
+    bad = rexi.ShPlan(T, nlat, nlon, A, prec, max_fields=nf, epilogue_wait_polls=1)
+    bad.synthesis(cs, g, nf)
+    with pytest.raises(rexi.RexiError) as e:
+        bad.check()
+    assert e.value.code == rexi.REXI_ETIMEOUT
+    bad.close()
+    good = rexi.ShPlan(T, nlat, nlon, A, prec, max_fields=nf)
+    good.synthesis(cs, g, nf)
+    good.check()
+    og = osht.Grid(T, nlat, nlon, A)
+    assert _rel(g.cpu().numpy()[0], og.synth(c[0])) < BOUND[prec]
+    good.close()

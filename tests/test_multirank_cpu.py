@@ -94,3 +94,86 @@ def test_ref_step_m_within_truncation():
     for t in (1, 2, 15, 63, 255, 511):
         ms = bench.ref_step_m(t)
         assert ms[0] == 0 and all(0 <= m <= t for m in ms)
+
+
+# ---- the pole / zonal-order partition of one step (paper Sec. 5.3-5.4) -------------------------
+TP, NP = 15, 64
+
+
+def _partition_rank(rank, world, port, mode, q):
+    """One rank of a partitioned step: its share by the library's host partition rule, computed
+    by the oracle, completed by a sum all-reduce over gloo (the step that NCCL does on GPUs)."""
+    import torch
+    import torch.distributed as dist
+    from paper_1805_06557_gb300 import rexi
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    X = orx.spectrum_bound(TP, DT, syn.OMEGA, syn.RADIUS, syn.PHIBAR)
+    p0, Xc = bench.contour(X)
+    z, w = oc.rexi_coefficients(NP, p0, Xc)
+    U0 = syn.gaussian_state(TP, 11)
+    own = rexi.partition(mode, TP, NP, rank, world)
+    if mode == "poles":       # this rank's REXI terms: the sum over its poles only
+        part = orx.rexi_step(U0, TP, DT, syn.OMEGA, syn.RADIUS, syn.PHIBAR, z[own], w[own])
+    else:                     # this rank's zonal orders (the operator is block diagonal in m)
+        mask = np.concatenate([np.full(TP + 1 - m, own[m]) for m in range(TP + 1)])
+        part = orx.rexi_step(U0 * mask[None, :], TP, DT, syn.OMEGA, syn.RADIUS, syn.PHIBAR, z, w)
+    t = torch.from_numpy(np.ascontiguousarray(part))
+    dist.all_reduce(torch.view_as_real(t), op=dist.ReduceOp.SUM)
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((rank, own.tolist(), t.numpy().tolist()))
+
+
+@pytest.mark.parametrize("mode", ["poles", "m"])
+def test_two_ranks_partitioned_step_equals_whole_step(mode):
+    """World size 2: every pole (conjugate pairs together) or zonal order is owned by exactly
+    one rank, and the all-reduced sum of the ranks' shares equals the one-process step within
+    FP64 summation-order rounding."""
+    pytest.importorskip("torch")
+    import __graft_entry__ as g
+    g.build()
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_partition_rank, args=(r, 2, port, mode, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=240) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    owns = np.array([r[1] for r in res])
+    assert np.all(owns.sum(axis=0) == 1)                          # each unit on exactly one rank
+    if mode == "poles":
+        assert np.array_equal(owns[0], owns[0][::-1])             # conjugate pairs {k, N-1-k} whole
+    else:
+        cost = [sum(TP + 1 - m for m in range(TP + 1) if o[m]) for o in owns]
+        assert abs(cost[0] - cost[1]) <= TP + 2                   # paired orders balance the chains
+    X = orx.spectrum_bound(TP, DT, syn.OMEGA, syn.RADIUS, syn.PHIBAR)
+    p0, Xc = bench.contour(X)
+    z, w = oc.rexi_coefficients(NP, p0, Xc)
+    whole = orx.rexi_step(syn.gaussian_state(TP, 11), TP, DT, syn.OMEGA, syn.RADIUS, syn.PHIBAR, z, w)
+    for r in res:
+        got = np.array(r[2])
+        assert np.all(orx.rel_l2(got, whole, TP) < 1e-12)
+
+
+def test_partition_rule_host():
+    """rexi_partition: ownership is a partition for any world size; the large-weight poles (both
+    ends of the node list) spread over the ranks; errors for bad arguments."""
+    import __graft_entry__ as g
+    g.build()
+    from paper_1805_06557_gb300 import rexi
+    for size in (1, 2, 3, 5):
+        P = np.array([rexi.partition("poles", 255, 513, r, size) for r in range(size)])
+        M = np.array([rexi.partition("m", 255, 513, r, size) for r in range(size)])
+        assert np.all(P.sum(0) == 1) and np.all(M.sum(0) == 1)
+        for r in range(size):
+            assert np.array_equal(P[r], P[r][::-1])
+        if size > 1:
+            ends = P[:, :8].sum(1)                               # the 8 largest-weight nodes
+            assert ends.max() - ends.min() <= 2
+    with pytest.raises(rexi.RexiError):
+        rexi.partition("poles", 15, 16, 2, 2)
