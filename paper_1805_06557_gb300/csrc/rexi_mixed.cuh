@@ -355,29 +355,63 @@ __device__ __forceinline__ HeavyRow heavy_row(const MixedArgs& a, const PoleDF& 
   return R;
 }
 
-// residual of one state's chain row k in double-float:  r_k - d_k x_k - lo_k x_{k-1} - up_k x_{k+1}
+// Compensated dot product (Ogita, Rump & Oishi's Dot2): the running sum s is kept in FP32 and
+// every rounding error -- of each product (TwoProduct by FMA) and of each addition (Knuth's
+// TwoSum) -- together with the low words of double-float operands is gathered in one FP32 word
+// err, so that s + err is as accurate as a sum formed in twice the working precision.
+struct dot2 {
+  float s, err;
+};
+// acc += (a_hi + a_lo) * b, b in FP32
+__device__ __forceinline__ void dot2_add(dot2& acc, df a, float b) {
+  const float p = a.hi * b;
+  const float ep = fmaf(a.hi, b, -p);
+  const df t = df_two_sum(acc.s, p);
+  acc.s = t.hi;
+  acc.err = fmaf(a.lo, b, acc.err + (ep + t.lo));
+}
+// acc += (a_hi + a_lo) * (b_hi + b_lo)
+__device__ __forceinline__ void dot2_add2(dot2& acc, df a, df b) {
+  const float p = a.hi * b.hi;
+  const float ep = fmaf(a.hi, b.hi, -p);
+  const df t = df_two_sum(acc.s, p);
+  acc.s = t.hi;
+  acc.err = fmaf(a.lo, b.hi, fmaf(a.hi, b.lo, acc.err + (ep + t.lo)));
+}
+
+// residual of one state's chain row k:  r_k - d_k x_k - lo_k x_{k-1} - up_k x_{k+1}, each
+// component one compensated dot product of the double-float row and right-hand side with the
+// FP32 solution; delta rows add q bPhi / z (double-float times double-float) to the right-hand
+// side inside the same sum
 __device__ __forceinline__ float2 heavy_residual(const HeavyRow& R, const PoleDF& pq, const RhsDF& rr, bool isZ,
                                                  bool has_m, bool has_p, float2 xm, float2 x0, float2 xp) {
-  dfc r;
+  dot2 re, im;
   if (isZ) {
-    r = dfc_of(rr.bz);
+    re = dot2{rr.bz.x, rr.bz.y};
+    im = dot2{rr.bz.z, rr.bz.w};
   } else {
-    const dfc t = dfc_mul(dfc_of(pq.iz), dfc_of(rr.qbp));
-    const dfc bd = dfc_of(rr.bd);
-    r = dfc{df_add(bd.re, t.re), df_add(bd.im, t.im)};
+    re = dot2{rr.bd.x, rr.bd.y};
+    im = dot2{rr.bd.z, rr.bd.w};
+    const df izr{pq.iz.x, pq.iz.y}, izi{pq.iz.z, pq.iz.w}, qr{rr.qbp.x, rr.qbp.y}, qi{rr.qbp.z, rr.qbp.w};
+    dot2_add2(re, izr, qr);
+    dot2_add2(re, df_neg(izi), qi);
+    dot2_add2(im, izr, qi);
+    dot2_add2(im, izi, qr);
   }
-  // acc = r - d x
-  df re = df_add(r.re, df_neg(df_add(df_mulf(R.d.re, x0.x), df_neg(df_mulf(R.d.im, x0.y)))));
-  df im = df_add(r.im, df_neg(df_add(df_mulf(R.d.re, x0.y), df_mulf(R.d.im, x0.x))));
+  // - d x0 = -(d.re x0.re - d.im x0.im) - i (d.re x0.im + d.im x0.re)
+  dot2_add(re, R.d.re, -x0.x);
+  dot2_add(re, R.d.im, x0.y);
+  dot2_add(im, R.d.re, -x0.y);
+  dot2_add(im, R.d.im, -x0.x);
   if (has_m) {
-    re = df_add(re, df_neg(df_mulf(R.lo, xm.x)));
-    im = df_add(im, df_neg(df_mulf(R.lo, xm.y)));
+    dot2_add(re, R.lo, -xm.x);
+    dot2_add(im, R.lo, -xm.y);
   }
   if (has_p) {
-    re = df_add(re, df_neg(df_mulf(R.up, xp.x)));
-    im = df_add(im, df_neg(df_mulf(R.up, xp.y)));
+    dot2_add(re, R.up, -xp.x);
+    dot2_add(im, R.up, -xp.y);
   }
-  return make_float2(re.hi + re.lo, im.hi + im.lo);
+  return make_float2(re.s + re.err, im.s + im.err);
 }
 
 // FP32 pivot recurrence of a chain at element k: returns the inverse pivot 1/(d_k - lo_k ct_{k-1})
