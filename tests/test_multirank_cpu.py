@@ -90,10 +90,15 @@ def test_reference_arm_under_torchrun_rank0_only():
     assert d["e2e"]["h2d_bytes_per_step"] == 0
 
 
-def test_ref_step_m_within_truncation():
-    for t in (1, 2, 15, 63, 255, 511):
-        ms = bench.ref_step_m(t)
-        assert ms[0] == 0 and all(0 <= m <= t for m in ms)
+def test_reference_arm_orders_cover_the_step():
+    """The reference arm's worker chunks hold every zonal order exactly once, with about equal
+    work (T + 1 - m per order), so each timed step is a full step."""
+    for t, parts in ((1, 4), (15, 3), (63, 16), (255, 16), (511, 7)):
+        ch = bench._balanced_orders(t, parts)
+        flat = sorted(m for c in ch for m in c)
+        assert flat == list(range(t + 1))
+        loads = [sum(t + 1 - m for m in c) for c in ch]
+        assert max(loads) - min(loads) <= t + 1
 
 
 # ---- the pole / zonal-order partition of one step (paper Sec. 5.3-5.4) -------------------------
