@@ -702,7 +702,12 @@ def _hbm_peak():
 def serving_run(args):
     import torch
     from paper_1805_06557_gb300 import serving
+    from paper_1805_06557_gb300 import rexi, synthetic as syn
     n = args.serving
+    # the service's contour table for its pole counts and the largest spectrum width it serves
+    # (T511 at dt = 14400 s): planning work before any request, reported, not timed with them
+    xmax = rexi.spectrum_bound(511, 14400.0, syn.OMEGA, syn.RADIUS, syn.PHIBAR)
+    table_s = serving.prepare_contours((256, 512, 1024, 2048), xmax)
     # calibration: capacity of the batched engine with everything queued at once
     cal = serving.make_requests(min(n, 200), seed=5, rate=1e9)
     eng = serving.ServingEngine(Tmax=511, max_slots=64, hbm_bytes=8 << 30, max_poles=64 * 2048)
@@ -716,7 +721,8 @@ def serving_run(args):
     base = serving.one_at_a_time(serving.make_requests(n, seed=5, rate=rate), precision="fp64")
     line = {"metric": "served REXI steps/s and latency, Poisson stream (T 63-511, dt 600-14400 s, "
                       "N 256-2048)", "unit": "steps/s", "requests": n, "rate_per_s": rate,
-            "calibration": cstats, "batched_mixed": st, "one_at_a_time_fp64": base}
+            "contour_table_s": table_s, "calibration": cstats, "batched_mixed": st,
+            "one_at_a_time_fp64": base}
     print(json.dumps(line), flush=True)
 
 

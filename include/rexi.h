@@ -293,8 +293,11 @@ typedef struct rexi_instance {
 int rexi_ragged_create(const rexi_ragged_desc* desc, rexi_ragged** out);
 int rexi_ragged_destroy(rexi_ragged* r);
 /* Sets the instance list (host array).  Pole sets are generated on the host and cached by
- * (T, N, dt, p0, Xc); tiles and descriptors are rebuilt and uploaded (synchronously).
- * Errors: REXI_EINVAL (bad instance), REXI_EBUSY (capacity exceeded), REXI_ECUDA. */
+ * (T, N, dt, p0, Xc); tiles and descriptors are rebuilt on the host and uploaded, with the new
+ * pole sets, by asynchronous copies on the plan stream from pinned packets: they run after the
+ * work already queued on that stream (a step in flight keeps its data), and the call does not
+ * wait for the device except to grow a buffer.  A failed call leaves no instance set.
+ * Errors: REXI_EINVAL (bad instance), REXI_EBUSY (capacity exceeded), REXI_ENOMEM, REXI_ECUDA. */
 int rexi_ragged_set(rexi_ragged* r, int ninst, const rexi_instance* inst);
 /* soff[0..ninst]: complex offsets of the states in the concatenated layout (soff[ninst] = total). */
 int rexi_ragged_offsets(const rexi_ragged* r, long long* soff);

@@ -385,12 +385,8 @@ int engine_init(Engine& e, int precision, int Ttab, double omega, double radius,
 }
 
 // Appends a pole set to the arena (scaled by 1/dt: z' = z/dt, w' = w/dt, w/z, 1/z', Phibar/z').
-int engine_upload_poles(Engine& e, PoleSet& ps) {
-  if (e.pole_used + ps.Npad > e.pole_cap)
-    return fail(REXI_EBUSY, "pole arena full (%d + %d > %d)", e.pole_used, ps.Npad, e.pole_cap);
-  std::vector<PoleD> pd(ps.Npad);
-  std::vector<PoleF> pf(ps.Npad);
-  std::vector<PoleDF> pq(ps.Npad);
+// the device forms of a pole set: FP64, FP32 and double-float constants of every (padded) pole
+void pack_poles(const Engine& e, const PoleSet& ps, PoleD* pd, PoleF* pf, PoleDF* pq) {
   for (int i = 0; i < ps.Npad; ++i) {
     const cplx z = ps.z[i], w = ps.w[i];
     const cplx zs = z / ps.dt, ws = w / ps.dt, wz = w / z, iz = 1.0 / zs, gz = e.phibar / zs;
@@ -401,6 +397,15 @@ int engine_upload_poles(Engine& e, PoleSet& ps) {
     pq[i] = PoleDF{split4(zs.real(), zs.imag()), split4(iz.real(), iz.imag()), split4(gz.real(), gz.imag()),
                    split4(ws.real(), ws.imag()), split4(wz.real(), wz.imag())};
   }
+}
+
+int engine_upload_poles(Engine& e, PoleSet& ps) {
+  if (e.pole_used + ps.Npad > e.pole_cap)
+    return fail(REXI_EBUSY, "pole arena full (%d + %d > %d)", e.pole_used, ps.Npad, e.pole_cap);
+  std::vector<PoleD> pd(ps.Npad);
+  std::vector<PoleF> pf(ps.Npad);
+  std::vector<PoleDF> pq(ps.Npad);
+  pack_poles(e, ps, pd.data(), pf.data(), pq.data());
   cudaError_t ce = cudaMemcpy(e.p64 + e.pole_used, pd.data(), sizeof(PoleD) * ps.Npad, cudaMemcpyHostToDevice);
   if (!ce && e.p32) ce = cudaMemcpy(e.p32 + e.pole_used, pf.data(), sizeof(PoleF) * ps.Npad, cudaMemcpyHostToDevice);
   if (!ce && e.pdf) ce = cudaMemcpy(e.pdf + e.pole_used, pq.data(), sizeof(PoleDF) * ps.Npad, cudaMemcpyHostToDevice);
@@ -1041,13 +1046,32 @@ struct rexi_ragged {
   std::vector<const PoleSet*> cur;
   std::vector<long long> soff;
   long long extent = 0;  // complex elements spanned by the states in U0 / U1
-  LaunchSet L;
+  LaunchSet L;  // device descriptors, kept between sets and grown when a set needs more
+  size_t cap_inst = 0, cap_tiles = 0, cap_ecum = 0;
   int qmul = 4;
   // captured graph of one step for fixed (U0, U1)
   cudaGraphExec_t gexec = nullptr;
   const void* g_u0 = nullptr;
   void* g_u1 = nullptr;
+  // pinned host packets for the asynchronous uploads of a set (new poles and descriptors),
+  // used alternately; a packet is rewritten once the copies from its previous use have run
+  struct Packet {
+    unsigned char* h = nullptr;
+    size_t cap = 0;
+    cudaEvent_t ev = nullptr;
+  } pk[2];
+  int pk_i = 0;
+  std::vector<PoleSet*> fresh;  // pole sets of the current set call not yet uploaded
+  std::vector<std::tuple<int, int, double, double, double>> fresh_keys;
 };
+
+// A set call that fails after reserving new pole sets drops them from the cache (they were
+// never uploaded, so a later call must not find them).
+static void drop_fresh(rexi_ragged* r) {
+  for (auto& k : r->fresh_keys) r->cache.erase(k);
+  r->fresh.clear();
+  r->fresh_keys.clear();
+}
 
 extern "C" int rexi_ragged_create(const rexi_ragged_desc* desc, rexi_ragged** out) {
   if (!desc || !out) return fail(REXI_EINVAL, "rexi_ragged_create: null argument");
@@ -1078,13 +1102,25 @@ extern "C" int rexi_ragged_create(const rexi_ragged_desc* desc, rexi_ragged** ou
 
 extern "C" int rexi_ragged_destroy(rexi_ragged* r) {
   if (!r) return REXI_OK;
+  cudaStreamSynchronize(r->e.stream);
   if (r->gexec) cudaGraphExecDestroy(r->gexec);
   engine_free(r->e);
   free_launch(r->L);
+  for (auto& q : r->pk) {
+    cudaFreeHost(q.h);
+    if (q.ev) cudaEventDestroy(q.ev);
+  }
   delete r;
   return REXI_OK;
 }
 
+static size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Rebuilds the tiles of the current instances and uploads them, with the pole sets in r->fresh,
+// asynchronously on the plan stream: everything is packed into a pinned host packet and copied
+// by cudaMemcpyAsync, so the copies run in stream order after the work already queued (a tick
+// in flight keeps its descriptors and poles until it has finished) and the host does not wait
+// for the device.  Only growing a device buffer synchronises the stream.
 static int ragged_rebuild(rexi_ragged* r) {
   std::vector<InstReq> req;
   for (size_t i = 0; i < r->cur.size(); ++i) req.push_back(InstReq{r->cur[i], r->soff[i]});
@@ -1095,7 +1131,78 @@ static int ragged_rebuild(rexi_ragged* r) {
   long long pe;
   build_launch(r->e, req, I, Tl, ec, ntl, pe, ntq, ntp, r->qmul);
   if (pe > (long long)r->e.partial_cap) return fail(REXI_EBUSY, "rexi_ragged: partial-sum workspace exceeded");
-  return upload_launch(r->L, I, Tl, ec, ntl, ntq, ntp, pe);
+  Engine& e = r->e;
+  cudaError_t ce;
+  // device descriptors: grow (after the stream's queued work) when this set needs more room
+  if (I.size() > r->cap_inst || Tl.size() > r->cap_tiles || ec.size() > r->cap_ecum) {
+    if ((ce = cudaStreamSynchronize(e.stream))) return cuda_fail(ce, "rexi_ragged: stream");
+    free_launch(r->L);
+    r->cap_inst = std::max(I.size(), r->cap_inst) * 3 / 2 + 16;
+    r->cap_tiles = std::max(Tl.size(), r->cap_tiles) * 3 / 2 + 64;
+    r->cap_ecum = std::max(ec.size(), r->cap_ecum) * 3 / 2 + 16;
+    if ((ce = cudaMalloc(&r->L.insts, sizeof(Inst) * r->cap_inst)) ||
+        (ce = cudaMalloc(&r->L.tiles, sizeof(Tile) * r->cap_tiles)) ||
+        (ce = cudaMalloc(&r->L.ecum, sizeof(long long) * r->cap_ecum))) {
+      cudaGetLastError();
+      r->cap_inst = r->cap_tiles = r->cap_ecum = 0;
+      return fail(REXI_ENOMEM, "rexi_ragged: launch descriptors: cudaMalloc failed");
+    }
+  }
+  // the packet: [poles of each fresh set: PoleD, PoleF, PoleDF][insts][tiles][ecum]
+  size_t bytes = 0;
+  for (const PoleSet* ps : r->fresh)
+    bytes += al256(sizeof(PoleD) * ps->Npad) + al256(sizeof(PoleF) * ps->Npad) + al256(sizeof(PoleDF) * ps->Npad);
+  const size_t o_inst = bytes, o_tile = o_inst + al256(sizeof(Inst) * I.size()),
+               o_ecum = o_tile + al256(sizeof(Tile) * Tl.size());
+  bytes = o_ecum + al256(sizeof(long long) * ec.size());
+  rexi_ragged::Packet& q = r->pk[r->pk_i];
+  r->pk_i ^= 1;
+  if (q.ev && (ce = cudaEventSynchronize(q.ev))) return cuda_fail(ce, "rexi_ragged: packet event");
+  if (!q.ev && (ce = cudaEventCreateWithFlags(&q.ev, cudaEventDisableTiming)))
+    return cuda_fail(ce, "rexi_ragged: cudaEventCreate");
+  if (bytes > q.cap) {
+    cudaFreeHost(q.h);
+    q.h = nullptr;
+    q.cap = 0;
+    if ((ce = cudaMallocHost((void**)&q.h, bytes * 3 / 2))) {
+      cudaGetLastError();
+      return fail(REXI_ENOMEM, "rexi_ragged: pinned upload buffer");
+    }
+    q.cap = bytes * 3 / 2;
+  }
+  size_t o = 0;
+  for (const PoleSet* ps : r->fresh) {
+    PoleD* pd = reinterpret_cast<PoleD*>(q.h + o);
+    o += al256(sizeof(PoleD) * ps->Npad);
+    PoleF* pf = reinterpret_cast<PoleF*>(q.h + o);
+    o += al256(sizeof(PoleF) * ps->Npad);
+    PoleDF* pq = reinterpret_cast<PoleDF*>(q.h + o);
+    o += al256(sizeof(PoleDF) * ps->Npad);
+    pack_poles(e, *ps, pd, pf, pq);
+    const int p0 = ps->pole0;
+    ce = cudaMemcpyAsync(e.p64 + p0, pd, sizeof(PoleD) * ps->Npad, cudaMemcpyHostToDevice, e.stream);
+    if (!ce && e.p32) ce = cudaMemcpyAsync(e.p32 + p0, pf, sizeof(PoleF) * ps->Npad, cudaMemcpyHostToDevice, e.stream);
+    if (!ce && e.pdf) ce = cudaMemcpyAsync(e.pdf + p0, pq, sizeof(PoleDF) * ps->Npad, cudaMemcpyHostToDevice, e.stream);
+    if (ce) return cuda_fail(ce, "rexi_ragged: cudaMemcpyAsync(poles)");
+  }
+  r->fresh.clear();
+  memcpy(q.h + o_inst, I.data(), sizeof(Inst) * I.size());
+  memcpy(q.h + o_tile, Tl.data(), sizeof(Tile) * Tl.size());
+  memcpy(q.h + o_ecum, ec.data(), sizeof(long long) * ec.size());
+  if ((ce = cudaMemcpyAsync(r->L.insts, q.h + o_inst, sizeof(Inst) * I.size(), cudaMemcpyHostToDevice, e.stream)) ||
+      (ce = cudaMemcpyAsync(r->L.tiles, q.h + o_tile, sizeof(Tile) * Tl.size(), cudaMemcpyHostToDevice, e.stream)) ||
+      (ce = cudaMemcpyAsync(r->L.ecum, q.h + o_ecum, sizeof(long long) * ec.size(), cudaMemcpyHostToDevice,
+                            e.stream)) ||
+      (ce = cudaEventRecord(q.ev, e.stream)))
+    return cuda_fail(ce, "rexi_ragged: cudaMemcpyAsync(launch descriptors)");
+  r->L.ninst = (int)I.size();
+  r->L.ntiles = (int)Tl.size();
+  r->L.ntiles_light = ntl;
+  r->L.ntiles_quad = ntq;
+  r->L.ntiles_pair = ntp;
+  r->L.total = ec.back();
+  r->L.partial_elems = pe;
+  return REXI_OK;
 }
 
 extern "C" int rexi_ragged_set(rexi_ragged* r, int ninst, const rexi_instance* inst) {
@@ -1117,38 +1224,6 @@ extern "C" int rexi_ragged_set(rexi_ragged* r, int ninst, const rexi_instance* i
     cudaGraphExecDestroy(r->gexec);
     r->gexec = nullptr;
   }
-  // pole sets are cached by (T, N, dt, p0, Xc); the arena starts over when it overflows
-  auto ensure = [&](const rexi_instance& q, const PoleSet** out) -> int {
-    auto key = std::make_tuple(q.T, q.N, q.dt, q.p0, q.Xc);
-    auto it = r->cache.find(key);
-    if (it != r->cache.end()) {
-      *out = &it->second;
-      return REXI_OK;
-    }
-    PoleSet ps;
-    const double X = rexi_spectrum_bound(q.T, q.dt, r->d.omega, r->d.radius, r->d.phibar);
-    // ragged sets: most instances have a pole set of their own and run tiles of one state
-    int rc = make_poleset_from_contour(ps, r->d.precision, q.T, q.N, q.dt, X, q.p0, q.Xc, r->d.heavy_tau,
-                                       r->d.prune_tau, 32);
-    if (rc) return rc;
-    if (r->e.pole_used + ps.Npad > r->e.pole_cap) return REXI_EBUSY;
-    rc = engine_upload_poles(r->e, ps);
-    if (rc) return rc;
-    it = r->cache.emplace(key, std::move(ps)).first;
-    *out = &it->second;
-    return REXI_OK;
-  };
-  std::vector<const PoleSet*> cur(ninst);
-  int rc = REXI_OK;
-  for (int i = 0; i < ninst && !rc; ++i) rc = ensure(inst[i], &cur[i]);
-  if (rc == REXI_EBUSY) {  // arena full: start over with the current pole sets only
-    r->cache.clear();
-    r->e.pole_used = 0;
-    rc = REXI_OK;
-    for (int i = 0; i < ninst && !rc; ++i) rc = ensure(inst[i], &cur[i]);
-    if (rc == REXI_EBUSY) return fail(REXI_EBUSY, "rexi_ragged_set: pole sets exceed max_poles");
-  }
-  if (rc) return rc;
   const bool given = inst[0].soff >= 0;
   for (int i = 0; i < ninst; ++i)
     if ((inst[i].soff >= 0) != given)
@@ -1171,10 +1246,64 @@ extern "C" int rexi_ragged_set(rexi_ragged* r, int ninst, const rexi_instance* i
         return fail(REXI_EINVAL, "rexi_ragged_set: states %d and %d overlap", a, b);
     }
   }
+  // pole sets are cached by (T, N, dt, p0, Xc); the arena starts over when it overflows
+  auto ensure = [&](const rexi_instance& q, const PoleSet** out) -> int {
+    auto key = std::make_tuple(q.T, q.N, q.dt, q.p0, q.Xc);
+    auto it = r->cache.find(key);
+    if (it != r->cache.end()) {
+      *out = &it->second;
+      return REXI_OK;
+    }
+    PoleSet ps;
+    const double X = rexi_spectrum_bound(q.T, q.dt, r->d.omega, r->d.radius, r->d.phibar);
+    // ragged sets: most instances have a pole set of their own and run tiles of one state
+    int rc = make_poleset_from_contour(ps, r->d.precision, q.T, q.N, q.dt, X, q.p0, q.Xc, r->d.heavy_tau,
+                                       r->d.prune_tau, 32);
+    if (rc) return rc;
+    if (r->e.pole_used + ps.Npad > r->e.pole_cap) return REXI_EBUSY;
+    // a place in the pole arena now; the upload goes with this set's descriptors (stream order:
+    // after the work already queued, which may still read the arena's earlier contents)
+    ps.pole0 = r->e.pole_used;
+    r->e.pole_used += ps.Npad;
+    it = r->cache.emplace(key, std::move(ps)).first;
+    r->fresh.push_back(&it->second);
+    r->fresh_keys.push_back(key);
+    *out = &it->second;
+    return REXI_OK;
+  };
+  std::vector<const PoleSet*> cur(ninst);
+  int rc = REXI_OK;
+  r->fresh.clear();
+  r->fresh_keys.clear();
+  for (int i = 0; i < ninst && !rc; ++i) rc = ensure(inst[i], &cur[i]);
+  if (rc == REXI_EBUSY) {  // arena full: start over with the current pole sets only
+    r->cache.clear();
+    r->fresh.clear();
+    r->fresh_keys.clear();
+    r->e.pole_used = 0;
+    rc = REXI_OK;
+    for (int i = 0; i < ninst && !rc; ++i) rc = ensure(inst[i], &cur[i]);
+    if (rc == REXI_EBUSY) {
+      drop_fresh(r);
+      return fail(REXI_EBUSY, "rexi_ragged_set: pole sets exceed max_poles");
+    }
+  }
+  if (rc) {
+    drop_fresh(r);
+    return rc;
+  }
   r->cur = cur;
   r->soff = so;
   r->extent = ext;
-  return ragged_rebuild(r);
+  rc = ragged_rebuild(r);
+  if (rc) {  // nothing of this set is usable: no step until a set succeeds
+    drop_fresh(r);
+    r->cur.clear();
+    r->soff.clear();
+    r->extent = 0;
+  }
+  r->fresh_keys.clear();
+  return rc;
 }
 
 extern "C" int rexi_ragged_offsets(const rexi_ragged* r, long long* soff) {

@@ -43,6 +43,20 @@ def contour(T, dt, omega, radius, phibar, N=None):
     return _CONTOURS[key]
 
 
+def prepare_contours(pole_counts, Xmax):
+    """Fills the contour table for every pole count served and every grid point of X up to Xmax
+    (the planning work of a service, done once before requests arrive); returns the seconds
+    it took."""
+    t0 = time.perf_counter()
+    qmax = math.ceil(math.log(max(Xmax, 20.0) / 20.0) / math.log(1.05))
+    for N in pole_counts:
+        for q in range(qmax + 1):
+            key = (int(N), q)
+            if key not in _CONTOURS:
+                _CONTOURS[key] = rexi.contour_select(20.0 * 1.05 ** q, int(N))
+    return time.perf_counter() - t0
+
+
 class Request:
     __slots__ = ("rid", "arrival", "T", "dt", "N", "p0", "Xc", "state", "status", "error",
                  "result", "t_admit", "t_done", "slot")
@@ -127,6 +141,7 @@ class ServingEngine:
         self.active = []      # admitted, waiting for a tick
         self.done = []
         self.ticks = 0
+        self.out_host = None  # pinned host buffer the results of a tick are copied into
 
     # ---- admission ---------------------------------------------------------------------
     def _validate(self, r):
@@ -194,6 +209,20 @@ class ServingEngine:
         self.stream.wait_event(ev)
         self.plan.set([(r.T, r.N, r.dt, r.p0, r.Xc, r.slot) for r in batch])
         self.plan.step(self.U0, self.U1)
+        # the results back to the host in the same stream order: one asynchronous copy per
+        # request into one pinned buffer, then one wait for the tick
+        total = sum(3 * r.nlm for r in batch)
+        if self.out_host is None or self.out_host.numel() < total:
+            self.out_host = torch.empty(max(total, 3 * (self.Tmax + 1) * (self.Tmax + 2) // 2),
+                                        dtype=torch.complex128, pin_memory=True)
+        offs = []
+        o = 0
+        with torch.cuda.stream(self.stream):
+            for r in batch:
+                n = 3 * r.nlm
+                self.out_host[o: o + n].copy_(self.U1[r.slot: r.slot + n], non_blocking=True)
+                offs.append(o)
+                o += n
         done_ev = torch.cuda.Event()
         done_ev.record(self.stream)
         if on_launch is not None:
@@ -201,8 +230,9 @@ class ServingEngine:
         self.active.extend(self._admit())    # their copies overlap the running tick
         done_ev.synchronize()
         now = time.perf_counter()
-        for r in batch:
-            r.result = self.U1[r.slot: r.slot + 3 * r.nlm].cpu().numpy().reshape(3, r.nlm)
+        host = self.out_host.numpy()
+        for r, o in zip(batch, offs):
+            r.result = host[o: o + 3 * r.nlm].reshape(3, r.nlm).copy()
             r.status = OK
             r.t_done = now
             self.arena.release(r.slot, 3 * r.nlm)
