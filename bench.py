@@ -477,11 +477,24 @@ def sh_transforms(torch, rexi, fp64_peak, T=511, nlat=768, nlon=1536, nf=2, reps
                 leg_roof = {"bound": "hbm", "kernel": "k_tc_gemm", "algorithmic_bytes": leg_bytes,
                             "achieved_gbs": leg_bytes / (gemm_ms * 1e6), "peak": hbm, "unit": "GB/s",
                             "frac": leg_bytes / (gemm_ms * 1e6) / hbm, "tflops": leg_flops / (gemm_ms * 1e9)}
+            # FFT: the conventional 5 n log2 n flops per complex length-n sequence (two real rows
+            # per sequence).  In FP64 the pipe binds on this GPU (about 2 FP64 FMAs per clock and
+            # SM); in FP32 the grid and Fourier bytes do.
+            fft_flops = 5.0 * nlon * math.log2(nlon) * narr * nlat / 2
+            gbs = fft_bytes / (fft_ms * 1e6) if fft_ms > 0 else None
+            if prec == "fp64":
+                fft_roof = {"bound": "alu", "pipe": "fp64", "algorithmic_flops": fft_flops,
+                            "achieved": fft_flops / (fft_ms * 1e9) if fft_ms > 0 else None, "unit": "TFLOP/s",
+                            "peak": fp64_peak,
+                            "frac": fft_flops / (fft_ms * 1e9) / fp64_peak if fft_ms > 0 else None,
+                            "algorithmic_bytes": fft_bytes, "achieved_gbs": gbs,
+                            "hbm_frac": gbs / hbm if gbs else None}
+            else:
+                fft_roof = {"bound": "hbm", "algorithmic_bytes": fft_bytes, "achieved_gbs": gbs, "unit": "GB/s",
+                            "peak": hbm, "frac": gbs / hbm if gbs else None, "algorithmic_flops": fft_flops}
             r = {"ms": total, "stage_ms": {k: v[0] / reps for k, v in prof.items() if v[1]},
                  "legendre_ms": leg_ms, "legendre_roofline": leg_roof,
-                 "fft_roofline": {"bound": "hbm", "algorithmic_bytes": fft_bytes,
-                                  "achieved_gbs": fft_bytes / (fft_ms * 1e6) if fft_ms > 0 else None,
-                                  "frac": fft_bytes / (fft_ms * 1e6) / hbm if fft_ms > 0 else None}}
+                 "fft_roofline": fft_roof}
             res[kind] = r
         p.check()
         g, b = grid.cpu().numpy(), back.cpu().numpy()

@@ -24,6 +24,7 @@ rexi    : the REXI step  U(dt) ~ sum_n beta_n (dt L + alpha_n)^-1 U(0)  (Eq. rex
           pole and zonal order with a pivoted banded LU, plus the exact exponential.
 rexi_lg : REXI of the gravity operator L_g alone (the lg_* methods of Table 2): a per-degree
           2 x 2 solve per pole, and its closed-form exponential.
-swe     : nonlinear term N(U) on the Gauss grid (Sec. 3, the N column of the split), RK2, RK4,
-          and the Strang ver1 step  N^{dt/2} o L^{dt} o N^{dt/2}  (Sec. 4.4).
+swe     : nonlinear term N(U) on the Gauss grid (Sec. 3, the N column of the split), RK2 (with
+          optional sub-steps), RK4, the Strang, ETD2RK and Crank-Nicolson steps (Sec. 4.1-4.4),
+          and the exact flow of a del^{2q} hyper-diffusion term split off around a step.
 """
