@@ -299,3 +299,32 @@ def test_graph_replay_equals_eager_steps(env, scheme, sprec):
     assert torch.equal(a, b) and torch.equal(a, c) and torch.equal(a, d)
     assert not torch.equal(a, U0)
     plan.close()
+
+
+_T127_REF = []  # the oracle's two steps, computed once for both precisions
+
+
+@pytest.mark.parametrize("rprec,tol", [("fp64", 1e-10), ("mixed", 1e-8)])
+def test_config_T127_nonlinear_steps_match_oracle(env, rprec, tol):
+    """The nonlinear configuration at full size: T127 on the 192 x 384 Gauss grid, 512 poles,
+    dt = 1800 s, the balanced n^-3 state (seed 2, 20 m/s rms) of the benchmark, two Strang ver1
+    steps against the oracle's (FP64 Legendre); the bench times 48 such steps."""
+    torch, rexi = env
+    T, nlat, nlon, N, dt, nsteps = 127, 192, 384, 512, 1800.0, 2
+    U0 = syn.balanced_state(T, 2)
+    g = osht.Grid(T, nlat, nlon, A)
+    p0, Xc = _contour(T, dt)
+    z, w = oc.rexi_coefficients(N, p0, Xc)
+    if not _T127_REF:
+        ref = U0
+        for _ in range(nsteps):
+            ref = oswe.strang_ver1(ref, g, dt, OM, PB, z, w)
+        _T127_REF.append(ref)
+    ref = _T127_REF[0]
+    plan = rexi.SwePlan(T, nlat, nlon, dt, OM, A, PB, N, p0, Xc, rexi_precision=rprec)
+    u = torch.from_numpy(U0).cuda()
+    plan.step(u, nsteps)
+    torch.cuda.synchronize()
+    err = orx.rel_l2(u.cpu().numpy(), ref, T)
+    assert np.all(err < tol), err
+    plan.close()
