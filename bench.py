@@ -856,7 +856,16 @@ def main():
         avg_s = kms / kn * 1e-3
         peak = fp32_tf if pipe == "fp32" else fp64_tf
         xfl = EXECUTED_FLOPS[kname] * elems * npoles
+        # the mixed path's two-pipe roofline (the method's solve on the FP32 pipe, its FP64-accurate
+        # weighted pole sums, 12 of the 49 flops, on the FP64 pipe), for kernels whose sums must be
+        # FP64-accurate; the light kernel's FP32 sums need no FP64
+        if kname == "k_rexi_heavy":
+            t_min = elems * npoles * ((fl - 12.0) / (fp32_tf * 1e12) + 12.0 / (fp64_tf * 1e12))
+            two_pipe = t_min / avg_s
+        else:
+            two_pipe = None
         kernels[kname] = {"bound": "alu", "pipe": pipe, "flops_per_chain_element": fl, "poles": npoles,
+                          "frac_two_pipe": two_pipe,
                           "ms": kms / kn, "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                           "frac": flops / avg_s / 1e12 / peak,
                           "frac_of_fp64_peak": flops / avg_s / 1e12 / fp64_tf,

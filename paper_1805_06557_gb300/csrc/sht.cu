@@ -12,7 +12,9 @@
 // (register butterflies), two real latitude rows packed into one complex sequence.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <initializer_list>
+#include <type_traits>
 #include <tuple>
 #include <vector>
 
@@ -282,7 +284,11 @@ struct FftPlan {
   int n, nrad;
   int rad[24];
   unsigned magic[24];  // ceil(2^32 / Ns) of each pass: j / Ns = umulhi(j, magic) for j < n
+  int twoff[24];       // first entry of each pass's twiddle table (see fft_twiddle_tables)
 };
+
+// row width of a pass's twiddle table: R, or 4 for radix 3 (rows of 16-byte pairs)
+__host__ __device__ constexpr int tw_width(int R) { return R == 3 ? 4 : R; }
 
 constexpr int FTH = 256;
 constexpr double SQRT3_2 = 0.86602540378443864676;  // sin(2 pi / 3)
@@ -355,24 +361,36 @@ __host__ __device__ constexpr int fft_padded(int n) { return n + (n >> 3) + 1; }
 
 // One Stockham pass of radix R (2, 3, 4 or 8): for j < n / R, jm = j mod Ns, q = j / Ns, the
 // R inputs src(j + r n/R) times the twiddles w^{r jm stride} are transformed and written to
-// dst(q Ns R + jm + r Ns).
+// dst(q Ns R + jm + r Ns).  twp is the pass's twiddle table, row jm = (w^{r jm stride}, r < R),
+// tw_width(R) entries per row, read as 16-byte pairs (FP32) or 16-byte entries (FP64); the
+// first pass (Ns = 1) has no twiddles.
 template <typename C, int R, typename Src, typename Dst>
-__device__ __forceinline__ void fft_pass(Src src, Dst dst, int n, int Ns, unsigned mg, const C* tw, int sign) {
+__device__ __forceinline__ void fft_pass(Src src, Dst dst, int n, int Ns, unsigned mg, const C* twp, int sign) {
   using Rt = typename Cx<C>::R;
+  constexpr int W = tw_width(R);
   const int nb = n / R;
-  const int stride = n / (Ns * R);
   for (int j = threadIdx.x; j < nb; j += blockDim.x) {
     const int q = (Ns == 1) ? j : (int)__umulhi((unsigned)j, mg);  // j / Ns
     const int jm = j - q * Ns;
     C v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = src(j + r * nb);
+    if (Ns > 1) {  // uniform over the block
+      auto apply = [&](int r, C tr) {
+        if (sign > 0) tr.y = -tr.y;
+        v[r] = c_mul(v[r], tr);
+      };
+      if constexpr (std::is_same<C, float2>::value) {
+        const float4* tp = reinterpret_cast<const float4*>(twp + jm * W);
 #pragma unroll
-    for (int r = 1; r < R; ++r) {
-      if (jm) {
-        C t = tw[r * jm * stride];  // r jm stride < n
-        if (sign > 0) t.y = -t.y;
-        v[r] = c_mul(v[r], t);
+        for (int h = 0; h < W / 2; ++h) {  // a 16-byte pair per load, applied as it arrives
+          const float4 pr = __ldg(tp + h);
+          if (h > 0) apply(2 * h, make_float2(pr.x, pr.y));
+          if (2 * h + 1 < R) apply(2 * h + 1, make_float2(pr.z, pr.w));
+        }
+      } else {
+#pragma unroll
+        for (int r = 1; r < R; ++r) apply(r, __ldg(twp + jm * W + r));
       }
     }
     if (R == 2) {
@@ -406,8 +424,8 @@ __device__ __forceinline__ void fft_pass_r(int R, Src src, Dst dst, int n, int N
   else fft_pass<C, 3>(src, dst, n, Ns, mg, tw, sign);
 }
 
-// All passes of one length-n transform (sign = -1 forward, +1 inverse, no scaling; tw[k] =
-// e^{-2 pi i k / n}).  The first pass reads its inputs through src (global memory); the passes
+// All passes of one length-n transform (sign = -1 forward, +1 inverse, no scaling; tw holds the
+// passes' twiddle tables of e^{-2 pi i k / n}, pass s from fp.twoff[s]).  The first pass reads its inputs through src (global memory); the passes
 // in between go through the padded shared buffers a and b; the last pass writes through dst,
 // or, with LAST_SMEM, into a shared buffer whose address is returned (padded indices).
 template <typename C, bool LAST_SMEM, typename Src, typename Dst>
@@ -419,17 +437,18 @@ __device__ C* fft_run(Src src, Dst dst, C* a, C* b, const FftPlan& fp, const C* 
   for (int s = 0; s < S; ++s) {
     const int R = fp.rad[s];
     const unsigned mg = fp.magic[s];
+    const C* twp = tw + fp.twoff[s];
     C* const rb = cur;
     C* const wb = nxt;
     auto rd = [rb](int i) { return rb[fpad(i)]; };
     auto wr = [wb](int i, C v) { wb[fpad(i)] = v; };
     const bool last = s == S - 1;
     if (s == 0) {
-      if (last && !LAST_SMEM) fft_pass_r<C>(R, src, dst, n, Ns, mg, tw, sign);
-      else fft_pass_r<C>(R, src, wr, n, Ns, mg, tw, sign);
+      if (last && !LAST_SMEM) fft_pass_r<C>(R, src, dst, n, Ns, mg, twp, sign);
+      else fft_pass_r<C>(R, src, wr, n, Ns, mg, twp, sign);
     } else {
-      if (last && !LAST_SMEM) fft_pass_r<C>(R, rd, dst, n, Ns, mg, tw, sign);
-      else fft_pass_r<C>(R, rd, wr, n, Ns, mg, tw, sign);
+      if (last && !LAST_SMEM) fft_pass_r<C>(R, rd, dst, n, Ns, mg, twp, sign);
+      else fft_pass_r<C>(R, rd, wr, n, Ns, mg, twp, sign);
     }
     __syncthreads();
     cur = wb;
@@ -588,11 +607,34 @@ bool fft_factor(int n, FftPlan& fp) {
     m /= 3;
   }
   unsigned long long Ns = 1;
+  int off = 0;
   for (int s = 0; s < fp.nrad; ++s) {
     fp.magic[s] = Ns == 1 ? 0u : (unsigned)(((1ULL << 32) + Ns - 1) / Ns);  // ceil(2^32 / Ns); unused for Ns = 1
+    fp.twoff[s] = off;
+    off += (int)Ns * tw_width(fp.rad[s]);
     Ns *= fp.rad[s];
   }
   return m == 1;
+}
+
+// Twiddle tables of all passes: pass s (radix R, Ns = product of the earlier radices, stride
+// n / (Ns R)) holds, for jm < Ns, the row (e^{-2 pi i r jm stride / n}, r < R) padded to
+// tw_width(R) entries; the total is fp.twoff[nrad - 1] + Ns_last * tw_width(R_last) entries.
+static std::vector<std::complex<double>> fft_twiddle_tables(const FftPlan& fp) {
+  std::vector<std::complex<double>> t;
+  long long Ns = 1;
+  for (int s = 0; s < fp.nrad; ++s) {
+    const int R = fp.rad[s], W = tw_width(R);
+    const long long stride = fp.n / (Ns * R);
+    for (long long jm = 0; jm < Ns; ++jm)
+      for (int r = 0; r < W; ++r) {
+        const long long k = r < R ? (r * jm * stride) % fp.n : 0;
+        const double a = -2.0 * M_PI * (double)k / fp.n;
+        t.push_back(r < R ? std::complex<double>(std::cos(a), std::sin(a)) : 0.0);
+      }
+    Ns *= R;
+  }
+  return t;
 }
 
 }  // namespace
@@ -610,8 +652,8 @@ struct sh_plan {
   double* d_wq = nullptr;   // w / (1 - mu^2) [nh]
   double* d_P = nullptr;    // [nlm][nh]
   double* d_H = nullptr;
-  double2* d_tw = nullptr;  // [nlon]
-  float2* d_tw32 = nullptr; // [nlon], FP32 FFT of the tensor-core plans
+  double2* d_tw = nullptr;  // twiddle tables of the FFT passes (fft_twiddle_tables)
+  float2* d_tw32 = nullptr; // the same in FP32, for the FFT of the tensor-core plans
   bool fft32 = false;
   double2* d_F = nullptr;   // Fourier workspace [2 * max_fields][T+1][nlat]
   FftPlan fp{};
@@ -652,19 +694,20 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
   gauss_legendre(d.nlat, p->mu, p->w);
   std::vector<double> wq(p->nh);
   for (int j = 0; j < p->nh; ++j) wq[j] = p->w[j] / ((1.0 - p->mu[j]) * (1.0 + p->mu[j]));
-  std::vector<double2> tw(d.nlon);
-  std::vector<float2> tw32(d.nlon);
-  for (int k = 0; k < d.nlon; ++k) {
-    const double a = -2.0 * M_PI * k / d.nlon;
-    tw[k] = make_double2(std::cos(a), std::sin(a));
-    tw32[k] = make_float2((float)tw[k].x, (float)tw[k].y);
+  const std::vector<std::complex<double>> twt = fft_twiddle_tables(p->fp);
+  const size_t ntw = twt.size();
+  std::vector<double2> tw(ntw);
+  std::vector<float2> tw32(ntw);
+  for (size_t k = 0; k < ntw; ++k) {
+    tw[k] = make_double2(twt[k].real(), twt[k].imag());
+    tw32[k] = make_float2((float)twt[k].real(), (float)twt[k].imag());
   }
   const size_t tab = (size_t)p->nlm * p->nh;
   cudaError_t e;
   if ((e = cudaMalloc(&p->d_mu, sizeof(double) * p->nh)) || (e = cudaMalloc(&p->d_w, sizeof(double) * p->nh)) ||
       (e = cudaMalloc(&p->d_wq, sizeof(double) * p->nh)) || (e = cudaMalloc(&p->d_P, sizeof(double) * tab)) ||
-      (e = cudaMalloc(&p->d_H, sizeof(double) * tab)) || (e = cudaMalloc(&p->d_tw, sizeof(double2) * d.nlon)) ||
-      (e = cudaMalloc(&p->d_tw32, sizeof(float2) * d.nlon)) ||
+      (e = cudaMalloc(&p->d_H, sizeof(double) * tab)) || (e = cudaMalloc(&p->d_tw, sizeof(double2) * ntw)) ||
+      (e = cudaMalloc(&p->d_tw32, sizeof(float2) * ntw)) ||
       (e = cudaMalloc(&p->d_F, sizeof(double2) * 2 * (size_t)d.max_fields * (d.T + 1) * d.nlat))) {
     cudaGetLastError();
     return bail(fail(REXI_ENOMEM, "sh_plan_create: cudaMalloc failed: %s", cudaGetErrorString(e)));
@@ -672,8 +715,8 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
   if ((e = cudaMemcpy(p->d_mu, p->mu.data(), sizeof(double) * p->nh, cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(p->d_w, p->w.data(), sizeof(double) * p->nh, cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(p->d_wq, wq.data(), sizeof(double) * p->nh, cudaMemcpyHostToDevice)) ||
-      (e = cudaMemcpy(p->d_tw, tw.data(), sizeof(double2) * d.nlon, cudaMemcpyHostToDevice)) ||
-      (e = cudaMemcpy(p->d_tw32, tw32.data(), sizeof(float2) * d.nlon, cudaMemcpyHostToDevice)))
+      (e = cudaMemcpy(p->d_tw, tw.data(), sizeof(double2) * ntw, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(p->d_tw32, tw32.data(), sizeof(float2) * ntw, cudaMemcpyHostToDevice)))
     return bail(cuda_fail(e, "sh_plan_create: cudaMemcpy"));
   k_legendre_table<<<dim3((p->nh + 127) / 128, d.T + 1), 128, 0, p->stream>>>(p->d_mu, p->d_P, p->d_H, d.T, p->nh);
   if ((e = cudaGetLastError())) return bail(cuda_fail(e, "k_legendre_table"));
