@@ -76,7 +76,8 @@ int rexi_contour_select(double X, int N, double* p0, double* Xc);
  *   heavy_tau, prune_tau   as in rexi_plan_desc (< 0 / 0 select the defaults)
  *   heavy_align  16 (plans with max_batch >= 4: state pairs on half-warps) or 32
  *   cls          caller-owned array of N ints: 1 heavy (FP32 solve refined with a double-float
- *                residual; every solved pole of an FP64 plan), 0 light, -1 pruned
+ *                residual; every solved pole of an FP64 plan), 0 light, -1 pruned, 2 (mixed)
+ *                solved and summed in FP64 (gain above the default fp64_tau of rexi_plan_desc)
  *   pruned_gain  optional: summed gain of the pruned poles (bound on the relative energy-norm
  *                change of the result, Sec. 4.2 contour sum with those terms left out)
  * The gain of pole n is |w_n| / dist(z_n, [-iX, iX]).  Errors: REXI_EINVAL (bad arguments or a
@@ -133,6 +134,12 @@ typedef struct rexi_plan_desc {
                       /* M: U1 holds the full result on the owned orders and 0 elsewhere.    */
                       /* Either way the element-wise sum of U1 over the ranks (one all-reduce */
                       /* of 3 nlm complex128 per state) is the whole step                    */
+  double fp64_tau;    /* REXI_MIXED: poles whose gain exceeds fp64_tau (rounded up to whole   */
+                      /* 32-pole groups with the next-largest gains) are solved and summed    */
+                      /* in FP64, as by an FP64 plan: a refined FP32 solve and double-float   */
+                      /* partial sums keep about 2^-48 of a partial sum, too little for the   */
+                      /* cancellation of very large weights; <= 0: 5e4 (none at T255,         */
+                      /* dt = 3600 s; the largest 64 at T511, dt = 7200 s)                    */
 } rexi_plan_desc;
 
 /*
@@ -193,13 +200,14 @@ typedef struct rexi_plan_info {
   double X;               /* covered half-width used for the heavy classification        */
   int n_pruned;           /* poles left out by pruning                                   */
   double pruned_gain;     /* their summed gain (bound on the relative energy-norm change) */
+  int n_fp64;             /* REXI_MIXED: poles solved in FP64 (gain > fp64_tau)          */
 } rexi_plan_info;
 
 int rexi_plan_get_info(const rexi_plan* plan, rexi_plan_info* info);
 
 /* Copies the plan's poles and weights (2*N doubles each: the solved poles in the plan's
- * internal order, then the pruned ones) and per-pole classes (N ints: 1 heavy, 0 light,
- * -1 pruned) to host arrays; any pointer may be NULL. */
+ * internal order, then the pruned ones) and per-pole classes (N ints: 2 solved in FP64 (mixed
+ * plans), 1 heavy, 0 light, -1 pruned) to host arrays; any pointer may be NULL. */
 int rexi_plan_get_poles(const rexi_plan* plan, double* z, double* w, int* heavy);
 
 /*
@@ -278,6 +286,7 @@ typedef struct rexi_ragged_desc {
   double heavy_tau;    /* as in rexi_plan_desc                                               */
   void* stream;        /* cudaStream_t (graph capture needs a non-default stream)            */
   double prune_tau;    /* as in rexi_plan_desc, per instance pole set                        */
+  double fp64_tau;     /* as in rexi_plan_desc                                               */
 } rexi_ragged_desc;
 
 typedef struct rexi_instance {

@@ -98,6 +98,8 @@ struct Inst {
   double2 S0;      // sum_n w_n / z_n of its pole set
   int mrank = 0, msize = 0;  // zonal-order partition: with msize > 1 the state owns the orders m
                              // with m_pair(T, m) % msize == mrank; the others are written as 0
+  long long poff64 = 0;      // mixed plans: complex offset of the FP64 partial sums [Q64][3][nlm]
+  int Q64 = 0;               // of the poles solved in FP64 (0: none)
 };
 
 // pair index of zonal order m when the orders are dealt in pairs (m, T - m), which have equal

@@ -42,6 +42,7 @@ struct Fp64Args {
   const Inst* insts;
   D4* scratch;         // [warps][kmax][32]
   int ntiles, Ttab, kmax;
+  int alt = 0;         // 1: the FP64 class of a mixed plan (partial slots at Inst::poff64)
 };
 
 constexpr int FP64_WARPS = 4;
@@ -70,7 +71,7 @@ k_rexi_fp64(Fp64Args a) {
     const double2* bP = a.U0 + I.soff;
     const double2* bZ = bP + nlm;
     const double2* bD = bP + 2 * nlm;
-    double2* part = a.partial + I.poff + (size_t)tl.q * 3 * nlm;
+    double2* part = a.partial + (a.alt ? I.poff64 : I.poff) + (size_t)tl.q * 3 * nlm;
 
     for (int gi = 0; gi < tl.ng; ++gi) {
       const PoleD pd = a.poles[I.pole0 + (tl.g0 + gi) * 32 + lane];
@@ -152,14 +153,15 @@ inline size_t fp64_smem_bytes() {
 }
 
 // U1 = (bPhi S0 - Phibar S_wz, S_zeta, S_delta) for every coefficient of every instance,
-// summing the instance's Q partial slots in order.
+// summing the instance's Q partial slots in order, then (mixed plans with poles solved in FP64)
+// its Q64 FP64 slots in partial64, in FP64.
 // Partial slots hold FP64 complex sums (DF = false, FP64 plans) or double-float pairs
 // (DF = true, mixed plans: float4 = re.hi, re.lo, im.hi, im.lo, the same 16 bytes per entry).
 template <bool DF>
 static __global__ void k_rexi_finalize(const double2* __restrict__ U0, const double2* __restrict__ partial,
                                        double2* __restrict__ U1, const Inst* __restrict__ insts,
                                        const long long* __restrict__ ecum, int ninst, long long total,
-                                       double phibar) {
+                                       double phibar, const double2* __restrict__ partial64) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= total) return;
   const int i = inst_of(ecum, ninst, e);
@@ -206,6 +208,15 @@ static __global__ void k_rexi_finalize(const double2* __restrict__ U0, const dou
       sd = cadd(sd, p[nlm]);
       sw = cadd(sw, p[2 * nlm]);
       p += 3 * nlm;
+    }
+  }
+  if (I.Q64 > 0) {  // the FP64 class: sums whose cancellation double-float slots cannot carry
+    const double2* p64 = partial64 + I.poff64 + idx;
+    for (int q = 0; q < I.Q64; ++q) {
+      sz = cadd(sz, p64[0]);
+      sd = cadd(sd, p64[nlm]);
+      sw = cadd(sw, p64[2 * nlm]);
+      p64 += 3 * nlm;
     }
   }
   const double2 bp = U0[I.soff + idx];

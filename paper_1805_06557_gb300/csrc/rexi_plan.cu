@@ -54,6 +54,7 @@ struct PoleSet {
   std::vector<cplx> zp, wp; // poles left out (reported by rexi_plan_get_poles)
   std::vector<int> cls;     // per input pole: 1 heavy, 0 light, -1 pruned
   int pole0 = -1;           // position in the device arena (-1: not uploaded)
+  int n_fp64 = 0, g_fp64 = 0;  // mixed plans: poles solved in FP64 (whole 32-pole groups, after heavy)
   int mrank = 0, msize = 0; // zonal-order partition (msize > 1): only the owned orders get tiles
   bool owns(int m) const { return msize <= 1 || m_pair(T, m) % msize == mrank; }
 };
@@ -63,6 +64,14 @@ struct PoleSet {
 // relative error the mixed path is held to.  The far poles that pruning removes act on U0
 // nearly as the scalar w/z, so each field changes by about the same relative amount.
 constexpr double PRUNE_TAU_MIXED = 1e-10;
+
+// Default gain above which a mixed plan solves a pole in FP64 (the FP64 kernel, FP64 partial
+// sums).  The refined FP32 solve and the double-float partial slots keep about 2^-48 of the
+// magnitude of a 32-pole partial sum, up to the gain sum of the group times the state: at
+// gains <= 5e4 that stays within 2e-9 of the state.  Contours with a larger cancellation (T511
+// at dt = 7200 s: gains up to 2e7) move their largest poles to FP64; the T255 contour at
+// dt = 3600 s (largest gain 2.6e4) has none.
+constexpr double FP64_TAU_MIXED = 5e4;
 
 // Orders (and pads) the poles.  Every pole n has the gain g_n = |w_n| / dist(z_n, [-iX, iX]),
 // a bound on the energy-norm size of its term w_n (z_n - dt L)^-1 U0 relative to U0 (dt L is
@@ -74,7 +83,7 @@ constexpr double PRUNE_TAU_MIXED = 1e-10;
 // order, padding at the end.
 // MIXED: light poles first, heavy ones (gain > heavy_tau, padded to whole groups) last.
 int make_poleset(PoleSet& ps, int precision, int T, int N, double dt, double X, const cplx* z,
-                 const cplx* w, double heavy_tau, double prune_tau, int heavy_align) {
+                 const cplx* w, double heavy_tau, double prune_tau, int heavy_align, double fp64_tau = 0.0) {
   ps.T = T;
   ps.N = N;
   ps.dt = dt;
@@ -159,29 +168,41 @@ int make_poleset(PoleSet& ps, int precision, int T, int N, double dt, double X, 
   };
   if (precision == REXI_FP64) return all_heavy();
   const double tau = heavy_tau < 0 ? 1e-3 : heavy_tau;
-  int nh = 0;
+  // FP64 class: the poles of largest gain above fp64_tau, rounded up to whole 32-pole groups
+  // with the next-largest gains (conjugate pairs, of equal gain, stay together)
+  const double t64 = fp64_tau > 0 ? fp64_tau : FP64_TAU_MIXED;
+  int n64 = 0;
   for (int i = 0; i < nkeep; ++i)
+    if (gain[by_gain[i]] > t64) ++n64;
+  if (n64 > 0) n64 = std::min((n64 + 31) / 32 * 32, nkeep);
+  int nh = 0;
+  for (int i = n64; i < nkeep; ++i)
     if (gain[by_gain[i]] > tau) ++nh;
-  // heavy class: the poles of largest gain, rounded up to heavy_align (16 where tiles of state
-  // pairs take 16 poles per half-warp, 32 where most tiles carry one state) with the next-largest
-  // gains; the pole array pads it to 32 for tiles of one state
-  const int nh16 = std::min((nh + heavy_align - 1) / heavy_align * heavy_align, nkeep);
-  if (nh16 == nkeep && nkeep % 16 != 0) return all_heavy();  // everything heavy, padding at the end
-  const int nl = nkeep - nh16, lpad = (nl + 31) / 32 * 32, hpad = (nh16 + 31) / 32 * 32;
-  ps.Npad = lpad + hpad;
+  // heavy class: the next poles of largest gain, rounded up to heavy_align (16 where tiles of
+  // state pairs take 16 poles per half-warp, 32 where most tiles carry one state) with the
+  // next-largest gains; the pole array pads it to 32 for tiles of one state
+  const int nh16 = std::min((nh + heavy_align - 1) / heavy_align * heavy_align, nkeep - n64);
+  if (n64 == 0 && nh16 == nkeep && nkeep % 16 != 0) return all_heavy();  // everything heavy, padding at the end
+  const int nl = nkeep - n64 - nh16, lpad = (nl + 31) / 32 * 32, hpad = (nh16 + 31) / 32 * 32;
+  ps.Npad = lpad + hpad + n64;
   ps.ngroups = ps.Npad / 32;
   ps.z.clear();
   ps.w.clear();
   ps.heavy.clear();
-  std::vector<int> hv(N, 0);
-  for (int i = 0; i < nh16; ++i) hv[by_gain[i]] = 1;
+  std::vector<int> hv(N, 0);  // 1 heavy, 2 FP64
+  for (int i = 0; i < n64; ++i) hv[by_gain[i]] = 2;
+  for (int i = n64; i < n64 + nh16; ++i) hv[by_gain[i]] = 1;
   for (int n = 0; n < N; ++n)
     if (keep[n] && !hv[n]) push(z[n], w[n], 0);
   for (int i = nl; i < lpad; ++i) push(1.0, 0.0, 0);
   for (int n = 0; n < N; ++n)
-    if (hv[n]) push(z[n], w[n], 1);
+    if (hv[n] == 1) push(z[n], w[n], 1);
   for (int i = nh16; i < hpad; ++i) push(1.0, 0.0, 1);
+  for (int n = 0; n < N; ++n)
+    if (hv[n] == 2) push(z[n], w[n], 2);
   ps.n_heavy = nh16;
+  ps.n_fp64 = n64;
+  ps.g_fp64 = n64 / 32;
   ps.cls.assign(N, -1);
   for (int n = 0; n < N; ++n)
     if (keep[n]) ps.cls[n] = hv[n];
@@ -192,7 +213,8 @@ int make_poleset(PoleSet& ps, int precision, int T, int N, double dt, double X, 
 }
 
 int make_poleset_from_contour(PoleSet& ps, int precision, int T, int N, double dt, double X, double p0,
-                              double Xc, double heavy_tau, double prune_tau, int heavy_align) {
+                              double Xc, double heavy_tau, double prune_tau, int heavy_align,
+                              double fp64_tau = 0.0) {
   std::vector<double> zz(2 * N), ww(2 * N);
   int rc = rexi_coeffs(N, p0, Xc, 0, zz.data(), ww.data());
   if (rc) return rc;
@@ -201,7 +223,7 @@ int make_poleset_from_contour(PoleSet& ps, int precision, int T, int N, double d
     z[n] = cplx(zz[2 * n], zz[2 * n + 1]);
     w[n] = cplx(ww[2 * n], ww[2 * n + 1]);
   }
-  return make_poleset(ps, precision, T, N, dt, X, z.data(), w.data(), heavy_tau, prune_tau, heavy_align);
+  return make_poleset(ps, precision, T, N, dt, X, z.data(), w.data(), heavy_tau, prune_tau, heavy_align, fp64_tau);
 }
 
 int ranges_used(int G, int Q) {
@@ -231,6 +253,11 @@ struct Engine {
   int pole_cap = 0, pole_used = 0;
   double2* partial = nullptr;
   size_t partial_cap = 0;
+  // mixed plans with poles solved in FP64: their partial sums and the FP64 kernel's scratch,
+  // allocated when a pole set first needs them
+  double2* partial64 = nullptr;
+  size_t partial64_cap = 0;
+  D4* scratch64 = nullptr;
   void* rhs = nullptr;
   size_t rhs_cap = 0;  // elements
   void* scratch = nullptr;
@@ -258,6 +285,8 @@ struct LaunchSet {
   long long* ecum = nullptr;
   int ninst = 0, ntiles = 0, ntiles_light = 0, ntiles_quad = 0, ntiles_pair = 0;
   long long total = 0, partial_elems = 0;
+  int ntiles_fp64 = 0;           // the last tiles: FP64 class of mixed plans
+  long long partial64_elems = 0;
 };
 
 namespace {
@@ -272,7 +301,7 @@ void free_launch(LaunchSet& L) {
 void engine_free(Engine& e) {
   if (e.stream || e.tab64) cudaStreamSynchronize(e.stream);
   for (void* p : {(void*)e.tab64, (void*)e.tab32, (void*)e.tabdf, (void*)e.p64, (void*)e.p32, (void*)e.pdf,
-                  (void*)e.partial, (void*)e.rhs, (void*)e.scratch})
+                  (void*)e.partial, (void*)e.rhs, (void*)e.scratch, (void*)e.partial64, (void*)e.scratch64})
     cudaFree(p);
   for (auto& q : e.pending) {
     cudaEventDestroy(q.a);
@@ -369,6 +398,14 @@ int engine_init(Engine& e, int precision, int Ttab, double omega, double radius,
         (ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_h2b, k_rexi_heavy<2, true>, MIX_WARPS * 32, hsm2)))
       return cuda_fail(ce, "occupancy(k_rexi_heavy)");
     per_h2 = std::min(per_h2, per_h2b);  // one grid size serves both tile forms of state pairs
+    {  // the FP64 class of a mixed plan runs on the FP64 kernel
+      const size_t smem = fp64_smem_bytes();
+      int per64 = 0;
+      if ((ce = cudaFuncSetAttribute(k_rexi_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) ||
+          (ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per64, k_rexi_fp64, FP64_WARPS * 32, smem)))
+        return cuda_fail(ce, "k_rexi_fp64 (FP64 class)");
+      e.grid_fp64 = e.nsm * std::max(1, std::min(per64, 2));
+    }
     e.grid_light = e.nsm * std::max(1, std::min(per_l, 4));
     e.grid_heavy = e.nsm * std::max(1, std::min(per_h, 6));
     e.grid_heavy2 = e.nsm * std::max(1, std::min(per_h2, 4));
@@ -385,6 +422,33 @@ int engine_init(Engine& e, int precision, int Ttab, double omega, double radius,
 }
 
 // Appends a pole set to the arena (scaled by 1/dt: z' = z/dt, w' = w/dt, w/z, 1/z', Phibar/z').
+// The FP64-class buffers of a mixed engine, grown to `p64_elems` partial-sum entries (after the
+// stream's queued work, which may still use the old ones); the scratch is made once.
+int engine_ensure_fp64(Engine& e, size_t p64_elems) {
+  cudaError_t ce;
+  if (p64_elems > e.partial64_cap) {
+    if ((ce = cudaStreamSynchronize(e.stream))) return cuda_fail(ce, "FP64 class: stream");
+    cudaFree(e.partial64);
+    e.partial64 = nullptr;
+    e.partial64_cap = 0;
+    if ((ce = cudaMalloc(&e.partial64, sizeof(double2) * p64_elems))) {
+      cudaGetLastError();
+      return fail(REXI_ENOMEM, "FP64 class: partial sums (%zu entries)", p64_elems);
+    }
+    e.partial64_cap = p64_elems;
+    e.workspace += (long long)(sizeof(double2) * p64_elems);
+  }
+  if (p64_elems > 0 && !e.scratch64) {
+    const size_t bytes = sizeof(D4) * (size_t)e.grid_fp64 * FP64_WARPS * e.kmax * 32;
+    if ((ce = cudaMalloc(&e.scratch64, bytes))) {
+      cudaGetLastError();
+      return fail(REXI_ENOMEM, "FP64 class: elimination scratch");
+    }
+    e.workspace += (long long)bytes;
+  }
+  return REXI_OK;
+}
+
 // the device forms of a pole set: FP64, FP32 and double-float constants of every (padded) pole
 void pack_poles(const Engine& e, const PoleSet& ps, PoleD* pd, PoleF* pf, PoleDF* pq) {
   for (int i = 0; i < ps.Npad; ++i) {
@@ -423,9 +487,15 @@ struct InstReq {
 // Builds the host launch description: per-instance descriptors (partial / rhs offsets),
 // tiles sorted by cost (light first, then heavy), element prefix sums.  Pole groups are cut
 // into ranges so that the launch has about qmul tiles per resident warp.
+struct LaunchExtra {  // the FP64 class of mixed plans
+  int ntiles_fp64 = 0;
+  long long partial64_elems = 0;
+};
+
 void build_launch(const Engine& e, const std::vector<InstReq>& req, std::vector<Inst>& insts,
                   std::vector<Tile>& tiles, std::vector<long long>& ecum, int& ntiles_light,
-                  long long& partial_elems, int& ntiles_quad, int& ntiles_pair, int qmul = 4) {
+                  long long& partial_elems, int& ntiles_quad, int& ntiles_pair, int qmul = 4,
+                  LaunchExtra* extra = nullptr) {
   insts.clear();
   tiles.clear();
   ecum.clear();
@@ -473,8 +543,8 @@ void build_launch(const Engine& e, const std::vector<InstReq>& req, std::vector<
     Ql_glob = std::min(Ql_glob, e.max_q);
     Qh_glob = std::min(Qh_glob, e.max_q);
   }
-  long long poff = 0, roff = 0, ec = 0;
-  std::vector<Tile> light, heavy, heavyQ, heavyP;
+  long long poff = 0, roff = 0, ec = 0, poff64 = 0;
+  std::vector<Tile> light, heavy, heavyQ, heavyP, fp64t;
   for (size_t i = 0; i < req.size(); ++i) {
     const PoleSet& ps = *req[i].ps;
     const int T = ps.T, nlm = (T + 1) * (T + 2) / 2;
@@ -497,6 +567,15 @@ void build_launch(const Engine& e, const std::vector<InstReq>& req, std::vector<
     I.S0 = make_double2(ps.S0.real(), ps.S0.imag());
     I.mrank = ps.mrank;
     I.msize = ps.msize;
+    // FP64 class: one 32-pole group per range (its own FP64 partial slots)
+    const int q64 = e.precision == REXI_MIXED ? ps.g_fp64 : 0;
+    I.poff64 = poff64;
+    I.Q64 = q64;
+    for (int g = 0; g < q64; ++g)
+      for (int m = 0; m <= T; ++m)
+        for (int c = 0; c < 2 && ps.owns(m); ++c)
+          fp64t.push_back(Tile{m, c, ps.g_light + ps.g_heavy + g, 1, g, 2, (T + 1 - m) * 8, (int)i, -1, -1, -1});
+    poff64 += (long long)q64 * 3 * nlm;
     insts.push_back(I);
     ecum.push_back(ec);
     auto add = [&](int gbase, int G, int Q, int qbase, int hv, std::vector<Tile>& out) {
@@ -547,6 +626,7 @@ void build_launch(const Engine& e, const std::vector<InstReq>& req, std::vector<
   std::stable_sort(heavyQ.begin(), heavyQ.end(), bycost);
   std::stable_sort(heavyP.begin(), heavyP.end(), bycost);
   std::stable_sort(heavy.begin(), heavy.end(), bycost);
+  std::stable_sort(fp64t.begin(), fp64t.end(), bycost);
   ntiles_light = (int)light.size();
   ntiles_quad = (int)heavyQ.size();
   ntiles_pair = (int)heavyP.size();
@@ -554,12 +634,17 @@ void build_launch(const Engine& e, const std::vector<InstReq>& req, std::vector<
   tiles.insert(tiles.end(), heavyQ.begin(), heavyQ.end());
   tiles.insert(tiles.end(), heavyP.begin(), heavyP.end());
   tiles.insert(tiles.end(), heavy.begin(), heavy.end());
+  tiles.insert(tiles.end(), fp64t.begin(), fp64t.end());  // last: the FP64 class
   partial_elems = poff;
+  if (extra) {
+    extra->ntiles_fp64 = (int)fp64t.size();
+    extra->partial64_elems = poff64;
+  }
 }
 
 int upload_launch(LaunchSet& L, const std::vector<Inst>& insts, const std::vector<Tile>& tiles,
                   const std::vector<long long>& ecum, int ntiles_light, int ntiles_quad, int ntiles_pair,
-                  long long partial_elems) {
+                  long long partial_elems, const LaunchExtra& extra = LaunchExtra()) {
   free_launch(L);
   cudaError_t ce;
   if ((ce = cudaMalloc(&L.insts, sizeof(Inst) * std::max<size_t>(insts.size(), 1))) ||
@@ -579,6 +664,8 @@ int upload_launch(LaunchSet& L, const std::vector<Inst>& insts, const std::vecto
   L.ntiles_pair = ntiles_pair;
   L.total = ecum.back();
   L.partial_elems = partial_elems;
+  L.ntiles_fp64 = extra.ntiles_fp64;
+  L.partial64_elems = extra.partial64_elems;
   return REXI_OK;
 }
 
@@ -644,7 +731,7 @@ int engine_launch(Engine& e, const LaunchSet& L, const double2* U0, double2* U1)
     a.rhsdf = rdf;
     a.scratch = e.scratch;
     a.ntiles_light = L.ntiles_light;
-    a.ntiles_heavy = L.ntiles - L.ntiles_light;
+    a.ntiles_heavy = L.ntiles - L.ntiles_light - L.ntiles_fp64;
     a.Ttab = e.Ttab;
     a.kmax = e.kmax;
     a.nseg_max = e.nseg_max;
@@ -680,6 +767,25 @@ int engine_launch(Engine& e, const LaunchSet& L, const double2* U0, double2* U1)
       k_rexi_heavy<1, false><<<e.grid_heavy, MIX_WARPS * 32, heavy_smem_bytes<1>(), e.stream>>>(a, t0, n1);
       prof_end(e, h);
     }
+    if (L.ntiles_fp64) {  // the FP64 class: the FP64 kernel on its tiles, FP64 partial slots
+      if ((long long)e.partial64_cap < L.partial64_elems || !e.scratch64)
+        return fail(REXI_EINVAL, "internal: FP64-class buffers too small");
+      Fp64Args f;
+      f.U0 = U0;
+      f.partial = e.partial64;
+      f.tab = e.tab64;
+      f.poles = e.p64;
+      f.tiles = L.tiles + (L.ntiles - L.ntiles_fp64);
+      f.insts = L.insts;
+      f.scratch = e.scratch64;
+      f.ntiles = L.ntiles_fp64;
+      f.Ttab = e.Ttab;
+      f.kmax = e.kmax;
+      f.alt = 1;
+      h = prof_begin(e, 1);
+      k_rexi_fp64<<<e.grid_fp64, FP64_WARPS * 32, fp64_smem_bytes(), e.stream>>>(f);
+      prof_end(e, h);
+    }
     if (a.ntiles_light) {
       h = prof_begin(e, 2, ls);
       k_rexi_light<<<e.grid_light, MIX_WARPS * 32, 0, ls>>>(a);
@@ -695,10 +801,12 @@ int engine_launch(Engine& e, const LaunchSet& L, const double2* U0, double2* U1)
   const int hf = prof_begin(e, 4);
   if (e.precision == REXI_FP64)
     k_rexi_finalize<false><<<(unsigned)((L.total + 255) / 256), 256, 0, e.stream>>>(U0, e.partial, U1, L.insts,
-                                                                                   L.ecum, L.ninst, L.total, e.phibar);
+                                                                                   L.ecum, L.ninst, L.total, e.phibar,
+                                                                                   nullptr);
   else
     k_rexi_finalize<true><<<(unsigned)((L.total + 255) / 256), 256, 0, e.stream>>>(U0, e.partial, U1, L.insts,
-                                                                                  L.ecum, L.ninst, L.total, e.phibar);
+                                                                                  L.ecum, L.ninst, L.total, e.phibar,
+                                                                                  e.partial64);
   prof_end(e, hf);
   ce = cudaGetLastError();
   if (ce != cudaSuccess) return cuda_fail(ce, "finalize kernel launch");
@@ -811,7 +919,8 @@ extern "C" int rexi_plan_create(const rexi_plan_desc* desc, rexi_plan** out) {
     const double base = prune_tau > 0 ? prune_tau : (prune_tau == 0 && d.precision == REXI_MIXED ? 1e-10 : -1.0);
     prune_tau = base > 0 ? base / d.part_size : base;
   }
-  rc = make_poleset(p->ps, d.precision, d.T, p->d.N, d.dt, X, z.data(), w.data(), d.heavy_tau, prune_tau, halign);
+  rc = make_poleset(p->ps, d.precision, d.T, p->d.N, d.dt, X, z.data(), w.data(), d.heavy_tau, prune_tau, halign,
+                    d.fp64_tau);
   if (rc) return bail(rc);
   if (d.part_mode == REXI_PART_M && d.part_size > 1) {
     p->ps.mrank = d.part_rank;
@@ -821,7 +930,7 @@ extern "C" int rexi_plan_create(const rexi_plan_desc* desc, rexi_plan** out) {
                    (size_t)p->nlm * d.max_batch);
   if (rc) return bail(rc);
   // largest partial-sum footprint over the batch sizes a call may use
-  size_t maxp = 0;
+  size_t maxp = 0, maxp64 = 0;
   for (int B = 1; B <= d.max_batch; ++B) {
     std::vector<InstReq> req;
     for (int b = 0; b < B; ++b) req.push_back(InstReq{&p->ps, (long long)b * 3 * p->nlm});
@@ -830,9 +939,12 @@ extern "C" int rexi_plan_create(const rexi_plan_desc* desc, rexi_plan** out) {
     std::vector<long long> ec;
     int ntl, ntq, ntp;
     long long pe;
-    build_launch(p->e, req, I, Tl, ec, ntl, pe, ntq, ntp);
+    LaunchExtra x;
+    build_launch(p->e, req, I, Tl, ec, ntl, pe, ntq, ntp, 4, &x);
     maxp = std::max(maxp, (size_t)pe);
+    maxp64 = std::max(maxp64, (size_t)x.partial64_elems);
   }
+  if (maxp64 > 0 && (rc = engine_ensure_fp64(p->e, maxp64))) return bail(rc);
   cudaFree(p->e.partial);
   p->e.partial = nullptr;
   p->e.partial_cap = maxp;
@@ -865,9 +977,10 @@ static int plan_launchset(rexi_plan* p, int B, LaunchSet** out) {
     std::vector<long long> ec;
     int ntl, ntq, ntp;
     long long pe;
-    build_launch(p->e, req, I, Tl, ec, ntl, pe, ntq, ntp);
+    LaunchExtra x;
+    build_launch(p->e, req, I, Tl, ec, ntl, pe, ntq, ntp, 4, &x);
     LaunchSet L;
-    int rc = upload_launch(L, I, Tl, ec, ntl, ntq, ntp, pe);
+    int rc = upload_launch(L, I, Tl, ec, ntl, ntq, ntp, pe, x);
     if (rc) {
       free_launch(L);
       return rc;
@@ -956,6 +1069,7 @@ extern "C" int rexi_plan_get_info(const rexi_plan* p, rexi_plan_info* info) {
   info->X = p->ps.X;
   info->n_pruned = p->ps.n_pruned;
   info->pruned_gain = p->ps.pruned_gain;
+  info->n_fp64 = p->ps.n_fp64;
   return REXI_OK;
 }
 
@@ -1129,9 +1243,12 @@ static int ragged_rebuild(rexi_ragged* r) {
   std::vector<long long> ec;
   int ntl, ntq, ntp;
   long long pe;
-  build_launch(r->e, req, I, Tl, ec, ntl, pe, ntq, ntp, r->qmul);
+  LaunchExtra x;
+  build_launch(r->e, req, I, Tl, ec, ntl, pe, ntq, ntp, r->qmul, &x);
   if (pe > (long long)r->e.partial_cap) return fail(REXI_EBUSY, "rexi_ragged: partial-sum workspace exceeded");
   Engine& e = r->e;
+  int rce = x.partial64_elems > 0 ? engine_ensure_fp64(e, (size_t)x.partial64_elems) : REXI_OK;
+  if (rce) return rce;
   cudaError_t ce;
   // device descriptors: grow (after the stream's queued work) when this set needs more room
   if (I.size() > r->cap_inst || Tl.size() > r->cap_tiles || ec.size() > r->cap_ecum) {
@@ -1202,6 +1319,8 @@ static int ragged_rebuild(rexi_ragged* r) {
   r->L.ntiles_pair = ntp;
   r->L.total = ec.back();
   r->L.partial_elems = pe;
+  r->L.ntiles_fp64 = x.ntiles_fp64;
+  r->L.partial64_elems = x.partial64_elems;
   return REXI_OK;
 }
 
@@ -1258,7 +1377,7 @@ extern "C" int rexi_ragged_set(rexi_ragged* r, int ninst, const rexi_instance* i
     const double X = rexi_spectrum_bound(q.T, q.dt, r->d.omega, r->d.radius, r->d.phibar);
     // ragged sets: most instances have a pole set of their own and run tiles of one state
     int rc = make_poleset_from_contour(ps, r->d.precision, q.T, q.N, q.dt, X, q.p0, q.Xc, r->d.heavy_tau,
-                                       r->d.prune_tau, 32);
+                                       r->d.prune_tau, 32, r->d.fp64_tau);
     if (rc) return rc;
     if (r->e.pole_used + ps.Npad > r->e.pole_cap) return REXI_EBUSY;
     // a place in the pole arena now; the upload goes with this set's descriptors (stream order:

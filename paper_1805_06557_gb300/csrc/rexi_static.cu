@@ -201,7 +201,7 @@ extern "C" int rexi_step_fp64_static(int T, int N, double dt, double omega, doub
   a.kmax = ST_KMAX;
   k_rexi_fp64<<<ST_BLOCKS, FP64_WARPS * 32, fp64_smem_bytes(), s>>>(a);
   k_rexi_finalize<false><<<(nlm + 255) / 256, 256, 0, s>>>((const double2*)U0, part, (double2*)U1, inst, ecum, 1,
-                                                    (long long)nlm, phibar);
+                                                    (long long)nlm, phibar, nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "rexi_step_fp64_static launch");
   return REXI_OK;

@@ -47,7 +47,8 @@ class PlanDesc(ctypes.Structure):
                 ("z", _dp), ("w", _dp), ("precision", ctypes.c_int),
                 ("heavy_tau", ctypes.c_double), ("max_batch", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("prune_tau", ctypes.c_double),
-                ("part_mode", ctypes.c_int), ("part_rank", ctypes.c_int), ("part_size", ctypes.c_int)]
+                ("part_mode", ctypes.c_int), ("part_rank", ctypes.c_int), ("part_size", ctypes.c_int),
+                ("fp64_tau", ctypes.c_double)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -57,7 +58,7 @@ class PlanInfo(ctypes.Structure):
                 ("grid_fp64", ctypes.c_int), ("grid_light", ctypes.c_int),
                 ("grid_heavy", ctypes.c_int), ("workspace_bytes", ctypes.c_longlong),
                 ("s0_re", ctypes.c_double), ("s0_im", ctypes.c_double), ("X", ctypes.c_double),
-                ("n_pruned", ctypes.c_int), ("pruned_gain", ctypes.c_double)]
+                ("n_pruned", ctypes.c_int), ("pruned_gain", ctypes.c_double), ("n_fp64", ctypes.c_int)]
 
 
 _lib.rexi_last_error.restype = ctypes.c_char_p
@@ -146,7 +147,7 @@ class RaggedDesc(ctypes.Structure):
                 ("max_elems", ctypes.c_longlong), ("omega", ctypes.c_double),
                 ("radius", ctypes.c_double), ("phibar", ctypes.c_double),
                 ("precision", ctypes.c_int), ("heavy_tau", ctypes.c_double),
-                ("stream", ctypes.c_void_p), ("prune_tau", ctypes.c_double)]
+                ("stream", ctypes.c_void_p), ("prune_tau", ctypes.c_double), ("fp64_tau", ctypes.c_double)]
 
 
 class Instance(ctypes.Structure):
@@ -171,13 +172,14 @@ class RaggedPlan:
     """One REXI launch over states of different truncation, time step and pole count."""
 
     def __init__(self, Tmax, max_inst, max_poles, max_elems, omega, radius, phibar,
-                 precision="mixed", heavy_tau=-1.0, prune_tau=0.0, stream=None):
+                 precision="mixed", heavy_tau=-1.0, prune_tau=0.0, stream=None, fp64_tau=0.0):
         d = RaggedDesc()
         d.Tmax, d.max_inst, d.max_poles, d.max_elems = int(Tmax), int(max_inst), int(max_poles), int(max_elems)
         d.omega, d.radius, d.phibar = float(omega), float(radius), float(phibar)
         d.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
         d.heavy_tau = float(heavy_tau)
         d.prune_tau = float(prune_tau)
+        d.fp64_tau = float(fp64_tau)
         d.stream = ctypes.c_void_p(_stream_handle(stream))
         h = ctypes.c_void_p()
         _check(_lib.rexi_ragged_create(ctypes.byref(d), ctypes.byref(h)))
@@ -327,7 +329,7 @@ class Plan:
 
     def __init__(self, T, N, dt, omega, radius, phibar, p0=None, Xc=None, z=None, w=None,
                  precision="fp64", heavy_tau=-1.0, max_batch=1, stream=None, prune_tau=0.0,
-                 partition=None):
+                 partition=None, fp64_tau=0.0):
         """partition: None, or (mode, rank, size) with mode "poles" or "m": this plan computes
         rank's share of the step (include/rexi.h part_mode); step_allreduce completes it."""
         d = PlanDesc()
@@ -347,6 +349,7 @@ class Plan:
         d.max_batch = int(max_batch)
         d.stream = ctypes.c_void_p(_stream_handle(stream))
         d.prune_tau = float(prune_tau)
+        d.fp64_tau = float(fp64_tau)
         if partition is not None:
             mode, rank, size = partition
             d.part_mode, d.part_rank, d.part_size = _PART[mode], int(rank), int(size)

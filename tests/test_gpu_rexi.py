@@ -370,3 +370,35 @@ def test_partitioned_plans_sum_to_the_whole_step(env, mode, prec, size):
         err = orx.rel_l2(tot[b], _PART_REF[b], T)
         tol = fp64_tol(z, w, X) if prec == "fp64" else 1e-8
         assert np.all(err < tol), (b, err, tol)
+
+
+def test_mixed_fp64_class_at_large_amplification(env):
+    """T511 with 2048 poles at dt = 7200 s on the contour of the library's search (p0 = 20,
+    amplification 2.4e8, gains up to 2e7): the mixed plan solves its 64 largest-gain poles in
+    FP64, so it is as accurate as the FP64 plan (within a factor of 2 per field, on sampled
+    zonal orders against the oracle); without that class, a refined FP32 solve and
+    double-float partial sums (about 2^-48 of a partial sum) leave it more than 10x worse."""
+    torch, rexi = env
+    T, N, dt = 511, 2048, 7200.0
+    X = orx.spectrum_bound(T, dt, OM, A, PB)
+    p0, Xc = rexi.contour_select(X, N)
+    z, w = oc.rexi_coefficients(N, p0, Xc)
+    U0 = syn.gaussian_state(T, 7)
+    ms = [0, 1, 255, 511]
+    ref = orx.rexi_step(U0, T, dt, OM, A, PB, z, w, m_list=ms)
+    errs = {}
+    for name, kw in (("fp64", dict(precision="fp64")), ("mixed", dict(precision="mixed")),
+                     ("mixed_b4", dict(precision="mixed", max_batch=4)),
+                     ("mixed_no_fp64_class", dict(precision="mixed", fp64_tau=1e300))):
+        kw = dict(kw)
+        B = kw.pop("max_batch", 1)
+        prec = kw.pop("precision")
+        out, info = run_plan(env, T, N, dt, np.stack([U0] * B), prec, p0, Xc, **kw)
+        errs[name] = masked_rel(out[0], ref, T, ms)
+        if prec == "mixed" and "fp64_tau" not in kw:
+            assert info["n_fp64"] == 64, info
+    tol = fp64_tol(z, w, X)
+    assert np.all(errs["fp64"] < tol), errs
+    for name in ("mixed", "mixed_b4"):
+        assert np.all(errs[name] < np.maximum(1e-8, 2 * errs["fp64"])), errs
+    assert np.max(errs["mixed_no_fp64_class"]) > 10 * np.max(errs["mixed"]), errs
