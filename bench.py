@@ -405,7 +405,9 @@ def _rel_fields(a, b, T):
 
 def sh_transforms(torch, rexi, fp64_peak, T=511, nlat=768, nlon=1536, nf=2, reps=5):
     """Synthesis and analysis of nf scalar fields and of one vector field (psi/chi -> U, V;
-    A, B -> div, curl) at T511 on the 768 x 1536 Gauss grid in every Legendre precision.
+    A, B -> div, curl), and the nonlinear term's one-pass combinations (2 scalar fields + 1
+    vector pair synthesised, 2 vector pairs + 1 scalar field analysed), at T511 on the
+    768 x 1536 Gauss grid in every Legendre precision.
     Per-stage device times from the plan's event profile; the roofline of the Legendre
     contraction is HBM-bound on its table (algorithmic bytes: the nlat/2 x nlm table read
     once per transform -- P for scalar transforms, P and H for vector transforms -- in the
@@ -425,16 +427,17 @@ def sh_transforms(torch, rexi, fp64_peak, T=511, nlat=768, nlon=1536, nf=2, reps
     back = torch.empty_like(spec)
     U = torch.empty(1, nlat, nlon, dtype=torch.float64, device="cuda")
     V = torch.empty_like(U)
-    dv = torch.empty(1, nlm, dtype=torch.complex128, device="cuda")
+    dv = torch.empty(2, nlm, dtype=torch.complex128, device="cuda")
     cu = torch.empty_like(dv)
     out = {"workload": "T%d, %d x %d Gauss grid, %d scalar fields + 1 vector field, n^-1.5 "
                        "spectra (seed 4)" % (T, nlat, nlon, nf), "hbm_peak_gbs": hbm}
     ref = {}
     for prec in ("fp64", "tf32", "bf16", "tf32x3"):
-        p = rexi.ShPlan(T, nlat, nlon, syn.RADIUS, prec, max_fields=nf)
+        p = rexi.ShPlan(T, nlat, nlon, syn.RADIUS, prec, max_fields=3)
         eb = {"fp64": 8, "tf32": 4, "bf16": 2, "tf32x3": 8}[prec]   # split TF32: hi and lo words
         res = {}
-        for kind in ("synthesis", "analysis", "synthesis_uv", "analysis_divcurl"):
+        for kind in ("synthesis", "analysis", "synthesis_uv", "analysis_divcurl", "synthesis_mixed",
+                     "analysis_mixed"):
             def call():
                 if kind == "synthesis":
                     p.synthesis(spec, grid, nf)
@@ -442,8 +445,12 @@ def sh_transforms(torch, rexi, fp64_peak, T=511, nlat=768, nlon=1536, nf=2, reps
                     p.analysis(grid, back, nf)
                 elif kind == "synthesis_uv":
                     p.synthesis_uv(spec[:1], spec[1:2], U, V, 1)
-                else:
+                elif kind == "analysis_divcurl":
                     p.analysis_divcurl(grid[:1], grid[1:2], dv, cu, 1)
+                elif kind == "synthesis_mixed":   # the nonlinear term's: 2 scalar + 1 vector
+                    p.synthesis_mixed(spec, grid, 2, spec[:1], spec[1:2], U, V, 1)
+                else:                             # 2 vector pairs + 1 scalar
+                    p.analysis_mixed(grid, grid, dv, cu, 2, grid[:1], back[:1], 1)
             for _ in range(2):
                 call()
             p.set_profiling(True)
@@ -459,8 +466,10 @@ def sh_transforms(torch, rexi, fp64_peak, T=511, nlat=768, nlon=1536, nf=2, reps
             p.set_profiling(False)
             total = e0.elapsed_time(e1) / reps
             vec = kind in ("synthesis_uv", "analysis_divcurl")
-            ntab = 2 if vec else 1        # P, or P and H
-            narr = 2 if vec else nf       # spectral arrays = Fourier arrays = grids
+            mixed = kind.endswith("_mixed")
+            ntab = 2 if (vec or mixed) else 1   # P, or P and H
+            # spectral arrays = Fourier arrays = grids: scalar fields + 2 per vector pair
+            narr = 2 if vec else (4 if kind == "synthesis_mixed" else 5 if mixed else nf)
             leg_ms = sum(prof[k][0] for k in ("legendre_fp64", "tc_pack", "tc_gemm", "tc_epilogue")) / reps
             gemm_ms = (prof["legendre_fp64"][0] if prec == "fp64" else prof["tc_gemm"][0]) / reps
             tab_bytes = ntab * nh * nlm * eb

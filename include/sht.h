@@ -79,6 +79,23 @@ int sh_synthesis_uv(sh_plan* plan, const void* psi, const void* chi, void* U, vo
 int sh_analysis_divcurl(sh_plan* plan, const void* A, const void* B, void* div, void* curl,
                         int nfields);
 
+/* Scalar and vector synthesis in one pass (the transforms of the nonlinear term share
+ * their inputs' zonal orders): nfields scalar spectra spec -> grid as sh_synthesis, and nvec
+ * (psi, chi) pairs -> (U, V) as sh_synthesis_uv, with one longitude-FFT launch for all
+ * 2 nvec + nfields grids.  The tensor-core precisions contract the scalar fields beside the
+ * vector pairs' columns, so the associated Legendre table Pt is read once (Ht once) instead
+ * of once per transform; the results equal those of the separate calls.  Needs nfields >= 1,
+ * nvec >= 1 and nfields + 2 nvec <= 2 max_fields.  Errors: REXI_EINVAL, REXI_ECUDA. */
+int sh_synthesis_mixed(sh_plan* plan, const void* spec, void* grid, int nfields, const void* psi,
+                       const void* chi, void* U, void* V, int nvec);
+
+/* Divergence and curl of nvec vector fields (A, B) as sh_analysis_divcurl, and the analysis
+ * of nfields scalar grids as sh_analysis, in one pass: one longitude-FFT launch, and for the
+ * tensor-core precisions one read of each table.  Same limits and errors as
+ * sh_synthesis_mixed. */
+int sh_analysis_mixed(sh_plan* plan, const void* A, const void* B, void* div, void* curl, int nvec,
+                      const void* grid, void* spec, int nfields);
+
 /* Synchronises the plan stream; returns REXI_ETIMEOUT if a tensor-core kernel's bounded
  * wait on its copy / MMA barriers gave up since the plan was created (its results are then
  * invalid), REXI_ECUDA on a CUDA error, REXI_OK otherwise. */

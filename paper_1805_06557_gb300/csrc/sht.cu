@@ -20,7 +20,6 @@
 
 #include "../../include/sht.h"
 #include "common.cuh"
-#include "sht_fused.cuh"
 #include "sht_tc.cuh"
 
 namespace rexi {
@@ -889,32 +888,52 @@ extern "C" int sh_analysis_divcurl(sh_plan* p, const void* A, const void* B, voi
   return launched("sh_analysis_divcurl");
 }
 
-int sh_synth_fused(sh_plan* p, const double2* S, int nf, double* G, const double2* psi, const double2* chi, int nfv,
-                   double* U, double* V) {
-  if (!p || nf < 1 || nfv < 1 || nf > p->d.max_fields || nfv > p->d.max_fields || nf + 2 * nfv > 2 * p->d.max_fields)
-    return fail(REXI_EINVAL, "fused synthesis: %d scalar + 2 x %d vector fields exceed the plan's work slots", nf, nfv);
+static int check_mixed(sh_plan* p, int nf, int nfv, const char* who) {
+  if (!p) return fail(REXI_EINVAL, "%s: null plan", who);
+  if (nf < 1 || nfv < 1 || nf > p->d.max_fields || nfv > p->d.max_fields || nf + 2 * nfv > 2 * p->d.max_fields)
+    return fail(REXI_EINVAL, "%s: %d scalar + 2 x %d vector fields exceed the plan's %d work slots", who, nf, nfv,
+                2 * p->d.max_fields);
+  return REXI_OK;
+}
+
+extern "C" int sh_synthesis_mixed(sh_plan* p, const void* spec, void* grid, int nf, const void* psi, const void* chi,
+                                  void* U, void* V, int nfv) {
+  int rc = check_mixed(p, nf, nfv, "sh_synthesis_mixed");
+  if (rc) return rc;
+  if (!spec || !grid || !psi || !chi || !U || !V) return fail(REXI_EINVAL, "sh_synthesis_mixed: null argument");
   double2* F = fslot(p, 0);
   double2* FU = fslot(p, nf);
   double2* FV = fslot(p, nf + nfv);
-  int rc;
-  if ((rc = leg_synth(p, S, F, nf))) return rc;
-  if ((rc = leg_synth_uv(p, psi, chi, FU, FV, nfv))) return rc;
-  launch_fft_synth(p, make_segs({{F, G, nf}, {FU, U, nfv}, {FV, V, nfv}}));
-  return launched("fused synthesis");
+  if (p->tc) {
+    if ((rc = tc_leg_synth_mixed(p->tc, (const double2*)psi, (const double2*)chi, FU, FV, nfv, (const double2*)spec, F,
+                                 nf, 1.0 / p->d.radius, p->stream)))
+      return rc;
+  } else {
+    if ((rc = leg_synth(p, (const double2*)spec, F, nf))) return rc;
+    if ((rc = leg_synth_uv(p, (const double2*)psi, (const double2*)chi, FU, FV, nfv))) return rc;
+  }
+  launch_fft_synth(p, make_segs({{F, (double*)grid, nf}, {FU, (double*)U, nfv}, {FV, (double*)V, nfv}}));
+  return launched("sh_synthesis_mixed");
 }
 
-int sh_anal_fused(sh_plan* p, const double* A, const double* B, int nfv, double2* dv, double2* cu, const double* G,
-                  int nf, double2* S) {
-  if (!p || nf < 1 || nfv < 1 || nf > p->d.max_fields || nfv > p->d.max_fields || nf + 2 * nfv > 2 * p->d.max_fields)
-    return fail(REXI_EINVAL, "fused analysis: 2 x %d vector + %d scalar fields exceed the plan's work slots", nfv, nf);
+extern "C" int sh_analysis_mixed(sh_plan* p, const void* A, const void* B, void* dv, void* cu, int nfv,
+                                 const void* grid, void* spec, int nf) {
+  int rc = check_mixed(p, nf, nfv, "sh_analysis_mixed");
+  if (rc) return rc;
+  if (!A || !B || !dv || !cu || !grid || !spec) return fail(REXI_EINVAL, "sh_analysis_mixed: null argument");
   double2* FA = fslot(p, 0);
   double2* FB = fslot(p, nfv);
   double2* FG = fslot(p, 2 * nfv);
-  launch_fft_anal(p, make_segs({{FA, (double*)A, nfv}, {FB, (double*)B, nfv}, {FG, (double*)G, nf}}));
-  int rc;
-  if ((rc = leg_anal_divcurl(p, FA, FB, dv, cu, nfv))) return rc;
-  if ((rc = leg_anal(p, FG, S, nf))) return rc;
-  return launched("fused analysis");
+  launch_fft_anal(p, make_segs({{FA, (double*)A, nfv}, {FB, (double*)B, nfv}, {FG, (double*)grid, nf}}));
+  if (p->tc) {
+    if ((rc = tc_leg_anal_mixed(p->tc, FA, FB, (double2*)dv, (double2*)cu, nfv, FG, (double2*)spec, nf,
+                                1.0 / p->d.radius, p->stream)))
+      return rc;
+  } else {
+    if ((rc = leg_anal_divcurl(p, FA, FB, (double2*)dv, (double2*)cu, nfv))) return rc;
+    if ((rc = leg_anal(p, FG, (double2*)spec, nf))) return rc;
+  }
+  return launched("sh_analysis_mixed");
 }
 
 extern "C" int sh_plan_check(sh_plan* p) {

@@ -66,22 +66,29 @@ struct Job {
 // precision modes of the GEMM (template parameter PM)
 constexpr int PM_TF32 = 0, PM_BF16 = 1, PM_TF32X3 = 2;
 
+// One call contracts nfv vector pairs and nfs scalar fields against the same table reads:
+// columns [0, 8 nfv) hold the vector pairs (8 each), columns from 8 nfv the scalar fields (4
+// each), so that every 8-column group is one vector pair or two scalar fields.
 struct GemmArgs {
   const unsigned char* tabP;
   const unsigned char* tabH;
-  // sources of the B operands: synthesis: spectra in0 (scalar; psi for vector) and in1 (chi),
-  // [nf][nlm]; analysis: Fourier coefficients in0 (A for vector), in1 (B), [nf][T+1][nlat],
-  // with the quadrature weights wts[nh] (w, or w / (1 - mu^2) for vector transforms)
+  // sources of the B operands: synthesis: spectra psi in0, chi in1 ([nfv][nlm]) and the scalar
+  // spectra in2 ([nfs][nlm]); analysis: Fourier coefficients A in0, B in1 ([nfv][T+1][nlat])
+  // and the scalar ones in2 ([nfs][T+1][nlat]), with the quadrature weights wts[nh]
+  // (w / (1 - mu^2), vector) and wts2[nh] (w, scalar)
   const double2* in0;
   const double2* in1;
+  const double2* in2;
   const double* wts;
+  const double* wts2;
   const Job* jobs;      // per-CTA lists: CTA c runs jobs[cta_off[c] .. cta_off[c + 1])
   const int* cta_off;
   int ncols, bf16;
-  int synth, pair;      // pair: (P, H) jobs of one (m, tile) follow each other (vector transforms)
-  double2* out0;        // synthesis: Fourier coefficients [nf][T+1][nlat] (U for vector)
-  double2* out1;        //   (V); analysis: spectral [nf][nlm] (div; curl for vector)
-  int T, nlat, nlm, nf, cpf;
+  int synth, pair;      // pair: (P, H) jobs of one (m, tile) follow each other (nfv > 0)
+  double2* out0;        // synthesis: Fourier coefficients [nfv][T+1][nlat] of U; analysis: div
+  double2* out1;        //   of V; analysis: curl ([nfv][nlm])
+  double2* out2;        // scalar results: synthesis [nfs][T+1][nlat], analysis [nfs][nlm]
+  int T, nlat, nlm, nfv, nfs;
   double inv_a;
   int stages;       // A ring depth (<= TC_MAXSTAGES)
   int nb;           // B buffers (1, 2 or 4): B operands are fetched up to nb - 1 jobs ahead
@@ -125,11 +132,9 @@ __device__ __forceinline__ void tmem_sum8(uint32_t ta, uint32_t cs, int nacc, fl
 }
 
 // Results of one row (synthesis: northern latitude `row`; analysis: k = n - m = row) from the
-// 8-column group gq of the sums P (and H for vector transforms), combined in FP32 (the sums
+// 8-column group gq of the sums P (and H for vector pairs), combined in FP32 (the sums
 // carry TF32 / BF16 operand rounding; FP64 arithmetic is a scarce pipe on this GPU) and stored
-// as FP64.  Columns are
-// interleaved per field (2 cpf columns each), so a group is two scalar fields or one vector
-// field:
+// as FP64.  Groups gq < nfv are vector pairs, the rest hold two scalar fields each:
 //   synthesis scalar  (N re, N im, S re, S im): northern latitude and its mirror;
 //   synthesis vector  (N: psi re, psi im, chi re, chi im; S: the same): U = (-H psi + i m P chi)/a,
 //                     V = (i m P psi + H chi)/a, with the southern H sums negated
@@ -143,12 +148,12 @@ __device__ __forceinline__ void epilogue8(const GemmArgs& g, int m, int row, int
   if (g.synth) {
     if (row >= g.nlat / 2) return;
     const int lat = row, lats = g.nlat - 1 - row;
-    if (!g.pair) {
+    if (gq >= g.nfv) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int f = 2 * gq + h;
-        if (f >= g.nf) break;
-        double2* o = g.out0 + ((size_t)f * (g.T + 1) + m) * g.nlat;
+        const int f = 2 * (gq - g.nfv) + h;
+        if (f >= g.nfs) break;
+        double2* o = g.out2 + ((size_t)f * (g.T + 1) + m) * g.nlat;
         o[lat] = make_double2(P[4 * h], P[4 * h + 1]);
         o[lats] = make_double2(P[4 * h + 2], P[4 * h + 3]);
       }
@@ -168,12 +173,12 @@ __device__ __forceinline__ void epilogue8(const GemmArgs& g, int m, int row, int
     if (row >= g.T + 1 - m) return;
     const int par = row & 1;
     const size_t i = (size_t)moff(g.T, m) + row;
-    if (!g.pair) {
+    if (gq >= g.nfv) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int f = 2 * gq + h;
-        if (f >= g.nf) break;
-        g.out0[(size_t)f * g.nlm + i] = par ? make_double2(P[4 * h + 2], P[4 * h + 3])
+        const int f = 2 * (gq - g.nfv) + h;
+        if (f >= g.nfs) break;
+        g.out2[(size_t)f * g.nlm + i] = par ? make_double2(P[4 * h + 2], P[4 * h + 3])
                                             : make_double2(P[4 * h], P[4 * h + 1]);
       }
     } else {
@@ -229,30 +234,37 @@ __device__ __forceinline__ void store_row16(unsigned char* grp, int c, int sbo, 
 
 // B operand of job (m, kpad) written into shared memory at `base` by the threads of the
 // builder warps (bt = thread index among them), in the tensor cores' canonical K-major layout
-// (K group g of E elements at g * 128 B, column c at (c >> 3) * sbo + (c & 7) * 16).  Field f
-// owns the 2 cpf columns from 2 cpf f.  Columns past 2 nf cpf are never written: each
-// accumulator column depends on its own B column only, and the epilogue never reads them.
-//   synthesis (K = degrees k = n - m): coefficient q of field f in column 2 cpf f + q (the
-//     northern latitude's P_n(mu)), times (-1)^k in column 2 cpf f + cpf + q (the southern
+// (K group g of E elements at g * 128 B, column c at (c >> 3) * sbo + (c & 7) * 16).  A field
+// (vector pair or scalar) with cpf values q per latitude owns 2 cpf columns from its first
+// column c0: vector pair f from c0 = 8 f (cpf = 4), scalar field f from c0 = 8 nfv + 4 f
+// (cpf = 2).  Columns past 8 nfv + 4 nfs are never written: each accumulator column depends
+// on its own B column only, and the epilogue never reads them.
+//   synthesis (K = degrees k = n - m): coefficient q of the field in column c0 + q (the
+//     northern latitude's P_n(mu)), times (-1)^k in column c0 + cpf + q (the southern
 //     one: P_n(-mu) = (-1)^(n-m) P_n(mu)); scalar q: re, im; vector q: psi re, im, chi re, im.
-//   analysis (K = northern latitudes j): w_j (F_N + F_S) in column 2 cpf f + q, w_j (F_N - F_S)
-//     in column 2 cpf f + cpf + q; scalar q: re, im; vector q: A re, im, B re, im.
-// One item = (K group, column pair p < nf cpf / 2): E loads of its pair, four 16-byte rows.
+//   analysis (K = northern latitudes j): w_j (F_N + F_S) in column c0 + q, w_j (F_N - F_S)
+//     in column c0 + cpf + q; scalar q: re, im; vector q: A re, im, B re, im.
+// One item = (K group, column pair p < 2 nfv + nfs): E loads of its pair, four 16-byte rows;
+// pairs 2 f and 2 f + 1 are the psi (A) and chi (B) columns of vector pair f, pair 2 nfv + f
+// the columns of scalar field f.
 template <int PM>
 __device__ __forceinline__ void build_b(const GemmArgs& g, int m, int kpad, unsigned char* base, int bt) {
   constexpr int E = PM == PM_BF16 ? 8 : 4;
-  const int cpf = g.cpf, np = g.nf * cpf / 2;
+  const int nv = 2 * g.nfv, np = nv + g.nfs;
   const int sbo = (kpad / E) * 128;
   const int nitems = (kpad / E) * np;
   for (int it = bt; it < nitems; it += TC_NBUILD * 32) {
     const int gk = it / np, p = it - gk * np;
-    const int f = (2 * p) / cpf, q = 2 * p - f * cpf;
-    const int cn = 2 * cpf * f + q;  // the first column; the second block is cpf further
+    const bool vec = p < nv;
+    const int f = vec ? p >> 1 : p - nv;
+    const int cpf = vec ? 4 : 2;
+    const int cn = vec ? 8 * f + 2 * (p & 1) : 8 * g.nfv + 4 * f;  // the second block is cpf further
+    const double2* in = vec ? ((p & 1) ? g.in1 : g.in0) : g.in2;
     unsigned char* grp = base + (size_t)gk * 128;
     float v0[E], v1[E], v2[E], v3[E];
     if (g.synth) {
       const int K = g.T + 1 - m;
-      const double2* src = (q < 2 ? g.in0 : g.in1) + (size_t)f * g.nlm + moff(g.T, m);
+      const double2* src = in + (size_t)f * g.nlm + moff(g.T, m);
       double2 c[E];
 #pragma unroll
       for (int e = 0; e < E; ++e) {
@@ -268,16 +280,17 @@ __device__ __forceinline__ void build_b(const GemmArgs& g, int m, int kpad, unsi
       }
     } else {
       const int nh = g.nlat / 2;
-      const double2* Fq = (q < 2 ? g.in0 : g.in1) + ((size_t)f * (g.T + 1) + m) * g.nlat;
+      const double2* Fq = in + ((size_t)f * (g.T + 1) + m) * g.nlat;
+      const double* wt = vec ? g.wts : g.wts2;
       double2 a[E], b[E];
       double w[E];
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int j = gk * E + e;
-        const bool in = j < nh;
-        a[e] = in ? Fq[j] : make_double2(0.0, 0.0);
-        b[e] = in ? Fq[g.nlat - 1 - j] : make_double2(0.0, 0.0);
-        w[e] = in ? g.wts[j] : 0.0;
+        const bool ok = j < nh;
+        a[e] = ok ? Fq[j] : make_double2(0.0, 0.0);
+        b[e] = ok ? Fq[g.nlat - 1 - j] : make_double2(0.0, 0.0);
+        w[e] = ok ? wt[j] : 0.0;
       }
       // combinations in FP32 (the operand is rounded to TF32 / BF16 next; FP64 arithmetic is a
       // scarce pipe on this GPU): only the conversions of the inputs touch FP64 values
@@ -472,7 +485,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
     // epilogue warps 0-3: warp w holds rows 32 w .. 32 w + 31 of every job (its TMEM lane
     // quarter); the jobs of a vector transform come in (P, H) pairs, released together
     const int step = g.pair ? 2 : 1;
-    const int ngrp = (2 * g.nf * g.cpf + 7) / 8;  // 8-column groups holding results
+    const int ngrp = g.nfv + (g.nfs + 1) / 2;  // 8-column groups holding results
     for (int i = 0; i + step <= nj; i += step) {
       const Job jb = sjobs[i];
       const int acc0 = i % njb, acc1 = (i + 1) % njb;
@@ -498,7 +511,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
         for (int gq = 0; gq < ngrp; ++gq) {
           float P[8], H[8];
           tmem_sum8(ta0 + 8 * gq, cs, nacc, P);
-          if (g.pair) tmem_sum8(ta1 + 8 * gq, cs, nacc, H);
+          if (gq < g.nfv) tmem_sum8(ta1 + 8 * gq, cs, nacc, H);
           epilogue8(g, jb.m, row, gq, P, H);
         }
       }
@@ -819,32 +832,36 @@ void tc_legendre_destroy(TcLegendre* t) {
   delete t;
 }
 
-// One GEMM launch with the fused epilogue: ncols = MMA N (the real columns 2 nf cpf, padded to
-// a multiple of 16; the padding columns of B are never written and their sums never read).
-static int gemm(TcLegendre* t, bool synth, bool vector, int nf, const double2* in0, const double2* in1,
-                const double* wts, double2* out0, double2* out1, double inv_a, cudaStream_t s) {
-  const int cpf = vector ? 4 : 2;
-  const int ncols = std::max(16, (2 * nf * cpf + 15) / 16 * 16);
-  const Sched& sc = t->sched[synth ? 0 : 1][vector ? 1 : 0];
+// One GEMM launch with the fused epilogue over nfv vector pairs and nfs scalar fields: ncols =
+// MMA N (the real columns 8 nfv + 4 nfs, padded to a multiple of 16; the padding columns of B
+// are never written and their sums never read).  With nfv > 0 the launch runs (P, H) job
+// pairs, and the scalar fields ride on the P jobs' table reads.
+static int gemm(TcLegendre* t, bool synth, int nfv, const double2* in0, const double2* in1, double2* out0,
+                double2* out1, int nfs, const double2* in2, double2* out2, double inv_a, cudaStream_t s) {
+  const int ncols = std::max(16, (8 * nfv + 4 * nfs + 15) / 16 * 16);
+  const Sched& sc = t->sched[synth ? 0 : 1][nfv > 0 ? 1 : 0];
   GemmArgs g;
   g.tabP = synth ? t->tabPs : t->tabPa;
   g.tabH = synth ? t->tabHs : t->tabHa;
   g.in0 = in0;
   g.in1 = in1;
-  g.wts = wts;
+  g.in2 = in2;
+  g.wts = synth ? nullptr : t->wq;
+  g.wts2 = synth ? nullptr : t->w;
   g.jobs = sc.jobs;
   g.cta_off = sc.off;
   g.ncols = ncols;
   g.bf16 = t->bf16;
   g.synth = synth ? 1 : 0;
-  g.pair = vector ? 1 : 0;
+  g.pair = nfv > 0 ? 1 : 0;
   g.out0 = out0;
   g.out1 = out1;
+  g.out2 = out2;
   g.T = t->T;
   g.nlat = t->nlat;
   g.nlm = t->nlm;
-  g.nf = nf;
-  g.cpf = cpf;
+  g.nfv = nfv;
+  g.nfs = nfs;
   g.inv_a = inv_a;
   g.err = t->err;
   g.nj_max = sc.nj_max;
@@ -876,21 +893,31 @@ static int gemm(TcLegendre* t, bool synth, bool vector, int nf, const double2* i
 }
 
 int tc_leg_synth(TcLegendre* t, const double2* spec, double2* F, int nf, cudaStream_t s) {
-  return gemm(t, true, false, nf, spec, spec, nullptr, F, F, 0.0, s);
+  return gemm(t, true, 0, nullptr, nullptr, nullptr, nullptr, nf, spec, F, 0.0, s);
 }
 
 int tc_leg_synth_uv(TcLegendre* t, const double2* psi, const double2* chi, double2* FU, double2* FV, int nf,
                     double inv_a, cudaStream_t s) {
-  return gemm(t, true, true, nf, psi, chi, nullptr, FU, FV, inv_a, s);
+  return gemm(t, true, nf, psi, chi, FU, FV, 0, nullptr, nullptr, inv_a, s);
 }
 
 int tc_leg_anal(TcLegendre* t, const double2* F, double2* spec, int nf, cudaStream_t s) {
-  return gemm(t, false, false, nf, F, F, t->w, spec, spec, 0.0, s);
+  return gemm(t, false, 0, nullptr, nullptr, nullptr, nullptr, nf, F, spec, 0.0, s);
 }
 
 int tc_leg_anal_divcurl(TcLegendre* t, const double2* FA, const double2* FB, double2* dv, double2* cu, int nf,
                         double inv_a, cudaStream_t s) {
-  return gemm(t, false, true, nf, FA, FB, t->wq, dv, cu, inv_a, s);
+  return gemm(t, false, nf, FA, FB, dv, cu, 0, nullptr, nullptr, inv_a, s);
+}
+
+int tc_leg_synth_mixed(TcLegendre* t, const double2* psi, const double2* chi, double2* FU, double2* FV, int nfv,
+                       const double2* spec, double2* F, int nfs, double inv_a, cudaStream_t s) {
+  return gemm(t, true, nfv, psi, chi, FU, FV, nfs, spec, F, inv_a, s);
+}
+
+int tc_leg_anal_mixed(TcLegendre* t, const double2* FA, const double2* FB, double2* dv, double2* cu, int nfv,
+                      const double2* F, double2* spec, int nfs, double inv_a, cudaStream_t s) {
+  return gemm(t, false, nfv, FA, FB, dv, cu, nfs, F, spec, inv_a, s);
 }
 
 void tc_legendre_set_prof(TcLegendre* t, StageProf* prof) {

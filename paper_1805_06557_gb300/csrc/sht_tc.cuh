@@ -84,6 +84,11 @@ int tc_leg_synth(TcLegendre* t, const double2* spec, double2* F, int nf, cudaStr
 int tc_leg_anal(TcLegendre* t, const double2* F, double2* spec, int nf, cudaStream_t s);
 int tc_leg_synth_uv(TcLegendre* t, const double2* psi, const double2* chi, double2* FU, double2* FV,
                     int nf, double inv_a, cudaStream_t s);
+// nfv vector pairs and nfs scalar fields in one launch that reads each table once
+int tc_leg_synth_mixed(TcLegendre* t, const double2* psi, const double2* chi, double2* FU, double2* FV, int nfv,
+                       const double2* spec, double2* F, int nfs, double inv_a, cudaStream_t s);
+int tc_leg_anal_mixed(TcLegendre* t, const double2* FA, const double2* FB, double2* dv, double2* cu, int nfv,
+                      const double2* F, double2* spec, int nfs, double inv_a, cudaStream_t s);
 // reads the device flag set by a tensor-core kernel whose bounded wait gave up (0 = none)
 int tc_legendre_error(TcLegendre* t, int* flag);
 int tc_leg_anal_divcurl(TcLegendre* t, const double2* FA, const double2* FB, double2* dv,

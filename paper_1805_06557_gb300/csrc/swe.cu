@@ -6,7 +6,6 @@
 #include "../../include/sht.h"
 #include "../../include/swe.h"
 #include "common.cuh"
-#include "sht_fused.cuh"
 #include "sht_tc.cuh"
 
 namespace rexi {
@@ -370,8 +369,8 @@ static int nonlinear_update(swe_plan* p, const double2* U, const double2* base, 
     p->prof.end(ph);
   }
   int rc;
-  // Phi', zeta and U, V: one FFT launch for the four fields
-  if ((rc = sh_synth_fused(p->sp, U, 2, p->PZ, p->psi, p->chi, 1, p->Ug, p->Vg))) return rc;
+  // Phi', zeta and U, V: one pass (one read of each Legendre table, one FFT launch)
+  if ((rc = sh_synthesis_mixed(p->sp, U, p->PZ, 2, p->psi, p->chi, p->Ug, p->Vg, 1))) return rc;
   {
     const int ph = p->prof.begin(0);
     k_swe_products<<<dim3((p->d.nlon + tb - 1) / tb, p->d.nlat), tb, 0, p->stream>>>(p->PZ, p->Ug, p->Vg, p->ikc,
@@ -379,8 +378,8 @@ static int nonlinear_update(swe_plan* p, const double2* U, const double2* base, 
                                                                 p->d.nlat, p->d.nlon);
     p->prof.end(ph);
   }
-  // div / curl of A, B (two fields each) and KE: one FFT launch for the five fields
-  if ((rc = sh_anal_fused(p->sp, p->A, p->B, 2, p->dv, p->cu, p->KE, 1, p->kes))) return rc;
+  // div / curl of A, B (two fields each) and KE: one pass, as the synthesis
+  if ((rc = sh_analysis_mixed(p->sp, p->A, p->B, p->dv, p->cu, 2, p->KE, p->kes, 1))) return rc;
   {
     const int ph = p->prof.begin(0);
     k_swe_combine<<<(nlm + tb - 1) / tb, tb, 0, p->stream>>>(base, p->dv, p->cu, p->kes, U, ctab, out, tau, T,

@@ -524,6 +524,10 @@ _lib.sh_plan_get_profile.argtypes = [ctypes.c_void_p, _dp, _ip, ctypes.c_int]
 SH_STAGE_NAMES = ("legendre_fp64", "tc_pack", "tc_gemm", "tc_epilogue", "fft")
 for _n in ("sh_synthesis_uv", "sh_analysis_divcurl"):
     getattr(_lib, _n).argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 4 + [ctypes.c_int]
+_lib.sh_synthesis_mixed.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 2 + [ctypes.c_int] + \
+    [ctypes.c_void_p] * 4 + [ctypes.c_int]
+_lib.sh_analysis_mixed.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 4 + [ctypes.c_int] + \
+    [ctypes.c_void_p] * 2 + [ctypes.c_int]
 
 
 def _ptr(t):
@@ -593,6 +597,23 @@ class ShPlan:
                                         self._spec(div, nfields, "div"), self._spec(curl, nfields, "curl"),
                                         int(nfields)))
         return div, curl
+
+    def synthesis_mixed(self, spec, grid, nfields, psi, chi, U, V, nvec):
+        """Scalar synthesis of nfields spectra beside the velocity synthesis of nvec (psi,
+        chi) pairs, in one pass (one read of each Legendre table)."""
+        _check(_lib.sh_synthesis_mixed(self._h, self._spec(spec, nfields, "spec"), self._grid(grid, nfields, "grid"),
+                                       int(nfields), self._spec(psi, nvec, "psi"), self._spec(chi, nvec, "chi"),
+                                       self._grid(U, nvec, "U"), self._grid(V, nvec, "V"), int(nvec)))
+        return grid, U, V
+
+    def analysis_mixed(self, A, B, div, curl, nvec, grid, spec, nfields):
+        """Divergence and curl of nvec vector fields beside the analysis of nfields scalar
+        grids, in one pass."""
+        _check(_lib.sh_analysis_mixed(self._h, self._grid(A, nvec, "A"), self._grid(B, nvec, "B"),
+                                      self._spec(div, nvec, "div"), self._spec(curl, nvec, "curl"), int(nvec),
+                                      self._grid(grid, nfields, "grid"), self._spec(spec, nfields, "spec"),
+                                      int(nfields)))
+        return div, curl, spec
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

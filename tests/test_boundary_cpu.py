@@ -155,3 +155,11 @@ def test_swe_substeps_rule(rexi):
                  (5, 1.0, 1.0, 0.0, 1.0), (5, 1.0, 1.0, a, 0.0)]:
         with pytest.raises(rexi.RexiError):
             rexi.swe_substeps(*args)
+
+
+def test_mixed_transforms_reject_a_null_plan(rexi):
+    """The one-pass scalar + vector transforms check their plan before anything else (no
+    kernel runs)."""
+    lib = rexi.library()
+    assert lib.sh_synthesis_mixed(None, None, None, 1, None, None, None, None, 1) == rexi.REXI_EINVAL
+    assert lib.sh_analysis_mixed(None, None, None, None, None, 1, None, None, 1) == rexi.REXI_EINVAL

@@ -182,3 +182,51 @@ def test_tc_gemm_timeout_path_reports_etimeout(env, prec):
     og = osht.Grid(T, nlat, nlon, A)
     assert _rel(g.cpu().numpy()[0], og.synth(c[0])) < BOUND[prec]
     good.close()
+
+
+MIXED = [(31, 48, 96, 4, 2, 1), (31, 48, 96, 4, 1, 2), (31, 48, 96, 4, 3, 2), (31, 48, 96, 4, 1, 3),
+         (127, 192, 384, 3, 1, 1), (511, 768, 1536, 3, 2, 1), (511, 768, 1536, 3, 1, 2)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32", "bf16", "tf32x3"])
+@pytest.mark.parametrize("T,nlat,nlon,mf,nfs,nfv", MIXED)
+def test_mixed_transforms_equal_separate_calls(env, prec, T, nlat, nlon, mf, nfs, nfv):
+    """sh_synthesis_mixed / sh_analysis_mixed (nfs scalar fields beside nfv vector pairs, one
+    read of each table) give the results of the separate scalar and vector calls bit for bit:
+    every accumulator column depends on its own B column only, and the epilogue combines the
+    same sums in the same order.  Includes the nonlinear term's combinations (2 scalar + 1
+    vector synthesis, 2 vector + 1 scalar analysis) at T511."""
+    torch, rexi = env
+    p = rexi.ShPlan(T, nlat, nlon, A, prec, max_fields=mf)
+    cs = torch.from_numpy(_spec(T, 21, nfs)).cuda()
+    psi = torch.from_numpy(_spec(T, 22, nfv, -2.0)).cuda()
+    chi = torch.from_numpy(_spec(T, 23, nfv, -2.0)).cuda()
+    grid = lambda n: torch.empty(n, nlat, nlon, dtype=torch.float64, device="cuda")
+    g1, U1, V1 = grid(nfs), grid(nfv), grid(nfv)
+    g2, U2, V2 = grid(nfs), grid(nfv), grid(nfv)
+    p.synthesis(cs, g1, nfs)
+    p.synthesis_uv(psi, chi, U1, V1, nfv)
+    p.synthesis_mixed(cs, g2, nfs, psi, chi, U2, V2, nfv)
+    s1, d1, c1 = torch.empty_like(cs), torch.empty_like(psi), torch.empty_like(psi)
+    s2, d2, c2 = torch.empty_like(cs), torch.empty_like(psi), torch.empty_like(psi)
+    p.analysis(g1, s1, nfs)
+    p.analysis_divcurl(U1, V1, d1, c1, nfv)
+    p.analysis_mixed(U1, V1, d2, c2, nfv, g1, s2, nfs)
+    p.check()
+    for name, a, b in (("grid", g1, g2), ("U", U1, U2), ("V", V1, V2), ("spec", s1, s2), ("div", d1, d2),
+                       ("curl", c1, c2)):
+        assert torch.isfinite(torch.view_as_real(a) if a.is_complex() else a).all(), name
+        assert torch.equal(a, b), (name, float((a - b).abs().max()), float(a.abs().max()))
+    p.close()
+
+
+def test_mixed_transform_limits(env):
+    torch, rexi = env
+    p = rexi.ShPlan(31, 48, 96, A, "tf32", max_fields=2)
+    z = torch.zeros(4, osht.nlm(31), dtype=torch.complex128, device="cuda")
+    g = torch.zeros(4, 48, 96, dtype=torch.float64, device="cuda")
+    with pytest.raises(rexi.RexiError):
+        p.synthesis_mixed(z, g, 1, z, z, g, g, 2)     # 1 + 2 x 2 > 2 max_fields
+    with pytest.raises(rexi.RexiError):
+        p.analysis_mixed(g, g, z, z, 0, g, z, 1)      # no vector pair
+    p.close()
