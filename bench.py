@@ -476,7 +476,9 @@ def sh_transforms(torch, rexi, fp64_peak, T=511, nlat=768, nlon=1536, nf=2, reps
             leg_bytes = tab_bytes + narr * (nlm + (T + 1) * nlat) * 16
             fft_ms = prof["fft"][0] / reps
             fft_bytes = narr * (nlat * nlon * 8 + nlat * (T + 1) * 16)
-            leg_flops = 4.0 * nh * nlm * narr * ntab   # FMA = 2; complex coefficient x real table
+            # FMA = 2; complex coefficient x real table; vector arrays meet P and H, scalar ones P
+            nvec_arr = 2 if kind == "synthesis_mixed" else 4 if kind == "analysis_mixed" else (narr if vec else 0)
+            leg_flops = 4.0 * nh * nlm * (2 * nvec_arr + (narr - nvec_arr))
             if prec == "fp64":   # FP64 CUDA-core contraction: bound by the FP64 pipe on this GPU
                 leg_roof = {"bound": "alu", "pipe": "fp64", "kernel": "k_leg_*", "algorithmic_flops": leg_flops,
                             "achieved": leg_flops / (gemm_ms * 1e9), "unit": "TFLOP/s", "peak": fp64_peak,
