@@ -166,6 +166,11 @@ static __global__ void k_mixed_rhs(const double2* __restrict__ U0, const D4* __r
   rdf[o] = RhsDF{split4(bz.x, bz.y), split4(bd.x, bd.y), split4(qbp.x, qbp.y)};
 }
 
+// Cache hint: bring the line holding p from DRAM into L2 ahead of its load (the heavy
+// kernel's per-warp scratch, which does not fit in L2).  Only addresses inside buffers the
+// kernel reads anyway are passed.
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // ---- light kernel ------------------------------------------------------------------
 // One lane solves BOTH parity chains of its (pole, m): at element k (n = m + k) chain k & 1
 // holds the zeta row and the other chain the delta row, so the two recurrences share every
@@ -643,6 +648,10 @@ k_rexi_heavy(MixedArgs a, int t0, int nt) {
               cs = cp[0];
 #pragma unroll
               for (int s = 0; s < G; ++s) ys[s] = cp[1 + s];
+              // checkpoints of the segments below (DRAM) into L2 while this one is worked on: two
+              // segments ahead, both on entering the top segment
+              if (sg > 2) prefetch_l2(ck + ((size_t)(sg - 3) * 32 + lane) * SW);
+              if (e == K - 1 && sg > 1) prefetch_l2(ck + ((size_t)(sg - 2) * 32 + lane) * SW);
             }
 #pragma unroll
             for (int k = sg * SEG; k <= e; ++k) {
@@ -712,8 +721,15 @@ k_rexi_heavy(MixedArgs a, int t0, int nt) {
       float2 dxm[G];
 #pragma unroll
       for (int s = 0; s < G; ++s) dxm[s] = make_float2(0.f, 0.f);
+      constexpr int PFD = 4;  // pass C: g and h rows brought into L2 this many elements ahead
 #pragma unroll 4  // loads of four elements in flight
       for (int k = 0; k < K; ++k) {
+        // four rows (1 KB per array) per hint, lane l at byte 32 l; rows below kmax are in the buffer
+        if ((k & 3) == 0 && k + PFD + 4 <= a.kmax) {
+          prefetch_l2(Gs + (size_t)(k + PFD) * 32 + 4 * lane);
+#pragma unroll
+          for (int s = 0; s < G; ++s) prefetch_l2(Hs + ((size_t)s * a.kmax + k + PFD) * 32 + 4 * lane);
+        }
         const float2 g = Gs[(size_t)k * 32 + lane];
 #pragma unroll
         for (int s = 0; s < G; ++s) {
