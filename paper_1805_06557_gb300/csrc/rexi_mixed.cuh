@@ -692,7 +692,9 @@ k_rexi_heavy(MixedArgs a, int t0, int nt) {
           const float2 den = make_float2(fmaf(-up, gU.x, d.x), fmaf(-up, gU.y, d.y));
           const float2 inv = crcpf(den);
           gU = make_float2(lo * inv.x, lo * inv.y);
-          Gs[(size_t)k * 32 + lane] = gU;
+          // g depends on the pole only: with half-warps, lanes r and r + 16 hold the same pole, so
+          // the lower half stores it and both halves read that copy
+          if (!HALVES || half == 0) Gs[(size_t)k * 32 + lane] = gU;
           const HeavyRow R = heavy_row(a, pq, toff, k, isZ);
 #pragma unroll
           for (int s = 0; s < G; ++s) {
@@ -718,6 +720,7 @@ k_rexi_heavy(MixedArgs a, int t0, int nt) {
         }
       }
       // ---- C: upward: dx_k = h_k - g_k dx_{k-1}, FP32 pole sums of dx ----------------------
+      if (HALVES) __syncwarp();  // orders the lower half's g stores before the upper half's loads
       float2 dxm[G];
 #pragma unroll
       for (int s = 0; s < G; ++s) dxm[s] = make_float2(0.f, 0.f);
@@ -726,11 +729,13 @@ k_rexi_heavy(MixedArgs a, int t0, int nt) {
       for (int k = 0; k < K; ++k) {
         // four rows (1 KB per array) per hint, lane l at byte 32 l; rows below kmax are in the buffer
         if ((k & 3) == 0 && k + PFD + 4 <= a.kmax) {
-          prefetch_l2(Gs + (size_t)(k + PFD) * 32 + 4 * lane);
+          // half-warps: only the first 128 bytes of each g row are used (8 lanes per row)
+          prefetch_l2(HALVES ? Gs + (size_t)(k + PFD + (lane >> 3)) * 32 + 2 * (lane & 7)
+                             : Gs + (size_t)(k + PFD) * 32 + 4 * lane);
 #pragma unroll
           for (int s = 0; s < G; ++s) prefetch_l2(Hs + ((size_t)s * a.kmax + k + PFD) * 32 + 4 * lane);
         }
-        const float2 g = Gs[(size_t)k * 32 + lane];
+        const float2 g = Gs[(size_t)k * 32 + (HALVES ? (lane & 15) : lane)];
 #pragma unroll
         for (int s = 0; s < G; ++s) {
           const float2 h = Hs[((size_t)s * a.kmax + k) * 32 + lane];
