@@ -403,7 +403,7 @@ def _rel_fields(a, b, T):
     return out
 
 
-def sh_transforms(torch, rexi, fp64_peak, T=511, nlat=768, nlon=1536, nf=2, reps=5):
+def sh_transforms(torch, rexi, fp64_peak, fp32_peak, T=511, nlat=768, nlon=1536, nf=2, reps=5):
     """Synthesis and analysis of nf scalar fields and of one vector field (psi/chi -> U, V;
     A, B -> div, curl), and the nonlinear term's one-pass combinations (2 scalar fields + 1
     vector pair synthesised, 2 vector pairs + 1 scalar field analysed), at T511 on the
@@ -432,9 +432,9 @@ def sh_transforms(torch, rexi, fp64_peak, T=511, nlat=768, nlon=1536, nf=2, reps
     out = {"workload": "T%d, %d x %d Gauss grid, %d scalar fields + 1 vector field, n^-1.5 "
                        "spectra (seed 4)" % (T, nlat, nlon, nf), "hbm_peak_gbs": hbm}
     ref = {}
-    for prec in ("fp64", "tf32", "bf16", "tf32x3"):
+    for prec in ("fp64", "tf32", "bf16", "tf32x3", "df"):
         p = rexi.ShPlan(T, nlat, nlon, syn.RADIUS, prec, max_fields=3)
-        eb = {"fp64": 8, "tf32": 4, "bf16": 2, "tf32x3": 8}[prec]   # split TF32: hi and lo words
+        eb = {"fp64": 8, "tf32": 4, "bf16": 2, "tf32x3": 8, "df": 8}[prec]   # split TF32, df: hi and lo words
         res = {}
         for kind in ("synthesis", "analysis", "synthesis_uv", "analysis_divcurl", "synthesis_mixed",
                      "analysis_mixed"):
@@ -470,8 +470,8 @@ def sh_transforms(torch, rexi, fp64_peak, T=511, nlat=768, nlon=1536, nf=2, reps
             ntab = 2 if (vec or mixed) else 1   # P, or P and H
             # spectral arrays = Fourier arrays = grids: scalar fields + 2 per vector pair
             narr = 2 if vec else (4 if kind == "synthesis_mixed" else 5 if mixed else nf)
-            leg_ms = sum(prof[k][0] for k in ("legendre_fp64", "tc_pack", "tc_gemm", "tc_epilogue")) / reps
-            gemm_ms = (prof["legendre_fp64"][0] if prec == "fp64" else prof["tc_gemm"][0]) / reps
+            leg_ms = sum(prof[k][0] for k in ("legendre_fp64", "legendre_df", "tc_gemm", "tc_epilogue")) / reps
+            gemm_ms = prof[{"fp64": "legendre_fp64", "df": "legendre_df"}.get(prec, "tc_gemm")][0] / reps
             tab_bytes = ntab * nh * nlm * eb
             leg_bytes = tab_bytes + narr * (nlm + (T + 1) * nlat) * 16
             fft_ms = prof["fft"][0] / reps
@@ -484,6 +484,16 @@ def sh_transforms(torch, rexi, fp64_peak, T=511, nlat=768, nlon=1536, nf=2, reps
                             "achieved": leg_flops / (gemm_ms * 1e9), "unit": "TFLOP/s", "peak": fp64_peak,
                             "frac": leg_flops / (gemm_ms * 1e9) / fp64_peak,
                             "achieved_gbs": leg_bytes / (gemm_ms * 1e6)}
+            elif prec == "df":   # double-float on the FP32 pipe: 12 FP32 operations per real
+                # multiply-add of a compensated dot product (TwoProduct 2, TwoSum 6, low words 4),
+                # so 6 per algorithmic flop; the split of the inputs is inside the timed stage
+                xops = 6.0 * leg_flops
+                leg_roof = {"bound": "alu", "pipe": "fp32", "kernel": "k_df_*", "algorithmic_flops": leg_flops,
+                            "achieved": leg_flops / (gemm_ms * 1e9), "unit": "TFLOP/s",
+                            "executed_fp32_ops": xops, "executed_tops": xops / (gemm_ms * 1e9), "peak": fp32_peak,
+                            "frac": xops / (gemm_ms * 1e9) / fp32_peak,
+                            "speed_vs_fp64_peak": leg_flops / (gemm_ms * 1e9) / fp64_peak,
+                            "achieved_gbs": leg_bytes / (gemm_ms * 1e6), "hbm_frac": leg_bytes / (gemm_ms * 1e6) / hbm}
             else:                # tensor-core contraction of 16 columns: bound by the table bytes
                 leg_roof = {"bound": "hbm", "kernel": "k_tc_gemm", "algorithmic_bytes": leg_bytes,
                             "achieved_gbs": leg_bytes / (gemm_ms * 1e6), "peak": hbm, "unit": "GB/s",
@@ -493,7 +503,7 @@ def sh_transforms(torch, rexi, fp64_peak, T=511, nlat=768, nlon=1536, nf=2, reps
             # SM); in FP32 the grid and Fourier bytes do.
             fft_flops = 5.0 * nlon * math.log2(nlon) * narr * nlat / 2
             gbs = fft_bytes / (fft_ms * 1e6) if fft_ms > 0 else None
-            if prec == "fp64":
+            if prec in ("fp64", "df"):   # the FP64 FFT
                 fft_roof = {"bound": "alu", "pipe": "fp64", "algorithmic_flops": fft_flops,
                             "achieved": fft_flops / (fft_ms * 1e9) if fft_ms > 0 else None, "unit": "TFLOP/s",
                             "peak": fp64_peak,
@@ -912,9 +922,9 @@ def main():
     ens = None if args.no_ensemble else ensemble(torch, rexi, syn, max(3, min(args.steps, 10)))
     sh = swe = lg = None
     if not args.no_sh:
-        sh = sh_transforms(torch, rexi, fp64_tf)
+        sh = sh_transforms(torch, rexi, fp64_tf, fp32_tf)
         swe = swe_steps(torch, rexi, [
-            (127, 192, 384, 512, 1800.0, 48, [("fp64", "fp64"), ("mixed", "fp64"), ("mixed", "tf32x3"),
+            (127, 192, 384, 512, 1800.0, 48, [("fp64", "fp64"), ("mixed", "fp64"), ("mixed", "df"), ("mixed", "tf32x3"),
                                               ("mixed", "tf32"), ("fp64", "fp64", "etdrk"),
                                               ("mixed", "fp64", "etdrk"), ("fp64", "fp64", "irk"),
                                               ("fp64", "fp64", "lg_ver1"), ("fp64", "fp64", "lg_etdrk"),
@@ -922,7 +932,7 @@ def main():
             # T511, dt = 7200 s: the library's contour search (the fixed rule leaves a scalar error
             # of 2e5 at X = 182), the explicit part sub-stepped at Courant 0.5 under the state's
             # largest wind, del^4 diffusion with the truncation degree e-folding in 900 s
-            (511, 768, 1536, 2048, 7200.0, 12, [("fp64", "fp64"), ("mixed", "fp64"), ("mixed", "tf32x3"),
+            (511, 768, 1536, 2048, 7200.0, 12, [("fp64", "fp64"), ("mixed", "fp64"), ("mixed", "df"), ("mixed", "tf32x3"),
                                                  ("mixed", "tf32"), ("mixed", "bf16"),
                                                  ("fp64", "tf32x3", "lg_ver1")],
              {"contour": "select", "courant": 0.5, "efold_s": 900.0})])

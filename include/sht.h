@@ -28,6 +28,12 @@ extern "C" {
  * divergence of the fluxes) keep a usable accuracy; table bytes are those of FP64 (hi and lo
  * words), still streamed through the tensor cores. */
 #define SH_TF32X3 3
+/* Double-float on the FP32 CUDA cores: tables, inputs and sums carried as pairs of FP32 words
+ * (about 48 significand bits), every contraction a compensated dot product (TwoProduct by FMA,
+ * Knuth's TwoSum); the FFT stays FP64.  Close to FP64 accuracy without the FP64 pipe, which
+ * GB300 has little of (about 2 FP64 FMAs per clock and SM against 128 FP32 ones).  Tables take
+ * three times the memory of SH_FP64 (the FP64 tables and two split layouts).  nlat <= 2132. */
+#define SH_DF 4
 
 typedef struct sh_plan sh_plan;
 
@@ -35,7 +41,7 @@ typedef struct sh_plan_desc {
   int T;            /* triangular truncation, 1 <= T <= 1023                                */
   int nlat, nlon;   /* Gauss grid, nlat even and > T, nlon > 2T, nlon = 2^p 3^q              */
   double radius;    /* sphere radius a [m] (vector transforms)                              */
-  int precision;    /* SH_FP64, SH_TF32, SH_BF16 or SH_TF32X3                               */
+  int precision;    /* SH_FP64, SH_TF32, SH_BF16, SH_TF32X3 or SH_DF                        */
   int max_fields;   /* largest nfields passed to a transform; tensor-core precisions: <= 8,  */
                     /* the vector operands (8 max_fields columns x nlat/2 latitudes for      */
                     /* analysis, x T+1 degrees for synthesis) must fit in shared memory      */
@@ -106,7 +112,8 @@ int sh_plan_check(sh_plan* plan);
  * stream around each kernel it launches; sh_plan_get_profile synchronises the stream and
  * returns, per stage, the total milliseconds (ms[k]) and the number of launches
  * (launches[k]) since the last reset (reset = 1 clears them after reading).  Stages:
- * 0 FP64 Legendre contraction (SH_FP64), 1 unused (always 0), 2 tcgen05 Legendre GEMM
+ * 0 FP64 Legendre contraction (SH_FP64), 1 double-float Legendre contraction with the split
+ * of its inputs (SH_DF), 2 tcgen05 Legendre GEMM
  * (its B operands built and its FP64 results written inside the kernel), 3 unused,
  * 4 longitude FFT.  Arrays hold SH_NSTAGES entries; either may be NULL.  Disabled by
  * default.  Errors: REXI_EINVAL, REXI_ECUDA.

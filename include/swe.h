@@ -55,7 +55,7 @@ typedef struct swe_plan_desc {
   int N;                    /* REXI poles                                                   */
   double p0, Xc;            /* REXI contour for the linear sub-step (dt for ver1 and etdrk, dt/2 ver0) */
   int rexi_precision;       /* REXI_FP64 or REXI_MIXED                                      */
-  int sh_precision;         /* SH_FP64, SH_TF32, SH_BF16 or SH_TF32X3                       */
+  int sh_precision;         /* SH_FP64, SH_TF32, SH_BF16, SH_TF32X3 or SH_DF                */
   int scheme;               /* one of the SWE_* scheme identifiers above                    */
   void* stream;             /* cudaStream_t; NULL (the legacy default stream): the plan makes */
                             /* its own blocking stream, implicitly ordered with the default  */

@@ -20,6 +20,7 @@
 // Both kernels share the tile scheme and chain equations of the FP64 kernel.
 #pragma once
 #include "common.cuh"
+#include "df.cuh"
 #include "rexi_fp64.cuh"
 
 namespace rexi {
@@ -27,37 +28,6 @@ namespace rexi {
 constexpr int MIX_WARPS = 4;
 constexpr int LTROW = 33;      // padded row (float2) of the light transposition tile
 
-// ---- double-float arithmetic (value = hi + lo, |lo| <= ulp(hi)/2) --------------------
-struct df {
-  float hi, lo;
-};
-__device__ __forceinline__ df df_two_sum(float a, float b) {
-  float s = a + b;
-  float bb = s - a;
-  float e = (a - (s - bb)) + (b - bb);
-  return df{s, e};
-}
-__device__ __forceinline__ df df_fast(float s, float e) {  // |s| >= |e|
-  float h = s + e;
-  return df{h, e - (h - s)};
-}
-__device__ __forceinline__ df df_add(df x, df y) {
-  df s = df_two_sum(x.hi, y.hi);
-  return df_fast(s.hi, s.lo + (x.lo + y.lo));
-}
-__device__ __forceinline__ df df_neg(df x) { return df{-x.hi, -x.lo}; }
-__device__ __forceinline__ df df_mul(df x, df y) {
-  float p = x.hi * y.hi;
-  float e = fmaf(x.hi, y.hi, -p);
-  e = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, e));
-  return df_fast(p, e);
-}
-__device__ __forceinline__ df df_mulf(df x, float f) {
-  float p = x.hi * f;
-  float e = fmaf(x.hi, f, -p);
-  e = fmaf(x.lo, f, e);
-  return df_fast(p, e);
-}
 struct dfc {
   df re, im;
 };
@@ -358,30 +328,6 @@ __device__ __forceinline__ HeavyRow heavy_row(const MixedArgs& a, const PoleDF& 
   R.lo = isZ ? cm : df_neg(cm);
   R.up = isZ ? cp : df_neg(cp);
   return R;
-}
-
-// Compensated dot product (Ogita, Rump & Oishi's Dot2): the running sum s is kept in FP32 and
-// every rounding error -- of each product (TwoProduct by FMA) and of each addition (Knuth's
-// TwoSum) -- together with the low words of double-float operands is gathered in one FP32 word
-// err, so that s + err is as accurate as a sum formed in twice the working precision.
-struct dot2 {
-  float s, err;
-};
-// acc += (a_hi + a_lo) * b, b in FP32
-__device__ __forceinline__ void dot2_add(dot2& acc, df a, float b) {
-  const float p = a.hi * b;
-  const float ep = fmaf(a.hi, b, -p);
-  const df t = df_two_sum(acc.s, p);
-  acc.s = t.hi;
-  acc.err = fmaf(a.lo, b, acc.err + (ep + t.lo));
-}
-// acc += (a_hi + a_lo) * (b_hi + b_lo)
-__device__ __forceinline__ void dot2_add2(dot2& acc, df a, df b) {
-  const float p = a.hi * b.hi;
-  const float ep = fmaf(a.hi, b.hi, -p);
-  const df t = df_two_sum(acc.s, p);
-  acc.s = t.hi;
-  acc.err = fmaf(a.lo, b.hi, fmaf(a.hi, b.lo, acc.err + (ep + t.lo)));
 }
 
 // residual of one state's chain row k:  r_k - d_k x_k - lo_k x_{k-1} - up_k x_{k+1}, each

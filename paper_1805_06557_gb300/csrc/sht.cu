@@ -20,6 +20,7 @@
 
 #include "../../include/sht.h"
 #include "common.cuh"
+#include "sht_df.cuh"
 #include "sht_tc.cuh"
 
 namespace rexi {
@@ -657,6 +658,7 @@ struct sh_plan {
   double2* d_F = nullptr;   // Fourier workspace [2 * max_fields][T+1][nlat]
   FftPlan fp{};
   TcLegendre* tc = nullptr;  // tensor-core Legendre state (SH_TF32 / SH_BF16 / SH_TF32X3)
+  DfLegendre* dfl = nullptr;  // double-float Legendre state (SH_DF)
   StageProf prof;            // per-stage event timing (sh_plan_set_profiling)
 };
 
@@ -675,7 +677,8 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
   if (d.nlon <= 2 * d.T) return fail(REXI_EINVAL, "sh_plan_create: nlon must exceed 2T");
   if (!(d.radius > 0) || d.max_fields < 1) return fail(REXI_EINVAL, "sh_plan_create: radius > 0, max_fields >= 1");
   if (d.epilogue_wait_polls < 0) return fail(REXI_EINVAL, "sh_plan_create: epilogue_wait_polls < 0");
-  if (d.precision != SH_FP64 && d.precision != SH_TF32 && d.precision != SH_BF16 && d.precision != SH_TF32X3)
+  if (d.precision != SH_FP64 && d.precision != SH_TF32 && d.precision != SH_BF16 && d.precision != SH_TF32X3 &&
+      d.precision != SH_DF)
     return fail(REXI_EINVAL, "sh_plan_create: unknown precision %d", d.precision);
   sh_plan* p = new sh_plan();
   p->d = d;
@@ -683,7 +686,7 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
   p->nlm = (d.T + 1) * (d.T + 2) / 2;
   p->stream = (cudaStream_t)d.stream;
   p->prof.stream = p->stream;
-  p->fft32 = d.precision != SH_FP64;
+  p->fft32 = d.precision != SH_FP64 && d.precision != SH_DF;  // SH_DF keeps the FP64 FFT
   auto bail = [&](int code) {
     sh_plan_destroy(p);
     return code;
@@ -727,7 +730,11 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
     if (!e) e = cudaFuncSetAttribute(k_fft_anal64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p));
   }
   if (e) return bail(cuda_fail(e, "cudaFuncSetAttribute(fft)"));
-  if (d.precision != SH_FP64) {
+  if (d.precision == SH_DF) {
+    int rc = df_legendre_create(&p->dfl, p->d_P, p->d_H, p->d_w, p->d_wq, d.T, d.nlat, d.max_fields, p->stream);
+    if (rc) return bail(rc);
+    df_legendre_set_prof(p->dfl, &p->prof);
+  } else if (d.precision != SH_FP64) {
     int rc = tc_legendre_create(&p->tc, p->d_P, p->d_H, p->d_w, p->d_wq, d.T, d.nlat, d.max_fields,
                                 d.precision, p->stream);
     if (rc) return bail(rc);
@@ -751,6 +758,7 @@ extern "C" int sh_plan_destroy(sh_plan* p) {
   cudaFree(p->d_tw32);
   cudaFree(p->d_F);
   tc_legendre_destroy(p->tc);
+  df_legendre_destroy(p->dfl);
   p->prof.release();
   delete p;
   return REXI_OK;
@@ -809,6 +817,7 @@ static void launch_fft_anal(sh_plan* p, const FftSegs& sg) {
 // Legendre stages (FP64 kernels or the tensor-core path) between spectra and Fourier arrays
 static int leg_synth(sh_plan* p, const double2* spec, double2* F, int nf) {
   if (p->tc) return tc_leg_synth(p->tc, spec, F, nf, p->stream);
+  if (p->dfl) return df_leg_synth(p->dfl, spec, F, nf, nullptr, nullptr, nullptr, nullptr, 0, 0.0, p->stream);
   const int ph = p->prof.begin(0);
   k_leg_synth<<<dim3(p->d.T + 1, nf, (p->nh + LTH - 1) / LTH), LTH, 0, p->stream>>>(p->d_P, spec, F, p->d.T,
                                                                                   p->d.nlat, p->nlm);
@@ -817,6 +826,7 @@ static int leg_synth(sh_plan* p, const double2* spec, double2* F, int nf) {
 }
 static int leg_synth_uv(sh_plan* p, const double2* psi, const double2* chi, double2* FU, double2* FV, int nf) {
   if (p->tc) return tc_leg_synth_uv(p->tc, psi, chi, FU, FV, nf, 1.0 / p->d.radius, p->stream);
+  if (p->dfl) return df_leg_synth(p->dfl, nullptr, nullptr, 0, psi, chi, FU, FV, nf, 1.0 / p->d.radius, p->stream);
   const int ph = p->prof.begin(0);
   k_leg_synth_uv<<<dim3(p->d.T + 1, nf, (p->nh + LTH - 1) / LTH), LTH, 0, p->stream>>>(
       p->d_P, p->d_H, psi, chi, FU, FV, p->d.T, p->d.nlat, p->nlm, 1.0 / p->d.radius);
@@ -825,6 +835,7 @@ static int leg_synth_uv(sh_plan* p, const double2* psi, const double2* chi, doub
 }
 static int leg_anal(sh_plan* p, const double2* F, double2* spec, int nf) {
   if (p->tc) return tc_leg_anal(p->tc, F, spec, nf, p->stream);
+  if (p->dfl) return df_leg_anal(p->dfl, nullptr, nullptr, nullptr, nullptr, 0, F, spec, nf, 0.0, p->stream);
   const int ph = p->prof.begin(0);
   k_leg_anal<<<dim3(p->d.T + 1, nf), ATH, sizeof(double2) * 2 * p->nh, p->stream>>>(p->d_P, p->d_w, F, spec,
                                                                                     p->d.T, p->d.nlat, p->nlm);
@@ -833,6 +844,7 @@ static int leg_anal(sh_plan* p, const double2* F, double2* spec, int nf) {
 }
 static int leg_anal_divcurl(sh_plan* p, const double2* FA, const double2* FB, double2* dv, double2* cu, int nf) {
   if (p->tc) return tc_leg_anal_divcurl(p->tc, FA, FB, dv, cu, nf, 1.0 / p->d.radius, p->stream);
+  if (p->dfl) return df_leg_anal(p->dfl, FA, FB, dv, cu, nf, nullptr, nullptr, 0, 1.0 / p->d.radius, p->stream);
   const int ph = p->prof.begin(0);
   k_leg_anal_divcurl<<<dim3(p->d.T + 1, nf), ATH, sizeof(double2) * 4 * p->nh, p->stream>>>(
       p->d_P, p->d_H, p->d_wq, FA, FB, dv, cu, p->d.T, p->d.nlat, p->nlm, 1.0 / p->d.radius);
@@ -908,6 +920,10 @@ extern "C" int sh_synthesis_mixed(sh_plan* p, const void* spec, void* grid, int 
     if ((rc = tc_leg_synth_mixed(p->tc, (const double2*)psi, (const double2*)chi, FU, FV, nfv, (const double2*)spec, F,
                                  nf, 1.0 / p->d.radius, p->stream)))
       return rc;
+  } else if (p->dfl) {
+    if ((rc = df_leg_synth(p->dfl, (const double2*)spec, F, nf, (const double2*)psi, (const double2*)chi, FU, FV, nfv,
+                           1.0 / p->d.radius, p->stream)))
+      return rc;
   } else {
     if ((rc = leg_synth(p, (const double2*)spec, F, nf))) return rc;
     if ((rc = leg_synth_uv(p, (const double2*)psi, (const double2*)chi, FU, FV, nfv))) return rc;
@@ -928,6 +944,10 @@ extern "C" int sh_analysis_mixed(sh_plan* p, const void* A, const void* B, void*
   if (p->tc) {
     if ((rc = tc_leg_anal_mixed(p->tc, FA, FB, (double2*)dv, (double2*)cu, nfv, FG, (double2*)spec, nf,
                                 1.0 / p->d.radius, p->stream)))
+      return rc;
+  } else if (p->dfl) {
+    if ((rc = df_leg_anal(p->dfl, FA, FB, (double2*)dv, (double2*)cu, nfv, FG, (double2*)spec, nf, 1.0 / p->d.radius,
+                          p->stream)))
       return rc;
   } else {
     if ((rc = leg_anal_divcurl(p, FA, FB, (double2*)dv, (double2*)cu, nfv))) return rc;

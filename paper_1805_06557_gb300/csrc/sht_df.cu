@@ -1,0 +1,558 @@
+// Double-float Legendre contractions (sh_plan precision SH_DF; paper Sec. 3.2: the Legendre
+// contraction per zonal order m of the SH transforms).
+//
+// GB300 issues about two FP64 FMAs per clock and SM against 128 FP32 ones, so the FP64
+// contraction is bound by its pipe while the tensor-core precisions stop near 1e-6.  Here every
+// operand is a double-float pair (hi + lo, two FP32 words; about 48 significand bits) and every
+// sum a compensated dot product (Ogita, Rump & Oishi's Dot2: TwoProduct by FMA, Knuth's TwoSum,
+// the errors gathered in one FP32 word), all on the FP32 pipe.  Only the conversions touch FP64:
+// the tables are split once at plan time, the inputs of a call by one pass kernel, and the
+// results are formed in FP64 from the two words of each sum.
+//
+// Tables (split from the FP64 ones): synthesis [moff(m)+k][nh] (latitude fastest, as the FP64
+// table: threads that own latitudes read coalesced); analysis, per m, [nh][K] with the even
+// degrees k first and the odd ones after them, so that the warps of one parity, which own
+// consecutive degrees, read coalesced.
+//
+// One launch contracts NS scalar fields and NV vector pairs against the same table reads; the
+// host runs groups of fields (NS <= 2, NV <= 1 for synthesis; NS, NV <= 2 for analysis).
+#include <algorithm>
+#include <cuda_runtime.h>
+#include <vector>
+
+#include "../../include/sht.h"
+#include "common.cuh"
+#include "df.cuh"
+#include "sht_df.cuh"
+
+namespace rexi {
+
+namespace {
+
+constexpr int DF_STH = 128;  // synthesis: threads per block (one northern latitude each)
+constexpr int DF_ATH = 128;  // analysis: threads per block (64 even and 64 odd degrees)
+
+__device__ __forceinline__ float2 split_df(double x) {
+  const float hi = (float)x;
+  return make_float2(hi, (float)(x - (double)hi));
+}
+__device__ __forceinline__ float4 split_dfc(double2 v) {
+  const float2 a = split_df(v.x), b = split_df(v.y);
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ df df_of(float2 v) { return df{v.x, v.y}; }
+__device__ __forceinline__ df dfre(float4 v) { return df{v.x, v.y}; }
+__device__ __forceinline__ df dfim(float4 v) { return df{v.z, v.w}; }
+
+// the value of a + sg b (sg = +-1) of two compensated sums, rounded once to FP64
+__device__ __forceinline__ double dsum(const dot2& a, const dot2& b, float sg) {
+  const df t = df_two_sum(a.s, sg * b.s);
+  return (double)t.hi + (double)(t.lo + (a.err + sg * b.err));
+}
+__device__ __forceinline__ double dval(const dot2& a) { return (double)a.s + (double)a.err; }
+
+// ---- plan-time splits --------------------------------------------------------------------
+// FP64 table [moff(m)+k][nh] -> synthesis table (same layout) and analysis table (per m [nh][K],
+// even k first); one thread per (m, latitude)
+__global__ void k_df_split_table(const double* __restrict__ src, float2* __restrict__ syn, float2* __restrict__ ana,
+                                 int T, int nh) {
+  const int m = blockIdx.x, j = blockIdx.y * blockDim.x + threadIdx.x;
+  if (j >= nh) return;
+  const int K = T + 1 - m, Ke = (K + 1) / 2;
+  const size_t base = (size_t)moff(T, m) * nh;
+  for (int k = 0; k < K; ++k) {
+    const float2 v = split_df(src[base + (size_t)k * nh + j]);
+    syn[base + (size_t)k * nh + j] = v;
+    ana[base + (size_t)j * K + ((k & 1) ? Ke + (k >> 1) : (k >> 1))] = v;
+  }
+}
+__global__ void k_df_split_weights(const double* __restrict__ w, const double* __restrict__ wq,
+                                   float4* __restrict__ out, int nh) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nh) return;
+  const float2 a = split_df(w[j]), b = split_df(wq[j]);
+  out[j] = make_float4(a.x, a.y, b.x, b.y);
+}
+
+// ---- per-call split of the complex FP64 inputs (up to three arrays) into one float4 buffer ---
+struct SplitSegs {
+  const double2* src[3];
+  long long end[3];  // cumulative element counts
+};
+__global__ void k_df_split_inputs(const __grid_constant__ SplitSegs sg, float4* __restrict__ dst) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= sg.end[2]) return;
+  const int s = (i >= sg.end[0]) + (i >= sg.end[1]);
+  const long long o = s ? i - sg.end[s - 1] : i;
+  dst[i] = split_dfc(sg.src[s][o]);
+}
+
+// ---- synthesis ----------------------------------------------------------------------------
+struct DfSynthArgs {
+  const float2* P;
+  const float2* H;
+  const float4* cs;   // scalar spectra, split [NS][nlm]
+  const float4* cp;   // psi [NV][nlm]
+  const float4* cc;   // chi [NV][nlm]
+  double2* F;         // [NS][T+1][nlat]
+  double2* FU;        // [NV][T+1][nlat]
+  double2* FV;
+  int T, nlat, nh, nlm;
+  double inv_a;
+};
+
+// k-step of parity PAR: the table entries p, h of degree k against every field's coefficient
+// (split coefficients of the block's zonal order staged in shared memory: scalar field f at
+// cf + f K, psi of pair v at cf + (NS + v) K, chi at cf + (NS + NV + v) K)
+template <int NS, int NV, int PAR>
+__device__ __forceinline__ void df_synth_step(float2 pv, float2 hv, const float4* cf, int K, int k,
+                                              dot2 (&S)[NS > 0 ? NS : 1][2][2], dot2 (&V)[NV > 0 ? NV : 1][4][2][2]) {
+  const df p = df_of(pv);
+#pragma unroll
+  for (int f = 0; f < NS; ++f) {
+    const float4 c = cf[f * K + k];
+    dot2_add2(S[f][PAR][0], p, dfre(c));
+    dot2_add2(S[f][PAR][1], p, dfim(c));
+  }
+  if (NV > 0) {
+    const df h = df_of(hv);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const float4 ps = cf[(NS + v) * K + k], ch = cf[(NS + NV + v) * K + k];
+      dot2_add2(V[v][0][PAR][0], p, dfre(ps));
+      dot2_add2(V[v][0][PAR][1], p, dfim(ps));
+      dot2_add2(V[v][1][PAR][0], p, dfre(ch));
+      dot2_add2(V[v][1][PAR][1], p, dfim(ch));
+      dot2_add2(V[v][2][PAR][0], h, dfre(ps));
+      dot2_add2(V[v][2][PAR][1], h, dfim(ps));
+      dot2_add2(V[v][3][PAR][0], h, dfre(ch));
+      dot2_add2(V[v][3][PAR][1], h, dfim(ch));
+    }
+  }
+}
+
+constexpr int DF_PF = 4;  // table entries loaded this many degrees (synthesis) or latitudes (analysis) ahead
+
+// one thread per northern latitude jh of zonal order m: even and odd partial sums over the
+// degrees, combined for the latitude and its mirror (P_n(-mu) = (-1)^(n-m) P_n(mu),
+// H_n(-mu) = -(-1)^(n-m) H_n(mu)); vector pairs give U = (-H psi + i m P chi)/a and
+// V = (i m P psi + H chi)/a.  The block stages its zonal order's split coefficients in shared
+// memory; each thread keeps the table entries of the next DF_PF degrees in flight.
+template <int NS, int NV>
+__global__ void __launch_bounds__(DF_STH) k_df_synth(const __grid_constant__ DfSynthArgs a) {
+  extern __shared__ float4 cf[];
+  const int m = blockIdx.x;
+  const int T = a.T, K = T + 1 - m, base = moff(T, m), nlat = a.nlat, nh = a.nh;
+  for (int i = threadIdx.x; i < (NS + 2 * NV) * K; i += DF_STH) {
+    const int q = i / K, k = i - q * K;
+    const float4* src = q < NS ? a.cs + (size_t)q * a.nlm : q < NS + NV ? a.cp + (size_t)(q - NS) * a.nlm
+                                                                         : a.cc + (size_t)(q - NS - NV) * a.nlm;
+    cf[i] = __ldg(src + base + k);
+  }
+  __syncthreads();
+  const int jh = blockIdx.y * DF_STH + threadIdx.x;
+  if (jh >= nh) return;  // no barrier below
+  const float2* Pm = a.P + (size_t)base * nh + jh;
+  const float2* Hm = a.H + (size_t)base * nh + jh;
+  dot2 S[NS > 0 ? NS : 1][2][2];
+  dot2 V[NV > 0 ? NV : 1][4][2][2];
+#pragma unroll
+  for (int f = 0; f < (NS > 0 ? NS : 1); ++f)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) S[f][q >> 1][q & 1] = dot2{0.f, 0.f};
+#pragma unroll
+  for (int v = 0; v < (NV > 0 ? NV : 1); ++v)
+#pragma unroll
+    for (int q = 0; q < 16; ++q) V[v][q >> 2][(q >> 1) & 1][q & 1] = dot2{0.f, 0.f};
+  const float2 z2 = make_float2(0.f, 0.f);
+  float2 pb[DF_PF], hb[DF_PF];
+#pragma unroll
+  for (int u = 0; u < DF_PF; ++u) {
+    pb[u] = u < K ? __ldg(Pm + (size_t)u * nh) : z2;
+    hb[u] = (NV > 0 && u < K) ? __ldg(Hm + (size_t)u * nh) : z2;
+  }
+  for (int k0 = 0; k0 < K; k0 += DF_PF) {
+    float2 pn[DF_PF], hn[DF_PF];
+#pragma unroll
+    for (int u = 0; u < DF_PF; ++u) {
+      const int kk = k0 + DF_PF + u;
+      pn[u] = kk < K ? __ldg(Pm + (size_t)kk * nh) : z2;
+      hn[u] = (NV > 0 && kk < K) ? __ldg(Hm + (size_t)kk * nh) : z2;
+    }
+#pragma unroll
+    for (int u = 0; u < DF_PF; u += 2) {  // k0 is even: the parity of k0 + u is that of u
+      if (k0 + u < K) df_synth_step<NS, NV, 0>(pb[u], hb[u], cf, K, k0 + u, S, V);
+      if (k0 + u + 1 < K) df_synth_step<NS, NV, 1>(pb[u + 1], hb[u + 1], cf, K, k0 + u + 1, S, V);
+    }
+#pragma unroll
+    for (int u = 0; u < DF_PF; ++u) {
+      pb[u] = pn[u];
+      hb[u] = hn[u];
+    }
+  }
+  const int lat = jh, lats = nlat - 1 - jh;
+#pragma unroll
+  for (int f = 0; f < NS; ++f) {
+    double2* o = a.F + ((size_t)f * (T + 1) + m) * nlat;
+    o[lat] = make_double2(dsum(S[f][0][0], S[f][1][0], 1.f), dsum(S[f][0][1], S[f][1][1], 1.f));
+    o[lats] = make_double2(dsum(S[f][0][0], S[f][1][0], -1.f), dsum(S[f][0][1], S[f][1][1], -1.f));
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    double2* oU = a.FU + ((size_t)v * (T + 1) + m) * nlat;
+    double2* oV = a.FV + ((size_t)v * (T + 1) + m) * nlat;
+#pragma unroll
+    for (int hs = 0; hs < 2; ++hs) {
+      const float so = hs ? -1.f : 1.f;  // odd degrees change sign in the south
+      const double sh = hs ? -1.0 : 1.0;  // and the H sums as a whole
+      // [0] P psi, [1] P chi, [2] H psi, [3] H chi; re, im
+      double x[4][2];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) x[q][c] = (q >= 2 ? sh : 1.0) * dsum(V[v][q][0][c], V[v][q][1][c], so);
+      const double fm = (double)m, ia = a.inv_a;
+      const int j = hs ? lats : lat;
+      oU[j] = make_double2(ia * (-x[2][0] - fm * x[1][1]), ia * (-x[2][1] + fm * x[1][0]));
+      oV[j] = make_double2(ia * (-fm * x[0][1] + x[3][0]), ia * (fm * x[0][0] + x[3][1]));
+    }
+  }
+}
+
+// ---- analysis -----------------------------------------------------------------------------
+struct DfAnalArgs {
+  const float2* P;      // analysis tables: per m [nh][K], even k first
+  const float2* H;
+  const float4* wdf;    // (w.hi, w.lo, wq.hi, wq.lo) [nh]
+  const float4* fa;     // split Fourier coefficients: A [NV][T+1][nlat]
+  const float4* fb;     // B [NV][T+1][nlat]
+  const float4* fg;     // scalar [NS][T+1][nlat]
+  double2* dv;          // [NV][nlm]
+  double2* cu;
+  double2* spec;        // [NS][nlm]
+  int T, nlat, nh, nlm;
+  double inv_a;
+};
+
+__device__ __forceinline__ float4 dfc_pack(df re, df im) { return make_float4(re.hi, re.lo, im.hi, im.lo); }
+// w (F_N + s F_S) of one latitude pair, in double-float
+__device__ __forceinline__ float4 df_wsum(df w, float4 n, float4 s, float sg) {
+  const df re = df_mul(w, df_add(dfre(n), df{sg * s.x, sg * s.y}));
+  const df im = df_mul(w, df_add(dfim(n), df{sg * s.z, sg * s.w}));
+  return dfc_pack(re, im);
+}
+
+// latitude j of one degree: the table entries p, h against the staged sums (sP, sH select the
+// sum or the difference array for P and H)
+template <int NS, int NV>
+__device__ __forceinline__ void df_anal_step(float2 pv, float2 hv, const float4* sm4, int nh, int j, int sP, int sH,
+                                             dot2 (&S)[NS > 0 ? NS : 1][2], dot2 (&V)[NV > 0 ? NV : 1][4][2]) {
+  const df p = df_of(pv);
+#pragma unroll
+  for (int f = 0; f < NS; ++f) {
+    const float4 g = sm4[(4 * NV + 2 * f + sP) * nh + j];
+    dot2_add2(S[f][0], p, dfre(g));
+    dot2_add2(S[f][1], p, dfim(g));
+  }
+  if (NV > 0) {
+    const df h = df_of(hv);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const float4 AP = sm4[(4 * v + 0 + sP) * nh + j], BP = sm4[(4 * v + 2 + sP) * nh + j];
+      const float4 AH = sm4[(4 * v + 0 + sH) * nh + j], BH = sm4[(4 * v + 2 + sH) * nh + j];
+      dot2_add2(V[v][0][0], p, dfre(AP));
+      dot2_add2(V[v][0][1], p, dfim(AP));
+      dot2_add2(V[v][1][0], p, dfre(BP));
+      dot2_add2(V[v][1][1], p, dfim(BP));
+      dot2_add2(V[v][2][0], h, dfre(AH));
+      dot2_add2(V[v][2][1], h, dfim(AH));
+      dot2_add2(V[v][3][0], h, dfre(BH));
+      dot2_add2(V[v][3][1], h, dfim(BH));
+    }
+  }
+}
+
+// Block (m, tile): shared memory holds, per northern latitude j, the weighted hemispheric sums
+// and differences of every field (vector pair v: A+, A-, B+, B- with w / (1 - mu^2); scalar f:
+// G+, G- with w); warps 0-1 own the even degrees k = 128 tile + 2 i, warps 2-3 the odd ones,
+// and each thread streams its table column over the latitudes, DF_PF latitudes of table entries
+// in flight.  P pairs with the sums for even k and the differences for odd k, H the other way
+// round.
+template <int NS, int NV>
+__global__ void __launch_bounds__(DF_ATH, 4) k_df_anal(const __grid_constant__ DfAnalArgs a) {
+  extern __shared__ float4 sm4[];
+  const int m = blockIdx.x, tile = blockIdx.y;
+  const int T = a.T, K = T + 1 - m, nh = a.nh, nlat = a.nlat;
+  if (tile * DF_ATH >= K) return;  // uniform over the block
+  const int base = moff(T, m);
+  // staging
+  for (int j = threadIdx.x; j < nh; j += DF_ATH) {
+    const float4 wv = __ldg(a.wdf + j);
+    const df w{wv.x, wv.y}, wq{wv.z, wv.w};
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const float4* A = a.fa + ((size_t)v * (T + 1) + m) * nlat;
+      const float4* B = a.fb + ((size_t)v * (T + 1) + m) * nlat;
+      const float4 an = __ldg(A + j), as = __ldg(A + nlat - 1 - j);
+      const float4 bn = __ldg(B + j), bs = __ldg(B + nlat - 1 - j);
+      sm4[(4 * v + 0) * nh + j] = df_wsum(wq, an, as, 1.f);
+      sm4[(4 * v + 1) * nh + j] = df_wsum(wq, an, as, -1.f);
+      sm4[(4 * v + 2) * nh + j] = df_wsum(wq, bn, bs, 1.f);
+      sm4[(4 * v + 3) * nh + j] = df_wsum(wq, bn, bs, -1.f);
+    }
+#pragma unroll
+    for (int f = 0; f < NS; ++f) {
+      const float4* G = a.fg + ((size_t)f * (T + 1) + m) * nlat;
+      const float4 gn = __ldg(G + j), gs = __ldg(G + nlat - 1 - j);
+      sm4[(4 * NV + 2 * f + 0) * nh + j] = df_wsum(w, gn, gs, 1.f);
+      sm4[(4 * NV + 2 * f + 1) * nh + j] = df_wsum(w, gn, gs, -1.f);
+    }
+  }
+  __syncthreads();
+  const int par = threadIdx.x >= DF_ATH / 2;  // uniform over each warp
+  const int idx = threadIdx.x & (DF_ATH / 2 - 1);
+  const int k = tile * DF_ATH + 2 * idx + par;
+  if (k >= K) return;  // no barrier below
+  const int Ke = (K + 1) / 2;
+  const size_t col = (size_t)base * nh + (par ? Ke : 0) + tile * (DF_ATH / 2) + idx;
+  const float2* Pc = a.P + col;
+  const float2* Hc = a.H + col;
+  // P meets (N + S) for even k, (N - S) for odd k; H the other one
+  const int sP = par, sH = 1 - par;
+  dot2 S[NS > 0 ? NS : 1][2];
+  dot2 V[NV > 0 ? NV : 1][4][2];  // [0] P.A, [1] P.B, [2] H.A, [3] H.B; re, im
+#pragma unroll
+  for (int f = 0; f < (NS > 0 ? NS : 1); ++f) S[f][0] = S[f][1] = dot2{0.f, 0.f};
+#pragma unroll
+  for (int v = 0; v < (NV > 0 ? NV : 1); ++v)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) V[v][q >> 1][q & 1] = dot2{0.f, 0.f};
+  const float2 z2 = make_float2(0.f, 0.f);
+  float2 pb[DF_PF], hb[DF_PF];
+#pragma unroll
+  for (int u = 0; u < DF_PF; ++u) {
+    pb[u] = u < nh ? __ldg(Pc + (size_t)u * K) : z2;
+    hb[u] = (NV > 0 && u < nh) ? __ldg(Hc + (size_t)u * K) : z2;
+  }
+  for (int j0 = 0; j0 < nh; j0 += DF_PF) {
+    float2 pn[DF_PF], hn[DF_PF];
+#pragma unroll
+    for (int u = 0; u < DF_PF; ++u) {
+      const int jj = j0 + DF_PF + u;
+      pn[u] = jj < nh ? __ldg(Pc + (size_t)jj * K) : z2;
+      hn[u] = (NV > 0 && jj < nh) ? __ldg(Hc + (size_t)jj * K) : z2;
+    }
+#pragma unroll
+    for (int u = 0; u < DF_PF; ++u) {
+      const int j = j0 + u;
+      if (j >= nh) break;
+      df_anal_step<NS, NV>(pb[u], hb[u], sm4, nh, j, sP, sH, S, V);
+    }
+#pragma unroll
+    for (int u = 0; u < DF_PF; ++u) {
+      pb[u] = pn[u];
+      hb[u] = hn[u];
+    }
+  }
+  const size_t i = (size_t)base + k;
+#pragma unroll
+  for (int f = 0; f < NS; ++f) a.spec[(size_t)f * a.nlm + i] = make_double2(dval(S[f][0]), dval(S[f][1]));
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const double fm = (double)m, ia = a.inv_a;
+    const double PAr = dval(V[v][0][0]), PAi = dval(V[v][0][1]), PBr = dval(V[v][1][0]), PBi = dval(V[v][1][1]);
+    const double HAr = dval(V[v][2][0]), HAi = dval(V[v][2][1]), HBr = dval(V[v][3][0]), HBi = dval(V[v][3][1]);
+    // div = (i m P.A - H.B) / a, curl = (i m P.B + H.A) / a
+    a.dv[(size_t)v * a.nlm + i] = make_double2(ia * (-fm * PAi - HBr), ia * (fm * PAr - HBi));
+    a.cu[(size_t)v * a.nlm + i] = make_double2(ia * (-fm * PBi + HAr), ia * (fm * PBr + HAi));
+  }
+}
+
+template <int NS, int NV>
+size_t df_synth_smem(int T) {
+  return sizeof(float4) * (size_t)(NS + 2 * NV) * (T + 1);
+}
+template <int NS, int NV>
+size_t df_anal_smem(int nh) {
+  return sizeof(float4) * (size_t)(4 * NV + 2 * NS) * nh;
+}
+
+}  // namespace
+
+struct DfLegendre {
+  int T = 0, nlat = 0, nh = 0, nlm = 0, max_fields = 0;
+  float2 *Ps = nullptr, *Hs = nullptr, *Pa = nullptr, *Ha = nullptr;
+  float4* wdf = nullptr;
+  float4* in = nullptr;  // split inputs of one call: [2 max_fields][max(nlm, (T+1) nlat)]
+  StageProf* prof = nullptr;
+};
+
+static int df_smem_attr(int nh, int T) {
+  cudaError_t e = cudaSuccess;
+#define DF_ATTR(NS, NV)                                                                                    \
+  if (!e)                                                                                                 \
+    e = cudaFuncSetAttribute(k_df_anal<NS, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
+                             (int)df_anal_smem<NS, NV>(nh));
+  DF_ATTR(1, 0) DF_ATTR(2, 0) DF_ATTR(0, 1) DF_ATTR(1, 1) DF_ATTR(2, 1) DF_ATTR(0, 2) DF_ATTR(1, 2) DF_ATTR(2, 2)
+#undef DF_ATTR
+#define DF_SATTR(NS, NV)                                                                                   \
+  if (!e)                                                                                                 \
+    e = cudaFuncSetAttribute(k_df_synth<NS, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize,             \
+                             (int)df_synth_smem<NS, NV>(T));
+  DF_SATTR(1, 0) DF_SATTR(2, 0) DF_SATTR(0, 1) DF_SATTR(1, 1) DF_SATTR(2, 1)
+#undef DF_SATTR
+  return e ? cuda_fail(e, "cudaFuncSetAttribute(k_df_*)") : REXI_OK;
+}
+
+int df_legendre_create(DfLegendre** out, const double* P, const double* H, const double* w, const double* wq, int T,
+                       int nlat, int max_fields, cudaStream_t stream) {
+  *out = nullptr;
+  const int nh = nlat / 2;
+  if (df_anal_smem<2, 2>(nh) > 200 * 1024)  // 12 staged arrays of nh float4
+    return fail(REXI_EINVAL, "sh_plan_create: SH_DF supports nlat <= 2132 (got %d)", nlat);
+  DfLegendre* t = new DfLegendre();
+  t->T = T;
+  t->nlat = nlat;
+  t->nh = nh;
+  t->nlm = (T + 1) * (T + 2) / 2;
+  t->max_fields = max_fields;
+  const size_t tab = (size_t)t->nlm * nh;
+  const size_t per = std::max<size_t>(t->nlm, (size_t)(T + 1) * nlat);
+  cudaError_t e;
+  if ((e = cudaMalloc(&t->Ps, sizeof(float2) * tab)) || (e = cudaMalloc(&t->Hs, sizeof(float2) * tab)) ||
+      (e = cudaMalloc(&t->Pa, sizeof(float2) * tab)) || (e = cudaMalloc(&t->Ha, sizeof(float2) * tab)) ||
+      (e = cudaMalloc(&t->wdf, sizeof(float4) * nh)) ||
+      (e = cudaMalloc(&t->in, sizeof(float4) * per * 2 * (size_t)max_fields))) {
+    cudaGetLastError();
+    df_legendre_destroy(t);
+    return fail(REXI_ENOMEM, "double-float Legendre tables: cudaMalloc failed: %s", cudaGetErrorString(e));
+  }
+  k_df_split_table<<<dim3(T + 1, (nh + 127) / 128), 128, 0, stream>>>(P, t->Ps, t->Pa, T, nh);
+  k_df_split_table<<<dim3(T + 1, (nh + 127) / 128), 128, 0, stream>>>(H, t->Hs, t->Ha, T, nh);
+  k_df_split_weights<<<(nh + 127) / 128, 128, 0, stream>>>(w, wq, t->wdf, nh);
+  int rc = REXI_OK;
+  if ((e = cudaGetLastError())) rc = cuda_fail(e, "double-float table kernels");
+  if (!rc) rc = df_smem_attr(nh, T);
+  if (rc) {
+    df_legendre_destroy(t);
+    return rc;
+  }
+  *out = t;
+  return REXI_OK;
+}
+
+void df_legendre_destroy(DfLegendre* t) {
+  if (!t) return;
+  for (void* p : {(void*)t->Ps, (void*)t->Hs, (void*)t->Pa, (void*)t->Ha, (void*)t->wdf, (void*)t->in}) cudaFree(p);
+  delete t;
+}
+
+void df_legendre_set_prof(DfLegendre* t, StageProf* prof) {
+  if (t) t->prof = prof;
+}
+
+static void split_inputs(DfLegendre* t, const double2* s0, long long n0, const double2* s1, long long n1,
+                         const double2* s2, long long n2, cudaStream_t s) {
+  SplitSegs sg{};
+  sg.src[0] = s0;
+  sg.src[1] = s1;
+  sg.src[2] = s2;
+  sg.end[0] = n0;
+  sg.end[1] = n0 + n1;
+  sg.end[2] = n0 + n1 + n2;
+  if (sg.end[2] == 0) return;
+  k_df_split_inputs<<<(unsigned)((sg.end[2] + 255) / 256), 256, 0, s>>>(sg, t->in);
+}
+
+template <int NS, int NV>
+static void launch_synth(DfLegendre* t, DfSynthArgs a, cudaStream_t s) {
+  k_df_synth<NS, NV><<<dim3(t->T + 1, (t->nh + DF_STH - 1) / DF_STH), DF_STH, df_synth_smem<NS, NV>(t->T), s>>>(a);
+}
+
+int df_leg_synth(DfLegendre* t, const double2* spec, double2* F, int nfs, const double2* psi, const double2* chi,
+                 double2* FU, double2* FV, int nfv, double inv_a, cudaStream_t s) {
+  if (nfs < 0 || nfv < 0 || nfs + 2 * nfv > 2 * t->max_fields) return fail(REXI_EINVAL, "df synthesis: too many fields");
+  const int ph = t->prof ? t->prof->begin(1) : -1;
+  const long long nlm = t->nlm;
+  split_inputs(t, spec, nfs * nlm, psi, nfv * nlm, chi, nfv * nlm, s);
+  DfSynthArgs a{};
+  a.P = t->Ps;
+  a.H = t->Hs;
+  a.T = t->T;
+  a.nlat = t->nlat;
+  a.nh = t->nh;
+  a.nlm = t->nlm;
+  a.inv_a = inv_a;
+  const float4* cs = t->in;
+  const float4* cp = t->in + nfs * nlm;
+  const float4* cc = cp + nfv * nlm;
+  const size_t fo = (size_t)(t->T + 1) * t->nlat;
+  int fs = 0, fv = 0;
+  while (fs < nfs || fv < nfv) {
+    const int ns = std::min(2, nfs - fs), nv = std::min(1, nfv - fv);
+    a.cs = cs + fs * nlm;
+    a.cp = cp + fv * nlm;
+    a.cc = cc + fv * nlm;
+    a.F = F ? F + fs * fo : nullptr;
+    a.FU = FU ? FU + fv * fo : nullptr;
+    a.FV = FV ? FV + fv * fo : nullptr;
+    if (ns == 2 && nv == 1) launch_synth<2, 1>(t, a, s);
+    else if (ns == 1 && nv == 1) launch_synth<1, 1>(t, a, s);
+    else if (ns == 0) launch_synth<0, 1>(t, a, s);
+    else if (ns == 2) launch_synth<2, 0>(t, a, s);
+    else launch_synth<1, 0>(t, a, s);
+    fs += ns;
+    fv += nv;
+  }
+  if (t->prof) t->prof->end(ph);
+  cudaError_t e = cudaGetLastError();
+  return e ? cuda_fail(e, "k_df_synth launch") : REXI_OK;
+}
+
+template <int NS, int NV>
+static void launch_anal(DfLegendre* t, DfAnalArgs a, cudaStream_t s) {
+  k_df_anal<NS, NV><<<dim3(t->T + 1, (t->T + DF_ATH) / DF_ATH), DF_ATH, df_anal_smem<NS, NV>(t->nh), s>>>(a);
+}
+
+int df_leg_anal(DfLegendre* t, const double2* FA, const double2* FB, double2* dv, double2* cu, int nfv,
+                const double2* F, double2* spec, int nfs, double inv_a, cudaStream_t s) {
+  if (nfs < 0 || nfv < 0 || nfs + 2 * nfv > 2 * t->max_fields) return fail(REXI_EINVAL, "df analysis: too many fields");
+  const int ph = t->prof ? t->prof->begin(1) : -1;
+  const long long fo = (long long)(t->T + 1) * t->nlat;
+  split_inputs(t, FA, nfv * fo, FB, nfv * fo, F, nfs * fo, s);
+  DfAnalArgs a{};
+  a.P = t->Pa;
+  a.H = t->Ha;
+  a.wdf = t->wdf;
+  a.T = t->T;
+  a.nlat = t->nlat;
+  a.nh = t->nh;
+  a.nlm = t->nlm;
+  a.inv_a = inv_a;
+  const float4* fa = t->in;
+  const float4* fb = fa + nfv * fo;
+  const float4* fg = fb + nfv * fo;
+  int fs = 0, fv = 0;
+  while (fs < nfs || fv < nfv) {
+    const int ns = std::min(2, nfs - fs), nv = std::min(2, nfv - fv);
+    a.fa = fa + fv * fo;
+    a.fb = fb + fv * fo;
+    a.fg = fg + fs * fo;
+    a.dv = dv ? dv + (size_t)fv * t->nlm : nullptr;
+    a.cu = cu ? cu + (size_t)fv * t->nlm : nullptr;
+    a.spec = spec ? spec + (size_t)fs * t->nlm : nullptr;
+#define DF_CASE(NS, NV) \
+  else if (ns == NS && nv == NV) launch_anal<NS, NV>(t, a, s);
+    if (false) {
+    }
+    DF_CASE(1, 0) DF_CASE(2, 0) DF_CASE(0, 1) DF_CASE(1, 1) DF_CASE(2, 1) DF_CASE(0, 2) DF_CASE(1, 2) DF_CASE(2, 2)
+#undef DF_CASE
+    fs += ns;
+    fv += nv;
+  }
+  if (t->prof) t->prof->end(ph);
+  cudaError_t e = cudaGetLastError();
+  return e ? cuda_fail(e, "k_df_anal launch") : REXI_OK;
+}
+
+}  // namespace rexi

@@ -10,7 +10,7 @@ namespace rexi {
 // Per-stage CUDA-event timing of the SH transforms (off unless enabled): a pair of events on
 // the plan stream around every kernel launch, accumulated when collected.
 struct StageProf {
-  static constexpr int NSTAGE = 5;  // FP64 Legendre, TC operand pack, tcgen05 GEMM, TC epilogue, FFT
+  static constexpr int NSTAGE = 5;  // FP64 Legendre, double-float Legendre, tcgen05 GEMM, TC epilogue, FFT
   bool on = false;
   cudaStream_t stream = nullptr;
   struct Pend {

@@ -502,8 +502,8 @@ class LgPlan:
 
 
 # ---- spherical-harmonic transforms (include/sht.h) ------------------------------------
-SH_FP64, SH_TF32, SH_BF16, SH_TF32X3 = 0, 1, 2, 3
-_SH_PREC = {"fp64": SH_FP64, "tf32": SH_TF32, "bf16": SH_BF16, "tf32x3": SH_TF32X3}
+SH_FP64, SH_TF32, SH_BF16, SH_TF32X3, SH_DF = 0, 1, 2, 3, 4
+_SH_PREC = {"fp64": SH_FP64, "tf32": SH_TF32, "bf16": SH_BF16, "tf32x3": SH_TF32X3, "df": SH_DF}
 
 
 class ShDesc(ctypes.Structure):
@@ -521,7 +521,7 @@ for _n in ("sh_synthesis", "sh_analysis"):
 _lib.sh_plan_check.argtypes = [ctypes.c_void_p]
 _lib.sh_plan_set_profiling.argtypes = [ctypes.c_void_p, ctypes.c_int]
 _lib.sh_plan_get_profile.argtypes = [ctypes.c_void_p, _dp, _ip, ctypes.c_int]
-SH_STAGE_NAMES = ("legendre_fp64", "tc_pack", "tc_gemm", "tc_epilogue", "fft")
+SH_STAGE_NAMES = ("legendre_fp64", "legendre_df", "tc_gemm", "tc_epilogue", "fft")
 for _n in ("sh_synthesis_uv", "sh_analysis_divcurl"):
     getattr(_lib, _n).argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 4 + [ctypes.c_int]
 _lib.sh_synthesis_mixed.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 2 + [ctypes.c_int] + \

@@ -1,5 +1,8 @@
 """GPU parity of the spherical-harmonic transforms (paper Sec. 3.2) against the FP64 oracle,
-through the C ABI (include/sht.h).  FP64 path: 1e-12 relative (max norm over fields)."""
+through the C ABI (include/sht.h).  FP64 path: 1e-12 relative (max norm over fields).  The
+double-float Legendre precision (SH_DF) is held to the same bounds: its operands carry about 48
+significand bits and its sums are compensated dot products, whose error grows like the square
+of the FP32 unit (about 1e-13 relative for the sums here), below the FP64 path's 1e-12."""
 import numpy as np
 import pytest
 
@@ -42,13 +45,14 @@ def test_grid_matches_oracle(env, T, nlat, nlon):
     p.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "df"])
 @pytest.mark.parametrize("T,nlat,nlon", SIZES)
-def test_scalar_synthesis_analysis(env, T, nlat, nlon):
+def test_scalar_synthesis_analysis(env, T, nlat, nlon, prec):
     torch, rexi = env
     g = osht.Grid(T, nlat, nlon, A)
     nf = 3
     c = _spec(T, T, nf)
-    p = rexi.ShPlan(T, nlat, nlon, A, max_fields=nf)
+    p = rexi.ShPlan(T, nlat, nlon, A, max_fields=nf, precision=prec)
     cs = torch.from_numpy(c).cuda()
     grid = torch.empty(nf, nlat, nlon, dtype=torch.float64, device="cuda")
     p.synthesis(cs, grid, nf)
@@ -72,14 +76,15 @@ def test_scalar_synthesis_analysis(env, T, nlat, nlon):
     p.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "df"])
 @pytest.mark.parametrize("T,nlat,nlon", SIZES)
-def test_vector_transforms(env, T, nlat, nlon):
+def test_vector_transforms(env, T, nlat, nlon, prec):
     torch, rexi = env
     g = osht.Grid(T, nlat, nlon, A)
     nf = 2
     psi, chi = _spec(T, 1, nf), _spec(T, 2, nf)
     psi[:, 0] = chi[:, 0] = 0
-    p = rexi.ShPlan(T, nlat, nlon, A, max_fields=nf)
+    p = rexi.ShPlan(T, nlat, nlon, A, max_fields=nf, precision=prec)
     U = torch.empty(nf, nlat, nlon, dtype=torch.float64, device="cuda")
     V = torch.empty_like(U)
     p.synthesis_uv(torch.from_numpy(psi).cuda(), torch.from_numpy(chi).cuda(), U, V, nf)
@@ -99,13 +104,14 @@ def test_vector_transforms(env, T, nlat, nlon):
     p.close()
 
 
-def test_T511_sampled(env):
+@pytest.mark.parametrize("prec", ["fp64", "df"])
+def test_T511_sampled(env, prec):
     """Full T511 grid (768 x 1536): synthesis / analysis round trip on the GPU and the
     oracle's synthesis on a few latitudes (its full T511 tables take ~10 s)."""
     torch, rexi = env
     T, nlat, nlon = 511, 768, 1536
     c = _spec(T, 4, 1) * (np.arange(osht.nlm(T)) % 7 + 1.0) ** -1
-    p = rexi.ShPlan(T, nlat, nlon, A)
+    p = rexi.ShPlan(T, nlat, nlon, A, precision=prec)
     cs = torch.from_numpy(c).cuda()
     grid = torch.empty(1, nlat, nlon, dtype=torch.float64, device="cuda")
     p.synthesis(cs, grid)

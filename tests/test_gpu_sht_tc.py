@@ -188,7 +188,7 @@ MIXED = [(31, 48, 96, 4, 2, 1), (31, 48, 96, 4, 1, 2), (31, 48, 96, 4, 3, 2), (3
          (127, 192, 384, 3, 1, 1), (511, 768, 1536, 3, 2, 1), (511, 768, 1536, 3, 1, 2)]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "tf32", "bf16", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "tf32", "bf16", "tf32x3", "df"])
 @pytest.mark.parametrize("T,nlat,nlon,mf,nfs,nfv", MIXED)
 def test_mixed_transforms_equal_separate_calls(env, prec, T, nlat, nlon, mf, nfs, nfv):
     """sh_synthesis_mixed / sh_analysis_mixed (nfs scalar fields beside nfv vector pairs, one

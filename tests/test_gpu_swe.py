@@ -36,20 +36,22 @@ def _contour(T, dt):
     return (min(6.0, 1.6 * X), 1.6 * X) if X < 20 else (14.0, 1.4 * X)
 
 
+@pytest.mark.parametrize("sprec", ["fp64", "df"])
 @pytest.mark.parametrize("T,nlat,nlon", [(31, 48, 96), (63, 96, 192), (127, 192, 384)])
 @pytest.mark.parametrize("kind,tol", [("gaussian", 2e-9), ("balanced", 5e-9)])
-def test_nonlinear_matches_oracle(env, T, nlat, nlon, kind, tol):
+def test_nonlinear_matches_oracle(env, T, nlat, nlon, kind, tol, sprec):
     """N(U) against the oracle.  lap(KE) multiplies the rounding of the kinetic-energy
     analysis by n(n+1)/a^2 (1.6e4 at n = 127 relative to n = 1), which sets the bound of the
     divergence tendency at T127; for the geostrophically balanced state the tendencies are
     also small differences of large terms (|curl(zeta V)| ~ |lap KE| ~ 12 |N_delta|, and
-    V.grad Phi' nearly vanishes along isobars)."""
+    V.grad Phi' nearly vanishes along isobars).  The double-float Legendre precision meets the
+    FP64 bounds."""
     torch, rexi = env
     U = _state(T, 3) if kind == "balanced" else syn.gaussian_state(T, 3, scales=(1e3, 2e-5, 5e-6))
     g = osht.Grid(T, nlat, nlon, A)
     ref = oswe.nonlinear(U, g)
     p0, Xc = _contour(T, 1800.0)
-    plan = rexi.SwePlan(T, nlat, nlon, 1800.0, OM, A, PB, 64, p0, Xc)
+    plan = rexi.SwePlan(T, nlat, nlon, 1800.0, OM, A, PB, 64, p0, Xc, sh_precision=sprec)
     u = torch.from_numpy(U).cuda()
     t = torch.empty_like(u)
     plan.nonlinear(u, t)
