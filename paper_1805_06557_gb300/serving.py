@@ -142,6 +142,7 @@ class ServingEngine:
         self.done = []
         self.ticks = 0
         self.out_host = None  # pinned host buffer the results of a tick are copied into
+        self.prepared = None  # (batch, upload event) whose launch is built for the next tick
 
     # ---- admission ---------------------------------------------------------------------
     def _validate(self, r):
@@ -194,20 +195,30 @@ class ServingEngine:
         return admitted
 
     # ---- one tick ------------------------------------------------------------------------
-    def tick(self, on_launch=None):
-        """Admits what fits, launches one ragged REXI step over every admitted request,
-        admits late arrivals while it runs (on_launch callback), completes the tick."""
-        torch = self.torch
-        new = self._admit()
-        self.active.extend(new)
+    def _prepare(self):
+        """Admits what fits and builds its ragged launch (plan.set: host tile lists, uploads
+        queued in stream order behind the work in flight).  Returns the batch, or None."""
+        self.active.extend(self._admit())
         if not self.active:
-            return 0
+            return None
         batch = self.active
         self.active = []
-        ev = torch.cuda.Event()
-        ev.record(self.copy_stream)
-        self.stream.wait_event(ev)
+        ev = self.torch.cuda.Event()
+        ev.record(self.copy_stream)   # the batch's state uploads
         self.plan.set([(r.T, r.N, r.dt, r.p0, r.Xc, r.slot) for r in batch])
+        return batch, ev
+
+    def tick(self, on_launch=None):
+        """Launches one ragged REXI step over a batch of admitted requests and completes it.
+        While it runs, late arrivals are admitted (on_launch callback) and the next batch's
+        launch is built, so that the host work between two steps is only the copy-out."""
+        torch = self.torch
+        prep = self.prepared if self.prepared is not None else self._prepare()
+        self.prepared = None
+        if prep is None:
+            return 0
+        batch, ev = prep
+        self.stream.wait_event(ev)
         self.plan.step(self.U0, self.U1)
         # the results back to the host in the same stream order: one asynchronous copy per
         # request into one pinned buffer, then one wait for the tick
@@ -227,7 +238,7 @@ class ServingEngine:
         done_ev.record(self.stream)
         if on_launch is not None:
             on_launch()                      # arrivals during the tick
-        self.active.extend(self._admit())    # their copies overlap the running tick
+        self.prepared = self._prepare()      # the next launch, built while this one runs
         done_ev.synchronize()
         now = time.perf_counter()
         host = self.out_host.numpy()
@@ -255,9 +266,9 @@ class ServingEngine:
                 self.submit(pending[i])
                 i += 1
 
-        while i < len(pending) or self.queue or self.active:
+        while i < len(pending) or self.queue or self.active or self.prepared is not None:
             arrivals()
-            if not self.queue and not self.active:
+            if not self.queue and not self.active and self.prepared is None:
                 if i < len(pending):
                     time.sleep(max(0.0, min(0.01, pending[i].arrival - clock())))
                 continue
