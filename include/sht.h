@@ -30,7 +30,8 @@ extern "C" {
 #define SH_TF32X3 3
 /* Double-float on the FP32 CUDA cores: tables, inputs and sums carried as pairs of FP32 words
  * (about 48 significand bits), every contraction a compensated dot product (TwoProduct by FMA,
- * Knuth's TwoSum); the FFT stays FP64.  Close to FP64 accuracy without the FP64 pipe, which
+ * Knuth's TwoSum), the longitude FFT in double-float arithmetic too (FP64 grids and Fourier
+ * arrays at its ends).  Close to FP64 accuracy without the FP64 pipe, which
  * GB300 has little of (about 2 FP64 FMAs per clock and SM against 128 FP32 ones).  Tables take
  * three times the memory of SH_FP64 (the FP64 tables and two split layouts).  nlat <= 2132. */
 #define SH_DF 4

@@ -63,4 +63,29 @@ __device__ __forceinline__ void dot2_add2(dot2& acc, df a, df b) {
   acc.err = fmaf(a.lo, b.hi, fmaf(a.hi, b.lo, acc.err + (ep + t.lo)));
 }
 
+
+// ---- a double-float real with arithmetic operators (for code templated on its real type,
+// such as the longitude FFT): sums by TwoSum, products by TwoProduct, both renormalised -------
+struct dfr {
+  float hi, lo;
+  dfr() = default;
+  __device__ __forceinline__ dfr(float h, float l) : hi(h), lo(l) {}
+  // from FP64 (an FP64 conversion; constant arguments fold at compile time)
+  __device__ __forceinline__ explicit dfr(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+  __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+__device__ __forceinline__ dfr operator-(dfr a) { return dfr(-a.hi, -a.lo); }
+__device__ __forceinline__ dfr operator+(dfr a, dfr b) {
+  const df s = df_two_sum(a.hi, b.hi);
+  const df r = df_fast(s.hi, s.lo + (a.lo + b.lo));
+  return dfr(r.hi, r.lo);
+}
+__device__ __forceinline__ dfr operator-(dfr a, dfr b) { return a + (-b); }
+__device__ __forceinline__ dfr operator*(dfr a, dfr b) {
+  const df r = df_mul(df{a.hi, a.lo}, df{b.hi, b.lo});
+  return dfr(r.hi, r.lo);
+}
+// by a sign (+1 or -1)
+__device__ __forceinline__ dfr operator*(int s, dfr a) { return s > 0 ? a : -a; }
+
 }  // namespace rexi

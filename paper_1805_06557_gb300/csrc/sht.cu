@@ -20,6 +20,7 @@
 
 #include "../../include/sht.h"
 #include "common.cuh"
+#include "df.cuh"
 #include "sht_df.cuh"
 #include "sht_tc.cuh"
 
@@ -279,7 +280,8 @@ __global__ void __launch_bounds__(ATH) k_leg_anal_divcurl(const double* __restri
 
 // ---- longitude FFT (Stockham autosort, radix 8, 4, 2 and 3, shared memory) -----------------
 // Templated on the arithmetic type: FP64 for SH_FP64 plans, FP32 for the tensor-core plans
-// (whose Legendre stage already rounds to TF32 / BF16); grids and Fourier arrays stay FP64.
+// (whose Legendre stage already rounds to TF32 / BF16), double-float for SH_DF plans (FP32
+// pipe, about 48 bits); grids and Fourier arrays stay FP64.
 struct FftPlan {
   int n, nrad;
   int rad[24];
@@ -302,6 +304,21 @@ template <> struct Cx<float2> {
   using R = float;
   static __device__ __forceinline__ float2 make(float x, float y) { return make_float2(x, y); }
 };
+// double-float complex (SH_DF plans): about 48 significand bits on the FP32 pipe, the same 16
+// bytes as double2 in shared memory and in the twiddle tables
+struct dfcx {
+  dfr x, y;
+};
+template <> struct Cx<dfcx> {
+  using R = dfr;
+  static __device__ __forceinline__ dfcx make(dfr x, dfr y) { return dfcx{x, y}; }
+};
+// one twiddle-table entry
+__device__ __forceinline__ double2 ld_tw(const double2* p) { return __ldg(p); }
+__device__ __forceinline__ dfcx ld_tw(const dfcx* p) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  return dfcx{dfr(v.x, v.y), dfr(v.z, v.w)};
+}
 template <typename C> __device__ __forceinline__ C c_mul(C a, C b) {
   return Cx<C>::make(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -390,7 +407,7 @@ __device__ __forceinline__ void fft_pass(Src src, Dst dst, int n, int Ns, unsign
         }
       } else {
 #pragma unroll
-        for (int r = 1; r < R; ++r) apply(r, __ldg(twp + jm * W + r));
+        for (int r = 1; r < R; ++r) apply(r, ld_tw(twp + jm * W + r));
       }
     }
     if (R == 2) {
@@ -403,7 +420,7 @@ __device__ __forceinline__ void fft_pass(Src src, Dst dst, int n, int Ns, unsign
       const C s1 = c_add(v[1], v[2]);
       const C t2 = Cx<C>::make(v[0].x - Rt(0.5) * s1.x, v[0].y - Rt(0.5) * s1.y);
       const C d = c_sub(v[1], v[2]);
-      const Rt sg = Rt(sign * SQRT3_2);
+      const Rt sg = sign > 0 ? Rt(SQRT3_2) : Rt(-SQRT3_2);  // constants: folded at compile time
       const C x0 = c_add(v[0], s1);
       v[1] = Cx<C>::make(t2.x - sg * d.y, t2.y + sg * d.x);
       v[2] = Cx<C>::make(t2.x + sg * d.y, t2.y - sg * d.x);
@@ -552,6 +569,18 @@ __global__ void __launch_bounds__(FTH) k_fft_anal64(const __grid_constant__ FftS
   fft_anal_block<double2>(sg, fp, tw, T, nlat);
 }
 
+// double-float transforms (SH_DF plans): FP64 inputs and outputs, arithmetic on the FP32 pipe
+__global__ void __launch_bounds__(FTH) k_fft_synth_df(const __grid_constant__ FftSegs sg,
+                                                      const __grid_constant__ FftPlan fp,
+                                                      const dfcx* __restrict__ tw, int T, int nlat) {
+  fft_synth_block<dfcx>(sg, fp, tw, T, nlat);
+}
+__global__ void __launch_bounds__(FTH) k_fft_anal_df(const __grid_constant__ FftSegs sg,
+                                                     const __grid_constant__ FftPlan fp,
+                                                     const dfcx* __restrict__ tw, int T, int nlat) {
+  fft_anal_block<dfcx>(sg, fp, tw, T, nlat);
+}
+
 // Gauss-Legendre nodes (north to south) and weights: Newton iteration on P_n
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
   x.assign(n, 0.0);
@@ -654,7 +683,9 @@ struct sh_plan {
   double* d_H = nullptr;
   double2* d_tw = nullptr;  // twiddle tables of the FFT passes (fft_twiddle_tables)
   float2* d_tw32 = nullptr; // the same in FP32, for the FFT of the tensor-core plans
+  float4* d_twdf = nullptr; // the same as double-float pairs (re.hi, re.lo, im.hi, im.lo), SH_DF
   bool fft32 = false;
+  bool fftdf = false;       // double-float FFT (SH_DF)
   double2* d_F = nullptr;   // Fourier workspace [2 * max_fields][T+1][nlat]
   FftPlan fp{};
   TcLegendre* tc = nullptr;  // tensor-core Legendre state (SH_TF32 / SH_BF16 / SH_TF32X3)
@@ -686,7 +717,8 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
   p->nlm = (d.T + 1) * (d.T + 2) / 2;
   p->stream = (cudaStream_t)d.stream;
   p->prof.stream = p->stream;
-  p->fft32 = d.precision != SH_FP64 && d.precision != SH_DF;  // SH_DF keeps the FP64 FFT
+  p->fft32 = d.precision != SH_FP64 && d.precision != SH_DF;
+  p->fftdf = d.precision == SH_DF;
   auto bail = [&](int code) {
     sh_plan_destroy(p);
     return code;
@@ -700,16 +732,20 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
   const size_t ntw = twt.size();
   std::vector<double2> tw(ntw);
   std::vector<float2> tw32(ntw);
+  std::vector<float4> twdf(ntw);
+  auto lo_of = [](double x) { return (float)(x - (double)(float)x); };
   for (size_t k = 0; k < ntw; ++k) {
-    tw[k] = make_double2(twt[k].real(), twt[k].imag());
-    tw32[k] = make_float2((float)twt[k].real(), (float)twt[k].imag());
+    const double re = twt[k].real(), im = twt[k].imag();
+    tw[k] = make_double2(re, im);
+    tw32[k] = make_float2((float)re, (float)im);
+    twdf[k] = make_float4((float)re, lo_of(re), (float)im, lo_of(im));
   }
   const size_t tab = (size_t)p->nlm * p->nh;
   cudaError_t e;
   if ((e = cudaMalloc(&p->d_mu, sizeof(double) * p->nh)) || (e = cudaMalloc(&p->d_w, sizeof(double) * p->nh)) ||
       (e = cudaMalloc(&p->d_wq, sizeof(double) * p->nh)) || (e = cudaMalloc(&p->d_P, sizeof(double) * tab)) ||
       (e = cudaMalloc(&p->d_H, sizeof(double) * tab)) || (e = cudaMalloc(&p->d_tw, sizeof(double2) * ntw)) ||
-      (e = cudaMalloc(&p->d_tw32, sizeof(float2) * ntw)) ||
+      (e = cudaMalloc(&p->d_tw32, sizeof(float2) * ntw)) || (e = cudaMalloc(&p->d_twdf, sizeof(float4) * ntw)) ||
       (e = cudaMalloc(&p->d_F, sizeof(double2) * 2 * (size_t)d.max_fields * (d.T + 1) * d.nlat))) {
     cudaGetLastError();
     return bail(fail(REXI_ENOMEM, "sh_plan_create: cudaMalloc failed: %s", cudaGetErrorString(e)));
@@ -718,13 +754,17 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
       (e = cudaMemcpy(p->d_w, p->w.data(), sizeof(double) * p->nh, cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(p->d_wq, wq.data(), sizeof(double) * p->nh, cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(p->d_tw, tw.data(), sizeof(double2) * ntw, cudaMemcpyHostToDevice)) ||
-      (e = cudaMemcpy(p->d_tw32, tw32.data(), sizeof(float2) * ntw, cudaMemcpyHostToDevice)))
+      (e = cudaMemcpy(p->d_tw32, tw32.data(), sizeof(float2) * ntw, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(p->d_twdf, twdf.data(), sizeof(float4) * ntw, cudaMemcpyHostToDevice)))
     return bail(cuda_fail(e, "sh_plan_create: cudaMemcpy"));
   k_legendre_table<<<dim3((p->nh + 127) / 128, d.T + 1), 128, 0, p->stream>>>(p->d_mu, p->d_P, p->d_H, d.T, p->nh);
   if ((e = cudaGetLastError())) return bail(cuda_fail(e, "k_legendre_table"));
   if (p->fft32) {
     e = cudaFuncSetAttribute(k_fft_synth32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p));
     if (!e) e = cudaFuncSetAttribute(k_fft_anal32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p));
+  } else if (p->fftdf) {
+    e = cudaFuncSetAttribute(k_fft_synth_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p));
+    if (!e) e = cudaFuncSetAttribute(k_fft_anal_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p));
   } else {
     e = cudaFuncSetAttribute(k_fft_synth64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p));
     if (!e) e = cudaFuncSetAttribute(k_fft_anal64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p));
@@ -756,6 +796,7 @@ extern "C" int sh_plan_destroy(sh_plan* p) {
   cudaFree(p->d_H);
   cudaFree(p->d_tw);
   cudaFree(p->d_tw32);
+  cudaFree(p->d_twdf);
   cudaFree(p->d_F);
   tc_legendre_destroy(p->tc);
   df_legendre_destroy(p->dfl);
@@ -800,6 +841,9 @@ static void launch_fft_synth(sh_plan* p, const FftSegs& sg) {
   const dim3 grid(p->d.nlat / 2, sg.start[3]);
   if (p->fft32)
     k_fft_synth32<<<grid, FTH, fft_smem(p), p->stream>>>(sg, p->fp, p->d_tw32, p->d.T, p->d.nlat);
+  else if (p->fftdf)
+    k_fft_synth_df<<<grid, FTH, fft_smem(p), p->stream>>>(sg, p->fp, reinterpret_cast<const dfcx*>(p->d_twdf),
+                                                          p->d.T, p->d.nlat);
   else
     k_fft_synth64<<<grid, FTH, fft_smem(p), p->stream>>>(sg, p->fp, p->d_tw, p->d.T, p->d.nlat);
   p->prof.end(ph);
@@ -809,6 +853,9 @@ static void launch_fft_anal(sh_plan* p, const FftSegs& sg) {
   const dim3 grid(p->d.nlat / 2, sg.start[3]);
   if (p->fft32)
     k_fft_anal32<<<grid, FTH, fft_smem(p), p->stream>>>(sg, p->fp, p->d_tw32, p->d.T, p->d.nlat);
+  else if (p->fftdf)
+    k_fft_anal_df<<<grid, FTH, fft_smem(p), p->stream>>>(sg, p->fp, reinterpret_cast<const dfcx*>(p->d_twdf),
+                                                         p->d.T, p->d.nlat);
   else
     k_fft_anal64<<<grid, FTH, fft_smem(p), p->stream>>>(sg, p->fp, p->d_tw, p->d.T, p->d.nlat);
   p->prof.end(ph);

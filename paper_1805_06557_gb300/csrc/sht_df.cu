@@ -7,7 +7,8 @@
 // sum a compensated dot product (Ogita, Rump & Oishi's Dot2: TwoProduct by FMA, Knuth's TwoSum,
 // the errors gathered in one FP32 word), all on the FP32 pipe.  Only the conversions touch FP64:
 // the tables are split once at plan time, the inputs of a call by one pass kernel, and the
-// results are formed in FP64 from the two words of each sum.
+// results are formed in FP64 from the two words of each sum.  The longitude FFT of these plans
+// runs in double-float arithmetic as well (sht.cu).
 //
 // Tables (split from the FP64 ones): synthesis [moff(m)+k][nh] (latitude fastest, as the FP64
 // table: threads that own latitudes read coalesced); analysis, per m, [nh][K] with the even
