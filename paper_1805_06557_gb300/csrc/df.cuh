@@ -88,4 +88,39 @@ __device__ __forceinline__ dfr operator*(dfr a, dfr b) {
 // by a sign (+1 or -1)
 __device__ __forceinline__ dfr operator*(int s, dfr a) { return s > 0 ? a : -a; }
 
+// ---- FP64 <-> double-float by the bit patterns (integer pipe; GB300's FP64 pipe, which the
+// conversion instructions use, issues about 2 operations per clock and SM) -------------------
+// the float with sign sgn, biased exponent be (1..254) and the 23 fraction bits below the
+// leading one of r (r != 0), truncated
+__device__ __forceinline__ float df_bits_float(unsigned sgn, int be, unsigned r) {
+  const int lz = __clz(r);  // <= 31; the shift below moves the leading one to bit 32
+  const unsigned frac = (unsigned)((((unsigned long long)r) << (lz + 1)) >> 9) & 0x7fffffu;
+  return __uint_as_float(sgn | ((unsigned)be << 23) | frac);
+}
+// x = hi + lo: hi its leading 24 significand bits, lo the next 24 (both truncated; about 48 bits
+// of x); values whose low word could leave the FP32 normal range (|x| < 2^-73, zeros and
+// subnormals included) or whose high word would overflow take the FP64 route
+__device__ __forceinline__ dfr dfr_from_bits(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned sgn = (unsigned)(u >> 32) & 0x80000000u;
+  const int e = (int)((u >> 52) & 0x7ff);
+  const int ef = e - 1023 + 127;  // FP32 biased exponent of the leading bit
+  if (ef < 54 || ef > 254) return dfr(x);
+  const unsigned long long m = u & 0xFFFFFFFFFFFFFull;  // 52 stored fraction bits
+  const float hi = __uint_as_float(sgn | ((unsigned)ef << 23) | (unsigned)(m >> 29));
+  const unsigned r = (unsigned)(m & 0x1FFFFFFFu);  // the remaining 29 bits, weight 2^(e - 1075)
+  if (r == 0) return dfr(hi, 0.f);
+  // leading bit of r at position 31 - clz(r) >= 0: biased exponent ef - 52 + (31 - clz(r)) >= 2
+  return dfr(hi, df_bits_float(sgn, ef - 52 + 31 - __clz(r), r));
+}
+// a float widened exactly to FP64 from its bits
+__device__ __forceinline__ double df_widen(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned ef = (b >> 23) & 0xff;
+  if (ef == 0 || ef == 255) return (double)f;  // zero, subnormal, inf, nan
+  const unsigned long long d = ((unsigned long long)(b & 0x80000000u) << 32) |
+                               ((unsigned long long)(ef + 896) << 52) | ((unsigned long long)(b & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)d);
+}
+
 }  // namespace rexi

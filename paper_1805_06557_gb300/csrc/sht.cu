@@ -296,13 +296,20 @@ constexpr int FTH = 256;
 constexpr double SQRT3_2 = 0.86602540378443864676;  // sin(2 pi / 3)
 
 template <typename C> struct Cx;
+// per arithmetic type: make, and the butterfly constants 1/sqrt(2), 1/2 and sin(2 pi / 3)
 template <> struct Cx<double2> {
   using R = double;
   static __device__ __forceinline__ double2 make(double x, double y) { return make_double2(x, y); }
+  static __device__ __forceinline__ double rsqrt2() { return 0.70710678118654752440; }
+  static __device__ __forceinline__ double half() { return 0.5; }
+  static __device__ __forceinline__ double sqrt3_2() { return SQRT3_2; }
 };
 template <> struct Cx<float2> {
   using R = float;
   static __device__ __forceinline__ float2 make(float x, float y) { return make_float2(x, y); }
+  static __device__ __forceinline__ float rsqrt2() { return 0.70710678118654752440f; }
+  static __device__ __forceinline__ float half() { return 0.5f; }
+  static __device__ __forceinline__ float sqrt3_2() { return (float)SQRT3_2; }
 };
 // double-float complex (SH_DF plans): about 48 significand bits on the FP32 pipe, the same 16
 // bytes as double2 in shared memory and in the twiddle tables
@@ -312,6 +319,10 @@ struct dfcx {
 template <> struct Cx<dfcx> {
   using R = dfr;
   static __device__ __forceinline__ dfcx make(dfr x, dfr y) { return dfcx{x, y}; }
+  // the constants as exact (hi, lo) pairs of FP32 literals: no FP64 conversion in the butterflies
+  static __device__ __forceinline__ dfr rsqrt2() { return dfr(0x1.6a09e6p-1f, 0x1.9fcef4p-27f); }
+  static __device__ __forceinline__ dfr half() { return dfr(0.5f, 0.f); }
+  static __device__ __forceinline__ dfr sqrt3_2() { return dfr(0x1.bb67aep-1f, 0x1.0b0996p-26f); }
 };
 // one twiddle-table entry
 __device__ __forceinline__ double2 ld_tw(const double2* p) { return __ldg(p); }
@@ -344,7 +355,7 @@ template <typename C> __device__ __forceinline__ void dft4(C& v0, C& v1, C& v2, 
 }
 template <typename C> __device__ __forceinline__ void dft8(C* v, int sign) {
   using R = typename Cx<C>::R;
-  const R h = R(0.70710678118654752440);  // 1/sqrt(2)
+  const R h = Cx<C>::rsqrt2();
   dft4(v[0], v[2], v[4], v[6], sign);     // even samples -> E_0..E_3 in v[0], v[2], v[4], v[6]
   dft4(v[1], v[3], v[5], v[7], sign);     // odd samples  -> O_0..O_3 in v[1], v[3], v[5], v[7]
   // twiddles w8^k O_k, w8 = (1 + sign i) / sqrt 2
@@ -418,9 +429,9 @@ __device__ __forceinline__ void fft_pass(Src src, Dst dst, int n, int Ns, unsign
       dft8(v, sign);
     } else {  // R == 3
       const C s1 = c_add(v[1], v[2]);
-      const C t2 = Cx<C>::make(v[0].x - Rt(0.5) * s1.x, v[0].y - Rt(0.5) * s1.y);
+      const C t2 = Cx<C>::make(v[0].x - Cx<C>::half() * s1.x, v[0].y - Cx<C>::half() * s1.y);
       const C d = c_sub(v[1], v[2]);
-      const Rt sg = sign > 0 ? Rt(SQRT3_2) : Rt(-SQRT3_2);  // constants: folded at compile time
+      const Rt sg = sign * Cx<C>::sqrt3_2();
       const C x0 = c_add(v[0], s1);
       v[1] = Cx<C>::make(t2.x - sg * d.y, t2.y + sg * d.x);
       v[2] = Cx<C>::make(t2.x + sg * d.y, t2.y - sg * d.x);

@@ -37,18 +37,23 @@ __device__ __forceinline__ float2 split_df(double x) {
   const float hi = (float)x;
   return make_float2(hi, (float)(x - (double)hi));
 }
+// the inputs of a call: split by the bit patterns (integer pipe), not by FP64 arithmetic
 __device__ __forceinline__ float4 split_dfc(double2 v) {
-  const float2 a = split_df(v.x), b = split_df(v.y);
-  return make_float4(a.x, a.y, b.x, b.y);
+  const dfr a = dfr_from_bits(v.x), b = dfr_from_bits(v.y);
+  return make_float4(a.hi, a.lo, b.hi, b.lo);
 }
 __device__ __forceinline__ df df_of(float2 v) { return df{v.x, v.y}; }
 __device__ __forceinline__ df dfre(float4 v) { return df{v.x, v.y}; }
 __device__ __forceinline__ df dfim(float4 v) { return df{v.z, v.w}; }
 
-// the value of a + sg b (sg = +-1) of two compensated sums, rounded once to FP64
+// the value of a + sg b (sg = +-1) of two compensated sums, rounded once to FP64; BITS widens
+// the two words from their bit patterns (integer pipe) instead of by FP64 conversions -- the
+// two forms give the same value and differ only in the registers the synthesis kernel takes
+template <bool BITS>
 __device__ __forceinline__ double dsum(const dot2& a, const dot2& b, float sg) {
   const df t = df_two_sum(a.s, sg * b.s);
-  return (double)t.hi + (double)(t.lo + (a.err + sg * b.err));
+  const float lo = t.lo + (a.err + sg * b.err);
+  return BITS ? df_widen(t.hi) + df_widen(lo) : (double)t.hi + (double)lo;
 }
 __device__ __forceinline__ double dval(const dot2& a) { return (double)a.s + (double)a.err; }
 
@@ -139,8 +144,11 @@ constexpr int DF_PF = 4;  // table entries loaded this many degrees (synthesis) 
 // H_n(-mu) = -(-1)^(n-m) H_n(mu)); vector pairs give U = (-H psi + i m P chi)/a and
 // V = (i m P psi + H chi)/a.  The block stages its zonal order's split coefficients in shared
 // memory; each thread keeps the table entries of the next DF_PF degrees in flight.
-template <int NS, int NV>
-__global__ void __launch_bounds__(DF_STH) k_df_synth(const __grid_constant__ DfSynthArgs a) {
+// MINB: blocks per SM the registers must allow (5 for launches of several waves, where
+// occupancy hides the table loads; 1 for small ones, where each block's own overlap counts)
+template <int NS, int NV, int MINB>
+__global__ void __launch_bounds__(DF_STH, MINB) k_df_synth(const __grid_constant__ DfSynthArgs a) {
+  constexpr bool BITS = MINB > 1;  // the result form that fits the tighter register budget
   extern __shared__ float4 cf[];
   const int m = blockIdx.x;
   const int T = a.T, K = T + 1 - m, base = moff(T, m), nlat = a.nlat, nh = a.nh;
@@ -195,8 +203,8 @@ __global__ void __launch_bounds__(DF_STH) k_df_synth(const __grid_constant__ DfS
 #pragma unroll
   for (int f = 0; f < NS; ++f) {
     double2* o = a.F + ((size_t)f * (T + 1) + m) * nlat;
-    o[lat] = make_double2(dsum(S[f][0][0], S[f][1][0], 1.f), dsum(S[f][0][1], S[f][1][1], 1.f));
-    o[lats] = make_double2(dsum(S[f][0][0], S[f][1][0], -1.f), dsum(S[f][0][1], S[f][1][1], -1.f));
+    o[lat] = make_double2(dsum<BITS>(S[f][0][0], S[f][1][0], 1.f), dsum<BITS>(S[f][0][1], S[f][1][1], 1.f));
+    o[lats] = make_double2(dsum<BITS>(S[f][0][0], S[f][1][0], -1.f), dsum<BITS>(S[f][0][1], S[f][1][1], -1.f));
   }
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
@@ -211,7 +219,7 @@ __global__ void __launch_bounds__(DF_STH) k_df_synth(const __grid_constant__ DfS
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int c = 0; c < 2; ++c) x[q][c] = (q >= 2 ? sh : 1.0) * dsum(V[v][q][0][c], V[v][q][1][c], so);
+        for (int c = 0; c < 2; ++c) x[q][c] = (q >= 2 ? sh : 1.0) * dsum<BITS>(V[v][q][0][c], V[v][q][1][c], so);
       const double fm = (double)m, ia = a.inv_a;
       const int j = hs ? lats : lat;
       oU[j] = make_double2(ia * (-x[2][0] - fm * x[1][1]), ia * (-x[2][1] + fm * x[1][0]));
@@ -381,7 +389,7 @@ size_t df_anal_smem(int nh) {
 }  // namespace
 
 struct DfLegendre {
-  int T = 0, nlat = 0, nh = 0, nlm = 0, max_fields = 0;
+  int T = 0, nlat = 0, nh = 0, nlm = 0, max_fields = 0, nsm = 0;
   float2 *Ps = nullptr, *Hs = nullptr, *Pa = nullptr, *Ha = nullptr;
   float4* wdf = nullptr;
   float4* in = nullptr;  // split inputs of one call: [2 max_fields][max(nlm, (T+1) nlat)]
@@ -398,7 +406,10 @@ static int df_smem_attr(int nh, int T) {
 #undef DF_ATTR
 #define DF_SATTR(NS, NV)                                                                                   \
   if (!e)                                                                                                 \
-    e = cudaFuncSetAttribute(k_df_synth<NS, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize,             \
+    e = cudaFuncSetAttribute(k_df_synth<NS, NV, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
+                             (int)df_synth_smem<NS, NV>(T));                                              \
+  if (!e)                                                                                                 \
+    e = cudaFuncSetAttribute(k_df_synth<NS, NV, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
                              (int)df_synth_smem<NS, NV>(T));
   DF_SATTR(1, 0) DF_SATTR(2, 0) DF_SATTR(0, 1) DF_SATTR(1, 1) DF_SATTR(2, 1)
 #undef DF_SATTR
@@ -417,6 +428,11 @@ int df_legendre_create(DfLegendre** out, const double* P, const double* H, const
   t->nh = nh;
   t->nlm = (T + 1) * (T + 2) / 2;
   t->max_fields = max_fields;
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&t->nsm, cudaDevAttrMultiProcessorCount, dev);
+  }
   const size_t tab = (size_t)t->nlm * nh;
   const size_t per = std::max<size_t>(t->nlm, (size_t)(T + 1) * nlat);
   cudaError_t e;
@@ -467,7 +483,12 @@ static void split_inputs(DfLegendre* t, const double2* s0, long long n0, const d
 
 template <int NS, int NV>
 static void launch_synth(DfLegendre* t, DfSynthArgs a, cudaStream_t s) {
-  k_df_synth<NS, NV><<<dim3(t->T + 1, (t->nh + DF_STH - 1) / DF_STH), DF_STH, df_synth_smem<NS, NV>(t->T), s>>>(a);
+  const dim3 grid(t->T + 1, (t->nh + DF_STH - 1) / DF_STH);
+  const size_t smem = df_synth_smem<NS, NV>(t->T);
+  if ((long long)grid.x * grid.y >= 4LL * t->nsm)
+    k_df_synth<NS, NV, 5><<<grid, DF_STH, smem, s>>>(a);
+  else
+    k_df_synth<NS, NV, 1><<<grid, DF_STH, smem, s>>>(a);
 }
 
 int df_leg_synth(DfLegendre* t, const double2* spec, double2* F, int nfs, const double2* psi, const double2* chi,
