@@ -141,3 +141,35 @@ def test_errors(env):
         rexi.ShPlan(31, 48, 60, A)       # nlon <= 2T
     with pytest.raises(rexi.RexiError):
         rexi.ShPlan(31, 48, 70, A)       # nlon not 2^p 3^q
+
+
+@pytest.mark.parametrize("scale", [1e-25, 1e25])
+def test_double_float_magnitudes(env, scale):
+    """SH_DF inside its documented range (the FP32 exponent range): spectra scaled by 1e+-25 give
+    the FP64 plan's results to the same relative accuracy (synthesis, analysis of the grids,
+    vector transforms); tiny values take the FP64 route of the input split."""
+    torch, rexi = env
+    T, nlat, nlon, nf = 63, 96, 192, 2
+    c = _spec(T, 31, nf) * scale
+    psi, chi = _spec(T, 32, 1) * scale, _spec(T, 33, 1) * scale
+    psi[:, 0] = chi[:, 0] = 0
+    out = {}
+    for prec in ("fp64", "df"):
+        p = rexi.ShPlan(T, nlat, nlon, A, max_fields=nf, precision=prec)
+        cs = torch.from_numpy(c).cuda()
+        grid = torch.empty(nf, nlat, nlon, dtype=torch.float64, device="cuda")
+        U = torch.empty(1, nlat, nlon, dtype=torch.float64, device="cuda")
+        V = torch.empty_like(U)
+        p.synthesis(cs, grid, nf)
+        p.synthesis_uv(torch.from_numpy(psi).cuda(), torch.from_numpy(chi).cuda(), U, V, 1)
+        back = torch.empty_like(cs)
+        p.analysis(grid, back, nf)
+        dv = torch.empty(1, osht.nlm(T), dtype=torch.complex128, device="cuda")
+        cu = torch.empty_like(dv)
+        p.analysis_divcurl(U, V, dv, cu, 1)
+        p.check()
+        out[prec] = [x.cpu().numpy() for x in (grid, U, V, back, dv, cu)]
+        p.close()
+    for name, a, b in zip(("grid", "U", "V", "spec", "div", "curl"), out["df"], out["fp64"]):
+        assert np.all(np.isfinite(a)), name
+        assert _rel(a, b) < 1e-12, (name, _rel(a, b))
