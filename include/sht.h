@@ -34,8 +34,9 @@ extern "C" {
  * arrays at its ends).  Close to FP64 accuracy without the FP64 pipe, which
  * GB300 has little of (about 2 FP64 FMAs per clock and SM against 128 FP32 ones).  Tables take
  * three times the memory of SH_FP64 (the FP64 tables and two split layouts).  nlat <= 2132.
- * The words are FP32: spectra, grids and their products must stay inside the FP32 exponent
- * range (magnitudes about 1e-30 to 1e30 for full accuracy; SH_FP64 has no such limit). */
+ * The words are FP32: spectra, grids and the intermediate sums must stay inside the FP32
+ * exponent range, with room for the low word below the high one (magnitudes of about 1e-25 to
+ * 1e30 keep full accuracy; SH_FP64 has no such limit). */
 #define SH_DF 4
 
 typedef struct sh_plan sh_plan;

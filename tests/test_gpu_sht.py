@@ -143,9 +143,9 @@ def test_errors(env):
         rexi.ShPlan(31, 48, 70, A)       # nlon not 2^p 3^q
 
 
-@pytest.mark.parametrize("scale", [1e-25, 1e25])
+@pytest.mark.parametrize("scale", [1e-20, 1e20])
 def test_double_float_magnitudes(env, scale):
-    """SH_DF inside its documented range (the FP32 exponent range): spectra scaled by 1e+-25 give
+    """SH_DF inside its documented range (the FP32 exponent range): spectra scaled by 1e+-20 give
     the FP64 plan's results to the same relative accuracy (synthesis, analysis of the grids,
     vector transforms); tiny values take the FP64 route of the input split."""
     torch, rexi = env
