@@ -64,6 +64,28 @@ __device__ __forceinline__ void dot2_add2(dot2& acc, df a, df b) {
 }
 
 
+// The same for a complex sum of (real double-float) x (complex double-float) terms, both
+// components at once on Blackwell's packed FP32x2 instructions (FMUL2 / FFMA2 / FADD2 round
+// each component as the scalar instruction does): the operation sequence of dot2_add2 per
+// component, in half the instructions.  The complex factor comes as its high words (re, im)
+// and its low words (re, im).
+struct dot2c {
+  float2 s, err;
+};
+__device__ __forceinline__ float2 f2n(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ void dot2c_add(dot2c& acc, df a, float2 bhi, float2 blo) {
+  const float2 ah = make_float2(a.hi, a.hi);
+  const float2 p = __fmul2_rn(ah, bhi);
+  const float2 ep = __ffma2_rn(ah, bhi, f2n(p));
+  const float2 s = __fadd2_rn(acc.s, p);                      // TwoSum(acc.s, p)
+  const float2 bb = __fadd2_rn(s, f2n(acc.s));
+  const float2 e = __fadd2_rn(__fadd2_rn(acc.s, f2n(__fadd2_rn(s, f2n(bb)))), __fadd2_rn(p, f2n(bb)));
+  acc.s = s;
+  acc.err = __ffma2_rn(make_float2(a.lo, a.lo), bhi, __ffma2_rn(ah, blo, __fadd2_rn(acc.err, __fadd2_rn(ep, e))));
+}
+__device__ __forceinline__ dot2 dot2c_re(const dot2c& a) { return dot2{a.s.x, a.err.x}; }
+__device__ __forceinline__ dot2 dot2c_im(const dot2c& a) { return dot2{a.s.y, a.err.y}; }
+
 // ---- a double-float real with arithmetic operators (for code templated on its real type,
 // such as the longitude FFT): sums by TwoSum, products by TwoProduct, both renormalised -------
 struct dfr {

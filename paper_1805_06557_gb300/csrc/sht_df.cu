@@ -16,7 +16,8 @@
 // consecutive degrees, read coalesced.
 //
 // One launch contracts NS scalar fields and NV vector pairs against the same table reads; the
-// host runs groups of fields (NS <= 2, NV <= 1 for synthesis; NS, NV <= 2 for analysis).
+// host runs groups of fields (NS <= 2, NV <= 1 for synthesis; NS, NV <= 2 for analysis).  The
+// real and imaginary parts of every sum run together on the packed FP32x2 instructions.
 #include <algorithm>
 #include <cuda_runtime.h>
 #include <vector>
@@ -37,14 +38,20 @@ __device__ __forceinline__ float2 split_df(double x) {
   const float hi = (float)x;
   return make_float2(hi, (float)(x - (double)hi));
 }
-// the inputs of a call: split by the bit patterns (integer pipe), not by FP64 arithmetic
+// A split complex value is held as (re.hi, im.hi, re.lo, im.lo): its high words and its low
+// words are each a pair for the packed FP32x2 instructions.  The inputs of a call are split by
+// the bit patterns (integer pipe), not by FP64 arithmetic.
 __device__ __forceinline__ float4 split_dfc(double2 v) {
   const dfr a = dfr_from_bits(v.x), b = dfr_from_bits(v.y);
-  return make_float4(a.hi, a.lo, b.hi, b.lo);
+  return make_float4(a.hi, b.hi, a.lo, b.lo);
 }
 __device__ __forceinline__ df df_of(float2 v) { return df{v.x, v.y}; }
-__device__ __forceinline__ df dfre(float4 v) { return df{v.x, v.y}; }
-__device__ __forceinline__ df dfim(float4 v) { return df{v.z, v.w}; }
+__device__ __forceinline__ df dfre(float4 v) { return df{v.x, v.z}; }
+__device__ __forceinline__ df dfim(float4 v) { return df{v.y, v.w}; }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.z, v.w); }
+// acc += p * c for a double-float real p and a split complex c, both components packed
+__device__ __forceinline__ void madd(dot2c& acc, df p, float4 c) { dot2c_add(acc, p, hi2(c), lo2(c)); }
 
 // the value of a + sg b (sg = +-1) of two compensated sums, rounded once to FP64; BITS widens
 // the two words from their bit patterns (integer pipe) instead of by FP64 conversions -- the
@@ -112,27 +119,19 @@ struct DfSynthArgs {
 // cf + f K, psi of pair v at cf + (NS + v) K, chi at cf + (NS + NV + v) K)
 template <int NS, int NV, int PAR>
 __device__ __forceinline__ void df_synth_step(float2 pv, float2 hv, const float4* cf, int K, int k,
-                                              dot2 (&S)[NS > 0 ? NS : 1][2][2], dot2 (&V)[NV > 0 ? NV : 1][4][2][2]) {
+                                              dot2c (&S)[NS > 0 ? NS : 1][2], dot2c (&V)[NV > 0 ? NV : 1][4][2]) {
   const df p = df_of(pv);
 #pragma unroll
-  for (int f = 0; f < NS; ++f) {
-    const float4 c = cf[f * K + k];
-    dot2_add2(S[f][PAR][0], p, dfre(c));
-    dot2_add2(S[f][PAR][1], p, dfim(c));
-  }
+  for (int f = 0; f < NS; ++f) madd(S[f][PAR], p, cf[f * K + k]);
   if (NV > 0) {
     const df h = df_of(hv);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const float4 ps = cf[(NS + v) * K + k], ch = cf[(NS + NV + v) * K + k];
-      dot2_add2(V[v][0][PAR][0], p, dfre(ps));
-      dot2_add2(V[v][0][PAR][1], p, dfim(ps));
-      dot2_add2(V[v][1][PAR][0], p, dfre(ch));
-      dot2_add2(V[v][1][PAR][1], p, dfim(ch));
-      dot2_add2(V[v][2][PAR][0], h, dfre(ps));
-      dot2_add2(V[v][2][PAR][1], h, dfim(ps));
-      dot2_add2(V[v][3][PAR][0], h, dfre(ch));
-      dot2_add2(V[v][3][PAR][1], h, dfim(ch));
+      madd(V[v][0][PAR], p, ps);
+      madd(V[v][1][PAR], p, ch);
+      madd(V[v][2][PAR], h, ps);
+      madd(V[v][3][PAR], h, ch);
     }
   }
 }
@@ -163,17 +162,15 @@ __global__ void __launch_bounds__(DF_STH, MINB) k_df_synth(const __grid_constant
   if (jh >= nh) return;  // no barrier below
   const float2* Pm = a.P + (size_t)base * nh + jh;
   const float2* Hm = a.H + (size_t)base * nh + jh;
-  dot2 S[NS > 0 ? NS : 1][2][2];
-  dot2 V[NV > 0 ? NV : 1][4][2][2];
+  const float2 z2 = make_float2(0.f, 0.f);
+  dot2c S[NS > 0 ? NS : 1][2];     // field, parity of k
+  dot2c V[NV > 0 ? NV : 1][4][2];  // pair, (P psi, P chi, H psi, H chi), parity of k
 #pragma unroll
-  for (int f = 0; f < (NS > 0 ? NS : 1); ++f)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) S[f][q >> 1][q & 1] = dot2{0.f, 0.f};
+  for (int f = 0; f < (NS > 0 ? NS : 1); ++f) S[f][0] = S[f][1] = dot2c{z2, z2};
 #pragma unroll
   for (int v = 0; v < (NV > 0 ? NV : 1); ++v)
 #pragma unroll
-    for (int q = 0; q < 16; ++q) V[v][q >> 2][(q >> 1) & 1][q & 1] = dot2{0.f, 0.f};
-  const float2 z2 = make_float2(0.f, 0.f);
+    for (int q = 0; q < 8; ++q) V[v][q >> 1][q & 1] = dot2c{z2, z2};
   float2 pb[DF_PF], hb[DF_PF];
 #pragma unroll
   for (int u = 0; u < DF_PF; ++u) {
@@ -203,8 +200,9 @@ __global__ void __launch_bounds__(DF_STH, MINB) k_df_synth(const __grid_constant
 #pragma unroll
   for (int f = 0; f < NS; ++f) {
     double2* o = a.F + ((size_t)f * (T + 1) + m) * nlat;
-    o[lat] = make_double2(dsum<BITS>(S[f][0][0], S[f][1][0], 1.f), dsum<BITS>(S[f][0][1], S[f][1][1], 1.f));
-    o[lats] = make_double2(dsum<BITS>(S[f][0][0], S[f][1][0], -1.f), dsum<BITS>(S[f][0][1], S[f][1][1], -1.f));
+    const dot2 er = dot2c_re(S[f][0]), ei = dot2c_im(S[f][0]), od = dot2c_re(S[f][1]), oi = dot2c_im(S[f][1]);
+    o[lat] = make_double2(dsum<BITS>(er, od, 1.f), dsum<BITS>(ei, oi, 1.f));
+    o[lats] = make_double2(dsum<BITS>(er, od, -1.f), dsum<BITS>(ei, oi, -1.f));
   }
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
@@ -219,7 +217,9 @@ __global__ void __launch_bounds__(DF_STH, MINB) k_df_synth(const __grid_constant
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int c = 0; c < 2; ++c) x[q][c] = (q >= 2 ? sh : 1.0) * dsum<BITS>(V[v][q][0][c], V[v][q][1][c], so);
+        for (int c = 0; c < 2; ++c)
+          x[q][c] = (q >= 2 ? sh : 1.0) * (c ? dsum<BITS>(dot2c_im(V[v][q][0]), dot2c_im(V[v][q][1]), so)
+                                             : dsum<BITS>(dot2c_re(V[v][q][0]), dot2c_re(V[v][q][1]), so));
       const double fm = (double)m, ia = a.inv_a;
       const int j = hs ? lats : lat;
       oU[j] = make_double2(ia * (-x[2][0] - fm * x[1][1]), ia * (-x[2][1] + fm * x[1][0]));
@@ -243,11 +243,12 @@ struct DfAnalArgs {
   double inv_a;
 };
 
-__device__ __forceinline__ float4 dfc_pack(df re, df im) { return make_float4(re.hi, re.lo, im.hi, im.lo); }
+__device__ __forceinline__ float4 dfc_pack(df re, df im) { return make_float4(re.hi, im.hi, re.lo, im.lo); }
 // w (F_N + s F_S) of one latitude pair, in double-float
 __device__ __forceinline__ float4 df_wsum(df w, float4 n, float4 s, float sg) {
-  const df re = df_mul(w, df_add(dfre(n), df{sg * s.x, sg * s.y}));
-  const df im = df_mul(w, df_add(dfim(n), df{sg * s.z, sg * s.w}));
+  const df sr = dfre(s), si = dfim(s);
+  const df re = df_mul(w, df_add(dfre(n), df{sg * sr.hi, sg * sr.lo}));
+  const df im = df_mul(w, df_add(dfim(n), df{sg * si.hi, sg * si.lo}));
   return dfc_pack(re, im);
 }
 
@@ -255,28 +256,18 @@ __device__ __forceinline__ float4 df_wsum(df w, float4 n, float4 s, float sg) {
 // sum or the difference array for P and H)
 template <int NS, int NV>
 __device__ __forceinline__ void df_anal_step(float2 pv, float2 hv, const float4* sm4, int nh, int j, int sP, int sH,
-                                             dot2 (&S)[NS > 0 ? NS : 1][2], dot2 (&V)[NV > 0 ? NV : 1][4][2]) {
+                                             dot2c (&S)[NS > 0 ? NS : 1], dot2c (&V)[NV > 0 ? NV : 1][4]) {
   const df p = df_of(pv);
 #pragma unroll
-  for (int f = 0; f < NS; ++f) {
-    const float4 g = sm4[(4 * NV + 2 * f + sP) * nh + j];
-    dot2_add2(S[f][0], p, dfre(g));
-    dot2_add2(S[f][1], p, dfim(g));
-  }
+  for (int f = 0; f < NS; ++f) madd(S[f], p, sm4[(4 * NV + 2 * f + sP) * nh + j]);
   if (NV > 0) {
     const df h = df_of(hv);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const float4 AP = sm4[(4 * v + 0 + sP) * nh + j], BP = sm4[(4 * v + 2 + sP) * nh + j];
-      const float4 AH = sm4[(4 * v + 0 + sH) * nh + j], BH = sm4[(4 * v + 2 + sH) * nh + j];
-      dot2_add2(V[v][0][0], p, dfre(AP));
-      dot2_add2(V[v][0][1], p, dfim(AP));
-      dot2_add2(V[v][1][0], p, dfre(BP));
-      dot2_add2(V[v][1][1], p, dfim(BP));
-      dot2_add2(V[v][2][0], h, dfre(AH));
-      dot2_add2(V[v][2][1], h, dfim(AH));
-      dot2_add2(V[v][3][0], h, dfre(BH));
-      dot2_add2(V[v][3][1], h, dfim(BH));
+      madd(V[v][0], p, sm4[(4 * v + 0 + sP) * nh + j]);  // P.A
+      madd(V[v][1], p, sm4[(4 * v + 2 + sP) * nh + j]);  // P.B
+      madd(V[v][2], h, sm4[(4 * v + 0 + sH) * nh + j]);  // H.A
+      madd(V[v][3], h, sm4[(4 * v + 2 + sH) * nh + j]);  // H.B
     }
   }
 }
@@ -328,15 +319,15 @@ __global__ void __launch_bounds__(DF_ATH, 4) k_df_anal(const __grid_constant__ D
   const float2* Hc = a.H + col;
   // P meets (N + S) for even k, (N - S) for odd k; H the other one
   const int sP = par, sH = 1 - par;
-  dot2 S[NS > 0 ? NS : 1][2];
-  dot2 V[NV > 0 ? NV : 1][4][2];  // [0] P.A, [1] P.B, [2] H.A, [3] H.B; re, im
+  const float2 z2 = make_float2(0.f, 0.f);
+  dot2c S[NS > 0 ? NS : 1];
+  dot2c V[NV > 0 ? NV : 1][4];  // [0] P.A, [1] P.B, [2] H.A, [3] H.B
 #pragma unroll
-  for (int f = 0; f < (NS > 0 ? NS : 1); ++f) S[f][0] = S[f][1] = dot2{0.f, 0.f};
+  for (int f = 0; f < (NS > 0 ? NS : 1); ++f) S[f] = dot2c{z2, z2};
 #pragma unroll
   for (int v = 0; v < (NV > 0 ? NV : 1); ++v)
 #pragma unroll
-    for (int q = 0; q < 8; ++q) V[v][q >> 1][q & 1] = dot2{0.f, 0.f};
-  const float2 z2 = make_float2(0.f, 0.f);
+    for (int q = 0; q < 4; ++q) V[v][q] = dot2c{z2, z2};
   float2 pb[DF_PF], hb[DF_PF];
 #pragma unroll
   for (int u = 0; u < DF_PF; ++u) {
@@ -365,12 +356,14 @@ __global__ void __launch_bounds__(DF_ATH, 4) k_df_anal(const __grid_constant__ D
   }
   const size_t i = (size_t)base + k;
 #pragma unroll
-  for (int f = 0; f < NS; ++f) a.spec[(size_t)f * a.nlm + i] = make_double2(dval(S[f][0]), dval(S[f][1]));
+  for (int f = 0; f < NS; ++f) a.spec[(size_t)f * a.nlm + i] = make_double2(dval(dot2c_re(S[f])), dval(dot2c_im(S[f])));
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const double fm = (double)m, ia = a.inv_a;
-    const double PAr = dval(V[v][0][0]), PAi = dval(V[v][0][1]), PBr = dval(V[v][1][0]), PBi = dval(V[v][1][1]);
-    const double HAr = dval(V[v][2][0]), HAi = dval(V[v][2][1]), HBr = dval(V[v][3][0]), HBi = dval(V[v][3][1]);
+    const double PAr = dval(dot2c_re(V[v][0])), PAi = dval(dot2c_im(V[v][0]));
+    const double PBr = dval(dot2c_re(V[v][1])), PBi = dval(dot2c_im(V[v][1]));
+    const double HAr = dval(dot2c_re(V[v][2])), HAi = dval(dot2c_im(V[v][2]));
+    const double HBr = dval(dot2c_re(V[v][3])), HBi = dval(dot2c_im(V[v][3]));
     // div = (i m P.A - H.B) / a, curl = (i m P.B + H.A) / a
     a.dv[(size_t)v * a.nlm + i] = make_double2(ia * (-fm * PAi - HBr), ia * (fm * PAr - HBi));
     a.cu[(size_t)v * a.nlm + i] = make_double2(ia * (-fm * PBi + HAr), ia * (fm * PBr + HAi));
