@@ -306,14 +306,17 @@ def test_graph_replay_equals_eager_steps(env, scheme, sprec):
 _T127_REF = []  # the oracle's two steps, computed once for both precisions
 
 
-@pytest.mark.parametrize("rprec,tol", [("fp64", (1e-10, 1e-10, 5e-9)), ("mixed", (1e-8, 1e-8, 1e-8))])
-def test_config_T127_nonlinear_steps_match_oracle(env, rprec, tol):
+@pytest.mark.parametrize("rprec,sprec,tol", [("fp64", "fp64", (1e-10, 1e-10, 5e-9)),
+                                             ("mixed", "fp64", (1e-8, 1e-8, 1e-8)),
+                                             ("fp64", "df", (1e-10, 1e-10, 5e-9)),
+                                             ("mixed", "df", (1e-8, 1e-8, 1e-8))])
+def test_config_T127_nonlinear_steps_match_oracle(env, rprec, sprec, tol):
     """The nonlinear configuration at full size: T127 on the 192 x 384 Gauss grid, 512 poles,
     dt = 1800 s, the balanced n^-3 state (seed 2, 20 m/s rms) of the benchmark, two Strang ver1
     steps against the oracle's (FP64 Legendre); the bench times 48 such steps.  The divergence
     starts at 0, so after two steps it is made of dt N_delta and carries the bound of the
     divergence tendency at T127 (5e-9, test_nonlinear_matches_oracle): lap(KE) multiplies the
-    analysis rounding by n(n+1)/a^2."""
+    analysis rounding by n(n+1)/a^2.  Double-float transforms (SH_DF) meet the same bounds."""
     torch, rexi = env
     T, nlat, nlon, N, dt, nsteps = 127, 192, 384, 512, 1800.0, 2
     U0 = syn.balanced_state(T, 2)
@@ -326,7 +329,7 @@ def test_config_T127_nonlinear_steps_match_oracle(env, rprec, tol):
             ref = oswe.strang_ver1(ref, g, dt, OM, PB, z, w)
         _T127_REF.append(ref)
     ref = _T127_REF[0]
-    plan = rexi.SwePlan(T, nlat, nlon, dt, OM, A, PB, N, p0, Xc, rexi_precision=rprec)
+    plan = rexi.SwePlan(T, nlat, nlon, dt, OM, A, PB, N, p0, Xc, rexi_precision=rprec, sh_precision=sprec)
     u = torch.from_numpy(U0).cuda()
     plan.step(u, nsteps)
     torch.cuda.synchronize()
