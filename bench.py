@@ -88,8 +88,10 @@ def parse():
     ap.add_argument("--serving", type=int, default=0,
                     help="run the request-stream workload with this many requests instead")
     ap.add_argument("--sh-only", nargs="?", const="fp64,tf32,bf16,tf32x3,df", default=None,
-                    help="run only the T511 SH-transform figures, for these Legendre precisions "
+                    help="run only the SH-transform figures, for these Legendre precisions "
                          "(comma list; default all)")
+    ap.add_argument("--sh-T", type=int, default=511,
+                    help="truncation of --sh-only (Gauss grid 3(T+1)/2 x 3(T+1))")
     return ap.parse_args()
 
 
@@ -784,8 +786,11 @@ def main():
         import torch
         from paper_1805_06557_gb300 import rexi
         fp64_tf, fp32_tf = rexi.alu_peaks()
-        out = sh_transforms(torch, rexi, fp64_tf, fp32_tf, precs=tuple(args.sh_only.split(",")))
-        print(json.dumps({"metric": "SH transforms at T511 (Legendre and FFT stages)", "sh_transforms": out}),
+        Ts = args.sh_T
+        nlat = 3 * (Ts + 1) // 2
+        out = sh_transforms(torch, rexi, fp64_tf, fp32_tf, T=Ts, nlat=nlat, nlon=2 * nlat,
+                            precs=tuple(args.sh_only.split(",")))
+        print(json.dumps({"metric": "SH transforms at T%d (Legendre and FFT stages)" % Ts, "sh_transforms": out}),
               flush=True)
         return
 
