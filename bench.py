@@ -415,14 +415,15 @@ def sh_transforms(torch, rexi, fp64_peak, fp32_peak, T=511, nlat=768, nlon=1536,
     vector pair synthesised, 2 vector pairs + 1 scalar field analysed), at T511 on the
     768 x 1536 Gauss grid in every Legendre precision.
     Per-stage device times from the plan's event profile; the roofline of the Legendre
-    contraction is HBM-bound on its table (algorithmic bytes: the nlat/2 x nlm table read
-    once per transform -- P for scalar transforms, P and H for vector transforms -- in the
-    stored element type, plus the spectral and Fourier operands), of the FFT on its grid and
-    Fourier arrays."""
+    contraction is HBM-bound on its table (algorithmic bytes: the table entries the polar-
+    truncated sums need, of the nlat/2 x nlm table, read once per transform -- P for scalar
+    transforms, P and H for vector transforms -- in the stored element type, plus the
+    spectral and Fourier operands), of the FFT on its grid and Fourier arrays.  The FP64 and
+    double-float contractions are ALU-bound: 4 flops per needed entry and real array."""
     import numpy as np
     from paper_1805_06557_gb300 import synthetic as syn
     hbm = _hbm_peak()
-    nh, nlm = nlat // 2, (T + 1) * (T + 2) // 2
+    nlm = (T + 1) * (T + 2) // 2
     rng = np.random.default_rng(4)
     n = np.concatenate([np.arange(m, T + 1) for m in range(T + 1)]).astype(float)
     amp = np.maximum(n, 1.0) ** -1.5
@@ -441,7 +442,8 @@ def sh_transforms(torch, rexi, fp64_peak, fp32_peak, T=511, nlat=768, nlon=1536,
     for prec in precs:
         p = rexi.ShPlan(T, nlat, nlon, syn.RADIUS, prec, max_fields=3)
         eb = {"fp64": 8, "tf32": 4, "bf16": 2, "tf32x3": 8, "df": 8}[prec]   # split TF32, df: hi and lo words
-        res = {}
+        use = p.table_use()
+        res = {"table_entries": use}
         for kind in ("synthesis", "analysis", "synthesis_uv", "analysis_divcurl", "synthesis_mixed",
                      "analysis_mixed"):
             def call():
@@ -474,17 +476,18 @@ def sh_transforms(torch, rexi, fp64_peak, fp32_peak, T=511, nlat=768, nlon=1536,
             vec = kind in ("synthesis_uv", "analysis_divcurl")
             mixed = kind.endswith("_mixed")
             ntab = 2 if (vec or mixed) else 1   # P, or P and H
+            need = use["needed_synth" if kind.startswith("synthesis") else "needed_anal"]
             # spectral arrays = Fourier arrays = grids: scalar fields + 2 per vector pair
             narr = 2 if vec else (4 if kind == "synthesis_mixed" else 5 if mixed else nf)
             leg_ms = sum(prof[k][0] for k in ("legendre_fp64", "legendre_df", "tc_gemm", "tc_epilogue")) / reps
             gemm_ms = prof[{"fp64": "legendre_fp64", "df": "legendre_df"}.get(prec, "tc_gemm")][0] / reps
-            tab_bytes = ntab * nh * nlm * eb
+            tab_bytes = ntab * need * eb
             leg_bytes = tab_bytes + narr * (nlm + (T + 1) * nlat) * 16
             fft_ms = prof["fft"][0] / reps
             fft_bytes = narr * (nlat * nlon * 8 + nlat * (T + 1) * 16)
             # FMA = 2; complex coefficient x real table; vector arrays meet P and H, scalar ones P
             nvec_arr = 2 if kind == "synthesis_mixed" else 4 if kind == "analysis_mixed" else (narr if vec else 0)
-            leg_flops = 4.0 * nh * nlm * (2 * nvec_arr + (narr - nvec_arr))
+            leg_flops = 4.0 * need * (2 * nvec_arr + (narr - nvec_arr))
             if prec == "fp64":   # FP64 CUDA-core contraction: bound by the FP64 pipe on this GPU
                 leg_roof = {"bound": "alu", "pipe": "fp64", "kernel": "k_leg_*", "algorithmic_flops": leg_flops,
                             "achieved": leg_flops / (gemm_ms * 1e9), "unit": "TFLOP/s", "peak": fp64_peak,

@@ -56,7 +56,23 @@ typedef struct sh_plan_desc {
                     /* accumulator after n non-blocking polls (the copy and MMA roles still  */
                     /* drain everything they issued); that transform's results are invalid  */
                     /* and sh_plan_check then returns REXI_ETIMEOUT                          */
+  double polar_threshold;  /* polar truncation of the Legendre sums (below): 0 = the default      */
+                    /* SH_POLAR_THRESHOLD_DEFAULT, > 0 (and < 1e-3) = this threshold, < 0 = off */
 } sh_plan_desc;
+
+/* Polar truncation.  Pt_n^m and Ht_n^m carry the factor (1 - mu^2)^{m/2}: near the poles, and
+ * for m large against n sin(theta), they are smaller than any fixed threshold, so that the
+ * leading terms of the sums over degrees (synthesis, per latitude) and over latitudes
+ * (analysis, per degree) contribute nothing at FP64 precision.  SHTns, the library the paper
+ * computes its transforms with (Sec. 3.2), skips them ("polar optimisation"); so does this
+ * plan: per zonal order m it finds, for each group of 32 latitudes, the first degree at which
+ * |Pt| or |Ht| exceeds the threshold at one of them, and for each group of 32 degrees the
+ * first such latitude, and its kernels start there.  Every skipped table entry is below the
+ * threshold in magnitude, so a skipped sum changes a result by at most the threshold times
+ * the sum of the magnitudes of the terms it meets (coefficients, or weighted Fourier
+ * coefficients).  The default, 1e-19, is about a thousandth of the FP64 rounding unit of the
+ * tables' O(1) entries: results equal the untruncated ones to rounding. */
+#define SH_POLAR_THRESHOLD_DEFAULT 1e-19
 
 /* Builds the Gauss grid (Newton iteration on P_nlat), the orthonormal associated Legendre
  * table Pt_n^m(mu_j) and Ht_n^m = (1 - mu^2) dPt_n^m/dmu for the northern half (the
@@ -105,6 +121,19 @@ int sh_synthesis_mixed(sh_plan* plan, const void* spec, void* grid, int nfields,
  * sh_synthesis_mixed. */
 int sh_analysis_mixed(sh_plan* plan, const void* A, const void* B, void* div, void* curl, int nvec,
                       const void* grid, void* spec, int nfields);
+
+/* Table entries per table (Pt, and Ht for vector transforms), to count the Legendre work:
+ * total = nlm x nlat/2 (degree, northern latitude) entries; needed_synth / needed_anal = the
+ * entries from each latitude's (each degree's) first one above the polar threshold on, the
+ * work of the truncated method; streamed_synth / streamed_anal = the entries this plan's
+ * kernels stream (whole warps, or whole tensor-core tiles and chunks, from their group's
+ * start; padding not counted); threshold = the threshold in use (0: truncation off, every
+ * count equal to total).  Errors: REXI_EINVAL. */
+typedef struct sh_table_use {
+  long long total, needed_synth, needed_anal, streamed_synth, streamed_anal;
+  double threshold;
+} sh_table_use;
+int sh_plan_get_table_use(const sh_plan* plan, sh_table_use* use);
 
 /* Synchronises the plan stream; returns REXI_ETIMEOUT if a tensor-core kernel's bounded
  * wait on its copy / MMA barriers gave up since the plan was created (its results are then

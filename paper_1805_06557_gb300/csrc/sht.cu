@@ -73,21 +73,70 @@ __global__ void k_legendre_table(const double* __restrict__ mu, double* __restri
   }
 }
 
+// ---- polar bounds (see PolarBounds) ----------------------------------------------------
+// One warp per (m, 32-latitude group): each lane scans the degrees of its latitude for the
+// first entry of P or H above thr in magnitude; the warp keeps the smallest start and the
+// number of entries from each latitude's own start on (the entries the method needs).
+__global__ void k_polar_synth(const double* __restrict__ P, const double* __restrict__ H, int T, int nh, double thr,
+                              int ngl, int* __restrict__ ks, int* __restrict__ need) {
+  const int g = blockIdx.x, m = blockIdx.y, jh = 32 * g + threadIdx.x;
+  const int K = T + 1 - m;
+  int k = K;
+  if (jh < nh) {
+    const double* Pm = P + (size_t)moff(T, m) * nh + jh;
+    const double* Hm = H + (size_t)moff(T, m) * nh + jh;
+    for (k = 0; k < K; ++k)
+      if (fabs(Pm[(size_t)k * nh]) > thr || fabs(Hm[(size_t)k * nh]) > thr) break;
+  }
+  const unsigned kmin = __reduce_min_sync(0xffffffffu, (unsigned)k);
+  const unsigned n = __reduce_add_sync(0xffffffffu, jh < nh ? (unsigned)(K - k) : 0u);
+  if (threadIdx.x == 0) {
+    ks[m * ngl + g] = (int)kmin;
+    need[m * ngl + g] = (int)n;
+  }
+}
+
+// One warp per (m, 32-degree group): each lane scans the latitudes of its degree.
+__global__ void k_polar_anal(const double* __restrict__ P, const double* __restrict__ H, int T, int nh, double thr,
+                             int ngd, int* __restrict__ ja, int* __restrict__ need) {
+  const int g = blockIdx.x, m = blockIdx.y, k = 32 * g + threadIdx.x;
+  const int K = T + 1 - m;
+  int j = nh;
+  if (k < K) {
+    const double* Pk = P + (size_t)(moff(T, m) + k) * nh;
+    const double* Hk = H + (size_t)(moff(T, m) + k) * nh;
+    for (j = 0; j < nh; ++j)
+      if (fabs(Pk[j]) > thr || fabs(Hk[j]) > thr) break;
+  }
+  const unsigned jmin = __reduce_min_sync(0xffffffffu, (unsigned)j);
+  const unsigned n = __reduce_add_sync(0xffffffffu, k < K ? (unsigned)(nh - j) : 0u);
+  if (threadIdx.x == 0) {
+    ja[m * ngd + g] = (int)jmin;
+    need[m * ngd + g] = (int)n;
+  }
+}
+
 // ---- Legendre synthesis ------------------------------------------------------------
+// One thread per (m, field, northern latitude): even- and odd-degree partial sums, combined
+// for the latitude and its mirror.  Each warp starts at the first degree its 32 latitudes
+// need (ks, rounded down to even so that the loop's parity pairing holds).  Latitude tiles
+// run equator first (the last tile has the most work left after the polar truncation, and
+// the first blocks launched finish last).
 constexpr int LTH = 128;
 
 __global__ void __launch_bounds__(LTH) k_leg_synth(const double* __restrict__ P,
                                                    const double2* __restrict__ spec,
-                                                   double2* __restrict__ F, int T, int nlat, int nlm) {
+                                                   double2* __restrict__ F, int T, int nlat, int nlm,
+                                                   const int* __restrict__ ks, int ngl) {
   const int m = blockIdx.x, f = blockIdx.y;
   const int nh = nlat / 2;
-  const int jh = blockIdx.z * LTH + threadIdx.x;
+  const int jh = (gridDim.z - 1 - blockIdx.z) * LTH + threadIdx.x;
   if (jh >= nh) return;
   const int K = T + 1 - m, base = moff(T, m);
   const double2* c = spec + (size_t)f * nlm + base;
   const double* Pm = P + (size_t)base * nh + jh;
   double2 e = make_double2(0, 0), o = make_double2(0, 0);
-  int k = 0;
+  int k = __ldg(ks + m * ngl + (jh >> 5)) & ~1;
   for (; k + 1 < K; k += 2) {
     const double pe = Pm[(size_t)k * nh], po = Pm[(size_t)(k + 1) * nh];
     const double2 ce = c[k], co = c[k + 1];
@@ -113,10 +162,11 @@ __global__ void __launch_bounds__(LTH) k_leg_synth_uv(const double* __restrict__
                                                       const double2* __restrict__ psi,
                                                       const double2* __restrict__ chi,
                                                       double2* __restrict__ FU, double2* __restrict__ FV,
-                                                      int T, int nlat, int nlm, double inv_a) {
+                                                      int T, int nlat, int nlm, double inv_a,
+                                                      const int* __restrict__ ks, int ngl) {
   const int m = blockIdx.x, f = blockIdx.y;
   const int nh = nlat / 2;
-  const int jh = blockIdx.z * LTH + threadIdx.x;
+  const int jh = (gridDim.z - 1 - blockIdx.z) * LTH + threadIdx.x;  // equator first
   if (jh >= nh) return;
   const int K = T + 1 - m, base = moff(T, m);
   const double2* cp = psi + (size_t)f * nlm + base;
@@ -125,7 +175,7 @@ __global__ void __launch_bounds__(LTH) k_leg_synth_uv(const double* __restrict__
   const double* Hm = H + (size_t)base * nh + jh;
   // [0] even k, [1] odd k
   double2 pps[2] = {}, pch[2] = {}, hps[2] = {}, hch[2] = {};
-  for (int k = 0; k < K; ++k) {
+  for (int k = __ldg(ks + m * ngl + (jh >> 5)); k < K; ++k) {
     const int par = k & 1;
     const double p = Pm[(size_t)k * nh], h = Hm[(size_t)k * nh];
     const double2 a = cp[k], b = cc[k];
@@ -163,7 +213,8 @@ constexpr int ATH = 256;
 __global__ void __launch_bounds__(ATH) k_leg_anal(const double* __restrict__ P,
                                                   const double* __restrict__ w,
                                                   const double2* __restrict__ F,
-                                                  double2* __restrict__ spec, int T, int nlat, int nlm) {
+                                                  double2* __restrict__ spec, int T, int nlat, int nlm,
+                                                  const int* __restrict__ ja, int ngd) {
   extern __shared__ double2 sm2[];
   const int m = blockIdx.x, f = blockIdx.y;
   const int nh = nlat / 2;
@@ -178,15 +229,17 @@ __global__ void __launch_bounds__(ATH) k_leg_anal(const double* __restrict__ P,
   }
   __syncthreads();
   // one thread per degree: it streams its own table row (32-byte pieces when nh % 4 == 0)
-  // against the shared hemispheric sums; no cross-lane reduction
+  // against the shared hemispheric sums; no cross-lane reduction.  Each warp (32 consecutive
+  // degrees) starts at the first latitude its degrees need (ja).
   const int K = T + 1 - m, base = moff(T, m);
   for (int k = threadIdx.x; k < K; k += ATH) {
     const double* Pk = P + (size_t)(base + k) * nh;
     const double2* src = (k & 1) ? So : Se;
+    const int jb = __ldg(ja + m * ngd + (k >> 5));
     double2 acc = make_double2(0, 0);
     if ((nh & 3) == 0) {
       const double2* P2 = reinterpret_cast<const double2*>(Pk);
-      for (int j4 = 0; j4 < nh / 4; ++j4) {
+      for (int j4 = jb >> 2; j4 < nh / 4; ++j4) {
         const double2 pa = __ldg(P2 + 2 * j4), pb = __ldg(P2 + 2 * j4 + 1);  // one 32-byte sector
         const double2 s0 = src[4 * j4], s1 = src[4 * j4 + 1], s2 = src[4 * j4 + 2], s3 = src[4 * j4 + 3];
         acc.x = fma(pa.x, s0.x, acc.x);
@@ -199,7 +252,7 @@ __global__ void __launch_bounds__(ATH) k_leg_anal(const double* __restrict__ P,
         acc.y = fma(pb.y, s3.y, acc.y);
       }
     } else {
-      for (int j = 0; j < nh; ++j) {
+      for (int j = jb; j < nh; ++j) {
         const double p = __ldg(Pk + j);
         acc.x = fma(p, src[j].x, acc.x);
         acc.y = fma(p, src[j].y, acc.y);
@@ -216,7 +269,8 @@ __global__ void __launch_bounds__(ATH) k_leg_anal_divcurl(const double* __restri
                                                           const double2* __restrict__ FB,
                                                           double2* __restrict__ dv,
                                                           double2* __restrict__ cu, int T, int nlat,
-                                                          int nlm, double inv_a) {
+                                                          int nlm, double inv_a, const int* __restrict__ ja,
+                                                          int ngd) {
   extern __shared__ double2 sm2[];
   const int m = blockIdx.x, f = blockIdx.y;
   const int nh = nlat / 2;
@@ -241,6 +295,7 @@ __global__ void __launch_bounds__(ATH) k_leg_anal_divcurl(const double* __restri
     const double* Pk = P + (size_t)(base + k) * nh;
     const double* Hk = H + (size_t)(base + k) * nh;
     const bool odd = k & 1;
+    const int jb = __ldg(ja + m * ngd + (k >> 5));
     // P terms pair with (north + s south), H terms with (north - s south), s = (-1)^k
     const double2* AP = odd ? Am : Ap;
     const double2* BP = odd ? Bm : Bp;
@@ -261,7 +316,7 @@ __global__ void __launch_bounds__(ATH) k_leg_anal_divcurl(const double* __restri
     if ((nh & 3) == 0) {
       const double2* P2 = reinterpret_cast<const double2*>(Pk);
       const double2* H2 = reinterpret_cast<const double2*>(Hk);
-      for (int j4 = 0; j4 < nh / 4; ++j4) {
+      for (int j4 = jb >> 2; j4 < nh / 4; ++j4) {
         const double2 pa = __ldg(P2 + 2 * j4), pb = __ldg(P2 + 2 * j4 + 1);
         const double2 ha = __ldg(H2 + 2 * j4), hb = __ldg(H2 + 2 * j4 + 1);
         step(pa.x, ha.x, 4 * j4);
@@ -270,7 +325,7 @@ __global__ void __launch_bounds__(ATH) k_leg_anal_divcurl(const double* __restri
         step(pb.y, hb.y, 4 * j4 + 3);
       }
     } else {
-      for (int j = 0; j < nh; ++j) step(__ldg(Pk + j), __ldg(Hk + j), j);
+      for (int j = jb; j < nh; ++j) step(__ldg(Pk + j), __ldg(Hk + j), j);
     }
     const double2 iPA = imul(m, sPA), iPB = imul(m, sPB);
     dv[(size_t)f * nlm + base + k] = make_double2(inv_a * (iPA.x - sHB.x), inv_a * (iPA.y - sHB.y));
@@ -702,6 +757,13 @@ struct sh_plan {
   TcLegendre* tc = nullptr;  // tensor-core Legendre state (SH_TF32 / SH_BF16 / SH_TF32X3)
   DfLegendre* dfl = nullptr;  // double-float Legendre state (SH_DF)
   StageProf prof;            // per-stage event timing (sh_plan_set_profiling)
+  // polar truncation: threshold (0 = off), start indices per (m, group) on host and device
+  double polar_thr = 0.0;
+  std::vector<int> ks, ja;
+  int* d_ks = nullptr;
+  int* d_ja = nullptr;
+  PolarBounds pb;
+  long long need_syn = 0, need_ana = 0;  // entries the method needs per table (sh_table_use)
 };
 
 // two padded work buffers
@@ -719,6 +781,8 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
   if (d.nlon <= 2 * d.T) return fail(REXI_EINVAL, "sh_plan_create: nlon must exceed 2T");
   if (!(d.radius > 0) || d.max_fields < 1) return fail(REXI_EINVAL, "sh_plan_create: radius > 0, max_fields >= 1");
   if (d.epilogue_wait_polls < 0) return fail(REXI_EINVAL, "sh_plan_create: epilogue_wait_polls < 0");
+  if (!(d.polar_threshold == d.polar_threshold) || d.polar_threshold >= 1e-3)
+    return fail(REXI_EINVAL, "sh_plan_create: polar_threshold must be below 1e-3 (or <= 0)");
   if (d.precision != SH_FP64 && d.precision != SH_TF32 && d.precision != SH_BF16 && d.precision != SH_TF32X3 &&
       d.precision != SH_DF)
     return fail(REXI_EINVAL, "sh_plan_create: unknown precision %d", d.precision);
@@ -770,6 +834,51 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
     return bail(cuda_fail(e, "sh_plan_create: cudaMemcpy"));
   k_legendre_table<<<dim3((p->nh + 127) / 128, d.T + 1), 128, 0, p->stream>>>(p->d_mu, p->d_P, p->d_H, d.T, p->nh);
   if ((e = cudaGetLastError())) return bail(cuda_fail(e, "k_legendre_table"));
+  // polar bounds
+  p->polar_thr = d.polar_threshold == 0.0 ? SH_POLAR_THRESHOLD_DEFAULT : d.polar_threshold > 0 ? d.polar_threshold : 0.0;
+  {
+    const int ngl = (p->nh + 31) / 32, ngd = (d.T + 1 + 31) / 32;
+    const size_t nks = (size_t)(d.T + 1) * ngl, nja = (size_t)(d.T + 1) * ngd;
+    p->ks.assign(nks, 0);
+    p->ja.assign(nja, 0);
+    std::vector<int> nds(nks, 0), nda(nja, 0);
+    int *d_nds = nullptr, *d_nda = nullptr;
+    if ((e = cudaMalloc(&p->d_ks, sizeof(int) * nks)) || (e = cudaMalloc(&p->d_ja, sizeof(int) * nja))) {
+      cudaGetLastError();
+      return bail(fail(REXI_ENOMEM, "sh_plan_create: cudaMalloc failed: %s", cudaGetErrorString(e)));
+    }
+    if (p->polar_thr > 0) {
+      if ((e = cudaMalloc(&d_nds, sizeof(int) * nks)) || (e = cudaMalloc(&d_nda, sizeof(int) * nja))) {
+        cudaFree(d_nds);
+        cudaGetLastError();
+        return bail(fail(REXI_ENOMEM, "sh_plan_create: cudaMalloc failed: %s", cudaGetErrorString(e)));
+      }
+      k_polar_synth<<<dim3(ngl, d.T + 1), 32, 0, p->stream>>>(p->d_P, p->d_H, d.T, p->nh, p->polar_thr, ngl, p->d_ks,
+                                                               d_nds);
+      k_polar_anal<<<dim3(ngd, d.T + 1), 32, 0, p->stream>>>(p->d_P, p->d_H, d.T, p->nh, p->polar_thr, ngd, p->d_ja,
+                                                              d_nda);
+      if (!(e = cudaGetLastError()) && !(e = cudaStreamSynchronize(p->stream)) &&
+          !(e = cudaMemcpy(p->ks.data(), p->d_ks, sizeof(int) * nks, cudaMemcpyDeviceToHost)) &&
+          !(e = cudaMemcpy(p->ja.data(), p->d_ja, sizeof(int) * nja, cudaMemcpyDeviceToHost)) &&
+          !(e = cudaMemcpy(nds.data(), d_nds, sizeof(int) * nks, cudaMemcpyDeviceToHost)))
+        e = cudaMemcpy(nda.data(), d_nda, sizeof(int) * nja, cudaMemcpyDeviceToHost);
+      cudaFree(d_nds);
+      cudaFree(d_nda);
+      if (e) return bail(cuda_fail(e, "sh_plan_create: polar bounds"));
+      for (int v : nds) p->need_syn += v;
+      for (int v : nda) p->need_ana += v;
+    } else {
+      if ((e = cudaMemset(p->d_ks, 0, sizeof(int) * nks)) || (e = cudaMemset(p->d_ja, 0, sizeof(int) * nja)))
+        return bail(cuda_fail(e, "sh_plan_create: polar bounds"));
+      p->need_syn = p->need_ana = (long long)p->nlm * p->nh;
+    }
+    p->pb.ngl = ngl;
+    p->pb.ngd = ngd;
+    p->pb.d_ks = p->d_ks;
+    p->pb.d_ja = p->d_ja;
+    p->pb.ks = p->ks.data();
+    p->pb.ja = p->ja.data();
+  }
   if (p->fft32) {
     e = cudaFuncSetAttribute(k_fft_synth32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p));
     if (!e) e = cudaFuncSetAttribute(k_fft_anal32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p));
@@ -782,12 +891,13 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
   }
   if (e) return bail(cuda_fail(e, "cudaFuncSetAttribute(fft)"));
   if (d.precision == SH_DF) {
-    int rc = df_legendre_create(&p->dfl, p->d_P, p->d_H, p->d_w, p->d_wq, d.T, d.nlat, d.max_fields, p->stream);
+    int rc = df_legendre_create(&p->dfl, p->d_P, p->d_H, p->d_w, p->d_wq, d.T, d.nlat, d.max_fields, p->pb,
+                                p->stream);
     if (rc) return bail(rc);
     df_legendre_set_prof(p->dfl, &p->prof);
   } else if (d.precision != SH_FP64) {
     int rc = tc_legendre_create(&p->tc, p->d_P, p->d_H, p->d_w, p->d_wq, d.T, d.nlat, d.max_fields,
-                                d.precision, p->stream);
+                                d.precision, p->pb, p->stream);
     if (rc) return bail(rc);
     tc_legendre_set_prof(p->tc, &p->prof);
     tc_legendre_set_epilogue_polls(p->tc, d.epilogue_wait_polls);
@@ -811,6 +921,8 @@ extern "C" int sh_plan_destroy(sh_plan* p) {
   cudaFree(p->d_F);
   tc_legendre_destroy(p->tc);
   df_legendre_destroy(p->dfl);
+  cudaFree(p->d_ks);
+  cudaFree(p->d_ja);
   p->prof.release();
   delete p;
   return REXI_OK;
@@ -877,8 +989,8 @@ static int leg_synth(sh_plan* p, const double2* spec, double2* F, int nf) {
   if (p->tc) return tc_leg_synth(p->tc, spec, F, nf, p->stream);
   if (p->dfl) return df_leg_synth(p->dfl, spec, F, nf, nullptr, nullptr, nullptr, nullptr, 0, 0.0, p->stream);
   const int ph = p->prof.begin(0);
-  k_leg_synth<<<dim3(p->d.T + 1, nf, (p->nh + LTH - 1) / LTH), LTH, 0, p->stream>>>(p->d_P, spec, F, p->d.T,
-                                                                                  p->d.nlat, p->nlm);
+  k_leg_synth<<<dim3(p->d.T + 1, nf, (p->nh + LTH - 1) / LTH), LTH, 0, p->stream>>>(
+      p->d_P, spec, F, p->d.T, p->d.nlat, p->nlm, p->d_ks, p->pb.ngl);
   p->prof.end(ph);
   return REXI_OK;
 }
@@ -887,7 +999,7 @@ static int leg_synth_uv(sh_plan* p, const double2* psi, const double2* chi, doub
   if (p->dfl) return df_leg_synth(p->dfl, nullptr, nullptr, 0, psi, chi, FU, FV, nf, 1.0 / p->d.radius, p->stream);
   const int ph = p->prof.begin(0);
   k_leg_synth_uv<<<dim3(p->d.T + 1, nf, (p->nh + LTH - 1) / LTH), LTH, 0, p->stream>>>(
-      p->d_P, p->d_H, psi, chi, FU, FV, p->d.T, p->d.nlat, p->nlm, 1.0 / p->d.radius);
+      p->d_P, p->d_H, psi, chi, FU, FV, p->d.T, p->d.nlat, p->nlm, 1.0 / p->d.radius, p->d_ks, p->pb.ngl);
   p->prof.end(ph);
   return REXI_OK;
 }
@@ -895,8 +1007,8 @@ static int leg_anal(sh_plan* p, const double2* F, double2* spec, int nf) {
   if (p->tc) return tc_leg_anal(p->tc, F, spec, nf, p->stream);
   if (p->dfl) return df_leg_anal(p->dfl, nullptr, nullptr, nullptr, nullptr, 0, F, spec, nf, 0.0, p->stream);
   const int ph = p->prof.begin(0);
-  k_leg_anal<<<dim3(p->d.T + 1, nf), ATH, sizeof(double2) * 2 * p->nh, p->stream>>>(p->d_P, p->d_w, F, spec,
-                                                                                    p->d.T, p->d.nlat, p->nlm);
+  k_leg_anal<<<dim3(p->d.T + 1, nf), ATH, sizeof(double2) * 2 * p->nh, p->stream>>>(
+      p->d_P, p->d_w, F, spec, p->d.T, p->d.nlat, p->nlm, p->d_ja, p->pb.ngd);
   p->prof.end(ph);
   return REXI_OK;
 }
@@ -905,7 +1017,7 @@ static int leg_anal_divcurl(sh_plan* p, const double2* FA, const double2* FB, do
   if (p->dfl) return df_leg_anal(p->dfl, FA, FB, dv, cu, nf, nullptr, nullptr, 0, 1.0 / p->d.radius, p->stream);
   const int ph = p->prof.begin(0);
   k_leg_anal_divcurl<<<dim3(p->d.T + 1, nf), ATH, sizeof(double2) * 4 * p->nh, p->stream>>>(
-      p->d_P, p->d_H, p->d_wq, FA, FB, dv, cu, p->d.T, p->d.nlat, p->nlm, 1.0 / p->d.radius);
+      p->d_P, p->d_H, p->d_wq, FA, FB, dv, cu, p->d.T, p->d.nlat, p->nlm, 1.0 / p->d.radius, p->d_ja, p->pb.ngd);
   p->prof.end(ph);
   return REXI_OK;
 }
@@ -1012,6 +1124,34 @@ extern "C" int sh_analysis_mixed(sh_plan* p, const void* A, const void* B, void*
     if ((rc = leg_anal(p, FG, (double2*)spec, nf))) return rc;
   }
   return launched("sh_analysis_mixed");
+}
+
+extern "C" int sh_plan_get_table_use(const sh_plan* p, sh_table_use* u) {
+  if (!p || !u) return fail(REXI_EINVAL, "sh_plan_get_table_use: null argument");
+  const int T = p->d.T, nh = p->nh, ngl = p->pb.ngl, ngd = p->pb.ngd;
+  u->total = (long long)p->nlm * nh;
+  u->needed_synth = p->need_syn;
+  u->needed_anal = p->need_ana;
+  u->threshold = p->polar_thr;
+  if (p->tc) {
+    tc_legendre_streamed(p->tc, &u->streamed_synth, &u->streamed_anal);
+  } else if (p->dfl) {
+    df_legendre_streamed(p->dfl, &u->streamed_synth, &u->streamed_anal);
+  } else {  // the FP64 kernels: whole warps from their group's start (rounded as they round it)
+    long long s = 0, a = 0;
+    for (int m = 0; m <= T; ++m) {
+      const int K = T + 1 - m;
+      for (int g = 0; g < ngl; ++g)
+        s += (long long)std::min(32, nh - 32 * g) * (K - (p->ks[m * ngl + g] & ~1));
+      for (int g = 0; g < ngd && 32 * g < K; ++g) {
+        const int jb = p->ja[m * ngd + g];
+        a += (long long)std::min(32, K - 32 * g) * (nh - ((nh & 3) == 0 ? jb & ~3 : jb));
+      }
+    }
+    u->streamed_synth = s;
+    u->streamed_anal = a;
+  }
+  return REXI_OK;
 }
 
 extern "C" int sh_plan_check(sh_plan* p) {

@@ -110,24 +110,26 @@ struct DfSynthArgs {
   double2* F;         // [NS][T+1][nlat]
   double2* FU;        // [NV][T+1][nlat]
   double2* FV;
-  int T, nlat, nh, nlm;
+  const int* ks;      // polar bounds: first degree index per (m, 32-latitude group) [T+1][ngl]
+  int T, nlat, nh, nlm, ngl;
   double inv_a;
 };
 
 // k-step of parity PAR: the table entries p, h of degree k against every field's coefficient
-// (split coefficients of the block's zonal order staged in shared memory: scalar field f at
-// cf + f K, psi of pair v at cf + (NS + v) K, chi at cf + (NS + NV + v) K)
+// (split coefficients of the block's zonal order staged in shared memory with the field
+// stride L = T + 1: scalar field f at cf + f L, psi of pair v at cf + (NS + v) L, chi at
+// cf + (NS + NV + v) L)
 template <int NS, int NV, int PAR>
-__device__ __forceinline__ void df_synth_step(float2 pv, float2 hv, const float4* cf, int K, int k,
+__device__ __forceinline__ void df_synth_step(float2 pv, float2 hv, const float4* cf, int L, int k,
                                               dot2c (&S)[NS > 0 ? NS : 1][2], dot2c (&V)[NV > 0 ? NV : 1][4][2]) {
   const df p = df_of(pv);
 #pragma unroll
-  for (int f = 0; f < NS; ++f) madd(S[f][PAR], p, cf[f * K + k]);
+  for (int f = 0; f < NS; ++f) madd(S[f][PAR], p, cf[f * L + k]);
   if (NV > 0) {
     const df h = df_of(hv);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const float4 ps = cf[(NS + v) * K + k], ch = cf[(NS + NV + v) * K + k];
+      const float4 ps = cf[(NS + v) * L + k], ch = cf[(NS + NV + v) * L + k];
       madd(V[v][0][PAR], p, ps);
       madd(V[v][1][PAR], p, ch);
       madd(V[v][2][PAR], h, ps);
@@ -138,11 +140,13 @@ __device__ __forceinline__ void df_synth_step(float2 pv, float2 hv, const float4
 
 constexpr int DF_PF = 4;  // table entries loaded this many degrees (synthesis) or latitudes (analysis) ahead
 
-// one thread per northern latitude jh of zonal order m: even and odd partial sums over the
+// One thread per northern latitude jh of zonal order m: even and odd partial sums over the
 // degrees, combined for the latitude and its mirror (P_n(-mu) = (-1)^(n-m) P_n(mu),
 // H_n(-mu) = -(-1)^(n-m) H_n(mu)); vector pairs give U = (-H psi + i m P chi)/a and
-// V = (i m P psi + H chi)/a.  The block stages its zonal order's split coefficients in shared
-// memory; each thread keeps the table entries of the next DF_PF degrees in flight.
+// V = (i m P psi + H chi)/a.  The block (four warps over 128 consecutive latitudes) stages its
+// zonal order's split coefficients in shared memory; each thread keeps the table entries of the
+// next DF_PF degrees (2 DF_PF without vector pairs or under MINB = 1) in flight.  Each warp starts
+// at the first degree its 32 latitudes need (polar bounds, rounded down to even).
 // MINB: blocks per SM the registers must allow (5 for launches of several waves, where
 // occupancy hides the table loads; 1 for small ones, where each block's own overlap counts)
 template <int NS, int NV, int MINB>
@@ -151,17 +155,23 @@ __global__ void __launch_bounds__(DF_STH, MINB) k_df_synth(const __grid_constant
   extern __shared__ float4 cf[];
   const int m = blockIdx.x;
   const int T = a.T, K = T + 1 - m, base = moff(T, m), nlat = a.nlat, nh = a.nh;
+  // latitude tiles run equator first: the last tile has the most work left after the polar
+  // truncation, and the first blocks launched finish last
+  const int jh = (gridDim.y - 1 - blockIdx.y) * DF_STH + threadIdx.x;
+  // from the warp's first degree kb (even: the parity of k - kb is that of k) on; requested
+  // before the staging, whose time hides its latency
+  const int kb = jh < nh ? __ldg(a.ks + m * a.ngl + (jh >> 5)) & ~1 : 0;  // warp-uniform
   for (int i = threadIdx.x; i < (NS + 2 * NV) * K; i += DF_STH) {
     const int q = i / K, k = i - q * K;
     const float4* src = q < NS ? a.cs + (size_t)q * a.nlm : q < NS + NV ? a.cp + (size_t)(q - NS) * a.nlm
                                                                          : a.cc + (size_t)(q - NS - NV) * a.nlm;
-    cf[i] = __ldg(src + base + k);
+    cf[q * (T + 1) + k] = __ldg(src + base + k);
   }
   __syncthreads();
-  const int jh = blockIdx.y * DF_STH + threadIdx.x;
   if (jh >= nh) return;  // no barrier below
-  const float2* Pm = a.P + (size_t)base * nh + jh;
-  const float2* Hm = a.H + (size_t)base * nh + jh;
+  const float2* Pm = a.P + (size_t)(base + kb) * nh + jh;
+  const float2* Hm = a.H + (size_t)(base + kb) * nh + jh;
+  const int Kr = K - kb;
   const float2 z2 = make_float2(0.f, 0.f);
   dot2c S[NS > 0 ? NS : 1][2];     // field, parity of k
   dot2c V[NV > 0 ? NV : 1][4][2];  // pair, (P psi, P chi, H psi, H chi), parity of k
@@ -171,29 +181,49 @@ __global__ void __launch_bounds__(DF_STH, MINB) k_df_synth(const __grid_constant
   for (int v = 0; v < (NV > 0 ? NV : 1); ++v)
 #pragma unroll
     for (int q = 0; q < 8; ++q) V[v][q >> 1][q & 1] = dot2c{z2, z2};
-  float2 pb[DF_PF], hb[DF_PF];
+  // Table rows in flight.  Under the tight register budget (MINB > 1) a rolling prefetch:
+  // slot u holds row k0 + u and, once consumed, is refilled with row k0 + PF + u, so every row
+  // is requested PF rows before its use with one register set (scalar-only blocks do less
+  // arithmetic per row and have the registers for twice the distance).  Otherwise (launches of
+  // one wave, latency-bound with a few warps per SM) a double buffer of twice the distance:
+  // the next PF rows are requested together before the current ones are used.
+  constexpr bool ROLL = MINB > 1;
+  constexpr int PF = (ROLL && NV > 0) ? DF_PF : 2 * DF_PF;
+  float2 pb[PF], hb[PF];
 #pragma unroll
-  for (int u = 0; u < DF_PF; ++u) {
-    pb[u] = u < K ? __ldg(Pm + (size_t)u * nh) : z2;
-    hb[u] = (NV > 0 && u < K) ? __ldg(Hm + (size_t)u * nh) : z2;
+  for (int u = 0; u < PF; ++u) {
+    pb[u] = u < Kr ? __ldg(Pm + (size_t)u * nh) : z2;
+    hb[u] = (NV > 0 && u < Kr) ? __ldg(Hm + (size_t)u * nh) : z2;
   }
-  for (int k0 = 0; k0 < K; k0 += DF_PF) {
-    float2 pn[DF_PF], hn[DF_PF];
+  for (int k0 = 0; k0 < Kr; k0 += PF) {
+    float2 pn[ROLL ? 1 : PF], hn[ROLL ? 1 : PF];
+    if (!ROLL) {
 #pragma unroll
-    for (int u = 0; u < DF_PF; ++u) {
-      const int kk = k0 + DF_PF + u;
-      pn[u] = kk < K ? __ldg(Pm + (size_t)kk * nh) : z2;
-      hn[u] = (NV > 0 && kk < K) ? __ldg(Hm + (size_t)kk * nh) : z2;
+      for (int u = 0; u < PF; ++u) {
+        const int kk = k0 + PF + u;
+        pn[ROLL ? 0 : u] = kk < Kr ? __ldg(Pm + (size_t)kk * nh) : z2;
+        hn[ROLL ? 0 : u] = (NV > 0 && kk < Kr) ? __ldg(Hm + (size_t)kk * nh) : z2;
+      }
     }
 #pragma unroll
-    for (int u = 0; u < DF_PF; u += 2) {  // k0 is even: the parity of k0 + u is that of u
-      if (k0 + u < K) df_synth_step<NS, NV, 0>(pb[u], hb[u], cf, K, k0 + u, S, V);
-      if (k0 + u + 1 < K) df_synth_step<NS, NV, 1>(pb[u + 1], hb[u + 1], cf, K, k0 + u + 1, S, V);
-    }
+    for (int u = 0; u < PF; u += 2) {  // k0 is even: the parity of k0 + u is that of u
+      if (k0 + u < Kr) df_synth_step<NS, NV, 0>(pb[u], hb[u], cf, a.T + 1, kb + k0 + u, S, V);
+      if (k0 + u + 1 < Kr) df_synth_step<NS, NV, 1>(pb[u + 1], hb[u + 1], cf, a.T + 1, kb + k0 + u + 1, S, V);
+      if (ROLL) {
 #pragma unroll
-    for (int u = 0; u < DF_PF; ++u) {
-      pb[u] = pn[u];
-      hb[u] = hn[u];
+        for (int v = u; v < u + 2; ++v) {
+          const int kk = k0 + PF + v;
+          pb[v] = kk < Kr ? __ldg(Pm + (size_t)kk * nh) : z2;
+          hb[v] = (NV > 0 && kk < Kr) ? __ldg(Hm + (size_t)kk * nh) : z2;
+        }
+      }
+    }
+    if (!ROLL) {
+#pragma unroll
+      for (int u = 0; u < PF; ++u) {
+        pb[u] = pn[ROLL ? 0 : u];
+        hb[u] = hn[ROLL ? 0 : u];
+      }
     }
   }
   const int lat = jh, lats = nlat - 1 - jh;
@@ -239,7 +269,8 @@ struct DfAnalArgs {
   double2* dv;          // [NV][nlm]
   double2* cu;
   double2* spec;        // [NS][nlm]
-  int T, nlat, nh, nlm;
+  const int* ja;        // polar bounds: first latitude per (m, 32-degree group) [T+1][ngd]
+  int T, nlat, nh, nlm, ngd;
   double inv_a;
 };
 
@@ -276,7 +307,8 @@ __device__ __forceinline__ void df_anal_step(float2 pv, float2 hv, const float4*
 // and differences of every field (vector pair v: A+, A-, B+, B- with w / (1 - mu^2); scalar f:
 // G+, G- with w); warps 0-1 own the even degrees k = 128 tile + 2 i, warps 2-3 the odd ones,
 // and each thread streams its table column over the latitudes, DF_PF latitudes of table entries
-// in flight.  P pairs with the sums for even k and the differences for odd k, H the other way
+// in flight, from the first latitude that the 64 degrees of its warp's span need (polar
+// bounds).  P pairs with the sums for even k and the differences for odd k, H the other way
 // round.
 template <int NS, int NV>
 __global__ void __launch_bounds__(DF_ATH, 4) k_df_anal(const __grid_constant__ DfAnalArgs a) {
@@ -285,6 +317,17 @@ __global__ void __launch_bounds__(DF_ATH, 4) k_df_anal(const __grid_constant__ D
   const int T = a.T, K = T + 1 - m, nh = a.nh, nlat = a.nlat;
   if (tile * DF_ATH >= K) return;  // uniform over the block
   const int base = moff(T, m);
+  const int par = threadIdx.x >= DF_ATH / 2;  // uniform over each warp
+  const int idx = threadIdx.x & (DF_ATH / 2 - 1);
+  const int k = tile * DF_ATH + 2 * idx + par;
+  // first latitude: warp w spans the degree indices tile 128 + 64 (w & 1) .. + 63, bound groups
+  // g0 and g0 + 1; requested before the staging, whose time hides its latency
+  int jb = nh;
+  if (k < K) {
+    const int g0 = tile * (DF_ATH / 32) + 2 * ((threadIdx.x >> 5) & 1);
+    const int* jam = a.ja + m * a.ngd;
+    jb = min(__ldg(jam + g0), g0 + 1 < a.ngd ? __ldg(jam + g0 + 1) : nh);  // warp-uniform
+  }
   // staging
   for (int j = threadIdx.x; j < nh; j += DF_ATH) {
     const float4 wv = __ldg(a.wdf + j);
@@ -309,9 +352,6 @@ __global__ void __launch_bounds__(DF_ATH, 4) k_df_anal(const __grid_constant__ D
     }
   }
   __syncthreads();
-  const int par = threadIdx.x >= DF_ATH / 2;  // uniform over each warp
-  const int idx = threadIdx.x & (DF_ATH / 2 - 1);
-  const int k = tile * DF_ATH + 2 * idx + par;
   if (k >= K) return;  // no barrier below
   const int Ke = (K + 1) / 2;
   const size_t col = (size_t)base * nh + (par ? Ke : 0) + tile * (DF_ATH / 2) + idx;
@@ -331,10 +371,10 @@ __global__ void __launch_bounds__(DF_ATH, 4) k_df_anal(const __grid_constant__ D
   float2 pb[DF_PF], hb[DF_PF];
 #pragma unroll
   for (int u = 0; u < DF_PF; ++u) {
-    pb[u] = u < nh ? __ldg(Pc + (size_t)u * K) : z2;
-    hb[u] = (NV > 0 && u < nh) ? __ldg(Hc + (size_t)u * K) : z2;
+    pb[u] = jb + u < nh ? __ldg(Pc + (size_t)(jb + u) * K) : z2;
+    hb[u] = (NV > 0 && jb + u < nh) ? __ldg(Hc + (size_t)(jb + u) * K) : z2;
   }
-  for (int j0 = 0; j0 < nh; j0 += DF_PF) {
+  for (int j0 = jb; j0 < nh; j0 += DF_PF) {
     float2 pn[DF_PF], hn[DF_PF];
 #pragma unroll
     for (int u = 0; u < DF_PF; ++u) {
@@ -383,6 +423,7 @@ size_t df_anal_smem(int nh) {
 
 struct DfLegendre {
   int T = 0, nlat = 0, nh = 0, nlm = 0, max_fields = 0, nsm = 0;
+  PolarBounds pb;
   float2 *Ps = nullptr, *Hs = nullptr, *Pa = nullptr, *Ha = nullptr;
   float4* wdf = nullptr;
   float4* in = nullptr;  // split inputs of one call: [2 max_fields][max(nlm, (T+1) nlat)]
@@ -410,7 +451,7 @@ static int df_smem_attr(int nh, int T) {
 }
 
 int df_legendre_create(DfLegendre** out, const double* P, const double* H, const double* w, const double* wq, int T,
-                       int nlat, int max_fields, cudaStream_t stream) {
+                       int nlat, int max_fields, const PolarBounds& pb, cudaStream_t stream) {
   *out = nullptr;
   const int nh = nlat / 2;
   if (df_anal_smem<2, 2>(nh) > 200 * 1024)  // 12 staged arrays of nh float4
@@ -421,6 +462,7 @@ int df_legendre_create(DfLegendre** out, const double* P, const double* H, const
   t->nh = nh;
   t->nlm = (T + 1) * (T + 2) / 2;
   t->max_fields = max_fields;
+  t->pb = pb;
   {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -455,6 +497,21 @@ void df_legendre_destroy(DfLegendre* t) {
   if (!t) return;
   for (void* p : {(void*)t->Ps, (void*)t->Hs, (void*)t->Pa, (void*)t->Ha, (void*)t->wdf, (void*)t->in}) cudaFree(p);
   delete t;
+}
+
+void df_legendre_streamed(const DfLegendre* t, long long* syn, long long* ana) {
+  const int T = t->T, nh = t->nh, ngl = t->pb.ngl, ngd = t->pb.ngd;
+  long long s = 0, a = 0;
+  for (int m = 0; m <= T; ++m) {
+    const int K = T + 1 - m;
+    for (int g = 0; g < ngl; ++g) s += (long long)std::min(32, nh - 32 * g) * (K - (t->pb.ks[m * ngl + g] & ~1));
+    for (int g = 0; 32 * g < K; g += 2) {  // one warp pair per 64-degree span
+      const int jb = std::min(t->pb.ja[m * ngd + g], g + 1 < ngd ? t->pb.ja[m * ngd + g + 1] : nh);
+      a += (long long)std::min(64, K - 32 * g) * (nh - jb);
+    }
+  }
+  *syn = s;
+  *ana = a;
 }
 
 void df_legendre_set_prof(DfLegendre* t, StageProf* prof) {
@@ -498,6 +555,8 @@ int df_leg_synth(DfLegendre* t, const double2* spec, double2* F, int nfs, const 
   a.nh = t->nh;
   a.nlm = t->nlm;
   a.inv_a = inv_a;
+  a.ks = t->pb.d_ks;
+  a.ngl = t->pb.ngl;
   const float4* cs = t->in;
   const float4* cp = t->in + nfs * nlm;
   const float4* cc = cp + nfv * nlm;
@@ -544,6 +603,8 @@ int df_leg_anal(DfLegendre* t, const double2* FA, const double2* FB, double2* dv
   a.nh = t->nh;
   a.nlm = t->nlm;
   a.inv_a = inv_a;
+  a.ja = t->pb.d_ja;
+  a.ngd = t->pb.ngd;
   const float4* fa = t->in;
   const float4* fb = fa + nfv * fo;
   const float4* fg = fb + nfv * fo;

@@ -7,8 +7,11 @@ namespace rexi {
 struct DfLegendre;
 
 // P, H: the FP64 tables [moff(m)+k][nh]; w, wq: Gauss weights and w / (1 - mu^2) [nh] (device).
+// pb: the plan's polar bounds (device arrays used by the kernels; must outlive the state)
 int df_legendre_create(DfLegendre** out, const double* P, const double* H, const double* w, const double* wq, int T,
-                       int nlat, int max_fields, cudaStream_t stream);
+                       int nlat, int max_fields, const PolarBounds& pb, cudaStream_t stream);
+// table entries (k < T + 1 - m, j < nh) the kernels stream per table: synthesis, analysis
+void df_legendre_streamed(const DfLegendre* t, long long* syn, long long* ana);
 void df_legendre_destroy(DfLegendre* t);
 void df_legendre_set_prof(DfLegendre* t, StageProf* prof);
 

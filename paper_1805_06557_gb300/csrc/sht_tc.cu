@@ -61,6 +61,8 @@ struct Job {
                     // stage, and the accumulator rows past `rows` hold stale sums that the
                     // epilogue never stores
   int newb;         // 1: the job starts a B group (consecutive jobs of one m share a B operand)
+  int c0;           // first K chunk streamed: the chunks before it hold only table entries below
+                    // the polar threshold (never stored; a_off points at chunk c0; c0 < nchunk)
 };
 
 // precision modes of the GEMM (template parameter PM)
@@ -377,12 +379,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
         const unsigned char* A = (jb.tab ? g.tabH : g.tabP) + jb.a_off;
         // rows / 8 core-matrix row groups: a prefix of the stage's canonical layout
         const uint32_t jchunk = (uint32_t)jb.rows * KC * eb;
-        for (int c = 0; c < jb.nchunk; ++c) {
+        for (int c = jb.c0; c < jb.nchunk; ++c) {
           if (round > 0) ok = tc::mbar_wait(empty0 + 8 * s, (round - 1) & 1);
           if (!ok) break;
           const uint32_t cb = (c == jb.nchunk - 1) ? (uint32_t)jb.rows * jb.kl * eb * (SPLIT ? 2 : 1) : jchunk;
           tc::mbar_expect_tx(full0 + 8 * s, cb);
-          tc::bulk_g2s(sa0 + s * chunk_bytes, A + (size_t)c * jchunk, cb, full0 + 8 * s);
+          tc::bulk_g2s(sa0 + s * chunk_bytes, A + (size_t)(c - jb.c0) * jchunk, cb, full0 + 8 * s);
           ++a_issued;
           if (++s == S) {
             s = 0;
@@ -438,7 +440,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
         // so that consecutive MMAs do not wait on each other's result
         const uint32_t dt = tmem + cs * TC_NACC * acc;
         const uint64_t bdesc0 = tc::smem_desc(sb0 + b * g.bslot, 128u, (uint32_t)(jb.kpad / E) * 128u);
-        for (int c = 0; c < jb.nchunk; ++c) {
+        for (int c = jb.c0; c < jb.nchunk; ++c) {
           ok = tc::mbar_wait(full0 + 8 * s, round & 1);
           if (!ok) break;
           tc::fence_after_sync();
@@ -451,7 +453,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
 #pragma unroll
           for (int q = 0; q < KSTEPS; ++q) {  // + 256 B per k-step: +16 in the address field
             // k-step q goes to accumulator q % TC_NACC; its first use initialises it
-            const uint32_t accum = (c > 0 || q >= TC_NACC) ? 1u : 0u;
+            const uint32_t accum = (c > jb.c0 || q >= TC_NACC) ? 1u : 0u;
             const uint32_t da = dt + cs * (q % TC_NACC);
             if (q < nks) {
               if (BF) {
@@ -503,8 +505,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
       }
       tc::fence_after_sync();
       if (32 * warp < jb.rows) {  // warp-uniform: tcgen05.ld is collective
-        // accumulators a < nacc received k-steps (all four unless the job is one short chunk)
-        const int nacc = jb.nchunk > 1 ? TC_NACC : min(TC_NACC, jb.kl / KSTEP);
+        // accumulators a < nacc received k-steps (all four unless the job streams one short chunk)
+        const int nacc = jb.nchunk - jb.c0 > 1 ? TC_NACC : min(TC_NACC, jb.kl / KSTEP);
         const uint32_t lq = (uint32_t)(32 * warp) << 16;
         const uint32_t ta0 = tmem + lq + cs * TC_NACC * acc0, ta1 = tmem + lq + cs * TC_NACC * acc1;
         const int row = jb.tile * 128 + 32 * warp + lane;
@@ -552,7 +554,8 @@ __device__ __forceinline__ void store_elem(unsigned char* base, size_t off, floa
 // pm = PM_TF32 / PM_BF16 / PM_TF32X3 (a chunk then holds kc hi elements, then kc lo elements)
 struct TabJob {
   long long a_off;
-  int m, rows, tile, nchunk, kl;  // rows: stored rows (<= 128); kl: K of the last chunk
+  int m, rows, tile, nchunk, kl, c0;  // rows: stored rows (<= 128); kl: K of the last chunk;
+                                      // chunks c0 .. nchunk - 1 are stored
 };
 __global__ void k_tc_table(const double* __restrict__ src, unsigned char* __restrict__ dst,
                            const TabJob* __restrict__ jobs, int njobs, int T, int nh, int synth,
@@ -567,11 +570,11 @@ __global__ void k_tc_table(const double* __restrict__ src, unsigned char* __rest
   const int KCK = split ? KC / 2 : KC;                                     // K per chunk
   const int K = T + 1 - j.m, base = moff(T, j.m);
   unsigned char* out = dst + j.a_off;
-  for (int c = 0; c < j.nchunk; ++c) {
+  for (int c = j.c0; c < j.nchunk; ++c) {
     // every chunk but the last covers KCK K-elements per row; the last covers j.kl
     const int kc = (c == j.nchunk - 1) ? j.kl : KCK;
     const int sbo = ((split ? 2 * kc : kc) / E) * 128;
-    unsigned char* ch = out + (size_t)c * j.rows * KC * eb;
+    unsigned char* ch = out + (size_t)(c - j.c0) * j.rows * KC * eb;
     for (int kk = 0; kk < kc; ++kk) {
       double x = 0.0;
       if (synth) {  // rows = latitudes of the northern half, K = all degrees n = m + k
@@ -617,6 +620,7 @@ struct TcLegendre {
   Sched sched[2][2];
   int kpad_smax = 0;  // largest K extent of a synthesis B operand
   int nsm = 0;
+  long long streamed_s = 0, streamed_a = 0;  // table entries inside the streamed chunks (per table)
   StageProf* prof = nullptr;
 };
 
@@ -626,9 +630,10 @@ static int tc_fail(const char* what, cudaError_t e) { return cuda_fail(e, what);
 // each tile's (P, H) pair), which then run back to back and share one B operand (the first job
 // of a unit starts a B group, `newb`); a unit heavier than half the mean CTA load is split into
 // its tiles, so that the heaviest zonal orders still balance.  Units go longest first (cost =
-// A bytes, rows x K), each to the least-loaded CTA so far.
-static cudaError_t make_sched(const std::vector<Job>& P, const std::vector<Job>* H, int nsm, Sched& sc) {
-  auto cost = [&](int u) { return (long long)P[u].rows * P[u].kpad * (H ? 2 : 1); };
+// A bytes, rows x the K streamed from chunk c0 on, kck K elements per chunk), each to the
+// least-loaded CTA so far.
+static cudaError_t make_sched(const std::vector<Job>& P, const std::vector<Job>* H, int nsm, int kck, Sched& sc) {
+  auto cost = [&](int u) { return (long long)P[u].rows * (P[u].kpad - P[u].c0 * kck) * (H ? 2 : 1); };
   std::vector<std::vector<int>> units;
   {
     std::map<int, std::vector<int>> by_m;
@@ -699,7 +704,7 @@ static cudaError_t make_sched(const std::vector<Job>& P, const std::vector<Job>*
 }
 
 int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const double* w, const double* wq,
-                       int T, int nlat, int max_fields, int mode, cudaStream_t stream) {
+                       int T, int nlat, int max_fields, int mode, const PolarBounds& pb, cudaStream_t stream) {
   *out = nullptr;
   if (max_fields > 8) return fail(REXI_EINVAL, "sh_plan_create: tensor-core precisions support max_fields <= 8");
   const bool bf16 = mode == SH_BF16, split = mode == SH_TF32X3;
@@ -743,10 +748,15 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
     t->kpad_smax = std::max(t->kpad_smax, kpad);
     for (int tile = 0; tile < t->ntile_s; ++tile) {
       const int rows = std::min(128, (t->nh - 128 * tile + 7) / 8 * 8);
-      tj.push_back(TabJob{aoff, m, rows, tile, nchunk, kl});
-      jsP.push_back(Job{aoff, m, tile, nchunk, kpad, 0, kl, rows});
-      jsH.push_back(Job{aoff, m, tile, nchunk, kpad, 1, kl, rows});
-      aoff += (long long)rows * ((nchunk - 1) * KC + kw * kl) * eb;
+      // first chunk: the smallest polar start of the tile's four 32-latitude groups
+      int kb = K;
+      for (int g = 4 * tile; g < std::min(4 * tile + 4, pb.ngl); ++g) kb = std::min(kb, pb.ks[m * pb.ngl + g]);
+      const int c0 = std::min(kb / KCK, nchunk - 1);
+      tj.push_back(TabJob{aoff, m, rows, tile, nchunk, kl, c0});
+      jsP.push_back(Job{aoff, m, tile, nchunk, kpad, 0, kl, rows, 0, c0});
+      jsH.push_back(Job{aoff, m, tile, nchunk, kpad, 1, kl, rows, 0, c0});
+      aoff += (long long)rows * ((nchunk - 1 - c0) * KC + kw * kl) * eb;
+      t->streamed_s += (long long)std::min(128, t->nh - 128 * tile) * std::max(0, K - c0 * KCK);
     }
   }
   const long long tab_s_bytes = aoff;
@@ -763,10 +773,16 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
     const int ntiles = (K + 127) / 128;
     for (int tile = 0; tile < ntiles; ++tile) {
       const int rows = std::min(128, (K - 128 * tile + 7) / 8 * 8);
-      ta.push_back(TabJob{aoff, m, rows, tile, nchunk_a, kl_a});
-      jaP.push_back(Job{aoff, m, tile, nchunk_a, t->kpad_a, 0, kl_a, rows});
-      jaH.push_back(Job{aoff, m, tile, nchunk_a, t->kpad_a, 1, kl_a, rows});
-      aoff += (long long)rows * ((nchunk_a - 1) * KC + kw * kl_a) * eb;
+      // first chunk: the smallest polar start of the tile's 32-degree groups
+      int jb = t->nh;
+      for (int g = 4 * tile; g < std::min(4 * tile + 4, pb.ngd) && 32 * g < K; ++g)
+        jb = std::min(jb, pb.ja[m * pb.ngd + g]);
+      const int c0 = std::min(jb / KCK, nchunk_a - 1);
+      ta.push_back(TabJob{aoff, m, rows, tile, nchunk_a, kl_a, c0});
+      jaP.push_back(Job{aoff, m, tile, nchunk_a, t->kpad_a, 0, kl_a, rows, 0, c0});
+      jaH.push_back(Job{aoff, m, tile, nchunk_a, t->kpad_a, 1, kl_a, rows, 0, c0});
+      aoff += (long long)rows * ((nchunk_a - 1 - c0) * KC + kw * kl_a) * eb;
+      t->streamed_a += (long long)std::min(128, K - 128 * tile) * std::max(0, t->nh - c0 * KCK);
     }
   }
   const long long tab_a_bytes = aoff;
@@ -788,8 +804,10 @@ int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const
       (e = cudaMalloc(&t->tabPa, tab_a_bytes)) || (e = cudaMalloc(&t->tabHa, tab_a_bytes)) ||
       (e = cudaMalloc(&t->err, sizeof(int))) ||
       (e = cudaMalloc(&d_tj, sizeof(TabJob) * tj.size())) || (e = cudaMalloc(&d_ta, sizeof(TabJob) * ta.size())) ||
-      (e = make_sched(jsP, nullptr, t->nsm, t->sched[0][0])) || (e = make_sched(jsP, &jsH, t->nsm, t->sched[0][1])) ||
-      (e = make_sched(jaP, nullptr, t->nsm, t->sched[1][0])) || (e = make_sched(jaP, &jaH, t->nsm, t->sched[1][1]))) {
+      (e = make_sched(jsP, nullptr, t->nsm, KCK, t->sched[0][0])) ||
+      (e = make_sched(jsP, &jsH, t->nsm, KCK, t->sched[0][1])) ||
+      (e = make_sched(jaP, nullptr, t->nsm, KCK, t->sched[1][0])) ||
+      (e = make_sched(jaP, &jaH, t->nsm, KCK, t->sched[1][1]))) {
     cudaGetLastError();
     tc_legendre_destroy(t);
     cudaFree(d_tj);
@@ -918,6 +936,11 @@ int tc_leg_synth_mixed(TcLegendre* t, const double2* psi, const double2* chi, do
 int tc_leg_anal_mixed(TcLegendre* t, const double2* FA, const double2* FB, double2* dv, double2* cu, int nfv,
                       const double2* F, double2* spec, int nfs, double inv_a, cudaStream_t s) {
   return gemm(t, false, nfv, FA, FB, dv, cu, nfs, F, spec, inv_a, s);
+}
+
+void tc_legendre_streamed(const TcLegendre* t, long long* syn, long long* ana) {
+  *syn = t->streamed_s;
+  *ana = t->streamed_a;
 }
 
 void tc_legendre_set_prof(TcLegendre* t, StageProf* prof) {

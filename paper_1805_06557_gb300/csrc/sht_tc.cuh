@@ -69,6 +69,24 @@ struct StageProf {
   }
 };
 
+// Polar truncation of the Legendre contractions (the "polar optimisation" of SHTns, the
+// transform library the paper uses): Pt_n^m and Ht_n^m carry the factor (1 - mu^2)^{m/2} and
+// are negligible where sin(theta) is small against m / n, so near the poles the leading
+// terms of every sum can be skipped.  Per zonal order m, from the FP64 tables:
+//   ks[m * ngl + g]: first degree index k = n - m at which P or H exceeds the threshold in
+//     magnitude at one of the northern latitudes 32 g .. 32 g + 31 (T + 1 - m if nowhere):
+//     the synthesis of those latitudes starts there;
+//   ja[m * ngd + g]: first northern latitude at which P or H of one of the degree indices
+//     k = 32 g .. 32 g + 31 exceeds it (nh if nowhere): their analysis starts there.
+// Every skipped entry is below the threshold.  With the truncation off, every start is 0.
+struct PolarBounds {
+  int ngl = 0, ngd = 0;        // groups of 32 latitudes, of 32 degrees
+  const int* d_ks = nullptr;   // device [T+1][ngl]
+  const int* d_ja = nullptr;   // device [T+1][ngd]
+  const int* ks = nullptr;     // host copies
+  const int* ja = nullptr;
+};
+
 struct TcLegendre;
 // stage timer of the owning plan (may be null)
 void tc_legendre_set_prof(TcLegendre* t, StageProf* prof);
@@ -76,9 +94,13 @@ void tc_legendre_set_prof(TcLegendre* t, StageProf* prof);
 void tc_legendre_set_epilogue_polls(TcLegendre* t, int polls);
 
 // mode: SH_TF32, SH_BF16 or SH_TF32X3
+// pb: the plan's polar bounds (host copies read here; the tables skip what they exclude)
 int tc_legendre_create(TcLegendre** out, const double* P, const double* H, const double* w,
                        const double* wq, int T, int nlat, int max_fields, int mode,
-                       cudaStream_t stream);
+                       const PolarBounds& pb, cudaStream_t stream);
+// table entries (k < T + 1 - m, j < nh) inside the chunks the GEMM streams, per table:
+// synthesis, analysis
+void tc_legendre_streamed(const TcLegendre* t, long long* syn, long long* ana);
 void tc_legendre_destroy(TcLegendre* t);
 int tc_leg_synth(TcLegendre* t, const double2* spec, double2* F, int nf, cudaStream_t s);
 int tc_leg_anal(TcLegendre* t, const double2* F, double2* spec, int nf, cudaStream_t s);

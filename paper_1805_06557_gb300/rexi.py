@@ -510,7 +510,13 @@ class ShDesc(ctypes.Structure):
     _fields_ = [("T", ctypes.c_int), ("nlat", ctypes.c_int), ("nlon", ctypes.c_int),
                 ("radius", ctypes.c_double), ("precision", ctypes.c_int),
                 ("max_fields", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("epilogue_wait_polls", ctypes.c_int)]
+                ("epilogue_wait_polls", ctypes.c_int), ("polar_threshold", ctypes.c_double)]
+
+
+class ShTableUse(ctypes.Structure):
+    _fields_ = [("total", ctypes.c_longlong), ("needed_synth", ctypes.c_longlong),
+                ("needed_anal", ctypes.c_longlong), ("streamed_synth", ctypes.c_longlong),
+                ("streamed_anal", ctypes.c_longlong), ("threshold", ctypes.c_double)]
 
 
 _lib.sh_plan_create.argtypes = [ctypes.POINTER(ShDesc), ctypes.POINTER(ctypes.c_void_p)]
@@ -519,6 +525,7 @@ _lib.sh_plan_get_grid.argtypes = [ctypes.c_void_p, _dp, _dp]
 for _n in ("sh_synthesis", "sh_analysis"):
     getattr(_lib, _n).argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
 _lib.sh_plan_check.argtypes = [ctypes.c_void_p]
+_lib.sh_plan_get_table_use.argtypes = [ctypes.c_void_p, ctypes.POINTER(ShTableUse)]
 _lib.sh_plan_set_profiling.argtypes = [ctypes.c_void_p, ctypes.c_int]
 _lib.sh_plan_get_profile.argtypes = [ctypes.c_void_p, _dp, _ip, ctypes.c_int]
 SH_STAGE_NAMES = ("legendre_fp64", "legendre_df", "tc_gemm", "tc_epilogue", "fft")
@@ -538,13 +545,16 @@ class ShPlan:
     """Spherical-harmonic transforms on a Gauss grid (nlat x nlon), truncation T."""
 
     def __init__(self, T, nlat, nlon, radius, precision="fp64", max_fields=1, stream=None,
-                 epilogue_wait_polls=0):
+                 epilogue_wait_polls=0, polar_threshold=0.0):
+        """polar_threshold: 0 = the library default (1e-19), > 0 = that threshold, < 0 = no
+        polar truncation of the Legendre sums."""
         d = ShDesc()
         d.T, d.nlat, d.nlon, d.radius = int(T), int(nlat), int(nlon), float(radius)
         d.precision = _SH_PREC[precision] if isinstance(precision, str) else int(precision)
         d.max_fields = int(max_fields)
         d.stream = ctypes.c_void_p(_stream_handle(stream))
         d.epilogue_wait_polls = int(epilogue_wait_polls)
+        d.polar_threshold = float(polar_threshold)
         h = ctypes.c_void_p()
         _check(_lib.sh_plan_create(ctypes.byref(d), ctypes.byref(h)))
         self._h = h
@@ -580,6 +590,13 @@ class ShPlan:
     def check(self):
         """Synchronise; raise if a device-side bounded wait gave up."""
         _check(_lib.sh_plan_check(self._h))
+
+    def table_use(self):
+        """Table entries per table: total, needed by the polar-truncated sums (synthesis,
+        analysis), streamed by this plan's kernels, and the threshold in use (0: off)."""
+        u = ShTableUse()
+        _check(_lib.sh_plan_get_table_use(self._h, ctypes.byref(u)))
+        return {k: getattr(u, k) for k, _ in ShTableUse._fields_}
 
     def set_profiling(self, enable=True):
         _check(_lib.sh_plan_set_profiling(self._h, 1 if enable else 0))

@@ -163,3 +163,19 @@ def test_mixed_transforms_reject_a_null_plan(rexi):
     lib = rexi.library()
     assert lib.sh_synthesis_mixed(None, None, None, 1, None, None, None, None, 1) == rexi.REXI_EINVAL
     assert lib.sh_analysis_mixed(None, None, None, None, None, 1, None, None, 1) == rexi.REXI_EINVAL
+
+
+def test_sh_plan_rejects_bad_polar_threshold(rexi):
+    """sh_plan_create checks the polar threshold before it touches the device (thresholds of
+    1e-3 and above, or NaN, would truncate visibly); the table-use query checks its plan."""
+    import ctypes
+    lib = rexi.library()
+    for thr in (1e-3, 0.5, float("nan")):
+        d = rexi.ShDesc()
+        d.T, d.nlat, d.nlon, d.radius, d.max_fields = 31, 48, 96, 6.37122e6, 1
+        d.precision = rexi.SH_FP64
+        d.polar_threshold = thr
+        h = ctypes.c_void_p()
+        assert lib.sh_plan_create(ctypes.byref(d), ctypes.byref(h)) == rexi.REXI_EINVAL
+        assert not h.value
+    assert lib.sh_plan_get_table_use(None, None) == rexi.REXI_EINVAL
