@@ -635,13 +635,15 @@ __global__ void __launch_bounds__(FTH) k_fft_anal64(const __grid_constant__ FftS
   fft_anal_block<double2>(sg, fp, tw, T, nlat);
 }
 
-// double-float transforms (SH_DF plans): FP64 inputs and outputs, arithmetic on the FP32 pipe
-__global__ void __launch_bounds__(FTH) k_fft_synth_df(const __grid_constant__ FftSegs sg,
+// double-float transforms (SH_DF plans): FP64 inputs and outputs, arithmetic on the FP32 pipe;
+// four blocks per SM, which their shared memory allows (at 76 registers only three fit: the
+// one-pass N(U) synthesis at T511 took 0.086 ms that way, 0.078 ms with four)
+__global__ void __launch_bounds__(FTH, 4) k_fft_synth_df(const __grid_constant__ FftSegs sg,
                                                       const __grid_constant__ FftPlan fp,
                                                       const dfcx* __restrict__ tw, int T, int nlat) {
   fft_synth_block<dfcx>(sg, fp, tw, T, nlat);
 }
-__global__ void __launch_bounds__(FTH) k_fft_anal_df(const __grid_constant__ FftSegs sg,
+__global__ void __launch_bounds__(FTH, 4) k_fft_anal_df(const __grid_constant__ FftSegs sg,
                                                      const __grid_constant__ FftPlan fp,
                                                      const dfcx* __restrict__ tw, int T, int nlat) {
   fft_anal_block<dfcx>(sg, fp, tw, T, nlat);
