@@ -183,8 +183,22 @@ int rexi_step(rexi_plan* plan, const void* U0, void* U1, int batch);
  */
 int rexi_step_host(rexi_plan* plan, const double* U0, double* U1, int batch);
 
-/* Synchronises the plan stream and reports any error raised by device work since the last
- * call (REXI_ECUDA).  */
+/*
+ * rexi_step_host_async -- rexi_step on HOST buffers, pipelined for a stream of steps: the call
+ * enqueues the copy of U0 to one of two plan-owned device staging slots (on a copy stream), the
+ * step (on the plan stream) and the copy of the result to U1 (on a second copy stream), and
+ * returns without waiting.  Consecutive calls alternate the slots, so the copies of the steps
+ * before and after run on the copy engines while a step's kernels run; each call's copies and
+ * step are ordered by events.  U0 and U1 (batch*3*nlm complex128 each, as rexi_step_host) must
+ * stay valid and unchanged (U0) or unread (U1) until rexi_sync returns; page-locked memory is
+ * needed for the copies to overlap (pageable memory still gives the right result).  The first
+ * call allocates the two slots (2 x 2 x batch_max x 3 x nlm complex128) and creates the streams.
+ * Errors: REXI_EINVAL, REXI_ENOMEM, REXI_ECUDA.
+ */
+int rexi_step_host_async(rexi_plan* plan, const double* U0, double* U1, int batch);
+
+/* Synchronises the plan stream (and the copy streams of rexi_step_host_async) and reports any
+ * error raised by device work since the last call (REXI_ECUDA).  */
 int rexi_sync(rexi_plan* plan);
 
 /* Plan facts for benchmarking and tests. */

@@ -854,7 +854,59 @@ struct rexi_plan {
   std::map<int, LaunchSet> launches;  // by batch size
   double2* stage_in = nullptr;
   double2* stage_out = nullptr;
+  // rexi_step_host_async (set up on its first call): two device staging slots, a copy-in and a
+  // copy-out stream, and per slot the events that order the copies and the step
+  struct Async {
+    bool ready = false;
+    double2* in[2] = {};
+    double2* out[2] = {};
+    cudaStream_t cin = nullptr, cout = nullptr;
+    cudaEvent_t ev_in[2] = {}, ev_comp[2] = {}, ev_out[2] = {};
+    long long calls = 0;
+  } as;
 };
+
+// Creates the asynchronous host-step resources; every event is recorded once on the plan
+// stream so that the first waits on them are satisfied.
+static int async_setup(rexi_plan* p) {
+  rexi_plan::Async& a = p->as;
+  if (a.ready) return REXI_OK;
+  const size_t sb = sizeof(double2) * 3 * (size_t)p->nlm * p->d.max_batch;
+  int rc;
+  for (int s = 0; s < 2; ++s) {
+    if ((rc = dev_alloc(&a.in[s], sb, &p->e.workspace)) || (rc = dev_alloc(&a.out[s], sb, &p->e.workspace)))
+      return rc;
+  }
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&a.cin, cudaStreamNonBlocking)) ||
+      (e = cudaStreamCreateWithFlags(&a.cout, cudaStreamNonBlocking)))
+    return cuda_fail(e, "rexi_step_host_async: stream creation");
+  for (int s = 0; s < 2; ++s) {
+    for (cudaEvent_t* ev : {&a.ev_in[s], &a.ev_comp[s], &a.ev_out[s]}) {
+      if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)))
+        return cuda_fail(e, "rexi_step_host_async: event creation");
+      if ((e = cudaEventRecord(*ev, p->e.stream))) return cuda_fail(e, "rexi_step_host_async: event record");
+    }
+  }
+  a.ready = true;
+  return REXI_OK;
+}
+
+static void async_free(rexi_plan* p) {
+  rexi_plan::Async& a = p->as;
+  if (a.ready) cudaStreamSynchronize(p->e.stream);  // a step may still write a slot
+  if (a.cin) cudaStreamSynchronize(a.cin);
+  if (a.cout) cudaStreamSynchronize(a.cout);
+  for (int s = 0; s < 2; ++s) {
+    cudaFree(a.in[s]);
+    cudaFree(a.out[s]);
+    for (cudaEvent_t ev : {a.ev_in[s], a.ev_comp[s], a.ev_out[s]})
+      if (ev) cudaEventDestroy(ev);
+  }
+  if (a.cin) cudaStreamDestroy(a.cin);
+  if (a.cout) cudaStreamDestroy(a.cout);
+  a = rexi_plan::Async();
+}
 
 extern "C" int rexi_plan_create(const rexi_plan_desc* desc, rexi_plan** out) {
   if (!desc || !out) return fail(REXI_EINVAL, "rexi_plan_create: null argument");
@@ -959,6 +1011,7 @@ extern "C" int rexi_plan_create(const rexi_plan_desc* desc, rexi_plan** out) {
 
 extern "C" int rexi_plan_destroy(rexi_plan* p) {
   if (!p) return REXI_OK;
+  async_free(p);
   engine_free(p->e);
   for (auto& kv : p->launches) free_launch(kv.second);
   cudaFree(p->stage_in);
@@ -1040,8 +1093,42 @@ extern "C" int rexi_step_host(rexi_plan* p, const double* U0, double* U1, int ba
   return REXI_OK;
 }
 
+// Pipelined host steps: call i uses staging slot s = i mod 2.  Its input copy (copy-in stream)
+// waits until the step of call i - 2 has read slot s; its step (plan stream) waits for that
+// copy and for the output copy of call i - 2 to have read slot s; its output copy (copy-out
+// stream) waits for its step.  So the copies of calls i + 1 and i - 1 run on the copy engines
+// while the kernels of call i run.
+extern "C" int rexi_step_host_async(rexi_plan* p, const double* U0, double* U1, int batch) {
+  if (!p || !U0 || !U1) return fail(REXI_EINVAL, "rexi_step_host_async: null argument");
+  if (batch < 1 || batch > p->d.max_batch)
+    return fail(REXI_EINVAL, "rexi_step_host_async: batch %d outside [1, %d]", batch, p->d.max_batch);
+  const size_t bytes = sizeof(double2) * 3 * (size_t)p->nlm * batch;
+  if (overlaps(U0, U1, bytes)) return fail(REXI_EINVAL, "rexi_step_host_async: U0 and U1 overlap");
+  int rc = async_setup(p);
+  if (rc) return rc;
+  rexi_plan::Async& a = p->as;
+  const int s = (int)(a.calls & 1);
+  cudaStream_t st = p->e.stream;
+  REXI_CUDA_TRY(cudaStreamWaitEvent(a.cin, a.ev_comp[s], 0));
+  REXI_CUDA_TRY(cudaMemcpyAsync(a.in[s], U0, bytes, cudaMemcpyHostToDevice, a.cin));
+  REXI_CUDA_TRY(cudaEventRecord(a.ev_in[s], a.cin));
+  REXI_CUDA_TRY(cudaStreamWaitEvent(st, a.ev_in[s], 0));
+  REXI_CUDA_TRY(cudaStreamWaitEvent(st, a.ev_out[s], 0));
+  if ((rc = rexi_step(p, a.in[s], a.out[s], batch))) return rc;
+  REXI_CUDA_TRY(cudaEventRecord(a.ev_comp[s], st));
+  REXI_CUDA_TRY(cudaStreamWaitEvent(a.cout, a.ev_comp[s], 0));
+  REXI_CUDA_TRY(cudaMemcpyAsync(U1, a.out[s], bytes, cudaMemcpyDeviceToHost, a.cout));
+  REXI_CUDA_TRY(cudaEventRecord(a.ev_out[s], a.cout));
+  ++a.calls;
+  return REXI_OK;
+}
+
 extern "C" int rexi_sync(rexi_plan* p) {
   if (!p) return fail(REXI_EINVAL, "rexi_sync: null plan");
+  if (p->as.ready) {
+    REXI_CUDA_TRY(cudaStreamSynchronize(p->as.cin));
+    REXI_CUDA_TRY(cudaStreamSynchronize(p->as.cout));
+  }
   REXI_CUDA_TRY(cudaStreamSynchronize(p->e.stream));
   REXI_CUDA_TRY(cudaGetLastError());
   return REXI_OK;

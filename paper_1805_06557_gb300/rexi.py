@@ -72,6 +72,7 @@ _lib.rexi_plan_create.argtypes = [ctypes.POINTER(PlanDesc), ctypes.POINTER(ctype
 _lib.rexi_plan_destroy.argtypes = [ctypes.c_void_p]
 _lib.rexi_step.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
 _lib.rexi_step_host.argtypes = [ctypes.c_void_p, _dp, _dp, ctypes.c_int]
+_lib.rexi_step_host_async.argtypes = [ctypes.c_void_p, _dp, _dp, ctypes.c_int]
 _lib.rexi_sync.argtypes = [ctypes.c_void_p]
 _lib.rexi_plan_get_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(PlanInfo)]
 _lib.rexi_plan_get_poles.argtypes = [ctypes.c_void_p, _dp, _dp, _ip]
@@ -383,6 +384,12 @@ class Plan:
     def step_host_ptr(self, U0_ptr, U1_ptr, batch):
         _check(_lib.rexi_step_host(self._h, ctypes.cast(U0_ptr, _dp), ctypes.cast(U1_ptr, _dp),
                                    int(batch)))
+
+    def step_host_async_ptr(self, U0_ptr, U1_ptr, batch):
+        """Pipelined host step (rexi_step_host_async): returns at once; U0 and U1 (page-locked
+        host memory) must stay untouched until sync()."""
+        _check(_lib.rexi_step_host_async(self._h, ctypes.cast(U0_ptr, _dp), ctypes.cast(U1_ptr, _dp),
+                                         int(batch)))
 
     def sync(self):
         _check(_lib.rexi_sync(self._h))

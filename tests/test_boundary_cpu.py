@@ -165,6 +165,12 @@ def test_mixed_transforms_reject_a_null_plan(rexi):
     assert lib.sh_analysis_mixed(None, None, None, None, None, 1, None, None, 1) == rexi.REXI_EINVAL
 
 
+def test_async_host_step_rejects_a_null_plan(rexi):
+    """The pipelined host step checks its plan and buffers before it allocates or enqueues."""
+    lib = rexi.library()
+    assert lib.rexi_step_host_async(None, None, None, 1) == rexi.REXI_EINVAL
+
+
 def test_sh_plan_rejects_bad_polar_threshold(rexi):
     """sh_plan_create checks the polar threshold before it touches the device (thresholds of
     1e-3 and above, or NaN, would truncate visibly); the table-use query checks its plan."""

@@ -262,6 +262,49 @@ def test_step_host_mixed_pinned_and_pageable(env):
     plan.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_step_host_async_pipelined(env, prec):
+    """rexi_step_host_async: a stream of steps on distinct pinned buffers (copies of the steps
+    before and after overlapping each step's kernels, two staging slots in turn), then one
+    pair of buffers reused by every call (as a serving loop would), a synchronous host step in
+    between, and pageable buffers: every result equals the device step of its input bit for
+    bit."""
+    torch, rexi = env
+    T, N, dt, B, n = 63, 256, 3600.0, 4, 5
+    p0, Xc, _ = contour(T, dt, N)
+    plan = rexi.Plan(T, N, dt, OM, A, PB, p0=p0, Xc=Xc, precision=prec, max_batch=B)
+    ins = [np.stack([syn.gaussian_state(T, 400 + 10 * j + i) for i in range(B)]) for j in range(n)]
+    refs = []
+    for U0 in ins:
+        u0 = torch.from_numpy(U0).cuda()
+        u1 = torch.empty_like(u0)
+        plan.step(u0, u1, B)
+        plan.sync()
+        refs.append(u1.cpu().numpy())
+    hin = [torch.from_numpy(U0).pin_memory() for U0 in ins]
+    hout = [torch.full_like(h, float("nan")).pin_memory() for h in hin]
+    for j in range(n):
+        plan.step_host_async_ptr(hin[j].data_ptr(), hout[j].data_ptr(), B)
+    plan.sync()
+    for j in range(n):
+        assert np.array_equal(hout[j].numpy(), refs[j]), j
+    # one buffer pair for every call: the last result stays
+    out = torch.full_like(hin[0], float("nan")).pin_memory()
+    for j in range(n):
+        plan.step_host_async_ptr(hin[j].data_ptr(), out.data_ptr(), B)
+    assert np.array_equal(plan.step_host(ins[1]), refs[1])   # a synchronous step in between
+    plan.sync()
+    assert np.array_equal(out.numpy(), refs[n - 1])
+    # pageable buffers: correct, without the overlap
+    pg = np.empty_like(ins[2])
+    plan.step_host_async_ptr(ins[2].ctypes.data, pg.ctypes.data, B)
+    plan.sync()
+    assert np.array_equal(pg, refs[2])
+    with pytest.raises(rexi.RexiError):
+        plan.step_host_async_ptr(hin[0].data_ptr(), hout[0].data_ptr(), B + 1)
+    plan.close()
+
+
 def test_explicit_poles_and_zero_input(env):
     """Poles given explicitly (the oracle's) give the same result; a zero state stays zero."""
     torch, rexi = env
