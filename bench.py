@@ -14,6 +14,7 @@ end-to-end rate through rexi_step_host with host buffers, and the CPU oracle.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
 import argparse
+import datetime
 import json
 import math
 import os
@@ -114,28 +115,41 @@ def workload_config(args, world):
 
 # ---------------------------------------------------------------------------------------
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    """nvidia-smi sampling (every 50 ms) of SM clocks and throttle reasons during the timed
+    region: start() returns once the sampler has written its first line, so that the region
+    begins with the sampler running; region_start() / stop() bracket the region, and the
+    summary uses the samples whose timestamps fall inside it (all samples if none do, as the
+    region can be shorter than the sampling interval)."""
 
     def __init__(self, index):
         self.index = index
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
-            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+            q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
                  "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            deadline = time.time() + 5.0
+            while time.time() < deadline and os.path.getsize(self.path) == 0 and self.proc.poll() is None:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
+        self.t0 = time.time()
+
+    def region_start(self):
+        self.t0 = time.time()
 
     def stop(self):
+        self.t1 = time.time()
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -143,25 +157,29 @@ class Clocks:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, mx, reasons = [], 0.0, set()
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx = max(mx, float(f[2]))
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None
+            try:
+                rows.append((ts, float(f[2]), float(f[3]), {nm for nm, v in zip(names, f[6:10])
+                                                             if v.lower().startswith("active")}))
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
         os.unlink(self.path)
-        if not sm:
+        if not rows:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        inside = [r for r in rows if r[0] is not None and self.t0 - 0.025 <= r[0] <= self.t1 + 0.025]
+        use = inside or rows
+        return {"sm_mhz": statistics.median(r[1] for r in use), "sm_max_mhz": max(r[2] for r in use),
+                "reasons": sorted(set().union(*(r[3] for r in use))), "samples": len(use),
+                "samples_in_region": len(inside), "region_s": round(self.t1 - self.t0, 4)}
 
 
 # ---------------------------------------------------------------------------------------
@@ -853,6 +871,7 @@ def main():
     barrier()
     clk = Clocks(local)
     clk.start()
+    clk.region_start()
     ms = timed(mixed, u0, u1, B, args.steps, 0)
     clocks = clk.stop()
     prof = mixed.profile(reset=True)
