@@ -33,8 +33,10 @@ __device__ __forceinline__ double eps_d(int n, int m) {
   return sqrt((double(n) * n - double(m) * m) / (4.0 * n * n - 1.0));
 }
 
+// P, H: [moff(m)+k][nh]; Pn: the next degree's row P_{T+1}^m [m][nh] (the analysis of vector
+// fields forms its H-sums from P-sums of the neighbouring degrees, k_divcurl_from_p)
 __global__ void k_legendre_table(const double* __restrict__ mu, double* __restrict__ P,
-                                 double* __restrict__ H, int T, int nh) {
+                                 double* __restrict__ H, double* __restrict__ Pn, int T, int nh) {
   const int jh = blockIdx.x * blockDim.x + threadIdx.x;
   const int m = blockIdx.y;
   if (jh >= nh) return;
@@ -71,6 +73,36 @@ __global__ void k_legendre_table(const double* __restrict__ mu, double* __restri
     vprev = vcur;
     vcur = vnext;
   }
+  Pn[(size_t)m * nh + jh] = vcur;  // P_{T+1}^m
+}
+
+// Divergence and curl of nfv vector fields from the P-sums of their analysis:
+// raw[(2 v) nlme + moff(T+1, m) + k] = sum_j wq_j Pt_n^m(mu_j) A_m(j) and raw[(2 v + 1) nlme + ...]
+// the same of B (n = m + k = m .. T + 1; each degree with the hemispheric sums or differences
+// of its own parity).  Since Ht_n = (n+1) eps_n Pt_{n-1} - n eps_{n+1} Pt_{n+1} (the relation
+// the table kernel builds Ht with), the H-sums are those P-sums of the neighbouring degrees,
+// which pair with the other parity's sums exactly as Ht_n does:
+//   div_n = (i m PA_n - HB_n) / a,  curl_n = (i m PB_n + HA_n) / a,
+//   HX_n = (n+1) eps_n PX_{n-1} - n eps_{n+1} PX_{n+1}   (PX_{m-1} does not enter: eps_m = 0).
+__global__ void k_divcurl_from_p(const double2* __restrict__ raw, double2* __restrict__ dv,
+                                 double2* __restrict__ cu, int T, int nlm, int nlme, double inv_a) {
+  const int m = blockIdx.x, v = blockIdx.y, K = T + 1 - m;
+  const double2* PA = raw + (size_t)(2 * v) * nlme + moff(T + 1, m);
+  const double2* PB = PA + nlme;
+  double2* od = dv + (size_t)v * nlm + moff(T, m);
+  double2* oc = cu + (size_t)v * nlm + moff(T, m);
+  const double fm = (double)m;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const int n = m + k;
+    const double c0 = (n + 1.0) * eps_d(n, m), c1 = (double)n * eps_d(n + 1, m);
+    const double2 a0 = PA[k], b0 = PB[k], ap = PA[k + 1], bp = PB[k + 1];
+    const double2 am = k > 0 ? PA[k - 1] : make_double2(0.0, 0.0);
+    const double2 bm = k > 0 ? PB[k - 1] : make_double2(0.0, 0.0);
+    const double hax = c0 * am.x - c1 * ap.x, hay = c0 * am.y - c1 * ap.y;
+    const double hbx = c0 * bm.x - c1 * bp.x, hby = c0 * bm.y - c1 * bp.y;
+    od[k] = make_double2(inv_a * (-fm * a0.y - hbx), inv_a * (fm * a0.x - hby));
+    oc[k] = make_double2(inv_a * (-fm * b0.y + hax), inv_a * (fm * b0.x + hay));
+  }
 }
 
 // ---- polar bounds (see PolarBounds) ----------------------------------------------------
@@ -96,9 +128,10 @@ __global__ void k_polar_synth(const double* __restrict__ P, const double* __rest
   }
 }
 
-// One warp per (m, 32-degree group): each lane scans the latitudes of its degree.
-__global__ void k_polar_anal(const double* __restrict__ P, const double* __restrict__ H, int T, int nh, double thr,
-                             int ngd, int* __restrict__ ja, int* __restrict__ need) {
+// One warp per (m, 32-degree group): each lane scans the latitudes of its degree; degree index
+// K (n = T + 1, whose P-sums the vector analysis uses) by its row of P alone.
+__global__ void k_polar_anal(const double* __restrict__ P, const double* __restrict__ H, const double* __restrict__ Pn,
+                             int T, int nh, double thr, int ngd, int* __restrict__ ja, int* __restrict__ need) {
   const int g = blockIdx.x, m = blockIdx.y, k = 32 * g + threadIdx.x;
   const int K = T + 1 - m;
   int j = nh;
@@ -107,6 +140,10 @@ __global__ void k_polar_anal(const double* __restrict__ P, const double* __restr
     const double* Hk = H + (size_t)(moff(T, m) + k) * nh;
     for (j = 0; j < nh; ++j)
       if (fabs(Pk[j]) > thr || fabs(Hk[j]) > thr) break;
+  } else if (k == K) {
+    const double* Pk = Pn + (size_t)m * nh;
+    for (j = 0; j < nh; ++j)
+      if (fabs(Pk[j]) > thr) break;
   }
   const unsigned jmin = __reduce_min_sync(0xffffffffu, (unsigned)j);
   const unsigned n = __reduce_add_sync(0xffffffffu, k < K ? (unsigned)(nh - j) : 0u);
@@ -735,6 +772,13 @@ static std::vector<std::complex<double>> fft_twiddle_tables(const FftPlan& fp) {
 }
 
 }  // namespace
+
+void launch_divcurl_from_p(const double2* raw, double2* dv, double2* cu, int nfv, int T, double inv_a, cudaStream_t s) {
+  if (nfv < 1) return;
+  const int nlm = (T + 1) * (T + 2) / 2, nlme = (T + 1) * (T + 4) / 2;
+  k_divcurl_from_p<<<dim3(T + 1, nfv), 128, 0, s>>>(raw, dv, cu, T, nlm, nlme, inv_a);
+}
+
 }  // namespace rexi
 
 using namespace rexi;
@@ -749,6 +793,7 @@ struct sh_plan {
   double* d_wq = nullptr;   // w / (1 - mu^2) [nh]
   double* d_P = nullptr;    // [nlm][nh]
   double* d_H = nullptr;
+  double* d_Pn = nullptr;   // P_{T+1}^m [T+1][nh]
   double2* d_tw = nullptr;  // twiddle tables of the FFT passes (fft_twiddle_tables)
   float2* d_tw32 = nullptr; // the same in FP32, for the FFT of the tensor-core plans
   float4* d_twdf = nullptr; // the same as double-float pairs (re.hi, re.lo, im.hi, im.lo), SH_DF
@@ -821,7 +866,9 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
   cudaError_t e;
   if ((e = cudaMalloc(&p->d_mu, sizeof(double) * p->nh)) || (e = cudaMalloc(&p->d_w, sizeof(double) * p->nh)) ||
       (e = cudaMalloc(&p->d_wq, sizeof(double) * p->nh)) || (e = cudaMalloc(&p->d_P, sizeof(double) * tab)) ||
-      (e = cudaMalloc(&p->d_H, sizeof(double) * tab)) || (e = cudaMalloc(&p->d_tw, sizeof(double2) * ntw)) ||
+      (e = cudaMalloc(&p->d_H, sizeof(double) * tab)) ||
+      (e = cudaMalloc(&p->d_Pn, sizeof(double) * (size_t)(d.T + 1) * p->nh)) ||
+      (e = cudaMalloc(&p->d_tw, sizeof(double2) * ntw)) ||
       (e = cudaMalloc(&p->d_tw32, sizeof(float2) * ntw)) || (e = cudaMalloc(&p->d_twdf, sizeof(float4) * ntw)) ||
       (e = cudaMalloc(&p->d_F, sizeof(double2) * 2 * (size_t)d.max_fields * (d.T + 1) * d.nlat))) {
     cudaGetLastError();
@@ -834,12 +881,13 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
       (e = cudaMemcpy(p->d_tw32, tw32.data(), sizeof(float2) * ntw, cudaMemcpyHostToDevice)) ||
       (e = cudaMemcpy(p->d_twdf, twdf.data(), sizeof(float4) * ntw, cudaMemcpyHostToDevice)))
     return bail(cuda_fail(e, "sh_plan_create: cudaMemcpy"));
-  k_legendre_table<<<dim3((p->nh + 127) / 128, d.T + 1), 128, 0, p->stream>>>(p->d_mu, p->d_P, p->d_H, d.T, p->nh);
+  k_legendre_table<<<dim3((p->nh + 127) / 128, d.T + 1), 128, 0, p->stream>>>(p->d_mu, p->d_P, p->d_H, p->d_Pn, d.T,
+                                                                                p->nh);
   if ((e = cudaGetLastError())) return bail(cuda_fail(e, "k_legendre_table"));
   // polar bounds
   p->polar_thr = d.polar_threshold == 0.0 ? SH_POLAR_THRESHOLD_DEFAULT : d.polar_threshold > 0 ? d.polar_threshold : 0.0;
   {
-    const int ngl = (p->nh + 31) / 32, ngd = (d.T + 1 + 31) / 32;
+    const int ngl = (p->nh + 31) / 32, ngd = (d.T + 2 + 31) / 32;  // degrees to n = T + 1
     const size_t nks = (size_t)(d.T + 1) * ngl, nja = (size_t)(d.T + 1) * ngd;
     p->ks.assign(nks, 0);
     p->ja.assign(nja, 0);
@@ -857,8 +905,8 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
       }
       k_polar_synth<<<dim3(ngl, d.T + 1), 32, 0, p->stream>>>(p->d_P, p->d_H, d.T, p->nh, p->polar_thr, ngl, p->d_ks,
                                                                d_nds);
-      k_polar_anal<<<dim3(ngd, d.T + 1), 32, 0, p->stream>>>(p->d_P, p->d_H, d.T, p->nh, p->polar_thr, ngd, p->d_ja,
-                                                              d_nda);
+      k_polar_anal<<<dim3(ngd, d.T + 1), 32, 0, p->stream>>>(p->d_P, p->d_H, p->d_Pn, d.T, p->nh, p->polar_thr, ngd,
+                                                              p->d_ja, d_nda);
       if (!(e = cudaGetLastError()) && !(e = cudaStreamSynchronize(p->stream)) &&
           !(e = cudaMemcpy(p->ks.data(), p->d_ks, sizeof(int) * nks, cudaMemcpyDeviceToHost)) &&
           !(e = cudaMemcpy(p->ja.data(), p->d_ja, sizeof(int) * nja, cudaMemcpyDeviceToHost)) &&
@@ -893,7 +941,7 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
   }
   if (e) return bail(cuda_fail(e, "cudaFuncSetAttribute(fft)"));
   if (d.precision == SH_DF) {
-    int rc = df_legendre_create(&p->dfl, p->d_P, p->d_H, p->d_w, p->d_wq, d.T, d.nlat, d.max_fields, p->pb,
+    int rc = df_legendre_create(&p->dfl, p->d_P, p->d_H, p->d_Pn, p->d_w, p->d_wq, d.T, d.nlat, d.max_fields, p->pb,
                                 p->stream);
     if (rc) return bail(rc);
     df_legendre_set_prof(p->dfl, &p->prof);
@@ -917,6 +965,7 @@ extern "C" int sh_plan_destroy(sh_plan* p) {
   cudaFree(p->d_wq);
   cudaFree(p->d_P);
   cudaFree(p->d_H);
+  cudaFree(p->d_Pn);
   cudaFree(p->d_tw);
   cudaFree(p->d_tw32);
   cudaFree(p->d_twdf);

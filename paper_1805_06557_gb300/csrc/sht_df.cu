@@ -11,9 +11,11 @@
 // runs in double-float arithmetic as well (sht.cu).
 //
 // Tables (split from the FP64 ones): synthesis [moff(m)+k][nh] (latitude fastest, as the FP64
-// table: threads that own latitudes read coalesced); analysis, per m, [nh][K] with the even
-// degrees k first and the odd ones after them, so that the warps of one parity, which own
-// consecutive degrees, read coalesced.
+// table: threads that own latitudes read coalesced), of P and H; analysis, of P alone, per m
+// [nh][K + 1] over the degrees n = m .. T + 1 with the even degree indices k first and the odd
+// ones after them, so that the warps of one parity, which own consecutive degrees, read
+// coalesced.  The analysis of vector fields takes P-sums only: their H-sums follow from the
+// P-sums of the neighbouring degrees (k_divcurl_from_p), which halves its multiply-adds.
 //
 // One launch contracts NS scalar fields and NV vector pairs against the same table reads; the
 // host runs groups of fields (NS <= 2, NV <= 1 for synthesis; NS, NV <= 2 for analysis).  The
@@ -65,18 +67,19 @@ __device__ __forceinline__ double dsum(const dot2& a, const dot2& b, float sg) {
 __device__ __forceinline__ double dval(const dot2& a) { return (double)a.s + (double)a.err; }
 
 // ---- plan-time splits --------------------------------------------------------------------
-// FP64 table [moff(m)+k][nh] -> synthesis table (same layout) and analysis table (per m [nh][K],
-// even k first); one thread per (m, latitude)
-__global__ void k_df_split_table(const double* __restrict__ src, float2* __restrict__ syn, float2* __restrict__ ana,
-                                 int T, int nh) {
+// FP64 table [moff(m)+k][nh] -> synthesis table (same layout) and, given the next degree's row
+// next [m][nh], the analysis table (per m at moff(T+1, m) nh: [nh][K + 1], even k first); one
+// thread per (m, latitude)
+__global__ void k_df_split_table(const double* __restrict__ src, const double* __restrict__ next,
+                                 float2* __restrict__ syn, float2* __restrict__ ana, int T, int nh) {
   const int m = blockIdx.x, j = blockIdx.y * blockDim.x + threadIdx.x;
   if (j >= nh) return;
-  const int K = T + 1 - m, Ke = (K + 1) / 2;
-  const size_t base = (size_t)moff(T, m) * nh;
-  for (int k = 0; k < K; ++k) {
-    const float2 v = split_df(src[base + (size_t)k * nh + j]);
-    syn[base + (size_t)k * nh + j] = v;
-    ana[base + (size_t)j * K + ((k & 1) ? Ke + (k >> 1) : (k >> 1))] = v;
+  const int K = T + 1 - m, Kx = K + 1, Ke = (Kx + 1) / 2;
+  const size_t base = (size_t)moff(T, m) * nh, abase = (size_t)moff(T + 1, m) * nh + (size_t)j * Kx;
+  for (int k = 0; k < Kx; ++k) {
+    const float2 v = split_df(k < K ? src[base + (size_t)k * nh + j] : next[(size_t)m * nh + j]);
+    if (k < K) syn[base + (size_t)k * nh + j] = v;
+    if (ana) ana[abase + ((k & 1) ? Ke + (k >> 1) : (k >> 1))] = v;
   }
 }
 __global__ void k_df_split_weights(const double* __restrict__ w, const double* __restrict__ wq,
@@ -260,18 +263,15 @@ __global__ void __launch_bounds__(DF_STH, MINB) k_df_synth(const __grid_constant
 
 // ---- analysis -----------------------------------------------------------------------------
 struct DfAnalArgs {
-  const float2* P;      // analysis tables: per m [nh][K], even k first
-  const float2* H;
+  const float2* P;      // analysis table: per m [nh][K + 1], even k first
   const float4* wdf;    // (w.hi, w.lo, wq.hi, wq.lo) [nh]
   const float4* fa;     // split Fourier coefficients: A [NV][T+1][nlat]
   const float4* fb;     // B [NV][T+1][nlat]
   const float4* fg;     // scalar [NS][T+1][nlat]
-  double2* dv;          // [NV][nlm]
-  double2* cu;
+  double2* raw;         // P-sums of A and B: [NV][2][nlme], degree index k at moff(T+1, m) + k
   double2* spec;        // [NS][nlm]
   const int* ja;        // polar bounds: first latitude per (m, 32-degree group) [T+1][ngd]
-  int T, nlat, nh, nlm, ngd;
-  double inv_a;
+  int T, nlat, nh, nlm, nlme, ngd;
 };
 
 __device__ __forceinline__ float4 dfc_pack(df re, df im) { return make_float4(re.hi, im.hi, re.lo, im.lo); }
@@ -283,47 +283,44 @@ __device__ __forceinline__ float4 df_wsum(df w, float4 n, float4 s, float sg) {
   return dfc_pack(re, im);
 }
 
-// latitude j of one degree: the table entries p, h against the staged sums (sP, sH select the
-// sum or the difference array for P and H)
+// latitude j of one degree: the table entry p against the staged sums (sP selects the sum or
+// the difference array of the degree's parity)
 template <int NS, int NV>
-__device__ __forceinline__ void df_anal_step(float2 pv, float2 hv, const float4* sm4, int nh, int j, int sP, int sH,
-                                             dot2c (&S)[NS > 0 ? NS : 1], dot2c (&V)[NV > 0 ? NV : 1][4]) {
+__device__ __forceinline__ void df_anal_step(float2 pv, const float4* sm4, int nh, int j, int sP,
+                                             dot2c (&S)[NS > 0 ? NS : 1], dot2c (&V)[NV > 0 ? NV : 1][2]) {
   const df p = df_of(pv);
 #pragma unroll
   for (int f = 0; f < NS; ++f) madd(S[f], p, sm4[(4 * NV + 2 * f + sP) * nh + j]);
-  if (NV > 0) {
-    const df h = df_of(hv);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      madd(V[v][0], p, sm4[(4 * v + 0 + sP) * nh + j]);  // P.A
-      madd(V[v][1], p, sm4[(4 * v + 2 + sP) * nh + j]);  // P.B
-      madd(V[v][2], h, sm4[(4 * v + 0 + sH) * nh + j]);  // H.A
-      madd(V[v][3], h, sm4[(4 * v + 2 + sH) * nh + j]);  // H.B
-    }
+  for (int v = 0; v < NV; ++v) {
+    madd(V[v][0], p, sm4[(4 * v + 0 + sP) * nh + j]);  // P.A
+    madd(V[v][1], p, sm4[(4 * v + 2 + sP) * nh + j]);  // P.B
   }
 }
 
 // Block (m, tile): shared memory holds, per northern latitude j, the weighted hemispheric sums
 // and differences of every field (vector pair v: A+, A-, B+, B- with w / (1 - mu^2); scalar f:
-// G+, G- with w); warps 0-1 own the even degrees k = 128 tile + 2 i, warps 2-3 the odd ones,
-// and each thread streams its table column over the latitudes, DF_PF latitudes of table entries
-// in flight, from the first latitude that the 64 degrees of its warp's span need (polar
-// bounds).  P pairs with the sums for even k and the differences for odd k, H the other way
-// round.
+// G+, G- with w); warps 0-1 own the even degree indices k = 128 tile + 2 i, warps 2-3 the odd
+// ones, and each thread streams its table column over the latitudes, DF_PF latitudes of table
+// entries in flight, from the first latitude that the 64 degrees of its warp's span need
+// (polar bounds).  P pairs with the sums for even k and the differences for odd k.  Scalar
+// fields give their spectra (k < K); vector fields give the P-sums of A and B (k <= K, n up to
+// T + 1), from which k_divcurl_from_p forms divergence and curl.
 template <int NS, int NV>
 __global__ void __launch_bounds__(DF_ATH, 4) k_df_anal(const __grid_constant__ DfAnalArgs a) {
   extern __shared__ float4 sm4[];
   const int m = blockIdx.x, tile = blockIdx.y;
   const int T = a.T, K = T + 1 - m, nh = a.nh, nlat = a.nlat;
-  if (tile * DF_ATH >= K) return;  // uniform over the block
-  const int base = moff(T, m);
+  const int Kx = K + 1;                   // table rows of m (degrees to n = T + 1)
+  const int Kl = NV > 0 ? Kx : K;         // degree indices this launch needs
+  if (tile * DF_ATH >= Kl) return;  // uniform over the block
   const int par = threadIdx.x >= DF_ATH / 2;  // uniform over each warp
   const int idx = threadIdx.x & (DF_ATH / 2 - 1);
   const int k = tile * DF_ATH + 2 * idx + par;
   // first latitude: warp w spans the degree indices tile 128 + 64 (w & 1) .. + 63, bound groups
   // g0 and g0 + 1; requested before the staging, whose time hides its latency
   int jb = nh;
-  if (k < K) {
+  if (k < Kl) {
     const int g0 = tile * (DF_ATH / 32) + 2 * ((threadIdx.x >> 5) & 1);
     const int* jam = a.ja + m * a.ngd;
     jb = min(__ldg(jam + g0), g0 + 1 < a.ngd ? __ldg(jam + g0 + 1) : nh);  // warp-uniform
@@ -352,61 +349,48 @@ __global__ void __launch_bounds__(DF_ATH, 4) k_df_anal(const __grid_constant__ D
     }
   }
   __syncthreads();
-  if (k >= K) return;  // no barrier below
-  const int Ke = (K + 1) / 2;
-  const size_t col = (size_t)base * nh + (par ? Ke : 0) + tile * (DF_ATH / 2) + idx;
+  if (k >= Kl) return;  // no barrier below
+  const int Ke = (Kx + 1) / 2;
+  const size_t col = (size_t)moff(T + 1, m) * nh + (par ? Ke : 0) + tile * (DF_ATH / 2) + idx;
   const float2* Pc = a.P + col;
-  const float2* Hc = a.H + col;
-  // P meets (N + S) for even k, (N - S) for odd k; H the other one
-  const int sP = par, sH = 1 - par;
+  const int sP = par;  // P meets (N + S) for even k, (N - S) for odd k
   const float2 z2 = make_float2(0.f, 0.f);
   dot2c S[NS > 0 ? NS : 1];
-  dot2c V[NV > 0 ? NV : 1][4];  // [0] P.A, [1] P.B, [2] H.A, [3] H.B
+  dot2c V[NV > 0 ? NV : 1][2];  // [0] P.A, [1] P.B
 #pragma unroll
   for (int f = 0; f < (NS > 0 ? NS : 1); ++f) S[f] = dot2c{z2, z2};
 #pragma unroll
-  for (int v = 0; v < (NV > 0 ? NV : 1); ++v)
+  for (int v = 0; v < (NV > 0 ? NV : 1); ++v) V[v][0] = V[v][1] = dot2c{z2, z2};
+  float2 pb[DF_PF];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) V[v][q] = dot2c{z2, z2};
-  float2 pb[DF_PF], hb[DF_PF];
-#pragma unroll
-  for (int u = 0; u < DF_PF; ++u) {
-    pb[u] = jb + u < nh ? __ldg(Pc + (size_t)(jb + u) * K) : z2;
-    hb[u] = (NV > 0 && jb + u < nh) ? __ldg(Hc + (size_t)(jb + u) * K) : z2;
-  }
+  for (int u = 0; u < DF_PF; ++u) pb[u] = jb + u < nh ? __ldg(Pc + (size_t)(jb + u) * Kx) : z2;
   for (int j0 = jb; j0 < nh; j0 += DF_PF) {
-    float2 pn[DF_PF], hn[DF_PF];
+    float2 pn[DF_PF];
 #pragma unroll
     for (int u = 0; u < DF_PF; ++u) {
       const int jj = j0 + DF_PF + u;
-      pn[u] = jj < nh ? __ldg(Pc + (size_t)jj * K) : z2;
-      hn[u] = (NV > 0 && jj < nh) ? __ldg(Hc + (size_t)jj * K) : z2;
+      pn[u] = jj < nh ? __ldg(Pc + (size_t)jj * Kx) : z2;
     }
 #pragma unroll
     for (int u = 0; u < DF_PF; ++u) {
       const int j = j0 + u;
       if (j >= nh) break;
-      df_anal_step<NS, NV>(pb[u], hb[u], sm4, nh, j, sP, sH, S, V);
+      df_anal_step<NS, NV>(pb[u], sm4, nh, j, sP, S, V);
     }
 #pragma unroll
-    for (int u = 0; u < DF_PF; ++u) {
-      pb[u] = pn[u];
-      hb[u] = hn[u];
-    }
+    for (int u = 0; u < DF_PF; ++u) pb[u] = pn[u];
   }
-  const size_t i = (size_t)base + k;
+  if (k < K) {
+    const size_t i = (size_t)moff(T, m) + k;
 #pragma unroll
-  for (int f = 0; f < NS; ++f) a.spec[(size_t)f * a.nlm + i] = make_double2(dval(dot2c_re(S[f])), dval(dot2c_im(S[f])));
+    for (int f = 0; f < NS; ++f)
+      a.spec[(size_t)f * a.nlm + i] = make_double2(dval(dot2c_re(S[f])), dval(dot2c_im(S[f])));
+  }
+  const size_t ie = (size_t)moff(T + 1, m) + k;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    const double fm = (double)m, ia = a.inv_a;
-    const double PAr = dval(dot2c_re(V[v][0])), PAi = dval(dot2c_im(V[v][0]));
-    const double PBr = dval(dot2c_re(V[v][1])), PBi = dval(dot2c_im(V[v][1]));
-    const double HAr = dval(dot2c_re(V[v][2])), HAi = dval(dot2c_im(V[v][2]));
-    const double HBr = dval(dot2c_re(V[v][3])), HBi = dval(dot2c_im(V[v][3]));
-    // div = (i m P.A - H.B) / a, curl = (i m P.B + H.A) / a
-    a.dv[(size_t)v * a.nlm + i] = make_double2(ia * (-fm * PAi - HBr), ia * (fm * PAr - HBi));
-    a.cu[(size_t)v * a.nlm + i] = make_double2(ia * (-fm * PBi + HAr), ia * (fm * PBr + HAi));
+    a.raw[(size_t)(2 * v) * a.nlme + ie] = make_double2(dval(dot2c_re(V[v][0])), dval(dot2c_im(V[v][0])));
+    a.raw[(size_t)(2 * v + 1) * a.nlme + ie] = make_double2(dval(dot2c_re(V[v][1])), dval(dot2c_im(V[v][1])));
   }
 }
 
@@ -424,9 +408,10 @@ size_t df_anal_smem(int nh) {
 struct DfLegendre {
   int T = 0, nlat = 0, nh = 0, nlm = 0, max_fields = 0, nsm = 0;
   PolarBounds pb;
-  float2 *Ps = nullptr, *Hs = nullptr, *Pa = nullptr, *Ha = nullptr;
+  float2 *Ps = nullptr, *Hs = nullptr, *Pa = nullptr;  // synthesis P, H; analysis P (to n = T + 1)
   float4* wdf = nullptr;
   float4* in = nullptr;  // split inputs of one call: [2 max_fields][max(nlm, (T+1) nlat)]
+  double2* raw = nullptr;  // P-sums of the vector fields of one call: [2 max_fields][2][nlme]
   StageProf* prof = nullptr;
 };
 
@@ -450,8 +435,8 @@ static int df_smem_attr(int nh, int T) {
   return e ? cuda_fail(e, "cudaFuncSetAttribute(k_df_*)") : REXI_OK;
 }
 
-int df_legendre_create(DfLegendre** out, const double* P, const double* H, const double* w, const double* wq, int T,
-                       int nlat, int max_fields, const PolarBounds& pb, cudaStream_t stream) {
+int df_legendre_create(DfLegendre** out, const double* P, const double* H, const double* Pn, const double* w,
+                       const double* wq, int T, int nlat, int max_fields, const PolarBounds& pb, cudaStream_t stream) {
   *out = nullptr;
   const int nh = nlat / 2;
   if (df_anal_smem<2, 2>(nh) > 200 * 1024)  // 12 staged arrays of nh float4
@@ -471,16 +456,18 @@ int df_legendre_create(DfLegendre** out, const double* P, const double* H, const
   const size_t tab = (size_t)t->nlm * nh;
   const size_t per = std::max<size_t>(t->nlm, (size_t)(T + 1) * nlat);
   cudaError_t e;
+  const size_t tabx = (size_t)nlm_ext(T) * nh;
   if ((e = cudaMalloc(&t->Ps, sizeof(float2) * tab)) || (e = cudaMalloc(&t->Hs, sizeof(float2) * tab)) ||
-      (e = cudaMalloc(&t->Pa, sizeof(float2) * tab)) || (e = cudaMalloc(&t->Ha, sizeof(float2) * tab)) ||
+      (e = cudaMalloc(&t->Pa, sizeof(float2) * tabx)) ||
+      (e = cudaMalloc(&t->raw, sizeof(double2) * 2 * 2 * (size_t)max_fields * nlm_ext(T))) ||
       (e = cudaMalloc(&t->wdf, sizeof(float4) * nh)) ||
       (e = cudaMalloc(&t->in, sizeof(float4) * per * 2 * (size_t)max_fields))) {
     cudaGetLastError();
     df_legendre_destroy(t);
     return fail(REXI_ENOMEM, "double-float Legendre tables: cudaMalloc failed: %s", cudaGetErrorString(e));
   }
-  k_df_split_table<<<dim3(T + 1, (nh + 127) / 128), 128, 0, stream>>>(P, t->Ps, t->Pa, T, nh);
-  k_df_split_table<<<dim3(T + 1, (nh + 127) / 128), 128, 0, stream>>>(H, t->Hs, t->Ha, T, nh);
+  k_df_split_table<<<dim3(T + 1, (nh + 127) / 128), 128, 0, stream>>>(P, Pn, t->Ps, t->Pa, T, nh);
+  k_df_split_table<<<dim3(T + 1, (nh + 127) / 128), 128, 0, stream>>>(H, Pn, t->Hs, nullptr, T, nh);
   k_df_split_weights<<<(nh + 127) / 128, 128, 0, stream>>>(w, wq, t->wdf, nh);
   int rc = REXI_OK;
   if ((e = cudaGetLastError())) rc = cuda_fail(e, "double-float table kernels");
@@ -495,7 +482,7 @@ int df_legendre_create(DfLegendre** out, const double* P, const double* H, const
 
 void df_legendre_destroy(DfLegendre* t) {
   if (!t) return;
-  for (void* p : {(void*)t->Ps, (void*)t->Hs, (void*)t->Pa, (void*)t->Ha, (void*)t->wdf, (void*)t->in}) cudaFree(p);
+  for (void* p : {(void*)t->Ps, (void*)t->Hs, (void*)t->Pa, (void*)t->wdf, (void*)t->in, (void*)t->raw}) cudaFree(p);
   delete t;
 }
 
@@ -505,7 +492,7 @@ void df_legendre_streamed(const DfLegendre* t, long long* syn, long long* ana) {
   for (int m = 0; m <= T; ++m) {
     const int K = T + 1 - m;
     for (int g = 0; g < ngl; ++g) s += (long long)std::min(32, nh - 32 * g) * (K - (t->pb.ks[m * ngl + g] & ~1));
-    for (int g = 0; 32 * g < K; g += 2) {  // one warp pair per 64-degree span
+    for (int g = 0; 32 * g < K; g += 2) {  // one warp pair per 64-degree span (entries of n <= T)
       const int jb = std::min(t->pb.ja[m * ngd + g], g + 1 < ngd ? t->pb.ja[m * ngd + g + 1] : nh);
       a += (long long)std::min(64, K - 32 * g) * (nh - jb);
     }
@@ -585,7 +572,8 @@ int df_leg_synth(DfLegendre* t, const double2* spec, double2* F, int nfs, const 
 
 template <int NS, int NV>
 static void launch_anal(DfLegendre* t, DfAnalArgs a, cudaStream_t s) {
-  k_df_anal<NS, NV><<<dim3(t->T + 1, (t->T + DF_ATH) / DF_ATH), DF_ATH, df_anal_smem<NS, NV>(t->nh), s>>>(a);
+  // degree tiles over n = m .. T + 1 (vector fields need n = T + 1)
+  k_df_anal<NS, NV><<<dim3(t->T + 1, (t->T + 1 + DF_ATH) / DF_ATH), DF_ATH, df_anal_smem<NS, NV>(t->nh), s>>>(a);
 }
 
 int df_leg_anal(DfLegendre* t, const double2* FA, const double2* FB, double2* dv, double2* cu, int nfv,
@@ -596,13 +584,12 @@ int df_leg_anal(DfLegendre* t, const double2* FA, const double2* FB, double2* dv
   split_inputs(t, FA, nfv * fo, FB, nfv * fo, F, nfs * fo, s);
   DfAnalArgs a{};
   a.P = t->Pa;
-  a.H = t->Ha;
   a.wdf = t->wdf;
   a.T = t->T;
   a.nlat = t->nlat;
   a.nh = t->nh;
   a.nlm = t->nlm;
-  a.inv_a = inv_a;
+  a.nlme = nlm_ext(t->T);
   a.ja = t->pb.d_ja;
   a.ngd = t->pb.ngd;
   const float4* fa = t->in;
@@ -614,8 +601,7 @@ int df_leg_anal(DfLegendre* t, const double2* FA, const double2* FB, double2* dv
     a.fa = fa + fv * fo;
     a.fb = fb + fv * fo;
     a.fg = fg + fs * fo;
-    a.dv = dv ? dv + (size_t)fv * t->nlm : nullptr;
-    a.cu = cu ? cu + (size_t)fv * t->nlm : nullptr;
+    a.raw = t->raw + (size_t)(2 * fv) * a.nlme;
     a.spec = spec ? spec + (size_t)fs * t->nlm : nullptr;
 #define DF_CASE(NS, NV) \
   else if (ns == NS && nv == NV) launch_anal<NS, NV>(t, a, s);
@@ -626,6 +612,7 @@ int df_leg_anal(DfLegendre* t, const double2* FA, const double2* FB, double2* dv
     fs += ns;
     fv += nv;
   }
+  launch_divcurl_from_p(t->raw, dv, cu, nfv, t->T, inv_a, s);
   if (t->prof) t->prof->end(ph);
   cudaError_t e = cudaGetLastError();
   return e ? cuda_fail(e, "k_df_anal launch") : REXI_OK;

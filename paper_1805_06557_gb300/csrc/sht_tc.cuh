@@ -77,7 +77,9 @@ struct StageProf {
 //     magnitude at one of the northern latitudes 32 g .. 32 g + 31 (T + 1 - m if nowhere):
 //     the synthesis of those latitudes starts there;
 //   ja[m * ngd + g]: first northern latitude at which P or H of one of the degree indices
-//     k = 32 g .. 32 g + 31 exceeds it (nh if nowhere): their analysis starts there.
+//     k = 32 g .. 32 g + 31 exceeds it (nh if nowhere): their analysis starts there.  The
+//     groups reach degree index K = T + 1 - m (n = T + 1, judged by P alone), whose P-sums the
+//     vector analysis uses (ngd = ceil((T + 2) / 32)).
 // Every skipped entry is below the threshold.  With the truncation off, every start is 0.
 struct PolarBounds {
   int ngl = 0, ngd = 0;        // groups of 32 latitudes, of 32 degrees
@@ -86,6 +88,12 @@ struct PolarBounds {
   const int* ks = nullptr;     // host copies
   const int* ja = nullptr;
 };
+
+// Divergence and curl of nfv vector fields [nfv][nlm] from the raw P-sums of their analysis,
+// raw[(2 v + {0: A, 1: B}) nlme + moff(T+1, m) + k] for n = m + k = m .. T + 1,
+// nlme = (T+1)(T+4)/2 (sht.cu, k_divcurl_from_p)
+void launch_divcurl_from_p(const double2* raw, double2* dv, double2* cu, int nfv, int T, double inv_a, cudaStream_t s);
+inline int nlm_ext(int T) { return (T + 1) * (T + 4) / 2; }
 
 struct TcLegendre;
 // stage timer of the owning plan (may be null)
