@@ -493,7 +493,11 @@ def sh_transforms(torch, rexi, fp64_peak, fp32_peak, T=511, nlat=768, nlon=1536,
             total = e0.elapsed_time(e1) / reps
             vec = kind in ("synthesis_uv", "analysis_divcurl")
             mixed = kind.endswith("_mixed")
-            ntab = 2 if (vec or mixed) else 1   # P, or P and H
+            # tables the method reads: P, or P and H for vector fields -- except the FP64 and
+            # double-float analyses, whose vector fields take P-sums only (H-sums from the
+            # neighbouring degrees' P-sums)
+            p_only = kind.startswith("analysis") and prec in ("fp64", "df")
+            ntab = 2 if (vec or mixed) and not p_only else 1
             need = use["needed_synth" if kind.startswith("synthesis") else "needed_anal"]
             # spectral arrays = Fourier arrays = grids: scalar fields + 2 per vector pair
             narr = 2 if vec else (4 if kind == "synthesis_mixed" else 5 if mixed else nf)
@@ -503,8 +507,11 @@ def sh_transforms(torch, rexi, fp64_peak, fp32_peak, T=511, nlat=768, nlon=1536,
             leg_bytes = tab_bytes + narr * (nlm + (T + 1) * nlat) * 16
             fft_ms = prof["fft"][0] / reps
             fft_bytes = narr * (nlat * nlon * 8 + nlat * (T + 1) * 16)
-            # FMA = 2; complex coefficient x real table; vector arrays meet P and H, scalar ones P
+            # FMA = 2; complex coefficient x real table; vector arrays meet P and H (P alone in the
+            # FP64 and double-float analyses), scalar ones P
             nvec_arr = 2 if kind == "synthesis_mixed" else 4 if kind == "analysis_mixed" else (narr if vec else 0)
+            if p_only:
+                nvec_arr = 0
             leg_flops = 4.0 * need * (2 * nvec_arr + (narr - nvec_arr))
             if prec == "fp64":   # FP64 CUDA-core contraction: bound by the FP64 pipe on this GPU
                 leg_roof = {"bound": "alu", "pipe": "fp64", "kernel": "k_leg_*", "algorithmic_flops": leg_flops,

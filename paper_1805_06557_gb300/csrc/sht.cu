@@ -299,15 +299,17 @@ __global__ void __launch_bounds__(ATH) k_leg_anal(const double* __restrict__ P,
   }
 }
 
+// P-sums of a vector field's A and B for the degrees n = m .. T + 1 (raw layout of
+// k_divcurl_from_p, which forms divergence and curl from them): one thread per degree, each
+// sum with the hemispheric sums or differences of its own parity; the row of n = T + 1 is Pn.
+// Two FP64 FMA pairs per table entry instead of four with the H table.
 __global__ void __launch_bounds__(ATH) k_leg_anal_divcurl(const double* __restrict__ P,
-                                                          const double* __restrict__ H,
+                                                          const double* __restrict__ Pn,
                                                           const double* __restrict__ wq,
                                                           const double2* __restrict__ FA,
                                                           const double2* __restrict__ FB,
-                                                          double2* __restrict__ dv,
-                                                          double2* __restrict__ cu, int T, int nlat,
-                                                          int nlm, double inv_a, const int* __restrict__ ja,
-                                                          int ngd) {
+                                                          double2* __restrict__ raw, int T, int nlat,
+                                                          int nlme, const int* __restrict__ ja, int ngd) {
   extern __shared__ double2 sm2[];
   const int m = blockIdx.x, f = blockIdx.y;
   const int nh = nlat / 2;
@@ -328,45 +330,37 @@ __global__ void __launch_bounds__(ATH) k_leg_anal_divcurl(const double* __restri
   __syncthreads();
   // one thread per degree (see k_leg_anal)
   const int K = T + 1 - m, base = moff(T, m);
-  for (int k = threadIdx.x; k < K; k += ATH) {
-    const double* Pk = P + (size_t)(base + k) * nh;
-    const double* Hk = H + (size_t)(base + k) * nh;
+  double2* oA = raw + (size_t)(2 * f) * nlme + moff(T + 1, m);
+  double2* oB = oA + nlme;
+  for (int k = threadIdx.x; k <= K; k += ATH) {
+    const double* Pk = k < K ? P + (size_t)(base + k) * nh : Pn + (size_t)m * nh;
     const bool odd = k & 1;
     const int jb = __ldg(ja + m * ngd + (k >> 5));
-    // P terms pair with (north + s south), H terms with (north - s south), s = (-1)^k
+    // P terms pair with (north + s south), s = (-1)^k
     const double2* AP = odd ? Am : Ap;
     const double2* BP = odd ? Bm : Bp;
-    const double2* AH = odd ? Ap : Am;
-    const double2* BH = odd ? Bp : Bm;
-    double2 sPA = make_double2(0, 0), sPB = sPA, sHA = sPA, sHB = sPA;
-    auto step = [&](double p, double h, int j) {
-      const double2 ap = AP[j], bp = BP[j], ah = AH[j], bh = BH[j];
+    double2 sPA = make_double2(0, 0), sPB = sPA;
+    auto step = [&](double p, int j) {
+      const double2 ap = AP[j], bp = BP[j];
       sPA.x = fma(p, ap.x, sPA.x);
       sPA.y = fma(p, ap.y, sPA.y);
       sPB.x = fma(p, bp.x, sPB.x);
       sPB.y = fma(p, bp.y, sPB.y);
-      sHA.x = fma(h, ah.x, sHA.x);
-      sHA.y = fma(h, ah.y, sHA.y);
-      sHB.x = fma(h, bh.x, sHB.x);
-      sHB.y = fma(h, bh.y, sHB.y);
     };
     if ((nh & 3) == 0) {
       const double2* P2 = reinterpret_cast<const double2*>(Pk);
-      const double2* H2 = reinterpret_cast<const double2*>(Hk);
       for (int j4 = jb >> 2; j4 < nh / 4; ++j4) {
         const double2 pa = __ldg(P2 + 2 * j4), pb = __ldg(P2 + 2 * j4 + 1);
-        const double2 ha = __ldg(H2 + 2 * j4), hb = __ldg(H2 + 2 * j4 + 1);
-        step(pa.x, ha.x, 4 * j4);
-        step(pa.y, ha.y, 4 * j4 + 1);
-        step(pb.x, hb.x, 4 * j4 + 2);
-        step(pb.y, hb.y, 4 * j4 + 3);
+        step(pa.x, 4 * j4);
+        step(pa.y, 4 * j4 + 1);
+        step(pb.x, 4 * j4 + 2);
+        step(pb.y, 4 * j4 + 3);
       }
     } else {
-      for (int j = jb; j < nh; ++j) step(__ldg(Pk + j), __ldg(Hk + j), j);
+      for (int j = jb; j < nh; ++j) step(__ldg(Pk + j), j);
     }
-    const double2 iPA = imul(m, sPA), iPB = imul(m, sPB);
-    dv[(size_t)f * nlm + base + k] = make_double2(inv_a * (iPA.x - sHB.x), inv_a * (iPA.y - sHB.y));
-    cu[(size_t)f * nlm + base + k] = make_double2(inv_a * (iPB.x + sHA.x), inv_a * (iPB.y + sHA.y));
+    oA[k] = sPA;
+    oB[k] = sPB;
   }
 }
 
@@ -794,6 +788,7 @@ struct sh_plan {
   double* d_P = nullptr;    // [nlm][nh]
   double* d_H = nullptr;
   double* d_Pn = nullptr;   // P_{T+1}^m [T+1][nh]
+  double2* d_raw = nullptr; // P-sums of the FP64 vector analysis [max_fields][2][nlme]
   double2* d_tw = nullptr;  // twiddle tables of the FFT passes (fft_twiddle_tables)
   float2* d_tw32 = nullptr; // the same in FP32, for the FFT of the tensor-core plans
   float4* d_twdf = nullptr; // the same as double-float pairs (re.hi, re.lo, im.hi, im.lo), SH_DF
@@ -868,6 +863,8 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
       (e = cudaMalloc(&p->d_wq, sizeof(double) * p->nh)) || (e = cudaMalloc(&p->d_P, sizeof(double) * tab)) ||
       (e = cudaMalloc(&p->d_H, sizeof(double) * tab)) ||
       (e = cudaMalloc(&p->d_Pn, sizeof(double) * (size_t)(d.T + 1) * p->nh)) ||
+      (d.precision == SH_FP64 &&
+       (e = cudaMalloc(&p->d_raw, sizeof(double2) * 2 * (size_t)d.max_fields * nlm_ext(d.T)))) ||
       (e = cudaMalloc(&p->d_tw, sizeof(double2) * ntw)) ||
       (e = cudaMalloc(&p->d_tw32, sizeof(float2) * ntw)) || (e = cudaMalloc(&p->d_twdf, sizeof(float4) * ntw)) ||
       (e = cudaMalloc(&p->d_F, sizeof(double2) * 2 * (size_t)d.max_fields * (d.T + 1) * d.nlat))) {
@@ -966,6 +963,7 @@ extern "C" int sh_plan_destroy(sh_plan* p) {
   cudaFree(p->d_P);
   cudaFree(p->d_H);
   cudaFree(p->d_Pn);
+  cudaFree(p->d_raw);
   cudaFree(p->d_tw);
   cudaFree(p->d_tw32);
   cudaFree(p->d_twdf);
@@ -1068,7 +1066,8 @@ static int leg_anal_divcurl(sh_plan* p, const double2* FA, const double2* FB, do
   if (p->dfl) return df_leg_anal(p->dfl, FA, FB, dv, cu, nf, nullptr, nullptr, 0, 1.0 / p->d.radius, p->stream);
   const int ph = p->prof.begin(0);
   k_leg_anal_divcurl<<<dim3(p->d.T + 1, nf), ATH, sizeof(double2) * 4 * p->nh, p->stream>>>(
-      p->d_P, p->d_H, p->d_wq, FA, FB, dv, cu, p->d.T, p->d.nlat, p->nlm, 1.0 / p->d.radius, p->d_ja, p->pb.ngd);
+      p->d_P, p->d_Pn, p->d_wq, FA, FB, p->d_raw, p->d.T, p->d.nlat, nlm_ext(p->d.T), p->d_ja, p->pb.ngd);
+  launch_divcurl_from_p(p->d_raw, dv, cu, nf, p->d.T, 1.0 / p->d.radius, p->stream);
   p->prof.end(ph);
   return REXI_OK;
 }
