@@ -161,16 +161,20 @@ __global__ void k_polar_anal(const double* __restrict__ P, const double* __restr
 // the first blocks launched finish last).
 constexpr int LTH = 128;
 
-__global__ void __launch_bounds__(LTH) k_leg_synth(const double* __restrict__ P,
-                                                   const double2* __restrict__ spec,
-                                                   double2* __restrict__ F, int T, int nlat, int nlm,
-                                                   const int* __restrict__ ks, int ngl) {
+// Scalar fields: coefficients spec [f][cstride] at moff(T, m), degrees n = m .. T (Pn null).
+// With Pn given, the coefficients run to n = T + 1 at moff(T + 1, m) (the vector syntheses'
+// u and v, below) and the row of n = T + 1 is Pn [m][nh].  Field f < nsplit goes to F, the
+// others to F2 (field f - nsplit).
+__global__ void __launch_bounds__(LTH) k_leg_synth(const double* __restrict__ P, const double* __restrict__ Pn,
+                                                   const double2* __restrict__ spec, double2* __restrict__ F,
+                                                   double2* __restrict__ F2, int nsplit, int T, int nlat,
+                                                   int cstride, const int* __restrict__ ks, int ngl) {
   const int m = blockIdx.x, f = blockIdx.y;
   const int nh = nlat / 2;
   const int jh = (gridDim.z - 1 - blockIdx.z) * LTH + threadIdx.x;
   if (jh >= nh) return;
   const int K = T + 1 - m, base = moff(T, m);
-  const double2* c = spec + (size_t)f * nlm + base;
+  const double2* c = spec + (size_t)f * cstride + (Pn ? moff(T + 1, m) : base);
   const double* Pm = P + (size_t)base * nh + jh;
   double2 e = make_double2(0, 0), o = make_double2(0, 0);
   int k = __ldg(ks + m * ngl + (jh >> 5)) & ~1;
@@ -187,59 +191,45 @@ __global__ void __launch_bounds__(LTH) k_leg_synth(const double* __restrict__ P,
     e.x = fma(pe, c[k].x, e.x);
     e.y = fma(pe, c[k].y, e.y);
   }
-  double2* out = F + ((size_t)f * (T + 1) + m) * nlat;
+  if (Pn) {  // n = T + 1, degree index K
+    const double pn = Pn[(size_t)m * nh + jh];
+    const double2 cn = c[K];
+    double2& acc = (K & 1) ? o : e;
+    acc.x = fma(pn, cn.x, acc.x);
+    acc.y = fma(pn, cn.y, acc.y);
+  }
+  double2* out = (f < nsplit ? F + ((size_t)f * (T + 1) + m) * nlat : F2 + ((size_t)(f - nsplit) * (T + 1) + m) * nlat);
   out[jh] = make_double2(e.x + o.x, e.y + o.y);
   out[nlat - 1 - jh] = make_double2(e.x - o.x, e.y - o.y);
 }
 
-__device__ __forceinline__ double2 imul(int m, double2 v) { return make_double2(-m * v.y, m * v.x); }
-
-__global__ void __launch_bounds__(LTH) k_leg_synth_uv(const double* __restrict__ P,
-                                                      const double* __restrict__ H,
-                                                      const double2* __restrict__ psi,
-                                                      const double2* __restrict__ chi,
-                                                      double2* __restrict__ FU, double2* __restrict__ FV,
-                                                      int T, int nlat, int nlm, double inv_a,
-                                                      const int* __restrict__ ks, int ngl) {
-  const int m = blockIdx.x, f = blockIdx.y;
-  const int nh = nlat / 2;
-  const int jh = (gridDim.z - 1 - blockIdx.z) * LTH + threadIdx.x;  // equator first
-  if (jh >= nh) return;
-  const int K = T + 1 - m, base = moff(T, m);
-  const double2* cp = psi + (size_t)f * nlm + base;
-  const double2* cc = chi + (size_t)f * nlm + base;
-  const double* Pm = P + (size_t)base * nh + jh;
-  const double* Hm = H + (size_t)base * nh + jh;
-  // [0] even k, [1] odd k
-  double2 pps[2] = {}, pch[2] = {}, hps[2] = {}, hch[2] = {};
-  for (int k = __ldg(ks + m * ngl + (jh >> 5)); k < K; ++k) {
-    const int par = k & 1;
-    const double p = Pm[(size_t)k * nh], h = Hm[(size_t)k * nh];
-    const double2 a = cp[k], b = cc[k];
-    pps[par].x = fma(p, a.x, pps[par].x);
-    pps[par].y = fma(p, a.y, pps[par].y);
-    pch[par].x = fma(p, b.x, pch[par].x);
-    pch[par].y = fma(p, b.y, pch[par].y);
-    hps[par].x = fma(h, a.x, hps[par].x);
-    hps[par].y = fma(h, a.y, hps[par].y);
-    hch[par].x = fma(h, b.x, hch[par].x);
-    hch[par].y = fma(h, b.y, hch[par].y);
-  }
-  double2* outU = FU + ((size_t)f * (T + 1) + m) * nlat;
-  double2* outV = FV + ((size_t)f * (T + 1) + m) * nlat;
-  for (int hemi = 0; hemi < 2; ++hemi) {
-    // north: P sums e + o, H sums e + o; south: P sums e - o, H sums -(e - o)
-    const double sp = hemi ? -1.0 : 1.0;
-    const double sh = hemi ? -1.0 : 1.0;
-    auto comb = [&](const double2* v, double s_odd, double s_all) {
-      return make_double2(s_all * (v[0].x + s_odd * v[1].x), s_all * (v[0].y + s_odd * v[1].y));
-    };
-    const double2 Pps = comb(pps, sp, 1.0), Pch = comb(pch, sp, 1.0);
-    const double2 Hps = comb(hps, sp, sh), Hch = comb(hch, sp, sh);
-    const double2 ich = imul(m, Pch), ips = imul(m, Pps);
-    const int j = hemi ? nlat - 1 - jh : jh;
-    outU[j] = make_double2(inv_a * (-Hps.x + ich.x), inv_a * (-Hps.y + ich.y));
-    outV[j] = make_double2(inv_a * (ips.x + Hch.x), inv_a * (ips.y + Hch.y));
+// Spectra of the velocity components of nf (psi, chi) pairs for n = m .. T + 1 (layout of
+// moff(T + 1, m), [f][nlme]): U = (1/a)(-H psi + i m P chi) and V = (1/a)(i m P psi + H chi)
+// with Ht_n = (n+1) eps_n Pt_{n-1} - n eps_{n+1} Pt_{n+1} become P-sums,
+//   U = sum_p Pt_p u_p,  u_p = (-psi'_p + i m chi_p) / a,
+//   V = sum_p Pt_p v_p,  v_p = (i m psi_p + chi'_p) / a,
+//   x'_p = (p + 2) eps_{p+1} x_{p+1} - (p - 1) eps_p x_{p-1}   (x_{T+1} = x_{m-1} = 0),
+// so a vector synthesis is two scalar ones over one table (the combinations in FP64, before any
+// rounding of a transform).
+__global__ void k_uv_coeffs(const double2* __restrict__ psi, const double2* __restrict__ chi, double2* __restrict__ u,
+                            double2* __restrict__ v, int T, int nlm, int nlme, double inv_a) {
+  const int m = blockIdx.x, f = blockIdx.y, K = T + 1 - m;
+  const double2* ps = psi + (size_t)f * nlm + moff(T, m);
+  const double2* ch = chi + (size_t)f * nlm + moff(T, m);
+  double2* uo = u + (size_t)f * nlme + moff(T + 1, m);
+  double2* vo = v + (size_t)f * nlme + moff(T + 1, m);
+  const double fm = (double)m;
+  const double2 z = make_double2(0.0, 0.0);
+  for (int k = threadIdx.x; k <= K; k += blockDim.x) {
+    const int p = m + k;
+    const double a1 = (p + 2.0) * eps_d(p + 1, m), a0 = (p - 1.0) * eps_d(p, m);
+    const double2 p0 = k < K ? ps[k] : z, c0 = k < K ? ch[k] : z;
+    const double2 pp = k + 1 < K ? ps[k + 1] : z, cp = k + 1 < K ? ch[k + 1] : z;
+    const double2 pm = k > 0 ? ps[k - 1] : z, cm = k > 0 ? ch[k - 1] : z;
+    const double dpx = a1 * pp.x - a0 * pm.x, dpy = a1 * pp.y - a0 * pm.y;  // psi'
+    const double dcx = a1 * cp.x - a0 * cm.x, dcy = a1 * cp.y - a0 * cm.y;  // chi'
+    uo[k] = make_double2(inv_a * (-dpx - fm * c0.y), inv_a * (-dpy + fm * c0.x));
+    vo[k] = make_double2(inv_a * (-fm * p0.y + dcx), inv_a * (fm * p0.x + dcy));
   }
 }
 
@@ -789,6 +779,7 @@ struct sh_plan {
   double* d_H = nullptr;
   double* d_Pn = nullptr;   // P_{T+1}^m [T+1][nh]
   double2* d_raw = nullptr; // P-sums of the FP64 vector analysis [max_fields][2][nlme]
+  double2* d_uv = nullptr;  // u and v spectra of the FP64 vector synthesis [2 max_fields][nlme]
   double2* d_tw = nullptr;  // twiddle tables of the FFT passes (fft_twiddle_tables)
   float2* d_tw32 = nullptr; // the same in FP32, for the FFT of the tensor-core plans
   float4* d_twdf = nullptr; // the same as double-float pairs (re.hi, re.lo, im.hi, im.lo), SH_DF
@@ -864,7 +855,8 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
       (e = cudaMalloc(&p->d_H, sizeof(double) * tab)) ||
       (e = cudaMalloc(&p->d_Pn, sizeof(double) * (size_t)(d.T + 1) * p->nh)) ||
       (d.precision == SH_FP64 &&
-       (e = cudaMalloc(&p->d_raw, sizeof(double2) * 2 * (size_t)d.max_fields * nlm_ext(d.T)))) ||
+       ((e = cudaMalloc(&p->d_raw, sizeof(double2) * 2 * (size_t)d.max_fields * nlm_ext(d.T))) ||
+        (e = cudaMalloc(&p->d_uv, sizeof(double2) * 2 * (size_t)d.max_fields * nlm_ext(d.T))))) ||
       (e = cudaMalloc(&p->d_tw, sizeof(double2) * ntw)) ||
       (e = cudaMalloc(&p->d_tw32, sizeof(float2) * ntw)) || (e = cudaMalloc(&p->d_twdf, sizeof(float4) * ntw)) ||
       (e = cudaMalloc(&p->d_F, sizeof(double2) * 2 * (size_t)d.max_fields * (d.T + 1) * d.nlat))) {
@@ -964,6 +956,7 @@ extern "C" int sh_plan_destroy(sh_plan* p) {
   cudaFree(p->d_H);
   cudaFree(p->d_Pn);
   cudaFree(p->d_raw);
+  cudaFree(p->d_uv);
   cudaFree(p->d_tw);
   cudaFree(p->d_tw32);
   cudaFree(p->d_twdf);
@@ -1039,7 +1032,7 @@ static int leg_synth(sh_plan* p, const double2* spec, double2* F, int nf) {
   if (p->dfl) return df_leg_synth(p->dfl, spec, F, nf, nullptr, nullptr, nullptr, nullptr, 0, 0.0, p->stream);
   const int ph = p->prof.begin(0);
   k_leg_synth<<<dim3(p->d.T + 1, nf, (p->nh + LTH - 1) / LTH), LTH, 0, p->stream>>>(
-      p->d_P, spec, F, p->d.T, p->d.nlat, p->nlm, p->d_ks, p->pb.ngl);
+      p->d_P, nullptr, spec, F, nullptr, nf, p->d.T, p->d.nlat, p->nlm, p->d_ks, p->pb.ngl);
   p->prof.end(ph);
   return REXI_OK;
 }
@@ -1047,8 +1040,12 @@ static int leg_synth_uv(sh_plan* p, const double2* psi, const double2* chi, doub
   if (p->tc) return tc_leg_synth_uv(p->tc, psi, chi, FU, FV, nf, 1.0 / p->d.radius, p->stream);
   if (p->dfl) return df_leg_synth(p->dfl, nullptr, nullptr, 0, psi, chi, FU, FV, nf, 1.0 / p->d.radius, p->stream);
   const int ph = p->prof.begin(0);
-  k_leg_synth_uv<<<dim3(p->d.T + 1, nf, (p->nh + LTH - 1) / LTH), LTH, 0, p->stream>>>(
-      p->d_P, p->d_H, psi, chi, FU, FV, p->d.T, p->d.nlat, p->nlm, 1.0 / p->d.radius, p->d_ks, p->pb.ngl);
+  // u and v spectra (k_uv_coeffs), then one scalar synthesis of the 2 nf fields: u to FU, v to FV
+  const int nlme = nlm_ext(p->d.T);
+  k_uv_coeffs<<<dim3(p->d.T + 1, nf), 128, 0, p->stream>>>(psi, chi, p->d_uv, p->d_uv + (size_t)nf * nlme, p->d.T,
+                                                            p->nlm, nlme, 1.0 / p->d.radius);
+  k_leg_synth<<<dim3(p->d.T + 1, 2 * nf, (p->nh + LTH - 1) / LTH), LTH, 0, p->stream>>>(
+      p->d_P, p->d_Pn, p->d_uv, FU, FV, nf, p->d.T, p->d.nlat, nlme, p->d_ks, p->pb.ngl);
   p->prof.end(ph);
   return REXI_OK;
 }
