@@ -930,7 +930,7 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
   }
   if (e) return bail(cuda_fail(e, "cudaFuncSetAttribute(fft)"));
   if (d.precision == SH_DF) {
-    int rc = df_legendre_create(&p->dfl, p->d_P, p->d_H, p->d_Pn, p->d_w, p->d_wq, d.T, d.nlat, d.max_fields, p->pb,
+    int rc = df_legendre_create(&p->dfl, p->d_P, p->d_Pn, p->d_w, p->d_wq, d.T, d.nlat, d.max_fields, p->pb,
                                 p->stream);
     if (rc) return bail(rc);
     df_legendre_set_prof(p->dfl, &p->prof);

@@ -10,16 +10,18 @@
 // results are formed in FP64 from the two words of each sum.  The longitude FFT of these plans
 // runs in double-float arithmetic as well (sht.cu).
 //
-// Tables (split from the FP64 ones): synthesis [moff(m)+k][nh] (latitude fastest, as the FP64
-// table: threads that own latitudes read coalesced), of P and H; analysis, of P alone, per m
-// [nh][K + 1] over the degrees n = m .. T + 1 with the even degree indices k first and the odd
-// ones after them, so that the warps of one parity, which own consecutive degrees, read
-// coalesced.  The analysis of vector fields takes P-sums only: their H-sums follow from the
-// P-sums of the neighbouring degrees (k_divcurl_from_p), which halves its multiply-adds.
+// Tables (split from the FP64 table of P, over the degrees n = m .. T + 1): synthesis
+// [moff(T+1, m) + k][nh] (latitude fastest: threads that own latitudes read coalesced);
+// analysis, per m [nh][K + 1] with the even degree indices k first and the odd ones after them,
+// so that the warps of one parity, which own consecutive degrees, read coalesced.  No table of
+// H: with Ht_n = (n+1) eps_n Pt_{n-1} - n eps_{n+1} Pt_{n+1}, a vector synthesis is the scalar
+// synthesis of the spectra u, v of its velocity components (k_df_synth_coeffs), and a vector
+// analysis takes P-sums only, whose neighbouring degrees give the H-sums (k_divcurl_from_p).
 //
-// One launch contracts NS scalar fields and NV vector pairs against the same table reads; the
-// host runs groups of fields (NS <= 2, NV <= 1 for synthesis; NS, NV <= 2 for analysis).  The
-// real and imaginary parts of every sum run together on the packed FP32x2 instructions.
+// One launch contracts up to four fields (synthesis: scalar spectra and the u, v spectra of
+// vector pairs) or NS scalar fields and NV vector pairs (analysis, NS, NV <= 2) against the
+// same table reads.  The real and imaginary parts of every sum run together on the packed
+// FP32x2 instructions.
 #include <algorithm>
 #include <cuda_runtime.h>
 #include <vector>
@@ -67,19 +69,59 @@ __device__ __forceinline__ double dsum(const dot2& a, const dot2& b, float sg) {
 __device__ __forceinline__ double dval(const dot2& a) { return (double)a.s + (double)a.err; }
 
 // ---- plan-time splits --------------------------------------------------------------------
-// FP64 table [moff(m)+k][nh] -> synthesis table (same layout) and, given the next degree's row
-// next [m][nh], the analysis table (per m at moff(T+1, m) nh: [nh][K + 1], even k first); one
-// thread per (m, latitude)
+// FP64 table of P [moff(m)+k][nh] and the next degree's row next [m][nh] -> synthesis table
+// [moff(T+1, m) + k][nh] and analysis table (per m at moff(T+1, m) nh: [nh][K + 1], even k
+// first), k = 0 .. K; one thread per (m, latitude)
 __global__ void k_df_split_table(const double* __restrict__ src, const double* __restrict__ next,
                                  float2* __restrict__ syn, float2* __restrict__ ana, int T, int nh) {
   const int m = blockIdx.x, j = blockIdx.y * blockDim.x + threadIdx.x;
   if (j >= nh) return;
   const int K = T + 1 - m, Kx = K + 1, Ke = (Kx + 1) / 2;
-  const size_t base = (size_t)moff(T, m) * nh, abase = (size_t)moff(T + 1, m) * nh + (size_t)j * Kx;
+  const size_t base = (size_t)moff(T, m) * nh, xbase = (size_t)moff(T + 1, m) * nh;
   for (int k = 0; k < Kx; ++k) {
     const float2 v = split_df(k < K ? src[base + (size_t)k * nh + j] : next[(size_t)m * nh + j]);
-    if (k < K) syn[base + (size_t)k * nh + j] = v;
-    if (ana) ana[abase + ((k & 1) ? Ke + (k >> 1) : (k >> 1))] = v;
+    syn[xbase + (size_t)k * nh + j] = v;
+    ana[xbase + (size_t)j * Kx + ((k & 1) ? Ke + (k >> 1) : (k >> 1))] = v;
+  }
+}
+
+__device__ __forceinline__ double eps_nm(int n, int m) {  // eps_n^m, 0 for n <= m
+  return n <= m ? 0.0 : sqrt((double(n) * n - double(m) * m) / (4.0 * n * n - 1.0));
+}
+
+// Split spectra of one synthesis in the layout of n = m .. T + 1 ([q][nlme] at moff(T+1, m)):
+// fields q < nfs the scalar spectra (0 at n = T + 1); then the u and v spectra of the nfv
+// (psi, chi) pairs, u_p = (-psi'_p + i m chi_p) / a and v_p = (i m psi_p + chi'_p) / a with
+// x'_p = (p + 2) eps_{p+1} x_{p+1} - (p - 1) eps_p x_{p-1} (formed in FP64, then split), whose
+// scalar syntheses are the velocity components U, V (Ht_n = (n+1) eps_n Pt_{n-1} -
+// n eps_{n+1} Pt_{n+1}).  Grid (T + 1, nfs + 2 nfv).
+__global__ void k_df_synth_coeffs(const double2* __restrict__ spec, const double2* __restrict__ psi,
+                                  const double2* __restrict__ chi, int nfs, int nfv, double inv_a,
+                                  float4* __restrict__ dst, int T, int nlm, int nlme) {
+  const int m = blockIdx.x, q = blockIdx.y, K = T + 1 - m;
+  float4* o = dst + (size_t)q * nlme + moff(T + 1, m);
+  const double2 z = make_double2(0.0, 0.0);
+  if (q < nfs) {
+    const double2* c = spec + (size_t)q * nlm + moff(T, m);
+    for (int k = threadIdx.x; k <= K; k += blockDim.x) o[k] = split_dfc(k < K ? c[k] : z);
+    return;
+  }
+  const int r = q - nfs, v = r < nfv ? r : r - nfv;
+  const bool uu = r < nfv;  // u of pair v, else v of pair v
+  const double2* ps = psi + (size_t)v * nlm + moff(T, m);
+  const double2* ch = chi + (size_t)v * nlm + moff(T, m);
+  const double fm = (double)m;
+  for (int k = threadIdx.x; k <= K; k += blockDim.x) {
+    const int p = m + k;
+    const double a1 = (p + 2.0) * eps_nm(p + 1, m), a0 = (p - 1.0) * eps_nm(p, m);
+    const double2 x0 = uu ? (k < K ? ch[k] : z) : (k < K ? ps[k] : z);   // the i m term's spectrum
+    const double2* d = uu ? ps : ch;                                      // the primed one's
+    const double2 dp = k + 1 < K ? d[k + 1] : z, dm = k > 0 ? d[k - 1] : z;
+    const double dx = a1 * dp.x - a0 * dm.x, dy = a1 * dp.y - a0 * dm.y;
+    // u = (-psi' + i m chi) / a;  v = (i m psi + chi') / a
+    const double2 val = uu ? make_double2(inv_a * (-dx - fm * x0.y), inv_a * (-dy + fm * x0.x))
+                           : make_double2(inv_a * (-fm * x0.y + dx), inv_a * (fm * x0.x + dy));
+    o[k] = split_dfc(val);
   }
 }
 __global__ void k_df_split_weights(const double* __restrict__ w, const double* __restrict__ wq,
@@ -105,159 +147,100 @@ __global__ void k_df_split_inputs(const __grid_constant__ SplitSegs sg, float4* 
 
 // ---- synthesis ----------------------------------------------------------------------------
 struct DfSynthArgs {
-  const float2* P;
-  const float2* H;
-  const float4* cs;   // scalar spectra, split [NS][nlm]
-  const float4* cp;   // psi [NV][nlm]
-  const float4* cc;   // chi [NV][nlm]
-  double2* F;         // [NS][T+1][nlat]
-  double2* FU;        // [NV][T+1][nlat]
-  double2* FV;
-  const int* ks;      // polar bounds: first degree index per (m, 32-latitude group) [T+1][ngl]
-  int T, nlat, nh, nlm, ngl;
-  double inv_a;
+  const float2* P;      // synthesis table [moff(T+1, m) + k][nh], k = 0 .. K
+  const float4* c;      // split spectra of the launch's fields [NF][nlme] at moff(T+1, m) + k
+  double2* out[4];      // Fourier coefficients of each field [T+1][nlat]
+  const int* ks;        // polar bounds: first degree index per (m, 32-latitude group) [T+1][ngl]
+  int T, nlat, nh, nlme, ngl;
 };
 
-// k-step of parity PAR: the table entries p, h of degree k against every field's coefficient
-// (split coefficients of the block's zonal order staged in shared memory with the field
-// stride L = T + 1: scalar field f at cf + f L, psi of pair v at cf + (NS + v) L, chi at
-// cf + (NS + NV + v) L)
-template <int NS, int NV, int PAR>
-__device__ __forceinline__ void df_synth_step(float2 pv, float2 hv, const float4* cf, int L, int k,
-                                              dot2c (&S)[NS > 0 ? NS : 1][2], dot2c (&V)[NV > 0 ? NV : 1][4][2]) {
+// k-step of parity PAR: the table entry p of degree k against every field's coefficient
+// (split coefficients of the block's zonal order staged in shared memory, field f at
+// cf + f L, L = T + 2)
+template <int NF, int PAR>
+__device__ __forceinline__ void df_synth_step(float2 pv, const float4* cf, int L, int k, dot2c (&S)[NF][2]) {
   const df p = df_of(pv);
 #pragma unroll
-  for (int f = 0; f < NS; ++f) madd(S[f][PAR], p, cf[f * L + k]);
-  if (NV > 0) {
-    const df h = df_of(hv);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const float4 ps = cf[(NS + v) * L + k], ch = cf[(NS + NV + v) * L + k];
-      madd(V[v][0][PAR], p, ps);
-      madd(V[v][1][PAR], p, ch);
-      madd(V[v][2][PAR], h, ps);
-      madd(V[v][3][PAR], h, ch);
-    }
-  }
+  for (int f = 0; f < NF; ++f) madd(S[f][PAR], p, cf[f * L + k]);
 }
 
 constexpr int DF_PF = 4;  // table entries loaded this many degrees (synthesis) or latitudes (analysis) ahead
 
-// One thread per northern latitude jh of zonal order m: even and odd partial sums over the
-// degrees, combined for the latitude and its mirror (P_n(-mu) = (-1)^(n-m) P_n(mu),
-// H_n(-mu) = -(-1)^(n-m) H_n(mu)); vector pairs give U = (-H psi + i m P chi)/a and
-// V = (i m P psi + H chi)/a.  The block (four warps over 128 consecutive latitudes) stages its
-// zonal order's split coefficients in shared memory; each thread keeps the table entries of the
-// next DF_PF degrees (2 DF_PF without vector pairs or under MINB = 1) in flight.  Each warp starts
-// at the first degree its 32 latitudes need (polar bounds, rounded down to even).
+// One thread per northern latitude jh of zonal order m: even and odd partial sums of NF fields
+// over the degrees n = m .. T + 1, combined for the latitude and its mirror
+// (P_n(-mu) = (-1)^(n-m) P_n(mu)).  The block (four warps over 128 consecutive latitudes)
+// stages its zonal order's split coefficients in shared memory; each warp starts at the first
+// degree its 32 latitudes need (polar bounds, rounded down to even).
 // MINB: blocks per SM the registers must allow (5 for launches of several waves, where
 // occupancy hides the table loads; 1 for small ones, where each block's own overlap counts)
-template <int NS, int NV, int MINB>
+template <int NF, int MINB>
 __global__ void __launch_bounds__(DF_STH, MINB) k_df_synth(const __grid_constant__ DfSynthArgs a) {
   constexpr bool BITS = MINB > 1;  // the result form that fits the tighter register budget
   extern __shared__ float4 cf[];
   const int m = blockIdx.x;
-  const int T = a.T, K = T + 1 - m, base = moff(T, m), nlat = a.nlat, nh = a.nh;
+  const int T = a.T, K = T + 1 - m, Kx = K + 1, L = T + 2, nlat = a.nlat, nh = a.nh;
   // latitude tiles run equator first: the last tile has the most work left after the polar
   // truncation, and the first blocks launched finish last
   const int jh = (gridDim.y - 1 - blockIdx.y) * DF_STH + threadIdx.x;
   // from the warp's first degree kb (even: the parity of k - kb is that of k) on; requested
   // before the staging, whose time hides its latency
-  const int kb = jh < nh ? __ldg(a.ks + m * a.ngl + (jh >> 5)) & ~1 : 0;  // warp-uniform
-  for (int i = threadIdx.x; i < (NS + 2 * NV) * K; i += DF_STH) {
-    const int q = i / K, k = i - q * K;
-    const float4* src = q < NS ? a.cs + (size_t)q * a.nlm : q < NS + NV ? a.cp + (size_t)(q - NS) * a.nlm
-                                                                         : a.cc + (size_t)(q - NS - NV) * a.nlm;
-    cf[q * (T + 1) + k] = __ldg(src + base + k);
+  const int kb = jh < nh ? __ldg(a.ks + m * a.ngl + (jh >> 5)) & ~1 : 0;  // warp-uniform, <= K
+  const float4* src = a.c + moff(T + 1, m);
+  for (int i = threadIdx.x; i < NF * Kx; i += DF_STH) {
+    const int q = i / Kx, k = i - q * Kx;
+    cf[q * L + k] = __ldg(src + (size_t)q * a.nlme + k);
   }
   __syncthreads();
   if (jh >= nh) return;  // no barrier below
-  const float2* Pm = a.P + (size_t)(base + kb) * nh + jh;
-  const float2* Hm = a.H + (size_t)(base + kb) * nh + jh;
-  const int Kr = K - kb;
+  const float2* Pm = a.P + (size_t)(moff(T + 1, m) + kb) * nh + jh;
+  const int Kr = Kx - kb;
   const float2 z2 = make_float2(0.f, 0.f);
-  dot2c S[NS > 0 ? NS : 1][2];     // field, parity of k
-  dot2c V[NV > 0 ? NV : 1][4][2];  // pair, (P psi, P chi, H psi, H chi), parity of k
+  dot2c S[NF][2];  // field, parity of k
 #pragma unroll
-  for (int f = 0; f < (NS > 0 ? NS : 1); ++f) S[f][0] = S[f][1] = dot2c{z2, z2};
+  for (int f = 0; f < NF; ++f) S[f][0] = S[f][1] = dot2c{z2, z2};
+  // Table rows in flight.  Under the tight register budget (MINB > 1) with three or four fields
+  // a rolling prefetch: slot u holds row k0 + u and, once consumed, is refilled with row
+  // k0 + PF + u, so every row is requested PF rows before its use with one register set.
+  // Otherwise a double buffer of twice the distance: the next PF rows are requested together
+  // before the current ones are used.
+  constexpr bool ROLL = MINB > 1 && NF > 2;
+  constexpr int PF = ROLL ? DF_PF : 2 * DF_PF;
+  float2 pb[PF];
 #pragma unroll
-  for (int v = 0; v < (NV > 0 ? NV : 1); ++v)
-#pragma unroll
-    for (int q = 0; q < 8; ++q) V[v][q >> 1][q & 1] = dot2c{z2, z2};
-  // Table rows in flight.  Under the tight register budget (MINB > 1) a rolling prefetch:
-  // slot u holds row k0 + u and, once consumed, is refilled with row k0 + PF + u, so every row
-  // is requested PF rows before its use with one register set (scalar-only blocks do less
-  // arithmetic per row and have the registers for twice the distance).  Otherwise (launches of
-  // one wave, latency-bound with a few warps per SM) a double buffer of twice the distance:
-  // the next PF rows are requested together before the current ones are used.
-  constexpr bool ROLL = MINB > 1;
-  constexpr int PF = (ROLL && NV > 0) ? DF_PF : 2 * DF_PF;
-  float2 pb[PF], hb[PF];
-#pragma unroll
-  for (int u = 0; u < PF; ++u) {
-    pb[u] = u < Kr ? __ldg(Pm + (size_t)u * nh) : z2;
-    hb[u] = (NV > 0 && u < Kr) ? __ldg(Hm + (size_t)u * nh) : z2;
-  }
+  for (int u = 0; u < PF; ++u) pb[u] = u < Kr ? __ldg(Pm + (size_t)u * nh) : z2;
   for (int k0 = 0; k0 < Kr; k0 += PF) {
-    float2 pn[ROLL ? 1 : PF], hn[ROLL ? 1 : PF];
+    float2 pn[ROLL ? 1 : PF];
     if (!ROLL) {
 #pragma unroll
       for (int u = 0; u < PF; ++u) {
         const int kk = k0 + PF + u;
         pn[ROLL ? 0 : u] = kk < Kr ? __ldg(Pm + (size_t)kk * nh) : z2;
-        hn[ROLL ? 0 : u] = (NV > 0 && kk < Kr) ? __ldg(Hm + (size_t)kk * nh) : z2;
       }
     }
 #pragma unroll
     for (int u = 0; u < PF; u += 2) {  // k0 is even: the parity of k0 + u is that of u
-      if (k0 + u < Kr) df_synth_step<NS, NV, 0>(pb[u], hb[u], cf, a.T + 1, kb + k0 + u, S, V);
-      if (k0 + u + 1 < Kr) df_synth_step<NS, NV, 1>(pb[u + 1], hb[u + 1], cf, a.T + 1, kb + k0 + u + 1, S, V);
+      if (k0 + u < Kr) df_synth_step<NF, 0>(pb[u], cf, L, kb + k0 + u, S);
+      if (k0 + u + 1 < Kr) df_synth_step<NF, 1>(pb[u + 1], cf, L, kb + k0 + u + 1, S);
       if (ROLL) {
 #pragma unroll
         for (int v = u; v < u + 2; ++v) {
           const int kk = k0 + PF + v;
           pb[v] = kk < Kr ? __ldg(Pm + (size_t)kk * nh) : z2;
-          hb[v] = (NV > 0 && kk < Kr) ? __ldg(Hm + (size_t)kk * nh) : z2;
         }
       }
     }
     if (!ROLL) {
 #pragma unroll
-      for (int u = 0; u < PF; ++u) {
-        pb[u] = pn[ROLL ? 0 : u];
-        hb[u] = hn[ROLL ? 0 : u];
-      }
+      for (int u = 0; u < PF; ++u) pb[u] = pn[ROLL ? 0 : u];
     }
   }
   const int lat = jh, lats = nlat - 1 - jh;
 #pragma unroll
-  for (int f = 0; f < NS; ++f) {
-    double2* o = a.F + ((size_t)f * (T + 1) + m) * nlat;
+  for (int f = 0; f < NF; ++f) {
+    double2* o = a.out[f] + (size_t)m * nlat;
     const dot2 er = dot2c_re(S[f][0]), ei = dot2c_im(S[f][0]), od = dot2c_re(S[f][1]), oi = dot2c_im(S[f][1]);
     o[lat] = make_double2(dsum<BITS>(er, od, 1.f), dsum<BITS>(ei, oi, 1.f));
     o[lats] = make_double2(dsum<BITS>(er, od, -1.f), dsum<BITS>(ei, oi, -1.f));
-  }
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    double2* oU = a.FU + ((size_t)v * (T + 1) + m) * nlat;
-    double2* oV = a.FV + ((size_t)v * (T + 1) + m) * nlat;
-#pragma unroll
-    for (int hs = 0; hs < 2; ++hs) {
-      const float so = hs ? -1.f : 1.f;  // odd degrees change sign in the south
-      const double sh = hs ? -1.0 : 1.0;  // and the H sums as a whole
-      // [0] P psi, [1] P chi, [2] H psi, [3] H chi; re, im
-      double x[4][2];
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int c = 0; c < 2; ++c)
-          x[q][c] = (q >= 2 ? sh : 1.0) * (c ? dsum<BITS>(dot2c_im(V[v][q][0]), dot2c_im(V[v][q][1]), so)
-                                             : dsum<BITS>(dot2c_re(V[v][q][0]), dot2c_re(V[v][q][1]), so));
-      const double fm = (double)m, ia = a.inv_a;
-      const int j = hs ? lats : lat;
-      oU[j] = make_double2(ia * (-x[2][0] - fm * x[1][1]), ia * (-x[2][1] + fm * x[1][0]));
-      oV[j] = make_double2(ia * (-fm * x[0][1] + x[3][0]), ia * (fm * x[0][0] + x[3][1]));
-    }
   }
 }
 
@@ -394,9 +377,9 @@ __global__ void __launch_bounds__(DF_ATH, 4) k_df_anal(const __grid_constant__ D
   }
 }
 
-template <int NS, int NV>
+template <int NF>
 size_t df_synth_smem(int T) {
-  return sizeof(float4) * (size_t)(NS + 2 * NV) * (T + 1);
+  return sizeof(float4) * (size_t)NF * (T + 2);
 }
 template <int NS, int NV>
 size_t df_anal_smem(int nh) {
@@ -408,7 +391,7 @@ size_t df_anal_smem(int nh) {
 struct DfLegendre {
   int T = 0, nlat = 0, nh = 0, nlm = 0, max_fields = 0, nsm = 0;
   PolarBounds pb;
-  float2 *Ps = nullptr, *Hs = nullptr, *Pa = nullptr;  // synthesis P, H; analysis P (to n = T + 1)
+  float2 *Ps = nullptr, *Pa = nullptr;  // synthesis and analysis tables of P (to n = T + 1)
   float4* wdf = nullptr;
   float4* in = nullptr;  // split inputs of one call: [2 max_fields][max(nlm, (T+1) nlat)]
   double2* raw = nullptr;  // P-sums of the vector fields of one call: [2 max_fields][2][nlme]
@@ -423,20 +406,20 @@ static int df_smem_attr(int nh, int T) {
                              (int)df_anal_smem<NS, NV>(nh));
   DF_ATTR(1, 0) DF_ATTR(2, 0) DF_ATTR(0, 1) DF_ATTR(1, 1) DF_ATTR(2, 1) DF_ATTR(0, 2) DF_ATTR(1, 2) DF_ATTR(2, 2)
 #undef DF_ATTR
-#define DF_SATTR(NS, NV)                                                                                   \
+#define DF_SATTR(NF)                                                                                       \
   if (!e)                                                                                                 \
-    e = cudaFuncSetAttribute(k_df_synth<NS, NV, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
-                             (int)df_synth_smem<NS, NV>(T));                                              \
+    e = cudaFuncSetAttribute(k_df_synth<NF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
+                             (int)df_synth_smem<NF>(T));                                                  \
   if (!e)                                                                                                 \
-    e = cudaFuncSetAttribute(k_df_synth<NS, NV, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
-                             (int)df_synth_smem<NS, NV>(T));
-  DF_SATTR(1, 0) DF_SATTR(2, 0) DF_SATTR(0, 1) DF_SATTR(1, 1) DF_SATTR(2, 1)
+    e = cudaFuncSetAttribute(k_df_synth<NF, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
+                             (int)df_synth_smem<NF>(T));
+  DF_SATTR(1) DF_SATTR(2) DF_SATTR(3) DF_SATTR(4)
 #undef DF_SATTR
   return e ? cuda_fail(e, "cudaFuncSetAttribute(k_df_*)") : REXI_OK;
 }
 
-int df_legendre_create(DfLegendre** out, const double* P, const double* H, const double* Pn, const double* w,
-                       const double* wq, int T, int nlat, int max_fields, const PolarBounds& pb, cudaStream_t stream) {
+int df_legendre_create(DfLegendre** out, const double* P, const double* Pn, const double* w, const double* wq, int T,
+                       int nlat, int max_fields, const PolarBounds& pb, cudaStream_t stream) {
   *out = nullptr;
   const int nh = nlat / 2;
   if (df_anal_smem<2, 2>(nh) > 200 * 1024)  // 12 staged arrays of nh float4
@@ -457,8 +440,7 @@ int df_legendre_create(DfLegendre** out, const double* P, const double* H, const
   const size_t per = std::max<size_t>(t->nlm, (size_t)(T + 1) * nlat);
   cudaError_t e;
   const size_t tabx = (size_t)nlm_ext(T) * nh;
-  if ((e = cudaMalloc(&t->Ps, sizeof(float2) * tab)) || (e = cudaMalloc(&t->Hs, sizeof(float2) * tab)) ||
-      (e = cudaMalloc(&t->Pa, sizeof(float2) * tabx)) ||
+  if ((e = cudaMalloc(&t->Ps, sizeof(float2) * tabx)) || (e = cudaMalloc(&t->Pa, sizeof(float2) * tabx)) ||
       (e = cudaMalloc(&t->raw, sizeof(double2) * 2 * 2 * (size_t)max_fields * nlm_ext(T))) ||
       (e = cudaMalloc(&t->wdf, sizeof(float4) * nh)) ||
       (e = cudaMalloc(&t->in, sizeof(float4) * per * 2 * (size_t)max_fields))) {
@@ -467,7 +449,6 @@ int df_legendre_create(DfLegendre** out, const double* P, const double* H, const
     return fail(REXI_ENOMEM, "double-float Legendre tables: cudaMalloc failed: %s", cudaGetErrorString(e));
   }
   k_df_split_table<<<dim3(T + 1, (nh + 127) / 128), 128, 0, stream>>>(P, Pn, t->Ps, t->Pa, T, nh);
-  k_df_split_table<<<dim3(T + 1, (nh + 127) / 128), 128, 0, stream>>>(H, Pn, t->Hs, nullptr, T, nh);
   k_df_split_weights<<<(nh + 127) / 128, 128, 0, stream>>>(w, wq, t->wdf, nh);
   int rc = REXI_OK;
   if ((e = cudaGetLastError())) rc = cuda_fail(e, "double-float table kernels");
@@ -482,7 +463,7 @@ int df_legendre_create(DfLegendre** out, const double* P, const double* H, const
 
 void df_legendre_destroy(DfLegendre* t) {
   if (!t) return;
-  for (void* p : {(void*)t->Ps, (void*)t->Hs, (void*)t->Pa, (void*)t->wdf, (void*)t->in, (void*)t->raw}) cudaFree(p);
+  for (void* p : {(void*)t->Ps, (void*)t->Pa, (void*)t->wdf, (void*)t->in, (void*)t->raw}) cudaFree(p);
   delete t;
 }
 
@@ -518,52 +499,45 @@ static void split_inputs(DfLegendre* t, const double2* s0, long long n0, const d
   k_df_split_inputs<<<(unsigned)((sg.end[2] + 255) / 256), 256, 0, s>>>(sg, t->in);
 }
 
-template <int NS, int NV>
-static void launch_synth(DfLegendre* t, DfSynthArgs a, cudaStream_t s) {
+template <int NF>
+static void launch_synth(DfLegendre* t, const DfSynthArgs& a, cudaStream_t s) {
   const dim3 grid(t->T + 1, (t->nh + DF_STH - 1) / DF_STH);
-  const size_t smem = df_synth_smem<NS, NV>(t->T);
+  const size_t smem = df_synth_smem<NF>(t->T);
   if ((long long)grid.x * grid.y >= 4LL * t->nsm)
-    k_df_synth<NS, NV, 5><<<grid, DF_STH, smem, s>>>(a);
+    k_df_synth<NF, 5><<<grid, DF_STH, smem, s>>>(a);
   else
-    k_df_synth<NS, NV, 1><<<grid, DF_STH, smem, s>>>(a);
+    k_df_synth<NF, 1><<<grid, DF_STH, smem, s>>>(a);
 }
 
+// Scalar spectra and (psi, chi) pairs as the scalar syntheses of nfs + 2 nfv spectra (the
+// scalars, the u's, the v's; k_df_synth_coeffs), up to four per launch, one table read each.
 int df_leg_synth(DfLegendre* t, const double2* spec, double2* F, int nfs, const double2* psi, const double2* chi,
                  double2* FU, double2* FV, int nfv, double inv_a, cudaStream_t s) {
   if (nfs < 0 || nfv < 0 || nfs + 2 * nfv > 2 * t->max_fields) return fail(REXI_EINVAL, "df synthesis: too many fields");
   const int ph = t->prof ? t->prof->begin(1) : -1;
-  const long long nlm = t->nlm;
-  split_inputs(t, spec, nfs * nlm, psi, nfv * nlm, chi, nfv * nlm, s);
+  const int nft = nfs + 2 * nfv, nlme = nlm_ext(t->T);
+  if (nft > 0)
+    k_df_synth_coeffs<<<dim3(t->T + 1, nft), 128, 0, s>>>(spec, psi, chi, nfs, nfv, inv_a, t->in, t->T, t->nlm, nlme);
+  const size_t fo = (size_t)(t->T + 1) * t->nlat;
   DfSynthArgs a{};
   a.P = t->Ps;
-  a.H = t->Hs;
   a.T = t->T;
   a.nlat = t->nlat;
   a.nh = t->nh;
-  a.nlm = t->nlm;
-  a.inv_a = inv_a;
+  a.nlme = nlme;
   a.ks = t->pb.d_ks;
   a.ngl = t->pb.ngl;
-  const float4* cs = t->in;
-  const float4* cp = t->in + nfs * nlm;
-  const float4* cc = cp + nfv * nlm;
-  const size_t fo = (size_t)(t->T + 1) * t->nlat;
-  int fs = 0, fv = 0;
-  while (fs < nfs || fv < nfv) {
-    const int ns = std::min(2, nfs - fs), nv = std::min(1, nfv - fv);
-    a.cs = cs + fs * nlm;
-    a.cp = cp + fv * nlm;
-    a.cc = cc + fv * nlm;
-    a.F = F ? F + fs * fo : nullptr;
-    a.FU = FU ? FU + fv * fo : nullptr;
-    a.FV = FV ? FV + fv * fo : nullptr;
-    if (ns == 2 && nv == 1) launch_synth<2, 1>(t, a, s);
-    else if (ns == 1 && nv == 1) launch_synth<1, 1>(t, a, s);
-    else if (ns == 0) launch_synth<0, 1>(t, a, s);
-    else if (ns == 2) launch_synth<2, 0>(t, a, s);
-    else launch_synth<1, 0>(t, a, s);
-    fs += ns;
-    fv += nv;
+  for (int q0 = 0; q0 < nft; q0 += 4) {
+    const int nf = std::min(4, nft - q0);
+    a.c = t->in + (size_t)q0 * nlme;
+    for (int i = 0; i < 4; ++i) {
+      const int q = q0 + i;
+      a.out[i] = i >= nf ? nullptr : q < nfs ? F + q * fo : q < nfs + nfv ? FU + (q - nfs) * fo : FV + (q - nfs - nfv) * fo;
+    }
+    if (nf == 4) launch_synth<4>(t, a, s);
+    else if (nf == 3) launch_synth<3>(t, a, s);
+    else if (nf == 2) launch_synth<2>(t, a, s);
+    else launch_synth<1>(t, a, s);
   }
   if (t->prof) t->prof->end(ph);
   cudaError_t e = cudaGetLastError();

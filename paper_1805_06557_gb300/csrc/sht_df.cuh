@@ -6,11 +6,12 @@ namespace rexi {
 
 struct DfLegendre;
 
-// P, H: the FP64 tables [moff(m)+k][nh]; w, wq: Gauss weights and w / (1 - mu^2) [nh] (device).
-// Pn: the next degree's row P_{T+1}^m [T+1][nh] (the analysis table reaches n = T + 1);
-// pb: the plan's polar bounds (device arrays used by the kernels; must outlive the state)
-int df_legendre_create(DfLegendre** out, const double* P, const double* H, const double* Pn, const double* w,
-                       const double* wq, int T, int nlat, int max_fields, const PolarBounds& pb, cudaStream_t stream);
+// P: the FP64 table [moff(m)+k][nh]; Pn: the next degree's row P_{T+1}^m [T+1][nh] (the split
+// tables reach n = T + 1; no table of H is needed); w, wq: Gauss weights and w / (1 - mu^2)
+// [nh] (device); pb: the plan's polar bounds (device arrays used by the kernels; must outlive
+// the state)
+int df_legendre_create(DfLegendre** out, const double* P, const double* Pn, const double* w, const double* wq, int T,
+                       int nlat, int max_fields, const PolarBounds& pb, cudaStream_t stream);
 // table entries (k < T + 1 - m, j < nh) the kernels stream per table: synthesis, analysis
 void df_legendre_streamed(const DfLegendre* t, long long* syn, long long* ana);
 void df_legendre_destroy(DfLegendre* t);
