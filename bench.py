@@ -494,9 +494,10 @@ def sh_transforms(torch, rexi, fp64_peak, fp32_peak, T=511, nlat=768, nlon=1536,
             vec = kind in ("synthesis_uv", "analysis_divcurl")
             mixed = kind.endswith("_mixed")
             # tables the method reads: P, or P and H for vector fields -- except the FP64 and
-            # double-float analyses, whose vector fields take P-sums only (H-sums from the
-            # neighbouring degrees' P-sums)
-            p_only = kind.startswith("analysis") and prec in ("fp64", "df")
+            # double-float plans, whose vector transforms use P alone (synthesis: the scalar
+            # syntheses of the velocity components' spectra; analysis: P-sums, whose
+            # neighbouring degrees give the H-sums)
+            p_only = prec in ("fp64", "df")
             ntab = 2 if (vec or mixed) and not p_only else 1
             need = use["needed_synth" if kind.startswith("synthesis") else "needed_anal"]
             # spectral arrays = Fourier arrays = grids: scalar fields + 2 per vector pair
@@ -508,7 +509,7 @@ def sh_transforms(torch, rexi, fp64_peak, fp32_peak, T=511, nlat=768, nlon=1536,
             fft_ms = prof["fft"][0] / reps
             fft_bytes = narr * (nlat * nlon * 8 + nlat * (T + 1) * 16)
             # FMA = 2; complex coefficient x real table; vector arrays meet P and H (P alone in the
-            # FP64 and double-float analyses), scalar ones P
+            # FP64 and double-float plans), scalar ones P
             nvec_arr = 2 if kind == "synthesis_mixed" else 4 if kind == "analysis_mixed" else (narr if vec else 0)
             if p_only:
                 nvec_arr = 0

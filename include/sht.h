@@ -33,7 +33,7 @@ extern "C" {
  * Knuth's TwoSum), the longitude FFT in double-float arithmetic too (FP64 grids and Fourier
  * arrays at its ends).  Close to FP64 accuracy without the FP64 pipe, which
  * GB300 has little of (about 2 FP64 FMAs per clock and SM against 128 FP32 ones).  Tables take
- * three times the memory of SH_FP64 (the FP64 tables and two split layouts).  nlat <= 2132.
+ * twice the memory of SH_FP64 (the FP64 tables and two split layouts of P).  nlat <= 2132.
  * The words are FP32: spectra, grids and the intermediate sums must stay inside the FP32
  * exponent range, with room for the low word below the high one (magnitudes of about 1e-25 to
  * 1e30 keep full accuracy; SH_FP64 has no such limit). */
