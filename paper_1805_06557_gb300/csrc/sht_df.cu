@@ -200,11 +200,12 @@ __global__ void __launch_bounds__(DF_STH, MINB) k_df_synth(const __grid_constant
   for (int f = 0; f < NF; ++f) S[f][0] = S[f][1] = dot2c{z2, z2};
   // Table rows in flight.  Under the tight register budget (MINB > 1) with three or four fields
   // a rolling prefetch: slot u holds row k0 + u and, once consumed, is refilled with row
-  // k0 + PF + u, so every row is requested PF rows before its use with one register set.
-  // Otherwise a double buffer of twice the distance: the next PF rows are requested together
-  // before the current ones are used.
+  // k0 + PF + u, so every row is requested PF rows before its use with one register set (six
+  // rows: what five blocks per SM leave registers for; the one-pass N(U) synthesis at T511
+  // took 0.277 ms with four, 0.258 ms with six).  Otherwise a double buffer of eight rows: the
+  // next PF rows are requested together before the current ones are used.
   constexpr bool ROLL = MINB > 1 && NF > 2;
-  constexpr int PF = ROLL ? DF_PF : 2 * DF_PF;
+  constexpr int PF = ROLL ? DF_PF + 2 : 2 * DF_PF;
   float2 pb[PF];
 #pragma unroll
   for (int u = 0; u < PF; ++u) pb[u] = u < Kr ? __ldg(Pm + (size_t)u * nh) : z2;
