@@ -9,7 +9,8 @@ CUDA library; both sides receive the same seeded inputs from
 
 Every function states the passage of the paper it follows.  Where the paper is silent the
 docstring states the reading that is taken.  Library primitives used as single steps:
-``numpy.polynomial.legendre.leggauss`` (Gauss nodes), ``numpy.fft`` (longitude DFT),
+``numpy.polynomial.legendre.leggauss`` (Gauss nodes; the weights follow their definition),
+``numpy.fft`` (longitude DFT),
 ``scipy.linalg.solve_banded`` (pivoted banded LU), ``scipy.linalg.expm`` / ``numpy.linalg.eig``
 (exact exponential for the pins).
 

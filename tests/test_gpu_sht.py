@@ -12,6 +12,9 @@ pytestmark = pytest.mark.gpu
 
 A = 6.37122e6
 SIZES = [(7, 12, 24), (31, 48, 96), (63, 96, 192), (127, 192, 384)]
+# the smallest truncations (one 32-latitude and one 32-degree group, the degree n = T + 1 that
+# the vector transforms of the FP64 and double-float plans use next to n = m)
+TINY = [(1, 4, 4), (2, 4, 6), (3, 6, 8)]
 
 
 @pytest.fixture(scope="module")
@@ -42,11 +45,12 @@ def test_grid_matches_oracle(env, T, nlat, nlon):
     mu, w = p.grid()
     omu, ow = osht.gauss_grid(nlat)
     assert np.max(np.abs(mu - omu)) < 1e-14 and np.max(np.abs(w - ow)) < 1e-14
+    assert np.max(np.abs(w / ow - 1)) < 1e-11   # relative, the polar weights included
     p.close()
 
 
 @pytest.mark.parametrize("prec", ["fp64", "df"])
-@pytest.mark.parametrize("T,nlat,nlon", SIZES)
+@pytest.mark.parametrize("T,nlat,nlon", TINY + SIZES)
 def test_scalar_synthesis_analysis(env, T, nlat, nlon, prec):
     torch, rexi = env
     g = osht.Grid(T, nlat, nlon, A)
@@ -77,8 +81,11 @@ def test_scalar_synthesis_analysis(env, T, nlat, nlon, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "df"])
-@pytest.mark.parametrize("T,nlat,nlon", SIZES)
+@pytest.mark.parametrize("T,nlat,nlon", TINY + SIZES + [(255, 384, 768)])
 def test_vector_transforms(env, T, nlat, nlon, prec):
+    """Velocity synthesis (the scalar syntheses of the u, v spectra over n = m .. T + 1) and
+    divergence / curl (P-sums of A and B, combined over neighbouring degrees) against the
+    oracle, which contracts the table of (1 - mu^2) dP/dmu directly."""
     torch, rexi = env
     g = osht.Grid(T, nlat, nlon, A)
     nf = 2

@@ -23,6 +23,30 @@ def test_gauss_grid():
     assert abs(np.sum(w * mu ** 94) - 2.0 / 95.0) < 1e-12 * (2.0 / 95.0)
 
 
+def test_gauss_weights_vs_high_precision():
+    """The Gauss-Legendre weights against 40-digit ones at the polar, near-polar and
+    mid-latitude nodes of a 384-point grid (the weights next to the poles carry the vector
+    analysis, weighted there by 1 / (1 - mu^2)).  Reference: Newton on mpmath's P_n from the
+    stored node to the true root z, then w(z) = 2 / ((1 - z^2) P_n'(z)^2).  The stored node
+    mu is the root rounded to double, and the weight belongs to mu: from the Legendre equation,
+    d ln w / dx = -2x / (1 - x^2) at a root (about 5e4 at the polar node here), so the check
+    is w(mu) = w(z) (1 - 2z (mu - z) / (1 - z^2)) to 2e-13 relative."""
+    n = 384
+    mu, w = sht.gauss_grid(n)
+    mpmath.mp.dps = 40
+    for i in (0, 1, 5, n // 4, n - 1):
+        x = mpmath.mpf(float(mu[i]))
+        z = x
+        for _ in range(6):
+            dp = n * (z * mpmath.legendre(n, z) - mpmath.legendre(n - 1, z)) / (z * z - 1)
+            z -= mpmath.legendre(n, z) / dp
+        dp = n * (z * mpmath.legendre(n, z) - mpmath.legendre(n - 1, z)) / (z * z - 1)
+        wr = 2 / ((1 - z * z) * dp * dp) * (1 - 2 * z * (x - z) / (1 - z * z))
+        assert abs(float(x - z)) < 2e-16, i
+        err = float(mpmath.mpf(float(w[i])) / wr - 1)
+        assert abs(err) < 2e-13, (i, err)
+
+
 def test_legendre_vs_scipy():
     T = 12
     mu, _ = sht.gauss_grid(20)
