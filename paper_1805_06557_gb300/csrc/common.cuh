@@ -16,6 +16,14 @@ void set_error(const char* fmt, ...);
 int fail(int code, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
 
+// Raises the dynamic shared-memory limit of kernel fn to at least `bytes`.  The limit is per
+// kernel and process-wide, so it only grows: a plan created later with a smaller need must not
+// lower it below what a live plan launches with.  Serialised across threads.
+cudaError_t raise_smem_limit(const void* fn, size_t bytes);
+template <typename F> cudaError_t raise_smem_limit(F* fn, size_t bytes) {
+  return raise_smem_limit(reinterpret_cast<const void*>(fn), bytes);
+}
+
 #define REXI_CUDA_TRY(expr)                                   \
   do {                                                        \
     cudaError_t _e = (expr);                                  \

@@ -568,18 +568,144 @@ __device__ C* fft_run(Src src, Dst dst, C* a, C* b, const FftPlan& fp, const C* 
   return cur;
 }
 
+// ---- transforms of fixed length (n = 384, 768, 1536: the T127, T255 and T511 grids) ---------
+// The same Stockham passes with the length known at compile time: radices, strides Ns, twiddle
+// offsets and trip counts are constants, j / Ns is a constant division, and each padded index is
+// formed once per butterfly and advanced by constant steps (fpad(x + 8k) = fpad(x) + 9k).  The
+// factorisation is fft_factor's (radix 8 first, then 4, 2, 3); the plan checks that they agree.
+// Used by the FP32 and double-float FFTs; the FP64 one is bound by the FP64 pipe.
+constexpr int ct_nrad(int n) {
+  int k = 0;
+  while (n % 8 == 0) n /= 8, ++k;
+  while (n % 4 == 0) n /= 4, ++k;
+  while (n % 2 == 0) n /= 2, ++k;
+  while (n % 3 == 0) n /= 3, ++k;
+  return k;
+}
+constexpr int ct_rad(int n, int s) {
+  const int rs[4] = {8, 4, 2, 3};
+  int k = 0;
+  for (int i = 0; i < 4; ++i)
+    while (n % rs[i] == 0) {
+      if (k++ == s) return rs[i];
+      n /= rs[i];
+    }
+  return 0;
+}
+constexpr int ct_ns(int n, int s) {
+  int p = 1;
+  for (int i = 0; i < s; ++i) p *= ct_rad(n, i);
+  return p;
+}
+constexpr int ct_twoff(int n, int s) {
+  int off = 0;
+  for (int i = 0; i < s; ++i) off += ct_ns(n, i) * tw_width(ct_rad(n, i));
+  return off;
+}
+
+// padded index of element j + r nb (the pass's reads) and of base + r Ns (its writes)
+template <int NB> __device__ __forceinline__ int ct_rd(int pj, int j, int r) {
+  if constexpr (NB % 8 == 0) return pj + r * (NB + NB / 8);
+  else return fpad(j + r * NB);
+}
+template <int NS, int R> __device__ __forceinline__ int ct_wr(int pb, int base, int r) {
+  if constexpr (NS % 8 == 0) return pb + r * (NS + NS / 8);
+  else if constexpr (NS == 1 && 8 % R == 0) return pb + r;  // base = q R, a multiple of R dividing 8
+  else return fpad(base + r * NS);
+}
+
+// One pass: radix R, length N, stride NS; reads the padded shared buffer rb or, with SRC_G,
+// global memory through src(k); writes the padded buffer wb or, with DST_G, dst(k, v).
+template <typename C, int R, int N, int NS, int SIGN, bool SRC_G, bool DST_G, typename Src, typename Dst>
+__device__ __forceinline__ void fft_pass_ct(const C* rb, Src src, C* wb, Dst dst, const C* twp) {
+  using Rt = typename Cx<C>::R;
+  constexpr int NB = N / R, W = tw_width(R), IT = (NB + FTH - 1) / FTH;
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int j = it * FTH + (int)threadIdx.x;
+    if (NB % FTH != 0 && j >= NB) break;
+    const int q = j / NS, jm = j - q * NS;
+    C v[R];
+    const int pj = fpad(j);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if constexpr (SRC_G) v[r] = src(j + r * NB);
+      else v[r] = rb[ct_rd<NB>(pj, j, r)];
+    }
+    if constexpr (NS > 1) {
+      auto apply = [&](int r, C tr) {
+        if (SIGN > 0) tr.y = -tr.y;
+        v[r] = c_mul(v[r], tr);
+      };
+      if constexpr (std::is_same<C, float2>::value) {
+        const float4* tp = reinterpret_cast<const float4*>(twp + jm * W);
+#pragma unroll
+        for (int h = 0; h < W / 2; ++h) {  // a 16-byte pair per load, applied as it arrives
+          const float4 pr = __ldg(tp + h);
+          if (h > 0) apply(2 * h, make_float2(pr.x, pr.y));
+          if (2 * h + 1 < R) apply(2 * h + 1, make_float2(pr.z, pr.w));
+        }
+      } else {
+#pragma unroll
+        for (int r = 1; r < R; ++r) apply(r, ld_tw(twp + jm * W + r));
+      }
+    }
+    if constexpr (R == 2) {
+      dft2(v[0], v[1]);
+    } else if constexpr (R == 4) {
+      dft4(v[0], v[1], v[2], v[3], SIGN);
+    } else if constexpr (R == 8) {
+      dft8(v, SIGN);
+    } else {
+      static_assert(R == 3, "radix 2, 3, 4 or 8");
+      const C s1 = c_add(v[1], v[2]);
+      const C t2 = Cx<C>::make(v[0].x - Cx<C>::half() * s1.x, v[0].y - Cx<C>::half() * s1.y);
+      const C d = c_sub(v[1], v[2]);
+      const Rt sg = SIGN * Cx<C>::sqrt3_2();
+      const C x0 = c_add(v[0], s1);
+      v[1] = Cx<C>::make(t2.x - sg * d.y, t2.y + sg * d.x);
+      v[2] = Cx<C>::make(t2.x + sg * d.y, t2.y - sg * d.x);
+      v[0] = x0;
+    }
+    const int base = q * NS * R + jm;
+    const int pb = fpad(base);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if constexpr (DST_G) dst(base + r * NS, v[r]);
+      else wb[ct_wr<NS, R>(pb, base, r)] = v[r];
+    }
+  }
+}
+
+// Passes S.. of the length-N transform: pass S reads cur (global memory through src when
+// S = 0 and FIRST_G) and writes nxt (dst when it is the last pass and not LAST_SMEM); the next
+// pass swaps the two buffers.  Returns the shared buffer holding the result (LAST_SMEM).
+template <typename C, int N, int S, int SIGN, bool FIRST_G, bool LAST_SMEM, typename Src, typename Dst>
+__device__ __forceinline__ C* fft_run_ct(Src src, Dst dst, C* cur, C* nxt, const C* tw) {
+  constexpr int R = ct_rad(N, S), NS = ct_ns(N, S);
+  constexpr bool last = S == ct_nrad(N) - 1;
+  fft_pass_ct<C, R, N, NS, SIGN, FIRST_G && S == 0, last && !LAST_SMEM>(cur, src, nxt, dst, tw + ct_twoff(N, S));
+  __syncthreads();
+  if constexpr (last) return nxt;
+  else return fft_run_ct<C, N, S + 1, SIGN, FIRST_G, LAST_SMEM>(src, dst, nxt, cur, tw);
+}
+
+// the lengths with fixed-length kernels
+constexpr bool fft_fixed_len(int n) { return n == 384 || n == 768 || n == 1536; }
+
+
 __device__ __forceinline__ int fft_seg(const FftSegs& sg, int y) {
   return (y >= sg.start[1]) + (y >= sg.start[2]);
 }
 
 // synthesis: F[field][m][nlat] (m <= T) -> grid[field][nlat][nlon], two latitude rows per block
 // (row j0 in the real part, j0 + 1 in the imaginary part of one complex sequence)
-template <typename C>
+template <typename C, int N = 0>  // N > 0: the fixed-length passes of that length
 __device__ __forceinline__ void fft_synth_block(const FftSegs& sg, const FftPlan& fp, const C* __restrict__ tw, int T,
                                                 int nlat) {
   extern __shared__ __align__(16) unsigned char fsm[];
   using R = typename Cx<C>::R;
-  const int n = fp.n, np = fft_padded(n);
+  const int n = N ? N : fp.n, np = fft_padded(n);
   C* a = reinterpret_cast<C*>(fsm);
   C* b = a + np;
   const int s = fft_seg(sg, blockIdx.y), f = blockIdx.y - sg.start[s];
@@ -609,16 +735,17 @@ __device__ __forceinline__ void fft_synth_block(const FftSegs& sg, const FftPlan
     r0[k] = (double)v.x;
     r1[k] = (double)v.y;
   };
-  fft_run<C, false>(src, dst, b, a, fp, tw, +1);  // the first pass reads b and writes a
+  if constexpr (N > 0) fft_run_ct<C, N, 0, +1, false, false>(src, dst, b, a, tw);  // reads b, writes a first
+  else fft_run<C, false>(src, dst, b, a, fp, tw, +1);  // the first pass reads b and writes a
 }
 
 // analysis: grid[field][nlat][nlon] -> F[field][m][nlat] = (2 pi / n) sum_k f e^{-i m lambda_k}
-template <typename C>
+template <typename C, int N = 0>  // N > 0: the fixed-length passes of that length
 __device__ __forceinline__ void fft_anal_block(const FftSegs& sg, const FftPlan& fp, const C* __restrict__ tw, int T,
                                                int nlat) {
   extern __shared__ __align__(16) unsigned char fsm[];
   using R = typename Cx<C>::R;
-  const int n = fp.n, np = fft_padded(n);
+  const int n = N ? N : fp.n, np = fft_padded(n);
   C* a = reinterpret_cast<C*>(fsm);
   C* b = a + np;
   const int s = fft_seg(sg, blockIdx.y), f = blockIdx.y - sg.start[s];
@@ -627,7 +754,9 @@ __device__ __forceinline__ void fft_anal_block(const FftSegs& sg, const FftPlan&
   const double* r1 = r0 + n;
   auto src = [r0, r1](int k) -> C { return Cx<C>::make(R(__ldg(r0 + k)), R(__ldg(r1 + k))); };
   auto none = [](int, C) {};
-  const C* z = fft_run<C, true>(src, none, a, b, fp, tw, -1);
+  const C* z;
+  if constexpr (N > 0) z = fft_run_ct<C, N, 0, -1, true, true>(src, none, a, b, tw);
+  else z = fft_run<C, true>(src, none, a, b, fp, tw, -1);
   const R sc = R(3.14159265358979323846 / n);  // (2 pi / n) / 2, in the transform's precision
   double2* out = sg.F[s] + (size_t)f * (T + 1) * nlat;
   for (int m = threadIdx.x; m <= T; m += blockDim.x) {
@@ -641,20 +770,23 @@ __device__ __forceinline__ void fft_anal_block(const FftSegs& sg, const FftPlan&
 
 // FP32 transforms (tensor-core plans) keep six blocks per SM resident; FP64 ones are bound by
 // the FP64 pipe and keep their registers
+// (N > 0: the fixed-length passes; N = 0: the length from fp)
+template <int N>
 __global__ void __launch_bounds__(FTH, 6) k_fft_synth32(const __grid_constant__ FftSegs sg,
                                                         const __grid_constant__ FftPlan fp,
                                                         const float2* __restrict__ tw, int T, int nlat) {
-  fft_synth_block<float2>(sg, fp, tw, T, nlat);
+  fft_synth_block<float2, N>(sg, fp, tw, T, nlat);
 }
 __global__ void __launch_bounds__(FTH) k_fft_synth64(const __grid_constant__ FftSegs sg,
                                                      const __grid_constant__ FftPlan fp,
                                                      const double2* __restrict__ tw, int T, int nlat) {
   fft_synth_block<double2>(sg, fp, tw, T, nlat);
 }
+template <int N>
 __global__ void __launch_bounds__(FTH, 6) k_fft_anal32(const __grid_constant__ FftSegs sg,
                                                        const __grid_constant__ FftPlan fp,
                                                        const float2* __restrict__ tw, int T, int nlat) {
-  fft_anal_block<float2>(sg, fp, tw, T, nlat);
+  fft_anal_block<float2, N>(sg, fp, tw, T, nlat);
 }
 __global__ void __launch_bounds__(FTH) k_fft_anal64(const __grid_constant__ FftSegs sg,
                                                     const __grid_constant__ FftPlan fp,
@@ -665,16 +797,42 @@ __global__ void __launch_bounds__(FTH) k_fft_anal64(const __grid_constant__ FftS
 // double-float transforms (SH_DF plans): FP64 inputs and outputs, arithmetic on the FP32 pipe;
 // four blocks per SM, which their shared memory allows (at 76 registers only three fit: the
 // one-pass N(U) synthesis at T511 took 0.086 ms that way, 0.078 ms with four)
+template <int N>
 __global__ void __launch_bounds__(FTH, 4) k_fft_synth_df(const __grid_constant__ FftSegs sg,
                                                       const __grid_constant__ FftPlan fp,
                                                       const dfcx* __restrict__ tw, int T, int nlat) {
-  fft_synth_block<dfcx>(sg, fp, tw, T, nlat);
+  fft_synth_block<dfcx, N>(sg, fp, tw, T, nlat);
 }
+template <int N>
 __global__ void __launch_bounds__(FTH, 4) k_fft_anal_df(const __grid_constant__ FftSegs sg,
                                                      const __grid_constant__ FftPlan fp,
                                                      const dfcx* __restrict__ tw, int T, int nlat) {
-  fft_anal_block<dfcx>(sg, fp, tw, T, nlat);
+  fft_anal_block<dfcx, N>(sg, fp, tw, T, nlat);
 }
+
+// the instantiation for length n: fixed-length kernels for 384, 768, 1536, else the general one
+#define FFT_KERNEL_FAMILY(NAME, C)                                                        \
+  struct NAME##_fam {                                                                     \
+    using Fn = void (*)(FftSegs, FftPlan, const C*, int, int);                            \
+    static Fn pick(int n, bool fixed) {                                                   \
+      if (fixed && n == 1536) return NAME<1536>;                                          \
+      if (fixed && n == 768) return NAME<768>;                                            \
+      if (fixed && n == 384) return NAME<384>;                                            \
+      return NAME<0>;                                                                     \
+    }                                                                                     \
+    static cudaError_t limits(size_t bytes) {                                             \
+      cudaError_t e = raise_smem_limit(NAME<0>, bytes);                                   \
+      if (!e) e = raise_smem_limit(NAME<384>, bytes);                                     \
+      if (!e) e = raise_smem_limit(NAME<768>, bytes);                                     \
+      if (!e) e = raise_smem_limit(NAME<1536>, bytes);                                    \
+      return e;                                                                           \
+    }                                                                                     \
+  };
+FFT_KERNEL_FAMILY(k_fft_synth32, float2)
+FFT_KERNEL_FAMILY(k_fft_anal32, float2)
+FFT_KERNEL_FAMILY(k_fft_synth_df, dfcx)
+FFT_KERNEL_FAMILY(k_fft_anal_df, dfcx)
+#undef FFT_KERNEL_FAMILY
 
 // Gauss-Legendre nodes (north to south) and weights: Newton iteration on P_n
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
@@ -791,6 +949,7 @@ struct sh_plan {
   float4* d_twdf = nullptr; // the same as double-float pairs (re.hi, re.lo, im.hi, im.lo), SH_DF
   bool fft32 = false;
   bool fftdf = false;       // double-float FFT (SH_DF)
+  bool fft_fixed = false;   // FP32 / double-float FFT by the fixed-length kernels
   double2* d_F = nullptr;   // Fourier workspace [2 * max_fields][T+1][nlat]
   FftPlan fp{};
   TcLegendre* tc = nullptr;  // tensor-core Legendre state (SH_TF32 / SH_BF16 / SH_TF32X3)
@@ -839,6 +998,12 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
   };
   if (!fft_factor(d.nlon, p->fp)) return bail(fail(REXI_EINVAL, "nlon = %d is not 2^p 3^q", d.nlon));
   if (fft_smem(p) > 200 * 1024) return bail(fail(REXI_EINVAL, "nlon = %d too large", d.nlon));
+  if ((p->fft32 || p->fftdf) && fft_fixed_len(d.nlon)) {  // their passes and twiddle offsets are fft_factor's
+    bool same = p->fp.nrad == ct_nrad(d.nlon);
+    for (int s = 0; same && s < p->fp.nrad; ++s)
+      same = p->fp.rad[s] == ct_rad(d.nlon, s) && p->fp.twoff[s] == ct_twoff(d.nlon, s);
+    p->fft_fixed = same;
+  }
   gauss_legendre(d.nlat, p->mu, p->w);
   std::vector<double> wq(p->nh);
   for (int j = 0; j < p->nh; ++j) wq[j] = p->w[j] / ((1.0 - p->mu[j]) * (1.0 + p->mu[j]));
@@ -925,14 +1090,14 @@ extern "C" int sh_plan_create(const sh_plan_desc* desc, sh_plan** out) {
     p->pb.ja = p->ja.data();
   }
   if (p->fft32) {
-    e = cudaFuncSetAttribute(k_fft_synth32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p));
-    if (!e) e = cudaFuncSetAttribute(k_fft_anal32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p));
+    e = k_fft_synth32_fam::limits(fft_smem(p));
+    if (!e) e = k_fft_anal32_fam::limits(fft_smem(p));
   } else if (p->fftdf) {
-    e = cudaFuncSetAttribute(k_fft_synth_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p));
-    if (!e) e = cudaFuncSetAttribute(k_fft_anal_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p));
+    e = k_fft_synth_df_fam::limits(fft_smem(p));
+    if (!e) e = k_fft_anal_df_fam::limits(fft_smem(p));
   } else {
-    e = cudaFuncSetAttribute(k_fft_synth64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p));
-    if (!e) e = cudaFuncSetAttribute(k_fft_anal64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(p));
+    e = raise_smem_limit(k_fft_synth64, fft_smem(p));
+    if (!e) e = raise_smem_limit(k_fft_anal64, fft_smem(p));
   }
   if (e) return bail(cuda_fail(e, "cudaFuncSetAttribute(fft)"));
   if (d.precision == SH_DF) {
@@ -1010,11 +1175,13 @@ static FftSegs make_segs(std::initializer_list<std::tuple<double2*, double*, int
 static void launch_fft_synth(sh_plan* p, const FftSegs& sg) {
   const int ph = p->prof.begin(4);
   const dim3 grid(p->d.nlat / 2, sg.start[3]);
+  const int n = p->d.nlon;
   if (p->fft32)
-    k_fft_synth32<<<grid, FTH, fft_smem(p), p->stream>>>(sg, p->fp, p->d_tw32, p->d.T, p->d.nlat);
+    k_fft_synth32_fam::pick(n, p->fft_fixed)<<<grid, FTH, fft_smem(p), p->stream>>>(sg, p->fp, p->d_tw32, p->d.T,
+                                                                                   p->d.nlat);
   else if (p->fftdf)
-    k_fft_synth_df<<<grid, FTH, fft_smem(p), p->stream>>>(sg, p->fp, reinterpret_cast<const dfcx*>(p->d_twdf),
-                                                          p->d.T, p->d.nlat);
+    k_fft_synth_df_fam::pick(n, p->fft_fixed)<<<grid, FTH, fft_smem(p), p->stream>>>(
+        sg, p->fp, reinterpret_cast<const dfcx*>(p->d_twdf), p->d.T, p->d.nlat);
   else
     k_fft_synth64<<<grid, FTH, fft_smem(p), p->stream>>>(sg, p->fp, p->d_tw, p->d.T, p->d.nlat);
   p->prof.end(ph);
@@ -1022,11 +1189,13 @@ static void launch_fft_synth(sh_plan* p, const FftSegs& sg) {
 static void launch_fft_anal(sh_plan* p, const FftSegs& sg) {
   const int ph = p->prof.begin(4);
   const dim3 grid(p->d.nlat / 2, sg.start[3]);
+  const int n = p->d.nlon;
   if (p->fft32)
-    k_fft_anal32<<<grid, FTH, fft_smem(p), p->stream>>>(sg, p->fp, p->d_tw32, p->d.T, p->d.nlat);
+    k_fft_anal32_fam::pick(n, p->fft_fixed)<<<grid, FTH, fft_smem(p), p->stream>>>(sg, p->fp, p->d_tw32, p->d.T,
+                                                                                  p->d.nlat);
   else if (p->fftdf)
-    k_fft_anal_df<<<grid, FTH, fft_smem(p), p->stream>>>(sg, p->fp, reinterpret_cast<const dfcx*>(p->d_twdf),
-                                                         p->d.T, p->d.nlat);
+    k_fft_anal_df_fam::pick(n, p->fft_fixed)<<<grid, FTH, fft_smem(p), p->stream>>>(
+        sg, p->fp, reinterpret_cast<const dfcx*>(p->d_twdf), p->d.T, p->d.nlat);
   else
     k_fft_anal64<<<grid, FTH, fft_smem(p), p->stream>>>(sg, p->fp, p->d_tw, p->d.T, p->d.nlat);
   p->prof.end(ph);

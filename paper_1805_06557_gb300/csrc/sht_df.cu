@@ -403,17 +403,14 @@ static int df_smem_attr(int nh, int T) {
   cudaError_t e = cudaSuccess;
 #define DF_ATTR(NS, NV)                                                                                    \
   if (!e)                                                                                                 \
-    e = cudaFuncSetAttribute(k_df_anal<NS, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
-                             (int)df_anal_smem<NS, NV>(nh));
+    e = raise_smem_limit(k_df_anal<NS, NV>, df_anal_smem<NS, NV>(nh));
   DF_ATTR(1, 0) DF_ATTR(2, 0) DF_ATTR(0, 1) DF_ATTR(1, 1) DF_ATTR(2, 1) DF_ATTR(0, 2) DF_ATTR(1, 2) DF_ATTR(2, 2)
 #undef DF_ATTR
 #define DF_SATTR(NF)                                                                                       \
   if (!e)                                                                                                 \
-    e = cudaFuncSetAttribute(k_df_synth<NF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
-                             (int)df_synth_smem<NF>(T));                                                  \
+    e = raise_smem_limit(k_df_synth<NF, 1>, df_synth_smem<NF>(T));                                       \
   if (!e)                                                                                                 \
-    e = cudaFuncSetAttribute(k_df_synth<NF, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
-                             (int)df_synth_smem<NF>(T));
+    e = raise_smem_limit(k_df_synth<NF, 5>, df_synth_smem<NF>(T));
   DF_SATTR(1) DF_SATTR(2) DF_SATTR(3) DF_SATTR(4)
 #undef DF_SATTR
   return e ? cuda_fail(e, "cudaFuncSetAttribute(k_df_*)") : REXI_OK;

@@ -180,3 +180,26 @@ def test_double_float_magnitudes(env, scale):
     for name, a, b in zip(("grid", "U", "V", "spec", "div", "curl"), out["df"], out["fp64"]):
         assert np.all(np.isfinite(a)), name
         assert _rel(a, b) < 1e-12, (name, _rel(a, b))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df", "tf32x3"])
+def test_plans_of_different_sizes_coexist(env, prec):
+    """A small plan created after a large one leaves the large one working: the kernels'
+    shared-memory limits are process-wide and only grow (the double-float FFT of 1536 points
+    needs 55 KB, the FP32 one 28 KB; a T7 plan's FFT needs under 2 KB).  Round trip of the
+    T511 plan after the T7 plan exists, against the band-limited input (exact for the FP64 and
+    double-float plans, split TF32 within its 4u = 3.8e-6 per-transform bound, twice)."""
+    torch, rexi = env
+    big = rexi.ShPlan(511, 768, 1536, A, precision=prec, max_fields=2)
+    small = rexi.ShPlan(7, 12, 24, A, precision=prec, max_fields=2)
+    for p, (T, nlat, nlon) in ((small, (7, 12, 24)), (big, (511, 768, 1536)), (small, (7, 12, 24))):
+        c = _spec(T, 5, 2)
+        g = torch.empty(2, nlat, nlon, dtype=torch.float64, device="cuda")
+        back = torch.empty(2, osht.nlm(T), dtype=torch.complex128, device="cuda")
+        p.synthesis(torch.from_numpy(c).cuda(), g, 2)
+        p.analysis(g, back, 2)
+        p.check()
+        err = _rel(back.cpu().numpy(), c)
+        assert err < (1e-12 if prec in ("fp64", "df") else 2 * 3.8e-6), (T, err)
+    small.close()
+    big.close()

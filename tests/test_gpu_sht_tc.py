@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 A = 6.37122e6
 BOUND = {"tf32": 4 * 2.0 ** -11, "bf16": 4 * 2.0 ** -8, "tf32x3": 4 * 2.0 ** -20}
-SIZES = [(31, 48, 96), (127, 192, 384), (511, 768, 1536)]
+SIZES = [(31, 48, 96), (127, 192, 384), (255, 384, 768), (511, 768, 1536)]
 
 
 @pytest.fixture(scope="module")
