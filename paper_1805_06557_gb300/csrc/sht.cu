@@ -20,6 +20,7 @@
 
 #include "../../include/sht.h"
 #include "common.cuh"
+#include "cvt.cuh"
 #include "df.cuh"
 #include "sht_df.cuh"
 #include "sht_tc.cuh"
@@ -406,6 +407,13 @@ template <> struct Cx<dfcx> {
   static __device__ __forceinline__ dfr half() { return dfr(0.5f, 0.f); }
   static __device__ __forceinline__ dfr sqrt3_2() { return dfr(0x1.bb67aep-1f, 0x1.0b0996p-26f); }
 };
+// FP64 grid and Fourier values into the transform's arithmetic and back: FP32 plans convert on
+// the integer pipe (cvt.cuh; the F2F instructions would occupy the scarce FP64 pipe)
+template <typename R> __device__ __forceinline__ R from_f64(double d) { return R(d); }
+template <> __device__ __forceinline__ float from_f64<float>(double d) { return cvt::f64_to_f32(d); }
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return cvt::f32_to_f64(x); }
+__device__ __forceinline__ double to_f64(dfr x) { return (double)x; }
 // one twiddle-table entry
 __device__ __forceinline__ double2 ld_tw(const double2* p) { return __ldg(p); }
 __device__ __forceinline__ dfcx ld_tw(const dfcx* p) {
@@ -719,7 +727,7 @@ __device__ __forceinline__ void fft_synth_block(const FftSegs& sg, const FftPlan
   for (int m = threadIdx.x; m <= T; m += blockDim.x) {
     const D4 AB = *reinterpret_cast<const D4*>(in + (size_t)m * nlat + j0);
     // in the transform's own precision: FP32 plans convert first and combine in FP32
-    const R ax = R(AB.x), ay = R(AB.y), bx = R(AB.z), by = R(AB.w);
+    const R ax = from_f64<R>(AB.x), ay = from_f64<R>(AB.y), bx = from_f64<R>(AB.z), by = from_f64<R>(AB.w);
     if (m == 0) {
       b[0] = Cx<C>::make(ax, bx);
     } else {
@@ -732,8 +740,8 @@ __device__ __forceinline__ void fft_synth_block(const FftSegs& sg, const FftPlan
   const C* bin = b;
   auto src = [bin](int k) -> C { return bin[fpad(k)]; };
   auto dst = [r0, r1](int k, C v) {
-    r0[k] = (double)v.x;
-    r1[k] = (double)v.y;
+    r0[k] = to_f64(v.x);
+    r1[k] = to_f64(v.y);
   };
   if constexpr (N > 0) fft_run_ct<C, N, 0, +1, false, false>(src, dst, b, a, tw);  // reads b, writes a first
   else fft_run<C, false>(src, dst, b, a, fp, tw, +1);  // the first pass reads b and writes a
@@ -752,7 +760,7 @@ __device__ __forceinline__ void fft_anal_block(const FftSegs& sg, const FftPlan&
   const int j0 = 2 * blockIdx.x;
   const double* r0 = sg.g[s] + ((size_t)f * nlat + j0) * n;
   const double* r1 = r0 + n;
-  auto src = [r0, r1](int k) -> C { return Cx<C>::make(R(__ldg(r0 + k)), R(__ldg(r1 + k))); };
+  auto src = [r0, r1](int k) -> C { return Cx<C>::make(from_f64<R>(__ldg(r0 + k)), from_f64<R>(__ldg(r1 + k))); };
   auto none = [](int, C) {};
   const C* z;
   if constexpr (N > 0) z = fft_run_ct<C, N, 0, -1, true, true>(src, none, a, b, tw);
@@ -763,8 +771,8 @@ __device__ __forceinline__ void fft_anal_block(const FftSegs& sg, const FftPlan&
     const C zm = z[fpad(m)], zn = z[fpad(m == 0 ? 0 : n - m)];
     // A = (Z_m + conj(Z_{n-m})) / 2,  B = (Z_m - conj(Z_{n-m})) / (2i); one aligned 32-byte store
     *reinterpret_cast<D4*>(out + (size_t)m * nlat + j0) =
-        D4{(double)(sc * (zm.x + zn.x)), (double)(sc * (zm.y - zn.y)), (double)(sc * (zm.y + zn.y)),
-           (double)(-sc * (zm.x - zn.x))};
+        D4{to_f64(sc * (zm.x + zn.x)), to_f64(sc * (zm.y - zn.y)), to_f64(sc * (zm.y + zn.y)),
+           to_f64(-sc * (zm.x - zn.x))};
   }
 }
 
