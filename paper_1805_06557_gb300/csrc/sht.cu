@@ -407,13 +407,19 @@ template <> struct Cx<dfcx> {
   static __device__ __forceinline__ dfr half() { return dfr(0.5f, 0.f); }
   static __device__ __forceinline__ dfr sqrt3_2() { return dfr(0x1.bb67aep-1f, 0x1.0b0996p-26f); }
 };
-// FP64 grid and Fourier values into the transform's arithmetic and back: FP32 plans convert on
-// the integer pipe (cvt.cuh; the F2F instructions would occupy the scarce FP64 pipe)
+// FP64 grid and Fourier values into the transform's arithmetic and back: FP32 and double-float
+// plans convert on the integer pipe (cvt.cuh; the F2F instructions would occupy the scarce FP64
+// pipe).  The double-float split is the same as dfr(double): hi = d rounded to FP32, lo = the
+// exact FP64 difference d - hi rounded to FP32; one FP64 subtraction each way remains.
 template <typename R> __device__ __forceinline__ R from_f64(double d) { return R(d); }
 template <> __device__ __forceinline__ float from_f64<float>(double d) { return cvt::f64_to_f32(d); }
+template <> __device__ __forceinline__ dfr from_f64<dfr>(double d) {
+  const float h = cvt::f64_to_f32(d);
+  return dfr(h, cvt::f64_to_f32(d - cvt::f32_to_f64(h)));
+}
 __device__ __forceinline__ double to_f64(double x) { return x; }
 __device__ __forceinline__ double to_f64(float x) { return cvt::f32_to_f64(x); }
-__device__ __forceinline__ double to_f64(dfr x) { return (double)x; }
+__device__ __forceinline__ double to_f64(dfr x) { return cvt::f32_to_f64(x.hi) + cvt::f32_to_f64(x.lo); }
 // one twiddle-table entry
 __device__ __forceinline__ double2 ld_tw(const double2* p) { return __ldg(p); }
 __device__ __forceinline__ dfcx ld_tw(const dfcx* p) {
