@@ -7,8 +7,8 @@
 * The flux forms -div(Phi' V), -div(zeta V), k.curl(zeta V) equal their advective forms
   -(V.grad q + q delta) and zeta^2 + (dq/dx v - dq/dy u), computed through a different
   route (scalar gradients on the grid), to rounding.
-* Strang ver1 with REXI converges at 2nd order to a small-step RK4 reference (the paper's
-  own reference is RK4 with a tiny step, Sec. 5).
+* Strang ver1 and ver0 with REXI converge at 2nd order to a small-step RK4 reference (the
+  paper's own reference is RK4 with a tiny step, Sec. 5).
 """
 import math
 
@@ -100,6 +100,27 @@ def test_strang_ver1_second_order():
         U = U0
         for _ in range(int(round(t_end / dt))):
             U = swe.strang_ver1(U, g, dt, OM, PB, z, w)
+        errs.append(float(np.max(rexi.rel_l2(U, ref, T))))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(1.7 < r < 2.5 for r in rates), (errs, rates)
+
+
+def test_strang_ver0_second_order():
+    """Version 0 of the split (Sec. 4.4: L^{dt/2} N^{dt} L^{dt/2}, REXI coefficients for dt/2)
+    converges at 2nd order to the same RK4 reference as version 1."""
+    T, nlat, nlon = 15, 24, 48
+    g = sht.Grid(T, nlat, nlon, A)
+    U0 = syn.balanced_state(T, 2, urms=40.0)
+    U0[2] = syn.gaussian_state(T, 8, scales=(0, 0, 2e-6))[2]
+    t_end = 4 * 1800.0
+    ref = swe.rk4_full(U0, g, t_end, 240, OM, PB)
+    errs = []
+    for dt in (1800.0, 900.0, 450.0):
+        X = rexi.spectrum_bound(T, 0.5 * dt, OM, A, PB)
+        z, w = coeffs.rexi_coefficients(128, min(6.0, 1.6 * X), 1.6 * X)
+        U = U0
+        for _ in range(int(round(t_end / dt))):
+            U = swe.strang_ver0(U, g, dt, OM, PB, z, w)
         errs.append(float(np.max(rexi.rel_l2(U, ref, T))))
     rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert all(1.7 < r < 2.5 for r in rates), (errs, rates)
